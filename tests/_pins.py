@@ -1,0 +1,205 @@
+"""Checks that pin the oracle to facts fixed outside it.
+
+Each function returns an error measure (0 when the oracle is right); the pin tests assert it
+is small and the planted-mistake tests assert it is large once a mistake is put in the oracle.
+Expected values here are computed from first principles with their own formulas (Cartesian
+G = 2 pi A^{-1} m, explicit loops), never by calling the oracle routine under test.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+import oracle
+import workloads
+
+
+def g_cart(lattice, m) -> np.ndarray:
+    """G for Miller triple m from a_i . G = 2 pi m_i (solve, not the reciprocal matrix)."""
+    return 2.0 * math.pi * np.linalg.solve(np.asarray(lattice, dtype=np.float64), np.asarray(m, dtype=np.float64))
+
+
+def tiny_problem(lattice=None, k=(0.0, 0.0, 0.0), ecut=1.2, fft=(7, 8, 9), nat=2, seed=11, dense_d=False):
+    """Small cell with a non-cubic box and (optionally) a full Hermitian D, for brute force."""
+    if lattice is None:
+        lattice = 0.5 * 9.0 * np.array([[0.0, 1.0, 1.0], [1.0, 0.0, 1.0], [1.0, 1.0, 0.0]])
+    p = workloads.small_cell(ecut=ecut, nat=nat, fft=fft, seed=seed, k=k, lattice=lattice)
+    k = np.asarray(k, dtype=np.float64)
+    miller = oracle.gsphere.gsphere(p.lattice, p.ecut, k)
+    vr = workloads.vloc_r(p.lattice, p.atoms, p.fft)
+    beta = workloads.beta(p.lattice, p.atoms, k, miller)
+    if dense_d:
+        rng = np.random.default_rng(seed + 1)
+        a = rng.standard_normal((len(beta), len(beta))) + 1j * rng.standard_normal((len(beta), len(beta)))
+        d = 0.25 * (a + a.conj().T)
+    else:
+        d = workloads.dmat(len(p.atoms))
+    return p, k, miller, vr, beta, d
+
+
+def bruteforce_hpsi(lattice, k, miller, fft, vr, beta, dmat, psi) -> np.ndarray:
+    """H psi from explicit sums with Cartesian G.r_j (no FFT, no index arithmetic)."""
+    lat = np.asarray(lattice, dtype=np.float64)
+    n1, n2, n3 = fft
+    r = []
+    for j1 in range(n1):
+        for j2 in range(n2):
+            for j3 in range(n3):
+                r.append(j1 / n1 * lat[0] + j2 / n2 * lat[1] + j3 / n3 * lat[2])
+    r = np.array(r)
+    v = np.asarray(vr).reshape(-1)
+    g = np.array([g_cart(lat, m) for m in miller])
+    phase = np.exp(1j * (g @ r.T))                           # [npw][N_r], e^{+i G.r_j}
+    out = np.empty_like(psi)
+    q = np.asarray(k)[None, :] + g
+    t = 0.5 * np.sum(q * q, axis=1)
+    for b in range(psi.shape[0]):
+        psir = psi[b] @ phase                                # sum_G psi(G) e^{iG.r}
+        vpsi = (np.conj(phase) @ (v * psir)) / len(r)        # N^{-1} sum_j e^{-iG.r} V psi
+        nl = np.zeros(len(miller), dtype=np.complex128)
+        for p_ in range(beta.shape[0]):
+            for q_ in range(beta.shape[0]):
+                if dmat[p_, q_] != 0:
+                    nl += beta[p_] * dmat[p_, q_] * np.sum(np.conj(beta[q_]) * psi[b])
+        out[b] = t * psi[b] + vpsi + nl
+    return out
+
+
+def gaussian_vtilde_analytic(lattice, atoms, qm) -> np.ndarray:
+    """Fourier coefficient of the periodic Gaussian wells at G = q (Miller), Omega^{-1} int e^{-iG.r} V.
+
+    int -2 exp(-r^2 / 2) e^{-iG.r} d^3r = -2 (2 pi)^{3/2} exp(-G^2/2); images make it a lattice sum.
+    """
+    lat = np.asarray(lattice, dtype=np.float64)
+    omega = abs(np.linalg.det(lat))
+    out = []
+    for m in np.atleast_2d(qm):
+        g = g_cart(lat, m)
+        s = sum(np.exp(-1j * (g @ ra)) for ra in atoms)
+        out.append(workloads.V_DEPTH * (2.0 * math.pi * workloads.V_SIGMA2) ** 1.5 / omega
+                   * math.exp(-0.5 * workloads.V_SIGMA2 * (g @ g)) * s)
+    return np.array(out)
+
+
+def rel(a, b) -> float:
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300))
+
+
+# --- the pins, as error measures -----------------------------------------------------------
+
+def pin_bruteforce(seed=11, dense_d=True, k=(0.13, -0.21, 0.07)) -> float:
+    p, k, miller, vr, beta, d = tiny_problem(k=k, seed=seed, dense_d=dense_d)
+    psi = workloads.random_block(len(miller), 3, seed)
+    ref = bruteforce_hpsi(p.lattice, k, miller, p.fft, vr, beta, d, psi)
+    got = oracle.hamiltonian.hpsi(p.lattice, k, miller, p.fft, vr, beta, d, psi)
+    return rel(got, ref)
+
+
+def pin_dense_vs_fft(seed=5, dense_d=True) -> float:
+    p, k, miller, vr, beta, d = tiny_problem(ecut=2.0, fft=(12, 13, 14), k=(0.1, 0.2, -0.3), seed=seed, dense_d=dense_d)
+    psi = workloads.random_block(len(miller), 4, seed)
+    h = oracle.hamiltonian.dense_h(p.lattice, k, miller, p.fft, vr, beta, d)
+    return rel(oracle.hamiltonian.hpsi(p.lattice, k, miller, p.fft, vr, beta, d, psi), (h @ psi.T).T)
+
+
+def pin_vtilde_analytic() -> float:
+    """Direct-DFT V~(q) against the closed-form Gaussian transform, |q_i| <= 3 (aliasing < e^-150)."""
+    p = workloads.config1()
+    vr = workloads.vloc_r(p.lattice, p.atoms, p.fft)
+    qs = np.array([(a, b, c) for a in range(-3, 4) for b in range(-3, 4) for c in range(-3, 4)])
+    got = oracle.hamiltonian.vtilde_direct(vr, qs)
+    ref = gaussian_vtilde_analytic(p.lattice, p.atoms, qs)
+    return float(np.max(np.abs(got - ref)))
+
+
+def pin_plane_wave_column(g0=(1, -2, 1)) -> float:
+    """H|k+G0> restricted to the local term is the column V~(G - G0) of the analytic transform."""
+    p = workloads.config1()
+    k = np.zeros(3)
+    miller = oracle.gsphere.gsphere(p.lattice, p.ecut, k)
+    vr = workloads.vloc_r(p.lattice, p.atoms, p.fft)
+    i0 = int(np.where((miller == np.array(g0)).all(axis=1))[0][0])
+    psi = np.zeros((1, len(miller)), dtype=np.complex128)
+    psi[0, i0] = 1.0
+    col = oracle.hamiltonian.local_term(vr, miller, p.fft, psi)[0]
+    sel = np.abs(miller - np.array(g0)).max(axis=1) <= 3
+    ref = gaussian_vtilde_analytic(p.lattice, p.atoms, miller[sel] - np.array(g0))
+    return float(np.max(np.abs(col[sel] - ref)))
+
+
+def pin_free_electron(k=(0.05, -0.11, 0.2)) -> tuple:
+    """V = 0, no projectors: H psi = T psi exactly; eigenvalues = sorted |k+G|^2/2 from Cartesian G."""
+    lat = 0.5 * 10.2 * np.array([[0.0, 1.0, 1.0], [1.0, 0.0, 1.0], [1.0, 1.0, 0.0]])
+    k = np.asarray(k)
+    miller = oracle.gsphere.gsphere(lat, 3.0, k)
+    fft = (24, 24, 24)
+    vr = np.zeros(fft)
+    beta = np.zeros((0, len(miller)), dtype=np.complex128)
+    d = np.zeros((0, 0), dtype=np.complex128)
+    t = np.array([0.5 * float(np.sum((k + g_cart(lat, m)) ** 2)) for m in miller])
+    psi = workloads.random_block(len(miller), 3, 4)
+    hp = oracle.hamiltonian.hpsi(lat, k, miller, fft, vr, beta, d, psi)
+    e_hpsi = float(np.max(np.abs(hp - t[None, :] * psi)))
+    h = oracle.hamiltonian.dense_h(lat, k, miller, fft, vr, beta, d)
+    ev = oracle.eigen.lowest_dense(h, 20)
+    e_eig = float(np.max(np.abs(ev - np.sort(t)[:20])))
+    return e_hpsi, e_eig
+
+
+def pin_constant_potential(c=-0.7) -> float:
+    """V(r) = c: the local term is c psi up to FFT rounding (checks the 1/N_r)."""
+    p = workloads.config1()
+    k = np.zeros(3)
+    miller = oracle.gsphere.gsphere(p.lattice, p.ecut, k)
+    psi = workloads.random_block(len(miller), 2, 9)
+    loc = oracle.hamiltonian.local_term(np.full(p.fft, c), miller, p.fft, psi)
+    return rel(loc, c * psi)
+
+
+def pin_hermiticity(seed=3) -> float:
+    p = workloads.config1()
+    k = np.zeros(3)
+    miller = oracle.gsphere.gsphere(p.lattice, p.ecut, k)
+    vr = workloads.vloc_r(p.lattice, p.atoms, p.fft)
+    beta = workloads.beta(p.lattice, p.atoms, k, miller)
+    rng = np.random.default_rng(seed)
+    a = rng.standard_normal((8, 8)) + 1j * rng.standard_normal((8, 8))
+    d = 0.25 * (a + a.conj().T)
+    x = workloads.random_block(len(miller), 2, seed)
+    hx = oracle.hamiltonian.hpsi(p.lattice, k, miller, p.fft, vr, beta, d, x)
+    lhs = np.vdot(x[0], hx[1])           # <phi|H psi>
+    rhs = np.conj(np.vdot(x[1], hx[0]))  # <psi|H phi>^*
+    return abs(lhs - rhs) / abs(lhs)
+
+
+def secular_residual(d_s=-0.8, nev=12) -> float:
+    """V = 0, one s projector (complex phases): each eigenvalue is a kinetic level or a root of
+    1 = d sum_G |beta(G)|^2 / (lambda - T_G) (rank-one update of a diagonal matrix)."""
+    lat = np.diag([9.0, 9.0, 9.0])
+    k = np.array([0.1, 0.03, -0.07])
+    miller = oracle.gsphere.gsphere(lat, 2.5, k)
+    fft = (24, 24, 24)
+    atoms = np.array([[1.3, 2.1, 0.4]])
+    beta = workloads.beta(lat, atoms, k, miller)[:1]
+    d = np.array([[d_s]], dtype=np.complex128)
+    h = oracle.hamiltonian.dense_h(lat, k, miller, fft, np.zeros(fft), beta, d)
+    ev = oracle.eigen.lowest_dense(h, nev)
+    t = np.array([0.5 * float(np.sum((k + g_cart(lat, m)) ** 2)) for m in miller])
+    w = np.abs(beta[0]) ** 2
+    worst = 0.0
+    for lam in ev:
+        gap = np.min(np.abs(lam - t))
+        if gap < 1e-9:
+            continue
+        worst = max(worst, abs(1.0 - d_s * np.sum(w / (lam - t))))
+    return worst
+
+
+def eigs_dense_of(lattice, atoms, ecut, fft, k, nbnd):
+    k = np.asarray(k, dtype=np.float64)
+    miller = oracle.gsphere.gsphere(lattice, ecut, k)
+    vr = workloads.vloc_r(lattice, atoms, fft)
+    beta = workloads.beta(lattice, atoms, k, miller)
+    h = oracle.hamiltonian.dense_h(lattice, k, miller, fft, vr, beta, workloads.dmat(len(atoms)))
+    return oracle.eigen.lowest_dense(h, nbnd)

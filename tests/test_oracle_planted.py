@@ -1,0 +1,105 @@
+"""Plant plausible mistakes in the oracle (on the CPU) and check that some pin catches each one."""
+import numpy as np
+import pytest
+import scipy.fft
+
+import oracle
+import oracle.hamiltonian as H
+import oracle.gsphere as GS
+import oracle.davidson as DV
+import _pins
+
+
+def _fwd_wrong_sign(phi_r, miller, fft):
+    idx = H.box_index(miller, fft)
+    full = scipy.fft.ifftn(phi_r, axes=(1, 2, 3), norm="backward")     # e^{+i} with 1/N
+    return full[(slice(None),) + idx]
+
+
+def _fwd_no_norm(phi_r, miller, fft):
+    idx = H.box_index(miller, fft)
+    full = scipy.fft.fftn(phi_r, axes=(1, 2, 3), norm="backward")      # drops the 1/N_r
+    return full[(slice(None),) + idx]
+
+
+def _calbec_no_conj(beta, psi):
+    return beta @ psi.T
+
+
+def _nonlocal_dt(beta, dmat, psi):
+    return ((dmat.T @ (np.conj(beta) @ psi.T)).T) @ beta
+
+
+def _box_swapped(miller, fft):
+    m = np.asarray(miller)
+    return (np.mod(m[:, 0], fft[0]), np.mod(m[:, 2], fft[1]), np.mod(m[:, 1], fft[2]))
+
+
+def _kinetic_no_half(lattice, k, miller):
+    q = GS.kplusg(lattice, k, miller)
+    return np.sum(q * q, axis=1)
+
+
+def _vtilde_plus(vr, q):
+    return np.conj(oracle.hamiltonian.__dict__["_orig_vtilde"](vr, q))
+
+
+def _precondition_flipped(g, hdiag, eps, tau=0.1):
+    return g / DV.clamp_denominator(np.asarray(eps)[:, None] - np.asarray(hdiag)[None, :], tau)
+
+
+def _gsphere_gamma_only(lattice, ecut, k):
+    return _orig_gsphere(lattice, ecut, np.zeros(3))
+
+
+_orig_gsphere = GS.gsphere
+
+
+@pytest.mark.parametrize("target,attr,bad,pin,thresh", [
+    (H, "to_reciprocal", _fwd_wrong_sign, "bruteforce", 1e-3),
+    (H, "to_reciprocal", _fwd_wrong_sign, "pwcol", 1e-3),
+    (H, "to_reciprocal", _fwd_no_norm, "constV", 1e-3),
+    (H, "calbec", _calbec_no_conj, "bruteforce", 1e-3),
+    (H, "calbec", _calbec_no_conj, "herm", 1e-3),
+    (H, "nonlocal_term", _nonlocal_dt, "bruteforce", 1e-3),
+    (H, "box_index", _box_swapped, "bruteforce", 1e-3),
+    (H, "kinetic", _kinetic_no_half, "free", 1e-3),
+    (H, "vtilde_direct", _vtilde_plus, "vtilde", 1e-4),
+    (DV, "precondition", _precondition_flipped, "precond", 1e-3),
+])
+def test_planted_mistake_is_caught(monkeypatch, target, attr, bad, pin, thresh):
+    monkeypatch.setattr(H, "_orig_vtilde", H.vtilde_direct, raising=False)
+    monkeypatch.setattr(target, attr, bad)
+    if pin == "bruteforce":
+        err = _pins.pin_bruteforce()
+    elif pin == "pwcol":
+        err = _pins.pin_plane_wave_column()
+    elif pin == "constV":
+        err = _pins.pin_constant_potential()
+    elif pin == "herm":
+        err = _pins.pin_hermiticity()
+    elif pin == "free":
+        err = max(_pins.pin_free_electron())
+    elif pin == "vtilde":
+        err = _pins.pin_vtilde_analytic()
+    elif pin == "precond":
+        hd = np.linspace(0.0, 5.0, 50)
+        psi = np.ones((1, 50), dtype=np.complex128)
+        eps = np.array([1.0])
+        dpsi = DV.precondition(DV.residuals(hd[None, :] * psi, psi, eps), hd, eps)
+        mask = np.abs(hd - 1.0) >= 0.1
+        err = float(np.max(np.abs(dpsi[0, mask] - 1.0)))
+    else:
+        raise AssertionError(pin)
+    assert err > thresh, f"pin {pin} missed a planted mistake in {attr}: err={err}"
+
+
+def test_planted_gsphere_k_shift_is_caught(monkeypatch):
+    monkeypatch.setattr(GS, "gsphere", _gsphere_gamma_only)
+    lat = 0.5 * 9.0 * np.array([[0.0, 1, 1], [1, 0, 1], [1, 1, 0]])
+    k = np.array([0.13, -0.21, 0.07])
+    got = GS.gsphere(lat, 4.0, k)
+    ok = all(0.5 * float(np.sum((k + _pins.g_cart(lat, m)) ** 2)) <= 4.0 for m in got)
+    count = sum(1 for m1 in range(-8, 9) for m2 in range(-8, 9) for m3 in range(-8, 9)
+                if 0.5 * float(np.sum((k + _pins.g_cart(lat, (m1, m2, m3))) ** 2)) <= 4.0)
+    assert not (ok and count == len(got))
