@@ -1,0 +1,168 @@
+/*
+ * hpsi.h -- plane-wave H|psi> and block-Davidson eigensolver on one GB300 (sm_103a).
+ *
+ * C ABI of libhpsi.so.  The operator is the Kohn-Sham Hamiltonian at fixed potential in a
+ * plane-wave basis (paper Sec. 3; KS equation of App. A.1), available as an operator that
+ * returns H|psi> for any block of states (App. A.2, Eq. (diag), with S = I for
+ * norm-conserving separable projectors):
+ *
+ *     (H psi)(G) = |k+G|^2/2 psi(G)                                   kinetic (diagonal)
+ *                + N_r^-1 sum_j e^{-iG.r_j} V(r_j) sum_G' e^{+iG'.r_j} psi(G')   local, via 3-D FFTs
+ *                + sum_pq beta_p(G) D_pq sum_G' conj(beta_q(G')) psi(G')         separable nonlocal
+ *
+ * Units: Hartree atomic units (energies in Ha, lengths in bohr, k and G in 1/bohr).
+ *
+ * Conventions shared by every entry point
+ *   - cell[9]: rows a1, a2, a3 of the lattice, row-major.  b = 2 pi (A^-1)^T.
+ *   - G-sphere of a k-point: {G = m1 b1 + m2 b2 + m3 b3 : |k+G|^2/2 <= ecut} (inclusive, float64),
+ *     ordered lexicographically by the signed Miller indices (m1, m2, m3).  hpsi_gsphere()
+ *     returns this list; every psi / beta array is indexed in this order.
+ *   - FFT grid: r_j = sum_i (j_i / n_i) a_i; V(r) is given as V[j1][j2][j3] (C order, j3 fastest).
+ *     The sphere must map one-to-one into the box: n_i >= 2 max|m_i| + 1 (else HPSI_EINVAL).
+ *   - Complex data are interleaved (re, im) float64 pairs (C99 double complex layout).
+ *   - Wavefunction blocks are band-major: psi[b][g], b < nbnd, g < npw(k), no padding.
+ *   - Every call is thread-compatible, not thread-safe: one context per host thread.
+ *   - Return value: HPSI_OK (0) or a negative status; nothing aborts and no exception crosses
+ *     the ABI.  hpsi_last_error() gives a one-line message for the last failure on a context
+ *     (or, for a NULL context, for the last failure of this thread before a context existed).
+ */
+#ifndef HPSI_H
+#define HPSI_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define HPSI_API __attribute__((visibility("default")))
+#else
+#define HPSI_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hpsi_ctx hpsi_ctx; /* opaque, owned by the library */
+
+enum hpsi_status {
+  HPSI_OK = 0,
+  HPSI_EINVAL = -1,     /* bad argument (size, pointer, box too small, index out of range) */
+  HPSI_ENOMEM = -2,     /* device or host allocation failed */
+  HPSI_ECUDA = -3,      /* a CUDA runtime / library call failed (message in hpsi_last_error) */
+  HPSI_ENOTCONV = -4,   /* davidson_solve reached maxiter; outputs hold the last iterate */
+  HPSI_ESINGULAR = -5,  /* the reduced overlap matrix could not be factorised */
+  HPSI_ETIMEOUT = -6,   /* a bounded device-side wait gave up (device error word set) */
+  HPSI_ENODEV = -7      /* no usable sm_103 device */
+};
+
+enum hpsi_precision {
+  HPSI_FP64 = 0,  /* every step in float64 / complex128 */
+  HPSI_MIXED = 1  /* FFTs and x V(r) in float32, nonlocal contractions as three-product
+                     split-bf16 tensor-core GEMMs with float32 accumulation; kinetic term,
+                     residuals, norms, Rayleigh-Ritz and Cholesky in float64 */
+};
+
+/*
+ * hpsi_gsphere -- the plane-wave basis at one k-point (paper Sec. 3, PW basis |k+G> of App. A.2.1).
+ *   cell[9]      in   lattice rows (bohr)
+ *   ecut         in   kinetic cutoff (Ha), > 0
+ *   k_cart[3]    in   k in Cartesian coordinates (1/bohr)
+ *   npw_out      out  number of plane waves
+ *   miller_out   out  nullable; if not NULL, receives [npw][3] int32 Miller indices in the
+ *                     documented order, provided capacity >= npw (else HPSI_EINVAL, npw_out set)
+ *   capacity     in   rows available in miller_out
+ * Host only; touches no GPU.
+ */
+HPSI_API int hpsi_gsphere(const double cell[9], double ecut, const double k_cart[3], int* npw_out,
+                 int32_t* miller_out, int capacity);
+
+/*
+ * hpsi_setup -- build the operator for one cell and nk k-points (paper Sec. 3 and App. A.1-A.2).
+ *   out          out  new context (NULL on failure)
+ *   cell, ecut        as in hpsi_gsphere
+ *   nk           in   number of k-points, >= 1
+ *   kpts         in   host [nk][3] Cartesian k-points (1/bohr)
+ *   fft[3]       in   FFT box n1, n2, n3 (each 2*3*5-smooth, 8 <= n <= 256)
+ *   vloc_r       in   host float64 [n1][n2][n3], the local potential V(r_j) (Ha), real
+ *   nproj        in   number of projectors P >= 0 (same for every k)
+ *   beta         in   host complex128: for k = 0..nk-1 in order, a block [P][npw(k)] of beta_p(k+G);
+ *                     ignored (may be NULL) when P = 0
+ *   dmat         in   host complex128 [P][P], Hermitian (only its nonzeros are used)
+ *   precision    in   HPSI_FP64 or HPSI_MIXED
+ *   cuda_stream  in   cudaStream_t (NULL = legacy default stream) on which all work is queued
+ * The library copies every input to device memory it owns; the caller may free them on return.
+ * Problem index ik of later calls is the k-point index.
+ */
+HPSI_API int hpsi_setup(hpsi_ctx** out, const double cell[9], double ecut, int nk, const double* kpts,
+               const int fft[3], const double* vloc_r, int nproj, const double* beta,
+               const double* dmat, int precision, void* cuda_stream);
+
+/*
+ * hpsi_setup_cells -- one context over ncell independent cells, each at Gamma (k = 0), each with
+ * its own box, potential and projectors (the many-small-cells batch).  Arguments are arrays
+ * over cells: cells [ncell][9], ecut [ncell], fft [ncell][3], vloc_r[c] host [n1][n2][n3],
+ * nproj [ncell], beta[c] host complex128 [P_c][npw_c] (NULL if P_c = 0), dmat[c] host
+ * complex128 [P_c][P_c].  Problem index ik of later calls is the cell index.
+ */
+HPSI_API int hpsi_setup_cells(hpsi_ctx** out, int ncell, const double* cells, const double* ecut,
+                     const int* fft, const double* const* vloc_r, const int* nproj,
+                     const double* const* beta, const double* const* dmat, int precision,
+                     void* cuda_stream);
+
+/* Number of problems (k-points or cells) in a context, and npw / nproj of problem ik
+ * (negative status on a bad index). */
+HPSI_API int hpsi_nprob(const hpsi_ctx* ctx);
+HPSI_API int hpsi_npw(const hpsi_ctx* ctx, int ik);
+HPSI_API int hpsi_nproj(const hpsi_ctx* ctx, int ik);
+
+/*
+ * hpsi_apply -- hpsi_out = H psi_in for a block of nbnd bands of problem ik
+ * (the operator of App. A.2, Eq. (diag); terms as in the file header).
+ *   psi_in       in   complex128 [nbnd][npw(ik)]
+ *   hpsi_out     out  complex128 [nbnd][npw(ik)]; must not overlap psi_in
+ *   nbnd         in   >= 0 (0 is a no-op)
+ * Either both pointers are device memory (then the call is asynchronous on the context's
+ * stream) or both are host memory (then the library stages them through device buffers it
+ * owns and returns after the result has been copied back).  Mixed host/device pairs are
+ * HPSI_EINVAL.  The library allocates its device workspace on first use and keeps it.
+ */
+HPSI_API int hpsi_apply(hpsi_ctx* ctx, int ik, const void* psi_in, void* hpsi_out, int nbnd);
+
+/*
+ * hpsi_apply_batch -- H psi for several problems in one launch sequence (one CUDA graph):
+ * for i < nitem: hpsi_out[i] = H(prob[i]) psi_in[i] with nbnd[i] bands.  Device pointers only.
+ * Items are independent; outputs must not overlap inputs or each other.
+ */
+HPSI_API int hpsi_apply_batch(hpsi_ctx* ctx, int nitem, const int* prob, const int* nbnd,
+                     const void* const* psi_in, void* const* hpsi_out);
+
+/*
+ * davidson_solve -- lowest nbnd eigenpairs of H for problem ik by block Davidson with the
+ * diagonal preconditioner (App. A.2.1).
+ *   nbnd         in   number of bands N (1 <= N <= npw/4)
+ *   tol          in   convergence when max_i ||H psi_i - eps_i psi_i||_2 <= tol
+ *   maxiter      in   iteration limit (>= 1)
+ *   psi_inout    in/out complex128 [N][npw(ik)], device or host: initial guess in (need not be
+ *                     orthonormal, must be linearly independent), orthonormal eigenvectors out
+ *   eig_out      out  host float64 [N], ascending eigenvalues (Ha)
+ *   iters_out    out  nullable; iterations taken
+ *   resnorm_out  out  nullable; host float64 [N], final residual norms
+ * Steps: orthonormalise psi (Cholesky); repeat { residuals g_i = (H - eps_i) psi_i and their
+ * norms; corrections D g_i with <k+G|D|k+G> = 1/(<k+G|H|k+G> - eps_i) (denominator kept at
+ * |.| >= 0.1 Ha); orthogonalise them against the reduced basis and add them; H_jk, S_jk of the
+ * reduced basis; solve (H - eps S) c = 0 in float64; psi_i <- sum_j c_j phi_j; when the basis
+ * would exceed 4N vectors restart from the N Ritz vectors }.  Synchronous: returns when done.
+ * HPSI_ENOTCONV if maxiter is reached (outputs then hold the last iterate).
+ */
+HPSI_API int davidson_solve(hpsi_ctx* ctx, int ik, int nbnd, double tol, int maxiter, void* psi_inout,
+                   double* eig_out, int* iters_out, double* resnorm_out);
+
+/* One-line message for the last failure on ctx (NULL ctx: this thread's last setup failure). */
+HPSI_API const char* hpsi_last_error(const hpsi_ctx* ctx);
+
+/* Free every device and host resource of ctx (NULL is a no-op).  Synchronizes its stream. */
+HPSI_API void hpsi_destroy(hpsi_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HPSI_H */

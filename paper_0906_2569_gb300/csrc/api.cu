@@ -1,0 +1,554 @@
+// extern "C" entry points of libhpsi (declared and documented in include/hpsi.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+
+#include "hpsi_internal.h"
+
+struct hpsi_ctx {
+  hpsi::Context c;
+};
+
+namespace hpsi {
+
+static thread_local std::string g_setup_err;
+
+int fail(Context& c, int code, const std::string& msg) {
+  c.err = msg;
+  return code;
+}
+
+int cuda_fail(Context& c, cudaError_t e, const char* what) {
+  c.err = std::string(what) + ": " + cudaGetErrorString(e);
+  return HPSI_ECUDA;
+}
+
+int ensure_buffer(Context& c, void** ptr, size_t* have, size_t need) {
+  if (need <= *have && *ptr) return HPSI_OK;
+  if (*ptr) {
+    cudaStreamSynchronize(c.stream);
+    cudaFree(*ptr);
+    *ptr = nullptr;
+    *have = 0;
+  }
+  cudaError_t e = cudaMalloc(ptr, std::max<size_t>(need, 256));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *ptr = nullptr;
+    return fail(c, HPSI_ENOMEM, "device allocation of " + std::to_string(need) + " bytes failed");
+  }
+  *have = std::max<size_t>(need, 256);
+  return HPSI_OK;
+}
+
+// <k+G|H|k+G> = |k+G|^2/2 + mean(V) + sum_{(p,q) in D} Re(beta_p(G) D_pq conj(beta_q(G)))
+__global__ void k_hdiag(int npw, double vmean, const double* __restrict__ kin, const double2* __restrict__ beta,
+                        int nproj, const int* __restrict__ rowptr, const int* __restrict__ col,
+                        const double2* __restrict__ val, double* __restrict__ out) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= npw) return;
+  double acc = kin[g] + vmean;
+  for (int p = 0; p < nproj; ++p) {
+    const double2 bp = beta[(size_t)p * npw + g];
+    for (int e = rowptr[p]; e < rowptr[p + 1]; ++e) {
+      const double2 bq = beta[(size_t)col[e] * npw + g];
+      const double2 d = val[e];
+      // Re( bp * d * conj(bq) )
+      const double tx = bp.x * d.x - bp.y * d.y, ty = bp.x * d.y + bp.y * d.x;
+      acc += tx * bq.x + ty * bq.y;
+    }
+  }
+  out[g] = acc;
+}
+
+template <typename T>
+static int upload(Context& c, T** dst, const T* src, size_t n) {
+  if (n == 0) {
+    *dst = nullptr;
+    return HPSI_OK;
+  }
+  cudaError_t e = cudaMalloc((void**)dst, n * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, HPSI_ENOMEM, "device allocation failed during setup");
+  }
+  e = cudaMemcpyAsync(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice, c.stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "setup upload");
+  // the host source may be freed by the caller right after setup returns
+  e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "setup upload");
+  return HPSI_OK;
+}
+
+static int init_device(Context& c, void* stream) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaGetDevice");
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, dev);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaGetDeviceProperties");
+  if (!(prop.major == 10 && prop.minor == 3))
+    return fail(c, HPSI_ENODEV, std::string("libhpsi is built for sm_103a (GB300); device is ") + prop.name);
+  c.device = dev;
+  c.sm_count = prop.multiProcessorCount;
+  c.smem_optin = prop.sharedMemPerBlockOptin;
+  c.stream = reinterpret_cast<cudaStream_t>(stream);
+  return HPSI_OK;
+}
+
+// V[j1][j2][j3] (host, C order) -> device V[j3][j2][j1] in float64 and float32; returns slot.
+static int upload_potential(Context& c, const int n[3], const double* vr, int* slot, double* vmean) {
+  const size_t nr = (size_t)n[0] * n[1] * n[2];
+  std::vector<double> t(nr);
+  std::vector<float> t32(nr);
+  double s = 0.0;
+  for (int j1 = 0; j1 < n[0]; ++j1)
+    for (int j2 = 0; j2 < n[1]; ++j2)
+      for (int j3 = 0; j3 < n[2]; ++j3) {
+        const double v = vr[((size_t)j1 * n[1] + j2) * n[2] + j3];
+        if (!std::isfinite(v)) return fail(c, HPSI_EINVAL, "vloc_r contains a non-finite value");
+        s += v;
+        const size_t o = ((size_t)j3 * n[1] + j2) * n[0] + j1;
+        t[o] = v;
+        t32[o] = (float)v;
+      }
+  *vmean = s / (double)nr;
+  double* d64 = nullptr;
+  float* d32 = nullptr;
+  int rc = upload(c, &d64, t.data(), nr);
+  if (rc) return rc;
+  c.vbufs.push_back(d64);
+  rc = upload(c, &d32, t32.data(), nr);
+  if (rc) return rc;
+  c.vbufs.push_back(d32);
+  *slot = (int)c.vbufs.size() - 2;
+  return HPSI_OK;
+}
+
+static int plan_for(Context& c, int n, FftPlan* out) {
+  for (auto& t : c.tw)
+    if (t.n == n) {
+      *out = t.plan;
+      return HPSI_OK;
+    }
+  TwiddleTable tt;
+  tt.n = n;
+  std::vector<double2> tab;
+  make_fft_plan(n, tt.plan, tab);
+  std::vector<float2> tab32(tab.size());
+  for (size_t i = 0; i < tab.size(); ++i) tab32[i] = make_float2((float)tab[i].x, (float)tab[i].y);
+  int rc = upload(c, &tt.d64, tab.data(), tab.size());
+  if (rc) return rc;
+  rc = upload(c, &tt.d32, tab32.data(), tab32.size());
+  if (rc) return rc;
+  tt.plan.tw64 = tt.d64;
+  tt.plan.tw32 = tt.d32;
+  c.tw.push_back(tt);
+  *out = tt.plan;
+  return HPSI_OK;
+}
+
+// Everything of one problem after its sphere is known: geometry, plans, device copies, D, hdiag.
+static int finish_problem(Context& c, Problem& p, const double* vr, int vslot_shared, double vmean,
+                          const double* beta, const double* dmat) {
+  std::string err;
+  int rc = build_geometry(p, err);
+  if (rc) return fail(c, rc, err);
+  for (int w = 0; w < 3; ++w)
+    if (local_smem_bytes(p, c.precision, w) > c.smem_optin)
+      return fail(c, HPSI_EINVAL, "FFT box / sphere too large for one CTA's shared memory at this precision");
+  for (int a = 0; a < 3; ++a) {
+    rc = plan_for(c, p.n[a], &p.plan[a]);
+    if (rc) return rc;
+  }
+  if ((rc = upload(c, &p.d_sticks, p.sticks.data(), p.sticks.size()))) return rc;
+  if ((rc = upload(c, &p.d_planes, p.planes.data(), p.planes.size()))) return rc;
+  if ((rc = upload(c, &p.d_kin, p.kin.data(), p.kin.size()))) return rc;
+  (void)vr;
+  p.vslot = vslot_shared;
+  p.d_v64 = reinterpret_cast<const double*>(c.vbufs[vslot_shared]);
+  p.d_v32 = reinterpret_cast<const float*>(c.vbufs[vslot_shared + 1]);
+  // projectors and D (CSR of its nonzeros)
+  const int P = p.nproj;
+  std::vector<int> rowptr(P + 1, 0), col;
+  std::vector<double2> val;
+  if (P > 0) {
+    const double2* D = reinterpret_cast<const double2*>(dmat);
+    double dmax = 0.0;
+    for (int i = 0; i < P * P; ++i) dmax = std::max(dmax, std::hypot(D[i].x, D[i].y));
+    for (int i = 0; i < P; ++i) {
+      for (int j = 0; j < P; ++j) {
+        const double2 a = D[(size_t)i * P + j], b = D[(size_t)j * P + i];
+        if (!std::isfinite(a.x) || !std::isfinite(a.y)) return fail(c, HPSI_EINVAL, "dmat contains a non-finite value");
+        if (std::fabs(a.x - b.x) > 1e-12 * dmax + 1e-300 || std::fabs(a.y + b.y) > 1e-12 * dmax + 1e-300)
+          return fail(c, HPSI_EINVAL, "dmat is not Hermitian");
+        if (a.x != 0.0 || a.y != 0.0) {
+          col.push_back(j);
+          val.push_back(a);
+        }
+      }
+      rowptr[i + 1] = (int)col.size();
+    }
+    p.nnz = (int)col.size();
+    const double2* B = reinterpret_cast<const double2*>(beta);
+    for (size_t i = 0; i < (size_t)P * p.npw; ++i)
+      if (!std::isfinite(B[i].x) || !std::isfinite(B[i].y)) return fail(c, HPSI_EINVAL, "beta contains a non-finite value");
+    if ((rc = upload(c, &p.d_beta, B, (size_t)P * p.npw))) return rc;
+    if ((rc = upload(c, &p.d_rowptr, rowptr.data(), rowptr.size()))) return rc;
+    if (p.nnz) {
+      if ((rc = upload(c, &p.d_col, col.data(), col.size()))) return rc;
+      if ((rc = upload(c, &p.d_dval, val.data(), val.size()))) return rc;
+    }
+  } else {
+    if ((rc = upload(c, &p.d_rowptr, rowptr.data(), rowptr.size()))) return rc;
+  }
+  cudaError_t e = cudaMalloc((void**)&p.d_hdiag, sizeof(double) * std::max(1, p.npw));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, HPSI_ENOMEM, "device allocation failed during setup");
+  }
+  k_hdiag<<<(p.npw + 255) / 256, 256, 0, c.stream>>>(p.npw, vmean, p.d_kin, p.d_beta, P, p.d_rowptr, p.d_col,
+                                                     p.d_dval, p.d_hdiag);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "hdiag kernel");
+  // band block of the local kernels: keep the X intermediate of one block near 48 MB (L2-resident)
+  const size_t cs = c.precision == HPSI_FP64 ? 16 : 8;
+  const size_t xper = cs * (size_t)p.n[2] * p.npl * p.n[1];
+  p.nbb = (int)std::max<size_t>(1, std::min<size_t>(4096, (size_t)(48u << 20) / std::max<size_t>(1, xper)));
+  if (c.precision == HPSI_MIXED && P > 0) {
+    rc = mixed_prepare_beta(c, p);
+    if (rc) return rc;
+  }
+  e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "setup");
+  return HPSI_OK;
+}
+
+static void free_problem(Problem& p) {
+  cudaFree(p.d_sticks);
+  cudaFree(p.d_planes);
+  cudaFree(p.d_kin);
+  cudaFree(p.d_hdiag);
+  cudaFree(p.d_beta);
+  cudaFree(p.d_rowptr);
+  cudaFree(p.d_col);
+  cudaFree(p.d_dval);
+  cudaFree(p.d_beta_bf);
+}
+
+static void free_context(Context& c) {
+  if (c.stream || true) cudaStreamSynchronize(c.stream);
+  for (auto& p : c.probs) free_problem(p);
+  for (auto& t : c.tw) {
+    cudaFree(t.d64);
+    cudaFree(t.d32);
+  }
+  for (void* v : c.vbufs) cudaFree(v);
+  cudaFree(c.ws.X);
+  cudaFree(c.ws.Y);
+  cudaFree(c.ws.part);
+  cudaFree(c.ws.w);
+  cudaFree(c.ws.stage_in);
+  cudaFree(c.ws.stage_out);
+  cudaFree(c.ws.mixed);
+  davidson_release(c);
+}
+
+int apply_device(Context& c, int ik, const double2* psi, double2* hpsi, int nbnd) {
+  const Problem& p = c.probs[ik];
+  int rc = local_apply(c, p, psi, hpsi, nbnd);
+  if (rc) return rc;
+  if (c.precision == HPSI_FP64) return nonlocal_apply_fp64(c, p, psi, hpsi, nbnd);
+  return nonlocal_apply_mixed(c, p, psi, hpsi, nbnd);
+}
+
+// 1 = device (or managed), 0 = host, -1 = error
+static int pointer_kind(const void* ptr) {
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, ptr);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return 1;
+  return 0;
+}
+
+}  // namespace hpsi
+
+using namespace hpsi;
+
+static bool check_cell(const double* cell) {
+  if (!cell) return false;
+  for (int i = 0; i < 9; ++i)
+    if (!std::isfinite(cell[i])) return false;
+  return true;
+}
+
+extern "C" int hpsi_gsphere(const double cell[9], double ecut, const double k_cart[3], int* npw_out,
+                            int32_t* miller_out, int capacity) {
+  if (!check_cell(cell) || !k_cart || !npw_out) {
+    g_setup_err = "hpsi_gsphere: null or non-finite argument";
+    return HPSI_EINVAL;
+  }
+  std::vector<int32_t> m;
+  std::string err;
+  int rc = enumerate_gsphere(cell, ecut, k_cart, m, err);
+  if (rc) {
+    g_setup_err = err;
+    return rc;
+  }
+  const int npw = (int)(m.size() / 3);
+  *npw_out = npw;
+  if (miller_out) {
+    if (capacity < npw) {
+      g_setup_err = "hpsi_gsphere: capacity smaller than npw";
+      return HPSI_EINVAL;
+    }
+    std::memcpy(miller_out, m.data(), m.size() * sizeof(int32_t));
+  }
+  return HPSI_OK;
+}
+
+static int setup_common(hpsi_ctx** out, int precision, void* stream, hpsi_ctx** ctx_out) {
+  if (!out) {
+    g_setup_err = "out is NULL";
+    return HPSI_EINVAL;
+  }
+  *out = nullptr;
+  if (precision != HPSI_FP64 && precision != HPSI_MIXED) {
+    g_setup_err = "precision must be HPSI_FP64 or HPSI_MIXED";
+    return HPSI_EINVAL;
+  }
+  hpsi_ctx* h = new (std::nothrow) hpsi_ctx();
+  if (!h) {
+    g_setup_err = "host allocation failed";
+    return HPSI_ENOMEM;
+  }
+  h->c.precision = precision;
+  int rc = init_device(h->c, stream);
+  if (rc) {
+    g_setup_err = h->c.err;
+    delete h;
+    return rc;
+  }
+  *ctx_out = h;
+  return HPSI_OK;
+}
+
+static int setup_fail(hpsi_ctx* h, int rc) {
+  g_setup_err = h->c.err;
+  free_context(h->c);
+  delete h;
+  return rc;
+}
+
+extern "C" int hpsi_setup(hpsi_ctx** out, const double cell[9], double ecut, int nk, const double* kpts,
+                          const int fft[3], const double* vloc_r, int nproj, const double* beta,
+                          const double* dmat, int precision, void* cuda_stream) {
+  hpsi_ctx* h = nullptr;
+  int rc = setup_common(out, precision, cuda_stream, &h);
+  if (rc) return rc;
+  Context& c = h->c;
+  if (!check_cell(cell) || nk < 1 || !kpts || !fft || !vloc_r || nproj < 0 || (nproj > 0 && (!beta || !dmat))) {
+    c.err = "hpsi_setup: bad argument (null pointer, nk < 1 or nproj < 0)";
+    return setup_fail(h, HPSI_EINVAL);
+  }
+  for (int a = 0; a < 3; ++a)
+    if (!fft_size_ok(fft[a])) {
+      c.err = "FFT edge " + std::to_string(fft[a]) + " is not a 2*3*5-smooth integer in [8, 256]";
+      return setup_fail(h, HPSI_EINVAL);
+    }
+  int slot = 0;
+  double vmean = 0.0;
+  rc = upload_potential(c, fft, vloc_r, &slot, &vmean);
+  if (rc) return setup_fail(h, rc);
+  size_t boff = 0;
+  c.probs.resize(nk);
+  for (int ik = 0; ik < nk; ++ik) {
+    Problem& p = c.probs[ik];
+    std::memcpy(p.cell, cell, sizeof(p.cell));
+    reciprocal(p.cell, p.recip);
+    p.ecut = ecut;
+    for (int a = 0; a < 3; ++a) {
+      p.k[a] = kpts[3 * ik + a];
+      p.n[a] = fft[a];
+      if (!std::isfinite(p.k[a])) {
+        c.err = "non-finite k-point";
+        return setup_fail(h, HPSI_EINVAL);
+      }
+    }
+    std::string err;
+    rc = enumerate_gsphere(p.cell, ecut, p.k, p.miller, err);
+    if (rc) {
+      c.err = err;
+      return setup_fail(h, rc);
+    }
+    p.nproj = nproj;
+    const double* bk = nproj > 0 ? beta + 2 * boff : nullptr;
+    boff += (size_t)nproj * (p.miller.size() / 3);
+    rc = finish_problem(c, p, vloc_r, slot, vmean, bk, dmat);
+    if (rc) return setup_fail(h, rc);
+  }
+  *out = h;
+  return HPSI_OK;
+}
+
+extern "C" int hpsi_setup_cells(hpsi_ctx** out, int ncell, const double* cells, const double* ecut, const int* fft,
+                                const double* const* vloc_r, const int* nproj, const double* const* beta,
+                                const double* const* dmat, int precision, void* cuda_stream) {
+  hpsi_ctx* h = nullptr;
+  int rc = setup_common(out, precision, cuda_stream, &h);
+  if (rc) return rc;
+  Context& c = h->c;
+  if (ncell < 1 || !cells || !ecut || !fft || !vloc_r || !nproj) {
+    c.err = "hpsi_setup_cells: bad argument";
+    return setup_fail(h, HPSI_EINVAL);
+  }
+  c.probs.resize(ncell);
+  for (int ic = 0; ic < ncell; ++ic) {
+    Problem& p = c.probs[ic];
+    if (!check_cell(cells + 9 * ic) || !vloc_r[ic] || nproj[ic] < 0 ||
+        (nproj[ic] > 0 && (!beta || !dmat || !beta[ic] || !dmat[ic]))) {
+      c.err = "hpsi_setup_cells: bad argument for cell " + std::to_string(ic);
+      return setup_fail(h, HPSI_EINVAL);
+    }
+    std::memcpy(p.cell, cells + 9 * ic, sizeof(p.cell));
+    reciprocal(p.cell, p.recip);
+    p.ecut = ecut[ic];
+    for (int a = 0; a < 3; ++a) {
+      p.k[a] = 0.0;
+      p.n[a] = fft[3 * ic + a];
+      if (!fft_size_ok(p.n[a])) {
+        c.err = "FFT edge " + std::to_string(p.n[a]) + " of cell " + std::to_string(ic) + " is not supported";
+        return setup_fail(h, HPSI_EINVAL);
+      }
+    }
+    int slot = 0;
+    double vmean = 0.0;
+    rc = upload_potential(c, p.n, vloc_r[ic], &slot, &vmean);
+    if (rc) return setup_fail(h, rc);
+    std::string err;
+    rc = enumerate_gsphere(p.cell, p.ecut, p.k, p.miller, err);
+    if (rc) {
+      c.err = err;
+      return setup_fail(h, rc);
+    }
+    p.nproj = nproj[ic];
+    rc = finish_problem(c, p, vloc_r[ic], slot, vmean, p.nproj ? beta[ic] : nullptr, p.nproj ? dmat[ic] : nullptr);
+    if (rc) return setup_fail(h, rc);
+  }
+  *out = h;
+  return HPSI_OK;
+}
+
+extern "C" int hpsi_nprob(const hpsi_ctx* ctx) {
+  if (!ctx) return HPSI_EINVAL;
+  return (int)ctx->c.probs.size();
+}
+
+extern "C" int hpsi_npw(const hpsi_ctx* ctx, int ik) {
+  if (!ctx || ik < 0 || ik >= (int)ctx->c.probs.size()) return HPSI_EINVAL;
+  return ctx->c.probs[ik].npw;
+}
+
+extern "C" int hpsi_nproj(const hpsi_ctx* ctx, int ik) {
+  if (!ctx || ik < 0 || ik >= (int)ctx->c.probs.size()) return HPSI_EINVAL;
+  return ctx->c.probs[ik].nproj;
+}
+
+extern "C" int hpsi_apply(hpsi_ctx* ctx, int ik, const void* psi_in, void* hpsi_out, int nbnd) {
+  if (!ctx) return HPSI_EINVAL;
+  Context& c = ctx->c;
+  if (ik < 0 || ik >= (int)c.probs.size()) return fail(c, HPSI_EINVAL, "hpsi_apply: problem index out of range");
+  if (nbnd < 0) return fail(c, HPSI_EINVAL, "hpsi_apply: nbnd < 0");
+  if (nbnd == 0) return HPSI_OK;
+  if (!psi_in || !hpsi_out) return fail(c, HPSI_EINVAL, "hpsi_apply: null pointer");
+  const Problem& p = c.probs[ik];
+  const size_t bytes = sizeof(double2) * (size_t)nbnd * p.npw;
+  const char* a0 = static_cast<const char*>(psi_in);
+  const char* b0 = static_cast<const char*>(hpsi_out);
+  if (a0 < b0 + bytes && b0 < a0 + bytes) return fail(c, HPSI_EINVAL, "hpsi_apply: psi_in and hpsi_out overlap");
+  const int ka = pointer_kind(psi_in), kb = pointer_kind(hpsi_out);
+  if (ka < 0 || kb < 0 || ka != kb)
+    return fail(c, HPSI_EINVAL, "hpsi_apply: psi_in and hpsi_out must both be device or both be host memory");
+  if (ka == 1)
+    return apply_device(c, ik, static_cast<const double2*>(psi_in), static_cast<double2*>(hpsi_out), nbnd);
+  int rc = ensure_buffer(c, &c.ws.stage_in, &c.ws.stage_in_bytes, bytes);
+  if (rc) return rc;
+  rc = ensure_buffer(c, &c.ws.stage_out, &c.ws.stage_out_bytes, bytes);
+  if (rc) return rc;
+  cudaError_t e = cudaMemcpyAsync(c.ws.stage_in, psi_in, bytes, cudaMemcpyHostToDevice, c.stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "hpsi_apply host->device copy");
+  rc = apply_device(c, ik, static_cast<const double2*>(c.ws.stage_in), static_cast<double2*>(c.ws.stage_out), nbnd);
+  if (rc) return rc;
+  e = cudaMemcpyAsync(hpsi_out, c.ws.stage_out, bytes, cudaMemcpyDeviceToHost, c.stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "hpsi_apply device->host copy");
+  e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "hpsi_apply");
+  return HPSI_OK;
+}
+
+extern "C" int hpsi_apply_batch(hpsi_ctx* ctx, int nitem, const int* prob, const int* nbnd,
+                                const void* const* psi_in, void* const* hpsi_out) {
+  if (!ctx) return HPSI_EINVAL;
+  Context& c = ctx->c;
+  if (nitem < 0 || (nitem > 0 && (!prob || !nbnd || !psi_in || !hpsi_out)))
+    return fail(c, HPSI_EINVAL, "hpsi_apply_batch: bad argument");
+  for (int i = 0; i < nitem; ++i) {
+    if (prob[i] < 0 || prob[i] >= (int)c.probs.size() || nbnd[i] < 0)
+      return fail(c, HPSI_EINVAL, "hpsi_apply_batch: bad item " + std::to_string(i));
+    if (nbnd[i] > 0 && (pointer_kind(psi_in[i]) != 1 || pointer_kind(hpsi_out[i]) != 1))
+      return fail(c, HPSI_EINVAL, "hpsi_apply_batch: item pointers must be device memory");
+  }
+  for (int i = 0; i < nitem; ++i) {
+    if (nbnd[i] == 0) continue;
+    int rc = apply_device(c, prob[i], static_cast<const double2*>(psi_in[i]), static_cast<double2*>(hpsi_out[i]),
+                          nbnd[i]);
+    if (rc) return rc;
+  }
+  return HPSI_OK;
+}
+
+extern "C" int davidson_solve(hpsi_ctx* ctx, int ik, int nbnd, double tol, int maxiter, void* psi_inout,
+                              double* eig_out, int* iters_out, double* resnorm_out) {
+  if (!ctx) return HPSI_EINVAL;
+  Context& c = ctx->c;
+  if (ik < 0 || ik >= (int)c.probs.size()) return fail(c, HPSI_EINVAL, "davidson_solve: problem index out of range");
+  const Problem& p = c.probs[ik];
+  if (nbnd < 1 || 4 * nbnd > p.npw) return fail(c, HPSI_EINVAL, "davidson_solve: need 1 <= nbnd <= npw/4");
+  if (!(tol > 0.0) || maxiter < 1 || !psi_inout || !eig_out)
+    return fail(c, HPSI_EINVAL, "davidson_solve: bad tol, maxiter or null pointer");
+  const int kind = pointer_kind(psi_inout);
+  if (kind < 0) return fail(c, HPSI_EINVAL, "davidson_solve: unrecognised psi pointer");
+  const size_t bytes = sizeof(double2) * (size_t)nbnd * p.npw;
+  if (kind == 1)
+    return davidson_run(c, ik, nbnd, tol, maxiter, static_cast<double2*>(psi_inout), eig_out, iters_out, resnorm_out);
+  int rc = ensure_buffer(c, &c.ws.stage_in, &c.ws.stage_in_bytes, bytes);
+  if (rc) return rc;
+  cudaError_t e = cudaMemcpyAsync(c.ws.stage_in, psi_inout, bytes, cudaMemcpyHostToDevice, c.stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "davidson_solve host->device copy");
+  rc = davidson_run(c, ik, nbnd, tol, maxiter, static_cast<double2*>(c.ws.stage_in), eig_out, iters_out, resnorm_out);
+  if (rc != HPSI_OK && rc != HPSI_ENOTCONV) return rc;
+  e = cudaMemcpyAsync(psi_inout, c.ws.stage_in, bytes, cudaMemcpyDeviceToHost, c.stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "davidson_solve device->host copy");
+  e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "davidson_solve");
+  return rc;
+}
+
+extern "C" const char* hpsi_last_error(const hpsi_ctx* ctx) {
+  if (!ctx) return g_setup_err.c_str();
+  return ctx->c.err.c_str();
+}
+
+extern "C" void hpsi_destroy(hpsi_ctx* ctx) {
+  if (!ctx) return;
+  free_context(ctx->c);
+  delete ctx;
+}

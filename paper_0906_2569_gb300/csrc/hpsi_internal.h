@@ -1,0 +1,141 @@
+// Internal declarations of libhpsi: problem geometry, FFT plans, context, launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/hpsi.h"
+
+namespace hpsi {
+
+constexpr int kMaxFftN = 256;     // largest FFT edge supported by the warp FFT
+constexpr int kMaxStages = 8;
+constexpr int kWarpsPerCta = 8;   // local-potential kernels run 256 threads
+
+// One radix pass list for a transform of length n (Stockham, radices 4, 2, 3, 5).
+struct FftPlan {
+  int n;
+  int nstages;
+  int radix[kMaxStages];
+  int twoff[kMaxStages];   // offset of each stage's twiddles in the table of this n
+  const double2* tw64;     // device: e^{-2 pi i r k / (Ns R)} for k < Ns, r = 1..R-1, per stage
+  const float2* tw32;
+};
+
+// A z-column ("stick") of the sphere: G = (m1, m2, m3lo + t), t < len, stored at g0 + t.
+struct StickDev {
+  int g0;
+  int len;
+  int z0;   // m3lo mod n3
+  int iy;   // m2 mod n2
+};
+
+// The sticks that share one m1 ("plane"): sticks s0 .. s0+ns-1, G's from g0.
+struct PlaneDev {
+  int s0;
+  int ns;
+  int ix;   // m1 mod n1
+  int g0;
+};
+
+// Nonlocal data of a problem in the layouts the kernels read.
+struct NonlocalDev {
+  int nproj;
+  const double2* beta;      // [P][npw] complex128
+  const int* d_rowptr;      // CSR of D: [P+1]
+  const int* d_col;         // [nnz]
+  const double2* d_val;     // [nnz]
+  const uint16_t* beta_bf;  // mixed path: bf16 split planes of beta (see nonlocal_tc.cu)
+};
+
+struct Problem {
+  double cell[9];
+  double recip[9];
+  double ecut;
+  double k[3];
+  int n[3];
+  int npw = 0, nst = 0, npl = 0, ns_max = 0, nproj = 0;
+  std::vector<int32_t> miller;
+  std::vector<StickDev> sticks;
+  std::vector<PlaneDev> planes;
+  std::vector<double> kin;      // |k+G|^2 / 2
+  std::vector<double> hdiag;    // <k+G|H|k+G>, for the Davidson preconditioner
+  // device
+  StickDev* d_sticks = nullptr;
+  PlaneDev* d_planes = nullptr;
+  double* d_kin = nullptr;
+  double* d_hdiag = nullptr;
+  const double* d_v64 = nullptr;   // V in [n3][n2][n1] layout (may be shared between problems)
+  const float* d_v32 = nullptr;
+  int vslot = -1;                  // index into Context::vbufs
+  double2* d_beta = nullptr;
+  int* d_rowptr = nullptr;
+  int* d_col = nullptr;
+  double2* d_dval = nullptr;
+  int nnz = 0;
+  uint16_t* d_beta_bf = nullptr;   // mixed path only
+  FftPlan plan[3];
+  int nbb = 1;                     // band block of the local-potential kernels
+};
+
+struct TwiddleTable {
+  int n;
+  FftPlan plan;   // with device pointers filled
+  double2* d64 = nullptr;
+  float2* d32 = nullptr;
+};
+
+struct Workspace {
+  void* X = nullptr; size_t xbytes = 0;
+  void* Y = nullptr; size_t ybytes = 0;
+  void* part = nullptr; size_t partbytes = 0;    // split-K partials of <beta|psi>
+  void* w = nullptr; size_t wbytes = 0;          // D <beta|psi>, [nb][P]
+  void* stage_in = nullptr; size_t stage_in_bytes = 0;    // host-pointer staging
+  void* stage_out = nullptr; size_t stage_out_bytes = 0;
+  void* mixed = nullptr; size_t mixedbytes = 0;  // bf16 operand planes of the mixed path
+};
+
+struct Context {
+  int precision = HPSI_FP64;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int sm_count = 152;
+  size_t smem_optin = 0;
+  std::vector<Problem> probs;
+  std::vector<TwiddleTable> tw;
+  std::vector<void*> vbufs;            // owned V buffers (64 and 32 bit)
+  Workspace ws;
+  std::string err;
+  void* blas = nullptr;                // cublasHandle_t (Davidson)
+  void* solver = nullptr;              // cusolverDnHandle_t (Davidson)
+};
+
+// ---- host helpers (plan.cpp) ----
+void reciprocal(const double cell[9], double recip[9]);
+int enumerate_gsphere(const double cell[9], double ecut, const double k[3], std::vector<int32_t>& miller,
+                      std::string& err);
+bool fft_size_ok(int n);
+void make_fft_plan(int n, FftPlan& plan, std::vector<double2>& table);
+int build_geometry(Problem& p, std::string& err);
+
+// ---- launchers (local_kernels.cu, nonlocal_fp64.cu) ----
+size_t local_smem_bytes(const Problem& p, int precision, int which);
+int local_apply(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd);
+int nonlocal_apply_fp64(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd);
+int nonlocal_apply_mixed(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd);
+int mixed_prepare_beta(Context& c, Problem& p);
+
+// ---- context helpers (api.cpp) ----
+int ensure_buffer(Context& c, void** ptr, size_t* have, size_t need);
+int fail(Context& c, int code, const std::string& msg);
+int cuda_fail(Context& c, cudaError_t e, const char* what);
+int apply_device(Context& c, int ik, const double2* psi, double2* hpsi, int nbnd);
+
+// ---- Davidson (davidson.cu) ----
+int davidson_run(Context& c, int ik, int nbnd, double tol, int maxiter, double2* psi, double* eig,
+                 int* iters, double* resnorm);
+void davidson_release(Context& c);
+
+}  // namespace hpsi

@@ -1,0 +1,169 @@
+// Separable nonlocal term in float64 (paper Sec. 3: Kleinman-Bylander separable NC projectors):
+//   becp[b][p] = <beta_p|psi_b> = sum_G conj(beta_p(G)) psi_b(G)            (calbec)
+//   w[b][p]    = sum_q D_pq becp[b][q]                                          (D-scale, CSR of D)
+//   hpsi_b(G) += sum_p beta_p(G) w[b][p]                                        (add_vuspsi)
+// On GB300 float64 runs at ~1.2 TFLOP/s on the CUDA cores (the FP64 MMA path is not faster), so
+// these are plain shared-memory-tiled complex GEMMs whose inner loop is DFMA-bound; calbec
+// (P x nb outputs, K = npw) splits K across CTAs and reduces the partials deterministically in
+// the D-scale kernel.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "hpsi_internal.h"
+
+namespace hpsi {
+
+namespace {
+
+constexpr int CB_TP = 32;   // projectors per CTA
+constexpr int CB_TB = 32;   // bands per CTA
+constexpr int CB_TK = 32;   // G per shared-memory tile
+
+// part[split][b][p] = sum_{G in split} conj(beta[p][G]) psi[b][G]
+__global__ void __launch_bounds__(256) k_calbec64(int npw, int nproj, int nb, int kchunk,
+                                                  const double2* __restrict__ beta,
+                                                  const double2* __restrict__ psi, double2* __restrict__ part) {
+  __shared__ double2 sb[CB_TP][CB_TK + 1];
+  __shared__ double2 sp[CB_TB][CB_TK + 1];
+  const int p0 = blockIdx.x * CB_TP, b0 = blockIdx.y * CB_TB, split = blockIdx.z;
+  const int gbeg = split * kchunk, gend = min(npw, gbeg + kchunk);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // tx -> p, ty -> b
+  double2 acc[2][2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) acc[i][j] = make_double2(0.0, 0.0);
+  for (int g0 = gbeg; g0 < gend; g0 += CB_TK) {
+    for (int i = threadIdx.x; i < CB_TP * CB_TK; i += 256) {
+      const int r = i / CB_TK, cc = i % CB_TK;
+      const int g = g0 + cc;
+      sb[r][cc] = (p0 + r < nproj && g < gend) ? beta[(size_t)(p0 + r) * npw + g] : make_double2(0.0, 0.0);
+      sp[r][cc] = (b0 + r < nb && g < gend) ? psi[(size_t)(b0 + r) * npw + g] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < CB_TK; ++kk) {
+      const double2 x0 = sb[tx][kk], x1 = sb[tx + 16][kk];
+      const double2 y0 = sp[ty][kk], y1 = sp[ty + 16][kk];
+      // conj(x) * y
+      acc[0][0].x += x0.x * y0.x + x0.y * y0.y; acc[0][0].y += x0.x * y0.y - x0.y * y0.x;
+      acc[0][1].x += x0.x * y1.x + x0.y * y1.y; acc[0][1].y += x0.x * y1.y - x0.y * y1.x;
+      acc[1][0].x += x1.x * y0.x + x1.y * y0.y; acc[1][0].y += x1.x * y0.y - x1.y * y0.x;
+      acc[1][1].x += x1.x * y1.x + x1.y * y1.y; acc[1][1].y += x1.x * y1.y - x1.y * y1.x;
+    }
+    __syncthreads();
+  }
+  double2* out = part + (size_t)split * nb * nproj;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int p = p0 + tx + 16 * i, b = b0 + ty + 16 * j;
+      if (p < nproj && b < nb) out[(size_t)b * nproj + p] = acc[i][j];
+    }
+}
+
+// w[b][p] = sum_{q in row p of D} D_pq sum_s part[s][b][q]
+__global__ void k_dscale64(int nproj, int nb, int nsplit, const double2* __restrict__ part,
+                           const int* __restrict__ rowptr, const int* __restrict__ col,
+                           const double2* __restrict__ val, double2* __restrict__ w) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nproj * nb) return;
+  const int b = i / nproj, p = i % nproj;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int e = rowptr[p]; e < rowptr[p + 1]; ++e) {
+    const int q = col[e];
+    double2 s = make_double2(0.0, 0.0);
+    for (int sp = 0; sp < nsplit; ++sp) {
+      const double2 t = part[((size_t)sp * nb + b) * nproj + q];
+      s.x += t.x;
+      s.y += t.y;
+    }
+    const double2 d = val[e];
+    acc.x += d.x * s.x - d.y * s.y;
+    acc.y += d.x * s.y + d.y * s.x;
+  }
+  w[i] = acc;
+}
+
+constexpr int AV_TG = 64;   // G per CTA
+constexpr int AV_TB = 32;   // bands per CTA
+constexpr int AV_TP = 16;   // projectors per shared-memory tile
+
+// hpsi[b][G] += sum_p w[b][p] beta[p][G]
+__global__ void __launch_bounds__(256) k_addvus64(int npw, int nproj, int nb, const double2* __restrict__ w,
+                                                  const double2* __restrict__ beta, double2* __restrict__ hpsi) {
+  __shared__ double2 sb[AV_TP][AV_TG];
+  __shared__ double2 sw[AV_TB][AV_TP + 1];
+  const int g0 = blockIdx.x * AV_TG, b0 = blockIdx.y * AV_TB;
+  const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;   // tx -> G, ty -> bands ty + 4 j
+  double2 acc[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) acc[j] = make_double2(0.0, 0.0);
+  for (int q0 = 0; q0 < nproj; q0 += AV_TP) {
+    for (int i = threadIdx.x; i < AV_TP * AV_TG; i += 256) {
+      const int r = i / AV_TG, cc = i % AV_TG;
+      const int q = q0 + r, g = g0 + cc;
+      sb[r][cc] = (q < nproj && g < npw) ? beta[(size_t)q * npw + g] : make_double2(0.0, 0.0);
+    }
+    for (int i = threadIdx.x; i < AV_TB * AV_TP; i += 256) {
+      const int r = i / AV_TP, cc = i % AV_TP;
+      const int b = b0 + r, q = q0 + cc;
+      sw[r][cc] = (b < nb && q < nproj) ? w[(size_t)b * nproj + q] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < AV_TP; ++kk) {
+      const double2 x = sb[kk][tx];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const double2 y = sw[ty + 4 * j][kk];
+        acc[j].x += y.x * x.x - y.y * x.y;
+        acc[j].y += y.x * x.y + y.y * x.x;
+      }
+    }
+    __syncthreads();
+  }
+  const int g = g0 + tx;
+  if (g < npw) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int b = b0 + ty + 4 * j;
+      if (b < nb) {
+        double2* o = hpsi + (size_t)b * npw + g;
+        double2 v = *o;
+        v.x += acc[j].x;
+        v.y += acc[j].y;
+        *o = v;
+      }
+    }
+  }
+}
+
+}  // namespace
+
+int nonlocal_apply_fp64(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd) {
+  if (p.nproj == 0 || nbnd == 0) return HPSI_OK;
+  const int tilesp = (p.nproj + CB_TP - 1) / CB_TP, tilesb = (nbnd + CB_TB - 1) / CB_TB;
+  int nsplit = std::max(1, (3 * c.sm_count) / std::max(1, tilesp * tilesb));
+  int kchunk = (p.npw + nsplit - 1) / nsplit;
+  kchunk = std::max(CB_TK * 4, ((kchunk + CB_TK - 1) / CB_TK) * CB_TK);
+  nsplit = (p.npw + kchunk - 1) / kchunk;
+  int rc = ensure_buffer(c, &c.ws.part, &c.ws.partbytes, sizeof(double2) * (size_t)nsplit * nbnd * p.nproj);
+  if (rc) return rc;
+  rc = ensure_buffer(c, &c.ws.w, &c.ws.wbytes, sizeof(double2) * (size_t)nbnd * p.nproj);
+  if (rc) return rc;
+  double2* part = reinterpret_cast<double2*>(c.ws.part);
+  double2* w = reinterpret_cast<double2*>(c.ws.w);
+  k_calbec64<<<dim3(tilesp, tilesb, nsplit), 256, 0, c.stream>>>(p.npw, p.nproj, nbnd, kchunk, p.d_beta, psi, part);
+  const int n = p.nproj * nbnd;
+  k_dscale64<<<(n + 255) / 256, 256, 0, c.stream>>>(p.nproj, nbnd, nsplit, part, p.d_rowptr, p.d_col, p.d_dval, w);
+  k_addvus64<<<dim3((p.npw + AV_TG - 1) / AV_TG, (nbnd + AV_TB - 1) / AV_TB), 256, 0, c.stream>>>(
+      p.npw, p.nproj, nbnd, w, p.d_beta, hpsi);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "nonlocal float64 kernels launch");
+  return HPSI_OK;
+}
+
+}  // namespace hpsi
