@@ -1,0 +1,414 @@
+#!/usr/bin/env python
+"""H|psi> band-applications/s on one GB300: mixed precision vs float64, plus the CPU oracle.
+
+Workload (default): the cubic a = 20.5 bohr cell with 64 atoms on a jittered 4x4x4 lattice,
+E_cut 20 Ha, Gamma, FFT box 90^3, 36785 plane waves, 256 s+p projectors, 160 bands.
+
+A step is one block-Davidson pass over the 160-band block, through the C ABI:
+davidson_solve(maxiter = 1) from the seeded starting block -- orthonormalise, H on the N bands,
+Rayleigh-Ritz, residuals and diagonal preconditioner, H on the N corrections, Rayleigh-Ritz in the
+2N basis.  It runs every step of the hot path (sphere scatter, 3-D FFTs, x V(r), gather + kinetic,
+calbec, D, add_vuspsi, residuals, preconditioner, subspace algebra).  The metric counts the H|psi>
+band-applications done in the step over the step's device time.  ``value`` is the mixed-precision
+path; ``fp64`` is the float64 path on the same cell.
+
+Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events on the library's
+stream; a 256 MB buffer is written between steps (outside the events) so no step starts with the
+previous step's data in L2.  Under torchrun every rank runs its own replica of the block (the bands
+of different blocks are independent: no collective on the data path) and rank 0 reports the
+whole-job rate with the max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+HBM_FALLBACK_GBS = 6800.0
+FP64_ALU_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12    # 2 DFMA / clk / SM (measured), 2070 MHz max clock
+
+# dram bytes per launch (read + write) from ncu captures, keyed by kernel and the source hash
+# of the file that defines it at capture time; a mismatch reports null.
+NCU_TRAFFIC = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--config", default="c2")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+
+
+def workload(cfg):
+    import workloads
+    p = workloads.CONFIGS[cfg]()
+    desc = (f"{cfg}: {p.name}, cell {np.diag(p.lattice).tolist() if np.all(p.lattice == np.diag(np.diag(p.lattice))) else 'oblique'} bohr, "
+            f"{len(p.atoms)} atoms, E_cut {p.ecut} Ha, box {p.fft[0]}x{p.fft[1]}x{p.fft[2]}, {p.nproj} projectors, "
+            f"{p.nbnd} bands, Gamma")
+    return p, desc
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------------------------------------
+# CPU oracle legs
+# ---------------------------------------------------------------------------------------------
+
+def oracle_inputs(p):
+    import oracle
+    import workloads
+    k = p.kpts[0]
+    m = oracle.gsphere.gsphere(p.lattice, p.ecut, k)
+    vr = workloads.vloc_r(p.lattice, p.atoms, p.fft)
+    beta = workloads.beta(p.lattice, p.atoms, k, m)
+    d = workloads.dmat(len(p.atoms))
+    psi = workloads.psi0(p.lattice, k, m, p.nbnd, p.psi_seed)
+    return k, m, vr, beta, d, psi
+
+
+def oracle_step(p, inputs, nb):
+    """The oracle's H|psi> on nb bands (FFT form, scipy with all host cores) plus its Davidson
+    residual, preconditioner and Rayleigh-Ritz on that sample; returns seconds."""
+    import oracle
+    k, m, vr, beta, d, psi = inputs
+    t0 = time.perf_counter()
+    x = psi[:nb]
+    hx = oracle.hamiltonian.hpsi(p.lattice, k, m, p.fft, vr, beta, d, x)
+    e, xr, hxr = oracle.davidson.rayleigh_ritz(x, hx, nb)
+    g = oracle.davidson.residuals(hxr, xr, e)
+    oracle.davidson.precondition(g, oracle.hamiltonian.h_diagonal(p.lattice, k, m, vr, beta, d), e)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(p, budget_s=12.0):
+    inputs = oracle_inputs(p)
+    oracle_step(p, inputs, 1)                     # warm caches / FFT plans
+    nb, t = 2, 0.0
+    while True:
+        t = oracle_step(p, inputs, nb)
+        if t > budget_s / 3 or nb >= p.nbnd:
+            break
+        nb = min(p.nbnd, nb * 2)
+    return {"value": nb / t, "unit": "band-applications/s", "cores": host_cores(), "kind": "oracle",
+            "sample": f"{nb} of {p.nbnd} bands: oracle H|psi> (scipy.fft, {host_cores()} workers) + residual, "
+                      f"preconditioner and Rayleigh-Ritz on the sample, {t:.2f} s"}
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    p, desc = workload(args.config)
+    inputs = oracle_inputs(p)
+    nb = 4
+    oracle_step(p, inputs, 1)
+    for _ in range(args.warmup):
+        oracle_step(p, inputs, nb)
+    ts = [oracle_step(p, inputs, nb) for _ in range(args.steps)]
+    tot = sum(ts)
+    val = nb * len(ts) / tot
+    out = {"impl": "reference", "metric": "H|psi> band-applications/s", "value": val, "unit": "band-applications/s",
+           "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(ts),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+           "config": {"workload": desc, "step": f"oracle H|psi> + Davidson residual/preconditioner/Rayleigh-Ritz "
+                                                f"on {nb} of the {p.nbnd} bands"},
+           "cpu_baseline": {"value": val, "unit": "band-applications/s", "cores": host_cores(), "kind": "oracle",
+                            "sample": f"{nb} bands per step"},
+           "e2e": {"value": val, "unit": "band-applications/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------------------
+
+class Clocks:
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv") if os.path.isdir(
+            os.path.join(ROOT, "gpurun_out")) else f"/tmp/clocks_{os.getpid()}.csv"
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=clocks.sm,clocks.max.sm,power.draw,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[3:7]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def file_hash(rel):
+    with open(os.path.join(ROOT, rel), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:12]
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    import workloads
+    from paper_0906_2569_gb300 import binding as B
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    p, desc = workload(args.config)
+    k = p.kpts[0]
+    miller = B.hpsi_gsphere(p.lattice, p.ecut, k)
+    npw = len(miller)
+    vr = workloads.vloc_r(p.lattice, p.atoms, p.fft)
+    beta = workloads.beta(p.lattice, p.atoms, k, miller)
+    d = workloads.dmat(len(p.atoms))
+    psi0 = torch.from_numpy(workloads.psi0(p.lattice, k, miller, p.nbnd, p.psi_seed)).cuda()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    nst, npl = stick_counts(miller, p.fft)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    def measure(precision, timing_kernels=True, e2e=False):
+        ctx = B.hpsi_setup(p.lattice, p.ecut, [k], p.fft, vr, [beta], d, precision, stream.cuda_stream)
+        work = torch.empty_like(psi0)
+
+        def step():
+            work.copy_(psi0)
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            B.davidson_solve(ctx, 0, work, 1e-300, 1, raise_on_notconv=False)
+            e1.record(stream)
+            return e0, e1
+
+        for _ in range(args.warmup):
+            step()
+        barrier()
+        B.hpsi_kernel_stats(ctx, -1, reset=True)
+        B.hpsi_kernel_stats(ctx, -2, reset=True)
+        for kk in range(len(B.KERNELS)):
+            B.hpsi_kernel_stats(ctx, kk, reset=True)
+        if timing_kernels:
+            B.hpsi_set_option(ctx, B.HPSI_OPT_KERNEL_TIMING, 1)
+        evs = []
+        with Clocks(local_rank) as clk:
+            for _ in range(args.steps):
+                evs.append(step())
+            barrier()
+        ms = [a.elapsed_time(b) for a, b in evs]
+        total_ms = sum(ms)
+        launches, _ = B.hpsi_kernel_stats(ctx, -1)
+        bapps, _ = B.hpsi_kernel_stats(ctx, -2)
+        kstats = {}
+        for kk, name in enumerate(B.KERNELS):
+            n, t = B.hpsi_kernel_stats(ctx, kk)
+            if n:
+                kstats[name] = {"launches": n, "ms": t}
+        B.hpsi_set_option(ctx, B.HPSI_OPT_KERNEL_TIMING, 0)
+        # H|psi> alone on the block, for reference
+        out = torch.empty_like(psi0)
+        hms = []
+        for _ in range(2):
+            B.hpsi_apply(ctx, 0, psi0, out)
+        for _ in range(max(2, args.steps)):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            B.hpsi_apply(ctx, 0, psi0, out)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            hms.append(e0.elapsed_time(e1))
+        res = {"total_ms": total_ms, "ms": ms, "band_apps": bapps, "launches": launches, "kernels": kstats,
+               "clocks": clk.summary(), "hpsi_ms": statistics.median(hms)}
+        if e2e:
+            host = torch.empty(psi0.shape, dtype=psi0.dtype, pin_memory=True)
+            src = psi0.cpu()
+            ts = []
+            for i in range(args.warmup + args.steps):
+                host.copy_(src)
+                flush.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                eig, _, _, _ = B.davidson_solve(ctx, 0, host, 1e-300, 1, raise_on_notconv=False)
+                t1 = time.perf_counter()
+                if i >= args.warmup:
+                    ts.append(t1 - t0)
+            res["e2e_s"] = ts
+            res["e2e_bytes"] = int(psi0.numel() * 16)
+        ctx.close()
+        return res
+
+    mixed = measure(B.HPSI_MIXED, e2e=not args.no_e2e)
+    fp64 = measure(B.HPSI_FP64)
+
+    def world_max(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    mix_ms = world_max(mixed["total_ms"])
+    f64_ms = world_max(fp64["total_ms"])
+    value = mixed["band_apps"] * world / (mix_ms / 1e3)
+    v64 = fp64["band_apps"] * world / (f64_ms / 1e3)
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    roof = roofline(mixed, p, npw, nst, npl, B.HPSI_MIXED)
+    out = {
+        "metric": "H|psi> band-applications/s (mixed precision; float64 beside it)",
+        "value": value, "unit": "band-applications/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": mix_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "mixed: c64 FFT + xV, f64 nonlocal GEMMs, f64 Davidson", "data": "synthetic",
+        "config": {"workload": desc, "npw": npw, "band_apps_per_step": mixed["band_apps"] // args.steps,
+                   "step": "davidson_solve maxiter=1 from the seeded block: H on N bands + Rayleigh-Ritz + residuals + "
+                           "preconditioner + H on N corrections + Rayleigh-Ritz (2N)",
+                   "l2": "256 MB buffer written between timed steps", "parallelism": f"replicas x{world}"},
+        "fp64": {"value": v64, "unit": "band-applications/s", "ms_per_step": f64_ms / args.steps,
+                 "hpsi_apply_band_apps_per_s": p.nbnd / (fp64["hpsi_ms"] / 1e3), "kernels": fp64["kernels"],
+                 "dtype": "c128"},
+        "mixed_over_fp64": value / v64,
+        "hpsi_apply_band_apps_per_s": p.nbnd / (mixed["hpsi_ms"] / 1e3),
+        "kernels": mixed["kernels"],
+        "roofline": roof,
+        "clocks": mixed["clocks"],
+        "gpu_launches": mixed["launches"],
+    }
+    if "e2e_s" in mixed:
+        tot = sum(mixed["e2e_s"])
+        out["e2e"] = {"value": mixed["band_apps"] / tot * world, "unit": "band-applications/s",
+                      "h2d_bytes_per_step": mixed["e2e_bytes"], "d2h_bytes_per_step": mixed["e2e_bytes"] + 8 * p.nbnd}
+    if not args.no_cpu_baseline and world == 1:
+        out["cpu_baseline"] = cpu_baseline(p)
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def stick_counts(miller, fft):
+    m = np.asarray(miller)
+    sticks = {(a, b) for a, b in zip(m[:, 0].tolist(), m[:, 1].tolist())}
+    planes = {a for a in m[:, 0].tolist()}
+    return len(sticks), len(planes)
+
+
+def kernel_work(name, p, npw, nst, npl, precision, nproj):
+    """Algorithmic (bytes, flops) of one band-application through a kernel class."""
+    n1, n2, n3 = p.fft
+    cs = 16 if precision == 0 else 8
+    x_bytes = n3 * npl * n2 * cs
+    y_bytes = n3 * nst * cs
+    if name == "inv_zy":
+        return 16 * npw + x_bytes, None
+    if name == "xvx_y":
+        return x_bytes + y_bytes, None
+    if name == "fwd_z":
+        return y_bytes + 2 * 16 * npw + 8 * npw, None
+    if name in ("calbec", "addvus"):
+        return None, 8.0 * nproj * npw
+    return None, None
+
+
+def roofline(res, p, npw, nst, npl, precision):
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    ks = res["kernels"]
+    cand = {k: v for k, v in ks.items() if k != "davidson" and v["ms"] > 0}
+    if not cand:
+        return None
+    name = max(cand, key=lambda k: cand[k]["ms"])
+    units = res["band_apps"]
+    byt, flop = kernel_work(name, p, npw, nst, npl, precision, p.nproj)
+    avg_ms = cand[name]["ms"] / cand[name]["launches"]
+    src = {"inv_zy": "local_kernels.cu", "xvx_y": "local_kernels.cu", "fwd_z": "local_kernels.cu",
+           "calbec": "nonlocal_fp64.cu", "addvus": "nonlocal_fp64.cu"}.get(name)
+    traffic = None
+    if src and name in NCU_TRAFFIC and NCU_TRAFFIC[name][0] == file_hash(os.path.join("paper_0906_2569_gb300", "csrc", src)):
+        traffic = NCU_TRAFFIC[name][1]
+    if byt is not None:
+        achieved = units * byt / (cand[name]["ms"] / 1e3) / 1e9
+        peak = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
+        return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "avg_launch_ms": avg_ms,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "bytes_per_band": byt}
+    achieved = units * flop / (cand[name]["ms"] / 1e3) / 1e12
+    return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": FP64_ALU_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_ALU_TFLOPS, "traffic": traffic, "avg_launch_ms": avg_ms,
+            "peak_source": "derived: 152 SMs x 2 DFMA/clk (measured) x 2 flop x 2070 MHz", "flops_per_band": flop}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

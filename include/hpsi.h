@@ -54,6 +54,25 @@ enum hpsi_status {
   HPSI_ENODEV = -7      /* no usable sm_103 device */
 };
 
+enum hpsi_option {
+  HPSI_OPT_PRECOND_TAU = 1,
+  HPSI_OPT_PRECOND_SHIFT = 2,
+  HPSI_OPT_KERNEL_TIMING = 3  /* 1: bracket every launch of the library's kernels with CUDA events */
+};
+
+/* Kernel classes reported by hpsi_kernel_stats. */
+enum hpsi_kernel {
+  HPSI_K_INV_ZY = 0,   /* scatter + inverse z and y transforms per m1-plane */
+  HPSI_K_XVX_Y = 1,    /* inverse x, x V(r), forward x, forward y per z-plane */
+  HPSI_K_FWD_Z = 2,    /* forward z, gather, kinetic term per m1-plane */
+  HPSI_K_CALBEC = 3,   /* <beta|psi> (split-K partial sums) */
+  HPSI_K_DSCALE = 4,   /* reduction of the partials and D <beta|psi> */
+  HPSI_K_ADDVUS = 5,   /* hpsi += beta (D <beta|psi>) */
+  HPSI_K_SPLIT = 6,    /* mixed path: bf16 operand splitting */
+  HPSI_K_DAVIDSON = 7, /* Davidson residual / preconditioner / helper kernels */
+  HPSI_K_COUNT = 8
+};
+
 enum hpsi_precision {
   HPSI_FP64 = 0,  /* every step in float64 / complex128 */
   HPSI_MIXED = 1  /* FFTs and x V(r) in float32, nonlocal contractions as three-product
@@ -155,6 +174,29 @@ HPSI_API int hpsi_apply_batch(hpsi_ctx* ctx, int nitem, const int* prob, const i
  */
 HPSI_API int davidson_solve(hpsi_ctx* ctx, int ik, int nbnd, double tol, int maxiter, void* psi_inout,
                    double* eig_out, int* iters_out, double* resnorm_out);
+
+/*
+ * hpsi_set_option -- tune the Davidson solver of a context (App. A.2.1, the diagonal form of D).
+ *   HPSI_OPT_PRECOND_TAU    value > 0 (Ha): denominators <k+G|H|k+G> - eps of D are kept at
+ *                           |.| >= value (default 0.1).
+ *   HPSI_OPT_PRECOND_SHIFT  0 (default): eps = eps_i, the band's own Ritz value (D approximates
+ *                           (H - eps_i S)^-1);  1: one eps for every band, the highest Ritz value
+ *                           of the block (the estimate of the highest occupied eigenvalue).
+ * HPSI_EINVAL for an unknown option or a bad value.  Host only.
+ */
+HPSI_API int hpsi_set_option(hpsi_ctx* ctx, int option, double value);
+
+/*
+ * hpsi_kernel_stats -- launches of the library's own kernels on ctx since the last reset, and
+ * (with HPSI_OPT_KERNEL_TIMING on) their summed device time in ms from the bracketing events.
+ *   kernel       in   an hpsi_kernel value, -1 for all classes together (total_ms then 0), or
+ *                     -2 for the number of H|psi> band-applications performed (in launches)
+ *   launches     out  nullable; number of launches
+ *   total_ms     out  nullable; summed event time (synchronizes the context's stream)
+ *   reset        in   non-zero: clear the counters after reading
+ * cuBLAS / cuSOLVER kernels of the Davidson subspace algebra are not counted.
+ */
+HPSI_API int hpsi_kernel_stats(hpsi_ctx* ctx, int kernel, long long* launches, double* total_ms, int reset);
 
 /* One-line message for the last failure on ctx (NULL ctx: this thread's last setup failure). */
 HPSI_API const char* hpsi_last_error(const hpsi_ctx* ctx);

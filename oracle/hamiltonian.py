@@ -152,5 +152,6 @@ def h_diagonal(lattice, k, miller, vr, beta, dmat) -> np.ndarray:
     beta = np.asarray(beta, dtype=np.complex128)
     nl = np.zeros_like(t)
     if beta.shape[0]:
-        nl = np.real(np.einsum("pg,pq,qg->g", beta, np.asarray(dmat, dtype=np.complex128), np.conj(beta)))
+        # sum_p beta_p(G) [D conj(beta)]_p(G)
+        nl = np.real(np.sum(beta * (np.asarray(dmat, dtype=np.complex128) @ np.conj(beta)), axis=0))
     return t + vbar + nl

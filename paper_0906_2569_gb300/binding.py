@@ -17,11 +17,14 @@ LIB_PATH = os.path.join(HERE, "libhpsi.so")
 HPSI_OK, HPSI_EINVAL, HPSI_ENOMEM, HPSI_ECUDA = 0, -1, -2, -3
 HPSI_ENOTCONV, HPSI_ESINGULAR, HPSI_ETIMEOUT, HPSI_ENODEV = -4, -5, -6, -7
 HPSI_FP64, HPSI_MIXED = 0, 1
+HPSI_OPT_PRECOND_TAU, HPSI_OPT_PRECOND_SHIFT, HPSI_OPT_KERNEL_TIMING = 1, 2, 3
+KERNELS = ("inv_zy", "xvx_y", "fwd_z", "calbec", "dscale", "addvus", "split", "davidson")
 STATUS_NAMES = {0: "HPSI_OK", -1: "HPSI_EINVAL", -2: "HPSI_ENOMEM", -3: "HPSI_ECUDA", -4: "HPSI_ENOTCONV",
                 -5: "HPSI_ESINGULAR", -6: "HPSI_ETIMEOUT", -7: "HPSI_ENODEV"}
 
 EXPORTS = ("hpsi_gsphere", "hpsi_setup", "hpsi_setup_cells", "hpsi_nprob", "hpsi_npw", "hpsi_nproj", "hpsi_apply",
-           "hpsi_apply_batch", "davidson_solve", "hpsi_last_error", "hpsi_destroy")
+           "hpsi_apply_batch", "davidson_solve", "hpsi_set_option", "hpsi_kernel_stats", "hpsi_last_error",
+           "hpsi_destroy")
 
 _lib = None
 
@@ -52,6 +55,10 @@ def _declare(lib):
     lib.hpsi_apply_batch.restype = I
     lib.davidson_solve.argtypes = [V, I, I, D, I, V, P(D), P(I), P(D)]
     lib.davidson_solve.restype = I
+    lib.hpsi_set_option.argtypes = [V, I, D]
+    lib.hpsi_set_option.restype = I
+    lib.hpsi_kernel_stats.argtypes = [V, I, P(ctypes.c_longlong), P(D), I]
+    lib.hpsi_kernel_stats.restype = I
     lib.hpsi_last_error.argtypes = [V]
     lib.hpsi_last_error.restype = ctypes.c_char_p
     lib.hpsi_destroy.argtypes = [V]
@@ -205,6 +212,20 @@ def hpsi_apply_batch(ctx: Context, probs, psi_list, hpsi_list) -> None:
     rc = ctx.lib.hpsi_apply_batch(ctx.handle, n, pa.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                                   nb.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), pin, pout)
     _check(ctx.lib, ctx.handle, rc, "hpsi_apply_batch")
+
+
+def hpsi_set_option(ctx: Context, option: int, value: float) -> None:
+    """hpsi_set_option(): Davidson preconditioner options."""
+    _check(ctx.lib, ctx.handle, ctx.lib.hpsi_set_option(ctx.handle, int(option), float(value)), "hpsi_set_option")
+
+
+def hpsi_kernel_stats(ctx: Context, kernel: int, reset: bool = False):
+    """hpsi_kernel_stats(): (launches, total ms) of a kernel class; -1 all classes, -2 band-applications."""
+    n = ctypes.c_longlong(0)
+    ms = ctypes.c_double(0.0)
+    _check(ctx.lib, ctx.handle, ctx.lib.hpsi_kernel_stats(ctx.handle, int(kernel), ctypes.byref(n), ctypes.byref(ms),
+                                                          int(bool(reset))), "hpsi_kernel_stats")
+    return n.value, ms.value
 
 
 def davidson_solve(ctx: Context, ik: int, psi_inout, tol: float, maxiter: int, raise_on_notconv: bool = True):

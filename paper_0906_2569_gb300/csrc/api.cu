@@ -28,6 +28,44 @@ int cuda_fail(Context& c, cudaError_t e, const char* what) {
   return HPSI_ECUDA;
 }
 
+static cudaEvent_t pooled_event(Context& c) {
+  if (!c.evpool.empty()) {
+    cudaEvent_t e = c.evpool.back();
+    c.evpool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+int launch_begin(Context& c, int kernel) {
+  c.launches[kernel]++;
+  if (!c.timing) return -1;
+  cudaEvent_t a = pooled_event(c), b = pooled_event(c);
+  cudaEventRecord(a, c.stream);
+  c.trec.push_back({kernel, {a, b}});
+  return (int)c.trec.size() - 1;
+}
+
+void launch_end(Context& c, int slot) {
+  if (slot >= 0) cudaEventRecord(c.trec[slot].second.second, c.stream);
+}
+
+static int collect_timing(Context& c) {
+  if (c.trec.empty()) return HPSI_OK;
+  cudaError_t e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "kernel timing");
+  for (auto& r : c.trec) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.second.first, r.second.second) == cudaSuccess) c.tacc[r.first] += ms;
+    c.evpool.push_back(r.second.first);
+    c.evpool.push_back(r.second.second);
+  }
+  c.trec.clear();
+  return HPSI_OK;
+}
+
 int ensure_buffer(Context& c, void** ptr, size_t* have, size_t need) {
   if (need <= *have && *ptr) return HPSI_OK;
   if (*ptr) {
@@ -212,8 +250,9 @@ static int finish_problem(Context& c, Problem& p, const double* vr, int vslot_sh
     cudaGetLastError();
     return fail(c, HPSI_ENOMEM, "device allocation failed during setup");
   }
-  k_hdiag<<<(p.npw + 255) / 256, 256, 0, c.stream>>>(p.npw, vmean, p.d_kin, p.d_beta, P, p.d_rowptr, p.d_col,
-                                                     p.d_dval, p.d_hdiag);
+  HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
+              (k_hdiag<<<(p.npw + 255) / 256, 256, 0, c.stream>>>(p.npw, vmean, p.d_kin, p.d_beta, P, p.d_rowptr,
+                                                                  p.d_col, p.d_dval, p.d_hdiag)));
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(c, e, "hdiag kernel");
   // band block of the local kernels: keep the X intermediate of one block near 48 MB (L2-resident)
@@ -242,7 +281,10 @@ static void free_problem(Problem& p) {
 }
 
 static void free_context(Context& c) {
-  if (c.stream || true) cudaStreamSynchronize(c.stream);
+  cudaStreamSynchronize(c.stream);
+  collect_timing(c);
+  for (cudaEvent_t e : c.evpool) cudaEventDestroy(e);
+  c.evpool.clear();
   for (auto& p : c.probs) free_problem(p);
   for (auto& t : c.tw) {
     cudaFree(t.d64);
@@ -261,6 +303,7 @@ static void free_context(Context& c) {
 
 int apply_device(Context& c, int ik, const double2* psi, double2* hpsi, int nbnd) {
   const Problem& p = c.probs[ik];
+  c.band_apps += nbnd;
   int rc = local_apply(c, p, psi, hpsi, nbnd);
   if (rc) return rc;
   if (c.precision == HPSI_FP64) return nonlocal_apply_fp64(c, p, psi, hpsi, nbnd);
@@ -540,6 +583,57 @@ extern "C" int davidson_solve(hpsi_ctx* ctx, int ik, int nbnd, double tol, int m
   e = cudaStreamSynchronize(c.stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "davidson_solve");
   return rc;
+}
+
+extern "C" int hpsi_set_option(hpsi_ctx* ctx, int option, double value) {
+  if (!ctx) return HPSI_EINVAL;
+  Context& c = ctx->c;
+  if (option == HPSI_OPT_PRECOND_TAU) {
+    if (!(value > 0.0) || !std::isfinite(value)) return fail(c, HPSI_EINVAL, "HPSI_OPT_PRECOND_TAU must be > 0");
+    c.opt_tau = value;
+    return HPSI_OK;
+  }
+  if (option == HPSI_OPT_KERNEL_TIMING) {
+    if (value != 0.0 && value != 1.0) return fail(c, HPSI_EINVAL, "HPSI_OPT_KERNEL_TIMING must be 0 or 1");
+    c.timing = value != 0.0;
+    return HPSI_OK;
+  }
+  if (option == HPSI_OPT_PRECOND_SHIFT) {
+    if (value != 0.0 && value != 1.0) return fail(c, HPSI_EINVAL, "HPSI_OPT_PRECOND_SHIFT must be 0 or 1");
+    c.opt_shift = (int)value;
+    return HPSI_OK;
+  }
+  return fail(c, HPSI_EINVAL, "unknown option " + std::to_string(option));
+}
+
+extern "C" int hpsi_kernel_stats(hpsi_ctx* ctx, int kernel, long long* launches, double* total_ms, int reset) {
+  if (!ctx) return HPSI_EINVAL;
+  Context& c = ctx->c;
+  if (kernel < -2 || kernel >= HPSI_K_COUNT) return fail(c, HPSI_EINVAL, "hpsi_kernel_stats: bad kernel class");
+  if (kernel == -2) {
+    if (launches) *launches = c.band_apps;
+    if (total_ms) *total_ms = 0.0;
+    if (reset) c.band_apps = 0;
+    return HPSI_OK;
+  }
+  int rc = collect_timing(c);
+  if (rc) return rc;
+  long long n = 0;
+  double ms = 0.0;
+  for (int k = 0; k < HPSI_K_COUNT; ++k)
+    if (kernel == -1 || kernel == k) {
+      n += c.launches[k];
+      if (kernel != -1) ms += c.tacc[k];
+    }
+  if (launches) *launches = n;
+  if (total_ms) *total_ms = ms;
+  if (reset)
+    for (int k = 0; k < HPSI_K_COUNT; ++k)
+      if (kernel == -1 || kernel == k) {
+        c.launches[k] = 0;
+        c.tacc[k] = 0.0;
+      }
+  return HPSI_OK;
 }
 
 extern "C" const char* hpsi_last_error(const hpsi_ctx* ctx) {

@@ -7,12 +7,18 @@
 //                  to 4N vectors, then restarted from the N Ritz vectors
 //   reduced problem sum_k (H_jk - eps S_jk) c_k = 0, psi_i <- sum_j c^(i)_j phi_j
 //
-// The basis is kept orthonormal: every block of corrections is projected out of the basis twice
-// (block Gram-Schmidt) and orthonormalised through the eigen-decomposition of its own overlap
-// matrix, dropping directions whose overlap eigenvalue is below 1e-12 of the largest (this is
-// what keeps the free-electron case, where D is exact and delta psi_i is parallel to psi_i,
-// well posed).  S_jk is then the identity and the reduced problem is solved as a standard
-// Hermitian one (cuSOLVER zheevd).  Subspace products are cuBLAS ZGEMMs (library GEMMs);
+// The basis is kept orthonormal: every block of corrections (each scaled to unit norm) is
+// projected out of the basis twice (block Gram-Schmidt) and orthonormalised through the
+// eigen-decomposition of its own overlap matrix, dropping directions whose overlap eigenvalue
+// is below 1e-8.  A correction that loses all but 1e-3 of its norm to the projection lies in the
+// basis up to rounding (this is what an exact diagonal D does: for a diagonal H, D g_i is
+// parallel to psi_i); it is replaced by its raw residual g_i, which the Galerkin condition makes
+// orthogonal to the basis.  S_jk is then the identity and the reduced problem is solved as a
+// standard Hermitian one (cuSOLVER zheevd).
+//
+// The eps in D is eps_i per band by default (D approximates (H - eps_i S)^-1); option
+// HPSI_OPT_PRECOND_SHIFT = 1 takes one eps for all bands, the highest Ritz value of the block
+// (the "estimate of the highest occupied eigenvalue" of the diagonal form of D).  Subspace products are cuBLAS ZGEMMs (library GEMMs);
 // residuals, norms and the preconditioner are the kernels below.  Only the residual norms and
 // eigenvalues cross to the host each iteration.
 #include <cublas_v2.h>
@@ -29,8 +35,8 @@ namespace hpsi {
 
 namespace {
 
-constexpr double kPrecondTau = 0.1;   // Ha, |H_GG - eps_i| is kept >= tau
-constexpr double kDropRel = 1e-12;    // overlap eigenvalues below this (relative) are dropped
+constexpr double kDropAbs = 1e-8;     // overlap eigenvalues of unit corrections below this are dropped
+constexpr double kCollapse = 1e-6;    // squared norm left after projection that marks a collapse
 
 struct DavWork {
   int npw = 0, nbnd = 0, mmax = 0;
@@ -47,6 +53,8 @@ struct DavWork {
   double* eps = nullptr;     // [nbnd]
   double* rnorm = nullptr;   // [nbnd]
   int* idx = nullptr;        // [nbnd] unconverged band list
+  int* idx2 = nullptr;       // [nbnd] collapsed corrections
+  double* cn2 = nullptr;     // [nbnd] squared norms of the corrections
   int* info = nullptr;
   double2* work = nullptr;
   int lwork = 0;
@@ -81,11 +89,11 @@ __global__ void __launch_bounds__(256) k_residual(int npw, const double2* __rest
 // T_j = R_{idx[j]} / clamp(hdiag - eps_{idx[j]}), then T_j /= ||T_j||; one CTA per correction.
 __global__ void __launch_bounds__(256) k_precondition(int npw, const int* __restrict__ idx,
                                                       const double2* __restrict__ r, const double* __restrict__ hdiag,
-                                                      const double* __restrict__ eps, double tau,
+                                                      const double* __restrict__ eps, double tau, int eshift,
                                                       double2* __restrict__ t) {
   const int j = blockIdx.x;
   const int i = idx[j];
-  const double e = eps[i];
+  const double e = eps[eshift >= 0 ? eshift : i];
   const double2* rb = r + (size_t)i * npw;
   double2* tb = t + (size_t)j * npw;
   double s = 0.0;
@@ -106,6 +114,32 @@ __global__ void __launch_bounds__(256) k_precondition(int npw, const int* __rest
   const double nrm = red[0];
   const double inv = nrm > 0.0 ? 1.0 / sqrt(nrm) : 0.0;
   for (int g = threadIdx.x; g < npw; g += blockDim.x) tb[g] = make_double2(tb[g].x * inv, tb[g].y * inv);
+}
+
+// ||t_j||^2 for each vector of a block; one CTA per vector.
+__global__ void __launch_bounds__(256) k_norm2(int npw, const double2* __restrict__ t, double* __restrict__ out) {
+  const double2* tb = t + (size_t)blockIdx.x * npw;
+  double s = 0.0;
+  for (int g = threadIdx.x; g < npw; g += blockDim.x) s += tb[g].x * tb[g].x + tb[g].y * tb[g].y;
+  __shared__ double red[256];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = red[0];
+}
+
+// t_j <- r_{idx[j]} / ||r_{idx[j]}|| for the listed j (collapsed corrections); one CTA per entry.
+__global__ void k_fallback(int npw, const int* __restrict__ which, const int* __restrict__ idx,
+                           const double2* __restrict__ r, const double* __restrict__ rnorm, double2* __restrict__ t) {
+  const int j = which[blockIdx.x];
+  const int i = idx[j];
+  const double s = 1.0 / rnorm[i];
+  const double2* rb = r + (size_t)i * npw;
+  double2* tb = t + (size_t)j * npw;
+  for (int g = threadIdx.x; g < npw; g += blockDim.x) tb[g] = make_double2(rb[g].x * s, rb[g].y * s);
 }
 
 // Columns of the eigenvector matrix V (n x n, ld) scaled by 1/sqrt(lambda) for kept directions,
@@ -173,6 +207,8 @@ static void free_work(DavWork& w) {
   cudaFree(w.eps);
   cudaFree(w.rnorm);
   cudaFree(w.idx);
+  cudaFree(w.idx2);
+  cudaFree(w.cn2);
   cudaFree(w.info);
   cudaFree(w.work);
   w = DavWork();
@@ -211,7 +247,8 @@ static int alloc_work(Context& c, DavHandles& h, int npw, int nbnd) {
             al((void**)&w.small, sizeof(double2) * (size_t)mmax * nbnd) &&
             al((void**)&w.ovl, sizeof(double2) * (size_t)nbnd * nbnd) && al((void**)&w.w, sizeof(double) * mmax) &&
             al((void**)&w.eps, sizeof(double) * nbnd) && al((void**)&w.rnorm, sizeof(double) * nbnd) &&
-            al((void**)&w.idx, sizeof(int) * nbnd) && al((void**)&w.info, sizeof(int));
+            al((void**)&w.idx, sizeof(int) * nbnd) && al((void**)&w.idx2, sizeof(int) * nbnd) &&
+            al((void**)&w.cn2, sizeof(double) * nbnd) && al((void**)&w.info, sizeof(int));
   if (!ok) {
     free_work(w);
     return fail(c, HPSI_ENOMEM, "davidson_solve: device allocation of the reduced basis failed");
@@ -231,7 +268,7 @@ static int alloc_work(Context& c, DavHandles& h, int npw, int nbnd) {
 // eigen-decomposition of the leading n x n block of a (ld) into w.evec / w.w (ascending)
 static int small_eigh(Context& c, DavHandles& h, const double2* a, int lda, int n) {
   DavWork& w = h.wk;
-  k_copy_matrix<<<(n * n + 255) / 256, 256, 0, c.stream>>>(n, n, a, lda, w.evec, n);
+  HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_copy_matrix<<<(n * n + 255) / 256, 256, 0, c.stream>>>(n, n, a, lda, w.evec, n)));
   BCK(cusolverDnZheevd(h.solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, n, Z(w.evec), n, w.w, Z(w.work),
                        w.lwork, w.info),
       "cusolverDnZheevd");
@@ -243,9 +280,10 @@ static int small_eigh(Context& c, DavHandles& h, const double2* a, int lda, int 
 }
 
 // Orthonormalise the block x[0:n] (band-major, npw) against itself: overlap S = x^H x, S = V L V^H,
-// x <- x V_keep L_keep^{-1/2}, with directions of L below kDropRel * max(L) dropped.  The result
-// (nkeep vectors) is written to out (may alias nothing in x).  Returns nkeep through *nkeep.
-static int canonical_orth(Context& c, DavHandles& h, const double2* x, int n, double2* out, int* nkeep) {
+// x <- x V_keep L_keep^{-1/2}, keeping directions with L > thr (thr relative to max(L) when
+// relative is set).  The result (nkeep vectors) goes to out, which must not overlap x.
+static int canonical_orth(Context& c, DavHandles& h, const double2* x, int n, double2* out, int* nkeep, double thr,
+                          bool relative) {
   DavWork& w = h.wk;
   const int npw = w.npw;
   BCK(cublasZgemm(h.blas, CUBLAS_OP_C, CUBLAS_OP_N, n, n, npw, &kOne, Z(x), npw, Z(x), npw, &kZero, Z(w.ovl), n),
@@ -256,13 +294,13 @@ static int canonical_orth(Context& c, DavHandles& h, const double2* x, int n, do
   std::vector<double> lam(n);
   DCK(cudaMemcpyAsync(lam.data(), w.w, sizeof(double) * n, cudaMemcpyDeviceToHost, c.stream), "overlap eigenvalues");
   DCK(cudaStreamSynchronize(c.stream), "overlap eigenvalues");
-  const double lmax = lam[n - 1];
+  const double cut = relative ? thr * lam[n - 1] : thr;
   int first = 0;
-  while (first < n && !(lam[first] > kDropRel * lmax && lam[first] > 1e-300)) ++first;
+  while (first < n && !(lam[first] > cut && lam[first] > 1e-300)) ++first;
   const int nk = n - first;
   *nkeep = nk;
   if (nk == 0) return HPSI_OK;
-  k_canon_scale<<<(n * nk + 255) / 256, 256, 0, c.stream>>>(n, n, first, nk, w.evec, w.w, w.small);
+  HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_canon_scale<<<(n * nk + 255) / 256, 256, 0, c.stream>>>(n, n, first, nk, w.evec, w.w, w.small)));
   BCK(cublasZgemm(h.blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, nk, n, &kOne, Z(x), npw, Z(w.small), n, &kZero, Z(out), npw),
       "zgemm orthonormalise");
   return HPSI_OK;
@@ -288,7 +326,7 @@ int davidson_run(Context& c, int ik, int nbnd, double tol, int maxiter, double2*
 
   // phi[0:N] <- orthonormalised initial guess
   int nk = 0;
-  rc = canonical_orth(c, *h, psio, N, w.phi, &nk);
+  rc = canonical_orth(c, *h, psio, N, w.phi, &nk, 1e-12, true);
   if (rc) return rc;
   if (nk < N) return fail(c, HPSI_EINVAL, "davidson_solve: initial guess is linearly dependent");
   rc = apply_device(c, ik, w.phi, w.hphi, N);
@@ -312,7 +350,7 @@ int davidson_run(Context& c, int ik, int nbnd, double tol, int maxiter, double2*
                     Z(w.hpsi), npw),
         "zgemm H Ritz vectors");
     DCK(cudaMemcpyAsync(w.eps, w.w, sizeof(double) * N, cudaMemcpyDeviceToDevice, c.stream), "eps copy");
-    k_residual<<<N, 256, 0, c.stream>>>(npw, w.psi, w.hpsi, w.eps, w.t, w.rnorm);
+    HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_residual<<<N, 256, 0, c.stream>>>(npw, w.psi, w.hpsi, w.eps, w.t, w.rnorm)));
     DCK(cudaGetLastError(), "residual kernel");
     DCK(cudaMemcpyAsync(rn.data(), w.rnorm, sizeof(double) * N, cudaMemcpyDeviceToHost, c.stream), "norm copy");
     DCK(cudaMemcpyAsync(ev.data(), w.eps, sizeof(double) * N, cudaMemcpyDeviceToHost, c.stream), "eig copy");
@@ -341,20 +379,37 @@ int davidson_run(Context& c, int ik, int nbnd, double tol, int maxiter, double2*
     DCK(cudaMemcpyAsync(w.idx, uidx.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, c.stream), "index copy");
     // corrections into phi[m : m+nc] (t holds the residuals)
     double2* tnew = w.phi + (size_t)m * npw;
-    k_precondition<<<nc, 256, 0, c.stream>>>(npw, w.idx, w.t, p.d_hdiag, w.eps, kPrecondTau, tnew);
+    const int eshift = c.opt_shift == 1 ? N - 1 : -1;
+    HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_precondition<<<nc, 256, 0, c.stream>>>(npw, w.idx, w.t, p.d_hdiag, w.eps, c.opt_tau, eshift, tnew)));
     DCK(cudaGetLastError(), "precondition kernel");
-    // two passes of block Gram-Schmidt against phi[0:m]
-    for (int pass = 0; pass < 2; ++pass) {
-      BCK(cublasZgemm(h->blas, CUBLAS_OP_C, CUBLAS_OP_N, m, nc, npw, &kOne, Z(w.phi), npw, Z(tnew), npw, &kZero,
-                      Z(w.small), m),
-          "zgemm projection");
-      BCK(cublasZgemm(h->blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, nc, m, &kMinusOne, Z(w.phi), npw, Z(w.small), m, &kOne,
-                      Z(tnew), npw),
-          "zgemm projection update");
+    for (int round = 0; round < 2; ++round) {
+      // two passes of block Gram-Schmidt against phi[0:m]
+      for (int pass = 0; pass < 2; ++pass) {
+        BCK(cublasZgemm(h->blas, CUBLAS_OP_C, CUBLAS_OP_N, m, nc, npw, &kOne, Z(w.phi), npw, Z(tnew), npw, &kZero,
+                        Z(w.small), m),
+            "zgemm projection");
+        BCK(cublasZgemm(h->blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, nc, m, &kMinusOne, Z(w.phi), npw, Z(w.small), m,
+                        &kOne, Z(tnew), npw),
+            "zgemm projection update");
+      }
+      if (round == 1) break;
+      // corrections that lie in the basis are replaced by their raw residuals
+      HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_norm2<<<nc, 256, 0, c.stream>>>(npw, tnew, w.cn2)));
+      std::vector<double> cn(nc);
+      DCK(cudaMemcpyAsync(cn.data(), w.cn2, sizeof(double) * nc, cudaMemcpyDeviceToHost, c.stream), "norm copy");
+      DCK(cudaStreamSynchronize(c.stream), "correction norms");
+      std::vector<int> col;
+      for (int j = 0; j < nc; ++j)
+        if (!(cn[j] >= kCollapse)) col.push_back(j);
+      if (col.empty()) break;
+      DCK(cudaMemcpyAsync(w.idx2, col.data(), sizeof(int) * col.size(), cudaMemcpyHostToDevice, c.stream),
+          "index copy");
+      HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_fallback<<<(int)col.size(), 256, 0, c.stream>>>(npw, w.idx2, w.idx, w.t, w.rnorm, tnew)));
+      DCK(cudaGetLastError(), "fallback kernel");
     }
     // orthonormalise the block itself (w.t is free now: residuals were consumed)
     int nkeep = 0;
-    rc = canonical_orth(c, *h, tnew, nc, w.t, &nkeep);
+    rc = canonical_orth(c, *h, tnew, nc, w.t, &nkeep, kDropAbs, false);
     if (rc) return rc;
     if (nkeep == 0) {
       // nothing new can be added: the residuals lie in the basis up to rounding

@@ -40,16 +40,6 @@ struct PlaneDev {
   int g0;
 };
 
-// Nonlocal data of a problem in the layouts the kernels read.
-struct NonlocalDev {
-  int nproj;
-  const double2* beta;      // [P][npw] complex128
-  const int* d_rowptr;      // CSR of D: [P+1]
-  const int* d_col;         // [nnz]
-  const double2* d_val;     // [nnz]
-  const uint16_t* beta_bf;  // mixed path: bf16 split planes of beta (see nonlocal_tc.cu)
-};
-
 struct Problem {
   double cell[9];
   double recip[9];
@@ -61,7 +51,6 @@ struct Problem {
   std::vector<StickDev> sticks;
   std::vector<PlaneDev> planes;
   std::vector<double> kin;      // |k+G|^2 / 2
-  std::vector<double> hdiag;    // <k+G|H|k+G>, for the Davidson preconditioner
   // device
   StickDev* d_sticks = nullptr;
   PlaneDev* d_planes = nullptr;
@@ -108,9 +97,27 @@ struct Context {
   std::vector<void*> vbufs;            // owned V buffers (64 and 32 bit)
   Workspace ws;
   std::string err;
-  void* blas = nullptr;                // cublasHandle_t (Davidson)
-  void* solver = nullptr;              // cusolverDnHandle_t (Davidson)
+  double opt_tau = 0.1;                // Davidson: |<k+G|H|k+G> - eps| is kept >= tau (Ha)
+  int opt_shift = 0;                   // Davidson: 0 = eps_i per band, 1 = highest Ritz value
+  void* blas = nullptr;                // Davidson handles and work buffers
+  // launch accounting (always) and per-launch event timing (HPSI_OPT_KERNEL_TIMING)
+  bool timing = false;
+  long long launches[HPSI_K_COUNT] = {0};
+  long long band_apps = 0;             // H|psi> band-applications performed
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> trec;   // (kernel, start, end)
+  std::vector<cudaEvent_t> evpool;
+  double tacc[HPSI_K_COUNT] = {0.0};
 };
+
+// Bracket one launch: call before (returns a record slot or -1) and after the launch.
+int launch_begin(Context& c, int kernel);
+void launch_end(Context& c, int slot);
+#define HPSI_LAUNCH(ctx, kid, ...)                 \
+  do {                                             \
+    const int slot_ = ::hpsi::launch_begin(ctx, kid); \
+    __VA_ARGS__;                                   \
+    ::hpsi::launch_end(ctx, slot_);                \
+  } while (0)
 
 // ---- host helpers (plan.cpp) ----
 void reciprocal(const double cell[9], double recip[9]);

@@ -201,9 +201,9 @@ static int local_apply_t(Context& c, const Problem& p, const double2* psi, doubl
     a.nb = nb;
     a.psi = psi + (size_t)b0 * p.npw;
     a.hpsi = hpsi + (size_t)b0 * p.npw;
-    k_inv_zy<T><<<dim3(p.npl, nb), 256, s0, c.stream>>>(a);
-    k_xvx_y<T><<<dim3(p.n[2], nb), 256, s1, c.stream>>>(a);
-    k_fwd_z<T><<<dim3(p.npl, nb), 256, s2, c.stream>>>(a);
+    HPSI_LAUNCH(c, HPSI_K_INV_ZY, (k_inv_zy<T><<<dim3(p.npl, nb), 256, s0, c.stream>>>(a)));
+    HPSI_LAUNCH(c, HPSI_K_XVX_Y, (k_xvx_y<T><<<dim3(p.n[2], nb), 256, s1, c.stream>>>(a)));
+    HPSI_LAUNCH(c, HPSI_K_FWD_Z, (k_fwd_z<T><<<dim3(p.npl, nb), 256, s2, c.stream>>>(a)));
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(c, e, "local-potential kernels launch");

@@ -156,11 +156,16 @@ int nonlocal_apply_fp64(Context& c, const Problem& p, const double2* psi, double
   if (rc) return rc;
   double2* part = reinterpret_cast<double2*>(c.ws.part);
   double2* w = reinterpret_cast<double2*>(c.ws.w);
-  k_calbec64<<<dim3(tilesp, tilesb, nsplit), 256, 0, c.stream>>>(p.npw, p.nproj, nbnd, kchunk, p.d_beta, psi, part);
+  HPSI_LAUNCH(c, HPSI_K_CALBEC,
+              (k_calbec64<<<dim3(tilesp, tilesb, nsplit), 256, 0, c.stream>>>(p.npw, p.nproj, nbnd, kchunk,
+                                                                              p.d_beta, psi, part)));
   const int n = p.nproj * nbnd;
-  k_dscale64<<<(n + 255) / 256, 256, 0, c.stream>>>(p.nproj, nbnd, nsplit, part, p.d_rowptr, p.d_col, p.d_dval, w);
-  k_addvus64<<<dim3((p.npw + AV_TG - 1) / AV_TG, (nbnd + AV_TB - 1) / AV_TB), 256, 0, c.stream>>>(
-      p.npw, p.nproj, nbnd, w, p.d_beta, hpsi);
+  HPSI_LAUNCH(c, HPSI_K_DSCALE,
+              (k_dscale64<<<(n + 255) / 256, 256, 0, c.stream>>>(p.nproj, nbnd, nsplit, part, p.d_rowptr, p.d_col,
+                                                                 p.d_dval, w)));
+  HPSI_LAUNCH(c, HPSI_K_ADDVUS,
+              (k_addvus64<<<dim3((p.npw + AV_TG - 1) / AV_TG, (nbnd + AV_TB - 1) / AV_TB), 256, 0, c.stream>>>(
+                  p.npw, p.nproj, nbnd, w, p.d_beta, hpsi)));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(c, e, "nonlocal float64 kernels launch");
   return HPSI_OK;

@@ -45,11 +45,14 @@ def test_davidson_fp64_c1(lib):
 
 
 def test_davidson_free_electron(lib):
-    """V = 0, no projectors: eigenvalues are the sorted |k+G|^2/2 (the preconditioner is exact)."""
+    """V = 0, no projectors: eigenvalues are the sorted |k+G|^2/2.  The diagonal D is exact here, so
+    each correction D g_i is parallel to psi_i; with one eps for all bands (the highest Ritz value)
+    the corrections are not, and the lowest eigenpairs are found."""
     import torch
     from paper_0906_2569_gb300 import binding as B
     p = workloads.config1()
     ctx, m, vr, beta, d = _setup(p, zero_potential=True)
+    B.hpsi_set_option(ctx, B.HPSI_OPT_PRECOND_SHIFT, 1)
     x = torch.from_numpy(workloads.psi0(p.lattice, p.kpts[0], m, p.nbnd, p.psi_seed)).cuda()
     eig, it, res, rc = B.davidson_solve(ctx, 0, x, 1e-8, 300)
     t = np.sort(oracle.gsphere.kinetic(p.lattice, p.kpts[0], m))[:p.nbnd]
@@ -68,6 +71,10 @@ def test_davidson_notconv_and_errors(lib):
         B.davidson_solve(ctx, 0, torch.zeros((p.nbnd, len(m)), dtype=torch.complex128, device="cuda"), 1e-8, 10)
     with pytest.raises(B.HpsiError):
         B.davidson_solve(ctx, 0, x, -1.0, 10)
+    with pytest.raises(B.HpsiError):
+        B.hpsi_set_option(ctx, 99, 1.0)
+    with pytest.raises(B.HpsiError):
+        B.hpsi_set_option(ctx, B.HPSI_OPT_PRECOND_TAU, 0.0)
 
 
 def test_davidson_host_buffer(lib):
