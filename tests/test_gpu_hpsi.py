@@ -135,7 +135,7 @@ def test_hpsi_errors(lib):
         B.hpsi_apply(ctx, 0, x, np.zeros((2, len(m)), dtype=np.complex128))   # host / device mix
     B.hpsi_apply(ctx, 0, x, torch.empty_like(x), 0)  # nbnd = 0 is a no-op
     with pytest.raises(B.HpsiError) as e:
-        B.hpsi_setup(p.lattice, p.ecut, p.kpts, (16, 16, 16), vr[:16, :16, :16], [beta], d)
+        B.hpsi_setup(p.lattice, p.ecut, p.kpts, (12, 12, 12), vr[:12, :12, :12], [beta], d)
     assert e.value.status == B.HPSI_EINVAL       # box too small for the sphere
     with pytest.raises(B.HpsiError):
         B.hpsi_setup(p.lattice, p.ecut, p.kpts, (33, 33, 33), np.zeros((33, 33, 33)), [beta], d)   # 33 = 3 * 11
