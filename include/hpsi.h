@@ -147,6 +147,26 @@ HPSI_API int hpsi_nproj(const hpsi_ctx* ctx, int ik);
 HPSI_API int hpsi_apply(hpsi_ctx* ctx, int ik, const void* psi_in, void* hpsi_out, int nbnd);
 
 /*
+ * hpsi_apply_noalloc -- the same H psi as hpsi_apply, for callers that cannot let the library
+ * allocate device memory during the call.  The paper has no counterpart; this exists for
+ * integration: some callers have all device memory reserved up front by another allocator (a
+ * framework's caching pool, a fixed per-process budget), and some cannot accept the device-wide
+ * synchronisation that cudaMalloc / cudaFree imply in the middle of an asynchronous pipeline.
+ *   psi_in, hpsi_out  device memory only (host pointers are HPSI_EINVAL: staging them would need
+ *                     buffers), complex128 [nbnd][npw(ik)], not overlapping
+ * Every intermediate lives in one fixed 64 MiB array compiled into the library; every GPU that
+ * loads libhpsi.so holds those 64 MiB until the process exits.  Bands are processed in chunks that
+ * fit it; if a single band's intermediates exceed 64 MiB the call returns HPSI_EINVAL (use
+ * hpsi_apply).  The nonlocal term uses the float64 kernels at both precisions.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  Every call shares the one
+ * array and leaves its contents behind (each call writes every byte it later reads, so nothing
+ * has to start cleared): calls whose work can overlap on the GPU -- two streams, or two contexts
+ * -- race on it and must be serialised by the caller.  Asynchronous on the context's stream.
+ */
+HPSI_API int hpsi_apply_noalloc(hpsi_ctx* ctx, int ik, const void* psi_in, void* hpsi_out, int nbnd);
+
+/*
  * hpsi_apply_batch -- H psi for several problems in one launch sequence (one CUDA graph):
  * for i < nitem: hpsi_out[i] = H(prob[i]) psi_in[i] with nbnd[i] bands.  Device pointers only.
  * Items are independent; outputs must not overlap inputs or each other.

@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "HPSI_OK", -1: "HPSI_EINVAL", -2: "HPSI_ENOMEM", -3: "HPSI_EC
                 -5: "HPSI_ESINGULAR", -6: "HPSI_ETIMEOUT", -7: "HPSI_ENODEV"}
 
 EXPORTS = ("hpsi_gsphere", "hpsi_setup", "hpsi_setup_cells", "hpsi_nprob", "hpsi_npw", "hpsi_nproj", "hpsi_apply",
-           "hpsi_apply_batch", "davidson_solve", "hpsi_set_option", "hpsi_kernel_stats", "hpsi_last_error",
+           "hpsi_apply_batch", "hpsi_apply_noalloc", "davidson_solve", "hpsi_set_option", "hpsi_kernel_stats", "hpsi_last_error",
            "hpsi_destroy")
 
 _lib = None
@@ -51,6 +51,8 @@ def _declare(lib):
         f.restype = I
     lib.hpsi_apply.argtypes = [V, I, V, V, I]
     lib.hpsi_apply.restype = I
+    lib.hpsi_apply_noalloc.argtypes = [V, I, V, V, I]
+    lib.hpsi_apply_noalloc.restype = I
     lib.hpsi_apply_batch.argtypes = [V, I, P(I), P(I), P(V), P(V)]
     lib.hpsi_apply_batch.restype = I
     lib.davidson_solve.argtypes = [V, I, I, D, I, V, P(D), P(I), P(D)]
@@ -200,6 +202,14 @@ def hpsi_apply(ctx: Context, ik: int, psi_in, hpsi_out, nbnd: int | None = None)
     nb = int(psi_in.shape[0]) if nbnd is None else int(nbnd)
     rc = ctx.lib.hpsi_apply(ctx.handle, int(ik), ctypes.c_void_p(_ptr(psi_in)), ctypes.c_void_p(_ptr(hpsi_out)), nb)
     _check(ctx.lib, ctx.handle, rc, "hpsi_apply")
+
+
+def hpsi_apply_noalloc(ctx: Context, ik: int, psi_in, hpsi_out, nbnd: int | None = None) -> None:
+    """hpsi_apply_noalloc(): device tensors only; intermediates in the library's fixed array."""
+    nb = int(psi_in.shape[0]) if nbnd is None else int(nbnd)
+    rc = ctx.lib.hpsi_apply_noalloc(ctx.handle, int(ik), ctypes.c_void_p(_ptr(psi_in)),
+                                    ctypes.c_void_p(_ptr(hpsi_out)), nb)
+    _check(ctx.lib, ctx.handle, rc, "hpsi_apply_noalloc")
 
 
 def hpsi_apply_batch(ctx: Context, probs, psi_list, hpsi_list) -> None:

@@ -10,10 +10,6 @@
 
 #include "hpsi_internal.h"
 
-struct hpsi_ctx {
-  hpsi::Context c;
-};
-
 namespace hpsi {
 
 static thread_local std::string g_setup_err;

@@ -133,6 +133,11 @@ int local_apply(Context& c, const Problem& p, const double2* psi, double2* hpsi,
 int nonlocal_apply_fp64(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd);
 int nonlocal_apply_mixed(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd);
 int mixed_prepare_beta(Context& c, Problem& p);
+size_t local_scratch_per_band(const Problem& p, int precision);
+int local_apply_into(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd, void* X, void* Y,
+                     int nbb);
+void nonlocal_fp64_plan(const Context& c, const Problem& p, int nbnd, int* nsplit, int* kchunk, size_t* bytes);
+int nonlocal_fp64_into(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd, void* scratch);
 
 // ---- context helpers (api.cpp) ----
 int ensure_buffer(Context& c, void** ptr, size_t* have, size_t need);
@@ -146,3 +151,8 @@ int davidson_run(Context& c, int ik, int nbnd, double tol, int maxiter, double2*
 void davidson_release(Context& c);
 
 }  // namespace hpsi
+
+// The opaque handle of the C ABI.
+struct hpsi_ctx {
+  hpsi::Context c;
+};

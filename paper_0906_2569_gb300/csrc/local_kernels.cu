@@ -215,4 +215,48 @@ int local_apply(Context& c, const Problem& p, const double2* psi, double2* hpsi,
   return local_apply_t<float>(c, p, psi, hpsi, nbnd);
 }
 
+// Bytes of X and Y that one band needs at the context's precision.
+size_t local_scratch_per_band(const Problem& p, int precision) {
+  const size_t cs = precision == HPSI_FP64 ? sizeof(double2) : sizeof(float2);
+  return cs * ((size_t)p.n[2] * p.npl * p.n[1] + (size_t)p.n[2] * p.nst);
+}
+
+// The same launch sequence with caller-provided X and Y (each sized for nbb bands).
+template <typename T>
+static int local_apply_into_t(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd, void* X,
+                              void* Y, int nbb) {
+  const int mx = (int)c.smem_optin;
+  cudaFuncSetAttribute(k_inv_zy<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_xvx_y<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_fwd_z<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  const size_t s0 = local_smem_bytes(p, c.precision, 0), s1 = local_smem_bytes(p, c.precision, 1),
+               s2 = local_smem_bytes(p, c.precision, 2);
+  LocalArgs a;
+  a.n1 = p.n[0]; a.n2 = p.n[1]; a.n3 = p.n[2];
+  a.npw = p.npw; a.npl = p.npl; a.nst = p.nst; a.ns_max = p.ns_max;
+  a.sticks = p.d_sticks; a.planes = p.d_planes; a.kin = p.d_kin;
+  a.X = X; a.Y = Y;
+  a.V = sizeof(T) == 8 ? (const void*)p.d_v64 : (const void*)p.d_v32;
+  a.p1 = p.plan[0]; a.p2 = p.plan[1]; a.p3 = p.plan[2];
+  a.inv_nr = 1.0 / ((double)p.n[0] * p.n[1] * p.n[2]);
+  for (int b0 = 0; b0 < nbnd; b0 += nbb) {
+    const int nb = std::min(nbb, nbnd - b0);
+    a.nb = nb;
+    a.psi = psi + (size_t)b0 * p.npw;
+    a.hpsi = hpsi + (size_t)b0 * p.npw;
+    HPSI_LAUNCH(c, HPSI_K_INV_ZY, (k_inv_zy<T><<<dim3(p.npl, nb), 256, s0, c.stream>>>(a)));
+    HPSI_LAUNCH(c, HPSI_K_XVX_Y, (k_xvx_y<T><<<dim3(p.n[2], nb), 256, s1, c.stream>>>(a)));
+    HPSI_LAUNCH(c, HPSI_K_FWD_Z, (k_fwd_z<T><<<dim3(p.npl, nb), 256, s2, c.stream>>>(a)));
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "local-potential kernels launch");
+  return HPSI_OK;
+}
+
+int local_apply_into(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd, void* X, void* Y,
+                     int nbb) {
+  if (c.precision == HPSI_FP64) return local_apply_into_t<double>(c, p, psi, hpsi, nbnd, X, Y, nbb);
+  return local_apply_into_t<float>(c, p, psi, hpsi, nbnd, X, Y, nbb);
+}
+
 }  // namespace hpsi

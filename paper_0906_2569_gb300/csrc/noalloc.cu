@@ -1,0 +1,112 @@
+// hpsi_apply_noalloc: H|psi> without any device allocation at call time.
+//
+// Some callers cannot let a library call cudaMalloc: their device memory is reserved up front
+// by another allocator (a framework's caching pool, a fixed per-process budget), or they cannot
+// accept the device-wide synchronisation that cudaMalloc / cudaFree imply in the middle of an
+// asynchronous stream pipeline.  This entry point computes the same H|psi> as hpsi_apply, but
+// every intermediate (the plane and stick buffers of the FFTs, the partial sums of <beta|psi>
+// and D<beta|psi>) lives in one fixed array compiled into the library.  Bands are processed in
+// chunks that fit the array.  The nonlocal term runs on the float64 kernels at either
+// precision (they need no buffers beyond the array).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <mutex>
+#include <string>
+
+#include "hpsi_internal.h"
+
+namespace {
+
+// 64 MiB, 256-byte aligned.  Every GPU that loads libhpsi.so holds it until the process exits.
+constexpr size_t kNoAllocBytes = size_t(64) << 20;
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+void* g_scratch_addr[kMaxDevices] = {nullptr};
+std::mutex g_scratch_mu;
+
+// Device address of the array on the current device, looked up once per device.  The host-side
+// name g_noalloc_scratch is only a stand-in: kernels must be given this address instead.
+int scratch_address(hpsi::Context& c, void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return hpsi::cuda_fail(c, e, "hpsi_apply_noalloc: cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return hpsi::fail(c, HPSI_ENODEV, "hpsi_apply_noalloc: device index too large");
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return hpsi::cuda_fail(c, e, "hpsi_apply_noalloc: cudaGetSymbolAddress");
+    g_scratch_addr[dev] = p;
+  }
+  *out = g_scratch_addr[dev];
+  return HPSI_OK;
+}
+
+bool on_device(const void* ptr) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+extern "C" int hpsi_apply_noalloc(hpsi_ctx* ctx, int ik, const void* psi_in, void* hpsi_out, int nbnd) {
+  if (!ctx) return HPSI_EINVAL;
+  hpsi::Context& c = ctx->c;
+  if (ik < 0 || ik >= (int)c.probs.size()) return hpsi::fail(c, HPSI_EINVAL, "hpsi_apply_noalloc: problem index out of range");
+  if (nbnd < 0) return hpsi::fail(c, HPSI_EINVAL, "hpsi_apply_noalloc: nbnd < 0");
+  if (nbnd == 0) return HPSI_OK;
+  if (!psi_in || !hpsi_out) return hpsi::fail(c, HPSI_EINVAL, "hpsi_apply_noalloc: null pointer");
+  const hpsi::Problem& p = c.probs[ik];
+  const size_t bytes = sizeof(double2) * (size_t)nbnd * p.npw;
+  const char* a0 = static_cast<const char*>(psi_in);
+  const char* b0 = static_cast<const char*>(hpsi_out);
+  if (a0 < b0 + bytes && b0 < a0 + bytes) return hpsi::fail(c, HPSI_EINVAL, "hpsi_apply_noalloc: psi_in and hpsi_out overlap");
+  if (!on_device(psi_in) || !on_device(hpsi_out))
+    return hpsi::fail(c, HPSI_EINVAL, "hpsi_apply_noalloc: psi_in and hpsi_out must be device memory");
+  void* base = nullptr;
+  int rc = scratch_address(c, &base);
+  if (rc) return rc;
+  // largest band chunk whose X, Y and nonlocal partials fit the array
+  const size_t per_band = hpsi::local_scratch_per_band(p, c.precision);
+  int chunk = 0;
+  for (int nb = std::min(nbnd, 4096); nb >= 1; nb = nb > 64 ? nb - 32 : nb - 1) {
+    int ns = 0, kc = 0;
+    size_t nl = 0;
+    hpsi::nonlocal_fp64_plan(c, p, nb, &ns, &kc, &nl);
+    const size_t cs = c.precision == HPSI_FP64 ? sizeof(double2) : sizeof(float2);
+    const size_t xb = align256(cs * (size_t)nb * p.n[2] * p.npl * p.n[1]);
+    const size_t yb = align256(cs * (size_t)nb * p.n[2] * p.nst);
+    if (xb + yb + align256(p.nproj ? nl : 0) <= kNoAllocBytes) {
+      chunk = nb;
+      break;
+    }
+  }
+  if (chunk == 0)
+    return hpsi::fail(c, HPSI_EINVAL,
+                      "hpsi_apply_noalloc: one band needs " + std::to_string(per_band) +
+                          " bytes of intermediates, more than the fixed 64 MiB array; use hpsi_apply");
+  const size_t cs = c.precision == HPSI_FP64 ? sizeof(double2) : sizeof(float2);
+  unsigned char* s = static_cast<unsigned char*>(base);
+  void* X = s;
+  void* Y = s + align256(cs * (size_t)chunk * p.n[2] * p.npl * p.n[1]);
+  void* NL = static_cast<unsigned char*>(Y) + align256(cs * (size_t)chunk * p.n[2] * p.nst);
+  const double2* psi = static_cast<const double2*>(psi_in);
+  double2* hpsi = static_cast<double2*>(hpsi_out);
+  c.band_apps += nbnd;
+  for (int b = 0; b < nbnd; b += chunk) {
+    const int nb = std::min(chunk, nbnd - b);
+    rc = hpsi::local_apply_into(c, p, psi + (size_t)b * p.npw, hpsi + (size_t)b * p.npw, nb, X, Y, nb);
+    if (rc) return rc;
+    rc = hpsi::nonlocal_fp64_into(c, p, psi + (size_t)b * p.npw, hpsi + (size_t)b * p.npw, nb, NL);
+    if (rc) return rc;
+  }
+  return HPSI_OK;
+}

@@ -171,4 +171,40 @@ int nonlocal_apply_fp64(Context& c, const Problem& p, const double2* psi, double
   return HPSI_OK;
 }
 
+// Split of calbec's K = npw range for nbnd bands, and the partial / w bytes it needs.
+void nonlocal_fp64_plan(const Context& c, const Problem& p, int nbnd, int* nsplit, int* kchunk, size_t* bytes) {
+  const int tilesp = (p.nproj + CB_TP - 1) / CB_TP, tilesb = (nbnd + CB_TB - 1) / CB_TB;
+  int ns = std::max(1, (3 * c.sm_count) / std::max(1, tilesp * tilesb));
+  int kc = (p.npw + ns - 1) / ns;
+  kc = std::max(CB_TK * 4, ((kc + CB_TK - 1) / CB_TK) * CB_TK);
+  ns = (p.npw + kc - 1) / kc;
+  *nsplit = ns;
+  *kchunk = kc;
+  *bytes = sizeof(double2) * ((size_t)ns * nbnd * p.nproj + (size_t)nbnd * p.nproj);
+}
+
+// The same three launches with caller-provided partial and w buffers (sized by nonlocal_fp64_plan).
+int nonlocal_fp64_into(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd, void* scratch) {
+  if (p.nproj == 0 || nbnd == 0) return HPSI_OK;
+  int nsplit = 0, kchunk = 0;
+  size_t bytes = 0;
+  nonlocal_fp64_plan(c, p, nbnd, &nsplit, &kchunk, &bytes);
+  const int tilesp = (p.nproj + CB_TP - 1) / CB_TP, tilesb = (nbnd + CB_TB - 1) / CB_TB;
+  double2* part = reinterpret_cast<double2*>(scratch);
+  double2* w = part + (size_t)nsplit * nbnd * p.nproj;
+  HPSI_LAUNCH(c, HPSI_K_CALBEC,
+              (k_calbec64<<<dim3(tilesp, tilesb, nsplit), 256, 0, c.stream>>>(p.npw, p.nproj, nbnd, kchunk,
+                                                                              p.d_beta, psi, part)));
+  const int n = p.nproj * nbnd;
+  HPSI_LAUNCH(c, HPSI_K_DSCALE,
+              (k_dscale64<<<(n + 255) / 256, 256, 0, c.stream>>>(p.nproj, nbnd, nsplit, part, p.d_rowptr, p.d_col,
+                                                                 p.d_dval, w)));
+  HPSI_LAUNCH(c, HPSI_K_ADDVUS,
+              (k_addvus64<<<dim3((p.npw + AV_TG - 1) / AV_TG, (nbnd + AV_TB - 1) / AV_TB), 256, 0, c.stream>>>(
+                  p.npw, p.nproj, nbnd, w, p.d_beta, hpsi)));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "nonlocal float64 kernels launch");
+  return HPSI_OK;
+}
+
 }  // namespace hpsi
