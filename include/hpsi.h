@@ -57,7 +57,9 @@ enum hpsi_status {
 enum hpsi_option {
   HPSI_OPT_PRECOND_TAU = 1,
   HPSI_OPT_PRECOND_SHIFT = 2,
-  HPSI_OPT_KERNEL_TIMING = 3  /* 1: bracket every launch of the library's kernels with CUDA events */
+  HPSI_OPT_KERNEL_TIMING = 3, /* 1: bracket every launch of the library's kernels with CUDA events */
+  HPSI_OPT_NL_TERMS = 4       /* mixed path: bf16 terms per nonlocal operand, 2 (three products,
+                                 default) or 3 (six products); re-splits the projectors */
 };
 
 /* Kernel classes reported by hpsi_kernel_stats. */
@@ -217,6 +219,14 @@ HPSI_API int hpsi_set_option(hpsi_ctx* ctx, int option, double value);
  * cuBLAS / cuSOLVER kernels of the Davidson subspace algebra are not counted.
  */
 HPSI_API int hpsi_kernel_stats(hpsi_ctx* ctx, int kernel, long long* launches, double* total_ms, int reset);
+
+/*
+ * hpsi_sync -- wait for all work queued on the context's stream, then report a device-side
+ * failure: HPSI_ETIMEOUT if a bounded wait inside a tensor-core kernel expired since the last
+ * check (the affected outputs are invalid; the error word is cleared).  Synchronous host-pointer
+ * calls and davidson_solve make the same check themselves.
+ */
+HPSI_API int hpsi_sync(hpsi_ctx* ctx);
 
 /* One-line message for the last failure on ctx (NULL ctx: this thread's last setup failure). */
 HPSI_API const char* hpsi_last_error(const hpsi_ctx* ctx);

@@ -17,13 +17,13 @@ LIB_PATH = os.path.join(HERE, "libhpsi.so")
 HPSI_OK, HPSI_EINVAL, HPSI_ENOMEM, HPSI_ECUDA = 0, -1, -2, -3
 HPSI_ENOTCONV, HPSI_ESINGULAR, HPSI_ETIMEOUT, HPSI_ENODEV = -4, -5, -6, -7
 HPSI_FP64, HPSI_MIXED = 0, 1
-HPSI_OPT_PRECOND_TAU, HPSI_OPT_PRECOND_SHIFT, HPSI_OPT_KERNEL_TIMING = 1, 2, 3
+HPSI_OPT_PRECOND_TAU, HPSI_OPT_PRECOND_SHIFT, HPSI_OPT_KERNEL_TIMING, HPSI_OPT_NL_TERMS = 1, 2, 3, 4
 KERNELS = ("inv_zy", "xvx_y", "fwd_z", "calbec", "dscale", "addvus", "split", "davidson")
 STATUS_NAMES = {0: "HPSI_OK", -1: "HPSI_EINVAL", -2: "HPSI_ENOMEM", -3: "HPSI_ECUDA", -4: "HPSI_ENOTCONV",
                 -5: "HPSI_ESINGULAR", -6: "HPSI_ETIMEOUT", -7: "HPSI_ENODEV"}
 
 EXPORTS = ("hpsi_gsphere", "hpsi_setup", "hpsi_setup_cells", "hpsi_nprob", "hpsi_npw", "hpsi_nproj", "hpsi_apply",
-           "hpsi_apply_batch", "hpsi_apply_noalloc", "davidson_solve", "hpsi_set_option", "hpsi_kernel_stats", "hpsi_last_error",
+           "hpsi_apply_batch", "hpsi_apply_noalloc", "davidson_solve", "hpsi_set_option", "hpsi_kernel_stats", "hpsi_sync", "hpsi_last_error",
            "hpsi_destroy")
 
 _lib = None
@@ -61,6 +61,8 @@ def _declare(lib):
     lib.hpsi_set_option.restype = I
     lib.hpsi_kernel_stats.argtypes = [V, I, P(ctypes.c_longlong), P(D), I]
     lib.hpsi_kernel_stats.restype = I
+    lib.hpsi_sync.argtypes = [V]
+    lib.hpsi_sync.restype = I
     lib.hpsi_last_error.argtypes = [V]
     lib.hpsi_last_error.restype = ctypes.c_char_p
     lib.hpsi_destroy.argtypes = [V]
@@ -227,6 +229,11 @@ def hpsi_apply_batch(ctx: Context, probs, psi_list, hpsi_list) -> None:
 def hpsi_set_option(ctx: Context, option: int, value: float) -> None:
     """hpsi_set_option(): Davidson preconditioner options."""
     _check(ctx.lib, ctx.handle, ctx.lib.hpsi_set_option(ctx.handle, int(option), float(value)), "hpsi_set_option")
+
+
+def hpsi_sync(ctx: Context) -> None:
+    """hpsi_sync(): wait for the context's stream; raises on a device-side timeout."""
+    _check(ctx.lib, ctx.handle, ctx.lib.hpsi_sync(ctx.handle), "hpsi_sync")
 
 
 def hpsi_kernel_stats(ctx: Context, kernel: int, reset: bool = False):

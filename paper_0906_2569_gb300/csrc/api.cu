@@ -62,6 +62,20 @@ static int collect_timing(Context& c) {
   return HPSI_OK;
 }
 
+int check_device_error(Context& c) {
+  cudaError_t e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
+  if (!c.d_err) return HPSI_OK;
+  int v = 0;
+  e = cudaMemcpy(&v, c.d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "error word read");
+  if (v != 0) {
+    cudaMemset(c.d_err, 0, sizeof(int));
+    return fail(c, HPSI_ETIMEOUT, "a bounded wait in a tensor-core kernel expired; its output is invalid");
+  }
+  return HPSI_OK;
+}
+
 int ensure_buffer(Context& c, void** ptr, size_t* have, size_t need) {
   if (need <= *have && *ptr) return HPSI_OK;
   if (*ptr) {
@@ -287,6 +301,7 @@ static void free_context(Context& c) {
     cudaFree(t.d32);
   }
   for (void* v : c.vbufs) cudaFree(v);
+  cudaFree(c.d_err);
   cudaFree(c.ws.X);
   cudaFree(c.ws.Y);
   cudaFree(c.ws.part);
@@ -371,8 +386,17 @@ static int setup_common(hpsi_ctx** out, int precision, void* stream, hpsi_ctx** 
   }
   h->c.precision = precision;
   int rc = init_device(h->c, stream);
+  if (rc == HPSI_OK) {
+    if (cudaMalloc((void**)&h->c.d_err, sizeof(int)) != cudaSuccess ||
+        cudaMemset(h->c.d_err, 0, sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      h->c.err = "device allocation of the error word failed";
+      rc = HPSI_ENOMEM;
+    }
+  }
   if (rc) {
     g_setup_err = h->c.err;
+    cudaFree(h->c.d_err);
     delete h;
     return rc;
   }
@@ -528,9 +552,7 @@ extern "C" int hpsi_apply(hpsi_ctx* ctx, int ik, const void* psi_in, void* hpsi_
   if (rc) return rc;
   e = cudaMemcpyAsync(hpsi_out, c.ws.stage_out, bytes, cudaMemcpyDeviceToHost, c.stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "hpsi_apply device->host copy");
-  e = cudaStreamSynchronize(c.stream);
-  if (e != cudaSuccess) return cuda_fail(c, e, "hpsi_apply");
-  return HPSI_OK;
+  return check_device_error(c);
 }
 
 extern "C" int hpsi_apply_batch(hpsi_ctx* ctx, int nitem, const int* prob, const int* nbnd,
@@ -594,6 +616,22 @@ extern "C" int hpsi_set_option(hpsi_ctx* ctx, int option, double value) {
     c.timing = value != 0.0;
     return HPSI_OK;
   }
+  if (option == HPSI_OPT_NL_TERMS) {
+    if (value != 2.0 && value != 3.0) return fail(c, HPSI_EINVAL, "HPSI_OPT_NL_TERMS must be 2 or 3");
+    if ((int)value == c.nl_terms) return HPSI_OK;
+    c.nl_terms = (int)value;
+    if (c.precision == HPSI_MIXED) {
+      cudaStreamSynchronize(c.stream);
+      for (auto& p : c.probs) {
+        if (p.nproj == 0) continue;
+        cudaFree(p.d_beta_bf);
+        p.d_beta_bf = nullptr;
+        int rc = mixed_prepare_beta(c, p);
+        if (rc) return rc;
+      }
+    }
+    return HPSI_OK;
+  }
   if (option == HPSI_OPT_PRECOND_SHIFT) {
     if (value != 0.0 && value != 1.0) return fail(c, HPSI_EINVAL, "HPSI_OPT_PRECOND_SHIFT must be 0 or 1");
     c.opt_shift = (int)value;
@@ -630,6 +668,11 @@ extern "C" int hpsi_kernel_stats(hpsi_ctx* ctx, int kernel, long long* launches,
         c.tacc[k] = 0.0;
       }
   return HPSI_OK;
+}
+
+extern "C" int hpsi_sync(hpsi_ctx* ctx) {
+  if (!ctx) return HPSI_EINVAL;
+  return check_device_error(ctx->c);
 }
 
 extern "C" const char* hpsi_last_error(const hpsi_ctx* ctx) {

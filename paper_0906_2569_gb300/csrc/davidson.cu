@@ -355,6 +355,8 @@ int davidson_run(Context& c, int ik, int nbnd, double tol, int maxiter, double2*
     DCK(cudaMemcpyAsync(rn.data(), w.rnorm, sizeof(double) * N, cudaMemcpyDeviceToHost, c.stream), "norm copy");
     DCK(cudaMemcpyAsync(ev.data(), w.eps, sizeof(double) * N, cudaMemcpyDeviceToHost, c.stream), "eig copy");
     DCK(cudaStreamSynchronize(c.stream), "davidson iteration");
+    rc = check_device_error(c);
+    if (rc) return rc;
     int nc = 0;
     double rmax = 0.0;
     for (int i = 0; i < N; ++i) {

@@ -100,6 +100,8 @@ struct Context {
   double opt_tau = 0.1;                // Davidson: |<k+G|H|k+G> - eps| is kept >= tau (Ha)
   int opt_shift = 0;                   // Davidson: 0 = eps_i per band, 1 = highest Ritz value
   void* blas = nullptr;                // Davidson handles and work buffers
+  int* d_err = nullptr;                // device error word raised by bounded waits
+  int nl_terms = 2;                    // mixed path: bf16 terms per operand (2 or 3)
   // launch accounting (always) and per-launch event timing (HPSI_OPT_KERNEL_TIMING)
   bool timing = false;
   long long launches[HPSI_K_COUNT] = {0};
@@ -144,6 +146,7 @@ int ensure_buffer(Context& c, void** ptr, size_t* have, size_t need);
 int fail(Context& c, int code, const std::string& msg);
 int cuda_fail(Context& c, cudaError_t e, const char* what);
 int apply_device(Context& c, int ik, const double2* psi, double2* hpsi, int nbnd);
+int check_device_error(Context& c);   // synchronizes; HPSI_ETIMEOUT if a bounded wait expired
 
 // ---- Davidson (davidson.cu) ----
 int davidson_run(Context& c, int ik, int nbnd, double tol, int maxiter, double2* psi, double* eig,

@@ -1,18 +1,485 @@
-// Nonlocal contractions of the mixed-precision path.
+// Nonlocal contractions of the mixed-precision path on the 5th-generation tensor cores.
+//
+// Separable projectors (paper Sec. 3): becp = <beta|psi>, w = D becp, hpsi += beta w.  Both
+// contractions are dense and run as real bf16 GEMMs with float32 accumulation in TMEM:
+//
+//   complex -> real:  with psi, beta, w stored as interleaved (re, im) real rows,
+//     calbec      C[p][n] = sum_k A[p][k] B[n][k],  A = beta (K = 2 npw),
+//                 B rows n < nb: psi_n (re, im); rows nb + b: (im, -re) of psi_b
+//                 -> C[p][b] = Re<beta_p|psi_b>, C[p][nb+b] = Im<beta_p|psi_b>
+//     add_vuspsi  C[b][n] = sum_k A[b][k] B[n][k],  A = w (K = 2P), B[2G+c][2p+c'] built from
+//                 beta so that C[b][2G] = Re(sum_p w_bp beta_p(G)), C[b][2G+1] = Im(...)
+//   precision:  every float64 operand x is split into bf16 terms x = x0 + x1 (+ x2) and the
+//     products x_i y_j with i + j < NT are accumulated (NT = 2: three products, ~16 significant
+//     bits; NT = 3: six products).
+//
+// Kernel: one CTA (4 warps) per 128 x 128 output tile (and per K-split for calbec).  Warp 0 lane 0
+// streams 128x64 bf16 tiles with TMA (128-byte swizzle) through a multi-stage mbarrier ring;
+// warp 1 lane 0 issues tcgen05.mma (M = 128, N = 128, K = 16) into one TMEM accumulator of 128
+// columns; all four warps read the accumulator back with tcgen05.ld (one TMEM lane per thread) and
+// write the epilogue.  Every wait is bounded by a clock limit: on expiry the CTA raises the
+// context's error word, drains what it issued, frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
+
+#include <algorithm>
+#include <mutex>
 
 #include "hpsi_internal.h"
 
 namespace hpsi {
 
-int mixed_prepare_beta(Context& c, Problem& p) {
-  (void)c;
-  (void)p;
+namespace {
+
+constexpr int TBM = 128;             // rows of A per tile (TMEM lanes)
+constexpr int TBN = 128;             // rows of B per tile (accumulator columns)
+constexpr int TBK = 64;              // bf16 per 128-byte swizzled row
+constexpr int kTileBytes = TBM * TBK * 2;   // 16 KB, A and B tiles alike
+constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
+
+template <int NT> struct TcCfg {
+  static constexpr int stages = NT == 2 ? 3 : 2;
+  static constexpr int stage_bytes = 2 * NT * kTileBytes;
+  static constexpr int smem = stages * stage_bytes + 1024;
+};
+
+struct TcArgs {
+  int M, N;          // logical rows of A and of B (output is M x N)
+  int nksteps;       // K / 64
+  int ksplit;        // K-steps per split (gridDim.z splits)
+  int mode;          // 0: store float partials [split][M][N]; 1: add into complex128 rows
+  float* part;
+  double2* out;      // mode 1: out[m][n/2] += (C[m][n], C[m][n+1]) for even n
+  int ldo;           // mode 1: complex elements per output row
+  int* err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: false if the clock limit expired or another thread of the CTA aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  const long long t0 = clock64();
+  for (unsigned it = 0;; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 255u) == 255u) {
+      if (*abort_flag) return false;
+      if (clock64() - t0 > kWaitCycles) {
+        *abort_flag = 1;
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// K-major operand, 128-byte swizzle: 8-row groups of 128-byte rows, 1024 bytes apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;              // leading byte offset (not used by swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;    // stride byte offset
+  d |= (uint64_t)1 << 46;              // descriptor version
+  d |= (uint64_t)2 << 61;              // 128-byte swizzle
+  return d;
+}
+
+// kind::f16 instruction descriptor: D f32, A and B bf16, both K-major, M = 128, N = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TBN >> 3) << 17) |
+                            ((uint32_t)(TBM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+               : "memory");
+}
+
+template <int NT>
+__global__ void __launch_bounds__(128, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
+              const __grid_constant__ CUtensorMap tA2, const __grid_constant__ CUtensorMap tB0,
+              const __grid_constant__ CUtensorMap tB1, const __grid_constant__ CUtensorMap tB2, TcArgs a) {
+  using Cfg = TcCfg<NT>;
+  constexpr int S = Cfg::stages;
+  extern __shared__ __align__(1024) unsigned char smem_dyn[];
+  __shared__ __align__(8) uint64_t full_bar[S];
+  __shared__ __align__(8) uint64_t empty_bar[S];
+  __shared__ __align__(8) uint64_t acc_bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int abort_flag;
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tile_n = blockIdx.x * TBN, tile_m = blockIdx.y * TBM, split = blockIdx.z;
+  const int kbeg = split * a.ksplit, kend = min(a.nksteps, kbeg + a.ksplit);
+  const int nk = kend - kbeg;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&full_bar[s])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&empty_bar[s])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&acc_bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    abort_flag = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_base)),
+                 "r"(TBN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  const CUtensorMap* mA[3] = {&tA0, &tA1, &tA2};
+  const CUtensorMap* mB[3] = {&tB0, &tB1, &tB2};
+
+  int issued[S];
+#pragma unroll
+  for (int s = 0; s < S; ++s) issued[s] = 0;
+  if (warp == 0 && lane == 0 && nk > 0) {
+    // producer
+    for (int i = 0; i < nk; ++i) {
+      const int s = i % S, round = i / S;
+      if (round > 0 && !mbar_wait(smem_u32(&empty_bar[s]), (round - 1) & 1, &abort_flag)) break;
+      const uint32_t fb = smem_u32(&full_bar[s]);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(Cfg::stage_bytes)
+                   : "memory");
+      unsigned char* st = smem + s * Cfg::stage_bytes;
+      const int kx = (kbeg + i) * TBK;
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        tma_load_2d(smem_u32(st + t * kTileBytes), mA[t], kx, tile_m, fb);
+        tma_load_2d(smem_u32(st + (NT + t) * kTileBytes), mB[t], kx, tile_n, fb);
+      }
+      issued[s] = round + 1;
+    }
+  } else if (warp == 1 && lane == 0 && nk > 0) {
+    // MMA issuer
+    uint32_t acc = 0;
+    for (int i = 0; i < nk; ++i) {
+      const int s = i % S, round = i / S;
+      if (!mbar_wait(smem_u32(&full_bar[s]), round & 1, &abort_flag)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const unsigned char* st = smem + s * Cfg::stage_bytes;
+#pragma unroll
+      for (int kk = 0; kk < TBK / 16; ++kk) {
+#pragma unroll
+        for (int ia = 0; ia < NT; ++ia)
+#pragma unroll
+          for (int ib = 0; ib < NT; ++ib) {
+            if (ia + ib >= NT) continue;
+            const uint64_t da = sw128_desc(smem_u32(st + ia * kTileBytes) + kk * 32);
+            const uint64_t db = sw128_desc(smem_u32(st + (NT + ib) * kTileBytes) + kk * 32);
+            mma_bf16(tmem, da, db, acc);
+            acc = 1;
+          }
+      }
+      mma_commit(smem_u32(&empty_bar[s]));
+    }
+    mma_commit(smem_u32(&acc_bar));
+  }
+  __syncwarp();
+  // epilogue: wait for the accumulator, TMEM lane = output row
+  bool ok = nk > 0 && mbar_wait(smem_u32(&acc_bar), 0, &abort_flag);
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  if (ok && !abort_flag) {
+    const int row = tile_m + warp * 32 + lane;
+    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+    for (int c0 = 0; c0 < TBN; c0 += 16) {
+      uint32_t r[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(lane_addr + (uint32_t)c0));
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+      if (row < a.M) {
+        const int n0 = tile_n + c0;
+        if (a.mode == 0) {
+          float* o = a.part + ((size_t)split * a.M + row) * a.N;
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (n0 + j < a.N) o[n0 + j] = __uint_as_float(r[j]);
+        } else {
+          double2* o = a.out + (size_t)row * a.ldo + (n0 >> 1);
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            if (n0 + 2 * j < a.N) {
+              double2 v = o[j];
+              v.x += (double)__uint_as_float(r[2 * j]);
+              v.y += (double)__uint_as_float(r[2 * j + 1]);
+              o[j] = v;
+            }
+        }
+      }
+    }
+  }
+  if (abort_flag && threadIdx.x == 0) atomicExch(a.err, 1);
+  // drain: every TMA this CTA issued has landed before the CTA (and its shared memory) goes away
+  if (warp == 0 && lane == 0) {
+    volatile int never = 0;
+    for (int s = 0; s < S; ++s)
+      if (issued[s] > 0) mbar_wait(smem_u32(&full_bar[s]), (issued[s] - 1) & 1, &never);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TBN));
+}
+
+// ---- operand preparation ----------------------------------------------------------------------
+
+template <int NT>
+__device__ __forceinline__ void split_store(double x, __nv_bfloat16* p0, size_t plane, size_t idx) {
+  double r = x;
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    const __nv_bfloat16 h = __float2bfloat16_rn((float)r);
+    p0[t * plane + idx] = h;
+    r -= (double)__bfloat162float(h);
+  }
+}
+
+// A of calbec: row p = beta_p as (re, im) pairs, K padded with zeros to kc.
+template <int NT>
+__global__ void k_split_beta_cal(int nproj, int npw, int kc, const double2* __restrict__ beta,
+                                 __nv_bfloat16* __restrict__ out) {
+  const size_t plane = (size_t)nproj * kc;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < plane; i += (size_t)gridDim.x * blockDim.x) {
+    const int p = (int)(i / kc), k = (int)(i % kc);
+    double x = 0.0;
+    if (k < 2 * npw) {
+      const double2 v = beta[(size_t)p * npw + (k >> 1)];
+      x = (k & 1) ? v.y : v.x;
+    }
+    split_store<NT>(x, out, plane, i);
+  }
+}
+
+// B of add_vuspsi: row n = 2G + c, column k = 2p + c':  c=0: (re, -im), c=1: (im, re) of beta_p(G).
+template <int NT>
+__global__ void k_split_beta_add(int nproj, int npw, int ka, const double2* __restrict__ beta,
+                                 __nv_bfloat16* __restrict__ out) {
+  const size_t plane = (size_t)2 * npw * ka;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < plane; i += (size_t)gridDim.x * blockDim.x) {
+    const int n = (int)(i / ka), k = (int)(i % ka);
+    double x = 0.0;
+    if (k < 2 * nproj) {
+      const double2 v = beta[(size_t)(k >> 1) * npw + (n >> 1)];
+      const int c = n & 1, cp = k & 1;
+      x = c == 0 ? (cp == 0 ? v.x : -v.y) : (cp == 0 ? v.y : v.x);
+    }
+    split_store<NT>(x, out, plane, i);
+  }
+}
+
+// B of calbec: rows b < nb: psi_b (re, im); rows nb + b: (im, -re).
+template <int NT>
+__global__ void k_split_psi(int nb, int npw, int kc, const double2* __restrict__ psi, __nv_bfloat16* __restrict__ out) {
+  const size_t plane = (size_t)2 * nb * kc;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < plane; i += (size_t)gridDim.x * blockDim.x) {
+    const int n = (int)(i / kc), k = (int)(i % kc);
+    double x = 0.0;
+    if (k < 2 * npw) {
+      const int b = n < nb ? n : n - nb;
+      const double2 v = psi[(size_t)b * npw + (k >> 1)];
+      x = n < nb ? ((k & 1) ? v.y : v.x) : ((k & 1) ? -v.x : v.y);
+    }
+    split_store<NT>(x, out, plane, i);
+  }
+}
+
+// w[b][p] = sum_q D_pq becp[b][q], becp from the float partials (summed in float64); written as
+// the bf16 terms of A of add_vuspsi, row b = (re, im) pairs of w_b.
+template <int NT>
+__global__ void k_dscale_tc(int nproj, int nb, int nsplit, int ka, const float* __restrict__ part,
+                            const int* __restrict__ rowptr, const int* __restrict__ col,
+                            const double2* __restrict__ val, __nv_bfloat16* __restrict__ wa) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nproj * nb) return;
+  const int b = i / nproj, p = i % nproj;
+  const int N = 2 * nb;
+  double wr = 0.0, wi = 0.0;
+  for (int e = rowptr[p]; e < rowptr[p + 1]; ++e) {
+    const int q = col[e];
+    double sr = 0.0, si = 0.0;
+    for (int s = 0; s < nsplit; ++s) {
+      const float* ps = part + ((size_t)s * nproj + q) * N;
+      sr += (double)ps[b];
+      si += (double)ps[nb + b];
+    }
+    const double2 d = val[e];
+    wr += d.x * sr - d.y * si;
+    wi += d.x * si + d.y * sr;
+  }
+  const size_t plane = (size_t)nb * ka;
+  split_store<NT>(wr, wa, plane, (size_t)b * ka + 2 * p);
+  split_store<NT>(wi, wa, plane, (size_t)b * ka + 2 * p + 1);
+}
+
+// ---- host side ------------------------------------------------------------------------------
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+int get_encoder(Context& c) {
+  std::call_once(g_encode_once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  });
+  if (!g_encode) return fail(c, HPSI_ECUDA, "cuTensorMapEncodeTiled is not available");
   return HPSI_OK;
 }
 
+// Map over a K-major bf16 matrix [rows][kpad], tiles of 128 rows x 64 columns, 128-byte swizzle.
+int make_map(Context& c, CUtensorMap* m, const void* base, int rows, int kpad) {
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || (kpad % TBK)) return fail(c, HPSI_EINVAL, "tensor map alignment");
+  cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)kpad * 2};
+  cuuint32_t box[2] = {(cuuint32_t)TBK, (cuuint32_t)TBM};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(c, HPSI_ECUDA, "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
+  return HPSI_OK;
+}
+
+inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+template <int NT>
+int launch_gemm(Context& c, const void* A, int M, const void* B, int N, int kpad, int nsplit, int ksplit, int mode,
+                float* part, double2* out, int ldo, int kernel_class) {
+  CUtensorMap ma[3], mb[3];
+  const size_t pa = (size_t)M * kpad, pb = (size_t)N * kpad;
+  for (int t = 0; t < 3; ++t) {
+    const int tt = t < NT ? t : NT - 1;
+    int rc = make_map(c, &ma[t], static_cast<const __nv_bfloat16*>(A) + tt * pa, M, kpad);
+    if (rc) return rc;
+    rc = make_map(c, &mb[t], static_cast<const __nv_bfloat16*>(B) + tt * pb, N, kpad);
+    if (rc) return rc;
+  }
+  TcArgs a;
+  a.M = M;
+  a.N = N;
+  a.nksteps = kpad / TBK;
+  a.ksplit = ksplit;
+  a.mode = mode;
+  a.part = part;
+  a.out = out;
+  a.ldo = ldo;
+  a.err = c.d_err;
+  static bool attr[4] = {false, false, false, false};
+  if (!attr[NT]) {
+    cudaFuncSetAttribute(k_tc_gemm<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<NT>::smem);
+    attr[NT] = true;
+  }
+  dim3 grid((N + TBN - 1) / TBN, (M + TBM - 1) / TBM, nsplit);
+  HPSI_LAUNCH(c, kernel_class,
+              (k_tc_gemm<NT><<<grid, 128, TcCfg<NT>::smem, c.stream>>>(ma[0], ma[1], ma[2], mb[0], mb[1], mb[2], a)));
+  return HPSI_OK;
+}
+
+template <int NT>
+int prepare_t(Context& c, Problem& p) {
+  const int P = p.nproj, npw = p.npw;
+  const int kc = round_up(2 * npw, TBK), ka = round_up(2 * P, TBK);
+  const size_t cal = (size_t)NT * P * kc, add = (size_t)NT * 2 * npw * ka;
+  cudaError_t e = cudaMalloc((void**)&p.d_beta_bf, sizeof(__nv_bfloat16) * (cal + add));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, HPSI_ENOMEM, "device allocation of the bf16 projector terms failed");
+  }
+  __nv_bfloat16* base = reinterpret_cast<__nv_bfloat16*>(p.d_beta_bf);
+  HPSI_LAUNCH(c, HPSI_K_SPLIT, (k_split_beta_cal<NT><<<4 * c.sm_count, 256, 0, c.stream>>>(P, npw, kc, p.d_beta, base)));
+  HPSI_LAUNCH(c, HPSI_K_SPLIT,
+              (k_split_beta_add<NT><<<4 * c.sm_count, 256, 0, c.stream>>>(P, npw, ka, p.d_beta, base + cal)));
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "bf16 projector split");
+  return HPSI_OK;
+}
+
+template <int NT>
+int apply_t(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd) {
+  const int P = p.nproj, npw = p.npw;
+  const int kc = round_up(2 * npw, TBK), ka = round_up(2 * P, TBK);
+  const size_t cal = (size_t)NT * P * kc;
+  const __nv_bfloat16* bcal = reinterpret_cast<const __nv_bfloat16*>(p.d_beta_bf);
+  const __nv_bfloat16* badd = bcal + cal;
+  // split-K of calbec: about two CTAs per SM over all output tiles
+  const int nks = kc / TBK;
+  const int tiles = ((2 * nbnd + TBN - 1) / TBN) * ((P + TBM - 1) / TBM);
+  int nsplit = std::max(1, std::min(nks, (2 * c.sm_count + tiles - 1) / tiles));
+  const int ksplit = (nks + nsplit - 1) / nsplit;
+  nsplit = (nks + ksplit - 1) / ksplit;
+  const size_t psib = sizeof(__nv_bfloat16) * (size_t)NT * 2 * nbnd * kc;
+  const size_t partb = sizeof(float) * (size_t)nsplit * P * 2 * nbnd;
+  const size_t wab = sizeof(__nv_bfloat16) * (size_t)NT * nbnd * ka;
+  const size_t need = psib + partb + wab + 3 * 256;
+  int rc = ensure_buffer(c, &c.ws.mixed, &c.ws.mixedbytes, need);
+  if (rc) return rc;
+  unsigned char* w0 = static_cast<unsigned char*>(c.ws.mixed);
+  __nv_bfloat16* psi_bf = reinterpret_cast<__nv_bfloat16*>(w0);
+  float* part = reinterpret_cast<float*>(w0 + ((psib + 255) & ~size_t(255)));
+  __nv_bfloat16* wa =
+      reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<unsigned char*>(part) + ((partb + 255) & ~size_t(255)));
+  // the K padding of w (columns 2P .. ka) is not written by the D-scale kernel
+  cudaError_t e0 = cudaMemsetAsync(wa, 0, wab, c.stream);
+  if (e0 != cudaSuccess) return cuda_fail(c, e0, "workspace clear");
+  HPSI_LAUNCH(c, HPSI_K_SPLIT, (k_split_psi<NT><<<4 * c.sm_count, 256, 0, c.stream>>>(nbnd, npw, kc, psi, psi_bf)));
+  rc = launch_gemm<NT>(c, bcal, P, psi_bf, 2 * nbnd, kc, nsplit, ksplit, 0, part, nullptr, 0, HPSI_K_CALBEC);
+  if (rc) return rc;
+  const int n = P * nbnd;
+  HPSI_LAUNCH(c, HPSI_K_DSCALE,
+              (k_dscale_tc<NT><<<(n + 255) / 256, 256, 0, c.stream>>>(P, nbnd, nsplit, ka, part, p.d_rowptr, p.d_col,
+                                                                      p.d_dval, wa)));
+  rc = launch_gemm<NT>(c, wa, nbnd, badd, 2 * npw, ka, 1, ka / TBK, 1, nullptr, hpsi, npw, HPSI_K_ADDVUS);
+  if (rc) return rc;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "tensor-core nonlocal kernels launch");
+  return HPSI_OK;
+}
+
+}  // namespace
+
+int mixed_prepare_beta(Context& c, Problem& p) {
+  int rc = get_encoder(c);
+  if (rc) return rc;
+  return c.nl_terms == 3 ? prepare_t<3>(c, p) : prepare_t<2>(c, p);
+}
+
 int nonlocal_apply_mixed(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd) {
-  return nonlocal_apply_fp64(c, p, psi, hpsi, nbnd);
+  if (p.nproj == 0 || nbnd == 0) return HPSI_OK;
+  return c.nl_terms == 3 ? apply_t<3>(c, p, psi, hpsi, nbnd) : apply_t<2>(c, p, psi, hpsi, nbnd);
 }
 
 }  // namespace hpsi

@@ -164,3 +164,31 @@ def test_hpsi_mixed_c1(lib):
     got = run_apply(ctx, 0, psi)
     ref = oracle.hamiltonian.hpsi(p.lattice, p.kpts[0], m, p.fft, vr, beta, d, psi)
     assert rel(got, ref) < TOLMIX
+
+
+def test_hpsi_mixed_c2_sampled(lib):
+    """Mixed path on the 36785-PW / 256-projector cell: 160 bands, 4 checked by the oracle."""
+    from paper_0906_2569_gb300 import binding as B
+    p = workloads.config2()
+    ctx, (m,), vr, (beta,), d = make_problem(p, precision=B.HPSI_MIXED)
+    psi = workloads.psi0(p.lattice, p.kpts[0], m, p.nbnd, p.psi_seed)
+    got = run_apply(ctx, 0, psi)
+    B.hpsi_sync(ctx)
+    sel = [0, 63, 128, 159]
+    ref = oracle.hamiltonian.hpsi(p.lattice, p.kpts[0], m, p.fft, vr, beta, d, psi[sel])
+    assert rel(got[sel], ref) < TOLMIX
+
+
+@pytest.mark.parametrize("nbnd", [3, 130])
+def test_hpsi_mixed_three_terms(lib, nbnd):
+    """Six-product split (three bf16 terms per operand) is at least as accurate as three products."""
+    from paper_0906_2569_gb300 import binding as B
+    p = workloads.config1()
+    ctx, (m,), vr, (beta,), d = make_problem(p, precision=B.HPSI_MIXED)
+    psi = workloads.random_block(len(m), nbnd, 7)
+    ref = oracle.hamiltonian.hpsi(p.lattice, p.kpts[0], m, p.fft, vr, beta, d, psi)
+    e2 = rel(run_apply(ctx, 0, psi), ref)
+    B.hpsi_set_option(ctx, B.HPSI_OPT_NL_TERMS, 3)
+    e3 = rel(run_apply(ctx, 0, psi), ref)
+    B.hpsi_sync(ctx)
+    assert e2 < TOLMIX and e3 < TOLMIX and e3 <= e2 * 1.5
