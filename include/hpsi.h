@@ -58,8 +58,10 @@ enum hpsi_option {
   HPSI_OPT_PRECOND_TAU = 1,
   HPSI_OPT_PRECOND_SHIFT = 2,
   HPSI_OPT_KERNEL_TIMING = 3, /* 1: bracket every launch of the library's kernels with CUDA events */
-  HPSI_OPT_NL_TERMS = 4       /* mixed path: bf16 terms per nonlocal operand, 2 (three products,
+  HPSI_OPT_NL_TERMS = 4,      /* mixed path: bf16 terms per nonlocal operand, 2 (three products,
                                  default) or 3 (six products); re-splits the projectors */
+  HPSI_OPT_LOCAL_PATH = 5     /* 0 (default): register-codelet kernels where the box allows them;
+                                 1: always the generic radix-2/3/4/5 kernels */
 };
 
 /* Kernel classes reported by hpsi_kernel_stats. */

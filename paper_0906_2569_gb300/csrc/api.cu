@@ -194,6 +194,17 @@ static int plan_for(Context& c, int n, FftPlan* out) {
   if (rc) return rc;
   rc = upload(c, &tt.d32, tab32.data(), tab32.size());
   if (rc) return rc;
+  std::vector<double2> nat(n);
+  std::vector<float2> nat32(n);
+  for (int j = 0; j < n; ++j) {
+    const double ang = -6.283185307179586476925286766559 * (double)j / (double)n;
+    nat[j] = make_double2(std::cos(ang), std::sin(ang));
+    nat32[j] = make_float2((float)nat[j].x, (float)nat[j].y);
+  }
+  rc = upload(c, &tt.nat64, nat.data(), nat.size());
+  if (rc) return rc;
+  rc = upload(c, &tt.nat32, nat32.data(), nat32.size());
+  if (rc) return rc;
   tt.plan.tw64 = tt.d64;
   tt.plan.tw32 = tt.d32;
   c.tw.push_back(tt);
@@ -215,6 +226,23 @@ static int finish_problem(Context& c, Problem& p, const double* vr, int vslot_sh
     if (rc) return rc;
   }
   if ((rc = upload(c, &p.d_sticks, p.sticks.data(), p.sticks.size()))) return rc;
+  {
+    // lookup maps of the fast path: stick of (plane, j2) and plane of ix
+    std::vector<int> ymap((size_t)p.npl * p.n[1], -1), xmap(p.n[0], -1);
+    for (int q = 0; q < p.npl; ++q) {
+      xmap[p.planes[q].ix] = q;
+      for (int s = p.planes[q].s0; s < p.planes[q].s0 + p.planes[q].ns; ++s)
+        ymap[(size_t)q * p.n[1] + p.sticks[s].iy] = s;
+    }
+    if ((rc = upload(c, &p.d_ymap, ymap.data(), ymap.size()))) return rc;
+    if ((rc = upload(c, &p.d_xmap, xmap.data(), xmap.size()))) return rc;
+    for (auto& t : c.tw)
+      if (t.n == p.n[0]) {
+        p.d_ftw64 = t.nat64;
+        p.d_ftw32 = t.nat32;
+      }
+    p.fast_flags = local_fast_plan(p, c.precision, c.smem_optin);
+  }
   if ((rc = upload(c, &p.d_planes, p.planes.data(), p.planes.size()))) return rc;
   if ((rc = upload(c, &p.d_kin, p.kin.data(), p.kin.size()))) return rc;
   (void)vr;
@@ -269,6 +297,9 @@ static int finish_problem(Context& c, Problem& p, const double* vr, int vslot_sh
   const size_t cs = c.precision == HPSI_FP64 ? 16 : 8;
   const size_t xper = cs * (size_t)p.n[2] * p.npl * p.n[1];
   p.nbb = (int)std::max<size_t>(1, std::min<size_t>(4096, (size_t)(48u << 20) / std::max<size_t>(1, xper)));
+  // fast path: the stick rows Zt and Y of one block (about 48 MB) stay L2-resident
+  const size_t zper = 2 * cs * (size_t)p.n[2] * p.nst;
+  p.nbb_fast = (int)std::max<size_t>(1, std::min<size_t>(4096, (size_t)(48u << 20) / std::max<size_t>(1, zper)));
   if (c.precision == HPSI_MIXED && P > 0) {
     rc = mixed_prepare_beta(c, p);
     if (rc) return rc;
@@ -281,6 +312,8 @@ static int finish_problem(Context& c, Problem& p, const double* vr, int vslot_sh
 static void free_problem(Problem& p) {
   cudaFree(p.d_sticks);
   cudaFree(p.d_planes);
+  cudaFree(p.d_ymap);
+  cudaFree(p.d_xmap);
   cudaFree(p.d_kin);
   cudaFree(p.d_hdiag);
   cudaFree(p.d_beta);
@@ -299,6 +332,8 @@ static void free_context(Context& c) {
   for (auto& t : c.tw) {
     cudaFree(t.d64);
     cudaFree(t.d32);
+    cudaFree(t.nat64);
+    cudaFree(t.nat32);
   }
   for (void* v : c.vbufs) cudaFree(v);
   cudaFree(c.d_err);
@@ -630,6 +665,11 @@ extern "C" int hpsi_set_option(hpsi_ctx* ctx, int option, double value) {
         if (rc) return rc;
       }
     }
+    return HPSI_OK;
+  }
+  if (option == HPSI_OPT_LOCAL_PATH) {
+    if (value != 0.0 && value != 1.0) return fail(c, HPSI_EINVAL, "HPSI_OPT_LOCAL_PATH must be 0 or 1");
+    c.force_generic = (int)value;
     return HPSI_OK;
   }
   if (option == HPSI_OPT_PRECOND_SHIFT) {

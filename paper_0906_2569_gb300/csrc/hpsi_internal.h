@@ -67,6 +67,13 @@ struct Problem {
   uint16_t* d_beta_bf = nullptr;   // mixed path only
   FftPlan plan[3];
   int nbb = 1;                     // band block of the local-potential kernels
+  // fast path (cubic boxes with register codelets, local_fast.cu)
+  int fast_flags = 0;              // bit 2: enabled; bit 0: stage V; bit 1: stage the stick row
+  int nbb_fast = 1;
+  int* d_ymap = nullptr;           // [npl][n2]: stick of (plane, j2) or -1
+  int* d_xmap = nullptr;           // [n1]: plane of ix or -1
+  const double2* d_ftw64 = nullptr;   // e^{-2 pi i j / n}, j < n (owned by the twiddle table)
+  const float2* d_ftw32 = nullptr;
 };
 
 struct TwiddleTable {
@@ -74,6 +81,8 @@ struct TwiddleTable {
   FftPlan plan;   // with device pointers filled
   double2* d64 = nullptr;
   float2* d32 = nullptr;
+  double2* nat64 = nullptr;   // e^{-2 pi i j / n}, j < n
+  float2* nat32 = nullptr;
 };
 
 struct Workspace {
@@ -102,6 +111,7 @@ struct Context {
   void* blas = nullptr;                // Davidson handles and work buffers
   int* d_err = nullptr;                // device error word raised by bounded waits
   int nl_terms = 2;                    // mixed path: bf16 terms per operand (2 or 3)
+  int force_generic = 0;               // 1: local part on the generic FFT kernels
   // launch accounting (always) and per-launch event timing (HPSI_OPT_KERNEL_TIMING)
   bool timing = false;
   long long launches[HPSI_K_COUNT] = {0};
@@ -136,6 +146,9 @@ int nonlocal_apply_fp64(Context& c, const Problem& p, const double2* psi, double
 int nonlocal_apply_mixed(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd);
 int mixed_prepare_beta(Context& c, Problem& p);
 size_t local_scratch_per_band(const Problem& p, int precision);
+int local_fast_plan(const Problem& p, int precision, size_t smem_optin);
+int local_fast_apply(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd, void* Zt, void* Yb,
+                     int nbb);
 int local_apply_into(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd, void* X, void* Y,
                      int nbb);
 void nonlocal_fp64_plan(const Context& c, const Problem& p, int nbnd, int* nsplit, int* kchunk, size_t* bytes);

@@ -170,6 +170,15 @@ size_t local_smem_bytes(const Problem& p, int precision, int which) {
 template <typename T>
 static int local_apply_t(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd) {
   const size_t cs = sizeof(typename Cx<T>::type);
+  if ((p.fast_flags & 4) && !c.force_generic) {
+    const int nbf = std::max(1, std::min(p.nbb_fast, nbnd));
+    const size_t zneed = cs * (size_t)nbf * p.n[2] * p.nst;
+    int rc = ensure_buffer(c, &c.ws.X, &c.ws.xbytes, zneed);
+    if (rc) return rc;
+    rc = ensure_buffer(c, &c.ws.Y, &c.ws.ybytes, zneed);
+    if (rc) return rc;
+    return local_fast_apply(c, p, psi, hpsi, nbnd, c.ws.X, c.ws.Y, nbf);
+  }
   const int nbb = std::max(1, std::min(p.nbb, nbnd));
   const size_t xneed = cs * (size_t)nbb * p.n[2] * p.npl * p.n[1];
   const size_t yneed = cs * (size_t)nbb * p.n[2] * p.nst;

@@ -1,0 +1,45 @@
+"""A small, self-contained H|psi> case for profiler captures.
+
+Runs ``--reps`` applications of H to the 160-band block of the 90^3 / 36785-PW / 256-projector
+cell (or the cell named by ``--config``) at the chosen precision, after one warm-up application,
+so that a profiler can skip the warm-up launches and capture a steady-state one.
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--config", default="c2")
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--reps", type=int, default=1)
+    ap.add_argument("--nbnd", type=int, default=0)
+    args = ap.parse_args()
+    import torch
+    import workloads
+    from paper_0906_2569_gb300 import binding as B
+    p = workloads.CONFIGS[args.config]()
+    nb = args.nbnd or p.nbnd
+    k = p.kpts[0]
+    m = B.hpsi_gsphere(p.lattice, p.ecut, k)
+    vr = workloads.vloc_r(p.lattice, p.atoms, p.fft)
+    beta = workloads.beta(p.lattice, p.atoms, k, m)
+    prec = B.HPSI_MIXED if args.precision == "mixed" else B.HPSI_FP64
+    ctx = B.hpsi_setup(p.lattice, p.ecut, [k], p.fft, vr, [beta], workloads.dmat(len(p.atoms)), prec,
+                       torch.cuda.current_stream().cuda_stream)
+    x = torch.from_numpy(workloads.psi0(p.lattice, k, m, nb, p.psi_seed)).cuda()
+    y = torch.empty_like(x)
+    for _ in range(1 + args.reps):
+        B.hpsi_apply(ctx, 0, x, y)
+    B.hpsi_sync(ctx)
+    print("ok", args.config, args.precision, nb, float(y.abs().sum()))
+
+
+if __name__ == "__main__":
+    main()
