@@ -320,7 +320,7 @@ def run_gpu(args):
         "metric": "H|psi> band-applications/s (mixed precision; float64 beside it)",
         "value": value, "unit": "band-applications/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": mix_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "mixed: c64 FFT + xV, bf16x3 tensor-core nonlocal (f32 accumulate), f64 Davidson", "data": "synthetic",
+        "dtype": "mixed: c64 FFT + xV; bf16 3-term split (6-product) tensor-core nonlocal, f32 accumulate; c64 Davidson subspace, f64 eigensolves/norms/Rayleigh quotients", "data": "synthetic",
         "config": {"workload": desc, "npw": npw, "band_apps_per_step": mixed["band_apps"] // args.steps,
                    "step": "davidson_solve maxiter=1 from the seeded block: H on N bands + Rayleigh-Ritz + residuals + "
                            "preconditioner + H on N corrections + Rayleigh-Ritz (2N)",

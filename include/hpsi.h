@@ -58,8 +58,8 @@ enum hpsi_option {
   HPSI_OPT_PRECOND_TAU = 1,
   HPSI_OPT_PRECOND_SHIFT = 2,
   HPSI_OPT_KERNEL_TIMING = 3, /* 1: bracket every launch of the library's kernels with CUDA events */
-  HPSI_OPT_NL_TERMS = 4,      /* mixed path: bf16 terms per nonlocal operand, 2 (three products,
-                                 default) or 3 (six products); re-splits the projectors */
+  HPSI_OPT_NL_TERMS = 4,      /* mixed path: bf16 terms per nonlocal operand, 3 (six products,
+                                 default) or 2 (three products); re-splits the projectors */
   HPSI_OPT_LOCAL_PATH = 5     /* 0 (default): register-codelet kernels where the box allows them;
                                  1: always the generic radix-2/3/4/5 kernels */
 };
@@ -79,9 +79,11 @@ enum hpsi_kernel {
 
 enum hpsi_precision {
   HPSI_FP64 = 0,  /* every step in float64 / complex128 */
-  HPSI_MIXED = 1  /* FFTs and x V(r) in float32, nonlocal contractions as three-product
-                     split-bf16 tensor-core GEMMs with float32 accumulation; kinetic term,
-                     residuals, norms, Rayleigh-Ritz and Cholesky in float64 */
+  HPSI_MIXED = 1  /* FFTs and x V(r) in float32, nonlocal contractions as split-bf16
+                     tensor-core GEMMs with float32 accumulation (three bf16 terms per operand,
+                     six products, by default); kinetic term in float64.  davidson_solve keeps
+                     its reduced basis in complex64 and does the small eigensolves, the residual
+                     norms and the final Rayleigh quotients in float64 */
 };
 
 /*

@@ -16,6 +16,11 @@
 // orthogonal to the basis.  S_jk is then the identity and the reduced problem is solved as a
 // standard Hermitian one (cuSOLVER zheevd).
 //
+// Mixed precision (HPSI_MIXED): the reduced basis and its products are complex64 (cuBLAS CGEMM);
+// the small eigenproblems, the residual norms and the final eigenvalues are float64 -- at exit H
+// is applied once more to the Ritz vectors and eps_i = <psi_i|H psi_i> / <psi_i|psi_i> is summed
+// in float64, whose error is second order in the eigenvector error.
+//
 // The eps in D is eps_i per band by default (D approximates (H - eps_i S)^-1); option
 // HPSI_OPT_PRECOND_SHIFT = 1 takes one eps for all bands, the highest Ritz value of the block
 // (the "estimate of the highest occupied eigenvalue" of the diagonal form of D).  Subspace products are cuBLAS ZGEMMs (library GEMMs);
@@ -58,6 +63,18 @@ struct DavWork {
   int* info = nullptr;
   double2* work = nullptr;
   int lwork = 0;
+  // mixed path: float32 basis and products, float64 staging for H|psi>
+  bool mixed = false;
+  float2* phi32 = nullptr;    // [mmax][npw]
+  float2* hphi32 = nullptr;   // [mmax][npw]
+  float2* psi32 = nullptr;    // [nbnd][npw]
+  float2* hpsi32 = nullptr;   // [nbnd][npw]
+  float2* t32 = nullptr;      // [nbnd][npw]
+  float2* small32 = nullptr;  // [mmax][nbnd]
+  float2* ovl32 = nullptr;    // [nbnd][nbnd]
+  float2* hcol32 = nullptr;   // [mmax][nbnd]
+  double2* in64 = nullptr;    // [nbnd][npw]
+  double2* out64 = nullptr;   // [nbnd][npw]
 };
 
 // R_i = HPsi_i - eps_i Psi_i (in place into R) and ||R_i||_2; one CTA per band.
@@ -211,6 +228,16 @@ static void free_work(DavWork& w) {
   cudaFree(w.cn2);
   cudaFree(w.info);
   cudaFree(w.work);
+  cudaFree(w.phi32);
+  cudaFree(w.hphi32);
+  cudaFree(w.psi32);
+  cudaFree(w.hpsi32);
+  cudaFree(w.t32);
+  cudaFree(w.small32);
+  cudaFree(w.ovl32);
+  cudaFree(w.hcol32);
+  cudaFree(w.in64);
+  cudaFree(w.out64);
   w = DavWork();
 }
 
@@ -224,14 +251,15 @@ void davidson_release(Context& c) {
   c.blas = nullptr;
 }
 
-static int alloc_work(Context& c, DavHandles& h, int npw, int nbnd) {
+static int alloc_work(Context& c, DavHandles& h, int npw, int nbnd, bool mixed) {
   DavWork& w = h.wk;
   const int mmax = 4 * nbnd;
-  if (w.npw == npw && w.nbnd == nbnd) return HPSI_OK;
+  if (w.npw == npw && w.nbnd == nbnd && w.mixed == mixed) return HPSI_OK;
   free_work(w);
   w.npw = npw;
   w.nbnd = nbnd;
   w.mmax = mmax;
+  w.mixed = mixed;
   auto al = [&](void** p, size_t bytes) -> bool {
     if (cudaMalloc(p, std::max<size_t>(bytes, 256)) != cudaSuccess) {
       cudaGetLastError();
@@ -240,15 +268,24 @@ static int alloc_work(Context& c, DavHandles& h, int npw, int nbnd) {
     return true;
   };
   const size_t v = sizeof(double2) * (size_t)npw;
-  bool ok = al((void**)&w.phi, v * mmax) && al((void**)&w.hphi, v * mmax) && al((void**)&w.psi, v * nbnd) &&
-            al((void**)&w.hpsi, v * nbnd) && al((void**)&w.t, v * nbnd) &&
-            al((void**)&w.hsub, sizeof(double2) * (size_t)mmax * mmax) &&
+  const size_t v32 = sizeof(float2) * (size_t)npw;
+  bool ok = al((void**)&w.hsub, sizeof(double2) * (size_t)mmax * mmax) &&
             al((void**)&w.evec, sizeof(double2) * (size_t)mmax * mmax) &&
             al((void**)&w.small, sizeof(double2) * (size_t)mmax * nbnd) &&
             al((void**)&w.ovl, sizeof(double2) * (size_t)nbnd * nbnd) && al((void**)&w.w, sizeof(double) * mmax) &&
             al((void**)&w.eps, sizeof(double) * nbnd) && al((void**)&w.rnorm, sizeof(double) * nbnd) &&
             al((void**)&w.idx, sizeof(int) * nbnd) && al((void**)&w.idx2, sizeof(int) * nbnd) &&
             al((void**)&w.cn2, sizeof(double) * nbnd) && al((void**)&w.info, sizeof(int));
+  if (ok && !mixed)
+    ok = al((void**)&w.phi, v * mmax) && al((void**)&w.hphi, v * mmax) && al((void**)&w.psi, v * nbnd) &&
+         al((void**)&w.hpsi, v * nbnd) && al((void**)&w.t, v * nbnd);
+  if (ok && mixed)
+    ok = al((void**)&w.phi32, v32 * mmax) && al((void**)&w.hphi32, v32 * mmax) && al((void**)&w.psi32, v32 * nbnd) &&
+         al((void**)&w.hpsi32, v32 * nbnd) && al((void**)&w.t32, v32 * nbnd) &&
+         al((void**)&w.small32, sizeof(float2) * (size_t)mmax * nbnd) &&
+         al((void**)&w.ovl32, sizeof(float2) * (size_t)nbnd * nbnd) &&
+         al((void**)&w.hcol32, sizeof(float2) * (size_t)mmax * nbnd) && al((void**)&w.in64, v * nbnd) &&
+         al((void**)&w.out64, v * nbnd);
   if (!ok) {
     free_work(w);
     return fail(c, HPSI_ENOMEM, "davidson_solve: device allocation of the reduced basis failed");
@@ -306,6 +343,9 @@ static int canonical_orth(Context& c, DavHandles& h, const double2* x, int n, do
   return HPSI_OK;
 }
 
+static int davidson_run_mixed(Context& c, DavHandles& h, int ik, int nbnd, double tol, int maxiter, double2* psio,
+                              double* eig_out, int* iters_out, double* resnorm_out);
+
 int davidson_run(Context& c, int ik, int nbnd, double tol, int maxiter, double2* psio, double* eig_out, int* iters_out,
                  double* resnorm_out) {
   const Problem& p = c.probs[ik];
@@ -318,7 +358,9 @@ int davidson_run(Context& c, int ik, int nbnd, double tol, int maxiter, double2*
   }
   BCK(cublasSetStream(h->blas, c.stream), "cublasSetStream");
   BCK(cusolverDnSetStream(h->solver, c.stream), "cusolverDnSetStream");
-  int rc = alloc_work(c, *h, p.npw, nbnd);
+  if (c.precision == HPSI_MIXED) return davidson_run_mixed(c, *h, ik, nbnd, tol, maxiter, psio, eig_out, iters_out,
+                                                          resnorm_out);
+  int rc = alloc_work(c, *h, p.npw, nbnd, false);
   if (rc) return rc;
   DavWork& w = h->wk;
   const int npw = p.npw, N = nbnd, mmax = w.mmax;
@@ -432,6 +474,348 @@ int davidson_run(Context& c, int ik, int nbnd, double tol, int maxiter, double2*
   for (int i = 0; i < N; ++i) eig_out[i] = ev[i];
   if (resnorm_out)
     for (int i = 0; i < N; ++i) resnorm_out[i] = rn[i];
+  if (iters_out) *iters_out = it;
+  if (!converged) return fail(c, HPSI_ENOTCONV, "davidson_solve: not converged within maxiter");
+  return HPSI_OK;
+}
+
+
+// ---- mixed path: float32 basis, float64 small problems, norms and Rayleigh quotients ----------
+
+namespace {
+
+__device__ __forceinline__ double block_sum256(double s, double* red) {
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// R_i = HPsi_i - eps_i Psi_i (float32 data, float64 norm); one CTA per band.
+__global__ void __launch_bounds__(256) k_residual32(int npw, const float2* __restrict__ psi,
+                                                    const float2* __restrict__ hpsi, const double* __restrict__ eps,
+                                                    float2* __restrict__ r, double* __restrict__ rnorm) {
+  __shared__ double red[256];
+  const int b = blockIdx.x;
+  const double e = eps[b];
+  const float2* x = psi + (size_t)b * npw;
+  const float2* hx = hpsi + (size_t)b * npw;
+  float2* rb = r + (size_t)b * npw;
+  double s = 0.0;
+  for (int g = threadIdx.x; g < npw; g += blockDim.x) {
+    const double qx = (double)hx[g].x - e * (double)x[g].x, qy = (double)hx[g].y - e * (double)x[g].y;
+    rb[g] = make_float2((float)qx, (float)qy);
+    s += qx * qx + qy * qy;
+  }
+  s = block_sum256(s, red);
+  if (threadIdx.x == 0) rnorm[b] = sqrt(s);
+}
+
+__global__ void __launch_bounds__(256) k_precondition32(int npw, const int* __restrict__ idx,
+                                                        const float2* __restrict__ r, const double* __restrict__ hdiag,
+                                                        const double* __restrict__ eps, double tau, int eshift,
+                                                        float2* __restrict__ t) {
+  __shared__ double red[256];
+  const int j = blockIdx.x;
+  const int i = idx[j];
+  const double e = eps[eshift >= 0 ? eshift : i];
+  const float2* rb = r + (size_t)i * npw;
+  float2* tb = t + (size_t)j * npw;
+  double s = 0.0;
+  for (int g = threadIdx.x; g < npw; g += blockDim.x) {
+    double x = hdiag[g] - e;
+    if (fabs(x) < tau) x = x >= 0.0 ? tau : -tau;
+    const double qx = (double)rb[g].x / x, qy = (double)rb[g].y / x;
+    tb[g] = make_float2((float)qx, (float)qy);
+    s += qx * qx + qy * qy;
+  }
+  s = block_sum256(s, red);
+  const float inv = s > 0.0 ? (float)(1.0 / sqrt(s)) : 0.f;
+  for (int g = threadIdx.x; g < npw; g += blockDim.x) tb[g] = make_float2(tb[g].x * inv, tb[g].y * inv);
+}
+
+__global__ void __launch_bounds__(256) k_norm2_32(int npw, const float2* __restrict__ t, double* __restrict__ out) {
+  __shared__ double red[256];
+  const float2* tb = t + (size_t)blockIdx.x * npw;
+  double s = 0.0;
+  for (int g = threadIdx.x; g < npw; g += blockDim.x) s += (double)tb[g].x * tb[g].x + (double)tb[g].y * tb[g].y;
+  s = block_sum256(s, red);
+  if (threadIdx.x == 0) out[blockIdx.x] = s;
+}
+
+__global__ void k_fallback32(int npw, const int* __restrict__ which, const int* __restrict__ idx,
+                             const float2* __restrict__ r, const double* __restrict__ rnorm, float2* __restrict__ t) {
+  const int j = which[blockIdx.x];
+  const int i = idx[j];
+  const float s = (float)(1.0 / rnorm[i]);
+  const float2* rb = r + (size_t)i * npw;
+  float2* tb = t + (size_t)j * npw;
+  for (int g = threadIdx.x; g < npw; g += blockDim.x) tb[g] = make_float2(rb[g].x * s, rb[g].y * s);
+}
+
+__global__ void k_canon_scale32(int n, int ld, int first, int nkeep, const double2* __restrict__ v,
+                                const double* __restrict__ w, float2* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * nkeep) return;
+  const int row = i % n, c = i / n;
+  const double s = 1.0 / sqrt(w[first + c]);
+  const double2 x = v[(size_t)(first + c) * ld + row];
+  out[(size_t)c * n + row] = make_float2((float)(x.x * s), (float)(x.y * s));
+}
+
+__global__ void k_cvt_64_32(size_t n, const double2* __restrict__ in, float2* __restrict__ out) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = make_float2((float)in[i].x, (float)in[i].y);
+}
+
+__global__ void k_cvt_32_64(size_t n, const float2* __restrict__ in, double2* __restrict__ out) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = make_double2((double)in[i].x, (double)in[i].y);
+}
+
+__global__ void k_mat_32_to_64(int rows, int cols, const float2* __restrict__ src, int lds, double2* __restrict__ dst,
+                               int ldd) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows * cols) return;
+  const int r = i % rows, c = i / rows;
+  const float2 x = src[(size_t)c * lds + r];
+  dst[(size_t)c * ldd + r] = make_double2((double)x.x, (double)x.y);
+}
+
+__global__ void k_mat_64_to_32(int rows, int cols, const double2* __restrict__ src, int lds, float2* __restrict__ dst,
+                               int ldd) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows * cols) return;
+  const int r = i % rows, c = i / rows;
+  const double2 x = src[(size_t)c * lds + r];
+  dst[(size_t)c * ldd + r] = make_float2((float)x.x, (float)x.y);
+}
+
+// eps_i = Re<psi_i|H psi_i> / <psi_i|psi_i> and ||H psi_i - eps_i psi_i|| / ||psi_i||, float64.
+__global__ void __launch_bounds__(256) k_rayleigh(int npw, const double2* __restrict__ psi,
+                                                  const double2* __restrict__ hpsi, double* __restrict__ eps,
+                                                  double* __restrict__ rnorm) {
+  __shared__ double red[256];
+  const int b = blockIdx.x;
+  const double2* x = psi + (size_t)b * npw;
+  const double2* hx = hpsi + (size_t)b * npw;
+  double xx = 0.0, xh = 0.0, hh = 0.0;
+  for (int g = threadIdx.x; g < npw; g += blockDim.x) {
+    xx += x[g].x * x[g].x + x[g].y * x[g].y;
+    xh += x[g].x * hx[g].x + x[g].y * hx[g].y;
+    hh += hx[g].x * hx[g].x + hx[g].y * hx[g].y;
+  }
+  xx = block_sum256(xx, red);
+  xh = block_sum256(xh, red);
+  hh = block_sum256(hh, red);
+  if (threadIdx.x == 0) {
+    const double e = xh / xx;
+    eps[b] = e;
+    // ||Hx - e x||^2 = hh - 2 e xh + e^2 xx, evaluated directly below for accuracy
+  }
+  __syncthreads();
+  const double e = xh / xx;
+  double rr = 0.0;
+  for (int g = threadIdx.x; g < npw; g += blockDim.x) {
+    const double qx = hx[g].x - e * x[g].x, qy = hx[g].y - e * x[g].y;
+    rr += qx * qx + qy * qy;
+  }
+  rr = block_sum256(rr, red);
+  if (threadIdx.x == 0) rnorm[b] = sqrt(rr / xx);
+}
+
+__global__ void k_gather_rows(int npw, const int* __restrict__ perm, const double2* __restrict__ src,
+                              double2* __restrict__ dst) {
+  const int b = blockIdx.x;
+  const double2* s = src + (size_t)perm[b] * npw;
+  double2* o = dst + (size_t)b * npw;
+  for (int g = threadIdx.x; g < npw; g += blockDim.x) o[g] = s[g];
+}
+
+const cuComplex cOne = {1.f, 0.f};
+const cuComplex cZero = {0.f, 0.f};
+const cuComplex cMinusOne = {-1.f, 0.f};
+inline cuComplex* Cf(float2* p) { return reinterpret_cast<cuComplex*>(p); }
+
+}  // namespace
+
+static int grid_of(size_t n) { return (int)std::min<size_t>(4096, (n + 255) / 256); }
+
+// H applied to nb float32 vectors x32 -> float32 hx32, through the float64 staging buffers.
+static int apply32(Context& c, DavWork& w, int ik, const float2* x32, float2* hx32, int nb) {
+  const size_t n = (size_t)nb * w.npw;
+  HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_cvt_32_64<<<grid_of(n), 256, 0, c.stream>>>(n, x32, w.in64)));
+  int rc = apply_device(c, ik, w.in64, w.out64, nb);
+  if (rc) return rc;
+  HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_cvt_64_32<<<grid_of(n), 256, 0, c.stream>>>(n, w.out64, hx32)));
+  return HPSI_OK;
+}
+
+// Orthonormalise the float32 block x[0:n] into out (canonical, float64 eigen-decomposition of the
+// overlap); directions with overlap eigenvalue <= thr (relative to the largest if relative) drop.
+static int canonical_orth32(Context& c, DavHandles& h, const float2* x, int n, float2* out, int* nkeep, double thr,
+                            bool relative) {
+  DavWork& w = h.wk;
+  const int npw = w.npw;
+  BCK(cublasCgemm(h.blas, CUBLAS_OP_C, CUBLAS_OP_N, n, n, npw, &cOne, reinterpret_cast<const cuComplex*>(x), npw,
+                  reinterpret_cast<const cuComplex*>(x), npw, &cZero, Cf(w.ovl32), n),
+      "cgemm overlap");
+  HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
+              (k_mat_32_to_64<<<(n * n + 255) / 256, 256, 0, c.stream>>>(n, n, w.ovl32, n, w.ovl, n)));
+  int rc = small_eigh(c, h, w.ovl, n, n);
+  if (rc) return rc;
+  std::vector<double> lam(n);
+  DCK(cudaMemcpyAsync(lam.data(), w.w, sizeof(double) * n, cudaMemcpyDeviceToHost, c.stream), "overlap eigenvalues");
+  DCK(cudaStreamSynchronize(c.stream), "overlap eigenvalues");
+  const double cut = relative ? thr * lam[n - 1] : thr;
+  int first = 0;
+  while (first < n && !(lam[first] > cut && lam[first] > 1e-300)) ++first;
+  const int nk = n - first;
+  *nkeep = nk;
+  if (nk == 0) return HPSI_OK;
+  HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
+              (k_canon_scale32<<<(n * nk + 255) / 256, 256, 0, c.stream>>>(n, n, first, nk, w.evec, w.w, w.small32)));
+  BCK(cublasCgemm(h.blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, nk, n, &cOne, reinterpret_cast<const cuComplex*>(x), npw,
+                  Cf(w.small32), n, &cZero, Cf(out), npw),
+      "cgemm orthonormalise");
+  return HPSI_OK;
+}
+
+// H_sub[0:rows, col0:col0+ncol] = phi32[0:rows]^H hphi32[col0:col0+ncol], stored in float64.
+static int hsub_columns32(Context& c, DavHandles& h, int rows, int col0, int ncol) {
+  DavWork& w = h.wk;
+  const int npw = w.npw, mmax = w.mmax;
+  BCK(cublasCgemm(h.blas, CUBLAS_OP_C, CUBLAS_OP_N, rows, ncol, npw, &cOne, Cf(w.phi32), npw,
+                  Cf(w.hphi32 + (size_t)col0 * npw), npw, &cZero, Cf(w.hcol32), mmax),
+      "cgemm H_sub columns");
+  HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
+              (k_mat_32_to_64<<<(rows * ncol + 255) / 256, 256, 0, c.stream>>>(rows, ncol, w.hcol32, mmax,
+                                                                                 w.hsub + (size_t)col0 * mmax, mmax)));
+  return HPSI_OK;
+}
+
+static int davidson_run_mixed(Context& c, DavHandles& h, int ik, int nbnd, double tol, int maxiter, double2* psio,
+                              double* eig_out, int* iters_out, double* resnorm_out) {
+  const Problem& p = c.probs[ik];
+  int rc = alloc_work(c, h, p.npw, nbnd, true);
+  if (rc) return rc;
+  DavWork& w = h.wk;
+  const int npw = p.npw, N = nbnd, mmax = w.mmax;
+  const size_t vb = sizeof(float2) * (size_t)npw;
+  // phi32[0:N] <- orthonormalised initial guess
+  HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
+              (k_cvt_64_32<<<grid_of((size_t)N * npw), 256, 0, c.stream>>>((size_t)N * npw, psio, w.t32)));
+  int nk = 0;
+  rc = canonical_orth32(c, h, w.t32, N, w.phi32, &nk, 1e-12, true);
+  if (rc) return rc;
+  if (nk < N) return fail(c, HPSI_EINVAL, "davidson_solve: initial guess is linearly dependent");
+  rc = apply32(c, w, ik, w.phi32, w.hphi32, N);
+  if (rc) return rc;
+  int m = N;
+  rc = hsub_columns32(c, h, m, 0, m);
+  if (rc) return rc;
+  std::vector<double> rn(N), ev(N);
+  std::vector<int> uidx(N);
+  int it = 0;
+  bool converged = false;
+  for (;;) {
+    rc = small_eigh(c, h, w.hsub, mmax, m);
+    if (rc) return rc;
+    HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
+                (k_mat_64_to_32<<<(m * N + 255) / 256, 256, 0, c.stream>>>(m, N, w.evec, m, w.small32, m)));
+    BCK(cublasCgemm(h.blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, N, m, &cOne, Cf(w.phi32), npw, Cf(w.small32), m, &cZero,
+                    Cf(w.psi32), npw),
+        "cgemm Ritz vectors");
+    BCK(cublasCgemm(h.blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, N, m, &cOne, Cf(w.hphi32), npw, Cf(w.small32), m, &cZero,
+                    Cf(w.hpsi32), npw),
+        "cgemm H Ritz vectors");
+    DCK(cudaMemcpyAsync(w.eps, w.w, sizeof(double) * N, cudaMemcpyDeviceToDevice, c.stream), "eps copy");
+    HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_residual32<<<N, 256, 0, c.stream>>>(npw, w.psi32, w.hpsi32, w.eps, w.t32, w.rnorm)));
+    DCK(cudaMemcpyAsync(rn.data(), w.rnorm, sizeof(double) * N, cudaMemcpyDeviceToHost, c.stream), "norm copy");
+    DCK(cudaStreamSynchronize(c.stream), "davidson iteration");
+    rc = check_device_error(c);
+    if (rc) return rc;
+    int nc = 0;
+    for (int i = 0; i < N; ++i)
+      if (!(rn[i] <= tol)) uidx[nc++] = i;
+    if (nc == 0) {
+      converged = true;
+      break;
+    }
+    if (it >= maxiter) break;
+    ++it;
+    if (m + nc > mmax) {
+      DCK(cudaMemcpyAsync(w.phi32, w.psi32, vb * N, cudaMemcpyDeviceToDevice, c.stream), "restart copy");
+      DCK(cudaMemcpyAsync(w.hphi32, w.hpsi32, vb * N, cudaMemcpyDeviceToDevice, c.stream), "restart copy");
+      m = N;
+      rc = hsub_columns32(c, h, m, 0, m);
+      if (rc) return rc;
+    }
+    DCK(cudaMemcpyAsync(w.idx, uidx.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, c.stream), "index copy");
+    float2* tnew = w.phi32 + (size_t)m * npw;
+    const int eshift = c.opt_shift == 1 ? N - 1 : -1;
+    HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_precondition32<<<nc, 256, 0, c.stream>>>(npw, w.idx, w.t32, p.d_hdiag, w.eps,
+                                                                                c.opt_tau, eshift, tnew)));
+    for (int round = 0; round < 2; ++round) {
+      for (int pass = 0; pass < 2; ++pass) {
+        BCK(cublasCgemm(h.blas, CUBLAS_OP_C, CUBLAS_OP_N, m, nc, npw, &cOne, Cf(w.phi32), npw, Cf(tnew), npw, &cZero,
+                        Cf(w.small32), m),
+            "cgemm projection");
+        BCK(cublasCgemm(h.blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, nc, m, &cMinusOne, Cf(w.phi32), npw, Cf(w.small32), m,
+                        &cOne, Cf(tnew), npw),
+            "cgemm projection update");
+      }
+      if (round == 1) break;
+      HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_norm2_32<<<nc, 256, 0, c.stream>>>(npw, tnew, w.cn2)));
+      std::vector<double> cn(nc);
+      DCK(cudaMemcpyAsync(cn.data(), w.cn2, sizeof(double) * nc, cudaMemcpyDeviceToHost, c.stream), "norm copy");
+      DCK(cudaStreamSynchronize(c.stream), "correction norms");
+      std::vector<int> col;
+      for (int j = 0; j < nc; ++j)
+        if (!(cn[j] >= kCollapse)) col.push_back(j);
+      if (col.empty()) break;
+      DCK(cudaMemcpyAsync(w.idx2, col.data(), sizeof(int) * col.size(), cudaMemcpyHostToDevice, c.stream),
+          "index copy");
+      HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
+                  (k_fallback32<<<(int)col.size(), 256, 0, c.stream>>>(npw, w.idx2, w.idx, w.t32, w.rnorm, tnew)));
+    }
+    int nkeep = 0;
+    rc = canonical_orth32(c, h, tnew, nc, w.t32, &nkeep, kDropAbs, false);
+    if (rc) return rc;
+    if (nkeep == 0) break;
+    DCK(cudaMemcpyAsync(tnew, w.t32, vb * nkeep, cudaMemcpyDeviceToDevice, c.stream), "basis copy");
+    rc = apply32(c, w, ik, tnew, w.hphi32 + (size_t)m * npw, nkeep);
+    if (rc) return rc;
+    rc = hsub_columns32(c, h, m + nkeep, m, nkeep);
+    if (rc) return rc;
+    m += nkeep;
+  }
+  // float64 Rayleigh quotients of the Ritz vectors with a fresh H|psi>
+  const size_t n = (size_t)N * npw;
+  HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_cvt_32_64<<<grid_of(n), 256, 0, c.stream>>>(n, w.psi32, w.in64)));
+  rc = apply_device(c, ik, w.in64, w.out64, N);
+  if (rc) return rc;
+  HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_rayleigh<<<N, 256, 0, c.stream>>>(npw, w.in64, w.out64, w.eps, w.rnorm)));
+  DCK(cudaMemcpyAsync(ev.data(), w.eps, sizeof(double) * N, cudaMemcpyDeviceToHost, c.stream), "eig copy");
+  DCK(cudaMemcpyAsync(rn.data(), w.rnorm, sizeof(double) * N, cudaMemcpyDeviceToHost, c.stream), "norm copy");
+  DCK(cudaStreamSynchronize(c.stream), "davidson end");
+  rc = check_device_error(c);
+  if (rc) return rc;
+  std::vector<int> perm(N);
+  for (int i = 0; i < N; ++i) perm[i] = i;
+  std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return ev[a] < ev[b]; });
+  DCK(cudaMemcpyAsync(w.idx, perm.data(), sizeof(int) * N, cudaMemcpyHostToDevice, c.stream), "perm copy");
+  HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_gather_rows<<<N, 256, 0, c.stream>>>(npw, w.idx, w.in64, psio)));
+  DCK(cudaStreamSynchronize(c.stream), "davidson end");
+  for (int i = 0; i < N; ++i) {
+    eig_out[i] = ev[perm[i]];
+    if (resnorm_out) resnorm_out[i] = rn[perm[i]];
+  }
   if (iters_out) *iters_out = it;
   if (!converged) return fail(c, HPSI_ENOTCONV, "davidson_solve: not converged within maxiter");
   return HPSI_OK;

@@ -110,7 +110,7 @@ struct Context {
   int opt_shift = 0;                   // Davidson: 0 = eps_i per band, 1 = highest Ritz value
   void* blas = nullptr;                // Davidson handles and work buffers
   int* d_err = nullptr;                // device error word raised by bounded waits
-  int nl_terms = 2;                    // mixed path: bf16 terms per operand (2 or 3)
+  int nl_terms = 3;                    // mixed path: bf16 terms per operand (2 or 3)
   int force_generic = 0;               // 1: local part on the generic FFT kernels
   // launch accounting (always) and per-launch event timing (HPSI_OPT_KERNEL_TIMING)
   bool timing = false;

@@ -12,7 +12,7 @@ import workloads
 pytestmark = pytest.mark.gpu
 
 
-def _setup(p, precision=0, zero_potential=False):
+def _setup(p, precision=0, zero_potential=False):  # noqa: D103
     import torch
     from paper_0906_2569_gb300 import binding as B
     k = p.kpts[0]
@@ -86,3 +86,59 @@ def test_davidson_host_buffer(lib):
     h = oracle.hamiltonian.dense_h(p.lattice, p.kpts[0], m, p.fft, vr, beta, d)
     assert np.max(np.abs(eig - oracle.eigen.lowest_dense(h, p.nbnd))) < 1e-10
     assert np.max(np.abs(np.conj(x) @ x.T - np.eye(p.nbnd))) < 1e-12
+
+
+def _golden(name):
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "eigenvalues.json")
+    data = json.load(open(path))
+    if name not in data:
+        pytest.fail(f"golden eigenvalues for {name} missing: run tests/golden/make_golden.py {name}")
+    return data[name]["eigenvalues"]
+
+
+@pytest.mark.parametrize("nbnd", [16, 160])
+def test_davidson_mixed_c1(lib, nbnd):
+    """Mixed path: float32 subspace, float64 eigensolves / norms / final Rayleigh quotients: 1e-6 Ha."""
+    import torch
+    from paper_0906_2569_gb300 import binding as B
+    p = workloads.config3(nbnd)
+    ctx, m, vr, beta, d = _setup(p, precision=B.HPSI_MIXED)
+    x = torch.from_numpy(workloads.psi0(p.lattice, p.kpts[0], m, p.nbnd, p.psi_seed)).cuda()
+    eig, it, res, rc = B.davidson_solve(ctx, 0, x, 1e-5, 400)
+    ref = np.asarray(_golden("c3")[:nbnd])
+    assert np.max(np.abs(eig - ref)) < 1e-6
+    v = x.cpu().numpy()
+    assert np.max(np.abs(np.conj(v) @ v.T - np.eye(nbnd))) < 1e-4
+
+
+@pytest.mark.parametrize("precision,tol,etol", [(0, 1e-8, 1e-10), (1, 1e-5, 1e-6)])
+def test_davidson_c2(lib, precision, tol, etol):
+    """The 36785-PW, 256-projector cell, 160 bands, against the oracle's LOBPCG eigenvalues."""
+    import torch
+    from paper_0906_2569_gb300 import binding as B
+    p = workloads.config2()
+    ctx, m, vr, beta, d = _setup(p, precision=precision)
+    x = torch.from_numpy(workloads.psi0(p.lattice, p.kpts[0], m, p.nbnd, p.psi_seed)).cuda()
+    eig, it, res, rc = B.davidson_solve(ctx, 0, x, tol, 300)
+    ref = np.asarray(_golden("c2"))
+    assert np.max(np.abs(eig - ref)) < etol
+
+
+def test_davidson_kpoints_c4a(lib):
+    """Two k-points of the fcc cell (k != 0, complex H), float64, against dense LAPACK."""
+    import torch
+    from paper_0906_2569_gb300 import binding as B
+    p = workloads.config4a()
+    ref = _golden("c4a")
+    kp = p.kpts[:2]
+    ms = [B.hpsi_gsphere(p.lattice, p.ecut, k) for k in kp]
+    vr = workloads.vloc_r(p.lattice, p.atoms, p.fft)
+    betas = [workloads.beta(p.lattice, p.atoms, k, m) for k, m in zip(kp, ms)]
+    ctx = B.hpsi_setup(p.lattice, p.ecut, kp, p.fft, vr, betas, workloads.dmat(len(p.atoms)), B.HPSI_FP64,
+                       torch.cuda.current_stream().cuda_stream)
+    for ik in range(2):
+        x = torch.from_numpy(workloads.psi0(p.lattice, kp[ik], ms[ik], p.nbnd, p.psi_seed + ik)).cuda()
+        eig, it, res, rc = B.davidson_solve(ctx, ik, x, 1e-8, 300)
+        assert np.max(np.abs(eig - np.asarray(ref[ik]))) < 1e-10
