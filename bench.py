@@ -23,6 +23,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -51,6 +52,7 @@ def parse():
     ap.add_argument("--config", default="c2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     return ap.parse_args()
 
 
@@ -316,6 +318,7 @@ def run_gpu(args):
             dist.destroy_process_group()
         return
     roof = roofline(mixed, p, npw, nst, npl, B.HPSI_MIXED)
+    roof64 = roofline(fp64, p, npw, nst, npl, B.HPSI_FP64)
     out = {
         "metric": "H|psi> band-applications/s (mixed precision; float64 beside it)",
         "value": value, "unit": "band-applications/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -327,7 +330,7 @@ def run_gpu(args):
                    "l2": "256 MB buffer written between timed steps", "parallelism": f"replicas x{world}"},
         "fp64": {"value": v64, "unit": "band-applications/s", "ms_per_step": f64_ms / args.steps,
                  "hpsi_apply_band_apps_per_s": p.nbnd / (fp64["hpsi_ms"] / 1e3), "kernels": fp64["kernels"],
-                 "dtype": "c128"},
+                 "roofline": roof64, "dtype": "c128"},
         "mixed_over_fp64": value / v64,
         "hpsi_apply_band_apps_per_s": p.nbnd / (mixed["hpsi_ms"] / 1e3),
         "kernels": mixed["kernels"],
@@ -339,11 +342,63 @@ def run_gpu(args):
         tot = sum(mixed["e2e_s"])
         out["e2e"] = {"value": mixed["band_apps"] / tot * world, "unit": "band-applications/s",
                       "h2d_bytes_per_step": mixed["e2e_bytes"], "d2h_bytes_per_step": mixed["e2e_bytes"] + 8 * p.nbnd}
+    if not args.no_batch:
+        out["batched"] = batch_throughput(args, B, torch, flush)
     if not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(p)
     print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def batch_throughput(args, B, torch, flush):
+    """hpsi_apply_batch (CUDA-graph replay) on the 16 k-points of the fcc cell and on the 32 cells:
+    band-applications/s, float64 and mixed."""
+    import workloads
+    stream = torch.cuda.current_stream()
+    out = {}
+    p = workloads.config4a()
+    ms = [B.hpsi_gsphere(p.lattice, p.ecut, k) for k in p.kpts]
+    vr = workloads.vloc_r(p.lattice, p.atoms, p.fft)
+    betas = [workloads.beta(p.lattice, p.atoms, k, m) for k, m in zip(p.kpts, ms)]
+    xs_k = [torch.from_numpy(workloads.psi0(p.lattice, k, m, p.nbnd, p.psi_seed + i)).cuda()
+            for i, (k, m) in enumerate(zip(p.kpts, ms))]
+    cells = workloads.config4b()
+    cm = [B.hpsi_gsphere(c.lattice, c.ecut, c.kpts[0]) for c in cells]
+    cv = [workloads.vloc_r(c.lattice, c.atoms, c.fft) for c in cells]
+    cb = [workloads.beta(c.lattice, c.atoms, c.kpts[0], m) for c, m in zip(cells, cm)]
+    xs_c = [torch.from_numpy(workloads.psi0(c.lattice, c.kpts[0], m, c.nbnd, c.psi_seed)).cuda()
+            for c, m in zip(cells, cm)]
+    for prec, pname in ((B.HPSI_FP64, "fp64"), (B.HPSI_MIXED, "mixed")):
+        for label, make, xs in (
+                ("kpoints_fcc_16k_24b", lambda: B.hpsi_setup(p.lattice, p.ecut, p.kpts, p.fft, vr, betas,
+                                                             workloads.dmat(len(p.atoms)), prec, stream.cuda_stream),
+                 xs_k),
+                ("cells_32", lambda: B.hpsi_setup_cells([c.lattice for c in cells], [c.ecut for c in cells],
+                                                        [c.fft for c in cells], cv, cb,
+                                                        [workloads.dmat(len(c.atoms)) for c in cells], prec,
+                                                        stream.cuda_stream), xs_c)):
+            ctx = make()
+            ys = [torch.empty_like(x) for x in xs]
+            probs = list(range(len(xs)))
+            for _ in range(max(3, args.warmup)):
+                B.hpsi_apply_batch(ctx, probs, xs, ys)
+            torch.cuda.synchronize()
+            ms_ = []
+            for _ in range(max(5, args.steps)):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                B.hpsi_apply_batch(ctx, probs, xs, ys)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms_.append(e0.elapsed_time(e1))
+            bands = sum(int(x.shape[0]) for x in xs)
+            out.setdefault(label, {})[pname] = {"band_apps_per_s": bands / (statistics.median(ms_) / 1e3),
+                                                "ms_per_batch": statistics.median(ms_), "items": len(xs),
+                                                "bands": bands}
+            ctx.close()
+    return out
 
 
 def stick_counts(miller, fft):
@@ -354,20 +409,26 @@ def stick_counts(miller, fft):
 
 
 def kernel_work(name, p, npw, nst, npl, precision, nproj):
-    """Algorithmic (bytes, flops) of one band-application through a kernel class."""
+    """Algorithmic (bytes, flops) of one band-application through a kernel class of the fast path.
+
+    Line FFTs count 5 n log2 n flops; bytes are the HBM data the method itself must move per band
+    (psi in, H|psi> out, the stick rows between the z and the plane kernels)."""
     n1, n2, n3 = p.fft
     cs = 16 if precision == 0 else 8
-    x_bytes = n3 * npl * n2 * cs
-    y_bytes = n3 * nst * cs
+    fft = lambda n: 5.0 * n * math.log2(n)
+    rows = n3 * nst * cs
     if name == "inv_zy":
-        return 16 * npw + x_bytes, None
+        return 16 * npw + rows, nst * fft(n3)
     if name == "xvx_y":
-        return x_bytes + y_bytes, None
+        return 2 * rows, n3 * (2 * npl * fft(n2) + 2 * n2 * fft(n1) + 2 * n1 * n2)
     if name == "fwd_z":
-        return y_bytes + 2 * 16 * npw + 8 * npw, None
+        return rows + 2 * 16 * npw + 8 * npw, nst * fft(n3)
     if name in ("calbec", "addvus"):
-        return None, 8.0 * nproj * npw
+        return 16 * npw, 8.0 * nproj * npw * (6 if precision == 1 else 1)
     return None, None
+
+
+FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2070 MHz
 
 
 def roofline(res, p, npw, nst, npl, precision):
@@ -376,30 +437,42 @@ def roofline(res, p, npw, nst, npl, precision):
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
+    hbm = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
     ks = res["kernels"]
-    cand = {k: v for k, v in ks.items() if k != "davidson" and v["ms"] > 0}
+    cand = {k: v for k, v in ks.items() if k in ("inv_zy", "xvx_y", "fwd_z", "calbec", "addvus") and v["ms"] > 0}
     if not cand:
         return None
     name = max(cand, key=lambda k: cand[k]["ms"])
     units = res["band_apps"]
     byt, flop = kernel_work(name, p, npw, nst, npl, precision, p.nproj)
+    secs = cand[name]["ms"] / 1e3
     avg_ms = cand[name]["ms"] / cand[name]["launches"]
-    src = {"inv_zy": "local_kernels.cu", "xvx_y": "local_kernels.cu", "fwd_z": "local_kernels.cu",
-           "calbec": "nonlocal_fp64.cu", "addvus": "nonlocal_fp64.cu"}.get(name)
+    src = {"inv_zy": "local_fast.cu", "xvx_y": "local_fast.cu", "fwd_z": "local_fast.cu",
+           "calbec": "nonlocal_tc.cu" if precision == 1 else "nonlocal_fp64.cu",
+           "addvus": "nonlocal_tc.cu" if precision == 1 else "nonlocal_fp64.cu"}[name]
     traffic = None
-    if src and name in NCU_TRAFFIC and NCU_TRAFFIC[name][0] == file_hash(os.path.join("paper_0906_2569_gb300", "csrc", src)):
-        traffic = NCU_TRAFFIC[name][1]
-    if byt is not None:
-        achieved = units * byt / (cand[name]["ms"] / 1e3) / 1e9
-        peak = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
-        return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "avg_launch_ms": avg_ms,
-                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-                "bytes_per_band": byt}
-    achieved = units * flop / (cand[name]["ms"] / 1e3) / 1e12
-    return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": FP64_ALU_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_ALU_TFLOPS, "traffic": traffic, "avg_launch_ms": avg_ms,
-            "peak_source": "derived: 152 SMs x 2 DFMA/clk (measured) x 2 flop x 2070 MHz", "flops_per_band": flop}
+    key = (name, precision)
+    if key in NCU_TRAFFIC and NCU_TRAFFIC[key][0] == file_hash(os.path.join("paper_0906_2569_gb300", "csrc", src)):
+        traffic = NCU_TRAFFIC[key][1]
+    out = {"kernel": name, "avg_launch_ms": avg_ms, "traffic": traffic, "bytes_per_band": byt, "flops_per_band": flop}
+    if name in ("calbec", "addvus") and precision == 1:
+        peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+        ach = units * flop / secs / 1e12
+        out.update({"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                    "peak_source": "measured bf16 sustained"})
+        return out
+    alu = FP64_ALU_TFLOPS if precision == 0 else FP32_ALU_TFLOPS
+    ridge = alu * 1e12 / (hbm * 1e9)
+    if flop / byt > ridge:
+        ach = units * flop / secs / 1e12
+        out.update({"bound": "alu", "achieved": ach, "peak": alu, "unit": "TFLOP/s", "frac": ach / alu,
+                    "peak_source": ("derived: 152 SMs x 2 DFMA/clk (measured) x 2 flop x 2070 MHz" if precision == 0
+                                    else "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz")})
+    else:
+        ach = units * byt / secs / 1e9
+        out.update({"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                    "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"})
+    return out
 
 
 def main():

@@ -173,9 +173,15 @@ HPSI_API int hpsi_apply(hpsi_ctx* ctx, int ik, const void* psi_in, void* hpsi_ou
 HPSI_API int hpsi_apply_noalloc(hpsi_ctx* ctx, int ik, const void* psi_in, void* hpsi_out, int nbnd);
 
 /*
- * hpsi_apply_batch -- H psi for several problems in one launch sequence (one CUDA graph):
+ * hpsi_apply_batch -- H psi for several problems (k-points or cells) in one launch sequence:
  * for i < nitem: hpsi_out[i] = H(prob[i]) psi_in[i] with nbnd[i] bands.  Device pointers only.
- * Items are independent; outputs must not overlap inputs or each other.
+ * Items whose cubic box has register-codelet kernels share one launch of each local-potential
+ * kernel per box edge (blockIdx.z runs over the items); the nonlocal term follows per item.
+ * The first call with a given argument list runs eagerly and captures the same sequence in a CUDA
+ * graph; later calls with identical arguments (same problems, band counts and pointers) replay
+ * the graph with one launch.  Items are independent; outputs must not overlap inputs or each other.
+ * (Pools of k-points and task groups of bands in the paper's Table 1 are prior art for this
+ * batching; here the items simply share the launches of one GPU.)
  */
 HPSI_API int hpsi_apply_batch(hpsi_ctx* ctx, int nitem, const int* prob, const int* nbnd,
                      const void* const* psi_in, void* const* hpsi_out);

@@ -78,6 +78,7 @@ int check_device_error(Context& c) {
 
 int ensure_buffer(Context& c, void** ptr, size_t* have, size_t need) {
   if (need <= *have && *ptr) return HPSI_OK;
+  c.ws.epoch++;
   if (*ptr) {
     cudaStreamSynchronize(c.stream);
     cudaFree(*ptr);
@@ -344,7 +345,15 @@ static void free_context(Context& c) {
   cudaFree(c.ws.stage_in);
   cudaFree(c.ws.stage_out);
   cudaFree(c.ws.mixed);
+  cudaFree(c.ws.batch);
+  if (c.graph.exec) cudaGraphExecDestroy(c.graph.exec);
+  if (c.cap_stream) cudaStreamDestroy(c.cap_stream);
   davidson_release(c);
+}
+
+int nonlocal_apply(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd) {
+  if (c.precision == HPSI_FP64) return nonlocal_apply_fp64(c, p, psi, hpsi, nbnd);
+  return nonlocal_apply_mixed(c, p, psi, hpsi, nbnd);
 }
 
 int apply_device(Context& c, int ik, const double2* psi, double2* hpsi, int nbnd) {
@@ -352,8 +361,66 @@ int apply_device(Context& c, int ik, const double2* psi, double2* hpsi, int nbnd
   c.band_apps += nbnd;
   int rc = local_apply(c, p, psi, hpsi, nbnd);
   if (rc) return rc;
-  if (c.precision == HPSI_FP64) return nonlocal_apply_fp64(c, p, psi, hpsi, nbnd);
-  return nonlocal_apply_mixed(c, p, psi, hpsi, nbnd);
+  return nonlocal_apply(c, p, psi, hpsi, nbnd);
+}
+
+// All items at once: problems whose box has the fast kernels share one launch per kernel and box
+// edge (their stick rows live side by side in one workspace); the others take the generic path;
+// the nonlocal term follows per item.
+int batch_apply(Context& c, int nitem, const int* prob, const int* nbnd, const double2* const* psi,
+                double2* const* hpsi) {
+  std::vector<int> fast, slow;
+  for (int i = 0; i < nitem; ++i) {
+    if (nbnd[i] == 0) continue;
+    const Problem& p = c.probs[prob[i]];
+    if ((p.fast_flags & 4) && !c.force_generic) fast.push_back(i);
+    else slow.push_back(i);
+  }
+  std::stable_sort(fast.begin(), fast.end(), [&](int x, int y) {
+    const Problem& a = c.probs[prob[x]];
+    const Problem& b = c.probs[prob[y]];
+    return a.n[0] != b.n[0] ? a.n[0] < b.n[0] : a.fast_flags < b.fast_flags;
+  });
+  const size_t cs = c.precision == HPSI_FP64 ? sizeof(double2) : sizeof(float2);
+  std::vector<size_t> off(fast.size());
+  size_t total = 0;
+  for (size_t j = 0; j < fast.size(); ++j) {
+    const Problem& p = c.probs[prob[fast[j]]];
+    off[j] = total;
+    total += 2 * ((cs * (size_t)nbnd[fast[j]] * p.n[2] * p.nst + 255) & ~size_t(255));
+  }
+  if (!fast.empty()) {
+    int rc = ensure_buffer(c, &c.ws.batch, &c.ws.batchbytes, total);
+    if (rc) return rc;
+    std::vector<int> fp(fast.size()), fn(fast.size());
+    std::vector<const double2*> fi(fast.size());
+    std::vector<double2*> fo(fast.size());
+    std::vector<void*> zt(fast.size()), yb(fast.size());
+    unsigned char* base = static_cast<unsigned char*>(c.ws.batch);
+    for (size_t j = 0; j < fast.size(); ++j) {
+      const int i = fast[j];
+      const Problem& p = c.probs[prob[i]];
+      fp[j] = prob[i];
+      fn[j] = nbnd[i];
+      fi[j] = psi[i];
+      fo[j] = hpsi[i];
+      zt[j] = base + off[j];
+      yb[j] = base + off[j] + ((cs * (size_t)nbnd[i] * p.n[2] * p.nst + 255) & ~size_t(255));
+    }
+    rc = local_fast_apply_multi(c, (int)fast.size(), fp.data(), fn.data(), fi.data(), fo.data(), zt.data(), yb.data());
+    if (rc) return rc;
+  }
+  for (int i : slow) {
+    int rc = local_apply(c, c.probs[prob[i]], psi[i], hpsi[i], nbnd[i]);
+    if (rc) return rc;
+  }
+  for (int i = 0; i < nitem; ++i) {
+    if (nbnd[i] == 0) continue;
+    int rc = nonlocal_apply(c, c.probs[prob[i]], psi[i], hpsi[i], nbnd[i]);
+    if (rc) return rc;
+    c.band_apps += nbnd[i];
+  }
+  return HPSI_OK;
 }
 
 // 1 = device (or managed), 0 = host, -1 = error
@@ -602,12 +669,67 @@ extern "C" int hpsi_apply_batch(hpsi_ctx* ctx, int nitem, const int* prob, const
     if (nbnd[i] > 0 && (pointer_kind(psi_in[i]) != 1 || pointer_kind(hpsi_out[i]) != 1))
       return fail(c, HPSI_EINVAL, "hpsi_apply_batch: item pointers must be device memory");
   }
+  std::vector<unsigned long long> key;
+  key.push_back((unsigned long long)nitem);
+  key.push_back((unsigned long long)(c.precision * 16 + c.nl_terms * 2 + c.force_generic));
   for (int i = 0; i < nitem; ++i) {
-    if (nbnd[i] == 0) continue;
-    int rc = apply_device(c, prob[i], static_cast<const double2*>(psi_in[i]), static_cast<double2*>(hpsi_out[i]),
-                          nbnd[i]);
-    if (rc) return rc;
+    key.push_back((unsigned long long)prob[i]);
+    key.push_back((unsigned long long)nbnd[i]);
+    key.push_back((unsigned long long)reinterpret_cast<uintptr_t>(psi_in[i]));
+    key.push_back((unsigned long long)reinterpret_cast<uintptr_t>(hpsi_out[i]));
   }
+  const double2* const* pi = reinterpret_cast<const double2* const*>(psi_in);
+  double2* const* po = reinterpret_cast<double2* const*>(hpsi_out);
+  GraphCache& g = c.graph;
+  if (g.exec && g.key == key && g.epoch == c.ws.epoch) {
+    cudaError_t e = cudaGraphLaunch(g.exec, c.stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "hpsi_apply_batch graph launch");
+    for (int k = 0; k < HPSI_K_COUNT; ++k) c.launches[k] += g.launches[k];
+    c.band_apps += g.band_apps;
+    return HPSI_OK;
+  }
+  // first call with these arguments: run it, then capture the same sequence for later calls
+  long long before[HPSI_K_COUNT];
+  for (int k = 0; k < HPSI_K_COUNT; ++k) before[k] = c.launches[k];
+  const long long bapps0 = c.band_apps;
+  int rc = batch_apply(c, nitem, prob, nbnd, pi, po);
+  if (rc) return rc;
+  if (g.exec) {
+    cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+  }
+  if (!c.cap_stream && cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return HPSI_OK;   // no capture stream: this call ran eagerly, later calls will too
+  }
+  long long after[HPSI_K_COUNT];
+  for (int k = 0; k < HPSI_K_COUNT; ++k) after[k] = c.launches[k];
+  const long long bapps1 = c.band_apps;
+  const long long epoch = c.ws.epoch;
+  cudaStream_t orig = c.stream;
+  const bool timing = c.timing;
+  c.timing = false;
+  c.stream = c.cap_stream;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(c.cap_stream, cudaStreamCaptureModeThreadLocal);
+  int rc2 = e == cudaSuccess ? batch_apply(c, nitem, prob, nbnd, pi, po) : HPSI_ECUDA;
+  cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(c.cap_stream, &graph) : e;
+  c.stream = orig;
+  c.timing = timing;
+  for (int k = 0; k < HPSI_K_COUNT; ++k) c.launches[k] = after[k];
+  c.band_apps = bapps1;
+  if (rc2 == HPSI_OK && e2 == cudaSuccess && graph && c.ws.epoch == epoch) {
+    cudaGraphExec_t exec = nullptr;
+    if (cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
+      g.exec = exec;
+      g.key = key;
+      g.epoch = epoch;
+      for (int k = 0; k < HPSI_K_COUNT; ++k) g.launches[k] = after[k] - before[k];
+      g.band_apps = bapps1 - bapps0;
+    }
+  }
+  if (graph) cudaGraphDestroy(graph);
+  cudaGetLastError();
   return HPSI_OK;
 }
 

@@ -93,6 +93,17 @@ struct Workspace {
   void* stage_in = nullptr; size_t stage_in_bytes = 0;    // host-pointer staging
   void* stage_out = nullptr; size_t stage_out_bytes = 0;
   void* mixed = nullptr; size_t mixedbytes = 0;  // bf16 operand planes of the mixed path
+  void* batch = nullptr; size_t batchbytes = 0;  // stick rows of a batched apply
+  long long epoch = 0;                           // bumped whenever a buffer is reallocated
+};
+
+// A captured hpsi_apply_batch sequence, replayed while its arguments and buffers are unchanged.
+struct GraphCache {
+  std::vector<unsigned long long> key;
+  cudaGraphExec_t exec = nullptr;
+  long long epoch = -1;
+  long long launches[HPSI_K_COUNT] = {0};
+  long long band_apps = 0;
 };
 
 struct Context {
@@ -112,6 +123,8 @@ struct Context {
   int* d_err = nullptr;                // device error word raised by bounded waits
   int nl_terms = 3;                    // mixed path: bf16 terms per operand (2 or 3)
   int force_generic = 0;               // 1: local part on the generic FFT kernels
+  cudaStream_t cap_stream = nullptr;   // internal stream for graph capture
+  GraphCache graph;
   // launch accounting (always) and per-launch event timing (HPSI_OPT_KERNEL_TIMING)
   bool timing = false;
   long long launches[HPSI_K_COUNT] = {0};
@@ -149,6 +162,11 @@ size_t local_scratch_per_band(const Problem& p, int precision);
 int local_fast_plan(const Problem& p, int precision, size_t smem_optin);
 int local_fast_apply(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd, void* Zt, void* Yb,
                      int nbb);
+int local_fast_apply_multi(Context& c, int nitem, const int* prob, const int* nbnd, const double2* const* psi,
+                           double2* const* hpsi, void* const* zt, void* const* yb);
+int nonlocal_apply(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd);
+int batch_apply(Context& c, int nitem, const int* prob, const int* nbnd, const double2* const* psi,
+                double2* const* hpsi);
 int local_apply_into(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd, void* X, void* Y,
                      int nbb);
 void nonlocal_fp64_plan(const Context& c, const Problem& p, int nbnd, int* nsplit, int* kchunk, size_t* bytes);

@@ -21,9 +21,9 @@ namespace hpsi {
 
 namespace {
 
-struct FastArgs {
-  int N, npw, npl, nst, nb, bpc;   // bpc: bands per k_plane CTA
-  int stage_v, stage_row;
+// One problem's share of a launch (a k-point or a cell with its band block).
+struct FastItem {
+  int nb, npw, npl, nst, bpc;  // bpc: bands per k_plane CTA
   const StickDev* sticks;
   const int* ymap;     // [npl][N]: stick of (plane, j2) or -1
   const int* xmap;     // [N]: plane of ix or -1
@@ -33,14 +33,22 @@ struct FastArgs {
   void* Zt;            // [nb][N][nst]
   void* Yb;            // [nb][N][nst]
   const void* V;       // [N][N][N] as [j3][j2][j1]
+};
+
+constexpr int kMaxItems = 32;
+
+// Every launch takes its items by value (the parameter block is 32 KB on sm_70 and later).
+struct FastBatch {
+  int nitems, N, stage_v, stage_row;
   const double2* tw64; // e^{-2 pi i j / N}, j < N
   const float2* tw32;
   double inv_nr;
+  FastItem item[kMaxItems];
 };
 
-template <typename V> __device__ __forceinline__ const V* twt(const FastArgs& a);
-template <> __device__ __forceinline__ const double2* twt<double2>(const FastArgs& a) { return a.tw64; }
-template <> __device__ __forceinline__ const float2* twt<float2>(const FastArgs& a) { return a.tw32; }
+template <typename V> __device__ __forceinline__ const V* twt(const FastBatch& a);
+template <> __device__ __forceinline__ const double2* twt<double2>(const FastBatch& a) { return a.tw64; }
+template <> __device__ __forceinline__ const float2* twt<float2>(const FastBatch& a) { return a.tw32; }
 
 template <typename V> __device__ __forceinline__ V d2v(double2 x);
 template <> __device__ __forceinline__ double2 d2v<double2>(double2 x) { return x; }
@@ -54,10 +62,12 @@ template <int R1, int R2> struct Geo {
 };
 
 template <typename T, int R1, int R2>
-__global__ void __launch_bounds__(256) k_zinv(FastArgs a) {
+__global__ void __launch_bounds__(256) k_zinv(const __grid_constant__ FastBatch bt) {
   using V = typename Cx<T>::type;
   using Gm = Geo<R1, R2>;
   constexpr int N = Gm::N, G = Gm::G, SC = Gm::GROUPS;
+  const FastItem& a = bt.item[blockIdx.z];
+  if ((int)blockIdx.x * SC >= a.nst || (int)blockIdx.y >= a.nb) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* tw = reinterpret_cast<V*>(smem_raw);
   V* xbuf = tw + N;                       // [SC][N]
@@ -66,7 +76,7 @@ __global__ void __launch_bounds__(256) k_zinv(FastArgs a) {
   const int grp = warp * Gm::LPW + lane / G, t = lane % G;
   const bool in_grp = lane < Gm::LPW * G;
   const int s0 = blockIdx.x * SC, b = blockIdx.y;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twt<V>(a)[i];
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twt<V>(bt)[i];
   __syncthreads();
   const int s = s0 + grp;
   const bool active = in_grp && s < a.nst;
@@ -96,17 +106,19 @@ __global__ void __launch_bounds__(256) k_zinv(FastArgs a) {
 }
 
 template <typename T, int R1, int R2>
-__global__ void __launch_bounds__(256) k_plane(FastArgs a) {
+__global__ void __launch_bounds__(256) k_plane(const __grid_constant__ FastBatch bt) {
   using V = typename Cx<T>::type;
   using Gm = Geo<R1, R2>;
   constexpr int N = Gm::N, G = Gm::G, NG = Gm::GROUPS;
+  const FastItem& a = bt.item[blockIdx.z];
+  if ((int)blockIdx.y * a.bpc >= a.nb) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* tw = reinterpret_cast<V*>(smem_raw);
   V* xbuf = tw + N;                              // [NG][N]
   V* P = xbuf + NG * N;                          // [npl][N]
   V* row = P + (size_t)a.npl * N;                // [nst] if stage_row
-  T* vpl = reinterpret_cast<T*>(row + (a.stage_row ? a.nst : 0));   // [N][N] if stage_v
-  int* xm = reinterpret_cast<int*>(vpl + (a.stage_v ? N * N : 0));  // [N]
+  T* vpl = reinterpret_cast<T*>(row + (bt.stage_row ? a.nst : 0));   // [N][N] if stage_v
+  int* xm = reinterpret_cast<int*>(vpl + (bt.stage_v ? N * N : 0));  // [N]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int grp = warp * Gm::LPW + lane / G, t = lane % G;
   const bool in_grp = lane < Gm::LPW * G;
@@ -114,22 +126,22 @@ __global__ void __launch_bounds__(256) k_plane(FastArgs a) {
   const int j3 = blockIdx.x;
   const T* Vg = reinterpret_cast<const T*>(a.V) + (size_t)j3 * N * N;
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    tw[i] = twt<V>(a)[i];
+    tw[i] = twt<V>(bt)[i];
     xm[i] = a.xmap[i];
   }
-  if (a.stage_v)
+  if (bt.stage_v)
     for (int i = threadIdx.x; i < N * N; i += blockDim.x) vpl[i] = Vg[i];
-  const T* Vp = a.stage_v ? vpl : Vg;
+  const T* Vp = bt.stage_v ? vpl : Vg;
   for (int bi = 0; bi < a.bpc; ++bi) {
     const int b = blockIdx.y * a.bpc + bi;
     if (b >= a.nb) break;
     const V* zin = reinterpret_cast<const V*>(a.Zt) + ((size_t)b * N + j3) * a.nst;
     V* yout = reinterpret_cast<V*>(a.Yb) + ((size_t)b * N + j3) * a.nst;
     __syncthreads();
-    if (a.stage_row)
+    if (bt.stage_row)
       for (int i = threadIdx.x; i < a.nst; i += blockDim.x) row[i] = zin[i];
     __syncthreads();
-    const V* src = a.stage_row ? row : zin;
+    const V* src = bt.stage_row ? row : zin;
     V reg[G];
     // inverse y per m1-plane: inputs at the plane's sticks
     for (int p0 = 0; p0 < a.npl; p0 += NG) {
@@ -178,7 +190,7 @@ __global__ void __launch_bounds__(256) k_plane(FastArgs a) {
     }
     __syncthreads();
     // forward y per m1-plane, keep the sticks
-    V* dst = a.stage_row ? row : yout;
+    V* dst = bt.stage_row ? row : yout;
     for (int p0 = 0; p0 < a.npl; p0 += NG) {
       const int p = p0 + grp;
       const bool act = in_grp && p < a.npl;
@@ -196,7 +208,7 @@ __global__ void __launch_bounds__(256) k_plane(FastArgs a) {
         }
       }
     }
-    if (a.stage_row) {
+    if (bt.stage_row) {
       __syncthreads();
       for (int i = threadIdx.x; i < a.nst; i += blockDim.x) yout[i] = row[i];
     }
@@ -204,10 +216,12 @@ __global__ void __launch_bounds__(256) k_plane(FastArgs a) {
 }
 
 template <typename T, int R1, int R2>
-__global__ void __launch_bounds__(256) k_zfwd(FastArgs a) {
+__global__ void __launch_bounds__(256) k_zfwd(const __grid_constant__ FastBatch bt) {
   using V = typename Cx<T>::type;
   using Gm = Geo<R1, R2>;
   constexpr int N = Gm::N, G = Gm::G, SC = Gm::GROUPS;
+  const FastItem& a = bt.item[blockIdx.z];
+  if ((int)blockIdx.x * SC >= a.nst || (int)blockIdx.y >= a.nb) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* tw = reinterpret_cast<V*>(smem_raw);
   V* xbuf = tw + N;                       // [SC][N]
@@ -218,7 +232,7 @@ __global__ void __launch_bounds__(256) k_zfwd(FastArgs a) {
   const int s0 = blockIdx.x * SC, b = blockIdx.y;
   const int ns = min(SC, a.nst - s0);
   const V* Y = reinterpret_cast<const V*>(a.Yb) + (size_t)b * N * a.nst;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twt<V>(a)[i];
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twt<V>(bt)[i];
   for (int i = threadIdx.x; i < N * SC; i += blockDim.x) {
     const int j3 = i / SC, sl = i - j3 * SC;
     ibuf[i] = sl < ns ? Y[(size_t)j3 * a.nst + s0 + sl] : czero<V>();
@@ -245,7 +259,7 @@ __global__ void __launch_bounds__(256) k_zfwd(FastArgs a) {
         const double2 x = ps[tt];
         const double kg = kin[tt];
         const V v = reg[k2];
-        out[tt] = make_double2(kg * x.x + (double)v.x * a.inv_nr, kg * x.y + (double)v.y * a.inv_nr);
+        out[tt] = make_double2(kg * x.x + (double)v.x * bt.inv_nr, kg * x.y + (double)v.y * bt.inv_nr);
       }
     }
   }
@@ -260,7 +274,8 @@ struct FastKernels {
     return sizeof(V) * (size_t)(Gm::N + Gm::GROUPS * Gm::N + (size_t)p.npl * Gm::N + (sr ? p.nst : 0)) +
            (sv ? sizeof(T) * (size_t)Gm::N * Gm::N : 0) + sizeof(int) * Gm::N;
   }
-  static int run(Context& c, const Problem& p, const FastArgs& a0, int nbnd, int nbb, int sv, int sr) {
+  // One launch of each kernel over every item of the batch (all share the edge N and the flags).
+  static int run(Context& c, FastBatch& bt, size_t max_plane_smem) {
     static bool attr = false;
     if (!attr) {
       const int mx = (int)c.smem_optin;
@@ -269,26 +284,26 @@ struct FastKernels {
       cudaFuncSetAttribute(k_zfwd<T, R1, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
       attr = true;
     }
-    FastArgs a = a0;
-    a.stage_v = sv;
-    a.stage_row = sr;
-    const size_t sz = smem_z(), sp = smem_plane(p, sv, sr);
-    const int zch = (p.nst + Gm::GROUPS - 1) / Gm::GROUPS;
-    for (int b0 = 0; b0 < nbnd; b0 += nbb) {
-      const int nb = std::min(nbb, nbnd - b0);
-      a.nb = nb;
-      a.psi = a0.psi + (size_t)b0 * p.npw;
-      a.hpsi = a0.hpsi + (size_t)b0 * p.npw;
-      // bands per k_plane CTA: amortise the staged V plane while keeping >= 2 waves
-      const int occ = sp <= c.smem_optin / 2 ? 2 : 1;
-      int bpc = std::max(1, (Gm::N * nb) / (2 * c.sm_count * occ));
-      bpc = std::min(bpc, 8);
-      a.bpc = bpc;
-      HPSI_LAUNCH(c, HPSI_K_INV_ZY, (k_zinv<T, R1, R2><<<dim3(zch, nb), 256, sz, c.stream>>>(a)));
-      HPSI_LAUNCH(c, HPSI_K_XVX_Y,
-                  (k_plane<T, R1, R2><<<dim3(Gm::N, (nb + bpc - 1) / bpc), 256, sp, c.stream>>>(a)));
-      HPSI_LAUNCH(c, HPSI_K_FWD_Z, (k_zfwd<T, R1, R2><<<dim3(zch, nb), 256, sz, c.stream>>>(a)));
+    const size_t sz = smem_z();
+    int zch = 1, nbmax = 1, pyb = 1, total_rows = 0;
+    for (int i = 0; i < bt.nitems; ++i) {
+      FastItem& it = bt.item[i];
+      zch = std::max(zch, (it.nst + Gm::GROUPS - 1) / Gm::GROUPS);
+      nbmax = std::max(nbmax, it.nb);
+      total_rows += it.nb;
     }
+    // bands per k_plane CTA: amortise the staged V plane while keeping >= 2 waves over the batch
+    const int occ = max_plane_smem <= c.smem_optin / 2 ? 2 : 1;
+    int bpc = std::max(1, (Gm::N * total_rows) / (2 * c.sm_count * occ));
+    bpc = std::min(bpc, 8);
+    for (int i = 0; i < bt.nitems; ++i) {
+      bt.item[i].bpc = bpc;
+      pyb = std::max(pyb, (bt.item[i].nb + bpc - 1) / bpc);
+    }
+    HPSI_LAUNCH(c, HPSI_K_INV_ZY, (k_zinv<T, R1, R2><<<dim3(zch, nbmax, bt.nitems), 256, sz, c.stream>>>(bt)));
+    HPSI_LAUNCH(c, HPSI_K_XVX_Y,
+                (k_plane<T, R1, R2><<<dim3(Gm::N, pyb, bt.nitems), 256, max_plane_smem, c.stream>>>(bt)));
+    HPSI_LAUNCH(c, HPSI_K_FWD_Z, (k_zfwd<T, R1, R2><<<dim3(zch, nbmax, bt.nitems), 256, sz, c.stream>>>(bt)));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "fast local kernels launch");
     return HPSI_OK;
@@ -345,31 +360,90 @@ int local_fast_plan(const Problem& p, int precision, size_t smem_optin) {
   return flags;
 }
 
+static FastItem make_item(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nb, void* Zt, void* Yb) {
+  FastItem it;
+  it.nb = nb;
+  it.npw = p.npw;
+  it.npl = p.npl;
+  it.nst = p.nst;
+  it.bpc = 1;
+  it.sticks = p.d_sticks;
+  it.ymap = p.d_ymap;
+  it.xmap = p.d_xmap;
+  it.psi = psi;
+  it.hpsi = hpsi;
+  it.kin = p.d_kin;
+  it.Zt = Zt;
+  it.Yb = Yb;
+  it.V = c.precision == HPSI_FP64 ? (const void*)p.d_v64 : (const void*)p.d_v32;
+  return it;
+}
+
+static size_t plane_smem(const Context& c, const Problem& p, int flags) {
+  size_t r = 0;
+  auto f = [&](auto k) { r = decltype(k)::smem_plane(p, flags & 1, (flags >> 1) & 1); };
+  if (c.precision == HPSI_FP64) dispatch_size<double>(p.n[0], f);
+  else dispatch_size<float>(p.n[0], f);
+  return r;
+}
+
+static int run_batch(Context& c, FastBatch& bt, size_t smem) {
+  int rc = HPSI_EINVAL;
+  auto go = [&](auto k) { rc = decltype(k)::run(c, bt, smem); };
+  if (c.precision == HPSI_FP64) dispatch_size<double>(bt.N, go);
+  else dispatch_size<float>(bt.N, go);
+  return rc;
+}
+
+static void batch_header(FastBatch& bt, const Problem& p, int flags) {
+  bt.nitems = 0;
+  bt.N = p.n[0];
+  bt.stage_v = flags & 1;
+  bt.stage_row = (flags >> 1) & 1;
+  bt.tw64 = p.d_ftw64;
+  bt.tw32 = p.d_ftw32;
+  bt.inv_nr = 1.0 / ((double)p.n[0] * p.n[1] * p.n[2]);
+}
+
 int local_fast_apply(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd, void* Zt, void* Yb,
                      int nbb) {
-  const int flags = p.fast_flags;
-  FastArgs a;
-  a.N = p.n[0];
-  a.npw = p.npw;
-  a.npl = p.npl;
-  a.nst = p.nst;
-  a.sticks = p.d_sticks;
-  a.ymap = p.d_ymap;
-  a.xmap = p.d_xmap;
-  a.psi = psi;
-  a.hpsi = hpsi;
-  a.kin = p.d_kin;
-  a.Zt = Zt;
-  a.Yb = Yb;
-  a.V = c.precision == HPSI_FP64 ? (const void*)p.d_v64 : (const void*)p.d_v32;
-  a.tw64 = p.d_ftw64;
-  a.tw32 = p.d_ftw32;
-  a.inv_nr = 1.0 / ((double)p.n[0] * p.n[1] * p.n[2]);
-  int rc = HPSI_EINVAL;
-  auto go = [&](auto k) { rc = decltype(k)::run(c, p, a, nbnd, nbb, flags & 1, (flags >> 1) & 1); };
-  if (c.precision == HPSI_FP64) dispatch_size<double>(p.n[0], go);
-  else dispatch_size<float>(p.n[0], go);
-  return rc;
+  static FastBatch bt;   // host staging of the parameter block (calls are not thread-safe by contract)
+  batch_header(bt, p, p.fast_flags);
+  const size_t smem = plane_smem(c, p, p.fast_flags);
+  for (int b0 = 0; b0 < nbnd; b0 += nbb) {
+    const int nb = std::min(nbb, nbnd - b0);
+    bt.nitems = 1;
+    bt.item[0] = make_item(c, p, psi + (size_t)b0 * p.npw, hpsi + (size_t)b0 * p.npw, nb, Zt, Yb);
+    int rc = run_batch(c, bt, smem);
+    if (rc) return rc;
+  }
+  return HPSI_OK;
+}
+
+// Several problems with the same cubic edge and flags in one launch per kernel; scratch[i] holds
+// item i's Zt and Y (each n3 * nst * nbnd complex values).
+int local_fast_apply_multi(Context& c, int nitem, const int* prob, const int* nbnd, const double2* const* psi,
+                           double2* const* hpsi, void* const* zt, void* const* yb) {
+  static FastBatch bt;
+  int done = 0;
+  while (done < nitem) {
+    const Problem& p0 = c.probs[prob[done]];
+    batch_header(bt, p0, p0.fast_flags);
+    size_t smem = 0;
+    int n = 0;
+    while (done + n < nitem && n < kMaxItems) {
+      const Problem& p = c.probs[prob[done + n]];
+      if (p.n[0] != p0.n[0] || p.fast_flags != p0.fast_flags) break;
+      bt.item[n] = make_item(c, p, psi[done + n], hpsi[done + n], nbnd[done + n], zt[done + n], yb[done + n]);
+      smem = std::max(smem, plane_smem(c, p, p.fast_flags));
+      ++n;
+    }
+    bt.nitems = n;
+    int rc = run_batch(c, bt, smem);
+    if (rc) return rc;
+    done += n;
+  }
+  return HPSI_OK;
 }
 
 }  // namespace hpsi

@@ -1,0 +1,102 @@
+"""Batched H|psi>: many k-points (one cell) and many independent cells in one launch sequence,
+captured in a CUDA graph on the first call and replayed on identical calls."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def _run_batch(ctx, xs):
+    import torch
+    from paper_0906_2569_gb300 import binding as B
+    ys = [torch.full_like(x, float("nan")) for x in xs]
+    B.hpsi_apply_batch(ctx, list(range(len(xs))), xs, ys)
+    B.hpsi_sync(ctx)
+    return [y.cpu().numpy() for y in ys]
+
+
+def _run_each(ctx, xs):
+    import torch
+    from paper_0906_2569_gb300 import binding as B
+    out = []
+    for i, x in enumerate(xs):
+        y = torch.full_like(x, float("nan"))
+        B.hpsi_apply(ctx, i, x, y)
+        out.append(y)
+    B.hpsi_sync(ctx)
+    return [y.cpu().numpy() for y in out]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_kpoints(lib, precision):
+    import torch
+    from paper_0906_2569_gb300 import binding as B
+    p = workloads.config4a()
+    ms = [B.hpsi_gsphere(p.lattice, p.ecut, k) for k in p.kpts]
+    vr = workloads.vloc_r(p.lattice, p.atoms, p.fft)
+    betas = [workloads.beta(p.lattice, p.atoms, k, m) for k, m in zip(p.kpts, ms)]
+    d = workloads.dmat(len(p.atoms))
+    ctx = B.hpsi_setup(p.lattice, p.ecut, p.kpts, p.fft, vr, betas, d, precision,
+                       torch.cuda.current_stream().cuda_stream)
+    xs = [torch.from_numpy(workloads.psi0(p.lattice, k, m, p.nbnd, p.psi_seed + i)).cuda()
+          for i, (k, m) in enumerate(zip(p.kpts, ms))]
+    each = _run_each(ctx, xs)
+    first = _run_batch(ctx, xs)      # eager + capture
+    second = _run_batch(ctx, xs)     # graph replay
+    for i in range(len(xs)):
+        assert np.array_equal(first[i], each[i]) and np.array_equal(second[i], each[i])
+    tol = 1e-12 if precision == 0 else 1e-5
+    for i in (0, 7, 15):
+        ref = oracle.hamiltonian.hpsi(p.lattice, p.kpts[i], ms[i], p.fft, vr, betas[i], d, xs[i].cpu().numpy())
+        assert np.linalg.norm(first[i] - ref) / np.linalg.norm(ref) < tol
+    n, _ = B.hpsi_kernel_stats(ctx, -2)
+    assert n == 3 * 16 * p.nbnd
+
+
+def test_batch_cells(lib):
+    """32 cubic cells with 25^3 ... 50^3 boxes, 1-4 atoms, 8-32 bands (float64)."""
+    import torch
+    from paper_0906_2569_gb300 import binding as B
+    cells = workloads.config4b()
+    ms = [B.hpsi_gsphere(c.lattice, c.ecut, c.kpts[0]) for c in cells]
+    vrs = [workloads.vloc_r(c.lattice, c.atoms, c.fft) for c in cells]
+    betas = [workloads.beta(c.lattice, c.atoms, c.kpts[0], m) for c, m in zip(cells, ms)]
+    ds = [workloads.dmat(len(c.atoms)) for c in cells]
+    ctx = B.hpsi_setup_cells([c.lattice for c in cells], [c.ecut for c in cells], [c.fft for c in cells], vrs,
+                             betas, ds, B.HPSI_FP64, torch.cuda.current_stream().cuda_stream)
+    assert ctx.nprob() == 32
+    xs = [torch.from_numpy(workloads.psi0(c.lattice, c.kpts[0], m, c.nbnd, c.psi_seed)).cuda()
+          for c, m in zip(cells, ms)]
+    each = _run_each(ctx, xs)
+    first = _run_batch(ctx, xs)
+    second = _run_batch(ctx, xs)
+    for i in range(32):
+        assert np.array_equal(first[i], each[i]) and np.array_equal(second[i], each[i])
+    for i in (0, 5, 17, 31):
+        c = cells[i]
+        ref = oracle.hamiltonian.hpsi(c.lattice, c.kpts[0], ms[i], c.fft, vrs[i], betas[i], ds[i], xs[i].cpu().numpy())
+        assert np.linalg.norm(first[i] - ref) / np.linalg.norm(ref) < 1e-12
+
+
+def test_batch_graph_invalidated_by_new_arguments(lib):
+    import torch
+    from paper_0906_2569_gb300 import binding as B
+    p = workloads.config4a()
+    kp = p.kpts[:3]
+    ms = [B.hpsi_gsphere(p.lattice, p.ecut, k) for k in kp]
+    vr = workloads.vloc_r(p.lattice, p.atoms, p.fft)
+    betas = [workloads.beta(p.lattice, p.atoms, k, m) for k, m in zip(kp, ms)]
+    ctx = B.hpsi_setup(p.lattice, p.ecut, kp, p.fft, vr, betas, workloads.dmat(2), B.HPSI_FP64,
+                       torch.cuda.current_stream().cuda_stream)
+    xs = [torch.from_numpy(workloads.random_block(len(m), 5, i)).cuda() for i, m in enumerate(ms)]
+    a = _run_batch(ctx, xs)
+    xs2 = [x[:3].clone() for x in xs]          # new pointers and band counts
+    b = _run_batch(ctx, xs2)
+    c = _run_batch(ctx, xs)                    # back to the first list
+    each = _run_each(ctx, xs)
+    for i in range(3):
+        assert np.array_equal(a[i], each[i]) and np.array_equal(c[i], each[i])
+        assert np.array_equal(b[i], each[i][:3])
