@@ -299,19 +299,32 @@ __global__ void k_split_beta_add(int nproj, int npw, int ka, const double2* __re
   }
 }
 
-// B of calbec: rows b < nb: psi_b (re, im); rows nb + b: (im, -re).
+// B of calbec: rows b < nb: psi_b (re, im); rows nb + b: (im, -re).  One thread per complex psi
+// element (or per pair of padding columns), writing bf16 pairs.
 template <int NT>
 __global__ void k_split_psi(int nb, int npw, int kc, const double2* __restrict__ psi, __nv_bfloat16* __restrict__ out) {
   const size_t plane = (size_t)2 * nb * kc;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < plane; i += (size_t)gridDim.x * blockDim.x) {
-    const int n = (int)(i / kc), k = (int)(i % kc);
-    double x = 0.0;
-    if (k < 2 * npw) {
-      const int b = n < nb ? n : n - nb;
-      const double2 v = psi[(size_t)b * npw + (k >> 1)];
-      x = n < nb ? ((k & 1) ? v.y : v.x) : ((k & 1) ? -v.x : v.y);
+  const int half = kc / 2;   // complex columns including the zero padding
+  const size_t n = (size_t)nb * half;
+  __nv_bfloat162* o2 = reinterpret_cast<__nv_bfloat162*>(out);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(i / half), g = (int)(i - (size_t)b * half);
+    double2 v = make_double2(0.0, 0.0);
+    if (g < npw) v = psi[(size_t)b * npw + g];
+    double r0 = v.x, r1 = v.y;      // row b:      (re, im)
+    double s0 = v.y, s1 = -v.x;     // row nb + b: (im, -re)
+    const size_t i0 = ((size_t)b * kc) / 2 + g, i1 = ((size_t)(nb + b) * kc) / 2 + g;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const __nv_bfloat16 h0 = __float2bfloat16_rn((float)r0), h1 = __float2bfloat16_rn((float)r1);
+      const __nv_bfloat16 k0 = __float2bfloat16_rn((float)s0), k1 = __float2bfloat16_rn((float)s1);
+      o2[t * (plane / 2) + i0] = __halves2bfloat162(h0, h1);
+      o2[t * (plane / 2) + i1] = __halves2bfloat162(k0, k1);
+      r0 -= (double)__bfloat162float(h0);
+      r1 -= (double)__bfloat162float(h1);
+      s0 -= (double)__bfloat162float(k0);
+      s1 -= (double)__bfloat162float(k1);
     }
-    split_store<NT>(x, out, plane, i);
   }
 }
 
@@ -455,7 +468,7 @@ int apply_t(Context& c, const Problem& p, const double2* psi, double2* hpsi, int
   // the K padding of w (columns 2P .. ka) is not written by the D-scale kernel
   cudaError_t e0 = cudaMemsetAsync(wa, 0, wab, c.stream);
   if (e0 != cudaSuccess) return cuda_fail(c, e0, "workspace clear");
-  HPSI_LAUNCH(c, HPSI_K_SPLIT, (k_split_psi<NT><<<4 * c.sm_count, 256, 0, c.stream>>>(nbnd, npw, kc, psi, psi_bf)));
+  HPSI_LAUNCH(c, HPSI_K_SPLIT, (k_split_psi<NT><<<8 * c.sm_count, 256, 0, c.stream>>>(nbnd, npw, kc, psi, psi_bf)));
   rc = launch_gemm<NT>(c, bcal, P, psi_bf, 2 * nbnd, kc, nsplit, ksplit, 0, part, nullptr, 0, HPSI_K_CALBEC);
   if (rc) return rc;
   const int n = P * nbnd;
