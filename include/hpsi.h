@@ -60,8 +60,14 @@ enum hpsi_option {
   HPSI_OPT_KERNEL_TIMING = 3, /* 1: bracket every launch of the library's kernels with CUDA events */
   HPSI_OPT_NL_TERMS = 4,      /* mixed path: bf16 terms per nonlocal operand, 3 (six products,
                                  default) or 2 (three products); re-splits the projectors */
-  HPSI_OPT_LOCAL_PATH = 5     /* 0 (default): register-codelet kernels where the box allows them;
+  HPSI_OPT_LOCAL_PATH = 5,    /* 0 (default): register-codelet kernels where the box allows them;
                                  1: always the generic radix-2/3/4/5 kernels */
+  HPSI_OPT_TC_KSPLIT = 6,     /* mixed path: at most this many 64-wide K steps accumulate in one
+                                 tensor-memory accumulator of <beta|psi> before the partial sums
+                                 are added in float64 (0: chosen for occupancy) */
+  HPSI_OPT_FINAL_FP64 = 7     /* mixed davidson_solve: 1 (default) takes the final Rayleigh
+                                 quotients with one float64 application of H to the Ritz vectors;
+                                 0 with the mixed H */
 };
 
 /* Kernel classes reported by hpsi_kernel_stats. */

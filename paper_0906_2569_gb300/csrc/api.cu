@@ -220,8 +220,8 @@ static int finish_problem(Context& c, Problem& p, const double* vr, int vslot_sh
   int rc = build_geometry(p, err);
   if (rc) return fail(c, rc, err);
   for (int w = 0; w < 3; ++w)
-    if (local_smem_bytes(p, c.precision, w) > c.smem_optin)
-      return fail(c, HPSI_EINVAL, "FFT box / sphere too large for one CTA's shared memory at this precision");
+    if (local_smem_bytes(p, HPSI_FP64, w) > c.smem_optin)
+      return fail(c, HPSI_EINVAL, "FFT box / sphere too large for one CTA's shared memory");
   for (int a = 0; a < 3; ++a) {
     rc = plan_for(c, p.n[a], &p.plan[a]);
     if (rc) return rc;
@@ -242,7 +242,7 @@ static int finish_problem(Context& c, Problem& p, const double* vr, int vslot_sh
         p.d_ftw64 = t.nat64;
         p.d_ftw32 = t.nat32;
       }
-    p.fast_flags = local_fast_plan(p, c.precision, c.smem_optin);
+    for (int pr = 0; pr < 2; ++pr) p.fflags[pr] = local_fast_plan(p, pr, c.smem_optin);
   }
   if ((rc = upload(c, &p.d_planes, p.planes.data(), p.planes.size()))) return rc;
   if ((rc = upload(c, &p.d_kin, p.kin.data(), p.kin.size()))) return rc;
@@ -294,13 +294,14 @@ static int finish_problem(Context& c, Problem& p, const double* vr, int vslot_sh
                                                                   p.d_col, p.d_dval, p.d_hdiag)));
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(c, e, "hdiag kernel");
-  // band block of the local kernels: keep the X intermediate of one block near 48 MB (L2-resident)
-  const size_t cs = c.precision == HPSI_FP64 ? 16 : 8;
-  const size_t xper = cs * (size_t)p.n[2] * p.npl * p.n[1];
-  p.nbb = (int)std::max<size_t>(1, std::min<size_t>(4096, (size_t)(48u << 20) / std::max<size_t>(1, xper)));
-  // fast path: the stick rows Zt and Y of one block (about 48 MB) stay L2-resident
-  const size_t zper = 2 * cs * (size_t)p.n[2] * p.nst;
-  p.nbb_fast = (int)std::max<size_t>(1, std::min<size_t>(4096, (size_t)(48u << 20) / std::max<size_t>(1, zper)));
+  // band blocks of the local kernels: one block's intermediates stay near 48 MB (L2-resident)
+  for (int pr = 0; pr < 2; ++pr) {
+    const size_t cs = pr == HPSI_FP64 ? 16 : 8;
+    const size_t xper = cs * (size_t)p.n[2] * p.npl * p.n[1];
+    p.nbb[pr] = (int)std::max<size_t>(1, std::min<size_t>(4096, (size_t)(48u << 20) / std::max<size_t>(1, xper)));
+    const size_t zper = 2 * cs * (size_t)p.n[2] * p.nst;
+    p.nbbf[pr] = (int)std::max<size_t>(1, std::min<size_t>(4096, (size_t)(48u << 20) / std::max<size_t>(1, zper)));
+  }
   if (c.precision == HPSI_MIXED && P > 0) {
     rc = mixed_prepare_beta(c, p);
     if (rc) return rc;
@@ -352,7 +353,7 @@ static void free_context(Context& c) {
 }
 
 int nonlocal_apply(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd) {
-  if (c.precision == HPSI_FP64) return nonlocal_apply_fp64(c, p, psi, hpsi, nbnd);
+  if (cur_prec(c) == HPSI_FP64) return nonlocal_apply_fp64(c, p, psi, hpsi, nbnd);
   return nonlocal_apply_mixed(c, p, psi, hpsi, nbnd);
 }
 
@@ -373,15 +374,15 @@ int batch_apply(Context& c, int nitem, const int* prob, const int* nbnd, const d
   for (int i = 0; i < nitem; ++i) {
     if (nbnd[i] == 0) continue;
     const Problem& p = c.probs[prob[i]];
-    if ((p.fast_flags & 4) && !c.force_generic) fast.push_back(i);
+    if ((p.fflags[cur_prec(c)] & 4) && !c.force_generic) fast.push_back(i);
     else slow.push_back(i);
   }
   std::stable_sort(fast.begin(), fast.end(), [&](int x, int y) {
     const Problem& a = c.probs[prob[x]];
     const Problem& b = c.probs[prob[y]];
-    return a.n[0] != b.n[0] ? a.n[0] < b.n[0] : a.fast_flags < b.fast_flags;
+    return a.n[0] != b.n[0] ? a.n[0] < b.n[0] : a.fflags[cur_prec(c)] < b.fflags[cur_prec(c)];
   });
-  const size_t cs = c.precision == HPSI_FP64 ? sizeof(double2) : sizeof(float2);
+  const size_t cs = cur_prec(c) == HPSI_FP64 ? sizeof(double2) : sizeof(float2);
   std::vector<size_t> off(fast.size());
   size_t total = 0;
   for (size_t j = 0; j < fast.size(); ++j) {
@@ -787,6 +788,16 @@ extern "C" int hpsi_set_option(hpsi_ctx* ctx, int option, double value) {
         if (rc) return rc;
       }
     }
+    return HPSI_OK;
+  }
+  if (option == HPSI_OPT_FINAL_FP64) {
+    if (value != 0.0 && value != 1.0) return fail(c, HPSI_EINVAL, "HPSI_OPT_FINAL_FP64 must be 0 or 1");
+    c.final_fp64 = (int)value;
+    return HPSI_OK;
+  }
+  if (option == HPSI_OPT_TC_KSPLIT) {
+    if (!(value >= 0.0) || value > 1e6) return fail(c, HPSI_EINVAL, "HPSI_OPT_TC_KSPLIT must be >= 0");
+    c.tc_kmax = (int)value;
     return HPSI_OK;
   }
   if (option == HPSI_OPT_LOCAL_PATH) {

@@ -8,9 +8,9 @@
 //   reduced problem sum_k (H_jk - eps S_jk) c_k = 0, psi_i <- sum_j c^(i)_j phi_j
 //
 // The basis is kept orthonormal: every block of corrections (each scaled to unit norm) is
-// projected out of the basis twice (block Gram-Schmidt) and orthonormalised through the
-// eigen-decomposition of its own overlap matrix, dropping directions whose overlap eigenvalue
-// is below 1e-8.  A correction that loses all but 1e-3 of its norm to the projection lies in the
+// projected out of the basis twice (block Gram-Schmidt) and orthonormalised by Cholesky QR of its
+// own overlap (float64 factor) when every squared pivot exceeds 1e-6, otherwise through the
+// eigen-decomposition of the overlap, dropping directions whose overlap eigenvalue is below 1e-8.  A correction that loses all but 1e-3 of its norm to the projection lies in the
 // basis up to rounding (this is what an exact diagonal D does: for a diagonal H, D g_i is
 // parallel to psi_i); it is replaced by its raw residual g_i, which the Galerkin condition makes
 // orthogonal to the basis.  S_jk is then the identity and the reduced problem is solved as a
@@ -18,8 +18,9 @@
 //
 // Mixed precision (HPSI_MIXED): the reduced basis and its products are complex64 (cuBLAS CGEMM);
 // the small eigenproblems, the residual norms and the final eigenvalues are float64 -- at exit H
-// is applied once more to the Ritz vectors and eps_i = <psi_i|H psi_i> / <psi_i|psi_i> is summed
-// in float64, whose error is second order in the eigenvector error.
+// is applied once more to the Ritz vectors, with the float64 operator unless HPSI_OPT_FINAL_FP64
+// is 0, and eps_i = <psi_i|H psi_i> / <psi_i|psi_i> is summed in float64: the eigenvalue error
+// is then second order in the eigenvector error left by the mixed iterations.
 //
 // The eps in D is eps_i per band by default (D approximates (H - eps_i S)^-1); option
 // HPSI_OPT_PRECOND_SHIFT = 1 takes one eps for all bands, the highest Ritz value of the block
@@ -290,11 +291,17 @@ static int alloc_work(Context& c, DavHandles& h, int npw, int nbnd, bool mixed) 
     free_work(w);
     return fail(c, HPSI_ENOMEM, "davidson_solve: device allocation of the reduced basis failed");
   }
-  int lw = 0;
+  int lw = 0, lw2 = 0, lw3 = 0, meig = 0;
   BCK(cusolverDnZheevd_bufferSize(h.solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, mmax, Z(w.evec), mmax,
                                   w.w, &lw),
       "cusolverDnZheevd_bufferSize");
-  w.lwork = lw;
+  BCK(cusolverDnZheevdx_bufferSize(h.solver, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I, CUBLAS_FILL_MODE_UPPER,
+                                   mmax, Z(w.evec), mmax, 0.0, 0.0, 1, nbnd, &meig, w.w, &lw2),
+      "cusolverDnZheevdx_bufferSize");
+  BCK(cusolverDnZpotrf_bufferSize(h.solver, CUBLAS_FILL_MODE_UPPER, nbnd, Z(w.ovl), nbnd, &lw3),
+      "cusolverDnZpotrf_bufferSize");
+  w.lwork = std::max(lw, std::max(lw2, lw3));
+  lw = w.lwork;
   if (!al((void**)&w.work, sizeof(double2) * (size_t)std::max(lw, 1))) {
     free_work(w);
     return fail(c, HPSI_ENOMEM, "davidson_solve: workspace allocation failed");
@@ -316,6 +323,52 @@ static int small_eigh(Context& c, DavHandles& h, const double2* a, int lda, int 
   return HPSI_OK;
 }
 
+// Lowest nwant eigenpairs of the leading n x n block of a (ld): values in w.w, vectors in the first
+// nwant columns of w.evec (ld n).
+static int lowest_eigh(Context& c, DavHandles& h, const double2* a, int lda, int n, int nwant) {
+  DavWork& w = h.wk;
+  HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_copy_matrix<<<(n * n + 255) / 256, 256, 0, c.stream>>>(n, n, a, lda, w.evec, n)));
+  int meig = 0;
+  BCK(cusolverDnZheevdx(h.solver, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I, CUBLAS_FILL_MODE_UPPER, n,
+                        Z(w.evec), n, 0.0, 0.0, 1, nwant, &meig, w.w, Z(w.work), w.lwork, w.info),
+      "cusolverDnZheevdx");
+  int info = 0;
+  DCK(cudaMemcpyAsync(&info, w.info, sizeof(int), cudaMemcpyDeviceToHost, c.stream), "davidson info copy");
+  DCK(cudaStreamSynchronize(c.stream), "davidson eigensolve");
+  if (info != 0 || meig < nwant)
+    return fail(c, HPSI_ESINGULAR, "zheevdx of the reduced matrix failed, info " + std::to_string(info));
+  return HPSI_OK;
+}
+
+// |U_ii|^2 of an n x n upper factor (ld n) into out[n]
+__global__ void k_diag2(int n, const double2* __restrict__ u, double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = u[(size_t)i * n + i].x * u[(size_t)i * n + i].x + u[(size_t)i * n + i].y * u[(size_t)i * n + i].y;
+}
+
+// Cholesky of the float64 overlap in w.ovl (n x n, ld n): true if it succeeded with every |U_ii|^2
+// above thr (relative to the largest when relative), i.e. the block is safely independent.
+static int chol_overlap(Context& c, DavHandles& h, int n, double thr, bool relative, bool* ok) {
+  DavWork& w = h.wk;
+  *ok = false;
+  BCK(cusolverDnZpotrf(h.solver, CUBLAS_FILL_MODE_UPPER, n, Z(w.ovl), n, Z(w.work), w.lwork, w.info),
+      "cusolverDnZpotrf");
+  HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_diag2<<<(n + 255) / 256, 256, 0, c.stream>>>(n, w.ovl, w.cn2)));
+  int info = 0;
+  std::vector<double> dg(n);
+  DCK(cudaMemcpyAsync(&info, w.info, sizeof(int), cudaMemcpyDeviceToHost, c.stream), "potrf info copy");
+  DCK(cudaMemcpyAsync(dg.data(), w.cn2, sizeof(double) * n, cudaMemcpyDeviceToHost, c.stream), "potrf diag copy");
+  DCK(cudaStreamSynchronize(c.stream), "potrf");
+  if (info != 0) return HPSI_OK;
+  double mx = 0.0, mn = 1e300;
+  for (double v : dg) {
+    mx = std::max(mx, v);
+    mn = std::min(mn, v);
+  }
+  *ok = mn > (relative ? thr * mx : thr);
+  return HPSI_OK;
+}
+
 // Orthonormalise the block x[0:n] (band-major, npw) against itself: overlap S = x^H x, S = V L V^H,
 // x <- x V_keep L_keep^{-1/2}, keeping directions with L > thr (thr relative to max(L) when
 // relative is set).  The result (nkeep vectors) goes to out, which must not overlap x.
@@ -323,6 +376,20 @@ static int canonical_orth(Context& c, DavHandles& h, const double2* x, int n, do
                           bool relative) {
   DavWork& w = h.wk;
   const int npw = w.npw;
+  // Cholesky QR when the block is well conditioned: x <- x U^-1 with S = U^H U
+  BCK(cublasZgemm(h.blas, CUBLAS_OP_C, CUBLAS_OP_N, n, n, npw, &kOne, Z(x), npw, Z(x), npw, &kZero, Z(w.ovl), n),
+      "zgemm overlap");
+  bool chol_ok = false;
+  int rc0 = chol_overlap(c, h, n, relative ? 1e-10 : 1e-6, relative, &chol_ok);
+  if (rc0) return rc0;
+  if (chol_ok) {
+    DCK(cudaMemcpyAsync(out, x, sizeof(double2) * (size_t)n * npw, cudaMemcpyDeviceToDevice, c.stream), "copy");
+    BCK(cublasZtrsm(h.blas, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT, npw, n,
+                    &kOne, Z(w.ovl), n, Z(out), npw),
+        "ztrsm");
+    *nkeep = n;
+    return HPSI_OK;
+  }
   BCK(cublasZgemm(h.blas, CUBLAS_OP_C, CUBLAS_OP_N, n, n, npw, &kOne, Z(x), npw, Z(x), npw, &kZero, Z(w.ovl), n),
       "zgemm overlap");
   // evec / w receive the decomposition of the overlap (the Ritz vectors were formed already)
@@ -382,7 +449,7 @@ int davidson_run(Context& c, int ik, int nbnd, double tol, int maxiter, double2*
   int it = 0;
   bool converged = false;
   for (;;) {
-    rc = small_eigh(c, *h, w.hsub, mmax, m);
+    rc = lowest_eigh(c, *h, w.hsub, mmax, m, N);
     if (rc) return rc;
     // Ritz vectors psi = phi C[:, 0:N], hpsi = hphi C[:, 0:N]
     BCK(cublasZgemm(h->blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, N, m, &kOne, Z(w.phi), npw, Z(w.evec), m, &kZero,
@@ -667,7 +734,24 @@ static int canonical_orth32(Context& c, DavHandles& h, const float2* x, int n, f
       "cgemm overlap");
   HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
               (k_mat_32_to_64<<<(n * n + 255) / 256, 256, 0, c.stream>>>(n, n, w.ovl32, n, w.ovl, n)));
-  int rc = small_eigh(c, h, w.ovl, n, n);
+  // Cholesky QR (float64 factor of the overlap) when the block is well conditioned enough for a
+  // float32 triangular solve (condition number of the factor below about 10)
+  bool chol_ok = false;
+  int rc = chol_overlap(c, h, n, relative ? 1e-6 : 1e-2, relative, &chol_ok);
+  if (rc) return rc;
+  if (chol_ok) {
+    HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
+                (k_mat_64_to_32<<<(n * n + 255) / 256, 256, 0, c.stream>>>(n, n, w.ovl, n, w.ovl32, n)));
+    DCK(cudaMemcpyAsync(out, x, sizeof(float2) * (size_t)n * npw, cudaMemcpyDeviceToDevice, c.stream), "copy");
+    BCK(cublasCtrsm(h.blas, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT, npw, n,
+                    &cOne, Cf(w.ovl32), n, Cf(out), npw),
+        "ctrsm");
+    *nkeep = n;
+    return HPSI_OK;
+  }
+  HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
+              (k_mat_32_to_64<<<(n * n + 255) / 256, 256, 0, c.stream>>>(n, n, w.ovl32, n, w.ovl, n)));
+  rc = small_eigh(c, h, w.ovl, n, n);
   if (rc) return rc;
   std::vector<double> lam(n);
   DCK(cudaMemcpyAsync(lam.data(), w.w, sizeof(double) * n, cudaMemcpyDeviceToHost, c.stream), "overlap eigenvalues");
@@ -724,7 +808,7 @@ static int davidson_run_mixed(Context& c, DavHandles& h, int ik, int nbnd, doubl
   int it = 0;
   bool converged = false;
   for (;;) {
-    rc = small_eigh(c, h, w.hsub, mmax, m);
+    rc = lowest_eigh(c, h, w.hsub, mmax, m, N);
     if (rc) return rc;
     HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
                 (k_mat_64_to_32<<<(m * N + 255) / 256, 256, 0, c.stream>>>(m, N, w.evec, m, w.small32, m)));
@@ -795,10 +879,13 @@ static int davidson_run_mixed(Context& c, DavHandles& h, int ik, int nbnd, doubl
     if (rc) return rc;
     m += nkeep;
   }
-  // float64 Rayleigh quotients of the Ritz vectors with a fresh H|psi>
+  // float64 Rayleigh quotients of the Ritz vectors with a fresh H|psi>, by default with the
+  // float64 operator: the eigenvalue error is then second order in the eigenvector error
   const size_t n = (size_t)N * npw;
   HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_cvt_32_64<<<grid_of(n), 256, 0, c.stream>>>(n, w.psi32, w.in64)));
+  if (c.final_fp64) c.prec_override = HPSI_FP64;
   rc = apply_device(c, ik, w.in64, w.out64, N);
+  c.prec_override = -1;
   if (rc) return rc;
   HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_rayleigh<<<N, 256, 0, c.stream>>>(npw, w.in64, w.out64, w.eps, w.rnorm)));
   DCK(cudaMemcpyAsync(ev.data(), w.eps, sizeof(double) * N, cudaMemcpyDeviceToHost, c.stream), "eig copy");

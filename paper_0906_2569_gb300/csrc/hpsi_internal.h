@@ -66,10 +66,10 @@ struct Problem {
   int nnz = 0;
   uint16_t* d_beta_bf = nullptr;   // mixed path only
   FftPlan plan[3];
-  int nbb = 1;                     // band block of the local-potential kernels
-  // fast path (cubic boxes with register codelets, local_fast.cu)
-  int fast_flags = 0;              // bit 2: enabled; bit 0: stage V; bit 1: stage the stick row
-  int nbb_fast = 1;
+  // per precision (index HPSI_FP64 / HPSI_MIXED): band blocks and the fast-path plan
+  int nbb[2] = {1, 1};             // band block of the generic local kernels
+  int fflags[2] = {0, 0};          // fast path: bit 2 enabled, bit 0 stage V, bit 1 stage the stick row
+  int nbbf[2] = {1, 1};            // band block of the fast local kernels
   int* d_ymap = nullptr;           // [npl][n2]: stick of (plane, j2) or -1
   int* d_xmap = nullptr;           // [n1]: plane of ix or -1
   const double2* d_ftw64 = nullptr;   // e^{-2 pi i j / n}, j < n (owned by the twiddle table)
@@ -123,6 +123,9 @@ struct Context {
   int* d_err = nullptr;                // device error word raised by bounded waits
   int nl_terms = 3;                    // mixed path: bf16 terms per operand (2 or 3)
   int force_generic = 0;               // 1: local part on the generic FFT kernels
+  int tc_kmax = 0;                     // mixed calbec: max 64-wide K-steps per split (0: automatic)
+  int prec_override = -1;              // >= 0: apply H at this precision instead of `precision`
+  int final_fp64 = 1;                  // mixed davidson_solve: final Rayleigh quotients with the float64 H
   cudaStream_t cap_stream = nullptr;   // internal stream for graph capture
   GraphCache graph;
   // launch accounting (always) and per-launch event timing (HPSI_OPT_KERNEL_TIMING)
@@ -133,6 +136,9 @@ struct Context {
   std::vector<cudaEvent_t> evpool;
   double tacc[HPSI_K_COUNT] = {0.0};
 };
+
+// Precision at which H is applied right now.
+inline int cur_prec(const Context& c) { return c.prec_override >= 0 ? c.prec_override : c.precision; }
 
 // Bracket one launch: call before (returns a record slot or -1) and after the launch.
 int launch_begin(Context& c, int kernel);

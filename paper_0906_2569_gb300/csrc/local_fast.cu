@@ -375,14 +375,14 @@ static FastItem make_item(Context& c, const Problem& p, const double2* psi, doub
   it.kin = p.d_kin;
   it.Zt = Zt;
   it.Yb = Yb;
-  it.V = c.precision == HPSI_FP64 ? (const void*)p.d_v64 : (const void*)p.d_v32;
+  it.V = cur_prec(c) == HPSI_FP64 ? (const void*)p.d_v64 : (const void*)p.d_v32;
   return it;
 }
 
 static size_t plane_smem(const Context& c, const Problem& p, int flags) {
   size_t r = 0;
   auto f = [&](auto k) { r = decltype(k)::smem_plane(p, flags & 1, (flags >> 1) & 1); };
-  if (c.precision == HPSI_FP64) dispatch_size<double>(p.n[0], f);
+  if (cur_prec(c) == HPSI_FP64) dispatch_size<double>(p.n[0], f);
   else dispatch_size<float>(p.n[0], f);
   return r;
 }
@@ -390,7 +390,7 @@ static size_t plane_smem(const Context& c, const Problem& p, int flags) {
 static int run_batch(Context& c, FastBatch& bt, size_t smem) {
   int rc = HPSI_EINVAL;
   auto go = [&](auto k) { rc = decltype(k)::run(c, bt, smem); };
-  if (c.precision == HPSI_FP64) dispatch_size<double>(bt.N, go);
+  if (cur_prec(c) == HPSI_FP64) dispatch_size<double>(bt.N, go);
   else dispatch_size<float>(bt.N, go);
   return rc;
 }
@@ -408,8 +408,9 @@ static void batch_header(FastBatch& bt, const Problem& p, int flags) {
 int local_fast_apply(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd, void* Zt, void* Yb,
                      int nbb) {
   static FastBatch bt;   // host staging of the parameter block (calls are not thread-safe by contract)
-  batch_header(bt, p, p.fast_flags);
-  const size_t smem = plane_smem(c, p, p.fast_flags);
+  const int fl = p.fflags[cur_prec(c)];
+  batch_header(bt, p, fl);
+  const size_t smem = plane_smem(c, p, fl);
   for (int b0 = 0; b0 < nbnd; b0 += nbb) {
     const int nb = std::min(nbb, nbnd - b0);
     bt.nitems = 1;
@@ -428,14 +429,15 @@ int local_fast_apply_multi(Context& c, int nitem, const int* prob, const int* nb
   int done = 0;
   while (done < nitem) {
     const Problem& p0 = c.probs[prob[done]];
-    batch_header(bt, p0, p0.fast_flags);
+    const int pr = cur_prec(c);
+    batch_header(bt, p0, p0.fflags[pr]);
     size_t smem = 0;
     int n = 0;
     while (done + n < nitem && n < kMaxItems) {
       const Problem& p = c.probs[prob[done + n]];
-      if (p.n[0] != p0.n[0] || p.fast_flags != p0.fast_flags) break;
+      if (p.n[0] != p0.n[0] || p.fflags[pr] != p0.fflags[pr]) break;
       bt.item[n] = make_item(c, p, psi[done + n], hpsi[done + n], nbnd[done + n], zt[done + n], yb[done + n]);
-      smem = std::max(smem, plane_smem(c, p, p.fast_flags));
+      smem = std::max(smem, plane_smem(c, p, p.fflags[pr]));
       ++n;
     }
     bt.nitems = n;

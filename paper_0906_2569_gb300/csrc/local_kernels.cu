@@ -170,8 +170,8 @@ size_t local_smem_bytes(const Problem& p, int precision, int which) {
 template <typename T>
 static int local_apply_t(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd) {
   const size_t cs = sizeof(typename Cx<T>::type);
-  if ((p.fast_flags & 4) && !c.force_generic) {
-    const int nbf = std::max(1, std::min(p.nbb_fast, nbnd));
+  if ((p.fflags[cur_prec(c)] & 4) && !c.force_generic) {
+    const int nbf = std::max(1, std::min(p.nbbf[cur_prec(c)], nbnd));
     const size_t zneed = cs * (size_t)nbf * p.n[2] * p.nst;
     int rc = ensure_buffer(c, &c.ws.X, &c.ws.xbytes, zneed);
     if (rc) return rc;
@@ -179,15 +179,15 @@ static int local_apply_t(Context& c, const Problem& p, const double2* psi, doubl
     if (rc) return rc;
     return local_fast_apply(c, p, psi, hpsi, nbnd, c.ws.X, c.ws.Y, nbf);
   }
-  const int nbb = std::max(1, std::min(p.nbb, nbnd));
+  const int nbb = std::max(1, std::min(p.nbb[cur_prec(c)], nbnd));
   const size_t xneed = cs * (size_t)nbb * p.n[2] * p.npl * p.n[1];
   const size_t yneed = cs * (size_t)nbb * p.n[2] * p.nst;
   int rc = ensure_buffer(c, &c.ws.X, &c.ws.xbytes, xneed);
   if (rc) return rc;
   rc = ensure_buffer(c, &c.ws.Y, &c.ws.ybytes, yneed);
   if (rc) return rc;
-  const size_t s0 = local_smem_bytes(p, c.precision, 0), s1 = local_smem_bytes(p, c.precision, 1),
-               s2 = local_smem_bytes(p, c.precision, 2);
+  const size_t s0 = local_smem_bytes(p, cur_prec(c), 0), s1 = local_smem_bytes(p, cur_prec(c), 1),
+               s2 = local_smem_bytes(p, cur_prec(c), 2);
   static bool attr_done[2] = {false, false};
   const int slot = sizeof(T) == 8 ? 0 : 1;
   if (!attr_done[slot]) {
@@ -220,7 +220,7 @@ static int local_apply_t(Context& c, const Problem& p, const double2* psi, doubl
 }
 
 int local_apply(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd) {
-  if (c.precision == HPSI_FP64) return local_apply_t<double>(c, p, psi, hpsi, nbnd);
+  if (cur_prec(c) == HPSI_FP64) return local_apply_t<double>(c, p, psi, hpsi, nbnd);
   return local_apply_t<float>(c, p, psi, hpsi, nbnd);
 }
 
@@ -238,8 +238,8 @@ static int local_apply_into_t(Context& c, const Problem& p, const double2* psi, 
   cudaFuncSetAttribute(k_inv_zy<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_xvx_y<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_fwd_z<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  const size_t s0 = local_smem_bytes(p, c.precision, 0), s1 = local_smem_bytes(p, c.precision, 1),
-               s2 = local_smem_bytes(p, c.precision, 2);
+  const size_t s0 = local_smem_bytes(p, cur_prec(c), 0), s1 = local_smem_bytes(p, cur_prec(c), 1),
+               s2 = local_smem_bytes(p, cur_prec(c), 2);
   LocalArgs a;
   a.n1 = p.n[0]; a.n2 = p.n[1]; a.n3 = p.n[2];
   a.npw = p.npw; a.npl = p.npl; a.nst = p.nst; a.ns_max = p.ns_max;
@@ -264,7 +264,7 @@ static int local_apply_into_t(Context& c, const Problem& p, const double2* psi, 
 
 int local_apply_into(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd, void* X, void* Y,
                      int nbb) {
-  if (c.precision == HPSI_FP64) return local_apply_into_t<double>(c, p, psi, hpsi, nbnd, X, Y, nbb);
+  if (cur_prec(c) == HPSI_FP64) return local_apply_into_t<double>(c, p, psi, hpsi, nbnd, X, Y, nbb);
   return local_apply_into_t<float>(c, p, psi, hpsi, nbnd, X, Y, nbb);
 }
 

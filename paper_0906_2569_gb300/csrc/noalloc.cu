@@ -75,13 +75,13 @@ extern "C" int hpsi_apply_noalloc(hpsi_ctx* ctx, int ik, const void* psi_in, voi
   int rc = scratch_address(c, &base);
   if (rc) return rc;
   // largest band chunk whose X, Y and nonlocal partials fit the array
-  const size_t per_band = hpsi::local_scratch_per_band(p, c.precision);
+  const size_t per_band = hpsi::local_scratch_per_band(p, hpsi::cur_prec(c));
   int chunk = 0;
   for (int nb = std::min(nbnd, 4096); nb >= 1; nb = nb > 64 ? nb - 32 : nb - 1) {
     int ns = 0, kc = 0;
     size_t nl = 0;
     hpsi::nonlocal_fp64_plan(c, p, nb, &ns, &kc, &nl);
-    const size_t cs = c.precision == HPSI_FP64 ? sizeof(double2) : sizeof(float2);
+    const size_t cs = hpsi::cur_prec(c) == HPSI_FP64 ? sizeof(double2) : sizeof(float2);
     const size_t xb = align256(cs * (size_t)nb * p.n[2] * p.npl * p.n[1]);
     const size_t yb = align256(cs * (size_t)nb * p.n[2] * p.nst);
     if (xb + yb + align256(p.nproj ? nl : 0) <= kNoAllocBytes) {
@@ -93,7 +93,7 @@ extern "C" int hpsi_apply_noalloc(hpsi_ctx* ctx, int ik, const void* psi_in, voi
     return hpsi::fail(c, HPSI_EINVAL,
                       "hpsi_apply_noalloc: one band needs " + std::to_string(per_band) +
                           " bytes of intermediates, more than the fixed 64 MiB array; use hpsi_apply");
-  const size_t cs = c.precision == HPSI_FP64 ? sizeof(double2) : sizeof(float2);
+  const size_t cs = hpsi::cur_prec(c) == HPSI_FP64 ? sizeof(double2) : sizeof(float2);
   unsigned char* s = static_cast<unsigned char*>(base);
   void* X = s;
   void* Y = s + align256(cs * (size_t)chunk * p.n[2] * p.npl * p.n[1]);

@@ -452,7 +452,8 @@ int apply_t(Context& c, const Problem& p, const double2* psi, double2* hpsi, int
   const int nks = kc / TBK;
   const int tiles = ((2 * nbnd + TBN - 1) / TBN) * ((P + TBM - 1) / TBM);
   int nsplit = std::max(1, std::min(nks, (2 * c.sm_count + tiles - 1) / tiles));
-  const int ksplit = (nks + nsplit - 1) / nsplit;
+  int ksplit = (nks + nsplit - 1) / nsplit;
+  if (c.tc_kmax > 0) ksplit = std::min(ksplit, c.tc_kmax);
   nsplit = (nks + ksplit - 1) / ksplit;
   const size_t psib = sizeof(__nv_bfloat16) * (size_t)NT * 2 * nbnd * kc;
   const size_t partb = sizeof(float) * (size_t)nsplit * P * 2 * nbnd;
