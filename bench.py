@@ -367,6 +367,7 @@ def run_gpu(args):
                       "h2d_bytes_per_step": mixed["e2e_bytes"], "d2h_bytes_per_step": mixed["e2e_bytes"] + 8 * p.nbnd}
     if not args.no_batch:
         out["batched"] = batch_throughput(args, B, torch, flush)
+        out["hpsi_apply_by_config"] = config_throughput(B, torch, flush)
     if not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(p)
     print(json.dumps(out), flush=True)
@@ -421,6 +422,42 @@ def batch_throughput(args, B, torch, flush):
                                                 "ms_per_batch": statistics.median(ms_), "items": len(xs),
                                                 "bands": bands}
             ctx.close()
+    return out
+
+
+def config_throughput(B, torch, flush, names=("c1", "c2", "c5")):
+    """Steady-state hpsi_apply (whole band block, CUDA events, L2 flushed) per configuration."""
+    import workloads
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name in names:
+        p = workloads.CONFIGS[name]()
+        k = p.kpts[0]
+        m = B.hpsi_gsphere(p.lattice, p.ecut, k)
+        vr = workloads.vloc_r(p.lattice, p.atoms, p.fft)
+        beta = workloads.beta(p.lattice, p.atoms, k, m)
+        x = torch.from_numpy(workloads.psi0(p.lattice, k, m, p.nbnd, p.psi_seed)).cuda()
+        y = torch.empty_like(x)
+        res = {"npw": len(m), "nbnd": p.nbnd, "box": p.fft[0], "nproj": p.nproj}
+        for prec, pname in ((B.HPSI_FP64, "fp64"), (B.HPSI_MIXED, "mixed")):
+            ctx = B.hpsi_setup(p.lattice, p.ecut, [k], p.fft, vr, [beta], workloads.dmat(len(p.atoms)), prec,
+                               stream.cuda_stream)
+            for _ in range(2):
+                B.hpsi_apply(ctx, 0, x, y)
+            ms_ = []
+            for _ in range(3 if name == "c5" else 5):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                B.hpsi_apply(ctx, 0, x, y)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms_.append(e0.elapsed_time(e1))
+            res[pname] = {"band_apps_per_s": p.nbnd / (statistics.median(ms_) / 1e3), "ms": statistics.median(ms_)}
+            ctx.close()
+        out[name] = res
+        del x, y
+        torch.cuda.empty_cache()
     return out
 
 

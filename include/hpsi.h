@@ -65,9 +65,11 @@ enum hpsi_option {
   HPSI_OPT_TC_KSPLIT = 6,     /* mixed path: at most this many 64-wide K steps accumulate in one
                                  tensor-memory accumulator of <beta|psi> before the partial sums
                                  are added in float64 (0: chosen for occupancy) */
-  HPSI_OPT_FINAL_FP64 = 7     /* mixed davidson_solve: 1 (default) takes the final Rayleigh
+  HPSI_OPT_FINAL_FP64 = 7,    /* mixed davidson_solve: 1 (default) takes the final Rayleigh
                                  quotients with one float64 application of H to the Ritz vectors;
                                  0 with the mixed H */
+  HPSI_OPT_BASIS = 8          /* davidson_solve: the reduced basis grows to this many times N
+                                 vectors (2: the basic 2N form, 3 or 4 (default)) before a restart */
 };
 
 /* Kernel classes reported by hpsi_kernel_stats. */
@@ -195,7 +197,7 @@ HPSI_API int hpsi_apply_batch(hpsi_ctx* ctx, int nitem, const int* prob, const i
 /*
  * davidson_solve -- lowest nbnd eigenpairs of H for problem ik by block Davidson with the
  * diagonal preconditioner (App. A.2.1).
- *   nbnd         in   number of bands N (1 <= N <= npw/4)
+ *   nbnd         in   number of bands N (1 <= N, and N * basis factor <= npw; factor 4 by default)
  *   tol          in   convergence when max_i ||H psi_i - eps_i psi_i||_2 <= tol
  *   maxiter      in   iteration limit (>= 1)
  *   psi_inout    in/out complex128 [N][npw(ik)], device or host: initial guess in (need not be
@@ -207,7 +209,10 @@ HPSI_API int hpsi_apply_batch(hpsi_ctx* ctx, int nitem, const int* prob, const i
  * norms; corrections D g_i with <k+G|D|k+G> = 1/(<k+G|H|k+G> - eps_i) (denominator kept at
  * |.| >= 0.1 Ha); orthogonalise them against the reduced basis and add them; H_jk, S_jk of the
  * reduced basis; solve (H - eps S) c = 0 in float64; psi_i <- sum_j c_j phi_j; when the basis
- * would exceed 4N vectors restart from the N Ritz vectors }.  Synchronous: returns when done.
+ * would exceed 4N vectors (HPSI_OPT_BASIS) restart from the N Ritz vectors }.  At HPSI_MIXED the
+ * basis is complex64 and the returned eigenvalues are float64 Rayleigh quotients (see
+ * HPSI_OPT_FINAL_FP64); the returned residual norms are those of the returned vectors.
+ * Synchronous: returns when done.
  * HPSI_ENOTCONV if maxiter is reached (outputs then hold the last iterate).
  */
 HPSI_API int davidson_solve(hpsi_ctx* ctx, int ik, int nbnd, double tol, int maxiter, void* psi_inout,

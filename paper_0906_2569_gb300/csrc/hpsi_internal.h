@@ -126,6 +126,7 @@ struct Context {
   int tc_kmax = 0;                     // mixed calbec: max 64-wide K-steps per split (0: automatic)
   int prec_override = -1;              // >= 0: apply H at this precision instead of `precision`
   int final_fp64 = 1;                  // mixed davidson_solve: final Rayleigh quotients with the float64 H
+  int basis_factor = 4;                // Davidson: the reduced basis grows to basis_factor * N vectors
   cudaStream_t cap_stream = nullptr;   // internal stream for graph capture
   GraphCache graph;
   // launch accounting (always) and per-launch event timing (HPSI_OPT_KERNEL_TIMING)

@@ -192,3 +192,17 @@ def test_hpsi_mixed_three_terms(lib, nbnd):
     e2 = rel(run_apply(ctx, 0, psi), ref)
     B.hpsi_sync(ctx)
     assert e2 < TOLMIX and e3 < TOLMIX and e3 <= e2 * 1.5
+
+
+@pytest.mark.parametrize("precision,tol", [(0, TOL64), (1, TOLMIX)])
+def test_hpsi_c5_sampled(lib, precision, tol):
+    """The large cell: 144^3 box, 161235 PWs, 864 projectors; 96 bands applied, 3 checked by the oracle."""
+    p = workloads.config5()
+    ctx, (m,), vr, (beta,), d = make_problem(p, precision=precision)
+    assert len(m) == 161235
+    psi = workloads.psi0(p.lattice, p.kpts[0], m, 96, p.psi_seed)
+    got = run_apply(ctx, 0, psi)
+    sel = [0, 47, 95]
+    ref = oracle.hamiltonian.hpsi(p.lattice, p.kpts[0], m, p.fft, vr, beta, d, psi[sel])
+    assert rel(got[sel], ref) < tol
+    ctx.close()
