@@ -68,8 +68,13 @@ enum hpsi_option {
   HPSI_OPT_FINAL_FP64 = 7,    /* mixed davidson_solve: 1 (default) takes the final Rayleigh
                                  quotients with one float64 application of H to the Ritz vectors;
                                  0 with the mixed H */
-  HPSI_OPT_BASIS = 8          /* davidson_solve: the reduced basis grows to this many times N
+  HPSI_OPT_BASIS = 8,         /* davidson_solve: the reduced basis grows to this many times N
                                  vectors (2: the basic 2N form, 3 or 4 (default)) before a restart */
+  HPSI_OPT_AUTOTUNE = 9       /* 1 (default): the first hpsi_apply of a problem with >= 4 bands at a
+                                 precision times every shared-memory plan of the register-codelet
+                                 kernels and three band-block sizes on its own bands and keeps the
+                                 fastest (that call synchronizes; results do not depend on the
+                                 choice); 0: fixed defaults */
 };
 
 /* Kernel classes reported by hpsi_kernel_stats. */

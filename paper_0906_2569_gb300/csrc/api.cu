@@ -791,6 +791,11 @@ extern "C" int hpsi_set_option(hpsi_ctx* ctx, int option, double value) {
     }
     return HPSI_OK;
   }
+  if (option == HPSI_OPT_AUTOTUNE) {
+    if (value != 0.0 && value != 1.0) return fail(c, HPSI_EINVAL, "HPSI_OPT_AUTOTUNE must be 0 or 1");
+    c.autotune = (int)value;
+    return HPSI_OK;
+  }
   if (option == HPSI_OPT_BASIS) {
     if (value != 2.0 && value != 3.0 && value != 4.0) return fail(c, HPSI_EINVAL, "HPSI_OPT_BASIS must be 2, 3 or 4");
     c.basis_factor = (int)value;

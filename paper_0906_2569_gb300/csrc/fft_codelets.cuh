@@ -148,19 +148,26 @@ __device__ __forceinline__ V twiddle_t(V v, V w) {
   return r;
 }
 
-// See the file comment.  reg has max(R1, R2) entries; xb is the group's N-entry exchange buffer;
-// tw the N-entry table.  Every lane of the warp must call (the exchange uses __syncwarp).
+// Entries of one group's exchange buffer: rows padded by one element so that the row reads of the
+// second stage fall in different shared-memory banks.
+template <int R1, int R2> struct Xch {
+  static constexpr int size = (R1 * (R2 + 1) > R2 * (R1 + 1) ? R1 * (R2 + 1) : R2 * (R1 + 1));
+};
+
+// See the file comment.  reg has max(R1, R2) entries; xb is the group's exchange buffer of
+// Xch<R1, R2>::size entries; tw the N-entry table.  Every lane of the warp must call (the
+// exchange uses __syncwarp).
 template <int R1, int R2, int DIR, typename V>
 __device__ __forceinline__ void fft2_nat(V* reg, V* xb, const V* tw, int t, bool active) {
   if (active && t < R2) {
     Cdl<R1, DIR, V>::run(reg);
 #pragma unroll
-    for (int k1 = 0; k1 < R1; ++k1) xb[k1 * R2 + t] = k1 == 0 ? reg[0] : twiddle_t<DIR>(reg[k1], tw[t * k1]);
+    for (int k1 = 0; k1 < R1; ++k1) xb[k1 * (R2 + 1) + t] = k1 == 0 ? reg[0] : twiddle_t<DIR>(reg[k1], tw[t * k1]);
   }
   __syncwarp();
   if (active && t < R1) {
 #pragma unroll
-    for (int n2 = 0; n2 < R2; ++n2) reg[n2] = xb[t * R2 + n2];
+    for (int n2 = 0; n2 < R2; ++n2) reg[n2] = xb[t * (R2 + 1) + n2];
     Cdl<R2, DIR, V>::run(reg);
   }
   __syncwarp();
@@ -171,12 +178,12 @@ __device__ __forceinline__ void fft2_rev(V* reg, V* xb, const V* tw, int t, bool
   if (active && t < R1) {
     Cdl<R2, DIR, V>::run(reg);
 #pragma unroll
-    for (int m2 = 0; m2 < R2; ++m2) xb[m2 * R1 + t] = m2 == 0 ? reg[0] : twiddle_t<DIR>(reg[m2], tw[t * m2]);
+    for (int m2 = 0; m2 < R2; ++m2) xb[m2 * (R1 + 1) + t] = m2 == 0 ? reg[0] : twiddle_t<DIR>(reg[m2], tw[t * m2]);
   }
   __syncwarp();
   if (active && t < R2) {
 #pragma unroll
-    for (int k1 = 0; k1 < R1; ++k1) reg[k1] = xb[t * R1 + k1];
+    for (int k1 = 0; k1 < R1; ++k1) reg[k1] = xb[t * (R1 + 1) + k1];
     Cdl<R1, DIR, V>::run(reg);
   }
   __syncwarp();

@@ -68,8 +68,9 @@ struct Problem {
   FftPlan plan[3];
   // per precision (index HPSI_FP64 / HPSI_MIXED): band blocks and the fast-path plan
   int nbb[2] = {1, 1};             // band block of the generic local kernels
-  int fflags[2] = {0, 0};          // fast path: bit 2 enabled, bit 0 stage V, bit 1 stage the stick row
-  int nbbf[2] = {1, 1};            // band block of the fast local kernels
+  mutable int fflags[2] = {0, 0};  // fast path: bit 2 enabled, bit 0 stage V, bit 1 stage the stick row
+  mutable int nbbf[2] = {1, 1};    // band block of the fast local kernels
+  mutable bool tuned[2] = {false, false};   // autotuner has chosen fflags / nbbf
   int* d_ymap = nullptr;           // [npl][n2]: stick of (plane, j2) or -1
   int* d_xmap = nullptr;           // [n1]: plane of ix or -1
   const double2* d_ftw64 = nullptr;   // e^{-2 pi i j / n}, j < n (owned by the twiddle table)
@@ -127,6 +128,7 @@ struct Context {
   int prec_override = -1;              // >= 0: apply H at this precision instead of `precision`
   int final_fp64 = 1;                  // mixed davidson_solve: final Rayleigh quotients with the float64 H
   int basis_factor = 4;                // Davidson: the reduced basis grows to basis_factor * N vectors
+  int autotune = 1;                    // time the fast-path plans on the first apply of a problem
   cudaStream_t cap_stream = nullptr;   // internal stream for graph capture
   GraphCache graph;
   // launch accounting (always) and per-launch event timing (HPSI_OPT_KERNEL_TIMING)
@@ -167,6 +169,7 @@ int nonlocal_apply_mixed(Context& c, const Problem& p, const double2* psi, doubl
 int mixed_prepare_beta(Context& c, Problem& p);
 size_t local_scratch_per_band(const Problem& p, int precision);
 int local_fast_plan(const Problem& p, int precision, size_t smem_optin);
+std::vector<int> local_fast_candidates(const Problem& p, int precision, size_t smem_optin);
 int local_fast_apply(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd, void* Zt, void* Yb,
                      int nbb);
 int local_fast_apply_multi(Context& c, int nitem, const int* prob, const int* nbnd, const double2* const* psi,

@@ -59,6 +59,8 @@ template <int R1, int R2> struct Geo {
   static constexpr int G = R1 > R2 ? R1 : R2;
   static constexpr int LPW = 32 / G;          // line groups per warp
   static constexpr int GROUPS = 8 * LPW;      // per 256-thread CTA
+  static constexpr int XS = Xch<R1, R2>::size; // exchange-buffer entries per group
+  static constexpr int PS = N + 1;            // row stride of the plane array (one pad entry)
 };
 
 template <typename T, int R1, int R2>
@@ -70,8 +72,8 @@ __global__ void __launch_bounds__(256) k_zinv(const __grid_constant__ FastBatch 
   if ((int)blockIdx.x * SC >= a.nst || (int)blockIdx.y >= a.nb) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* tw = reinterpret_cast<V*>(smem_raw);
-  V* xbuf = tw + N;                       // [SC][N]
-  V* obuf = xbuf + SC * N;                // [N][SC]
+  V* xbuf = tw + N;                       // [SC][XS]
+  V* obuf = xbuf + SC * Gm::XS;           // [N][SC]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int grp = warp * Gm::LPW + lane / G, t = lane % G;
   const bool in_grp = lane < Gm::LPW * G;
@@ -91,7 +93,7 @@ __global__ void __launch_bounds__(256) k_zinv(const __grid_constant__ FastBatch 
       reg[n1] = tt < st.len ? d2v<V>(ps[tt]) : czero<V>();
     }
   }
-  fft2_nat<R1, R2, +1>(reg, xbuf + (in_grp ? grp : 0) * N, tw, t, active);
+  fft2_nat<R1, R2, +1>(reg, xbuf + (in_grp ? grp : 0) * Gm::XS, tw, t, active);
   if (active && t < R1) {
 #pragma unroll
     for (int k2 = 0; k2 < R2; ++k2) obuf[(t + R1 * k2) * SC + grp] = reg[k2];
@@ -114,15 +116,16 @@ __global__ void __launch_bounds__(256) k_plane(const __grid_constant__ FastBatch
   if ((int)blockIdx.y * a.bpc >= a.nb) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* tw = reinterpret_cast<V*>(smem_raw);
-  V* xbuf = tw + N;                              // [NG][N]
-  V* P = xbuf + NG * N;                          // [npl][N]
-  V* row = P + (size_t)a.npl * N;                // [nst] if stage_row
+  constexpr int PS = Gm::PS;
+  V* xbuf = tw + N;                              // [NG][XS]
+  V* P = xbuf + NG * Gm::XS;                     // [npl][PS]
+  V* row = P + (size_t)a.npl * PS;               // [nst] if stage_row
   T* vpl = reinterpret_cast<T*>(row + (bt.stage_row ? a.nst : 0));   // [N][N] if stage_v
   int* xm = reinterpret_cast<int*>(vpl + (bt.stage_v ? N * N : 0));  // [N]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int grp = warp * Gm::LPW + lane / G, t = lane % G;
   const bool in_grp = lane < Gm::LPW * G;
-  V* xb = xbuf + (in_grp ? grp : 0) * N;
+  V* xb = xbuf + (in_grp ? grp : 0) * Gm::XS;
   const int j3 = blockIdx.x;
   const T* Vg = reinterpret_cast<const T*>(a.V) + (size_t)j3 * N * N;
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
@@ -158,7 +161,7 @@ __global__ void __launch_bounds__(256) k_plane(const __grid_constant__ FastBatch
       fft2_nat<R1, R2, +1>(reg, xb, tw, t, act);
       if (act && t < R1) {
 #pragma unroll
-        for (int k2 = 0; k2 < R2; ++k2) P[(size_t)p * N + t + R1 * k2] = reg[k2];
+        for (int k2 = 0; k2 < R2; ++k2) P[(size_t)p * PS + t + R1 * k2] = reg[k2];
       }
     }
     __syncthreads();
@@ -170,7 +173,7 @@ __global__ void __launch_bounds__(256) k_plane(const __grid_constant__ FastBatch
 #pragma unroll
         for (int n1 = 0; n1 < R1; ++n1) {
           const int pp = xm[R2 * n1 + t];
-          reg[n1] = pp >= 0 ? P[(size_t)pp * N + j2] : czero<V>();
+          reg[n1] = pp >= 0 ? P[(size_t)pp * PS + j2] : czero<V>();
         }
       }
       fft2_nat<R1, R2, +1>(reg, xb, tw, t, act);
@@ -184,7 +187,7 @@ __global__ void __launch_bounds__(256) k_plane(const __grid_constant__ FastBatch
 #pragma unroll
         for (int m1 = 0; m1 < R1; ++m1) {
           const int pp = xm[t + R2 * m1];
-          if (pp >= 0) P[(size_t)pp * N + j2] = reg[m1];
+          if (pp >= 0) P[(size_t)pp * PS + j2] = reg[m1];
         }
       }
     }
@@ -196,7 +199,7 @@ __global__ void __launch_bounds__(256) k_plane(const __grid_constant__ FastBatch
       const bool act = in_grp && p < a.npl;
       if (act && t < R2) {
 #pragma unroll
-        for (int n1 = 0; n1 < R1; ++n1) reg[n1] = P[(size_t)p * N + R2 * n1 + t];
+        for (int n1 = 0; n1 < R1; ++n1) reg[n1] = P[(size_t)p * PS + R2 * n1 + t];
       }
       fft2_nat<R1, R2, -1>(reg, xb, tw, t, act);
       if (act && t < R1) {
@@ -224,8 +227,8 @@ __global__ void __launch_bounds__(256) k_zfwd(const __grid_constant__ FastBatch 
   if ((int)blockIdx.x * SC >= a.nst || (int)blockIdx.y >= a.nb) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* tw = reinterpret_cast<V*>(smem_raw);
-  V* xbuf = tw + N;                       // [SC][N]
-  V* ibuf = xbuf + SC * N;                // [N][SC]
+  V* xbuf = tw + N;                       // [SC][XS]
+  V* ibuf = xbuf + SC * Gm::XS;           // [N][SC]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int grp = warp * Gm::LPW + lane / G, t = lane % G;
   const bool in_grp = lane < Gm::LPW * G;
@@ -245,7 +248,7 @@ __global__ void __launch_bounds__(256) k_zfwd(const __grid_constant__ FastBatch 
 #pragma unroll
     for (int n1 = 0; n1 < R1; ++n1) reg[n1] = ibuf[(R2 * n1 + t) * SC + grp];
   }
-  fft2_nat<R1, R2, -1>(reg, xbuf + (in_grp ? grp : 0) * N, tw, t, active);
+  fft2_nat<R1, R2, -1>(reg, xbuf + (in_grp ? grp : 0) * Gm::XS, tw, t, active);
   if (active && t < R1) {
     const StickDev st = a.sticks[s];
     const double2* ps = a.psi + (size_t)b * a.npw + st.g0;
@@ -269,9 +272,9 @@ template <typename T, int R1, int R2>
 struct FastKernels {
   using V = typename Cx<T>::type;
   using Gm = Geo<R1, R2>;
-  static size_t smem_z() { return sizeof(V) * (size_t)(Gm::N + 2 * Gm::GROUPS * Gm::N); }
+  static size_t smem_z() { return sizeof(V) * (size_t)(Gm::N + Gm::GROUPS * Gm::XS + Gm::GROUPS * Gm::N); }
   static size_t smem_plane(const Problem& p, int sv, int sr) {
-    return sizeof(V) * (size_t)(Gm::N + Gm::GROUPS * Gm::N + (size_t)p.npl * Gm::N + (sr ? p.nst : 0)) +
+    return sizeof(V) * (size_t)(Gm::N + Gm::GROUPS * Gm::XS + (size_t)p.npl * Gm::PS + (sr ? p.nst : 0)) +
            (sv ? sizeof(T) * (size_t)Gm::N * Gm::N : 0) + sizeof(int) * Gm::N;
   }
   // One launch of each kernel over every item of the batch (all share the edge N and the flags).
@@ -403,6 +406,21 @@ static void batch_header(FastBatch& bt, const Problem& p, int flags) {
   bt.tw64 = p.d_ftw64;
   bt.tw32 = p.d_ftw32;
   bt.inv_nr = 1.0 / ((double)p.n[0] * p.n[1] * p.n[2]);
+}
+
+// Every plan (staging flags | 4) whose kernels fit the shared memory, for the autotuner.
+std::vector<int> local_fast_candidates(const Problem& p, int precision, size_t smem_optin) {
+  std::vector<int> out;
+  if (p.n[0] != p.n[1] || p.n[1] != p.n[2]) return out;
+  auto pick = [&](auto k) {
+    using K = decltype(k);
+    for (int cand : {3, 2, 1, 0})
+      if (K::smem_z() <= smem_optin && K::smem_plane(p, cand & 1, (cand >> 1) & 1) <= smem_optin)
+        out.push_back(4 | cand);
+  };
+  if (precision == HPSI_FP64) dispatch_size<double>(p.n[0], pick);
+  else dispatch_size<float>(p.n[0], pick);
+  return out;
 }
 
 int local_fast_apply(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd, void* Zt, void* Yb,

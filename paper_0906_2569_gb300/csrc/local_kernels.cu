@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "hpsi_internal.h"
 #include "warp_fft.cuh"
@@ -167,10 +168,67 @@ size_t local_smem_bytes(const Problem& p, int precision, int which) {
   return cs * (size_t)p.ns_max * p.n[2];
 }
 
+// Autotuner of the fast path: time every plan that fits the shared memory (which of the V plane
+// and the stick row the plane kernel stages) against band blocks of half, one and two times the
+// default, on this call's own bands, and keep the fastest.  Neither choice changes the arithmetic.
+static int tune_fast(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd, size_t cs) {
+  const int pr = cur_prec(c);
+  const std::vector<int> plans = local_fast_candidates(p, pr, c.smem_optin);
+  const int nb0 = p.nbbf[pr];
+  std::vector<int> blocks;
+  for (int nb : {std::max(1, nb0 / 2), nb0, 2 * nb0}) {
+    const int v = std::min(nb, nbnd);
+    if (std::find(blocks.begin(), blocks.end(), v) == blocks.end()) blocks.push_back(v);
+  }
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    return HPSI_OK;
+  }
+  float best = 1e30f;
+  int best_plan = p.fflags[pr], best_nb = nb0;
+  const bool timing = c.timing;
+  c.timing = false;
+  int rc = HPSI_OK;
+  for (int plan : plans)
+    for (int nb : blocks) {
+      const size_t need = cs * (size_t)nb * p.n[2] * p.nst;
+      rc = ensure_buffer(c, &c.ws.X, &c.ws.xbytes, need);
+      if (!rc) rc = ensure_buffer(c, &c.ws.Y, &c.ws.ybytes, need);
+      if (rc) break;
+      p.fflags[pr] = plan;
+      float ms = 0.f;
+      for (int rep = 0; rep < 2 && !rc; ++rep) {   // first run warms up, second is timed
+        cudaEventRecord(e0, c.stream);
+        rc = local_fast_apply(c, p, psi, hpsi, nbnd, c.ws.X, c.ws.Y, nb);
+        cudaEventRecord(e1, c.stream);
+      }
+      if (rc) break;
+      if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best) {
+        best = ms;
+        best_plan = plan;
+        best_nb = nb;
+      }
+    }
+  c.timing = timing;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  p.fflags[pr] = best_plan;
+  p.nbbf[pr] = best_nb;
+  p.tuned[pr] = true;
+  return rc;
+}
+
 template <typename T>
 static int local_apply_t(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd) {
   const size_t cs = sizeof(typename Cx<T>::type);
   if ((p.fflags[cur_prec(c)] & 4) && !c.force_generic) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(c.stream, &cap);
+    if (c.autotune && !p.tuned[cur_prec(c)] && nbnd >= 4 && cap == cudaStreamCaptureStatusNone) {
+      int rc = tune_fast(c, p, psi, hpsi, nbnd, cs);
+      if (rc) return rc;
+    }
     const int nbf = std::max(1, std::min(p.nbbf[cur_prec(c)], nbnd));
     const size_t zneed = cs * (size_t)nbf * p.n[2] * p.nst;
     int rc = ensure_buffer(c, &c.ws.X, &c.ws.xbytes, zneed);

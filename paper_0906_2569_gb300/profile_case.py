@@ -1,8 +1,10 @@
 """A small, self-contained H|psi> case for profiler captures.
 
 Runs ``--reps`` applications of H to the 160-band block of the 90^3 / 36785-PW / 256-projector
-cell (or the cell named by ``--config``) at the chosen precision, after one warm-up application,
-so that a profiler can skip the warm-up launches and capture a steady-state one.
+cell (or the cell named by ``--config``) at the chosen precision.  Two warm-up applications come
+first (the first one runs the autotuner); the steady-state applications are bracketed by
+cudaProfilerStart / cudaProfilerStop, so a profiler started with ``--profile-from-start off``
+captures only them.
 """
 from __future__ import annotations
 
@@ -35,9 +37,14 @@ def main():
                        torch.cuda.current_stream().cuda_stream)
     x = torch.from_numpy(workloads.psi0(p.lattice, k, m, nb, p.psi_seed)).cuda()
     y = torch.empty_like(x)
-    for _ in range(1 + args.reps):
+    for _ in range(2):
         B.hpsi_apply(ctx, 0, x, y)
     B.hpsi_sync(ctx)
+    torch.cuda.profiler.start()
+    for _ in range(args.reps):
+        B.hpsi_apply(ctx, 0, x, y)
+    B.hpsi_sync(ctx)
+    torch.cuda.profiler.stop()
     print("ok", args.config, args.precision, nb, float(y.abs().sum()))
 
 

@@ -42,3 +42,28 @@ def test_cubic_boxes_both_paths(lib, a, fft, precision):
         err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
         assert err < tol, f"box {fft} precision {precision} generic={generic}: {err:.3e}"
     ctx.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_autotuner_does_not_change_results(lib, precision):
+    """The plan the autotuner picks (staging, band block) leaves H|psi> bit-identical."""
+    import torch
+    from paper_0906_2569_gb300 import binding as B
+    p = workloads.config2()
+    k = p.kpts[0]
+    m = B.hpsi_gsphere(p.lattice, p.ecut, k)
+    vr = workloads.vloc_r(p.lattice, p.atoms, p.fft)
+    beta = workloads.beta(p.lattice, p.atoms, k, m)
+    x = torch.from_numpy(workloads.psi0(p.lattice, k, m, 40, p.psi_seed)).cuda()
+    outs = []
+    for tune in (0, 1):
+        ctx = B.hpsi_setup(p.lattice, p.ecut, [k], p.fft, vr, [beta], workloads.dmat(len(p.atoms)), precision,
+                           torch.cuda.current_stream().cuda_stream)
+        B.hpsi_set_option(ctx, B.HPSI_OPT_AUTOTUNE, tune)
+        y = torch.empty_like(x)
+        B.hpsi_apply(ctx, 0, x, y)
+        B.hpsi_apply(ctx, 0, x, y)
+        B.hpsi_sync(ctx)
+        outs.append(y.cpu().numpy())
+        ctx.close()
+    assert np.array_equal(outs[0], outs[1])
