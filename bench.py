@@ -38,9 +38,14 @@ sys.path.insert(0, ROOT)
 HBM_FALLBACK_GBS = 6800.0
 FP64_ALU_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12    # 2 DFMA / clk / SM (measured), 2070 MHz max clock
 
-# dram bytes per launch (read + write) from ncu captures, keyed by kernel and the source hash
-# of the file that defines it at capture time; a mismatch reports null.
-NCU_TRAFFIC = {}
+# DRAM bytes (read + write) per band-application measured by ncu for a kernel class, keyed by
+# (kernel, precision) with the hash of its source files at capture time; a mismatch reports null.
+#   xvx_y mixed: k_plane<float,9,10>, 48-band launch, 51.73 MB read + 4.81 MB write (ncu_plane_c2.md)
+#   calbec fp64: k_calbec64, 160-band launch, 267.31 MB read + 7.14 MB write (ncu_calbec64_c2.md)
+NCU_TRAFFIC = {
+    ("xvx_y", 1): (("local_fast.cu", "fft_codelets.cuh"), "92564643ab55", (51.725568e6 + 4.813056e6) / 48),
+    ("calbec", 0): (("nonlocal_fp64.cu",), "f2c91a1c9ad9", (267.307264e6 + 7.139584e6) / 160),
+}
 
 
 def parse():
@@ -200,9 +205,12 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def file_hash(rel):
-    with open(os.path.join(ROOT, rel), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:12]
+def source_hash(files):
+    h = hashlib.sha256()
+    for rel in files:
+        with open(os.path.join(ROOT, "paper_0906_2569_gb300", "csrc", rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
 
 
 def run_gpu(args):
@@ -265,9 +273,13 @@ def run_gpu(args):
         B.hpsi_set_option(ctx, B.HPSI_OPT_KERNEL_TIMING, 1)
         evs = []
         with Clocks(local_rank) as clk:
+            if precision == B.HPSI_MIXED:
+                torch.cuda.profiler.start()     # a profiler started with --profile-from-start off sees these
             for _ in range(steps):
                 evs.append(step())
             barrier()
+            if precision == B.HPSI_MIXED:
+                torch.cuda.profiler.stop()
         ms = [a.elapsed_time(b) for a, b in evs]
         launches, _ = B.hpsi_kernel_stats(ctx, -1)
         bapps, _ = B.hpsi_kernel_stats(ctx, -2)
@@ -507,14 +519,14 @@ def roofline(res, p, npw, nst, npl, precision):
     byt, flop = kernel_work(name, p, npw, nst, npl, precision, p.nproj)
     secs = cand[name]["ms"] / 1e3
     avg_ms = cand[name]["ms"] / cand[name]["launches"]
-    src = {"inv_zy": "local_fast.cu", "xvx_y": "local_fast.cu", "fwd_z": "local_fast.cu",
-           "calbec": "nonlocal_tc.cu" if precision == 1 else "nonlocal_fp64.cu",
-           "addvus": "nonlocal_tc.cu" if precision == 1 else "nonlocal_fp64.cu"}[name]
     traffic = None
     key = (name, precision)
-    if key in NCU_TRAFFIC and NCU_TRAFFIC[key][0] == file_hash(os.path.join("paper_0906_2569_gb300", "csrc", src)):
-        traffic = NCU_TRAFFIC[key][1]
-    out = {"kernel": name, "avg_launch_ms": avg_ms, "traffic": traffic, "bytes_per_band": byt, "flops_per_band": flop}
+    bands_per_launch = units / cand[name]["launches"]
+    if key in NCU_TRAFFIC and NCU_TRAFFIC[key][1] == source_hash(NCU_TRAFFIC[key][0]):
+        traffic = NCU_TRAFFIC[key][2] * bands_per_launch
+    out = {"kernel": name, "avg_launch_ms": avg_ms, "traffic": traffic, "bytes_per_band": byt, "flops_per_band": flop,
+           "bands_per_launch": bands_per_launch,
+           "traffic_note": "ncu dram read+write per band of a steady-state launch (profiles/), x bands per launch"}
     if name in ("calbec", "addvus") and precision == 1:
         peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
         ach = units * flop / secs / 1e12

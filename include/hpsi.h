@@ -254,6 +254,15 @@ HPSI_API int hpsi_kernel_stats(hpsi_ctx* ctx, int kernel, long long* launches, d
  */
 HPSI_API int hpsi_sync(hpsi_ctx* ctx);
 
+/*
+ * hpsi_selftest_timeout -- exercise the device failure path: queue on the context's stream a
+ * one-thread kernel that waits, with a limit of about 2e6 cycles (~1 ms), on a shared-memory
+ * barrier nothing ever arrives at, the same bounded wait the tensor-core kernels use; on expiry it
+ * raises the context's error word and returns.  The next hpsi_sync reports HPSI_ETIMEOUT (and
+ * clears the word).  Nothing faults or hangs; the context stays usable.
+ */
+HPSI_API int hpsi_selftest_timeout(hpsi_ctx* ctx);
+
 /* One-line message for the last failure on ctx (NULL ctx: this thread's last setup failure). */
 HPSI_API const char* hpsi_last_error(const hpsi_ctx* ctx);
 

@@ -24,7 +24,7 @@ STATUS_NAMES = {0: "HPSI_OK", -1: "HPSI_EINVAL", -2: "HPSI_ENOMEM", -3: "HPSI_EC
                 -5: "HPSI_ESINGULAR", -6: "HPSI_ETIMEOUT", -7: "HPSI_ENODEV"}
 
 EXPORTS = ("hpsi_gsphere", "hpsi_setup", "hpsi_setup_cells", "hpsi_nprob", "hpsi_npw", "hpsi_nproj", "hpsi_apply",
-           "hpsi_apply_batch", "hpsi_apply_noalloc", "davidson_solve", "hpsi_set_option", "hpsi_kernel_stats", "hpsi_sync", "hpsi_last_error",
+           "hpsi_apply_batch", "hpsi_apply_noalloc", "davidson_solve", "hpsi_set_option", "hpsi_kernel_stats", "hpsi_sync", "hpsi_selftest_timeout", "hpsi_last_error",
            "hpsi_destroy")
 
 _lib = None
@@ -64,6 +64,8 @@ def _declare(lib):
     lib.hpsi_kernel_stats.restype = I
     lib.hpsi_sync.argtypes = [V]
     lib.hpsi_sync.restype = I
+    lib.hpsi_selftest_timeout.argtypes = [V]
+    lib.hpsi_selftest_timeout.restype = I
     lib.hpsi_last_error.argtypes = [V]
     lib.hpsi_last_error.restype = ctypes.c_char_p
     lib.hpsi_destroy.argtypes = [V]
@@ -235,6 +237,11 @@ def hpsi_set_option(ctx: Context, option: int, value: float) -> None:
 def hpsi_sync(ctx: Context) -> None:
     """hpsi_sync(): wait for the context's stream; raises on a device-side timeout."""
     _check(ctx.lib, ctx.handle, ctx.lib.hpsi_sync(ctx.handle), "hpsi_sync")
+
+
+def hpsi_selftest_timeout(ctx: Context) -> None:
+    """hpsi_selftest_timeout(): queue the bounded-wait self-test (the next hpsi_sync raises ETIMEOUT)."""
+    _check(ctx.lib, ctx.handle, ctx.lib.hpsi_selftest_timeout(ctx.handle), "hpsi_selftest_timeout")
 
 
 def hpsi_kernel_stats(ctx: Context, kernel: int, reset: bool = False):

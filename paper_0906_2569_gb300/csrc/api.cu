@@ -854,6 +854,11 @@ extern "C" int hpsi_kernel_stats(hpsi_ctx* ctx, int kernel, long long* launches,
   return HPSI_OK;
 }
 
+extern "C" int hpsi_selftest_timeout(hpsi_ctx* ctx) {
+  if (!ctx) return HPSI_EINVAL;
+  return wait_selftest(ctx->c);
+}
+
 extern "C" int hpsi_sync(hpsi_ctx* ctx) {
   if (!ctx) return HPSI_EINVAL;
   return check_device_error(ctx->c);

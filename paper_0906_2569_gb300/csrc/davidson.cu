@@ -551,23 +551,23 @@ int davidson_run(Context& c, int ik, int nbnd, double tol, int maxiter, double2*
 
 namespace {
 
+// Sum over a block of up to 1024 threads: warp shuffles, then one value per warp.
 __device__ __forceinline__ double block_sum256(double s, double* red) {
-  red[threadIdx.x] = s;
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if ((threadIdx.x & 31) == 0) red[w] = s;
   __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
-  }
-  const double r = red[0];
+  double r = 0.0;
+  for (int i = 0; i < nw; ++i) r += red[i];
   __syncthreads();
   return r;
 }
 
 // R_i = HPsi_i - eps_i Psi_i (float32 data, float64 norm); one CTA per band.
-__global__ void __launch_bounds__(256) k_residual32(int npw, const float2* __restrict__ psi,
+__global__ void __launch_bounds__(1024) k_residual32(int npw, const float2* __restrict__ psi,
                                                     const float2* __restrict__ hpsi, const double* __restrict__ eps,
                                                     float2* __restrict__ r, double* __restrict__ rnorm) {
-  __shared__ double red[256];
+  __shared__ double red[32];
   const int b = blockIdx.x;
   const double e = eps[b];
   const float2* x = psi + (size_t)b * npw;
@@ -583,11 +583,11 @@ __global__ void __launch_bounds__(256) k_residual32(int npw, const float2* __res
   if (threadIdx.x == 0) rnorm[b] = sqrt(s);
 }
 
-__global__ void __launch_bounds__(256) k_precondition32(int npw, const int* __restrict__ idx,
+__global__ void __launch_bounds__(1024) k_precondition32(int npw, const int* __restrict__ idx,
                                                         const float2* __restrict__ r, const double* __restrict__ hdiag,
                                                         const double* __restrict__ eps, double tau, int eshift,
                                                         float2* __restrict__ t) {
-  __shared__ double red[256];
+  __shared__ double red[32];
   const int j = blockIdx.x;
   const int i = idx[j];
   const double e = eps[eshift >= 0 ? eshift : i];
@@ -606,8 +606,8 @@ __global__ void __launch_bounds__(256) k_precondition32(int npw, const int* __re
   for (int g = threadIdx.x; g < npw; g += blockDim.x) tb[g] = make_float2(tb[g].x * inv, tb[g].y * inv);
 }
 
-__global__ void __launch_bounds__(256) k_norm2_32(int npw, const float2* __restrict__ t, double* __restrict__ out) {
-  __shared__ double red[256];
+__global__ void __launch_bounds__(1024) k_norm2_32(int npw, const float2* __restrict__ t, double* __restrict__ out) {
+  __shared__ double red[32];
   const float2* tb = t + (size_t)blockIdx.x * npw;
   double s = 0.0;
   for (int g = threadIdx.x; g < npw; g += blockDim.x) s += (double)tb[g].x * tb[g].x + (double)tb[g].y * tb[g].y;
@@ -664,10 +664,10 @@ __global__ void k_mat_64_to_32(int rows, int cols, const double2* __restrict__ s
 }
 
 // eps_i = Re<psi_i|H psi_i> / <psi_i|psi_i> and ||H psi_i - eps_i psi_i|| / ||psi_i||, float64.
-__global__ void __launch_bounds__(256) k_rayleigh(int npw, const double2* __restrict__ psi,
+__global__ void __launch_bounds__(1024) k_rayleigh(int npw, const double2* __restrict__ psi,
                                                   const double2* __restrict__ hpsi, double* __restrict__ eps,
                                                   double* __restrict__ rnorm) {
-  __shared__ double red[256];
+  __shared__ double red[32];
   const int b = blockIdx.x;
   const double2* x = psi + (size_t)b * npw;
   const double2* hx = hpsi + (size_t)b * npw;
@@ -819,7 +819,7 @@ static int davidson_run_mixed(Context& c, DavHandles& h, int ik, int nbnd, doubl
                     Cf(w.hpsi32), npw),
         "cgemm H Ritz vectors");
     DCK(cudaMemcpyAsync(w.eps, w.w, sizeof(double) * N, cudaMemcpyDeviceToDevice, c.stream), "eps copy");
-    HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_residual32<<<N, 256, 0, c.stream>>>(npw, w.psi32, w.hpsi32, w.eps, w.t32, w.rnorm)));
+    HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_residual32<<<N, 1024, 0, c.stream>>>(npw, w.psi32, w.hpsi32, w.eps, w.t32, w.rnorm)));
     DCK(cudaMemcpyAsync(rn.data(), w.rnorm, sizeof(double) * N, cudaMemcpyDeviceToHost, c.stream), "norm copy");
     DCK(cudaStreamSynchronize(c.stream), "davidson iteration");
     rc = check_device_error(c);
@@ -843,7 +843,7 @@ static int davidson_run_mixed(Context& c, DavHandles& h, int ik, int nbnd, doubl
     DCK(cudaMemcpyAsync(w.idx, uidx.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, c.stream), "index copy");
     float2* tnew = w.phi32 + (size_t)m * npw;
     const int eshift = c.opt_shift == 1 ? N - 1 : -1;
-    HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_precondition32<<<nc, 256, 0, c.stream>>>(npw, w.idx, w.t32, p.d_hdiag, w.eps,
+    HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_precondition32<<<nc, 1024, 0, c.stream>>>(npw, w.idx, w.t32, p.d_hdiag, w.eps,
                                                                                 c.opt_tau, eshift, tnew)));
     for (int round = 0; round < 2; ++round) {
       for (int pass = 0; pass < 2; ++pass) {
@@ -855,7 +855,7 @@ static int davidson_run_mixed(Context& c, DavHandles& h, int ik, int nbnd, doubl
             "cgemm projection update");
       }
       if (round == 1) break;
-      HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_norm2_32<<<nc, 256, 0, c.stream>>>(npw, tnew, w.cn2)));
+      HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_norm2_32<<<nc, 1024, 0, c.stream>>>(npw, tnew, w.cn2)));
       std::vector<double> cn(nc);
       DCK(cudaMemcpyAsync(cn.data(), w.cn2, sizeof(double) * nc, cudaMemcpyDeviceToHost, c.stream), "norm copy");
       DCK(cudaStreamSynchronize(c.stream), "correction norms");
@@ -866,7 +866,7 @@ static int davidson_run_mixed(Context& c, DavHandles& h, int ik, int nbnd, doubl
       DCK(cudaMemcpyAsync(w.idx2, col.data(), sizeof(int) * col.size(), cudaMemcpyHostToDevice, c.stream),
           "index copy");
       HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
-                  (k_fallback32<<<(int)col.size(), 256, 0, c.stream>>>(npw, w.idx2, w.idx, w.t32, w.rnorm, tnew)));
+                  (k_fallback32<<<(int)col.size(), 1024, 0, c.stream>>>(npw, w.idx2, w.idx, w.t32, w.rnorm, tnew)));
     }
     int nkeep = 0;
     rc = canonical_orth32(c, h, tnew, nc, w.t32, &nkeep, kDropAbs, false);
@@ -887,7 +887,7 @@ static int davidson_run_mixed(Context& c, DavHandles& h, int ik, int nbnd, doubl
   rc = apply_device(c, ik, w.in64, w.out64, N);
   c.prec_override = -1;
   if (rc) return rc;
-  HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_rayleigh<<<N, 256, 0, c.stream>>>(npw, w.in64, w.out64, w.eps, w.rnorm)));
+  HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_rayleigh<<<N, 1024, 0, c.stream>>>(npw, w.in64, w.out64, w.eps, w.rnorm)));
   DCK(cudaMemcpyAsync(ev.data(), w.eps, sizeof(double) * N, cudaMemcpyDeviceToHost, c.stream), "eig copy");
   DCK(cudaMemcpyAsync(rn.data(), w.rnorm, sizeof(double) * N, cudaMemcpyDeviceToHost, c.stream), "norm copy");
   DCK(cudaStreamSynchronize(c.stream), "davidson end");

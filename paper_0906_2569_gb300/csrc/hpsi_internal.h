@@ -167,6 +167,7 @@ int local_apply(Context& c, const Problem& p, const double2* psi, double2* hpsi,
 int nonlocal_apply_fp64(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd);
 int nonlocal_apply_mixed(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd);
 int mixed_prepare_beta(Context& c, Problem& p);
+int wait_selftest(Context& c);
 size_t local_scratch_per_band(const Problem& p, int precision);
 int local_fast_plan(const Problem& p, int precision, size_t smem_optin);
 std::vector<int> local_fast_candidates(const Problem& p, int precision, size_t smem_optin);

@@ -71,17 +71,31 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
 }
 
 // Bounded wait: false if the clock limit expired or another thread of the CTA aborted.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                          long long limit = kWaitCycles) {
   const long long t0 = clock64();
   for (unsigned it = 0;; ++it) {
     if (mbar_try(bar, parity)) return true;
     if ((it & 255u) == 255u) {
       if (*abort_flag) return false;
-      if (clock64() - t0 > kWaitCycles) {
+      if (clock64() - t0 > limit) {
         *abort_flag = 1;
         return false;
       }
     }
+  }
+}
+
+// Self-test of the failure path: one thread waits, with a short limit, on an mbarrier that no
+// thread and no copy ever arrives at; the expiry raises the error word exactly as in k_tc_gemm.
+__global__ void k_wait_selftest(int* err, long long limit) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ volatile int abort_flag;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    abort_flag = 0;
+    if (!mbar_wait(smem_u32(&bar), 0, &abort_flag, limit)) atomicExch(err, 1);
   }
 }
 
@@ -484,6 +498,14 @@ int apply_t(Context& c, const Problem& p, const double2* psi, double2* hpsi, int
 }
 
 }  // namespace
+
+// Launch the bounded-wait self-test (about 2e6 cycles, ~1 ms).
+int wait_selftest(Context& c) {
+  HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_wait_selftest<<<1, 32, 0, c.stream>>>(c.d_err, 2000000LL)));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "self-test launch");
+  return HPSI_OK;
+}
 
 int mixed_prepare_beta(Context& c, Problem& p) {
   int rc = get_encoder(c);

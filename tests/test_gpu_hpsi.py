@@ -206,3 +206,20 @@ def test_hpsi_c5_sampled(lib, precision, tol):
     ref = oracle.hamiltonian.hpsi(p.lattice, p.kpts[0], m, p.fft, vr, beta, d, psi[sel])
     assert rel(got[sel], ref) < tol
     ctx.close()
+
+
+def test_bounded_wait_reports_timeout(lib):
+    """A device wait that nothing satisfies expires, sets the error word, and the host sees
+    HPSI_ETIMEOUT; the context keeps working afterwards (nothing faults or hangs)."""
+    from paper_0906_2569_gb300 import binding as B
+    p = workloads.config1()
+    ctx, (m,), vr, (beta,), d = make_problem(p, precision=B.HPSI_MIXED)
+    B.hpsi_sync(ctx)
+    B.hpsi_selftest_timeout(ctx)
+    with pytest.raises(B.HpsiError) as e:
+        B.hpsi_sync(ctx)
+    assert e.value.status == B.HPSI_ETIMEOUT
+    B.hpsi_sync(ctx)                               # the word was cleared
+    psi = workloads.random_block(len(m), 4, 1)
+    ref = oracle.hamiltonian.hpsi(p.lattice, p.kpts[0], m, p.fft, vr, beta, d, psi)
+    assert rel(run_apply(ctx, 0, psi), ref) < TOLMIX
