@@ -69,6 +69,22 @@ def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
 
 
+def world_max(x, world, device):
+    """Largest x over the ranks of the default process group (x itself when world == 1)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(units_per_rank, max_ms, world):
+    """Whole-job throughput of independent replicas: every rank's units over the slowest rank's time."""
+    return units_per_rank * world / (max_ms / 1e3)
+
+
 def workload(cfg):
     import workloads
     p = workloads.CONFIGS[cfg]()
@@ -332,17 +348,10 @@ def run_gpu(args):
     mixed = measure(B.HPSI_MIXED, args.tol_mixed, args.steps, args.warmup, e2e=not args.no_e2e)
     fp64 = measure(B.HPSI_FP64, args.tol_fp64, args.fp64_steps, args.fp64_warmup)
 
-    def world_max(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    mix_ms = world_max(mixed["total_ms"])
-    f64_ms = world_max(fp64["total_ms"])
-    value = mixed["band_apps"] * world / (mix_ms / 1e3)
-    v64 = fp64["band_apps"] * world / (f64_ms / 1e3)
+    mix_ms = world_max(mixed["total_ms"], world, "cuda")
+    f64_ms = world_max(fp64["total_ms"], world, "cuda")
+    value = replica_value(mixed["band_apps"], mix_ms, world)
+    v64 = replica_value(fp64["band_apps"], f64_ms, world)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
