@@ -70,11 +70,16 @@ enum hpsi_option {
                                  0 with the mixed H */
   HPSI_OPT_BASIS = 8,         /* davidson_solve: the reduced basis grows to this many times N
                                  vectors (2: the basic 2N form, 3 or 4 (default)) before a restart */
-  HPSI_OPT_AUTOTUNE = 9       /* 1 (default): the first hpsi_apply of a problem with >= 4 bands at a
+  HPSI_OPT_AUTOTUNE = 9,      /* 1 (default): the first hpsi_apply of a problem with >= 4 bands at a
                                  precision times every shared-memory plan of the register-codelet
                                  kernels and three band-block sizes on its own bands and keeps the
                                  fastest (that call synchronizes; results do not depend on the
                                  choice); 0: fixed defaults */
+  HPSI_OPT_EIGENSOLVER = 10   /* reduced eigenproblems of davidson_solve and hpsi_eigh_lowest:
+                                 1 (default): the library's own kernels (Householder reduction,
+                                 Sturm multisection, inverse iteration, back-transformation) for
+                                 n <= 1024, cuSOLVER zheevdx above that or if inverse iteration
+                                 loses a vector; 0: cuSOLVER zheevdx always */
 };
 
 /* Kernel classes reported by hpsi_kernel_stats. */
@@ -87,7 +92,9 @@ enum hpsi_kernel {
   HPSI_K_ADDVUS = 5,   /* hpsi += beta (D <beta|psi>) */
   HPSI_K_SPLIT = 6,    /* mixed path: bf16 operand splitting */
   HPSI_K_DAVIDSON = 7, /* Davidson residual / preconditioner / helper kernels */
-  HPSI_K_COUNT = 8
+  HPSI_K_EIGH = 8,     /* reduced eigenproblem: tridiagonal reduction, multisection, inverse
+                          iteration, back-transformation */
+  HPSI_K_COUNT = 9
 };
 
 enum hpsi_precision {
@@ -222,6 +229,30 @@ HPSI_API int hpsi_apply_batch(hpsi_ctx* ctx, int nitem, const int* prob, const i
  */
 HPSI_API int davidson_solve(hpsi_ctx* ctx, int ik, int nbnd, double tol, int maxiter, void* psi_inout,
                    double* eig_out, int* iters_out, double* resnorm_out);
+
+/*
+ * hpsi_eigh_lowest -- the lowest nwant eigenpairs of a dense Hermitian matrix: the reduced
+ * problem sum_k (H_jk - eps S_jk) c_k = 0 that the Rayleigh-Ritz step of block Davidson solves
+ * over its orthonormal reduced basis (App. A.2.1; S_jk is then the identity).  davidson_solve
+ * calls the same solver; this entry point exposes it on its own.
+ *   n            in   order of the matrix, >= 1
+ *   a            in   device complex128, column-major with leading dimension lda >= n; only the
+ *                     upper triangle (row <= column) is read and the imaginary parts of the
+ *                     diagonal are ignored; not modified
+ *   nwant        in   1 <= nwant <= n
+ *   w_out        out  device double[nwant], eigenvalues ascending
+ *   v_out        out  device complex128 [nwant][n] (column-major n x nwant, leading dim n):
+ *                     orthonormal eigenvectors, each determined up to a phase (and, within a
+ *                     degenerate eigenvalue, up to a unitary mixing)
+ * Float64 throughout.  With HPSI_OPT_EIGENSOLVER = 1 (default) and n <= 1024: Householder
+ * reduction to a real tridiagonal T (one cooperative launch with bounded grid-barrier waits),
+ * Sturm multisection for the eigenvalues of T, inverse iteration with Gram-Schmidt inside
+ * clusters of close eigenvalues and Cholesky QR for the eigenvectors, back-transformation;
+ * otherwise cuSOLVER zheevdx.  Synchronizes the context's stream.  HPSI_EINVAL on bad sizes or
+ * pointers, HPSI_ETIMEOUT if a barrier wait ran out, HPSI_ECUDA / HPSI_ENOMEM on CUDA failures,
+ * HPSI_ESINGULAR if zheevdx fails.
+ */
+HPSI_API int hpsi_eigh_lowest(hpsi_ctx* ctx, int n, const void* a, int lda, int nwant, void* w_out, void* v_out);
 
 /*
  * hpsi_set_option -- tune the Davidson solver of a context (App. A.2.1, the diagonal form of D).

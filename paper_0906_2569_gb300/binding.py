@@ -19,12 +19,13 @@ HPSI_ENOTCONV, HPSI_ESINGULAR, HPSI_ETIMEOUT, HPSI_ENODEV = -4, -5, -6, -7
 HPSI_FP64, HPSI_MIXED = 0, 1
 HPSI_OPT_PRECOND_TAU, HPSI_OPT_PRECOND_SHIFT, HPSI_OPT_KERNEL_TIMING, HPSI_OPT_NL_TERMS = 1, 2, 3, 4
 HPSI_OPT_LOCAL_PATH, HPSI_OPT_TC_KSPLIT, HPSI_OPT_FINAL_FP64, HPSI_OPT_BASIS, HPSI_OPT_AUTOTUNE = 5, 6, 7, 8, 9
-KERNELS = ("inv_zy", "xvx_y", "fwd_z", "calbec", "dscale", "addvus", "split", "davidson")
+HPSI_OPT_EIGENSOLVER = 10
+KERNELS = ("inv_zy", "xvx_y", "fwd_z", "calbec", "dscale", "addvus", "split", "davidson", "eigh")
 STATUS_NAMES = {0: "HPSI_OK", -1: "HPSI_EINVAL", -2: "HPSI_ENOMEM", -3: "HPSI_ECUDA", -4: "HPSI_ENOTCONV",
                 -5: "HPSI_ESINGULAR", -6: "HPSI_ETIMEOUT", -7: "HPSI_ENODEV"}
 
 EXPORTS = ("hpsi_gsphere", "hpsi_setup", "hpsi_setup_cells", "hpsi_nprob", "hpsi_npw", "hpsi_nproj", "hpsi_apply",
-           "hpsi_apply_batch", "hpsi_apply_noalloc", "davidson_solve", "hpsi_set_option", "hpsi_kernel_stats", "hpsi_sync", "hpsi_selftest_timeout", "hpsi_last_error",
+           "hpsi_apply_batch", "hpsi_apply_noalloc", "davidson_solve", "hpsi_eigh_lowest", "hpsi_set_option", "hpsi_kernel_stats", "hpsi_sync", "hpsi_selftest_timeout", "hpsi_last_error",
            "hpsi_destroy")
 
 _lib = None
@@ -58,6 +59,8 @@ def _declare(lib):
     lib.hpsi_apply_batch.restype = I
     lib.davidson_solve.argtypes = [V, I, I, D, I, V, P(D), P(I), P(D)]
     lib.davidson_solve.restype = I
+    lib.hpsi_eigh_lowest.argtypes = [V, I, V, I, I, V, V]
+    lib.hpsi_eigh_lowest.restype = I
     lib.hpsi_set_option.argtypes = [V, I, D]
     lib.hpsi_set_option.restype = I
     lib.hpsi_kernel_stats.argtypes = [V, I, P(ctypes.c_longlong), P(D), I]
@@ -227,6 +230,15 @@ def hpsi_apply_batch(ctx: Context, probs, psi_list, hpsi_list) -> None:
     rc = ctx.lib.hpsi_apply_batch(ctx.handle, n, pa.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                                   nb.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), pin, pout)
     _check(ctx.lib, ctx.handle, rc, "hpsi_apply_batch")
+
+
+def hpsi_eigh_lowest(ctx: Context, a_colmajor, n: int, lda: int, nwant: int, w_out, v_out) -> None:
+    """hpsi_eigh_lowest(): device tensors; a_colmajor holds the matrix column-major (row i of the
+    tensor is column i), only its upper triangle is read; v_out [nwant][n] receives one
+    eigenvector per row, w_out [nwant] the eigenvalues ascending."""
+    rc = ctx.lib.hpsi_eigh_lowest(ctx.handle, int(n), ctypes.c_void_p(_ptr(a_colmajor)), int(lda), int(nwant),
+                                  ctypes.c_void_p(_ptr(w_out)), ctypes.c_void_p(_ptr(v_out)))
+    _check(ctx.lib, ctx.handle, rc, "hpsi_eigh_lowest")
 
 
 def hpsi_set_option(ctx: Context, option: int, value: float) -> None:

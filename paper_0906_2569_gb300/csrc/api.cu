@@ -71,7 +71,7 @@ int check_device_error(Context& c) {
   if (e != cudaSuccess) return cuda_fail(c, e, "error word read");
   if (v != 0) {
     cudaMemset(c.d_err, 0, sizeof(int));
-    return fail(c, HPSI_ETIMEOUT, "a bounded wait in a tensor-core kernel expired; its output is invalid");
+    return fail(c, HPSI_ETIMEOUT, "a bounded device-side wait expired; the output of that call is invalid");
   }
   return HPSI_OK;
 }
@@ -350,6 +350,7 @@ static void free_context(Context& c) {
   if (c.graph.exec) cudaGraphExecDestroy(c.graph.exec);
   if (c.cap_stream) cudaStreamDestroy(c.cap_stream);
   davidson_release(c);
+  eigh_release(c);
 }
 
 int nonlocal_apply(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd) {
@@ -789,6 +790,11 @@ extern "C" int hpsi_set_option(hpsi_ctx* ctx, int option, double value) {
         if (rc) return rc;
       }
     }
+    return HPSI_OK;
+  }
+  if (option == HPSI_OPT_EIGENSOLVER) {
+    if (value != 0.0 && value != 1.0) return fail(c, HPSI_EINVAL, "HPSI_OPT_EIGENSOLVER must be 0 or 1");
+    c.eigensolver = (int)value;
     return HPSI_OK;
   }
   if (option == HPSI_OPT_AUTOTUNE) {

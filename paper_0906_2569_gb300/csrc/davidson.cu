@@ -327,6 +327,11 @@ static int small_eigh(Context& c, DavHandles& h, const double2* a, int lda, int 
 // nwant columns of w.evec (ld n).
 static int lowest_eigh(Context& c, DavHandles& h, const double2* a, int lda, int n, int nwant) {
   DavWork& w = h.wk;
+  if (c.eigensolver == 1) {
+    bool fallback = false;
+    const int rc = eigh_lowest(c, a, lda, n, nwant, w.w, w.evec, &fallback);
+    if (rc || !fallback) return rc;
+  }
   HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_copy_matrix<<<(n * n + 255) / 256, 256, 0, c.stream>>>(n, n, a, lda, w.evec, n)));
   int meig = 0;
   BCK(cusolverDnZheevdx(h.solver, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I, CUBLAS_FILL_MODE_UPPER, n,

@@ -1,0 +1,908 @@
+// Lowest eigenpairs of a dense Hermitian matrix on the GPU, in float64: the reduced problem
+// sum_k (H_jk - eps S_jk) c_k = 0 of the Rayleigh-Ritz step of block Davidson (paper App. A.2.1),
+// where the reduced basis is orthonormal so S_jk is the identity.
+//
+//   1. Householder reduction Q^H A Q = T, Q = H_0 H_1 ... H_{n-2}, H_j = I - tau_j v_j v_j^H acting
+//      on indices j+1..n-1 with v_j[j+1] = 1; T is real symmetric tridiagonal (diagonal d,
+//      off-diagonal e).  Column j: H_j^H x = beta e_1 for the part x of the column below the
+//      diagonal (beta real); then with y = A22 v_j, s = v_j^H y and w = tau_j y - |tau_j|^2 s v_j / 2
+//      the trailing block becomes H_j^H A22 H_j = A22 - w v_j^H - v_j w^H.
+//   2. The lowest nwant eigenvalues of T by multisection on Sturm counts.
+//   3. Their eigenvectors z_i by inverse iteration.  Eigenvalues closer than 1e-10 |T| form a
+//      cluster whose vectors are orthogonalised against each other (modified Gram-Schmidt) at each
+//      iteration; the whole set is then orthonormalised by Cholesky QR (Z^T Z = U^T U,
+//      Z <- Z U^-1), which mixes two vectors only in proportion to their loss of orthogonality, itself
+//      of the order of rounding / gap, so residuals stay at rounding level.
+//   4. Back-transformation x_i = Q z_i = H_0 (H_1 (... (H_{n-2} z_i))), in blocks of 64 reflectors
+//      written in compact WY form H_a ... H_b = I - V T V^H and applied with two ZGEMMs and a
+//      back substitution with T^-1 = diag(1 / tau) + strictly-upper(V^H V).
+//
+// Step 1 is one cooperative launch over G CTAs.  Row r of A lives in the shared memory of CTA
+// r mod G for the whole reduction.  For column j every CTA rebuilds the same reflector from row j
+// (A is Hermitian, so the column below the diagonal is the conjugate of the row's tail; the owner
+// of row j published that row, updated, at the end of column j-1), updates its own rows with the
+// previous column's w and v, and forms its rows of y = A22 v_j and its part of s.  One grid-wide
+// barrier per column then publishes y, s and row j+1.  Every barrier wait is bounded in time: a
+// wait that runs out raises the context's device error word and the kernel returns.
+#include <cublas_v2.h>
+#include <cuda_runtime.h>
+#include <cusolverDn.h>
+
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+#include <string>
+
+#include "hpsi_internal.h"
+
+namespace hpsi {
+
+namespace {
+
+constexpr int kTriThreads = 256;                     // threads per CTA of the reduction
+constexpr int kMaxN = 1024;                          // largest n handled here
+constexpr long long kBarrierLimit = 2000000000LL;    // clock cycles (about 1 s) per barrier wait
+constexpr int kInvIters = 3;                         // inverse-iteration solves per eigenvector
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a - w1 conj(v1) - v2 conj(w2) as eight fused multiply-adds
+__device__ __forceinline__ double2 rank2_sub(double2 a, double2 w1, double2 v1, double2 v2, double2 w2) {
+  double x = fma(-w1.x, v1.x, a.x);
+  x = fma(-w1.y, v1.y, x);
+  x = fma(-v2.x, w2.x, x);
+  x = fma(-v2.y, w2.y, x);
+  double y = fma(-w1.y, v1.x, a.y);
+  y = fma(w1.x, v1.y, y);
+  y = fma(-v2.y, w2.x, y);
+  y = fma(v2.x, w2.y, y);
+  return make_double2(x, y);
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Element (r, c) of the Hermitian matrix whose upper triangle is a (column-major, leading dim lda).
+__device__ __forceinline__ double2 herm_at(const double2* __restrict__ a, int lda, int r, int c) {
+  if (r <= c) {
+    double2 v = a[r + (size_t)c * lda];
+    if (r == c) v.y = 0.0;
+    return v;
+  }
+  double2 v = a[c + (size_t)r * lda];
+  v.y = -v.y;
+  return v;
+}
+
+struct TriArgs {
+  int n, lda, G;
+  const double2* a;
+  double* d;            // [n] diagonal of T
+  double* e;            // [n] off-diagonal of T (e[j] couples j and j+1)
+  double* e2;           // [n] e^2
+  double2* tau;         // [n] reflector factors
+  double2* vref;        // [n][n] row j: v_j at columns j+1..n-1
+  double2* ybuf;        // [2][n] y of the last two columns
+  double2* rnext;       // [2][n] the next row, published by its owner
+  double* spart;        // [2][G] per-CTA parts of s
+  unsigned int* bar;    // [2 * kBarGen] barrier count and generation
+  int* err;             // device error word
+};
+
+// Grid-wide barrier of a cooperative launch.  bar[0] counts arrivals, bar[kBarGen] (another
+// 128-byte line, so waiting CTAs do not poll the line the arrivals update) is the generation.
+// Returns false when this CTA's wait ran out or another CTA reported a failure (the error word is
+// then set).
+constexpr int kBarGen = 32;
+
+__device__ bool grid_barrier(unsigned int* bar, unsigned int G, int* err) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* gen = bar + kBarGen;
+    const unsigned int g0 = *gen;
+    __threadfence();
+    int good = 1;
+    if (atomicAdd(bar, 1u) == G - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + kBarGen, 1u);
+    } else {
+      const long long t0 = clock64();
+      unsigned int spins = 0;
+      while (*gen == g0) {
+        if ((++spins & 255u) == 0u &&
+            (*(volatile int*)err != 0 || clock64() - t0 > kBarrierLimit)) {
+          atomicCAS(err, 0, 3);
+          good = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    ok = good && *(volatile int*)err == 0;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// Column j keeps the previous reflector in the folded form used by the updates: with u the
+// updated row j-1 (so v_{j-1}[c] = conj(u[c]) scale for c > j, v_{j-1}[j] = 1) and
+// w = tau y - hh v (hh = |tau|^2 s / 2), the rank-2 update of element (r, c), c > j, is
+//   a -= P_r u[c] + Q_r conj(y[c]),  P_r = (tau y_r - 2 hh v_r) conj(scale),  Q_r = conj(tau) v_r,
+// so neither w nor v is formed as a vector; the new row's reflector enters the product with A as
+// conj(u[c]) and its scale is applied to each row sum at the end, which lets one warp compute the
+// scalars of the reflector while the others update the rows.
+__global__ void __launch_bounds__(kTriThreads, 1) k_eh_tridiag(TriArgs p) {
+  extern __shared__ double2 sm[];
+  constexpr int NW = kTriThreads / 32;
+  constexpr int kChainWarp = NW - 1;          // computes beta, tau, scale during the row updates
+  const int n = p.n, G = p.G, g = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int R = g < n ? (n - 1 - g) / G + 1 : 0;
+  const int Rmax = (n + G - 1) / G;
+  double2* ubuf0 = sm;
+  double2* ubuf1 = sm + n;
+  double2* yP = sm + 2 * n;
+  double2* rows = sm + 3 * n;
+  double2* racc = rows + (size_t)Rmax * n;    // [Rmax] row sums with conj(u)
+  double2* ra1 = racc + Rmax;                 // [Rmax] row element at column j+1
+  __shared__ double red[NW];
+  __shared__ double sP_sh;
+  __shared__ double2 alpha_sh, tau_sh, scale_sh;
+  __shared__ double beta_sh;
+
+  for (int lr = 0; lr < R; ++lr) {
+    const int r = g + lr * G;
+    for (int c = tid; c < n; c += kTriThreads) rows[(size_t)lr * n + c] = herm_at(p.a, p.lda, r, c);
+  }
+  double2 tauP = make_double2(0.0, 0.0), scP = make_double2(0.0, 0.0);
+  for (int j = 0; j < n; ++j) {
+    double2* uC = (j & 1) ? ubuf1 : ubuf0;   // this column's reflector, unscaled
+    double2* uP = (j & 1) ? ubuf0 : ubuf1;   // previous column's
+    // (A) row j (updated through column j-2 by its owner) and y of column j-1, into shared memory
+    for (int c = j + tid; c < n; c += kTriThreads) {
+      if (j == 0) {
+        uC[c] = herm_at(p.a, p.lda, 0, c);
+      } else {
+        uC[c] = __ldcg(&p.rnext[((j - 1) & 1) * n + c]);
+        yP[c] = __ldcg(&p.ybuf[((j - 1) & 1) * n + c]);
+      }
+    }
+    if (j > 0 && wid == 0) {
+      double s = 0.0;
+      for (int q = lane; q < G; q += 32) s += __ldcg(&p.spart[((j - 1) & 1) * G + q]);
+      s = warp_sum(s);
+      if (lane == 0) sP_sh = s;
+    }
+    __syncthreads();
+    const double hh = 0.5 * (tauP.x * tauP.x + tauP.y * tauP.y) * (j > 0 ? sP_sh : 0.0);
+    const double2 ctauP = make_double2(tauP.x, -tauP.y);
+    const double2 cscP = make_double2(scP.x, -scP.y);
+    // (B) column j-1's update of row j; its diagonal; the reflector of column j (uC[c], c > j)
+    double sig = 0.0, dj = 0.0;
+    double2 Pp = make_double2(0.0, 0.0), P = Pp, Q = Pp;
+    if (j > 0) {
+      const double2 yj = yP[j];
+      Pp = make_double2(tauP.x * yj.x - tauP.y * yj.y - 2.0 * hh, tauP.x * yj.y + tauP.y * yj.x);
+      P = cmul(Pp, cscP);
+      Q = ctauP;     // v_{j-1}[j] = 1
+    }
+    for (int c = j + tid; c < n; c += kTriThreads) {
+      double2 a = uC[c];
+      if (j > 0) {
+        const double2 yc = yP[c];
+        if (c == j) {   // conj(v_{j-1}[j]) = 1
+          a.x -= Pp.x + Q.x * yc.x + Q.y * yc.y;
+          a.y -= Pp.y + Q.y * yc.x - Q.x * yc.y;
+        } else {
+          a = rank2_sub(a, P, make_double2(uP[c].x, -uP[c].y), Q, yc);
+        }
+      }
+      if (c == j) {
+        dj = a.x;
+      } else {
+        uC[c] = a;
+        if (c == j + 1) alpha_sh = make_double2(a.x, -a.y);
+        else sig = fma(a.x, a.x, fma(a.y, a.y, sig));
+      }
+    }
+    if (j == n - 1) {
+      if (g == 0 && tid == 0) p.d[j] = dj;
+      break;
+    }
+    sig = warp_sum(sig);
+    if (lane == 0) red[wid] = sig;
+    __syncthreads();
+    // (C) one warp: beta, tau, scale;  the others: column j-1's update of the own rows r > j and
+    //     their products with conj(u) (columns >= j+2) and their element at column j+1
+    if (wid == kChainWarp) {
+      if (lane == 0) {
+        double sigma = 0.0;
+        for (int q = 0; q < NW; ++q) sigma += red[q];
+        const double ar = alpha_sh.x, ai = alpha_sh.y;
+        double beta;
+        double2 tau, scale;
+        if (sigma == 0.0 && ai == 0.0) {
+          beta = ar;
+          tau = make_double2(0.0, 0.0);
+          scale = make_double2(0.0, 0.0);
+        } else {
+          beta = -copysign(sqrt(ar * ar + ai * ai + sigma), ar);
+          const double ib = 1.0 / beta;
+          tau = make_double2((beta - ar) * ib, -ai * ib);
+          const double dr = ar - beta, iden = 1.0 / (dr * dr + ai * ai);
+          scale = make_double2(dr * iden, -ai * iden);       // 1 / (alpha - beta)
+        }
+        tau_sh = tau;
+        scale_sh = scale;
+        beta_sh = beta;
+      }
+    } else {
+      for (int lr = wid; lr < R; lr += NW - 1) {
+        const int r = g + lr * G;
+        if (r <= j) continue;
+        double2* row = rows + (size_t)lr * n;
+        double2 P = make_double2(0.0, 0.0), Q = make_double2(0.0, 0.0);
+        if (j > 0) {
+          const double2 ur = uP[r], yr = yP[r];
+          const double2 vr = cmul(make_double2(ur.x, -ur.y), scP);      // v_{j-1}[r], r > j
+          const double2 ty = cmul(tauP, yr);
+          P = cmul(make_double2(ty.x - 2.0 * hh * vr.x, ty.y - 2.0 * hh * vr.y), cscP);
+          Q = cmul(ctauP, vr);
+        }
+        double ax = 0.0, ay = 0.0, bx = 0.0, by = 0.0;
+        double2 a1 = make_double2(0.0, 0.0);
+        for (int c = j + 1 + lane; c < n; c += 64) {
+          const int c2 = c + 32;
+          const bool two = c2 < n;
+          double2 a = row[c];
+          double2 b = two ? row[c2] : make_double2(0.0, 0.0);
+          if (j > 0) {
+            a = rank2_sub(a, P, make_double2(uP[c].x, -uP[c].y), Q, yP[c]);
+            row[c] = a;
+            if (two) {
+              b = rank2_sub(b, P, make_double2(uP[c2].x, -uP[c2].y), Q, yP[c2]);
+              row[c2] = b;
+            }
+          }
+          if (c == j + 1) {
+            a1 = a;
+          } else {
+            const double2 u = uC[c];            // a * conj(u)
+            ax = fma(a.x, u.x, fma(a.y, u.y, ax));
+            ay = fma(a.y, u.x, fma(-a.x, u.y, ay));
+          }
+          if (two) {
+            const double2 u = uC[c2];
+            bx = fma(b.x, u.x, fma(b.y, u.y, bx));
+            by = fma(b.y, u.x, fma(-b.x, u.y, by));
+          }
+          if (r == j + 1) {
+            p.rnext[(j & 1) * n + c] = a;
+            if (two) p.rnext[(j & 1) * n + c2] = b;
+          }
+        }
+        ax += bx;
+        ay += by;
+        ax = warp_sum(ax);
+        ay = warp_sum(ay);
+        if (lane == 0) {
+          racc[lr] = make_double2(ax, ay);
+          ra1[lr] = a1;
+        }
+      }
+    }
+    __syncthreads();
+    // (D) y_j[r] = a1 + scale * racc for the own rows, their part of s_j = v_j^H y_j, outputs
+    const double2 tauC = tau_sh, scC = scale_sh;
+    if (wid == 0) {
+      double sp = 0.0;
+      const double2 cscC = make_double2(scC.x, -scC.y);
+      for (int lr = lane; lr < R; lr += 32) {
+        const int r = g + lr * G;
+        if (r <= j) continue;
+        const double2 y = make_double2(ra1[lr].x + scC.x * racc[lr].x - scC.y * racc[lr].y,
+                                       ra1[lr].y + scC.x * racc[lr].y + scC.y * racc[lr].x);
+        p.ybuf[(j & 1) * n + r] = y;
+        const double2 cv = r == j + 1 ? make_double2(1.0, 0.0) : cmul(uC[r], cscC);   // conj(v_j[r])
+        sp += cv.x * y.x - cv.y * y.y;
+      }
+      sp = warp_sum(sp);
+      if (lane == 0) {
+        p.spart[(j & 1) * G + g] = sp;
+        if (g == 0) {
+          p.d[j] = dj;
+          p.e[j] = beta_sh;
+          p.e2[j] = beta_sh * beta_sh;
+          p.tau[j] = tauC;
+        }
+      }
+    }
+    if (g == j % G) {   // the owner of row j stores v_j for the back-transformation
+      for (int c = j + 1 + tid; c < n; c += kTriThreads) {
+        const double2 u = uC[c];
+        p.vref[(size_t)j * n + c] = c == j + 1 ? make_double2(1.0, 0.0) : cmul(make_double2(u.x, -u.y), scC);
+      }
+    }
+    tauP = tauC;
+    scP = scC;
+    if (!grid_barrier(p.bar, (unsigned)G, p.err)) return;
+  }
+}
+
+__device__ __forceinline__ int biased_exp(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7ff); }
+
+// Gershgorin interval [lo, hi] of T, |T| bound and largest e^2, reduced over a warp.
+__device__ void gershgorin(int n, const double* __restrict__ d, const double* __restrict__ e, double* lo, double* hi,
+                           double* emax2) {
+  const int lane = threadIdx.x & 31;
+  double l = DBL_MAX, h = -DBL_MAX, m = 0.0;
+  for (int k = lane; k < n; k += 32) {
+    const double el = k > 0 ? fabs(e[k - 1]) : 0.0, er = k < n - 1 ? fabs(e[k]) : 0.0;
+    l = fmin(l, d[k] - el - er);
+    h = fmax(h, d[k] + el + er);
+    m = fmax(m, er * er);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    l = fmin(l, __shfl_xor_sync(0xffffffffu, l, o));
+    h = fmax(h, __shfl_xor_sync(0xffffffffu, h, o));
+    m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  }
+  *lo = l;
+  *hi = h;
+  *emax2 = m;
+}
+
+// Number of eigenvalues of T below sigma: the sign changes of the leading principal minors
+// p_k of T - sigma I (p_k = (d_k - sigma) p_{k-1} - e_{k-1}^2 p_{k-2}), kept scaled by powers of
+// two; a minor that is exactly zero is taken as -pivmin times the previous one.  Signs, zero tests
+// and the scaling test read the bit patterns (integer pipe); only the recurrence is float64.
+__device__ int sturm_count(int n, const double* __restrict__ d, const double* __restrict__ e2, double sigma,
+                           double pivmin) {
+  double pm = 1.0, p = d[0] - sigma;
+  if ((__double_as_longlong(p) << 1) == 0) p = -pivmin;
+  int cnt = __double_as_longlong(p) < 0;
+  for (int k = 1; k < n; ++k) {
+    double pn = fma(d[k] - sigma, p, -e2[k - 1] * pm);
+    if ((__double_as_longlong(pn) << 1) == 0) pn = -pivmin * p;
+    cnt += (__double_as_longlong(pn) ^ __double_as_longlong(p)) < 0;
+    pm = p;
+    p = pn;
+    if ((k & 3) == 0) {
+      const int ex = max(biased_exp(p), biased_exp(pm));
+      if (ex > 1023 + 400) {
+        p *= 0x1p-400;
+        pm *= 0x1p-400;
+      } else if (ex < 1023 - 400) {
+        p *= 0x1p400;
+        pm *= 0x1p400;
+      }
+    }
+  }
+  return cnt;
+}
+
+// One CTA of kBisWarps warps per wanted eigenvalue i: (32 kBisWarps + 1)-way multisection of an
+// interval with count(lo) <= i < count(hi), one Sturm count per thread and round, so the float64
+// recurrences run on every sub-partition of the SM at once.
+constexpr int kBisWarps = 4;
+__global__ void __launch_bounds__(32 * kBisWarps) k_eh_bisect(int n, const double* __restrict__ d,
+                                                              const double* __restrict__ e,
+                                                              const double* __restrict__ e2, int nwant,
+                                                              double* __restrict__ lam) {
+  constexpr int NP = 32 * kBisWarps;   // points per round
+  __shared__ unsigned bal[kBisWarps];
+  const int i = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (i >= nwant) return;
+  double lo, hi, emax2;
+  gershgorin(n, d, e, &lo, &hi, &emax2);
+  const double tnorm = fmax(fmax(fabs(lo), fabs(hi)), DBL_MIN);
+  const double pivmin = 1e-30 * fmax(1.0, emax2);
+  lo -= 4.0 * DBL_EPSILON * tnorm + 4.0 * pivmin;
+  hi += 4.0 * DBL_EPSILON * tnorm + 4.0 * pivmin;
+  const double tol = 4.0 * DBL_EPSILON * tnorm;
+  for (int round = 0; round < 64 && hi - lo > tol; ++round) {
+    const double w = (hi - lo) / (double)(NP + 1);
+    const int cnt = sturm_count(n, d, e2, lo + w * (double)(tid + 1), pivmin);
+    const unsigned above = __ballot_sync(0xffffffffu, cnt > i);
+    if (lane == 0) bal[wid] = above;
+    __syncthreads();
+    int f = NP;   // index (point - 1) of the first point whose count exceeds i; NP if none
+    for (int q = 0; q < kBisWarps; ++q)
+      if (bal[q]) {
+        f = 32 * q + __ffs(bal[q]) - 1;
+        break;
+      }
+    __syncthreads();
+    double nlo, nhi;
+    if (f == NP) {
+      nlo = lo + w * (double)NP;
+      nhi = hi;
+    } else {
+      nlo = f > 0 ? lo + w * (double)f : lo;
+      nhi = lo + w * (double)(f + 1);
+    }
+    if (nlo == lo && nhi == hi) break;   // the interval is down to a few ulps
+    lo = nlo;
+    hi = nhi;
+  }
+  if (tid == 0) lam[i] = 0.5 * (lo + hi);
+}
+
+__device__ __forceinline__ double hash_unit(unsigned int i, unsigned int k) {
+  unsigned int x = i * 0x9E3779B9u ^ (k * 0x85EBCA6Bu + 0x27D4EB2Fu);
+  x ^= x >> 16;
+  x *= 0x7FEB352Du;
+  x ^= x >> 15;
+  x *= 0x846CA68Bu;
+  x ^= x >> 16;
+  return (double)(x >> 8) * (1.0 / 16777216.0) - 0.5;
+}
+
+// z <- z - (zq . z) zq for the earlier members q of the cluster, then z /= |z|; whole warp.
+__device__ bool orth_normalize(int n, double* z, const double* __restrict__ Z, int i0, int i) {
+  const int lane = threadIdx.x & 31;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int q = i0; q < i; ++q) {
+      const double* zq = Z + (size_t)q * n;
+      double dot = 0.0;
+      for (int k = lane; k < n; k += 32) dot += zq[k] * z[k];
+      dot = warp_sum(dot);
+      for (int k = lane; k < n; k += 32) z[k] -= dot * zq[k];
+      __syncwarp();
+    }
+  }
+  double nn = 0.0;
+  for (int k = lane; k < n; k += 32) nn += z[k] * z[k];
+  nn = warp_sum(nn);
+  if (!(nn > 0.0) || !isfinite(nn)) return false;
+  const double inv = 1.0 / sqrt(nn);
+  for (int k = lane; k < n; k += 32) z[k] *= inv;
+  __syncwarp();
+  return true;
+}
+
+// One warp (one CTA) per cluster of the wanted eigenvalues; lane 0 factors T - lam I and runs the
+// solves, the warp orthogonalises and normalises.  Vectors go to Z (column i, leading dim n).
+__global__ void __launch_bounds__(32) k_eh_invit(int n, const double* __restrict__ d, const double* __restrict__ e,
+                                                 int nwant, const double* __restrict__ lam, double* __restrict__ Z,
+                                                 int* __restrict__ status) {
+  extern __shared__ double sh[];
+  double* sd = sh;
+  double* se = sd + n;
+  double* sl = se + n;
+  double* su1 = sl + n;   // reciprocals of U's diagonal
+  double* su2 = su1 + n;
+  double* su3 = su2 + n;
+  double* z = su3 + n;
+  unsigned char* spv = reinterpret_cast<unsigned char*>(z + n);
+  const int i0 = blockIdx.x, lane = threadIdx.x;
+  if (i0 >= nwant) return;
+  double glo, ghi, emax2;
+  gershgorin(n, d, e, &glo, &ghi, &emax2);
+  double tnorm = fmax(fabs(glo), fabs(ghi));
+  if (!(tnorm > 0.0)) tnorm = 1.0;
+  const double ctol = 1e-10 * tnorm;
+  if (i0 > 0 && lam[i0] - lam[i0 - 1] <= ctol) return;   // not the first of its cluster
+  for (int k = lane; k < n; k += 32) {
+    sd[k] = d[k];
+    se[k] = k < n - 1 ? e[k] : 0.0;
+  }
+  __syncwarp();
+  const double tiny = DBL_EPSILON * tnorm;
+  for (int i = i0; i < nwant && (i == i0 || lam[i] - lam[i - 1] <= ctol); ++i) {
+    const double li = lam[i];
+    if (lane == 0) {
+      // T - li I = P L U by Gaussian elimination with row interchanges
+      double al = sd[0] - li, be = n > 1 ? se[0] : 0.0;
+      for (int k = 0; k < n - 1; ++k) {
+        const double sub = se[k], dn = sd[k + 1] - li, cn = k + 1 < n - 1 ? se[k + 1] : 0.0;
+        if (fabs(al) >= fabs(sub)) {
+          double u = al;
+          if (fabs(u) < tiny) u = u < 0.0 ? -tiny : tiny;
+          const double ui = 1.0 / u;
+          const double l = sub * ui;
+          sl[k] = l;
+          spv[k] = 0;
+          su1[k] = ui;
+          su2[k] = be;
+          su3[k] = 0.0;
+          al = dn - l * be;
+          be = cn;
+        } else {
+          const double ui = 1.0 / sub;
+          const double l = al * ui;
+          sl[k] = l;
+          spv[k] = 1;
+          su1[k] = ui;
+          su2[k] = dn;
+          su3[k] = cn;
+          al = be - l * dn;
+          be = -l * cn;
+        }
+      }
+      double u = al;
+      if (fabs(u) < tiny) u = u < 0.0 ? -tiny : tiny;
+      su1[n - 1] = 1.0 / u;
+    }
+    for (int k = lane; k < n; k += 32) z[k] = hash_unit((unsigned)i, (unsigned)k);
+    __syncwarp();
+    bool ok = orth_normalize(n, z, Z, i0, i);
+    for (int it = 0; it < kInvIters && ok; ++it) {
+      if (lane == 0) {
+        for (int k = 0; k < n - 1; ++k) {
+          if (spv[k]) {
+            const double t = z[k];
+            z[k] = z[k + 1];
+            z[k + 1] = t;
+          }
+          z[k + 1] -= sl[k] * z[k];
+        }
+        z[n - 1] *= su1[n - 1];
+        if (n >= 2) z[n - 2] = (z[n - 2] - su2[n - 2] * z[n - 1]) * su1[n - 2];
+        for (int k = n - 3; k >= 0; --k) z[k] = (z[k] - su2[k] * z[k + 1] - su3[k] * z[k + 2]) * su1[k];
+      }
+      __syncwarp();
+      ok = orth_normalize(n, z, Z, i0, i);
+    }
+    if (!ok) {
+      if (lane == 0) atomicExch(status, 1);
+      return;
+    }
+    double* zi = Z + (size_t)i * n;
+    for (int k = lane; k < n; k += 32) zi[k] = z[k];
+    __syncwarp();
+  }
+}
+
+constexpr int kWY = 64;   // reflectors per compact-WY block of the back-transformation
+
+// x = z (real eigenvectors of T into the complex output, column-major, leading dim n)
+__global__ void k_eh_widen(int n, int nwant, const double* __restrict__ Z, double2* __restrict__ X) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)n * nwant) return;
+  X[idx] = make_double2(Z[idx], 0.0);
+}
+
+// The upper-triangular factor of a compact-WY block, H_{k nb} ... H_{k nb + nb - 1} = I - V T V^H,
+// has the inverse S = T^-1 = diag(1 / tau_i) + (strictly upper part of G = V^H V).  Y = T W is then
+// a back substitution with S: y_q = tau_q (w_q - sum_{r > q} S_qr y_r), which needs no division and
+// gives y_q = 0 for an identity reflector (tau_q = 0).  One warp per column of W (in place), lane l
+// holds rows l and l + 32; rows are finalised from the last one, each subtracting its contribution
+// from the rows above.  G is the block's Gram matrix (column-major kWY x kWY; only its strictly
+// upper part is read), tau the block's kWY reflector factors.
+__global__ void __launch_bounds__(128) k_eh_trsv(int ncol, const double2* __restrict__ G, const double2* __restrict__ tau,
+                                                 double2* __restrict__ W) {
+  static_assert(kWY == 64, "two rows per lane");
+  __shared__ double2 gs[kWY * (kWY - 1) / 2];   // strictly upper part, column q at q (q - 1) / 2
+  for (int q = 1; q < kWY; ++q)
+    for (int r = threadIdx.x; r < q; r += blockDim.x) gs[q * (q - 1) / 2 + r] = G[r + (size_t)q * kWY];
+  __syncthreads();
+  const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (col >= ncol) return;
+  double2* w = W + (size_t)col * kWY;
+  double2 acc0 = w[lane], acc1 = w[lane + 32];     // right-hand side, reduced as rows finalise
+  for (int q = kWY - 1; q >= 0; --q) {
+    // the owner finalises y_q = acc_q / S_qq, then every row r < q subtracts S_rq y_q
+    const int own = q & 31;
+    double2 yq = make_double2(0.0, 0.0);
+    if (lane == own) {
+      const double2 a = q < 32 ? acc0 : acc1, t = tau[q];
+      yq = make_double2(t.x * a.x - t.y * a.y, t.x * a.y + t.y * a.x);
+      if (q < 32) acc0 = yq; else acc1 = yq;
+    }
+    yq.x = __shfl_sync(0xffffffffu, yq.x, own);
+    yq.y = __shfl_sync(0xffffffffu, yq.y, own);
+    if (lane < q) {
+      const double2 s = gs[q * (q - 1) / 2 + lane];
+      acc0.x -= s.x * yq.x - s.y * yq.y;
+      acc0.y -= s.x * yq.y + s.y * yq.x;
+    }
+    if (lane + 32 < q) {
+      const double2 s = gs[q * (q - 1) / 2 + lane + 32];
+      acc1.x -= s.x * yq.x - s.y * yq.y;
+      acc1.y -= s.x * yq.y + s.y * yq.x;
+    }
+  }
+  w[lane] = acc0;
+  w[lane + 32] = acc1;
+}
+
+struct EighState {
+  cublasHandle_t blas = nullptr;
+  cusolverDnHandle_t solver = nullptr;
+  int ncap = 0, wcap = 0;
+  double *d = nullptr, *e = nullptr, *e2 = nullptr, *spart = nullptr, *lam = nullptr, *Z = nullptr;
+  double *gram = nullptr, *work = nullptr;
+  int lwork = 0;
+  double2 *tau = nullptr, *vref = nullptr, *ybuf = nullptr, *rnext = nullptr;
+  double2 *wgram = nullptr, *w1 = nullptr;   // compact-WY blocks
+  unsigned int* bar = nullptr;
+  int* info = nullptr;    // [0] potrf info, [1] inverse-iteration status
+  // cuSOLVER zheevdx path
+  int zcap = 0, zlwork = 0;
+  double2 *acopy = nullptr, *zwork = nullptr;
+  double* wfull = nullptr;
+  int* zinfo = nullptr;
+};
+
+void free_state(EighState& s) {
+  void* ptrs[] = {s.d,     s.e,     s.e2,    s.spart, s.lam,  s.Z,  s.gram, s.work, s.tau,
+                  s.vref,  s.ybuf,  s.rnext, s.wgram, s.w1,   s.bar,  s.info};
+  for (void* q : ptrs) cudaFree(q);
+  const EighState keep = s;
+  s = EighState{};
+  s.blas = keep.blas;
+  s.solver = keep.solver;
+  s.zcap = keep.zcap;
+  s.zlwork = keep.zlwork;
+  s.acopy = keep.acopy;
+  s.zwork = keep.zwork;
+  s.wfull = keep.wfull;
+  s.zinfo = keep.zinfo;
+}
+
+void free_zheevdx(EighState& s) {
+  cudaFree(s.acopy);
+  cudaFree(s.zwork);
+  cudaFree(s.wfull);
+  cudaFree(s.zinfo);
+  s.acopy = s.zwork = nullptr;
+  s.wfull = nullptr;
+  s.zinfo = nullptr;
+  s.zcap = s.zlwork = 0;
+}
+
+int grow(Context& c, EighState& s, int n, int nwant) {
+  if (n <= s.ncap && nwant <= s.wcap) return HPSI_OK;
+  const int ncap0 = s.ncap, wcap0 = s.wcap;
+  free_state(s);
+  s.ncap = ncap0;
+  s.wcap = wcap0;
+  const int N = std::max(n, s.ncap), W = std::max(nwant, s.wcap);
+  const int G = 256;
+  bool ok = true;
+  auto al = [&](void** q, size_t bytes) { ok = ok && cudaMalloc(q, std::max<size_t>(bytes, 16)) == cudaSuccess; };
+  al((void**)&s.d, sizeof(double) * N);
+  al((void**)&s.e, sizeof(double) * N);
+  al((void**)&s.e2, sizeof(double) * N);
+  al((void**)&s.spart, sizeof(double) * 2 * G);
+  al((void**)&s.lam, sizeof(double) * W);
+  al((void**)&s.Z, sizeof(double) * (size_t)N * W);
+  al((void**)&s.gram, sizeof(double) * (size_t)W * W);
+  const int K = (N + kWY - 1) / kWY;
+  al((void**)&s.tau, sizeof(double2) * (N + kWY));
+  al((void**)&s.vref, sizeof(double2) * (size_t)(N + kWY) * N);
+  al((void**)&s.wgram, sizeof(double2) * (size_t)K * kWY * kWY);
+  al((void**)&s.w1, sizeof(double2) * (size_t)kWY * W);
+  al((void**)&s.ybuf, sizeof(double2) * 2 * N);
+  al((void**)&s.rnext, sizeof(double2) * 2 * N);
+  al((void**)&s.bar, sizeof(unsigned int) * 2 * kBarGen);
+  al((void**)&s.info, sizeof(int) * 2);
+  int lw = 0;
+  if (ok && cusolverDnDpotrf_bufferSize(s.solver, CUBLAS_FILL_MODE_UPPER, W, s.gram, W, &lw) != CUSOLVER_STATUS_SUCCESS)
+    ok = false;
+  if (ok) {
+    s.lwork = std::max(lw, 1);
+    al((void**)&s.work, sizeof(double) * s.lwork);
+  }
+  if (!ok) {
+    free_state(s);
+    return fail(c, HPSI_ENOMEM, "eigensolver workspace allocation failed");
+  }
+  s.ncap = N;
+  s.wcap = W;
+  return HPSI_OK;
+}
+
+int ensure_state(Context& c, EighState** out) {
+  EighState* s = reinterpret_cast<EighState*>(c.eigh);
+  if (!s) {
+    s = new EighState();
+    c.eigh = s;
+    if (cublasCreate(&s->blas) != CUBLAS_STATUS_SUCCESS) return fail(c, HPSI_ECUDA, "eigensolver: cublasCreate failed");
+    if (cusolverDnCreate(&s->solver) != CUSOLVER_STATUS_SUCCESS)
+      return fail(c, HPSI_ECUDA, "eigensolver: cusolverDnCreate failed");
+  }
+  cublasSetStream(s->blas, c.stream);
+  cusolverDnSetStream(s->solver, c.stream);
+  *out = s;
+  return HPSI_OK;
+}
+
+// cuSOLVER zheevdx on a copy of the matrix: lowest nwant pairs.
+int eigh_zheevdx(Context& c, EighState& s, const double2* a, int lda, int n, int nwant, double* w_out,
+                 double2* v_out) {
+  if (n > s.zcap) {
+    free_zheevdx(s);
+    int lw = 0, meig = 0;
+    if (cudaMalloc((void**)&s.acopy, sizeof(double2) * (size_t)n * n) != cudaSuccess ||
+        cudaMalloc((void**)&s.wfull, sizeof(double) * n) != cudaSuccess ||
+        cudaMalloc((void**)&s.zinfo, sizeof(int)) != cudaSuccess) {
+      free_zheevdx(s);
+      return fail(c, HPSI_ENOMEM, "eigensolver: zheevdx workspace allocation failed");
+    }
+    if (cusolverDnZheevdx_bufferSize(s.solver, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I,
+                                     CUBLAS_FILL_MODE_UPPER, n, reinterpret_cast<cuDoubleComplex*>(s.acopy), n, 0.0,
+                                     0.0, 1, n, &meig, s.wfull, &lw) != CUSOLVER_STATUS_SUCCESS) {
+      free_zheevdx(s);
+      return fail(c, HPSI_ECUDA, "eigensolver: zheevdx buffer size failed");
+    }
+    s.zlwork = std::max(lw, 1);
+    if (cudaMalloc((void**)&s.zwork, sizeof(double2) * s.zlwork) != cudaSuccess) {
+      free_zheevdx(s);
+      return fail(c, HPSI_ENOMEM, "eigensolver: zheevdx workspace allocation failed");
+    }
+    s.zcap = n;
+  }
+  cudaError_t err = cudaMemcpy2DAsync(s.acopy, sizeof(double2) * n, a, sizeof(double2) * lda, sizeof(double2) * n, n,
+                                      cudaMemcpyDeviceToDevice, c.stream);
+  if (err != cudaSuccess) return cuda_fail(c, err, "eigensolver: matrix copy");
+  int meig = 0;
+  if (cusolverDnZheevdx(s.solver, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I, CUBLAS_FILL_MODE_UPPER, n,
+                        reinterpret_cast<cuDoubleComplex*>(s.acopy), n, 0.0, 0.0, 1, nwant, &meig, s.wfull,
+                        reinterpret_cast<cuDoubleComplex*>(s.zwork), s.zlwork, s.zinfo) != CUSOLVER_STATUS_SUCCESS)
+    return fail(c, HPSI_ECUDA, "eigensolver: cusolverDnZheevdx failed");
+  err = cudaMemcpyAsync(w_out, s.wfull, sizeof(double) * nwant, cudaMemcpyDeviceToDevice, c.stream);
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(v_out, s.acopy, sizeof(double2) * (size_t)n * nwant, cudaMemcpyDeviceToDevice, c.stream);
+  if (err != cudaSuccess) return cuda_fail(c, err, "eigensolver: result copy");
+  int info = 0;
+  err = cudaMemcpyAsync(&info, s.zinfo, sizeof(int), cudaMemcpyDeviceToHost, c.stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(c.stream);
+  if (err != cudaSuccess) return cuda_fail(c, err, "eigensolver: zheevdx");
+  if (info != 0 || meig < nwant)
+    return fail(c, HPSI_ESINGULAR, "zheevdx of the reduced matrix failed, info " + std::to_string(info));
+  return HPSI_OK;
+}
+
+int tri_ctas(const Context& c, int n) {
+  int G = std::min(c.sm_count, std::max(8, (n + 3) / 4));
+  return std::max(1, std::min(G, n));
+}
+
+size_t tri_smem(int n, int G) {
+  const int R = (n + G - 1) / G;
+  return sizeof(double2) * ((size_t)(3 + R) * n + 2 * (size_t)R);
+}
+
+}  // namespace
+
+bool eigh_supported(const Context& c, int n) {
+  if (n < 1 || n > kMaxN) return false;
+  return tri_smem(n, tri_ctas(c, n)) <= c.smem_optin;
+}
+
+void eigh_release(Context& c) {
+  EighState* s = reinterpret_cast<EighState*>(c.eigh);
+  if (!s) return;
+  free_state(*s);
+  free_zheevdx(*s);
+  if (s->blas) cublasDestroy(s->blas);
+  if (s->solver) cusolverDnDestroy(s->solver);
+  delete s;
+  c.eigh = nullptr;
+}
+
+int eigh_lowest(Context& c, const double2* a, int lda, int n, int nwant, double* w_out, double2* v_out,
+                bool* fallback) {
+  *fallback = false;
+  if (n < 1 || nwant < 1 || nwant > n || lda < n) return fail(c, HPSI_EINVAL, "eigh_lowest: bad sizes");
+  if (!eigh_supported(c, n)) {
+    *fallback = true;
+    return HPSI_OK;
+  }
+  EighState* s = nullptr;
+  int rc = ensure_state(c, &s);
+  if (rc) return rc;
+  rc = grow(c, *s, n, nwant);
+  if (rc) return rc;
+  cudaError_t err;
+
+  // 1. tridiagonal reduction (cooperative)
+  const int G = tri_ctas(c, n);
+  const size_t smem = tri_smem(n, G);
+  err = cudaFuncSetAttribute(k_eh_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return cuda_fail(c, err, "eigh_lowest: smem attribute");
+  err = cudaMemsetAsync(s->bar, 0, sizeof(unsigned int) * 2 * kBarGen, c.stream);
+  if (err == cudaSuccess) err = cudaMemsetAsync(s->vref, 0, sizeof(double2) * (size_t)(n + kWY) * n, c.stream);
+  if (err == cudaSuccess) err = cudaMemsetAsync(s->tau, 0, sizeof(double2) * (n + kWY), c.stream);
+  if (err != cudaSuccess) return cuda_fail(c, err, "eigh_lowest: workspace reset");
+  err = cudaMemsetAsync(s->info, 0, sizeof(int) * 2, c.stream);
+  if (err != cudaSuccess) return cuda_fail(c, err, "eigh_lowest: status reset");
+  TriArgs ta{n, lda, G, a, s->d, s->e, s->e2, s->tau, s->vref, s->ybuf, s->rnext, s->spart, s->bar, c.d_err};
+  void* args[] = {&ta};
+  HPSI_LAUNCH(c, HPSI_K_EIGH,
+              (err = cudaLaunchCooperativeKernel((const void*)k_eh_tridiag, dim3(G), dim3(kTriThreads), args, smem,
+                                                 c.stream)));
+  if (err == cudaErrorCooperativeLaunchTooLarge) {   // the device cannot hold the grid at once
+    cudaGetLastError();
+    *fallback = true;
+    return HPSI_OK;
+  }
+  if (err != cudaSuccess) return cuda_fail(c, err, "eigh_lowest: tridiagonal reduction launch");
+  // 2. eigenvalues
+  HPSI_LAUNCH(c, HPSI_K_EIGH,
+              (k_eh_bisect<<<nwant, 32 * kBisWarps, 0, c.stream>>>(n, s->d, s->e, s->e2, nwant, s->lam)));
+  // 3. eigenvectors of T
+  const size_t ismem = sizeof(double) * 7 * (size_t)n + (size_t)n + 16;
+  if (ismem > 48 * 1024) {
+    err = cudaFuncSetAttribute(k_eh_invit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ismem);
+    if (err != cudaSuccess) return cuda_fail(c, err, "eigh_lowest: smem attribute");
+  }
+  HPSI_LAUNCH(c, HPSI_K_EIGH,
+              (k_eh_invit<<<nwant, 32, ismem, c.stream>>>(n, s->d, s->e, nwant, s->lam, s->Z, s->info + 1)));
+  //    Cholesky QR of Z
+  const double one = 1.0, zero = 0.0;
+  if (cublasDsyrk(s->blas, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_T, nwant, n, &one, s->Z, n, &zero, s->gram, nwant) !=
+      CUBLAS_STATUS_SUCCESS)
+    return fail(c, HPSI_ECUDA, "eigh_lowest: cublasDsyrk failed");
+  if (cusolverDnDpotrf(s->solver, CUBLAS_FILL_MODE_UPPER, nwant, s->gram, nwant, s->work, s->lwork, s->info) !=
+      CUSOLVER_STATUS_SUCCESS)
+    return fail(c, HPSI_ECUDA, "eigh_lowest: cusolverDnDpotrf failed");
+  if (cublasDtrsm(s->blas, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT, n, nwant, &one,
+                  s->gram, nwant, s->Z, n) != CUBLAS_STATUS_SUCCESS)
+    return fail(c, HPSI_ECUDA, "eigh_lowest: cublasDtrsm failed");
+  // 4. back-transformation, one compact-WY block of kWY reflectors at a time from the last:
+  //    X <- (I - V_k T_k V_k^H) X over rows k kWY + 1 .. n-1 (reflectors past n-2 are zero)
+  HPSI_LAUNCH(c, HPSI_K_EIGH,
+              (k_eh_widen<<<(unsigned)(((size_t)n * nwant + 255) / 256), 256, 0, c.stream>>>(n, nwant, s->Z, v_out)));
+  if (n > 1) {
+    const int K = (n - 1 + kWY - 1) / kWY;
+    const cuDoubleComplex zone = make_cuDoubleComplex(1.0, 0.0), zzero = make_cuDoubleComplex(0.0, 0.0),
+                          zmone = make_cuDoubleComplex(-1.0, 0.0);
+    auto Zc = [](double2* q) { return reinterpret_cast<cuDoubleComplex*>(q); };
+    if (cublasZgemmStridedBatched(s->blas, CUBLAS_OP_C, CUBLAS_OP_N, kWY, kWY, n - 1, &zone, Zc(s->vref + 1), n,
+                                  (long long)kWY * n, Zc(s->vref + 1), n, (long long)kWY * n, &zzero, Zc(s->wgram),
+                                  kWY, (long long)kWY * kWY, K) != CUBLAS_STATUS_SUCCESS)
+      return fail(c, HPSI_ECUDA, "eigh_lowest: reflector Gram matrices failed");
+    for (int k = K - 1; k >= 0; --k) {
+      const int r0 = k * kWY + 1, m = n - r0;
+      double2* V = s->vref + (size_t)k * kWY * n + r0;
+      if (cublasZgemm(s->blas, CUBLAS_OP_C, CUBLAS_OP_N, kWY, nwant, m, &zone, Zc(V), n, Zc(v_out + r0), n, &zzero,
+                      Zc(s->w1), kWY) != CUBLAS_STATUS_SUCCESS ||
+          (k_eh_trsv<<<(nwant + 3) / 4, 128, 0, c.stream>>>(nwant, s->wgram + (size_t)k * kWY * kWY,
+                                                             s->tau + (size_t)k * kWY, s->w1),
+           cudaGetLastError() != cudaSuccess) ||
+          cublasZgemm(s->blas, CUBLAS_OP_N, CUBLAS_OP_N, m, nwant, kWY, &zmone, Zc(V), n, Zc(s->w1), kWY, &zone,
+                      Zc(v_out + r0), n) != CUBLAS_STATUS_SUCCESS)
+        return fail(c, HPSI_ECUDA, "eigh_lowest: back-transformation GEMM failed");
+    }
+  }
+  err = cudaMemcpyAsync(w_out, s->lam, sizeof(double) * nwant, cudaMemcpyDeviceToDevice, c.stream);
+  if (err != cudaSuccess) return cuda_fail(c, err, "eigh_lowest: eigenvalue copy");
+  int info[2] = {0, 0};
+  err = cudaMemcpyAsync(info, s->info, sizeof(int) * 2, cudaMemcpyDeviceToHost, c.stream);
+  if (err != cudaSuccess) return cuda_fail(c, err, "eigh_lowest: status copy");
+  rc = check_device_error(c);
+  if (rc) return rc;
+  if (info[0] != 0 || info[1] != 0) *fallback = true;   // inverse iteration lost a vector: caller falls back
+  return HPSI_OK;
+}
+
+int eigh_reduced(Context& c, const double2* a, int lda, int n, int nwant, double* w_out, double2* v_out) {
+  if (c.eigensolver == 1) {
+    bool fallback = false;
+    const int rc = eigh_lowest(c, a, lda, n, nwant, w_out, v_out, &fallback);
+    if (rc || !fallback) return rc;
+  }
+  EighState* s = nullptr;
+  const int rc = ensure_state(c, &s);
+  if (rc) return rc;
+  return eigh_zheevdx(c, *s, a, lda, n, nwant, w_out, v_out);
+}
+
+}  // namespace hpsi
+
+extern "C" int hpsi_eigh_lowest(hpsi_ctx* ctx, int n, const void* a, int lda, int nwant, void* w_out, void* v_out) {
+  if (!ctx) return HPSI_EINVAL;
+  hpsi::Context& c = ctx->c;
+  if (!a || !w_out || !v_out) return hpsi::fail(c, HPSI_EINVAL, "hpsi_eigh_lowest: null pointer");
+  if (n < 1 || nwant < 1 || nwant > n || lda < n) return hpsi::fail(c, HPSI_EINVAL, "hpsi_eigh_lowest: bad sizes");
+  return hpsi::eigh_reduced(c, static_cast<const double2*>(a), lda, n, nwant, static_cast<double*>(w_out),
+                            static_cast<double2*>(v_out));
+}

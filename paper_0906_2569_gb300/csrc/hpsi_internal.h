@@ -129,6 +129,8 @@ struct Context {
   int final_fp64 = 1;                  // mixed davidson_solve: final Rayleigh quotients with the float64 H
   int basis_factor = 4;                // Davidson: the reduced basis grows to basis_factor * N vectors
   int autotune = 1;                    // time the fast-path plans on the first apply of a problem
+  int eigensolver = 1;                 // reduced eigenproblems: 1 = the library's kernels, 0 = cuSOLVER
+  void* eigh = nullptr;                // eigensolver handles and work buffers (eigh.cu)
   cudaStream_t cap_stream = nullptr;   // internal stream for graph capture
   GraphCache graph;
   // launch accounting (always) and per-launch event timing (HPSI_OPT_KERNEL_TIMING)
@@ -194,6 +196,15 @@ int check_device_error(Context& c);   // synchronizes; HPSI_ETIMEOUT if a bounde
 int davidson_run(Context& c, int ik, int nbnd, double tol, int maxiter, double2* psi, double* eig,
                  int* iters, double* resnorm);
 void davidson_release(Context& c);
+
+// ---- reduced Hermitian eigenproblem (eigh.cu) ----
+bool eigh_supported(const Context& c, int n);
+// Library kernels; *fallback is set (and nothing is wrong) when the caller should use cuSOLVER.
+int eigh_lowest(Context& c, const double2* a, int lda, int n, int nwant, double* w_out, double2* v_out,
+                bool* fallback);
+// The solver chosen by HPSI_OPT_EIGENSOLVER, with cuSOLVER zheevdx behind the library kernels.
+int eigh_reduced(Context& c, const double2* a, int lda, int n, int nwant, double* w_out, double2* v_out);
+void eigh_release(Context& c);
 
 }  // namespace hpsi
 

@@ -5,6 +5,10 @@ cell (or the cell named by ``--config``) at the chosen precision.  Two warm-up a
 first (the first one runs the autotuner); the steady-state applications are bracketed by
 cudaProfilerStart / cudaProfilerStop, so a profiler started with ``--profile-from-start off``
 captures only them.
+
+With ``--eigh N`` it instead solves the reduced Hermitian eigenproblem of order N (lowest
+``--nwant`` pairs) on a seeded random matrix of the scale of a Davidson reduced H, the same way:
+two warm-up solves, then ``--reps`` bracketed ones.
 """
 from __future__ import annotations
 
@@ -22,10 +26,15 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--reps", type=int, default=1)
     ap.add_argument("--nbnd", type=int, default=0)
+    ap.add_argument("--eigh", type=int, default=0)
+    ap.add_argument("--nwant", type=int, default=160)
     args = ap.parse_args()
     import torch
     import workloads
     from paper_0906_2569_gb300 import binding as B
+    if args.eigh:
+        eigh_case(args, torch, workloads, B)
+        return
     p = workloads.CONFIGS[args.config]()
     nb = args.nbnd or p.nbnd
     k = p.kpts[0]
@@ -46,6 +55,26 @@ def main():
     B.hpsi_sync(ctx)
     torch.cuda.profiler.stop()
     print("ok", args.config, args.precision, nb, float(y.abs().sum()))
+
+
+def eigh_case(args, torch, workloads, B):
+    import numpy as np
+    p = workloads.config1()
+    ctx = B.hpsi_setup(p.lattice, p.ecut, [p.kpts[0]], p.fft, np.zeros(p.fft), None, None, B.HPSI_FP64,
+                       torch.cuda.current_stream().cuda_stream)
+    n, nw = args.eigh, min(args.nwant, args.eigh)
+    a = torch.from_numpy(np.ascontiguousarray(workloads.hermitian_matrix(n, n, scale=20.0).T)).cuda()
+    w = torch.empty(nw, dtype=torch.float64, device="cuda")
+    v = torch.empty((nw, n), dtype=torch.complex128, device="cuda")
+    for _ in range(2):
+        B.hpsi_eigh_lowest(ctx, a, n, n, nw, w, v)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    for _ in range(args.reps):
+        B.hpsi_eigh_lowest(ctx, a, n, n, nw, w, v)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    print("ok eigh", n, nw, float(w.sum()))
 
 
 if __name__ == "__main__":

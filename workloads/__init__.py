@@ -281,6 +281,21 @@ def random_block(npw: int, nbnd: int, seed: int) -> np.ndarray:
     return (rng.standard_normal((nbnd, npw)) + 1j * rng.standard_normal((nbnd, npw))) / math.sqrt(2.0)
 
 
+def hermitian_matrix(n: int, seed: int, spectrum=None, scale: float = 1.0) -> np.ndarray:
+    """Seeded dense Hermitian test matrix [n][n] (reduced-problem tests of the eigensolver).
+
+    Without ``spectrum``: (B + B^H) / 2 for a complex Gaussian B, times ``scale``.  With it: U diag(spectrum) U^H
+    for a Haar-like unitary U (QR of a complex Gaussian), so repeated values give exact degeneracies."""
+    rng = np.random.default_rng(seed)
+    b = (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / math.sqrt(2.0)
+    if spectrum is None:
+        return scale * (b + b.conj().T) / 2.0
+    q, r = np.linalg.qr(b)
+    q = q * (np.diag(r) / np.abs(np.diag(r)))[None, :]
+    a = (q * np.asarray(spectrum, dtype=float)[None, :]) @ q.conj().T
+    return (a + a.conj().T) / 2.0
+
+
 CONFIGS = {
     "c1": config1,
     "c2": config2,
