@@ -41,6 +41,9 @@ namespace {
 
 constexpr int kTriThreads = 256;                     // threads per CTA of the reduction
 constexpr int kMaxN = 1024;                          // largest n handled here
+constexpr int kMaxParts = 16;                        // row parts per CTA and column
+constexpr int kMaxPartsPerRow = 4;
+constexpr int kLoadK = (kMaxN + 255) / 256;          // row elements per thread of the column loads
 constexpr long long kBarrierLimit = 2000000000LL;    // clock cycles (about 1 s) per barrier wait
 constexpr int kInvIters = 3;                         // inverse-iteration solves per eigenvector
 
@@ -87,59 +90,87 @@ struct TriArgs {
   double2* vref;        // [n][n] row j: v_j at columns j+1..n-1
   double2* ybuf;        // [2][n] y of the last two columns
   double2* rnext;       // [2][n] the next row, published by its owner
-  double* spart;        // [2][G] per-CTA parts of s
-  unsigned int* bar;    // [2 * kBarGen] barrier count and generation
+  double2* rowcoef;     // [2][4] coefficients of the published row: A, B, Q, (E, 0)
+  double2* vscale;      // [n] scale of each reflector
+  double* sacc;         // [3] s of the last columns, accumulated by atomics
+  unsigned int* bar;    // barrier arrival counter (zero at launch)
   int* err;             // device error word
 };
 
-// Grid-wide barrier of a cooperative launch.  bar[0] counts arrivals, bar[kBarGen] (another
-// 128-byte line, so waiting CTAs do not poll the line the arrivals update) is the generation.
-// Returns false when this CTA's wait ran out or another CTA reported a failure (the error word is
-// then set).
-constexpr int kBarGen = 32;
-
-__device__ bool grid_barrier(unsigned int* bar, unsigned int G, int* err) {
+// Grid-wide barrier of a cooperative launch on a monotonic arrival counter: barrier number k
+// (k = 1, 2, ...) is passed once the counter reaches k G.  Each CTA adds 1 with release semantics
+// after a CTA barrier and polls with acquire loads, so neither a reset nor a generation flip sits
+// between the last arrival and the release.  Returns false when this CTA's wait ran out or another
+// CTA reported a failure (the error word is then set).
+__device__ bool grid_barrier(unsigned int* count, unsigned int target, int* err) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned int* gen = bar + kBarGen;
-    const unsigned int g0 = *gen;
-    __threadfence();
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
     int good = 1;
-    if (atomicAdd(bar, 1u) == G - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + kBarGen, 1u);
-    } else {
-      const long long t0 = clock64();
-      unsigned int spins = 0;
-      while (*gen == g0) {
-        if ((++spins & 255u) == 0u &&
-            (*(volatile int*)err != 0 || clock64() - t0 > kBarrierLimit)) {
-          atomicCAS(err, 0, 3);
-          good = 0;
-          break;
-        }
+    const long long t0 = clock64();
+    unsigned int spins = 0;
+    for (;;) {
+      unsigned int v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+      if ((int)(v - target) >= 0) break;
+      if ((++spins & 255u) == 0u && (*(volatile int*)err != 0 || clock64() - t0 > kBarrierLimit)) {
+        atomicCAS(err, 0, 3);
+        good = 0;
+        break;
       }
     }
-    __threadfence();
     ok = good && *(volatile int*)err == 0;
   }
   __syncthreads();
   return ok != 0;
 }
 
-// Column j keeps the previous reflector in the folded form used by the updates: with u the
-// updated row j-1 (so v_{j-1}[c] = conj(u[c]) scale for c > j, v_{j-1}[j] = 1) and
-// w = tau y - hh v (hh = |tau|^2 s / 2), the rank-2 update of element (r, c), c > j, is
-//   a -= P_r u[c] + Q_r conj(y[c]),  P_r = (tau y_r - 2 hh v_r) conj(scale),  Q_r = conj(tau) v_r,
-// so neither w nor v is formed as a vector; the new row's reflector enters the product with A as
-// conj(u[c]) and its scale is applied to each row sum at the end, which lets one warp compute the
-// scalars of the reflector while the others update the rows.
+__device__ __forceinline__ int biased_exp(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7ff); }
+
+// 1/x by two Newton-Raphson steps r <- r (2 - x r) from a float32 seed (quadratic convergence:
+// 2^-23 -> 2^-46 -> 2^-92); plain division outside |x| in [2^-100, 2^100].  Four float64
+// operations instead of the 600-cycle division sequence.
+__device__ __forceinline__ double recip_nr(double x) {
+  const int ex = biased_exp(x);
+  if (ex < 1023 - 100 || ex > 1023 + 100) return 1.0 / x;
+  double r = (double)__frcp_rn((float)x);
+  r = fma(r, fma(-x, r, 1.0), r);
+  r = fma(r, fma(-x, r, 1.0), r);
+  return r;
+}
+
+// 1/sqrt(x) for x > 0 by two Newton steps y <- y (3/2 - (x/2) y^2) from a float32 seed; library
+// sqrt and division outside x in [2^-100, 2^100].
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  const int ex = biased_exp(x);
+  if (ex < 1023 - 100 || ex > 1023 + 100) return 1.0 / sqrt(x);
+  const double h = 0.5 * x;
+  double y = (double)rsqrtf((float)x);
+  y = y * fma(-h, y * y, 1.5);
+  y = y * fma(-h, y * y, 1.5);
+  return y;
+}
+
+__device__ __forceinline__ double2 cmulc2(double2 a, double2 b) {   // a * conj(b)
+  return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -a.x * b.y));
+}
+
+// Column j keeps the previous reflector in a folded form: with u the updated row j-1 (so
+// v_{j-1}[c] = conj(u[c]) scale for c > j, v_{j-1}[j] = 1) and w = tau y - hh v (hh = |tau|^2 s / 2,
+// s = v^H y), the rank-2 update of element (r, c), c > j, is
+//   a -= P_r u[c] + Q_r conj(y[c]),  P_r = A_r - hh B_r,  A_r = tau y_r conj(scale),
+//   B_r = 2 v_r conj(scale),  Q_r = conj(tau) v_r,
+// and the diagonal element of row j loses E_j - 2 hh with E_j = 2 Re(tau y_j).  A, B, Q (and E)
+// are formed for every row before the barrier; after it only hh is new.  The new reflector enters
+// the product with A as conj(u) and its scale is applied to each row sum at the end, so one warp
+// computes the reflector's scalars while the others update the rows.  s is accumulated across
+// CTAs by float64 atomics.  The own rows' work is cut into parts spread over the eight warps
+// (two per scheduler), since every scheduler issues float64 at its own fixed rate.
 __global__ void __launch_bounds__(kTriThreads, 1) k_eh_tridiag(TriArgs p) {
   extern __shared__ double2 sm[];
   constexpr int NW = kTriThreads / 32;
-  constexpr int kChainWarp = NW - 1;          // computes beta, tau, scale during the row updates
+  constexpr int kChainWarp = NW - 1;
   const int n = p.n, G = p.G, g = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int R = g < n ? (n - 1 - g) / G + 1 : 0;
   const int Rmax = (n + G - 1) / G;
@@ -147,63 +178,76 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_eh_tridiag(TriArgs p) {
   double2* ubuf1 = sm + n;
   double2* yP = sm + 2 * n;
   double2* rows = sm + 3 * n;
-  double2* racc = rows + (size_t)Rmax * n;    // [Rmax] row sums with conj(u)
-  double2* ra1 = racc + Rmax;                 // [Rmax] row element at column j+1
+  double2* cA = rows + (size_t)Rmax * n;   // [Rmax] A_r, B_r, Q_r of the own rows
+  double2* cB = cA + Rmax;
+  double2* cQ = cB + Rmax;
+  double2* pacc = cQ + Rmax;               // [kMaxParts] part sums with conj(u)
+  double2* pa1 = pacc + kMaxParts;         // [kMaxParts] element at column j+1 (part 0 of a row)
   __shared__ double red[NW];
-  __shared__ double sP_sh;
-  __shared__ double2 alpha_sh, tau_sh, scale_sh;
-  __shared__ double beta_sh;
+  __shared__ double2 alpha_sh, tau_sh, scale_sh, tcs_sh, cts_sh;
+  __shared__ double beta_sh, s2_sh;
 
   for (int lr = 0; lr < R; ++lr) {
     const int r = g + lr * G;
     for (int c = tid; c < n; c += kTriThreads) rows[(size_t)lr * n + c] = herm_at(p.a, p.lda, r, c);
   }
-  double2 tauP = make_double2(0.0, 0.0), scP = make_double2(0.0, 0.0);
+  double2 scP = make_double2(0.0, 0.0);
+  double tauAbs2 = 0.0;   // |tau_{j-1}|^2
   for (int j = 0; j < n; ++j) {
     double2* uC = (j & 1) ? ubuf1 : ubuf0;   // this column's reflector, unscaled
     double2* uP = (j & 1) ? ubuf0 : ubuf1;   // previous column's
-    // (A) row j (updated through column j-2 by its owner) and y of column j-1, into shared memory
-    for (int c = j + tid; c < n; c += kTriThreads) {
-      if (j == 0) {
-        uC[c] = herm_at(p.a, p.lda, 0, c);
-      } else {
-        uC[c] = __ldcg(&p.rnext[((j - 1) & 1) * n + c]);
-        yP[c] = __ldcg(&p.ybuf[((j - 1) & 1) * n + c]);
-      }
-    }
-    if (j > 0 && wid == 0) {
-      double s = 0.0;
-      for (int q = lane; q < G; q += 32) s += __ldcg(&p.spart[((j - 1) & 1) * G + q]);
-      s = warp_sum(s);
-      if (lane == 0) sP_sh = s;
-    }
-    __syncthreads();
-    const double hh = 0.5 * (tauP.x * tauP.x + tauP.y * tauP.y) * (j > 0 ? sP_sh : 0.0);
-    const double2 ctauP = make_double2(tauP.x, -tauP.y);
-    const double2 cscP = make_double2(scP.x, -scP.y);
-    // (B) column j-1's update of row j; its diagonal; the reflector of column j (uC[c], c > j)
-    double sig = 0.0, dj = 0.0;
-    double2 Pp = make_double2(0.0, 0.0), P = Pp, Q = Pp;
-    if (j > 0) {
-      const double2 yj = yP[j];
-      Pp = make_double2(tauP.x * yj.x - tauP.y * yj.y - 2.0 * hh, tauP.x * yj.y + tauP.y * yj.x);
-      P = cmul(Pp, cscP);
-      Q = ctauP;     // v_{j-1}[j] = 1
-    }
-    for (int c = j + tid; c < n; c += kTriThreads) {
-      double2 a = uC[c];
+    // (A) row j and y of column j-1 into shared memory; s, hh and row j's coefficients (every load
+    //     is issued before the first use)
+    double hh = 0.0;
+    double2 Pj = make_double2(0.0, 0.0), Qj = Pj;
+    double Ej = 0.0;
+    {
+      double sv = 0.0;
+      double2 A = Pj, B = Pj;
       if (j > 0) {
-        const double2 yc = yP[c];
-        if (c == j) {   // conj(v_{j-1}[j]) = 1
-          a.x -= Pp.x + Q.x * yc.x + Q.y * yc.y;
-          a.y -= Pp.y + Q.y * yc.x - Q.x * yc.y;
-        } else {
-          a = rank2_sub(a, P, make_double2(uP[c].x, -uP[c].y), Q, yc);
+        const double2* rc = p.rowcoef + ((j - 1) & 1) * 4;
+        sv = __ldcg(&p.sacc[(j - 1) % 3]);
+        A = __ldcg(&rc[0]);
+        B = __ldcg(&rc[1]);
+        Qj = __ldcg(&rc[2]);
+        Ej = __ldcg(&rc[3]).x;
+      }
+      double2 ra[kLoadK], ya[kLoadK];
+#pragma unroll
+      for (int k = 0; k < kLoadK; ++k) {
+        const int c = j + tid + k * kTriThreads;
+        if (c < n) {
+          if (j == 0) {
+            ra[k] = herm_at(p.a, p.lda, 0, c);
+          } else {
+            ra[k] = __ldcg(&p.rnext[((j - 1) & 1) * n + c]);
+            ya[k] = __ldcg(&p.ybuf[((j - 1) & 1) * n + c]);
+          }
         }
       }
+#pragma unroll
+      for (int k = 0; k < kLoadK; ++k) {
+        const int c = j + tid + k * kTriThreads;
+        if (c < n) {
+          uC[c] = ra[k];
+          if (j > 0) yP[c] = ya[k];
+        }
+      }
+      if (j > 0) {
+        hh = 0.5 * tauAbs2 * sv;
+        Pj = make_double2(fma(-hh, B.x, A.x), fma(-hh, B.y, A.y));
+      }
+    }
+    if (g == 0 && tid == 0) p.sacc[(j + 1) % 3] = 0.0;   // last read at the start of column j-1
+    __syncthreads();
+    // (B) column j-1's update of row j, its diagonal, the reflector's vector uC[c] (c > j) and sigma
+    double sig = 0.0, dj = 0.0;
+    for (int c = j + tid; c < n; c += kTriThreads) {
+      double2 a = uC[c];
       if (c == j) {
-        dj = a.x;
+        dj = a.x - (Ej - 2.0 * hh);
       } else {
+        if (j > 0) a = rank2_sub(a, Pj, make_double2(uP[c].x, -uP[c].y), Qj, yP[c]);
         uC[c] = a;
         if (c == j + 1) alpha_sh = make_double2(a.x, -a.y);
         else sig = fma(a.x, a.x, fma(a.y, a.y, sig));
@@ -216,124 +260,148 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_eh_tridiag(TriArgs p) {
     sig = warp_sum(sig);
     if (lane == 0) red[wid] = sig;
     __syncthreads();
-    // (C) one warp: beta, tau, scale;  the others: column j-1's update of the own rows r > j and
-    //     their products with conj(u) (columns >= j+2) and their element at column j+1
+    // (C) the chain warp: beta, tau, scale of column j;  all warps: own rows r > j, in parts
     if (wid == kChainWarp) {
+      double sg = lane < NW ? red[lane] : 0.0;
+      sg += __shfl_xor_sync(0xffffffffu, sg, 4);
+      sg += __shfl_xor_sync(0xffffffffu, sg, 2);
+      sg += __shfl_xor_sync(0xffffffffu, sg, 1);
       if (lane == 0) {
-        double sigma = 0.0;
-        for (int q = 0; q < NW; ++q) sigma += red[q];
         const double ar = alpha_sh.x, ai = alpha_sh.y;
         double beta;
         double2 tau, scale;
-        if (sigma == 0.0 && ai == 0.0) {
+        if ((__double_as_longlong(sg) << 1) == 0 && (__double_as_longlong(ai) << 1) == 0) {
           beta = ar;
           tau = make_double2(0.0, 0.0);
           scale = make_double2(0.0, 0.0);
         } else {
-          beta = -copysign(sqrt(ar * ar + ai * ai + sigma), ar);
-          const double ib = 1.0 / beta;
-          tau = make_double2((beta - ar) * ib, -ai * ib);
-          const double dr = ar - beta, iden = 1.0 / (dr * dr + ai * ai);
+          const double S = fma(ar, ar, fma(ai, ai, sg));
+          const double y = rsqrt_nr(S);
+          const bool neg = __double_as_longlong(ar) < 0;     // beta = -sign(ar) |x|
+          beta = neg ? S * y : -(S * y);
+          const double ib = neg ? y : -y;                    // 1 / beta
+          tau = make_double2(fma(-ar, ib, 1.0), -ai * ib);
+          const double dr = ar - beta;
+          const double iden = recip_nr(fma(dr, dr, ai * ai));
           scale = make_double2(dr * iden, -ai * iden);       // 1 / (alpha - beta)
         }
         tau_sh = tau;
         scale_sh = scale;
         beta_sh = beta;
+        tcs_sh = cmulc2(tau, scale);                                         // tau conj(scale)
+        cts_sh = cmul(make_double2(tau.x, -tau.y), scale);                   // conj(tau) scale
+        s2_sh = 2.0 * fma(scale.x, scale.x, scale.y * scale.y);              // 2 |scale|^2
       }
-    } else {
-      for (int lr = wid; lr < R; lr += NW - 1) {
-        const int r = g + lr * G;
-        if (r <= j) continue;
-        double2* row = rows + (size_t)lr * n;
-        double2 P = make_double2(0.0, 0.0), Q = make_double2(0.0, 0.0);
-        if (j > 0) {
-          const double2 ur = uP[r], yr = yP[r];
-          const double2 vr = cmul(make_double2(ur.x, -ur.y), scP);      // v_{j-1}[r], r > j
-          const double2 ty = cmul(tauP, yr);
-          P = cmul(make_double2(ty.x - 2.0 * hh * vr.x, ty.y - 2.0 * hh * vr.y), cscP);
-          Q = cmul(ctauP, vr);
-        }
-        double ax = 0.0, ay = 0.0, bx = 0.0, by = 0.0;
-        double2 a1 = make_double2(0.0, 0.0);
-        for (int c = j + 1 + lane; c < n; c += 64) {
-          const int c2 = c + 32;
-          const bool two = c2 < n;
-          double2 a = row[c];
-          double2 b = two ? row[c2] : make_double2(0.0, 0.0);
-          if (j > 0) {
-            a = rank2_sub(a, P, make_double2(uP[c].x, -uP[c].y), Q, yP[c]);
-            row[c] = a;
-            if (two) {
-              b = rank2_sub(b, P, make_double2(uP[c2].x, -uP[c2].y), Q, yP[c2]);
-              row[c2] = b;
+    }
+    {
+      int Ra = 0;   // own rows r > j are lr = first .. R-1
+      const int first = j >= g ? (j - g) / G + 1 : 0;
+      Ra = R - first;
+      if (Ra > 0) {
+        const int q = min(min((NW + Ra - 1) / Ra, kMaxParts / Ra), kMaxPartsPerRow);
+        const int m = n - 1 - j;
+        const int chunk = ((m + q - 1) / q + 31) & ~31;
+        for (int part = wid; part < Ra * q; part += NW) {
+          const int lr = first + part / q, k = part % q;
+          const int r = g + lr * G;
+          double2* row = rows + (size_t)lr * n;
+          const double2 P = make_double2(fma(-hh, cB[lr].x, cA[lr].x), fma(-hh, cB[lr].y, cA[lr].y));
+          const double2 Q = cQ[lr];
+          const int c0 = j + 1 + k * chunk, c1 = min(n, c0 + chunk);
+          double ax = 0.0, ay = 0.0;
+          double2 a1 = make_double2(0.0, 0.0);
+          for (int c = c0 + lane; c < c1; c += 32) {
+            double2 a = row[c];
+            if (j > 0) {
+              a = rank2_sub(a, P, make_double2(uP[c].x, -uP[c].y), Q, yP[c]);
+              row[c] = a;
             }
+            if (c == j + 1) {
+              a1 = a;
+            } else {
+              const double2 u = uC[c];            // a * conj(u)
+              ax = fma(a.x, u.x, fma(a.y, u.y, ax));
+              ay = fma(a.y, u.x, fma(-a.x, u.y, ay));
+            }
+            if (r == j + 1) p.rnext[(j & 1) * n + c] = a;
           }
-          if (c == j + 1) {
-            a1 = a;
-          } else {
-            const double2 u = uC[c];            // a * conj(u)
-            ax = fma(a.x, u.x, fma(a.y, u.y, ax));
-            ay = fma(a.y, u.x, fma(-a.x, u.y, ay));
+          ax = warp_sum(ax);
+          ay = warp_sum(ay);
+          if (lane == 0) {
+            pacc[part] = make_double2(ax, ay);
+            pa1[part] = a1;
           }
-          if (two) {
-            const double2 u = uC[c2];
-            bx = fma(b.x, u.x, fma(b.y, u.y, bx));
-            by = fma(b.y, u.x, fma(-b.x, u.y, by));
-          }
-          if (r == j + 1) {
-            p.rnext[(j & 1) * n + c] = a;
-            if (two) p.rnext[(j & 1) * n + c2] = b;
-          }
-        }
-        ax += bx;
-        ay += by;
-        ax = warp_sum(ax);
-        ay = warp_sum(ay);
-        if (lane == 0) {
-          racc[lr] = make_double2(ax, ay);
-          ra1[lr] = a1;
         }
       }
     }
     __syncthreads();
-    // (D) y_j[r] = a1 + scale * racc for the own rows, their part of s_j = v_j^H y_j, outputs
+    // (D) warp 0: y_j[r] = a1 + scale * sum for the own rows and their part of s_j = v_j^H y_j;
+    //     warp 1: the own rows' A, B, Q for column j+1 (and E for row j+1, published with it);
+    //     the owner of row j stores v_j; CTA 0 the outputs of column j
     const double2 tauC = tau_sh, scC = scale_sh;
-    if (wid == 0) {
+    const double2 cscC = make_double2(scC.x, -scC.y);
+    const int first = j >= g ? (j - g) / G + 1 : 0;
+    const int Ra = R - first;
+    const int q = Ra > 0 ? min(min((NW + Ra - 1) / Ra, kMaxParts / Ra), kMaxPartsPerRow) : 1;
+    if (wid <= 1) {
+      const double2 tcs = tcs_sh, cts = cts_sh;
+      const double s2 = s2_sh;
       double sp = 0.0;
-      const double2 cscC = make_double2(scC.x, -scC.y);
-      for (int lr = lane; lr < R; lr += 32) {
-        const int r = g + lr * G;
-        if (r <= j) continue;
-        const double2 y = make_double2(ra1[lr].x + scC.x * racc[lr].x - scC.y * racc[lr].y,
-                                       ra1[lr].y + scC.x * racc[lr].y + scC.y * racc[lr].x);
-        p.ybuf[(j & 1) * n + r] = y;
-        const double2 cv = r == j + 1 ? make_double2(1.0, 0.0) : cmul(uC[r], cscC);   // conj(v_j[r])
-        sp += cv.x * y.x - cv.y * y.y;
+      for (int i = lane; i < Ra; i += 32) {
+        const int lr = first + i, r = g + lr * G;
+        double2 acc = pacc[i * q];
+        for (int k = 1; k < q; ++k) {
+          acc.x += pacc[i * q + k].x;
+          acc.y += pacc[i * q + k].y;
+        }
+        const double2 a1 = pa1[i * q];
+        const double2 y = make_double2(fma(scC.x, acc.x, fma(-scC.y, acc.y, a1.x)),
+                                       fma(scC.x, acc.y, fma(scC.y, acc.x, a1.y)));
+        const bool lead = r == j + 1;                       // v_j[j+1] = 1, else v_j[r] = conj(u_r) scale
+        const double2 cu = make_double2(uC[r].x, -uC[r].y);
+        if (wid == 0) {
+          p.ybuf[(j & 1) * n + r] = y;
+          // Re(conj(v_r) y_r)
+          sp += lead ? y.x : fma(uC[r].x, fma(cscC.x, y.x, -cscC.y * y.y), -uC[r].y * fma(cscC.x, y.y, cscC.y * y.x));
+        } else {
+          const double2 A = cmul(y, tcs);
+          const double2 B = lead ? make_double2(2.0 * scC.x, -2.0 * scC.y) : make_double2(s2 * cu.x, s2 * cu.y);
+          const double2 Q = lead ? make_double2(tauC.x, -tauC.y) : cmul(cu, cts);
+          cA[lr] = A;
+          cB[lr] = B;
+          cQ[lr] = Q;
+          if (lead) {
+            double2* rc = p.rowcoef + (j & 1) * 4;
+            rc[0] = A;
+            rc[1] = B;
+            rc[2] = Q;
+            rc[3] = make_double2(2.0 * fma(tauC.x, y.x, -tauC.y * y.y), 0.0);          // E = 2 Re(tau y)
+          }
+        }
       }
-      sp = warp_sum(sp);
-      if (lane == 0) {
-        p.spart[(j & 1) * G + g] = sp;
-        if (g == 0) {
-          p.d[j] = dj;
-          p.e[j] = beta_sh;
-          p.e2[j] = beta_sh * beta_sh;
-          p.tau[j] = tauC;
+      if (wid == 0) {
+        sp = warp_sum(sp);
+        if (lane == 0) {
+          atomicAdd(&p.sacc[j % 3], sp);
+          if (g == 0) {
+            p.d[j] = dj;
+            p.e[j] = beta_sh;
+            p.e2[j] = beta_sh * beta_sh;
+            p.tau[j] = tauC;
+            p.vscale[j] = scC;
+          }
         }
       }
     }
-    if (g == j % G) {   // the owner of row j stores v_j for the back-transformation
-      for (int c = j + 1 + tid; c < n; c += kTriThreads) {
-        const double2 u = uC[c];
-        p.vref[(size_t)j * n + c] = c == j + 1 ? make_double2(1.0, 0.0) : cmul(make_double2(u.x, -u.y), scC);
-      }
+    if (g == j % G) {   // the owner of row j stores u_j; k_eh_vscale forms v_j = conj(u_j) scale_j
+      for (int c = j + 2 + tid; c < n; c += kTriThreads) p.vref[(size_t)j * n + c] = uC[c];
     }
-    tauP = tauC;
+    tauAbs2 = fma(tauC.x, tauC.x, tauC.y * tauC.y);
     scP = scC;
-    if (!grid_barrier(p.bar, (unsigned)G, p.err)) return;
+    if (!grid_barrier(p.bar, (unsigned)(G * (j + 1)), p.err)) return;
   }
 }
 
-__device__ __forceinline__ int biased_exp(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7ff); }
 
 // Gershgorin interval [lo, hi] of T, |T| bound and largest e^2, reduced over a warp.
 __device__ void gershgorin(int n, const double* __restrict__ d, const double* __restrict__ e, double* lo, double* hi,
@@ -357,39 +425,47 @@ __device__ void gershgorin(int n, const double* __restrict__ d, const double* __
   *emax2 = m;
 }
 
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+
 // Number of eigenvalues of T below sigma: the sign changes of the leading principal minors
-// p_k of T - sigma I (p_k = (d_k - sigma) p_{k-1} - e_{k-1}^2 p_{k-2}), kept scaled by powers of
-// two; a minor that is exactly zero is taken as -pivmin times the previous one.  Signs, zero tests
-// and the scaling test read the bit patterns (integer pipe); only the recurrence is float64.
-__device__ int sturm_count(int n, const double* __restrict__ d, const double* __restrict__ e2, double sigma,
-                           double pivmin) {
+// p_k of T - sigma I (p_k = (d_k - sigma) p_{k-1} - e_{k-1}^2 p_{k-2}).  Only the recurrence is
+// float64; signs, zero tests and scaling work on the bit patterns (integer pipe).  A minor that is
+// exactly zero becomes a tiny value of the sign opposite to the previous one (a pivmin-style
+// perturbation of the diagonal); every 8 steps the pair is scaled by 2^-+400 through its exponent
+// fields (a partner too small to scale down is negligible and flushed to zero; a subnormal is left
+// as it is).
+__device__ int sturm_count(int n, const double* __restrict__ d, const double* __restrict__ e2, double sigma) {
+  constexpr long long kSign = (long long)0x8000000000000000ULL;
+  constexpr long long kTiny = 0x0910000000000000LL;             // 2^-878
+  constexpr long long kShift = 400LL << 52;
   double pm = 1.0, p = d[0] - sigma;
-  if ((__double_as_longlong(p) << 1) == 0) p = -pivmin;
-  int cnt = __double_as_longlong(p) < 0;
+  if ((dbits(p) << 1) == 0) p = __longlong_as_double(kSign | kTiny);
+  int cnt = dbits(p) < 0;
   for (int k = 1; k < n; ++k) {
     double pn = fma(d[k] - sigma, p, -e2[k - 1] * pm);
-    if ((__double_as_longlong(pn) << 1) == 0) pn = -pivmin * p;
-    cnt += (__double_as_longlong(pn) ^ __double_as_longlong(p)) < 0;
+    if ((dbits(pn) << 1) == 0) pn = __longlong_as_double(((dbits(p) & kSign) ^ kSign) | kTiny);
+    cnt += (dbits(pn) ^ dbits(p)) < 0;
     pm = p;
     p = pn;
-    if ((k & 3) == 0) {
-      const int ex = max(biased_exp(p), biased_exp(pm));
+    if ((k & 7) == 0) {
+      const int ep = biased_exp(p), em = biased_exp(pm), ex = max(ep, em);
       if (ex > 1023 + 400) {
-        p *= 0x1p-400;
-        pm *= 0x1p-400;
+        p = __longlong_as_double(ep > 400 ? dbits(p) - kShift : dbits(p) & kSign);
+        pm = __longlong_as_double(em > 400 ? dbits(pm) - kShift : dbits(pm) & kSign);
       } else if (ex < 1023 - 400) {
-        p *= 0x1p400;
-        pm *= 0x1p400;
+        if (ep > 0) p = __longlong_as_double(dbits(p) + kShift);
+        if (em > 0) pm = __longlong_as_double(dbits(pm) + kShift);
       }
     }
   }
   return cnt;
 }
 
+
 // One CTA of kBisWarps warps per wanted eigenvalue i: (32 kBisWarps + 1)-way multisection of an
 // interval with count(lo) <= i < count(hi), one Sturm count per thread and round, so the float64
 // recurrences run on every sub-partition of the SM at once.
-constexpr int kBisWarps = 4;
+constexpr int kBisWarps = 2;
 __global__ void __launch_bounds__(32 * kBisWarps) k_eh_bisect(int n, const double* __restrict__ d,
                                                               const double* __restrict__ e,
                                                               const double* __restrict__ e2, int nwant,
@@ -407,7 +483,7 @@ __global__ void __launch_bounds__(32 * kBisWarps) k_eh_bisect(int n, const doubl
   const double tol = 4.0 * DBL_EPSILON * tnorm;
   for (int round = 0; round < 64 && hi - lo > tol; ++round) {
     const double w = (hi - lo) / (double)(NP + 1);
-    const int cnt = sturm_count(n, d, e2, lo + w * (double)(tid + 1), pivmin);
+    const int cnt = sturm_count(n, d, e2, lo + w * (double)(tid + 1));
     const unsigned above = __ballot_sync(0xffffffffu, cnt > i);
     if (lane == 0) bal[wid] = above;
     __syncthreads();
@@ -497,37 +573,38 @@ __global__ void __launch_bounds__(32) k_eh_invit(int n, const double* __restrict
   for (int i = i0; i < nwant && (i == i0 || lam[i] - lam[i - 1] <= ctol); ++i) {
     const double li = lam[i];
     if (lane == 0) {
-      // T - li I = P L U by Gaussian elimination with row interchanges
+      // T - li I = P L U by Gaussian elimination with row interchanges (|.| compared on bits)
+      constexpr long long kMag = 0x7fffffffffffffffLL;
       double al = sd[0] - li, be = n > 1 ? se[0] : 0.0;
       for (int k = 0; k < n - 1; ++k) {
         const double sub = se[k], dn = sd[k + 1] - li, cn = k + 1 < n - 1 ? se[k + 1] : 0.0;
-        if (fabs(al) >= fabs(sub)) {
+        if ((__double_as_longlong(al) & kMag) >= (__double_as_longlong(sub) & kMag)) {
           double u = al;
-          if (fabs(u) < tiny) u = u < 0.0 ? -tiny : tiny;
-          const double ui = 1.0 / u;
+          if ((__double_as_longlong(u) & kMag) < (__double_as_longlong(tiny) & kMag)) u = u < 0.0 ? -tiny : tiny;
+          const double ui = recip_nr(u);
           const double l = sub * ui;
           sl[k] = l;
           spv[k] = 0;
           su1[k] = ui;
           su2[k] = be;
           su3[k] = 0.0;
-          al = dn - l * be;
+          al = fma(-l, be, dn);
           be = cn;
         } else {
-          const double ui = 1.0 / sub;
+          const double ui = recip_nr(sub);
           const double l = al * ui;
           sl[k] = l;
           spv[k] = 1;
           su1[k] = ui;
           su2[k] = dn;
           su3[k] = cn;
-          al = be - l * dn;
+          al = fma(-l, dn, be);
           be = -l * cn;
         }
       }
       double u = al;
-      if (fabs(u) < tiny) u = u < 0.0 ? -tiny : tiny;
-      su1[n - 1] = 1.0 / u;
+      if ((__double_as_longlong(u) & kMag) < (__double_as_longlong(tiny) & kMag)) u = u < 0.0 ? -tiny : tiny;
+      su1[n - 1] = recip_nr(u);
     }
     for (int k = lane; k < n; k += 32) z[k] = hash_unit((unsigned)i, (unsigned)k);
     __syncwarp();
@@ -560,6 +637,20 @@ __global__ void __launch_bounds__(32) k_eh_invit(int n, const double* __restrict
 }
 
 constexpr int kWY = 64;   // reflectors per compact-WY block of the back-transformation
+
+// v_j[c] = conj(u_j[c]) scale_j for c > j + 1 and v_j[j + 1] = 1, in place (rows j < n - 1).
+__global__ void k_eh_vscale(int n, const double2* __restrict__ vscale, double2* __restrict__ vref) {
+  const int j = blockIdx.y;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n - 1 || c <= j || c >= n) return;
+  double2* v = vref + (size_t)j * n + c;
+  if (c == j + 1) {
+    *v = make_double2(1.0, 0.0);
+    return;
+  }
+  const double2 u = *v, sc = vscale[j];
+  *v = make_double2(fma(sc.x, u.x, sc.y * u.y), fma(sc.y, u.x, -sc.x * u.y));
+}
 
 // x = z (real eigenvectors of T into the complex output, column-major, leading dim n)
 __global__ void k_eh_widen(int n, int nwant, const double* __restrict__ Z, double2* __restrict__ X) {
@@ -616,10 +707,10 @@ struct EighState {
   cublasHandle_t blas = nullptr;
   cusolverDnHandle_t solver = nullptr;
   int ncap = 0, wcap = 0;
-  double *d = nullptr, *e = nullptr, *e2 = nullptr, *spart = nullptr, *lam = nullptr, *Z = nullptr;
+  double *d = nullptr, *e = nullptr, *e2 = nullptr, *sacc = nullptr, *lam = nullptr, *Z = nullptr;
   double *gram = nullptr, *work = nullptr;
   int lwork = 0;
-  double2 *tau = nullptr, *vref = nullptr, *ybuf = nullptr, *rnext = nullptr;
+  double2 *tau = nullptr, *vref = nullptr, *ybuf = nullptr, *rnext = nullptr, *rowcoef = nullptr, *vscale = nullptr;
   double2 *wgram = nullptr, *w1 = nullptr;   // compact-WY blocks
   unsigned int* bar = nullptr;
   int* info = nullptr;    // [0] potrf info, [1] inverse-iteration status
@@ -631,8 +722,8 @@ struct EighState {
 };
 
 void free_state(EighState& s) {
-  void* ptrs[] = {s.d,     s.e,     s.e2,    s.spart, s.lam,  s.Z,  s.gram, s.work, s.tau,
-                  s.vref,  s.ybuf,  s.rnext, s.wgram, s.w1,   s.bar,  s.info};
+  void* ptrs[] = {s.d,    s.e,     s.e2,    s.sacc,    s.lam,   s.Z,  s.gram, s.work, s.tau,
+                  s.vref, s.ybuf,  s.rnext, s.rowcoef, s.wgram, s.w1, s.bar,  s.info, s.vscale};
   for (void* q : ptrs) cudaFree(q);
   const EighState keep = s;
   s = EighState{};
@@ -664,13 +755,14 @@ int grow(Context& c, EighState& s, int n, int nwant) {
   s.ncap = ncap0;
   s.wcap = wcap0;
   const int N = std::max(n, s.ncap), W = std::max(nwant, s.wcap);
-  const int G = 256;
   bool ok = true;
   auto al = [&](void** q, size_t bytes) { ok = ok && cudaMalloc(q, std::max<size_t>(bytes, 16)) == cudaSuccess; };
   al((void**)&s.d, sizeof(double) * N);
   al((void**)&s.e, sizeof(double) * N);
   al((void**)&s.e2, sizeof(double) * N);
-  al((void**)&s.spart, sizeof(double) * 2 * G);
+  al((void**)&s.sacc, sizeof(double) * 4);
+  al((void**)&s.rowcoef, sizeof(double2) * 8);
+  al((void**)&s.vscale, sizeof(double2) * N);
   al((void**)&s.lam, sizeof(double) * W);
   al((void**)&s.Z, sizeof(double) * (size_t)N * W);
   al((void**)&s.gram, sizeof(double) * (size_t)W * W);
@@ -681,7 +773,7 @@ int grow(Context& c, EighState& s, int n, int nwant) {
   al((void**)&s.w1, sizeof(double2) * (size_t)kWY * W);
   al((void**)&s.ybuf, sizeof(double2) * 2 * N);
   al((void**)&s.rnext, sizeof(double2) * 2 * N);
-  al((void**)&s.bar, sizeof(unsigned int) * 2 * kBarGen);
+  al((void**)&s.bar, sizeof(unsigned int) * 64);
   al((void**)&s.info, sizeof(int) * 2);
   int lw = 0;
   if (ok && cusolverDnDpotrf_bufferSize(s.solver, CUBLAS_FILL_MODE_UPPER, W, s.gram, W, &lw) != CUSOLVER_STATUS_SUCCESS)
@@ -767,7 +859,7 @@ int tri_ctas(const Context& c, int n) {
 
 size_t tri_smem(int n, int G) {
   const int R = (n + G - 1) / G;
-  return sizeof(double2) * ((size_t)(3 + R) * n + 2 * (size_t)R);
+  return sizeof(double2) * ((size_t)(3 + R) * n + 3 * (size_t)R + 2 * kMaxParts);
 }
 
 }  // namespace
@@ -808,13 +900,15 @@ int eigh_lowest(Context& c, const double2* a, int lda, int n, int nwant, double*
   const size_t smem = tri_smem(n, G);
   err = cudaFuncSetAttribute(k_eh_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return cuda_fail(c, err, "eigh_lowest: smem attribute");
-  err = cudaMemsetAsync(s->bar, 0, sizeof(unsigned int) * 2 * kBarGen, c.stream);
+  err = cudaMemsetAsync(s->bar, 0, sizeof(unsigned int) * 64, c.stream);
   if (err == cudaSuccess) err = cudaMemsetAsync(s->vref, 0, sizeof(double2) * (size_t)(n + kWY) * n, c.stream);
   if (err == cudaSuccess) err = cudaMemsetAsync(s->tau, 0, sizeof(double2) * (n + kWY), c.stream);
+  if (err == cudaSuccess) err = cudaMemsetAsync(s->sacc, 0, sizeof(double) * 4, c.stream);
   if (err != cudaSuccess) return cuda_fail(c, err, "eigh_lowest: workspace reset");
   err = cudaMemsetAsync(s->info, 0, sizeof(int) * 2, c.stream);
   if (err != cudaSuccess) return cuda_fail(c, err, "eigh_lowest: status reset");
-  TriArgs ta{n, lda, G, a, s->d, s->e, s->e2, s->tau, s->vref, s->ybuf, s->rnext, s->spart, s->bar, c.d_err};
+  TriArgs ta{n, lda, G, a, s->d, s->e, s->e2, s->tau, s->vref, s->ybuf, s->rnext, s->rowcoef, s->vscale, s->sacc, s->bar,
+             c.d_err};
   void* args[] = {&ta};
   HPSI_LAUNCH(c, HPSI_K_EIGH,
               (err = cudaLaunchCooperativeKernel((const void*)k_eh_tridiag, dim3(G), dim3(kTriThreads), args, smem,
@@ -847,6 +941,7 @@ int eigh_lowest(Context& c, const double2* a, int lda, int n, int nwant, double*
   if (cublasDtrsm(s->blas, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT, n, nwant, &one,
                   s->gram, nwant, s->Z, n) != CUBLAS_STATUS_SUCCESS)
     return fail(c, HPSI_ECUDA, "eigh_lowest: cublasDtrsm failed");
+  if (n > 1) HPSI_LAUNCH(c, HPSI_K_EIGH, (k_eh_vscale<<<dim3((n + 255) / 256, n - 1), 256, 0, c.stream>>>(n, s->vscale, s->vref)));
   // 4. back-transformation, one compact-WY block of kWY reflectors at a time from the last:
   //    X <- (I - V_k T_k V_k^H) X over rows k kWY + 1 .. n-1 (reflectors past n-2 are zero)
   HPSI_LAUNCH(c, HPSI_K_EIGH,
