@@ -75,11 +75,16 @@ enum hpsi_option {
                                  kernels and three band-block sizes on its own bands and keeps the
                                  fastest (that call synchronizes; results do not depend on the
                                  choice); 0: fixed defaults */
-  HPSI_OPT_EIGENSOLVER = 10   /* reduced eigenproblems of davidson_solve and hpsi_eigh_lowest:
+  HPSI_OPT_EIGENSOLVER = 10,  /* reduced eigenproblems of davidson_solve and hpsi_eigh_lowest:
                                  1 (default): the library's own kernels (Householder reduction,
                                  Sturm multisection, inverse iteration, back-transformation) for
                                  n <= 1024, cuSOLVER zheevdx above that or if inverse iteration
                                  loses a vector; 0: cuSOLVER zheevdx always */
+  HPSI_OPT_FP32_GEMM = 11     /* mixed davidson_solve: complex64 subspace GEMMs (projections, reduced
+                                 matrices, Ritz vectors) 0 (default): float32 on the CUDA cores;
+                                 1: float32 emulated by cuBLAS with bf16 tensor-core products
+                                 (three bf16 terms per operand, nine products); 2: the Gauss
+                                 three-product complex form (CGEMM3M) */
 };
 
 /* Kernel classes reported by hpsi_kernel_stats. */

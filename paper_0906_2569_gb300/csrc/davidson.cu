@@ -74,6 +74,7 @@ struct DavWork {
   float2* small32 = nullptr;  // [mmax][nbnd]
   float2* ovl32 = nullptr;    // [nbnd][nbnd]
   float2* hcol32 = nullptr;   // [mmax][nbnd]
+  float* hdiag32 = nullptr;   // [npw] float copy of <k+G|H|k+G>
   double2* in64 = nullptr;    // [nbnd][npw]
   double2* out64 = nullptr;   // [nbnd][npw]
 };
@@ -118,7 +119,8 @@ __global__ void __launch_bounds__(256) k_precondition(int npw, const int* __rest
   for (int g = threadIdx.x; g < npw; g += blockDim.x) {
     double x = hdiag[g] - e;
     if (fabs(x) < tau) x = x >= 0.0 ? tau : -tau;
-    const double2 q = make_double2(rb[g].x / x, rb[g].y / x);
+    const double inv = 1.0 / x;
+    const double2 q = make_double2(rb[g].x * inv, rb[g].y * inv);
     tb[g] = q;
     s += q.x * q.x + q.y * q.y;
   }
@@ -237,6 +239,7 @@ static void free_work(DavWork& w) {
   cudaFree(w.small32);
   cudaFree(w.ovl32);
   cudaFree(w.hcol32);
+  cudaFree(w.hdiag32);
   cudaFree(w.in64);
   cudaFree(w.out64);
   w = DavWork();
@@ -285,7 +288,7 @@ static int alloc_work(Context& c, DavHandles& h, int npw, int nbnd, bool mixed) 
          al((void**)&w.hpsi32, v32 * nbnd) && al((void**)&w.t32, v32 * nbnd) &&
          al((void**)&w.small32, sizeof(float2) * (size_t)mmax * nbnd) &&
          al((void**)&w.ovl32, sizeof(float2) * (size_t)nbnd * nbnd) &&
-         al((void**)&w.hcol32, sizeof(float2) * (size_t)mmax * nbnd) && al((void**)&w.in64, v * nbnd) &&
+         al((void**)&w.hcol32, sizeof(float2) * (size_t)mmax * nbnd) && al((void**)&w.hdiag32, sizeof(float) * npw) && al((void**)&w.in64, v * nbnd) &&
          al((void**)&w.out64, v * nbnd);
   if (!ok) {
     free_work(w);
@@ -312,15 +315,7 @@ static int alloc_work(Context& c, DavHandles& h, int npw, int nbnd, bool mixed) 
 // eigen-decomposition of the leading n x n block of a (ld) into w.evec / w.w (ascending)
 static int small_eigh(Context& c, DavHandles& h, const double2* a, int lda, int n) {
   DavWork& w = h.wk;
-  HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_copy_matrix<<<(n * n + 255) / 256, 256, 0, c.stream>>>(n, n, a, lda, w.evec, n)));
-  BCK(cusolverDnZheevd(h.solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, n, Z(w.evec), n, w.w, Z(w.work),
-                       w.lwork, w.info),
-      "cusolverDnZheevd");
-  int info = 0;
-  DCK(cudaMemcpyAsync(&info, w.info, sizeof(int), cudaMemcpyDeviceToHost, c.stream), "davidson info copy");
-  DCK(cudaStreamSynchronize(c.stream), "davidson eigensolve");
-  if (info != 0) return fail(c, HPSI_ESINGULAR, "zheevd of the reduced matrix failed, info " + std::to_string(info));
-  return HPSI_OK;
+  return eigh_reduced(c, a, lda, n, n, w.w, w.evec);
 }
 
 // Lowest nwant eigenpairs of the leading n x n block of a (ld): values in w.w, vectors in the first
@@ -556,67 +551,99 @@ int davidson_run(Context& c, int ik, int nbnd, double tol, int maxiter, double2*
 
 namespace {
 
-// Sum over a block of up to 1024 threads: warp shuffles, then one value per warp.
+// Sum over a block of up to 1024 threads: warp shuffles, then warp 0 reduces the per-warp values
+// (one float64 chain of depth 10 instead of every thread adding all partials); red holds >= 33.
 __device__ __forceinline__ double block_sum256(double s, double* red) {
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-  if ((threadIdx.x & 31) == 0) red[w] = s;
+  const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) red[w] = s;
   __syncthreads();
-  double r = 0.0;
-  for (int i = 0; i < nw; ++i) r += red[i];
+  if (w == 0) {
+    double r = lane < nw ? red[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    if (lane == 0) red[32] = r;
+  }
+  __syncthreads();
+  const double r = red[32];
   __syncthreads();
   return r;
 }
 
-// R_i = HPsi_i - eps_i Psi_i (float32 data, float64 norm); one CTA per band.
+// Neumaier's compensated summation in float32: the running error of each addition is kept in c,
+// so a thread's partial sum of positive float32 terms is accurate to about one float32 rounding
+// of the total, whatever the number of terms.
+struct CompSum {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = s + x;
+    c += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+// R_i = HPsi_i - eps_i Psi_i (float32 data) and ||R_i||_2 (float64 total of compensated float32
+// partial sums); one CTA per band.  eps = e_hi + e_lo in two floats keeps hpsi - eps psi at
+// float32 accuracy of the (small) result.
 __global__ void __launch_bounds__(1024) k_residual32(int npw, const float2* __restrict__ psi,
                                                     const float2* __restrict__ hpsi, const double* __restrict__ eps,
                                                     float2* __restrict__ r, double* __restrict__ rnorm) {
-  __shared__ double red[32];
+  __shared__ double red[33];
   const int b = blockIdx.x;
   const double e = eps[b];
+  const float ehi = (float)e, elo = (float)(e - (double)ehi);
   const float2* x = psi + (size_t)b * npw;
   const float2* hx = hpsi + (size_t)b * npw;
   float2* rb = r + (size_t)b * npw;
-  double s = 0.0;
+  CompSum cs;
   for (int g = threadIdx.x; g < npw; g += blockDim.x) {
-    const double qx = (double)hx[g].x - e * (double)x[g].x, qy = (double)hx[g].y - e * (double)x[g].y;
-    rb[g] = make_float2((float)qx, (float)qy);
-    s += qx * qx + qy * qy;
+    const float2 xv = x[g], hv = hx[g];
+    const float qx = fmaf(-elo, xv.x, fmaf(-ehi, xv.x, hv.x));
+    const float qy = fmaf(-elo, xv.y, fmaf(-ehi, xv.y, hv.y));
+    rb[g] = make_float2(qx, qy);
+    cs.add(fmaf(qx, qx, qy * qy));
   }
-  s = block_sum256(s, red);
+  const double s = block_sum256(cs.value(), red);
   if (threadIdx.x == 0) rnorm[b] = sqrt(s);
 }
 
+// T_j = R_{idx[j]} / clamp(hdiag - eps), then T_j /= ||T_j||, in float32 (hdiag32 is the float copy
+// of the diagonal of H); one CTA per correction.
 __global__ void __launch_bounds__(1024) k_precondition32(int npw, const int* __restrict__ idx,
-                                                        const float2* __restrict__ r, const double* __restrict__ hdiag,
+                                                        const float2* __restrict__ r, const float* __restrict__ hdiag32,
                                                         const double* __restrict__ eps, double tau, int eshift,
                                                         float2* __restrict__ t) {
-  __shared__ double red[32];
+  __shared__ double red[33];
   const int j = blockIdx.x;
   const int i = idx[j];
-  const double e = eps[eshift >= 0 ? eshift : i];
+  const float e = (float)eps[eshift >= 0 ? eshift : i];
+  const float tf = (float)tau;
   const float2* rb = r + (size_t)i * npw;
   float2* tb = t + (size_t)j * npw;
-  double s = 0.0;
+  CompSum cs;
   for (int g = threadIdx.x; g < npw; g += blockDim.x) {
-    double x = hdiag[g] - e;
-    if (fabs(x) < tau) x = x >= 0.0 ? tau : -tau;
-    const double qx = (double)rb[g].x / x, qy = (double)rb[g].y / x;
-    tb[g] = make_float2((float)qx, (float)qy);
-    s += qx * qx + qy * qy;
+    float x = hdiag32[g] - e;
+    if (fabsf(x) < tf) x = x >= 0.f ? tf : -tf;
+    const float inv = 1.0f / x;
+    const float2 rv = rb[g];
+    const float qx = rv.x * inv, qy = rv.y * inv;
+    tb[g] = make_float2(qx, qy);
+    cs.add(fmaf(qx, qx, qy * qy));
   }
-  s = block_sum256(s, red);
+  const double s = block_sum256(cs.value(), red);
   const float inv = s > 0.0 ? (float)(1.0 / sqrt(s)) : 0.f;
   for (int g = threadIdx.x; g < npw; g += blockDim.x) tb[g] = make_float2(tb[g].x * inv, tb[g].y * inv);
 }
 
 __global__ void __launch_bounds__(1024) k_norm2_32(int npw, const float2* __restrict__ t, double* __restrict__ out) {
-  __shared__ double red[32];
+  __shared__ double red[33];
   const float2* tb = t + (size_t)blockIdx.x * npw;
-  double s = 0.0;
-  for (int g = threadIdx.x; g < npw; g += blockDim.x) s += (double)tb[g].x * tb[g].x + (double)tb[g].y * tb[g].y;
-  s = block_sum256(s, red);
+  CompSum cs;
+  for (int g = threadIdx.x; g < npw; g += blockDim.x) {
+    const float2 v = tb[g];
+    cs.add(fmaf(v.x, v.x, v.y * v.y));
+  }
+  const double s = block_sum256(cs.value(), red);
   if (threadIdx.x == 0) out[blockIdx.x] = s;
 }
 
@@ -643,6 +670,11 @@ __global__ void k_canon_scale32(int n, int ld, int first, int nkeep, const doubl
 __global__ void k_cvt_64_32(size_t n, const double2* __restrict__ in, float2* __restrict__ out) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     out[i] = make_float2((float)in[i].x, (float)in[i].y);
+}
+
+__global__ void k_cvt_d2f(int n, const double* __restrict__ in, float* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (float)in[i];
 }
 
 __global__ void k_cvt_32_64(size_t n, const float2* __restrict__ in, double2* __restrict__ out) {
@@ -672,7 +704,7 @@ __global__ void k_mat_64_to_32(int rows, int cols, const double2* __restrict__ s
 __global__ void __launch_bounds__(1024) k_rayleigh(int npw, const double2* __restrict__ psi,
                                                   const double2* __restrict__ hpsi, double* __restrict__ eps,
                                                   double* __restrict__ rnorm) {
-  __shared__ double red[32];
+  __shared__ double red[33];
   const int b = blockIdx.x;
   const double2* x = psi + (size_t)b * npw;
   const double2* hx = hpsi + (size_t)b * npw;
@@ -714,6 +746,15 @@ const cuComplex cZero = {0.f, 0.f};
 const cuComplex cMinusOne = {-1.f, 0.f};
 inline cuComplex* Cf(float2* p) { return reinterpret_cast<cuComplex*>(p); }
 
+// complex64 GEMM of the mixed subspace: plain CGEMM, or the Gauss three-product form (CGEMM3M)
+// when HPSI_OPT_FP32_GEMM is 2
+cublasStatus_t cgemm32(const Context& c, cublasHandle_t h, cublasOperation_t ta, cublasOperation_t tb, int m, int n,
+                       int k, const cuComplex* alpha, const cuComplex* A, int lda, const cuComplex* B, int ldb,
+                       const cuComplex* beta, cuComplex* C, int ldc) {
+  if (c.fp32_gemm == 2) return cublasCgemm3m(h, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+  return cublasCgemm(h, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+}
+
 }  // namespace
 
 static int grid_of(size_t n) { return (int)std::min<size_t>(4096, (n + 255) / 256); }
@@ -734,7 +775,7 @@ static int canonical_orth32(Context& c, DavHandles& h, const float2* x, int n, f
                             bool relative) {
   DavWork& w = h.wk;
   const int npw = w.npw;
-  BCK(cublasCgemm(h.blas, CUBLAS_OP_C, CUBLAS_OP_N, n, n, npw, &cOne, reinterpret_cast<const cuComplex*>(x), npw,
+  BCK(cgemm32(c, h.blas, CUBLAS_OP_C, CUBLAS_OP_N, n, n, npw, &cOne, reinterpret_cast<const cuComplex*>(x), npw,
                   reinterpret_cast<const cuComplex*>(x), npw, &cZero, Cf(w.ovl32), n),
       "cgemm overlap");
   HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
@@ -769,7 +810,7 @@ static int canonical_orth32(Context& c, DavHandles& h, const float2* x, int n, f
   if (nk == 0) return HPSI_OK;
   HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
               (k_canon_scale32<<<(n * nk + 255) / 256, 256, 0, c.stream>>>(n, n, first, nk, w.evec, w.w, w.small32)));
-  BCK(cublasCgemm(h.blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, nk, n, &cOne, reinterpret_cast<const cuComplex*>(x), npw,
+  BCK(cgemm32(c, h.blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, nk, n, &cOne, reinterpret_cast<const cuComplex*>(x), npw,
                   Cf(w.small32), n, &cZero, Cf(out), npw),
       "cgemm orthonormalise");
   return HPSI_OK;
@@ -779,7 +820,7 @@ static int canonical_orth32(Context& c, DavHandles& h, const float2* x, int n, f
 static int hsub_columns32(Context& c, DavHandles& h, int rows, int col0, int ncol) {
   DavWork& w = h.wk;
   const int npw = w.npw, mmax = w.mmax;
-  BCK(cublasCgemm(h.blas, CUBLAS_OP_C, CUBLAS_OP_N, rows, ncol, npw, &cOne, Cf(w.phi32), npw,
+  BCK(cgemm32(c, h.blas, CUBLAS_OP_C, CUBLAS_OP_N, rows, ncol, npw, &cOne, Cf(w.phi32), npw,
                   Cf(w.hphi32 + (size_t)col0 * npw), npw, &cZero, Cf(w.hcol32), mmax),
       "cgemm H_sub columns");
   HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
@@ -796,6 +837,15 @@ static int davidson_run_mixed(Context& c, DavHandles& h, int ik, int nbnd, doubl
   DavWork& w = h.wk;
   const int npw = p.npw, N = nbnd, mmax = w.mmax;
   const size_t vb = sizeof(float2) * (size_t)npw;
+  HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_cvt_d2f<<<(npw + 255) / 256, 256, 0, c.stream>>>(npw, p.d_hdiag, w.hdiag32)));
+  // subspace GEMMs: float32 on the CUDA cores, or float32 emulated with bf16 tensor-core products
+  BCK(cublasSetMathMode(h.blas, c.fp32_gemm == 1 ? CUBLAS_FP32_EMULATED_BF16X9_MATH : CUBLAS_DEFAULT_MATH),
+      "cublasSetMathMode");
+  if (c.fp32_gemm == 1) BCK(cublasSetEmulationStrategy(h.blas, CUBLAS_EMULATION_STRATEGY_EAGER), "cublasSetEmulationStrategy");
+  struct MathReset {
+    cublasHandle_t b;
+    ~MathReset() { cublasSetMathMode(b, CUBLAS_DEFAULT_MATH); }
+  } math_reset{h.blas};
   // phi32[0:N] <- orthonormalised initial guess
   HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
               (k_cvt_64_32<<<grid_of((size_t)N * npw), 256, 0, c.stream>>>((size_t)N * npw, psio, w.t32)));
@@ -817,10 +867,10 @@ static int davidson_run_mixed(Context& c, DavHandles& h, int ik, int nbnd, doubl
     if (rc) return rc;
     HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
                 (k_mat_64_to_32<<<(m * N + 255) / 256, 256, 0, c.stream>>>(m, N, w.evec, m, w.small32, m)));
-    BCK(cublasCgemm(h.blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, N, m, &cOne, Cf(w.phi32), npw, Cf(w.small32), m, &cZero,
+    BCK(cgemm32(c, h.blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, N, m, &cOne, Cf(w.phi32), npw, Cf(w.small32), m, &cZero,
                     Cf(w.psi32), npw),
         "cgemm Ritz vectors");
-    BCK(cublasCgemm(h.blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, N, m, &cOne, Cf(w.hphi32), npw, Cf(w.small32), m, &cZero,
+    BCK(cgemm32(c, h.blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, N, m, &cOne, Cf(w.hphi32), npw, Cf(w.small32), m, &cZero,
                     Cf(w.hpsi32), npw),
         "cgemm H Ritz vectors");
     DCK(cudaMemcpyAsync(w.eps, w.w, sizeof(double) * N, cudaMemcpyDeviceToDevice, c.stream), "eps copy");
@@ -848,14 +898,14 @@ static int davidson_run_mixed(Context& c, DavHandles& h, int ik, int nbnd, doubl
     DCK(cudaMemcpyAsync(w.idx, uidx.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, c.stream), "index copy");
     float2* tnew = w.phi32 + (size_t)m * npw;
     const int eshift = c.opt_shift == 1 ? N - 1 : -1;
-    HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_precondition32<<<nc, 1024, 0, c.stream>>>(npw, w.idx, w.t32, p.d_hdiag, w.eps,
+    HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_precondition32<<<nc, 1024, 0, c.stream>>>(npw, w.idx, w.t32, w.hdiag32, w.eps,
                                                                                 c.opt_tau, eshift, tnew)));
     for (int round = 0; round < 2; ++round) {
       for (int pass = 0; pass < 2; ++pass) {
-        BCK(cublasCgemm(h.blas, CUBLAS_OP_C, CUBLAS_OP_N, m, nc, npw, &cOne, Cf(w.phi32), npw, Cf(tnew), npw, &cZero,
+        BCK(cgemm32(c, h.blas, CUBLAS_OP_C, CUBLAS_OP_N, m, nc, npw, &cOne, Cf(w.phi32), npw, Cf(tnew), npw, &cZero,
                         Cf(w.small32), m),
             "cgemm projection");
-        BCK(cublasCgemm(h.blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, nc, m, &cMinusOne, Cf(w.phi32), npw, Cf(w.small32), m,
+        BCK(cgemm32(c, h.blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, nc, m, &cMinusOne, Cf(w.phi32), npw, Cf(w.small32), m,
                         &cOne, Cf(tnew), npw),
             "cgemm projection update");
       }

@@ -130,6 +130,7 @@ struct Context {
   int basis_factor = 4;                // Davidson: the reduced basis grows to basis_factor * N vectors
   int autotune = 1;                    // time the fast-path plans on the first apply of a problem
   int eigensolver = 1;                 // reduced eigenproblems: 1 = the library's kernels, 0 = cuSOLVER
+  int fp32_gemm = 0;                   // mixed Davidson subspace GEMMs: 1 = bf16x9-emulated float32
   void* eigh = nullptr;                // eigensolver handles and work buffers (eigh.cu)
   cudaStream_t cap_stream = nullptr;   // internal stream for graph capture
   GraphCache graph;
