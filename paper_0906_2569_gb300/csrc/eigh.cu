@@ -10,9 +10,10 @@
 //   2. The lowest nwant eigenvalues of T by multisection on Sturm counts.
 //   3. Their eigenvectors z_i by inverse iteration.  Eigenvalues closer than 1e-10 |T| form a
 //      cluster whose vectors are orthogonalised against each other (modified Gram-Schmidt) at each
-//      iteration; the whole set is then orthonormalised by Cholesky QR (Z^T Z = U^T U,
-//      Z <- Z U^-1), which mixes two vectors only in proportion to their loss of orthogonality, itself
-//      of the order of rounding / gap, so residuals stay at rounding level.
+//      iteration; the whole set is then orthonormalised by one Newton-Schulz step of the polar
+//      decomposition (Z <- Z (3 I - Z^T Z) / 2), which mixes two vectors only in proportion to their
+//      loss of orthogonality, itself of the order of rounding / gap, so residuals stay at rounding
+//      level.
 //   4. Back-transformation x_i = Q z_i = H_0 (H_1 (... (H_{n-2} z_i))), in blocks of 64 reflectors
 //      written in compact WY form H_a ... H_b = I - V T V^H and applied with two ZGEMMs and a
 //      back substitution with T^-1 = diag(1 / tau) + strictly-upper(V^H V).
@@ -441,23 +442,27 @@ __device__ int sturm_count(int n, const double* __restrict__ d, const double* __
   double pm = 1.0, p = d[0] - sigma;
   if ((dbits(p) << 1) == 0) p = __longlong_as_double(kSign | kTiny);
   int cnt = dbits(p) < 0;
-  for (int k = 1; k < n; ++k) {
+  auto step = [&](int k) {
     double pn = fma(d[k] - sigma, p, -e2[k - 1] * pm);
     if ((dbits(pn) << 1) == 0) pn = __longlong_as_double(((dbits(p) & kSign) ^ kSign) | kTiny);
     cnt += (dbits(pn) ^ dbits(p)) < 0;
     pm = p;
     p = pn;
-    if ((k & 7) == 0) {
-      const int ep = biased_exp(p), em = biased_exp(pm), ex = max(ep, em);
-      if (ex > 1023 + 400) {
-        p = __longlong_as_double(ep > 400 ? dbits(p) - kShift : dbits(p) & kSign);
-        pm = __longlong_as_double(em > 400 ? dbits(pm) - kShift : dbits(pm) & kSign);
-      } else if (ex < 1023 - 400) {
-        if (ep > 0) p = __longlong_as_double(dbits(p) + kShift);
-        if (em > 0) pm = __longlong_as_double(dbits(pm) + kShift);
-      }
+  };
+  int k = 1;
+  for (; k + 8 <= n; k += 8) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) step(k + u);
+    const int ep = biased_exp(p), em = biased_exp(pm), ex = max(ep, em);
+    if (ex > 1023 + 400) {
+      p = __longlong_as_double(ep > 400 ? dbits(p) - kShift : dbits(p) & kSign);
+      pm = __longlong_as_double(em > 400 ? dbits(pm) - kShift : dbits(pm) & kSign);
+    } else if (ex < 1023 - 400) {
+      if (ep > 0) p = __longlong_as_double(dbits(p) + kShift);
+      if (em > 0) pm = __longlong_as_double(dbits(pm) + kShift);
     }
   }
+  for (; k < n; ++k) step(k);
   return cnt;
 }
 
@@ -652,6 +657,14 @@ __global__ void k_eh_vscale(int n, const double2* __restrict__ vscale, double2* 
   *v = make_double2(fma(sc.x, u.x, sc.y * u.y), fma(sc.y, u.x, -sc.x * u.y));
 }
 
+// status[0] = 1 when some |G_ij - delta_ij| exceeds tol (G = Z^T Z, nwant x nwant)
+__global__ void k_eh_orthcheck(int nw, const double* __restrict__ G, double tol, int* __restrict__ status) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nw * nw) return;
+  const double g = G[i] - ((i % nw) == (i / nw) ? 1.0 : 0.0);
+  if (!(fabs(g) <= tol)) atomicExch(status, 1);
+}
+
 // x = z (real eigenvectors of T into the complex output, column-major, leading dim n)
 __global__ void k_eh_widen(int n, int nwant, const double* __restrict__ Z, double2* __restrict__ X) {
   const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -670,8 +683,13 @@ __global__ void __launch_bounds__(128) k_eh_trsv(int ncol, const double2* __rest
                                                  double2* __restrict__ W) {
   static_assert(kWY == 64, "two rows per lane");
   __shared__ double2 gs[kWY * (kWY - 1) / 2];   // strictly upper part, column q at q (q - 1) / 2
-  for (int q = 1; q < kWY; ++q)
-    for (int r = threadIdx.x; r < q; r += blockDim.x) gs[q * (q - 1) / 2 + r] = G[r + (size_t)q * kWY];
+#pragma unroll 4
+  for (int idx = threadIdx.x; idx < kWY * (kWY - 1) / 2; idx += blockDim.x) {
+    int q = (int)(0.5f * (1.0f + sqrtf(1.0f + 8.0f * (float)idx)));   // column: q (q - 1) / 2 <= idx
+    while (q * (q - 1) / 2 > idx) --q;
+    while ((q + 1) * q / 2 <= idx) ++q;
+    gs[idx] = G[(idx - q * (q - 1) / 2) + (size_t)q * kWY];
+  }
   __syncthreads();
   const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (col >= ncol) return;
@@ -707,13 +725,12 @@ struct EighState {
   cublasHandle_t blas = nullptr;
   cusolverDnHandle_t solver = nullptr;
   int ncap = 0, wcap = 0;
-  double *d = nullptr, *e = nullptr, *e2 = nullptr, *sacc = nullptr, *lam = nullptr, *Z = nullptr;
-  double *gram = nullptr, *work = nullptr;
-  int lwork = 0;
+  double *d = nullptr, *e = nullptr, *e2 = nullptr, *sacc = nullptr, *lam = nullptr, *Z = nullptr, *Z2 = nullptr;
+  double* gram = nullptr;
   double2 *tau = nullptr, *vref = nullptr, *ybuf = nullptr, *rnext = nullptr, *rowcoef = nullptr, *vscale = nullptr;
   double2 *wgram = nullptr, *w1 = nullptr;   // compact-WY blocks
   unsigned int* bar = nullptr;
-  int* info = nullptr;    // [0] potrf info, [1] inverse-iteration status
+  int* info = nullptr;    // [0] orthogonality check of the eigenvectors, [1] inverse-iteration status
   // cuSOLVER zheevdx path
   int zcap = 0, zlwork = 0;
   double2 *acopy = nullptr, *zwork = nullptr;
@@ -722,8 +739,8 @@ struct EighState {
 };
 
 void free_state(EighState& s) {
-  void* ptrs[] = {s.d,    s.e,     s.e2,    s.sacc,    s.lam,   s.Z,  s.gram, s.work, s.tau,
-                  s.vref, s.ybuf,  s.rnext, s.rowcoef, s.wgram, s.w1, s.bar,  s.info, s.vscale};
+  void* ptrs[] = {s.d,    s.e,     s.e2,    s.sacc,    s.lam,   s.Z,  s.gram, s.tau,
+                  s.vref, s.ybuf,  s.rnext, s.rowcoef, s.wgram, s.w1, s.bar,  s.info, s.vscale, s.Z2};
   for (void* q : ptrs) cudaFree(q);
   const EighState keep = s;
   s = EighState{};
@@ -765,6 +782,7 @@ int grow(Context& c, EighState& s, int n, int nwant) {
   al((void**)&s.vscale, sizeof(double2) * N);
   al((void**)&s.lam, sizeof(double) * W);
   al((void**)&s.Z, sizeof(double) * (size_t)N * W);
+  al((void**)&s.Z2, sizeof(double) * (size_t)N * W);
   al((void**)&s.gram, sizeof(double) * (size_t)W * W);
   const int K = (N + kWY - 1) / kWY;
   al((void**)&s.tau, sizeof(double2) * (N + kWY));
@@ -775,13 +793,6 @@ int grow(Context& c, EighState& s, int n, int nwant) {
   al((void**)&s.rnext, sizeof(double2) * 2 * N);
   al((void**)&s.bar, sizeof(unsigned int) * 64);
   al((void**)&s.info, sizeof(int) * 2);
-  int lw = 0;
-  if (ok && cusolverDnDpotrf_bufferSize(s.solver, CUBLAS_FILL_MODE_UPPER, W, s.gram, W, &lw) != CUSOLVER_STATUS_SUCCESS)
-    ok = false;
-  if (ok) {
-    s.lwork = std::max(lw, 1);
-    al((void**)&s.work, sizeof(double) * s.lwork);
-  }
   if (!ok) {
     free_state(s);
     return fail(c, HPSI_ENOMEM, "eigensolver workspace allocation failed");
@@ -930,22 +941,26 @@ int eigh_lowest(Context& c, const double2* a, int lda, int n, int nwant, double*
   }
   HPSI_LAUNCH(c, HPSI_K_EIGH,
               (k_eh_invit<<<nwant, 32, ismem, c.stream>>>(n, s->d, s->e, nwant, s->lam, s->Z, s->info + 1)));
-  //    Cholesky QR of Z
-  const double one = 1.0, zero = 0.0;
-  if (cublasDsyrk(s->blas, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_T, nwant, n, &one, s->Z, n, &zero, s->gram, nwant) !=
+  //    orthonormalisation of Z by one Newton-Schulz step of the polar decomposition,
+  //    Z <- Z (3 I - Z^T Z) / 2: inverse iteration leaves |Z^T Z - I| at rounding / gap (below
+  //    1e-6 for gaps above the cluster tolerance), which one step squares; a larger departure
+  //    (a lost vector) makes the caller fall back to cuSOLVER
+  const double one = 1.0, zero = 0.0, mhalf = -0.5, three_half = 1.5;
+  if (cublasDgemm(s->blas, CUBLAS_OP_T, CUBLAS_OP_N, nwant, nwant, n, &one, s->Z, n, s->Z, n, &zero, s->gram, nwant) !=
       CUBLAS_STATUS_SUCCESS)
-    return fail(c, HPSI_ECUDA, "eigh_lowest: cublasDsyrk failed");
-  if (cusolverDnDpotrf(s->solver, CUBLAS_FILL_MODE_UPPER, nwant, s->gram, nwant, s->work, s->lwork, s->info) !=
-      CUSOLVER_STATUS_SUCCESS)
-    return fail(c, HPSI_ECUDA, "eigh_lowest: cusolverDnDpotrf failed");
-  if (cublasDtrsm(s->blas, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT, n, nwant, &one,
-                  s->gram, nwant, s->Z, n) != CUBLAS_STATUS_SUCCESS)
-    return fail(c, HPSI_ECUDA, "eigh_lowest: cublasDtrsm failed");
+    return fail(c, HPSI_ECUDA, "eigh_lowest: Gram matrix of the eigenvectors failed");
+  HPSI_LAUNCH(c, HPSI_K_EIGH,
+              (k_eh_orthcheck<<<(nwant * nwant + 255) / 256, 256, 0, c.stream>>>(nwant, s->gram, 1e-4, s->info)));
+  if (cudaMemcpyAsync(s->Z2, s->Z, sizeof(double) * (size_t)n * nwant, cudaMemcpyDeviceToDevice, c.stream) !=
+          cudaSuccess ||
+      cublasDgemm(s->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, nwant, nwant, &mhalf, s->Z, n, s->gram, nwant, &three_half,
+                  s->Z2, n) != CUBLAS_STATUS_SUCCESS)
+    return fail(c, HPSI_ECUDA, "eigh_lowest: Newton-Schulz step failed");
   if (n > 1) HPSI_LAUNCH(c, HPSI_K_EIGH, (k_eh_vscale<<<dim3((n + 255) / 256, n - 1), 256, 0, c.stream>>>(n, s->vscale, s->vref)));
   // 4. back-transformation, one compact-WY block of kWY reflectors at a time from the last:
   //    X <- (I - V_k T_k V_k^H) X over rows k kWY + 1 .. n-1 (reflectors past n-2 are zero)
   HPSI_LAUNCH(c, HPSI_K_EIGH,
-              (k_eh_widen<<<(unsigned)(((size_t)n * nwant + 255) / 256), 256, 0, c.stream>>>(n, nwant, s->Z, v_out)));
+              (k_eh_widen<<<(unsigned)(((size_t)n * nwant + 255) / 256), 256, 0, c.stream>>>(n, nwant, s->Z2, v_out)));
   if (n > 1) {
     const int K = (n - 1 + kWY - 1) / kWY;
     const cuDoubleComplex zone = make_cuDoubleComplex(1.0, 0.0), zzero = make_cuDoubleComplex(0.0, 0.0),
