@@ -273,8 +273,10 @@ HPSI_API int hpsi_set_option(hpsi_ctx* ctx, int option, double value);
 /*
  * hpsi_kernel_stats -- launches of the library's own kernels on ctx since the last reset, and
  * (with HPSI_OPT_KERNEL_TIMING on) their summed device time in ms from the bracketing events.
- *   kernel       in   an hpsi_kernel value, -1 for all classes together (total_ms then 0), or
- *                     -2 for the number of H|psi> band-applications performed (in launches)
+ *   kernel       in   an hpsi_kernel value, -1 for all classes together (total_ms then 0),
+ *                     -2 for the number of H|psi> band-applications performed (in launches), or
+ *                     -3 for the reduced eigenproblems solved by the library's own eigensolver
+ *                     (in launches) and how many of them it handed to cuSOLVER (in total_ms)
  *   launches     out  nullable; number of launches
  *   total_ms     out  nullable; summed event time (synchronizes the context's stream)
  *   reset        in   non-zero: clear the counters after reading
@@ -284,7 +286,7 @@ HPSI_API int hpsi_kernel_stats(hpsi_ctx* ctx, int kernel, long long* launches, d
 
 /*
  * hpsi_sync -- wait for all work queued on the context's stream, then report a device-side
- * failure: HPSI_ETIMEOUT if a bounded wait inside a tensor-core kernel expired since the last
+ * failure: HPSI_ETIMEOUT if a bounded wait inside a library kernel expired since the last
  * check (the affected outputs are invalid; the error word is cleared).  Synchronous host-pointer
  * calls and davidson_solve make the same check themselves.
  */

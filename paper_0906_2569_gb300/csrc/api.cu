@@ -838,7 +838,13 @@ extern "C" int hpsi_set_option(hpsi_ctx* ctx, int option, double value) {
 extern "C" int hpsi_kernel_stats(hpsi_ctx* ctx, int kernel, long long* launches, double* total_ms, int reset) {
   if (!ctx) return HPSI_EINVAL;
   Context& c = ctx->c;
-  if (kernel < -2 || kernel >= HPSI_K_COUNT) return fail(c, HPSI_EINVAL, "hpsi_kernel_stats: bad kernel class");
+  if (kernel < -3 || kernel >= HPSI_K_COUNT) return fail(c, HPSI_EINVAL, "hpsi_kernel_stats: bad kernel class");
+  if (kernel == -3) {
+    if (launches) *launches = c.eig_calls;
+    if (total_ms) *total_ms = (double)c.eig_fallbacks;
+    if (reset) c.eig_calls = c.eig_fallbacks = 0;
+    return HPSI_OK;
+  }
   if (kernel == -2) {
     if (launches) *launches = c.band_apps;
     if (total_ms) *total_ms = 0.0;

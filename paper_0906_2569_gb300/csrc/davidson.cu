@@ -769,8 +769,10 @@ static int apply32(Context& c, DavWork& w, int ik, const float2* x32, float2* hx
   return HPSI_OK;
 }
 
-// Orthonormalise the float32 block x[0:n] into out (canonical, float64 eigen-decomposition of the
-// overlap); directions with overlap eigenvalue <= thr (relative to the largest if relative) drop.
+// Orthonormalise the float32 block x[0:n] into out: Cholesky QR (float64 factor of the overlap) when
+// the block is well conditioned, Cholesky QR twice when it is moderately conditioned (absolute
+// threshold only), else canonically through the float64 eigen-decomposition of the overlap, where
+// directions with overlap eigenvalue <= thr (relative to the largest if relative) drop.
 static int canonical_orth32(Context& c, DavHandles& h, const float2* x, int n, float2* out, int* nkeep, double thr,
                             bool relative) {
   DavWork& w = h.wk;
@@ -794,6 +796,44 @@ static int canonical_orth32(Context& c, DavHandles& h, const float2* x, int n, f
         "ctrsm");
     *nkeep = n;
     return HPSI_OK;
+  }
+  if (!relative) {
+    // moderately conditioned correction block (factor condition below about 1e3): Cholesky QR twice,
+    // the second pass on the (nearly orthonormal) result of the first
+    HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
+                (k_mat_32_to_64<<<(n * n + 255) / 256, 256, 0, c.stream>>>(n, n, w.ovl32, n, w.ovl, n)));
+    bool loose_ok = false;
+    rc = chol_overlap(c, h, n, 1e-6, false, &loose_ok);
+    if (rc) return rc;
+    if (loose_ok) {
+      HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
+                  (k_mat_64_to_32<<<(n * n + 255) / 256, 256, 0, c.stream>>>(n, n, w.ovl, n, w.ovl32, n)));
+      DCK(cudaMemcpyAsync(out, x, sizeof(float2) * (size_t)n * npw, cudaMemcpyDeviceToDevice, c.stream), "copy");
+      BCK(cublasCtrsm(h.blas, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT, npw, n,
+                      &cOne, Cf(w.ovl32), n, Cf(out), npw),
+          "ctrsm");
+      BCK(cgemm32(c, h.blas, CUBLAS_OP_C, CUBLAS_OP_N, n, n, npw, &cOne, Cf(out), npw, Cf(out), npw, &cZero,
+                  Cf(w.ovl32), n),
+          "cgemm overlap");
+      HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
+                  (k_mat_32_to_64<<<(n * n + 255) / 256, 256, 0, c.stream>>>(n, n, w.ovl32, n, w.ovl, n)));
+      bool second_ok = false;
+      rc = chol_overlap(c, h, n, 1e-2, false, &second_ok);
+      if (rc) return rc;
+      if (second_ok) {
+        HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
+                    (k_mat_64_to_32<<<(n * n + 255) / 256, 256, 0, c.stream>>>(n, n, w.ovl, n, w.ovl32, n)));
+        BCK(cublasCtrsm(h.blas, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT, npw, n,
+                        &cOne, Cf(w.ovl32), n, Cf(out), npw),
+            "ctrsm");
+        *nkeep = n;
+        return HPSI_OK;
+      }
+    }
+    // otherwise the overlap of x again, for its eigen-decomposition
+    BCK(cgemm32(c, h.blas, CUBLAS_OP_C, CUBLAS_OP_N, n, n, npw, &cOne, reinterpret_cast<const cuComplex*>(x), npw,
+                reinterpret_cast<const cuComplex*>(x), npw, &cZero, Cf(w.ovl32), n),
+        "cgemm overlap");
   }
   HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
               (k_mat_32_to_64<<<(n * n + 255) / 256, 256, 0, c.stream>>>(n, n, w.ovl32, n, w.ovl, n)));

@@ -99,15 +99,19 @@ struct TriArgs {
 };
 
 // Grid-wide barrier of a cooperative launch on a monotonic arrival counter: barrier number k
-// (k = 1, 2, ...) is passed once the counter reaches k G.  Each CTA adds 1 with release semantics
-// after a CTA barrier and polls with acquire loads, so neither a reset nor a generation flip sits
-// between the last arrival and the release.  Returns false when this CTA's wait ran out or another
-// CTA reported a failure (the error word is then set).
-__device__ bool grid_barrier(unsigned int* count, unsigned int target, int* err) {
-  __shared__ int ok;
+// (k = 1, 2, ...) is passed once the counter reaches k G.  Arrival (after a CTA barrier, so every
+// thread's writes precede it) adds 1 with release semantics; the wait polls with acquire loads, so
+// neither a reset nor a generation flip sits between the last arrival and the release.  The two are
+// separate so that a CTA can do local work between them.  grid_wait returns false when this CTA's
+// wait ran out or another CTA reported a failure (the error word is then set).
+__device__ __forceinline__ void grid_arrive(unsigned int* count) {
   __syncthreads();
+  if (threadIdx.x == 0) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
+}
+
+__device__ bool grid_wait(unsigned int* count, unsigned int target, int* err) {
+  __shared__ int ok;
   if (threadIdx.x == 0) {
-    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
     int good = 1;
     const long long t0 = clock64();
     unsigned int spins = 0;
@@ -344,62 +348,76 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_eh_tridiag(TriArgs p) {
     const int first = j >= g ? (j - g) / G + 1 : 0;
     const int Ra = R - first;
     const int q = Ra > 0 ? min(min((NW + Ra - 1) / Ra, kMaxParts / Ra), kMaxPartsPerRow) : 1;
-    if (wid <= 1) {
-      const double2 tcs = tcs_sh, cts = cts_sh;
-      const double s2 = s2_sh;
+    const double2 tcs = tcs_sh, cts = cts_sh;
+    const double s2 = s2_sh;
+    // the own rows' y_j (lanes of warps 0 and 1 over the rows) and the coefficients of column j's
+    // update for row lr: A = tau y conj(scale), B = 2 v conj(scale), Q = conj(tau) v
+    auto row_y = [&](int i) {
+      double2 acc = pacc[i * q];
+      for (int k = 1; k < q; ++k) {
+        acc.x += pacc[i * q + k].x;
+        acc.y += pacc[i * q + k].y;
+      }
+      const double2 a1 = pa1[i * q];
+      return make_double2(fma(scC.x, acc.x, fma(-scC.y, acc.y, a1.x)), fma(scC.x, acc.y, fma(scC.y, acc.x, a1.y)));
+    };
+    auto coefs = [&](int lr, int r, double2 y, double2* A, double2* B, double2* Q) {
+      const bool lead = r == j + 1;                       // v_j[j+1] = 1, else v_j[r] = conj(u_r) scale
+      const double2 cu = make_double2(uC[r].x, -uC[r].y);
+      *A = cmul(y, tcs);
+      *B = lead ? make_double2(2.0 * scC.x, -2.0 * scC.y) : make_double2(s2 * cu.x, s2 * cu.y);
+      *Q = lead ? make_double2(tauC.x, -tauC.y) : cmul(cu, cts);
+    };
+    if (wid == 0) {
       double sp = 0.0;
       for (int i = lane; i < Ra; i += 32) {
-        const int lr = first + i, r = g + lr * G;
-        double2 acc = pacc[i * q];
-        for (int k = 1; k < q; ++k) {
-          acc.x += pacc[i * q + k].x;
-          acc.y += pacc[i * q + k].y;
-        }
-        const double2 a1 = pa1[i * q];
-        const double2 y = make_double2(fma(scC.x, acc.x, fma(-scC.y, acc.y, a1.x)),
-                                       fma(scC.x, acc.y, fma(scC.y, acc.x, a1.y)));
-        const bool lead = r == j + 1;                       // v_j[j+1] = 1, else v_j[r] = conj(u_r) scale
-        const double2 cu = make_double2(uC[r].x, -uC[r].y);
-        if (wid == 0) {
-          p.ybuf[(j & 1) * n + r] = y;
-          // Re(conj(v_r) y_r)
-          sp += lead ? y.x : fma(uC[r].x, fma(cscC.x, y.x, -cscC.y * y.y), -uC[r].y * fma(cscC.x, y.y, cscC.y * y.x));
-        } else {
-          const double2 A = cmul(y, tcs);
-          const double2 B = lead ? make_double2(2.0 * scC.x, -2.0 * scC.y) : make_double2(s2 * cu.x, s2 * cu.y);
-          const double2 Q = lead ? make_double2(tauC.x, -tauC.y) : cmul(cu, cts);
-          cA[lr] = A;
-          cB[lr] = B;
-          cQ[lr] = Q;
-          if (lead) {
-            double2* rc = p.rowcoef + (j & 1) * 4;
-            rc[0] = A;
-            rc[1] = B;
-            rc[2] = Q;
-            rc[3] = make_double2(2.0 * fma(tauC.x, y.x, -tauC.y * y.y), 0.0);          // E = 2 Re(tau y)
-          }
+        const int r = g + (first + i) * G;
+        const double2 y = row_y(i);
+        p.ybuf[(j & 1) * n + r] = y;
+        // Re(conj(v_r) y_r), conj(v_r) = u_r conj(scale) (1 for the leading row)
+        sp += r == j + 1 ? y.x
+                         : fma(uC[r].x, fma(cscC.x, y.x, -cscC.y * y.y), -uC[r].y * fma(cscC.x, y.y, cscC.y * y.x));
+      }
+      sp = warp_sum(sp);
+      if (lane == 0) {
+        atomicAdd(&p.sacc[j % 3], sp);
+        if (g == 0) {
+          p.d[j] = dj;
+          p.e[j] = beta_sh;
+          p.e2[j] = beta_sh * beta_sh;
+          p.tau[j] = tauC;
+          p.vscale[j] = scC;
         }
       }
-      if (wid == 0) {
-        sp = warp_sum(sp);
-        if (lane == 0) {
-          atomicAdd(&p.sacc[j % 3], sp);
-          if (g == 0) {
-            p.d[j] = dj;
-            p.e[j] = beta_sh;
-            p.e2[j] = beta_sh * beta_sh;
-            p.tau[j] = tauC;
-            p.vscale[j] = scC;
-          }
-        }
-      }
+    } else if (wid == 1 && Ra > 0 && g + first * G == j + 1 && lane == 0) {
+      // this CTA owns row j+1: publish its coefficients (and E = 2 Re(tau y)) before arriving
+      const double2 y = row_y(0);
+      double2 A, B, Q;
+      coefs(first, j + 1, y, &A, &B, &Q);
+      double2* rc = p.rowcoef + (j & 1) * 4;
+      rc[0] = A;
+      rc[1] = B;
+      rc[2] = Q;
+      rc[3] = make_double2(2.0 * fma(tauC.x, y.x, -tauC.y * y.y), 0.0);
     }
     if (g == j % G) {   // the owner of row j stores u_j; k_eh_vscale forms v_j = conj(u_j) scale_j
       for (int c = j + 2 + tid; c < n; c += kTriThreads) p.vref[(size_t)j * n + c] = uC[c];
     }
+    grid_arrive(p.bar);
+    // local work while the other CTAs arrive: the own rows' coefficients for column j+1
+    if (wid == 1) {
+      for (int i = lane; i < Ra; i += 32) {
+        const int lr = first + i, r = g + lr * G;
+        double2 A, B, Q;
+        coefs(lr, r, row_y(i), &A, &B, &Q);
+        cA[lr] = A;
+        cB[lr] = B;
+        cQ[lr] = Q;
+      }
+    }
     tauAbs2 = fma(tauC.x, tauC.x, tauC.y * tauC.y);
     scP = scC;
-    if (!grid_barrier(p.bar, (unsigned)(G * (j + 1)), p.err)) return;
+    if (!grid_wait(p.bar, (unsigned)(G * (j + 1)), p.err)) return;
   }
 }
 
@@ -990,7 +1008,11 @@ int eigh_lowest(Context& c, const double2* a, int lda, int n, int nwant, double*
   if (err != cudaSuccess) return cuda_fail(c, err, "eigh_lowest: status copy");
   rc = check_device_error(c);
   if (rc) return rc;
-  if (info[0] != 0 || info[1] != 0) *fallback = true;   // inverse iteration lost a vector: caller falls back
+  ++c.eig_calls;
+  if (info[0] != 0 || info[1] != 0) {   // inverse iteration lost a vector: the caller falls back
+    *fallback = true;
+    ++c.eig_fallbacks;
+  }
   return HPSI_OK;
 }
 

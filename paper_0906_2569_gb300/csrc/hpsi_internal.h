@@ -138,6 +138,8 @@ struct Context {
   bool timing = false;
   long long launches[HPSI_K_COUNT] = {0};
   long long band_apps = 0;             // H|psi> band-applications performed
+  long long eig_calls = 0;             // reduced eigenproblems solved by the library's kernels
+  long long eig_fallbacks = 0;         // ... and handed to cuSOLVER instead
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> trec;   // (kernel, start, end)
   std::vector<cudaEvent_t> evpool;
   double tacc[HPSI_K_COUNT] = {0.0};
