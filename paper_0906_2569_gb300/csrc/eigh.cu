@@ -42,8 +42,6 @@ namespace {
 
 constexpr int kTriThreads = 256;                     // threads per CTA of the reduction
 constexpr int kMaxN = 1024;                          // largest n handled here
-constexpr int kMaxParts = 16;                        // row parts per CTA and column
-constexpr int kMaxPartsPerRow = 4;
 constexpr int kLoadK = (kMaxN + 255) / 256;          // row elements per thread of the column loads
 constexpr long long kBarrierLimit = 2000000000LL;    // clock cycles (about 1 s) per barrier wait
 constexpr int kInvIters = 3;                         // inverse-iteration solves per eigenvector
@@ -93,7 +91,7 @@ struct TriArgs {
   double2* rnext;       // [2][n] the next row, published by its owner
   double2* rowcoef;     // [2][4] coefficients of the published row: A, B, Q, (E, 0)
   double2* vscale;      // [n] scale of each reflector
-  double* sacc;         // [3] s of the last columns, accumulated by atomics
+  double* sacc;         // [4] s of the last columns (slot j & 3), accumulated by atomics
   unsigned int* bar;    // barrier arrival counter (zero at launch)
   int* err;             // device error word
 };
@@ -157,6 +155,12 @@ __device__ __forceinline__ double rsqrt_nr(double x) {
   return y;
 }
 
+// Column chunk of one of q parts of a row of m columns, rounded up to whole warps (no division).
+__device__ __forceinline__ int split_chunk(int m, int q) {
+  const int c = q == 1 ? m : q == 2 ? (m + 1) >> 1 : q == 4 ? (m + 3) >> 2 : ((m + 2) * 0x5556) >> 16;
+  return (c + 31) & ~31;
+}
+
 __device__ __forceinline__ double2 cmulc2(double2 a, double2 b) {   // a * conj(b)
   return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -a.x * b.y));
 }
@@ -171,7 +175,8 @@ __device__ __forceinline__ double2 cmulc2(double2 a, double2 b) {   // a * conj(
 // the product with A as conj(u) and its scale is applied to each row sum at the end, so one warp
 // computes the reflector's scalars while the others update the rows.  s is accumulated across
 // CTAs by float64 atomics.  The own rows' work is cut into parts spread over the eight warps
-// (two per scheduler), since every scheduler issues float64 at its own fixed rate.
+// (two per scheduler) so that each scheduler carries the same float64 work: a scheduler issues
+// float64 at its own fixed rate, and a CTA barrier does not wait for float64 work still queued.
 __global__ void __launch_bounds__(kTriThreads, 1) k_eh_tridiag(TriArgs p) {
   extern __shared__ double2 sm[];
   constexpr int NW = kTriThreads / 32;
@@ -186,8 +191,8 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_eh_tridiag(TriArgs p) {
   double2* cA = rows + (size_t)Rmax * n;   // [Rmax] A_r, B_r, Q_r of the own rows
   double2* cB = cA + Rmax;
   double2* cQ = cB + Rmax;
-  double2* pacc = cQ + Rmax;               // [kMaxParts] part sums with conj(u)
-  double2* pa1 = pacc + kMaxParts;         // [kMaxParts] element at column j+1 (part 0 of a row)
+  double2* pacc = cQ + Rmax;               // [4 Rmax] quarter (or whole-row) sums with conj(u)
+  double2* pa1 = pacc + 4 * Rmax;          // [Rmax] element at column j+1 of each row
   __shared__ double red[NW];
   __shared__ double2 alpha_sh, tau_sh, scale_sh, tcs_sh, cts_sh;
   __shared__ double beta_sh, s2_sh;
@@ -198,7 +203,11 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_eh_tridiag(TriArgs p) {
   }
   double2 scP = make_double2(0.0, 0.0);
   double tauAbs2 = 0.0;   // |tau_{j-1}|^2
-  for (int j = 0; j < n; ++j) {
+  int first = 0;          // the own rows r > j are lr = first .. R-1
+  int jmodG = 0;          // j mod G: this CTA owns row j when jmodG == g
+  for (int j = 0; j < n; ++j, jmodG = jmodG + 1 == G ? 0 : jmodG + 1) {
+    if (first < R && g + first * G <= j) ++first;   // j passed an own row (at most one per column)
+    const int Ra = R - first;
     double2* uC = (j & 1) ? ubuf1 : ubuf0;   // this column's reflector, unscaled
     double2* uP = (j & 1) ? ubuf0 : ubuf1;   // previous column's
     // (A) row j and y of column j-1 into shared memory; s, hh and row j's coefficients (every load
@@ -211,7 +220,7 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_eh_tridiag(TriArgs p) {
       double2 A = Pj, B = Pj;
       if (j > 0) {
         const double2* rc = p.rowcoef + ((j - 1) & 1) * 4;
-        sv = __ldcg(&p.sacc[(j - 1) % 3]);
+        sv = __ldcg(&p.sacc[(j - 1) & 3]);
         A = __ldcg(&rc[0]);
         B = __ldcg(&rc[1]);
         Qj = __ldcg(&rc[2]);
@@ -243,7 +252,7 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_eh_tridiag(TriArgs p) {
         Pj = make_double2(fma(-hh, B.x, A.x), fma(-hh, B.y, A.y));
       }
     }
-    if (g == 0 && tid == 0) p.sacc[(j + 1) % 3] = 0.0;   // last read at the start of column j-1
+    if (g == 0 && tid == 0) p.sacc[(j + 2) & 3] = 0.0;   // slot of column j-2, read at the start of j-1
     __syncthreads();
     // (B) column j-1's update of row j, its diagonal, the reflector's vector uC[c] (c > j) and sigma
     double sig = 0.0, dj = 0.0;
@@ -298,44 +307,72 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_eh_tridiag(TriArgs p) {
         s2_sh = 2.0 * fma(scale.x, scale.x, scale.y * scale.y);              // 2 |scale|^2
       }
     }
-    {
-      int Ra = 0;   // own rows r > j are lr = first .. R-1
-      const int first = j >= g ? (j - g) / G + 1 : 0;
-      Ra = R - first;
-      if (Ra > 0) {
-        const int q = min(min((NW + Ra - 1) / Ra, kMaxParts / Ra), kMaxPartsPerRow);
-        const int m = n - 1 - j;
-        const int chunk = ((m + q - 1) / q + 31) & ~31;
-        for (int part = wid; part < Ra * q; part += NW) {
-          const int lr = first + part / q, k = part % q;
-          const int r = g + lr * G;
-          double2* row = rows + (size_t)lr * n;
-          const double2 P = make_double2(fma(-hh, cB[lr].x, cA[lr].x), fma(-hh, cB[lr].y, cA[lr].y));
-          const double2 Q = cQ[lr];
-          const int c0 = j + 1 + k * chunk, c1 = min(n, c0 + chunk);
-          double ax = 0.0, ay = 0.0;
-          double2 a1 = make_double2(0.0, 0.0);
-          for (int c = c0 + lane; c < c1; c += 32) {
-            double2 a = row[c];
-            if (j > 0) {
-              a = rank2_sub(a, P, make_double2(uP[c].x, -uP[c].y), Q, yP[c]);
-              row[c] = a;
+    if (Ra > 0) {
+      // whole rows go round-robin to the four schedulers (warp & 3), each leftover row is cut into
+      // quarters, one per scheduler, so every scheduler carries Ra / 4 rows of float64 work; the two
+      // warps of a scheduler (wid and wid + 4) alternate over its items.  Slot k of a row's partial
+      // sums is its quarter k (slot 0 for a whole row, which then holds column j+1).
+      const int m = n - 1 - j;
+      const int rem = Ra & 3, full = Ra - rem;
+      const int sched = wid & 3, half = wid >> 2;
+      const int quarter = split_chunk(m, 4);
+      int ord = 0;
+      for (int it = sched; it < full + 4 * rem; it += 4, ++ord) {
+        if ((ord & 1) != half) continue;
+        int i, k, c0, c1;
+        if (it < full) {
+          i = it;
+          k = 0;
+          c0 = j + 1;
+          c1 = n;
+        } else {
+          i = full + (it - full) / 4;   // it - full = 4 t + sched
+          k = sched;
+          c0 = j + 1 + k * quarter;
+          c1 = min(n, c0 + quarter);
+        }
+        const int lr = first + i;
+        const int r = g + lr * G;
+        double2* row = rows + (size_t)lr * n;
+        const double2 P = make_double2(fma(-hh, cB[lr].x, cA[lr].x), fma(-hh, cB[lr].y, cA[lr].y));
+        const double2 Q = cQ[lr];
+        double ax = 0.0, ay = 0.0, bx = 0.0, by = 0.0;
+        double2 a1 = make_double2(0.0, 0.0);
+        for (int c = c0 + lane; c < c1; c += 64) {
+          const int c2 = c + 32;
+          const bool two = c2 < c1;
+          double2 a = row[c];
+          double2 b = two ? row[c2] : make_double2(0.0, 0.0);
+          if (j > 0) {
+            a = rank2_sub(a, P, make_double2(uP[c].x, -uP[c].y), Q, yP[c]);
+            row[c] = a;
+            if (two) {
+              b = rank2_sub(b, P, make_double2(uP[c2].x, -uP[c2].y), Q, yP[c2]);
+              row[c2] = b;
             }
-            if (c == j + 1) {
-              a1 = a;
-            } else {
-              const double2 u = uC[c];            // a * conj(u)
-              ax = fma(a.x, u.x, fma(a.y, u.y, ax));
-              ay = fma(a.y, u.x, fma(-a.x, u.y, ay));
-            }
-            if (r == j + 1) p.rnext[(j & 1) * n + c] = a;
           }
-          ax = warp_sum(ax);
-          ay = warp_sum(ay);
-          if (lane == 0) {
-            pacc[part] = make_double2(ax, ay);
-            pa1[part] = a1;
+          if (c == j + 1) {
+            a1 = a;
+          } else {
+            const double2 u = uC[c];            // a * conj(u)
+            ax = fma(a.x, u.x, fma(a.y, u.y, ax));
+            ay = fma(a.y, u.x, fma(-a.x, u.y, ay));
           }
+          if (two) {
+            const double2 u = uC[c2];
+            bx = fma(b.x, u.x, fma(b.y, u.y, bx));
+            by = fma(b.y, u.x, fma(-b.x, u.y, by));
+          }
+          if (r == j + 1) {
+            p.rnext[(j & 1) * n + c] = a;
+            if (two) p.rnext[(j & 1) * n + c2] = b;
+          }
+        }
+        ax = warp_sum(ax + bx);
+        ay = warp_sum(ay + by);
+        if (lane == 0) {
+          pacc[i * 4 + k] = make_double2(ax, ay);
+          if (k == 0) pa1[i] = a1;
         }
       }
     }
@@ -345,20 +382,17 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_eh_tridiag(TriArgs p) {
     //     the owner of row j stores v_j; CTA 0 the outputs of column j
     const double2 tauC = tau_sh, scC = scale_sh;
     const double2 cscC = make_double2(scC.x, -scC.y);
-    const int first = j >= g ? (j - g) / G + 1 : 0;
-    const int Ra = R - first;
-    const int q = Ra > 0 ? min(min((NW + Ra - 1) / Ra, kMaxParts / Ra), kMaxPartsPerRow) : 1;
     const double2 tcs = tcs_sh, cts = cts_sh;
     const double s2 = s2_sh;
     // the own rows' y_j (lanes of warps 0 and 1 over the rows) and the coefficients of column j's
     // update for row lr: A = tau y conj(scale), B = 2 v conj(scale), Q = conj(tau) v
     auto row_y = [&](int i) {
-      double2 acc = pacc[i * q];
-      for (int k = 1; k < q; ++k) {
-        acc.x += pacc[i * q + k].x;
-        acc.y += pacc[i * q + k].y;
+      double2 acc = pacc[i * 4];
+      if (i >= Ra - (Ra & 3)) {   // a leftover row: four quarters
+        acc.x += (pacc[i * 4 + 1].x + pacc[i * 4 + 2].x) + pacc[i * 4 + 3].x;
+        acc.y += (pacc[i * 4 + 1].y + pacc[i * 4 + 2].y) + pacc[i * 4 + 3].y;
       }
-      const double2 a1 = pa1[i * q];
+      const double2 a1 = pa1[i];
       return make_double2(fma(scC.x, acc.x, fma(-scC.y, acc.y, a1.x)), fma(scC.x, acc.y, fma(scC.y, acc.x, a1.y)));
     };
     auto coefs = [&](int lr, int r, double2 y, double2* A, double2* B, double2* Q) {
@@ -380,7 +414,7 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_eh_tridiag(TriArgs p) {
       }
       sp = warp_sum(sp);
       if (lane == 0) {
-        atomicAdd(&p.sacc[j % 3], sp);
+        atomicAdd(&p.sacc[j & 3], sp);
         if (g == 0) {
           p.d[j] = dj;
           p.e[j] = beta_sh;
@@ -400,7 +434,7 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_eh_tridiag(TriArgs p) {
       rc[2] = Q;
       rc[3] = make_double2(2.0 * fma(tauC.x, y.x, -tauC.y * y.y), 0.0);
     }
-    if (g == j % G) {   // the owner of row j stores u_j; k_eh_vscale forms v_j = conj(u_j) scale_j
+    if (jmodG == g) {   // the owner of row j stores u_j; k_eh_vscale forms v_j = conj(u_j) scale_j
       for (int c = j + 2 + tid; c < n; c += kTriThreads) p.vref[(size_t)j * n + c] = uC[c];
     }
     grid_arrive(p.bar);
@@ -888,7 +922,7 @@ int tri_ctas(const Context& c, int n) {
 
 size_t tri_smem(int n, int G) {
   const int R = (n + G - 1) / G;
-  return sizeof(double2) * ((size_t)(3 + R) * n + 3 * (size_t)R + 2 * kMaxParts);
+  return sizeof(double2) * ((size_t)(3 + R) * n + 8 * (size_t)R);
 }
 
 }  // namespace
