@@ -84,7 +84,10 @@ enum hpsi_option {
                                  matrices, Ritz vectors) 0 (default): float32 on the CUDA cores;
                                  1: float32 emulated by cuBLAS with bf16 tensor-core products
                                  (three bf16 terms per operand, nine products); 2: the Gauss
-                                 three-product complex form (CGEMM3M) */
+                                 three-product complex form (CGEMM3M); 3: the library's split:
+                                 three bf16 terms per operand, six products accumulated in float32
+                                 by bf16 tensor-core GEMMs, on the interleaved storage read as real
+                                 matrices (the basis splits are cached across the iteration) */
 };
 
 /* Kernel classes reported by hpsi_kernel_stats. */

@@ -75,6 +75,8 @@ struct DavWork {
   float2* ovl32 = nullptr;    // [nbnd][nbnd]
   float2* hcol32 = nullptr;   // [mmax][nbnd]
   float* hdiag32 = nullptr;   // [npw] float copy of <k+G|H|k+G>
+  SplitBasis phi_split, hphi_split;   // bf16 splits of the basis for the tensor-core products
+  SubspaceGemm sg;
   double2* in64 = nullptr;    // [nbnd][npw]
   double2* out64 = nullptr;   // [nbnd][npw]
 };
@@ -240,6 +242,9 @@ static void free_work(DavWork& w) {
   cudaFree(w.ovl32);
   cudaFree(w.hcol32);
   cudaFree(w.hdiag32);
+  w.phi_split.release();
+  w.hphi_split.release();
+  w.sg.release();
   cudaFree(w.in64);
   cudaFree(w.out64);
   w = DavWork();
@@ -860,6 +865,9 @@ static int canonical_orth32(Context& c, DavHandles& h, const float2* x, int n, f
 static int hsub_columns32(Context& c, DavHandles& h, int rows, int col0, int ncol) {
   DavWork& w = h.wk;
   const int npw = w.npw, mmax = w.mmax;
+  if (c.fp32_gemm == 3)
+    return w.sg.ah_b(c, h.blas, rows, ncol, npw, w.phi_split, w.phi32, npw, w.hphi32 + (size_t)col0 * npw, npw, 1.f,
+                     0.f, nullptr, w.hsub + (size_t)col0 * mmax, mmax);
   BCK(cgemm32(c, h.blas, CUBLAS_OP_C, CUBLAS_OP_N, rows, ncol, npw, &cOne, Cf(w.phi32), npw,
                   Cf(w.hphi32 + (size_t)col0 * npw), npw, &cZero, Cf(w.hcol32), mmax),
       "cgemm H_sub columns");
@@ -886,6 +894,9 @@ static int davidson_run_mixed(Context& c, DavHandles& h, int ik, int nbnd, doubl
     cublasHandle_t b;
     ~MathReset() { cublasSetMathMode(b, CUBLAS_DEFAULT_MATH); }
   } math_reset{h.blas};
+  w.phi_split.invalidate();
+  w.hphi_split.invalidate();
+  const bool tc = c.fp32_gemm == 3;
   // phi32[0:N] <- orthonormalised initial guess
   HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
               (k_cvt_64_32<<<grid_of((size_t)N * npw), 256, 0, c.stream>>>((size_t)N * npw, psio, w.t32)));
@@ -907,12 +918,18 @@ static int davidson_run_mixed(Context& c, DavHandles& h, int ik, int nbnd, doubl
     if (rc) return rc;
     HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
                 (k_mat_64_to_32<<<(m * N + 255) / 256, 256, 0, c.stream>>>(m, N, w.evec, m, w.small32, m)));
-    BCK(cgemm32(c, h.blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, N, m, &cOne, Cf(w.phi32), npw, Cf(w.small32), m, &cZero,
-                    Cf(w.psi32), npw),
-        "cgemm Ritz vectors");
-    BCK(cgemm32(c, h.blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, N, m, &cOne, Cf(w.hphi32), npw, Cf(w.small32), m, &cZero,
-                    Cf(w.hpsi32), npw),
-        "cgemm H Ritz vectors");
+    if (tc) {
+      rc = w.sg.a_b(c, h.blas, npw, N, m, w.phi_split, w.phi32, npw, w.small32, m, 1.f, 0.f, w.psi32, npw);
+      if (!rc) rc = w.sg.a_b(c, h.blas, npw, N, m, w.hphi_split, w.hphi32, npw, w.small32, m, 1.f, 0.f, w.hpsi32, npw);
+      if (rc) return rc;
+    } else {
+      BCK(cgemm32(c, h.blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, N, m, &cOne, Cf(w.phi32), npw, Cf(w.small32), m, &cZero,
+                  Cf(w.psi32), npw),
+          "cgemm Ritz vectors");
+      BCK(cgemm32(c, h.blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, N, m, &cOne, Cf(w.hphi32), npw, Cf(w.small32), m, &cZero,
+                  Cf(w.hpsi32), npw),
+          "cgemm H Ritz vectors");
+    }
     DCK(cudaMemcpyAsync(w.eps, w.w, sizeof(double) * N, cudaMemcpyDeviceToDevice, c.stream), "eps copy");
     HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_residual32<<<N, 1024, 0, c.stream>>>(npw, w.psi32, w.hpsi32, w.eps, w.t32, w.rnorm)));
     DCK(cudaMemcpyAsync(rn.data(), w.rnorm, sizeof(double) * N, cudaMemcpyDeviceToHost, c.stream), "norm copy");
@@ -931,6 +948,8 @@ static int davidson_run_mixed(Context& c, DavHandles& h, int ik, int nbnd, doubl
     if (m + nc > mmax) {
       DCK(cudaMemcpyAsync(w.phi32, w.psi32, vb * N, cudaMemcpyDeviceToDevice, c.stream), "restart copy");
       DCK(cudaMemcpyAsync(w.hphi32, w.hpsi32, vb * N, cudaMemcpyDeviceToDevice, c.stream), "restart copy");
+      w.phi_split.invalidate();
+      w.hphi_split.invalidate();
       m = N;
       rc = hsub_columns32(c, h, m, 0, m);
       if (rc) return rc;
@@ -942,12 +961,18 @@ static int davidson_run_mixed(Context& c, DavHandles& h, int ik, int nbnd, doubl
                                                                                 c.opt_tau, eshift, tnew)));
     for (int round = 0; round < 2; ++round) {
       for (int pass = 0; pass < 2; ++pass) {
-        BCK(cgemm32(c, h.blas, CUBLAS_OP_C, CUBLAS_OP_N, m, nc, npw, &cOne, Cf(w.phi32), npw, Cf(tnew), npw, &cZero,
-                        Cf(w.small32), m),
-            "cgemm projection");
-        BCK(cgemm32(c, h.blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, nc, m, &cMinusOne, Cf(w.phi32), npw, Cf(w.small32), m,
-                        &cOne, Cf(tnew), npw),
-            "cgemm projection update");
+        if (tc) {
+          rc = w.sg.ah_b(c, h.blas, m, nc, npw, w.phi_split, w.phi32, npw, tnew, npw, 1.f, 0.f, w.small32, nullptr, m);
+          if (!rc) rc = w.sg.a_b(c, h.blas, npw, nc, m, w.phi_split, w.phi32, npw, w.small32, m, -1.f, 1.f, tnew, npw);
+          if (rc) return rc;
+        } else {
+          BCK(cgemm32(c, h.blas, CUBLAS_OP_C, CUBLAS_OP_N, m, nc, npw, &cOne, Cf(w.phi32), npw, Cf(tnew), npw, &cZero,
+                      Cf(w.small32), m),
+              "cgemm projection");
+          BCK(cgemm32(c, h.blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, nc, m, &cMinusOne, Cf(w.phi32), npw, Cf(w.small32), m,
+                      &cOne, Cf(tnew), npw),
+              "cgemm projection update");
+        }
       }
       if (round == 1) break;
       HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_norm2_32<<<nc, 1024, 0, c.stream>>>(npw, tnew, w.cn2)));

@@ -1,6 +1,8 @@
 // Internal declarations of libhpsi: problem geometry, FFT plans, context, launchers.
 #pragma once
 
+#include <cublas_v2.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <string>
@@ -199,6 +201,33 @@ int check_device_error(Context& c);   // synchronizes; HPSI_ETIMEOUT if a bounde
 int davidson_run(Context& c, int ik, int nbnd, double tol, int maxiter, double2* psi, double* eig,
                  int* iters, double* resnorm);
 void davidson_release(Context& c);
+
+// ---- complex64 subspace products on the bf16 tensor cores (subspace_gemm.cu) ----
+// Three-term bf16 split of a complex64 matrix's columns, kept valid up to `valid` columns.
+struct SplitBasis {
+  __nv_bfloat16* terms[3] = {nullptr, nullptr, nullptr};
+  size_t cap = 0;
+  int valid = 0;
+  const float2* base = nullptr;
+  int lds = 0;
+  int ensure(Context& c, const float2* src, int ld, int cols);
+  void invalidate() { valid = 0; }
+  void release();
+};
+struct SubspaceGemm {
+  __nv_bfloat16* bt[3] = {nullptr, nullptr, nullptr};
+  float* P = nullptr;
+  size_t bcap = 0, pcap = 0;
+  int grow(Context& c, size_t bterms, size_t pfloats);
+  // C (m x n) = alpha A^H B + beta C with A (k x m, lda) split through `split`; C64 (if not null)
+  // is written instead of C32
+  int ah_b(Context& c, cublasHandle_t h, int m, int n, int k, SplitBasis& split, const float2* A, int lda,
+           const float2* B, int ldb, float alpha, float beta, float2* C32, double2* C64, int ldc);
+  // C (M x n) = alpha A B + beta C with A (M x k, lda) split through `split`
+  int a_b(Context& c, cublasHandle_t h, int M, int n, int k, SplitBasis& split, const float2* A, int lda,
+          const float2* B, int ldb, float alpha, float beta, float2* C, int ldc);
+  void release();
+};
 
 // ---- reduced Hermitian eigenproblem (eigh.cu) ----
 bool eigh_supported(const Context& c, int n);
