@@ -142,3 +142,36 @@ def test_davidson_kpoints_c4a(lib):
         x = torch.from_numpy(workloads.psi0(p.lattice, kp[ik], ms[ik], p.nbnd, p.psi_seed + ik)).cuda()
         eig, it, res, rc = B.davidson_solve(ctx, ik, x, 1e-8, 300)
         assert np.max(np.abs(eig - np.asarray(ref[ik]))) < 1e-10
+
+
+@pytest.mark.parametrize("gemm", [3, 2])
+def test_davidson_mixed_c2_subspace_gemm_options(lib, gemm):
+    """The mixed solve with the split-bf16 tensor-core subspace products (3) and with CGEMM3M (2)
+    reaches the same eigenvalues, and its reduced problems all go through the library's eigensolver."""
+    import torch
+    from paper_0906_2569_gb300 import binding as B
+    p = workloads.config2()
+    ctx, m, vr, beta, d = _setup(p, precision=B.HPSI_MIXED)
+    B.hpsi_set_option(ctx, B.HPSI_OPT_FP32_GEMM, gemm)
+    B.hpsi_kernel_stats(ctx, -3, reset=True)
+    x = torch.from_numpy(workloads.psi0(p.lattice, p.kpts[0], m, p.nbnd, p.psi_seed)).cuda()
+    eig, it, res, rc = B.davidson_solve(ctx, 0, x, 1e-5, 300)
+    assert np.max(np.abs(eig - np.asarray(_golden("c2")))) < 1e-6
+    calls, fallbacks = B.hpsi_kernel_stats(ctx, -3)
+    assert calls >= it and fallbacks == 0
+
+
+def test_davidson_cusolver_option_matches(lib):
+    """HPSI_OPT_EIGENSOLVER = 0 (cuSOLVER zheevdx for the reduced problems) gives the same float64
+    eigenvalues as the library's own eigensolver, and the library counters stay at zero."""
+    import torch
+    from paper_0906_2569_gb300 import binding as B
+    p = workloads.config1()
+    ctx, m, vr, beta, d = _setup(p)
+    x0 = torch.from_numpy(workloads.psi0(p.lattice, p.kpts[0], m, p.nbnd, p.psi_seed)).cuda()
+    e1, _, _, _ = B.davidson_solve(ctx, 0, x0.clone(), 1e-8, 200)
+    B.hpsi_set_option(ctx, B.HPSI_OPT_EIGENSOLVER, 0)
+    B.hpsi_kernel_stats(ctx, -3, reset=True)
+    e0, _, _, _ = B.davidson_solve(ctx, 0, x0.clone(), 1e-8, 200)
+    assert B.hpsi_kernel_stats(ctx, -3)[0] == 0
+    assert np.max(np.abs(e1 - e0)) < 1e-10
