@@ -44,7 +44,7 @@ constexpr int kTriThreads = 256;                     // threads per CTA of the r
 constexpr int kMaxN = 1024;                          // largest n handled here
 constexpr int kLoadK = (kMaxN + 255) / 256;          // row elements per thread of the column loads
 constexpr long long kBarrierLimit = 2000000000LL;    // clock cycles (about 1 s) per barrier wait
-constexpr int kInvIters = 3;                         // inverse-iteration solves per eigenvector
+constexpr int kInvIters = 2;                         // inverse-iteration solves per eigenvector
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -694,6 +694,7 @@ __global__ void __launch_bounds__(32) k_eh_invit(int n, const double* __restrict
 }
 
 constexpr int kWY = 64;   // reflectors per compact-WY block of the back-transformation
+constexpr int kWYRows = kWY / 32;   // rows of a block per lane in the back substitution
 
 // v_j[c] = conj(u_j[c]) scale_j for c > j + 1 and v_j[j + 1] = 1, in place (rows j < n - 1).
 __global__ void k_eh_vscale(int n, const double2* __restrict__ vscale, double2* __restrict__ vref) {
@@ -728,13 +729,12 @@ __global__ void k_eh_widen(int n, int nwant, const double* __restrict__ Z, doubl
 // has the inverse S = T^-1 = diag(1 / tau_i) + (strictly upper part of G = V^H V).  Y = T W is then
 // a back substitution with S: y_q = tau_q (w_q - sum_{r > q} S_qr y_r), which needs no division and
 // gives y_q = 0 for an identity reflector (tau_q = 0).  One warp per column of W (in place), lane l
-// holds rows l and l + 32; rows are finalised from the last one, each subtracting its contribution
-// from the rows above.  G is the block's Gram matrix (column-major kWY x kWY; only its strictly
+// holds rows l, l + 32, ...; rows are finalised from the last one, each subtracting its
+// contribution from the rows above.  G is the block's Gram matrix (column-major kWY x kWY; only its strictly
 // upper part is read), tau the block's kWY reflector factors.
 __global__ void __launch_bounds__(128) k_eh_trsv(int ncol, const double2* __restrict__ G, const double2* __restrict__ tau,
                                                  double2* __restrict__ W) {
-  static_assert(kWY == 64, "two rows per lane");
-  __shared__ double2 gs[kWY * (kWY - 1) / 2];   // strictly upper part, column q at q (q - 1) / 2
+  extern __shared__ double2 gs[];   // strictly upper part of G, column q at q (q - 1) / 2
 #pragma unroll 4
   for (int idx = threadIdx.x; idx < kWY * (kWY - 1) / 2; idx += blockDim.x) {
     int q = (int)(0.5f * (1.0f + sqrtf(1.0f + 8.0f * (float)idx)));   // column: q (q - 1) / 2 <= idx
@@ -746,32 +746,43 @@ __global__ void __launch_bounds__(128) k_eh_trsv(int ncol, const double2* __rest
   const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (col >= ncol) return;
   double2* w = W + (size_t)col * kWY;
-  double2 acc0 = w[lane], acc1 = w[lane + 32];     // right-hand side, reduced as rows finalise
+  double2 acc[kWYRows];   // right-hand side rows lane + 32 s, reduced as rows finalise
+#pragma unroll
+  for (int sl = 0; sl < kWYRows; ++sl) acc[sl] = w[lane + 32 * sl];
   for (int q = kWY - 1; q >= 0; --q) {
-    // the owner finalises y_q = acc_q / S_qq, then every row r < q subtracts S_rq y_q
-    const int own = q & 31;
+    // the owner finalises y_q = tau_q acc_q, then every row r < q subtracts S_rq y_q
+    const int own = q & 31, oslot = q >> 5;
     double2 yq = make_double2(0.0, 0.0);
     if (lane == own) {
-      const double2 a = q < 32 ? acc0 : acc1, t = tau[q];
-      yq = make_double2(t.x * a.x - t.y * a.y, t.x * a.y + t.y * a.x);
-      if (q < 32) acc0 = yq; else acc1 = yq;
+      const double2 t = tau[q];
+#pragma unroll
+      for (int sl = 0; sl < kWYRows; ++sl)
+        if (sl == oslot) {
+          const double2 a = acc[sl];
+          yq = make_double2(t.x * a.x - t.y * a.y, t.x * a.y + t.y * a.x);
+          acc[sl] = yq;
+        }
     }
     yq.x = __shfl_sync(0xffffffffu, yq.x, own);
     yq.y = __shfl_sync(0xffffffffu, yq.y, own);
-    if (lane < q) {
-      const double2 s = gs[q * (q - 1) / 2 + lane];
-      acc0.x -= s.x * yq.x - s.y * yq.y;
-      acc0.y -= s.x * yq.y + s.y * yq.x;
-    }
-    if (lane + 32 < q) {
-      const double2 s = gs[q * (q - 1) / 2 + lane + 32];
-      acc1.x -= s.x * yq.x - s.y * yq.y;
-      acc1.y -= s.x * yq.y + s.y * yq.x;
+    const double2* gq = gs + q * (q - 1) / 2;
+#pragma unroll
+    for (int sl = 0; sl < kWYRows; ++sl) {
+      if (32 * sl < q) {   // warp-uniform: some row of this slot lies above q
+        const int r = lane + 32 * sl;
+        if (r < q) {
+          const double2 s = gq[r];
+          acc[sl].x -= s.x * yq.x - s.y * yq.y;
+          acc[sl].y -= s.x * yq.y + s.y * yq.x;
+        }
+      }
     }
   }
-  w[lane] = acc0;
-  w[lane + 32] = acc1;
+#pragma unroll
+  for (int sl = 0; sl < kWYRows; ++sl) w[lane + 32 * sl] = acc[sl];
 }
+
+constexpr size_t kTrsvSmem = sizeof(double2) * (size_t)kWY * (kWY - 1) / 2;
 
 struct EighState {
   cublasHandle_t blas = nullptr;
@@ -1022,12 +1033,14 @@ int eigh_lowest(Context& c, const double2* a, int lda, int n, int nwant, double*
                                   (long long)kWY * n, Zc(s->vref + 1), n, (long long)kWY * n, &zzero, Zc(s->wgram),
                                   kWY, (long long)kWY * kWY, K) != CUBLAS_STATUS_SUCCESS)
       return fail(c, HPSI_ECUDA, "eigh_lowest: reflector Gram matrices failed");
+    err = cudaFuncSetAttribute(k_eh_trsv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrsvSmem);
+    if (err != cudaSuccess) return cuda_fail(c, err, "eigh_lowest: smem attribute");
     for (int k = K - 1; k >= 0; --k) {
       const int r0 = k * kWY + 1, m = n - r0;
       double2* V = s->vref + (size_t)k * kWY * n + r0;
       if (cublasZgemm(s->blas, CUBLAS_OP_C, CUBLAS_OP_N, kWY, nwant, m, &zone, Zc(V), n, Zc(v_out + r0), n, &zzero,
                       Zc(s->w1), kWY) != CUBLAS_STATUS_SUCCESS ||
-          (k_eh_trsv<<<(nwant + 3) / 4, 128, 0, c.stream>>>(nwant, s->wgram + (size_t)k * kWY * kWY,
+          (k_eh_trsv<<<(nwant + 3) / 4, 128, kTrsvSmem, c.stream>>>(nwant, s->wgram + (size_t)k * kWY * kWY,
                                                              s->tau + (size_t)k * kWY, s->w1),
            cudaGetLastError() != cudaSuccess) ||
           cublasZgemm(s->blas, CUBLAS_OP_N, CUBLAS_OP_N, m, nwant, kWY, &zmone, Zc(V), n, Zc(s->w1), kWY, &zone,
