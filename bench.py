@@ -42,7 +42,10 @@ FP64_ALU_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12    # 2 DFMA / clk / SM (measured)
 # (kernel, precision) with the hash of its source files at capture time; a mismatch reports null.
 #   xvx_y mixed: k_plane<float,9,10>, 48-band launch, 51.73 MB read + 4.81 MB write (ncu_plane_c2.md)
 #   calbec fp64: k_calbec64, 160-band launch, 267.31 MB read + 7.14 MB write (ncu_calbec64_c2.md)
+#   tridiag: k_eh_tridiag, one n = 640 launch, 3.372 MB read + 0.030 MB write, per matrix element
+#            (ncu_eigh_n640.md)
 NCU_TRAFFIC = {
+    ("tridiag", -1): (("eigh.cu",), "92283e7e012b", (3372032 + 30464) / 640 ** 2),
     ("xvx_y", 1): (("local_fast.cu", "fft_codelets.cuh"), "92564643ab55", (51.725568e6 + 4.813056e6) / 48),
     ("calbec", 0): (("nonlocal_fp64.cu",), "f2c91a1c9ad9", (267.307264e6 + 7.139584e6) / 160),
 }
@@ -284,6 +287,7 @@ def run_gpu(args):
         barrier()
         B.hpsi_kernel_stats(ctx, -1, reset=True)
         B.hpsi_kernel_stats(ctx, -2, reset=True)
+        B.hpsi_kernel_stats(ctx, -4, reset=True)
         for kk in range(len(B.KERNELS)):
             B.hpsi_kernel_stats(ctx, kk, reset=True)
         B.hpsi_set_option(ctx, B.HPSI_OPT_KERNEL_TIMING, 1)
@@ -299,6 +303,7 @@ def run_gpu(args):
         ms = [a.elapsed_time(b) for a, b in evs]
         launches, _ = B.hpsi_kernel_stats(ctx, -1)
         bapps, _ = B.hpsi_kernel_stats(ctx, -2)
+        _, tri_flops = B.hpsi_kernel_stats(ctx, -4)
         kstats = {}
         for kk, name in enumerate(B.KERNELS):
             n, t = B.hpsi_kernel_stats(ctx, kk)
@@ -306,6 +311,7 @@ def run_gpu(args):
                 kstats[name] = {"launches": n, "ms": t}
         B.hpsi_set_option(ctx, B.HPSI_OPT_KERNEL_TIMING, 0)
         res = {"total_ms": sum(ms), "ms": ms, "band_apps": bapps, "launches": launches, "kernels": kstats,
+               "tridiag_flops": tri_flops,
                "clocks": clk.summary(), "iters": info["iters"], "max_residual": info["res"], "status": info["rc"]}
         if golden is not None and len(golden["eigenvalues"]) == p.nbnd:
             res["max_eig_error_ha"] = float(np.max(np.abs(info["eig"] - np.asarray(golden["eigenvalues"]))))
@@ -357,6 +363,7 @@ def run_gpu(args):
             dist.destroy_process_group()
         return
     roof = roofline(mixed, p, npw, nst, npl, B.HPSI_MIXED)
+    roof_hpsi = roofline(mixed, p, npw, nst, npl, B.HPSI_MIXED, classes=HPSI_CLASSES)
     roof64 = roofline(fp64, p, npw, nst, npl, B.HPSI_FP64)
     out = {
         "metric": "H|psi> band-applications/s (mixed precision; float64 beside it)",
@@ -379,6 +386,7 @@ def run_gpu(args):
         "hpsi_apply_band_apps_per_s": p.nbnd / (mixed["hpsi_ms"] / 1e3),
         "kernels": mixed["kernels"],
         "roofline": roof,
+        "roofline_hpsi": roof_hpsi,
         "clocks": mixed["clocks"],
         "gpu_launches": mixed["launches"],
     }
@@ -512,7 +520,32 @@ def kernel_work(name, p, npw, nst, npl, precision, nproj):
 FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2070 MHz
 
 
-def roofline(res, p, npw, nst, npl, precision):
+def tridiag_roofline(res, kst, hbm):
+    """Roofline of the Householder reduction of the reduced eigenproblems: float64 ALU bound.
+
+    Algorithmic work per launch: 16 n^3 / 3 real flops (complex Hermitian tridiagonalisation), summed
+    by the library over the timed launches; the launches' n vary with the reduced basis."""
+    secs = kst["ms"] / 1e3
+    ach = res["tridiag_flops"] / secs / 1e12
+    nlaunch = kst["launches"]
+    n_eff = (res["tridiag_flops"] / nlaunch / (16.0 / 3.0)) ** (1.0 / 3.0)
+    traffic = None
+    key = ("tridiag", -1)
+    if key in NCU_TRAFFIC and NCU_TRAFFIC[key][1] == source_hash(NCU_TRAFFIC[key][0]):
+        traffic = NCU_TRAFFIC[key][2] * n_eff ** 2      # bytes per matrix element, x n^2
+    return {"kernel": "tridiag", "avg_launch_ms": kst["ms"] / nlaunch, "launches": nlaunch,
+            "flops_per_launch": res["tridiag_flops"] / nlaunch, "n_cube_root_mean_cube": n_eff,
+            "traffic": traffic,
+            "traffic_note": "ncu dram read+write of one n = 640 launch per matrix element (profiles/), "
+                            "x n_eff^2 with n_eff the cube root of the mean n^3 of the timed launches",
+            "bound": "alu", "achieved": ach, "peak": FP64_ALU_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_ALU_TFLOPS,
+            "peak_source": "derived: 152 SMs x 2 DFMA/clk (measured) x 2 flop x 2070 MHz"}
+
+
+HPSI_CLASSES = ("inv_zy", "xvx_y", "fwd_z", "calbec", "addvus")
+
+
+def roofline(res, p, npw, nst, npl, precision, classes=HPSI_CLASSES + ("tridiag",)):
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -520,10 +553,12 @@ def roofline(res, p, npw, nst, npl, precision):
         pass
     hbm = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
     ks = res["kernels"]
-    cand = {k: v for k, v in ks.items() if k in ("inv_zy", "xvx_y", "fwd_z", "calbec", "addvus") and v["ms"] > 0}
+    cand = {k: v for k, v in ks.items() if k in classes and v["ms"] > 0}
     if not cand:
         return None
     name = max(cand, key=lambda k: cand[k]["ms"])
+    if name == "tridiag" and res.get("tridiag_flops"):
+        return tridiag_roofline(res, cand[name], hbm)
     units = res["band_apps"]
     byt, flop = kernel_work(name, p, npw, nst, npl, precision, p.nproj)
     secs = cand[name]["ms"] / 1e3

@@ -100,9 +100,10 @@ enum hpsi_kernel {
   HPSI_K_ADDVUS = 5,   /* hpsi += beta (D <beta|psi>) */
   HPSI_K_SPLIT = 6,    /* mixed path: bf16 operand splitting */
   HPSI_K_DAVIDSON = 7, /* Davidson residual / preconditioner / helper kernels */
-  HPSI_K_EIGH = 8,     /* reduced eigenproblem: tridiagonal reduction, multisection, inverse
-                          iteration, back-transformation */
-  HPSI_K_COUNT = 9
+  HPSI_K_EIGH = 8,     /* reduced eigenproblem: multisection, inverse iteration,
+                          back-transformation helpers */
+  HPSI_K_TRIDIAG = 9,  /* reduced eigenproblem: the Householder reduction to tridiagonal form */
+  HPSI_K_COUNT = 10
 };
 
 enum hpsi_precision {
@@ -279,7 +280,9 @@ HPSI_API int hpsi_set_option(hpsi_ctx* ctx, int option, double value);
  *   kernel       in   an hpsi_kernel value, -1 for all classes together (total_ms then 0),
  *                     -2 for the number of H|psi> band-applications performed (in launches), or
  *                     -3 for the reduced eigenproblems solved by the library's own eigensolver
- *                     (in launches) and how many of them it handed to cuSOLVER (in total_ms)
+ *                     (in launches) and how many of them it handed to cuSOLVER (in total_ms), or
+ *                     -4 for the tridiagonal reductions run by the library (in launches) and
+ *                     their algorithmic float64 work, sum of 16 n^3 / 3 real flops (in total_ms)
  *   launches     out  nullable; number of launches
  *   total_ms     out  nullable; summed event time (synchronizes the context's stream)
  *   reset        in   non-zero: clear the counters after reading

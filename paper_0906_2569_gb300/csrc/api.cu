@@ -839,7 +839,16 @@ extern "C" int hpsi_set_option(hpsi_ctx* ctx, int option, double value) {
 extern "C" int hpsi_kernel_stats(hpsi_ctx* ctx, int kernel, long long* launches, double* total_ms, int reset) {
   if (!ctx) return HPSI_EINVAL;
   Context& c = ctx->c;
-  if (kernel < -3 || kernel >= HPSI_K_COUNT) return fail(c, HPSI_EINVAL, "hpsi_kernel_stats: bad kernel class");
+  if (kernel < -4 || kernel >= HPSI_K_COUNT) return fail(c, HPSI_EINVAL, "hpsi_kernel_stats: bad kernel class");
+  if (kernel == -4) {
+    if (launches) *launches = c.tri_calls;
+    if (total_ms) *total_ms = c.tri_flops;
+    if (reset) {
+      c.tri_calls = 0;
+      c.tri_flops = 0.0;
+    }
+    return HPSI_OK;
+  }
   if (kernel == -3) {
     if (launches) *launches = c.eig_calls;
     if (total_ms) *total_ms = (double)c.eig_fallbacks;

@@ -984,9 +984,11 @@ int eigh_lowest(Context& c, const double2* a, int lda, int n, int nwant, double*
   TriArgs ta{n, lda, G, a, s->d, s->e, s->e2, s->tau, s->vref, s->ybuf, s->rnext, s->rowcoef, s->vscale, s->sacc, s->bar,
              c.d_err};
   void* args[] = {&ta};
-  HPSI_LAUNCH(c, HPSI_K_EIGH,
+  HPSI_LAUNCH(c, HPSI_K_TRIDIAG,
               (err = cudaLaunchCooperativeKernel((const void*)k_eh_tridiag, dim3(G), dim3(kTriThreads), args, smem,
                                                  c.stream)));
+  ++c.tri_calls;
+  c.tri_flops += 16.0 / 3.0 * (double)n * (double)n * (double)n;
   if (err == cudaErrorCooperativeLaunchTooLarge) {   // the device cannot hold the grid at once
     cudaGetLastError();
     *fallback = true;

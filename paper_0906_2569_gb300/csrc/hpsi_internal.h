@@ -142,6 +142,8 @@ struct Context {
   long long band_apps = 0;             // H|psi> band-applications performed
   long long eig_calls = 0;             // reduced eigenproblems solved by the library's kernels
   long long eig_fallbacks = 0;         // ... and handed to cuSOLVER instead
+  long long tri_calls = 0;             // tridiagonal reductions run by the library
+  double tri_flops = 0.0;              // sum over them of 16 n^3 / 3 (complex Hermitian)
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> trec;   // (kernel, start, end)
   std::vector<cudaEvent_t> evpool;
   double tacc[HPSI_K_COUNT] = {0.0};

@@ -117,8 +117,12 @@ def test_library_path_ran_and_matches_cusolver(ctx):
     a = workloads.hermitian_matrix(400, 11, scale=30.0)
     keig = B.KERNELS.index("eigh")
     B.hpsi_kernel_stats(ctx, -1, reset=True)
+    B.hpsi_kernel_stats(ctx, -4, reset=True)
     w1, x1 = _solve(ctx, a, 100)
-    assert B.hpsi_kernel_stats(ctx, keig)[0] >= 4   # reduction, multisection, inverse iteration, back-transform
+    assert B.hpsi_kernel_stats(ctx, keig)[0] >= 3   # multisection, inverse iteration, back-transform helpers
+    assert B.hpsi_kernel_stats(ctx, B.KERNELS.index("tridiag"))[0] == 1
+    calls, flops = B.hpsi_kernel_stats(ctx, -4)
+    assert calls == 1 and flops == pytest.approx(16.0 / 3.0 * 400 ** 3)
     B.hpsi_set_option(ctx, B.HPSI_OPT_EIGENSOLVER, 0)
     try:
         B.hpsi_kernel_stats(ctx, -1, reset=True)
