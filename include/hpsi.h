@@ -80,7 +80,7 @@ enum hpsi_option {
                                  Sturm multisection, inverse iteration, back-transformation) for
                                  n <= 1024, cuSOLVER zheevdx above that or if inverse iteration
                                  loses a vector; 0: cuSOLVER zheevdx always */
-  HPSI_OPT_FP32_GEMM = 11     /* mixed davidson_solve: complex64 subspace GEMMs (projections, reduced
+  HPSI_OPT_FP32_GEMM = 11,    /* mixed davidson_solve: complex64 subspace GEMMs (projections, reduced
                                  matrices, Ritz vectors) 0 (default): float32 on the CUDA cores;
                                  1: float32 emulated by cuBLAS with bf16 tensor-core products
                                  (three bf16 terms per operand, nine products); 2: the Gauss
@@ -88,6 +88,26 @@ enum hpsi_option {
                                  three bf16 terms per operand, six products accumulated in float32
                                  by bf16 tensor-core GEMMs, on the interleaved storage read as real
                                  matrices (the basis splits are cached across the iteration) */
+  HPSI_OPT_LOCKING = 12,      /* mixed davidson_solve: hard locking of converged Ritz pairs.  0: none
+                                 (converged bands get no correction but stay in the Rayleigh-Ritz
+                                 problem); 1: the lowest run of converged bands is frozen, taken out
+                                 of the reduced basis, and later corrections are orthogonalised
+                                 against it; 2: every converged band is frozen that way.  A lock
+                                 restarts the reduced basis from the remaining Ritz vectors. */
+  HPSI_OPT_LOCK_BATCH = 13,   /* a lock is taken once at least this fraction (0..1, default 0: one
+                                 band) of the active bands is lockable */
+  HPSI_OPT_LOCK_BASIS = 14,   /* after the first lock the reduced basis grows to at most this many
+                                 times the active band count (>= 2, default 4) before a restart,
+                                 and never past HPSI_OPT_BASIS times N */
+  HPSI_OPT_THICK_RESTART = 15, /* davidson_solve: 0: a restart (or a lock) keeps the wanted (active)
+                                 Ritz vectors; 1 (default): it keeps the lowest non-locked Ritz
+                                 vectors up to half the basis limit (at least the active ones).  A
+                                 mixed solve whose largest residual has not fallen by 10% in 8
+                                 iterations continues with plain restarts */
+  HPSI_OPT_RITZ_SPLIT = 16    /* mixed davidson_solve: 1: the Ritz-vector and restart products
+                                 (inner dimension = basis size) run as float32 GEMMs over at most 8
+                                 chunks of the inner dimension whose results are added in float64;
+                                 0: one float32 GEMM */
 };
 
 /* Kernel classes reported by hpsi_kernel_stats. */

@@ -798,6 +798,32 @@ extern "C" int hpsi_set_option(hpsi_ctx* ctx, int option, double value) {
     c.fp32_gemm = (int)value;
     return HPSI_OK;
   }
+  if (option == HPSI_OPT_LOCKING) {
+    if (value != 0.0 && value != 1.0 && value != 2.0) return fail(c, HPSI_EINVAL, "HPSI_OPT_LOCKING must be 0, 1 or 2");
+    c.locking = (int)value;
+    return HPSI_OK;
+  }
+  if (option == HPSI_OPT_LOCK_BATCH) {
+    if (!(value >= 0.0 && value <= 1.0)) return fail(c, HPSI_EINVAL, "HPSI_OPT_LOCK_BATCH must be in [0, 1]");
+    c.lock_batch = value;
+    return HPSI_OK;
+  }
+  if (option == HPSI_OPT_LOCK_BASIS) {
+    if (!(value >= 2.0 && value <= 64.0) || value != std::floor(value))
+      return fail(c, HPSI_EINVAL, "HPSI_OPT_LOCK_BASIS must be an integer in [2, 64]");
+    c.lock_basis = (int)value;
+    return HPSI_OK;
+  }
+  if (option == HPSI_OPT_THICK_RESTART) {
+    if (value != 0.0 && value != 1.0) return fail(c, HPSI_EINVAL, "HPSI_OPT_THICK_RESTART must be 0 or 1");
+    c.thick_restart = (int)value;
+    return HPSI_OK;
+  }
+  if (option == HPSI_OPT_RITZ_SPLIT) {
+    if (value != 0.0 && value != 1.0) return fail(c, HPSI_EINVAL, "HPSI_OPT_RITZ_SPLIT must be 0 or 1");
+    c.ritz_split = (int)value;
+    return HPSI_OK;
+  }
   if (option == HPSI_OPT_EIGENSOLVER) {
     if (value != 0.0 && value != 1.0) return fail(c, HPSI_EINVAL, "HPSI_OPT_EIGENSOLVER must be 0 or 1");
     c.eigensolver = (int)value;

@@ -43,6 +43,7 @@ namespace {
 
 constexpr double kDropAbs = 1e-8;     // overlap eigenvalues of unit corrections below this are dropped
 constexpr double kCollapse = 1e-6;    // squared norm left after projection that marks a collapse
+constexpr int kStall = 8;             // mixed thick restart: iterations without progress before plain restarts
 
 struct DavWork {
   int npw = 0, nbnd = 0, mmax = 0;
@@ -51,6 +52,7 @@ struct DavWork {
   double2* psi = nullptr;    // [nbnd][npw] Ritz vectors
   double2* hpsi = nullptr;   // [nbnd][npw]
   double2* t = nullptr;      // [nbnd][npw] corrections / scratch
+  double2* rst = nullptr;    // [kmax][npw] restart scratch
   double2* hsub = nullptr;   // [mmax][mmax] column-major
   double2* evec = nullptr;   // [mmax][mmax]
   double2* small = nullptr;  // [mmax][nbnd] coefficients
@@ -71,9 +73,16 @@ struct DavWork {
   float2* psi32 = nullptr;    // [nbnd][npw]
   float2* hpsi32 = nullptr;   // [nbnd][npw]
   float2* t32 = nullptr;      // [nbnd][npw]
+  float2* lock32 = nullptr;   // [nbnd][npw] hard-locked Ritz vectors
+  int kmax = 0;               // most Ritz vectors a restart keeps: max(nbnd, mmax / 2)
+  float2* ysub32 = nullptr;   // [kmax][mmax] reduced eigenvectors of the kept Ritz vectors
+  float2* rst32 = nullptr;    // [kmax][npw] restart scratch
+  int* sel = nullptr;         // [kmax] Ritz indices a restart keeps
+  float2* part32 = nullptr;   // K-chunk partial products of the Ritz and restart GEMMs
+  size_t part_cap = 0;        // elements of part32
   float2* small32 = nullptr;  // [mmax][nbnd]
   float2* ovl32 = nullptr;    // [nbnd][nbnd]
-  float2* hcol32 = nullptr;   // [mmax][nbnd]
+  float2* hcol32 = nullptr;   // [kmax][mmax] H_sub columns in float32
   float* hdiag32 = nullptr;   // [npw] float copy of <k+G|H|k+G>
   SplitBasis phi_split, hphi_split;   // bf16 splits of the basis for the tensor-core products
   SubspaceGemm sg;
@@ -221,6 +230,7 @@ static void free_work(DavWork& w) {
   cudaFree(w.psi);
   cudaFree(w.hpsi);
   cudaFree(w.t);
+  cudaFree(w.rst);
   cudaFree(w.hsub);
   cudaFree(w.evec);
   cudaFree(w.small);
@@ -238,6 +248,11 @@ static void free_work(DavWork& w) {
   cudaFree(w.psi32);
   cudaFree(w.hpsi32);
   cudaFree(w.t32);
+  cudaFree(w.lock32);
+  cudaFree(w.ysub32);
+  cudaFree(w.rst32);
+  cudaFree(w.sel);
+  cudaFree(w.part32);
   cudaFree(w.small32);
   cudaFree(w.ovl32);
   cudaFree(w.hcol32);
@@ -278,6 +293,7 @@ static int alloc_work(Context& c, DavHandles& h, int npw, int nbnd, bool mixed) 
   };
   const size_t v = sizeof(double2) * (size_t)npw;
   const size_t v32 = sizeof(float2) * (size_t)npw;
+  w.kmax = std::max(nbnd, mmax / 2);
   bool ok = al((void**)&w.hsub, sizeof(double2) * (size_t)mmax * mmax) &&
             al((void**)&w.evec, sizeof(double2) * (size_t)mmax * mmax) &&
             al((void**)&w.small, sizeof(double2) * (size_t)mmax * nbnd) &&
@@ -287,13 +303,15 @@ static int alloc_work(Context& c, DavHandles& h, int npw, int nbnd, bool mixed) 
             al((void**)&w.cn2, sizeof(double) * nbnd) && al((void**)&w.info, sizeof(int));
   if (ok && !mixed)
     ok = al((void**)&w.phi, v * mmax) && al((void**)&w.hphi, v * mmax) && al((void**)&w.psi, v * nbnd) &&
-         al((void**)&w.hpsi, v * nbnd) && al((void**)&w.t, v * nbnd);
+         al((void**)&w.hpsi, v * nbnd) && al((void**)&w.t, v * nbnd) && al((void**)&w.rst, v * w.kmax);
   if (ok && mixed)
-    ok = al((void**)&w.phi32, v32 * mmax) && al((void**)&w.hphi32, v32 * mmax) && al((void**)&w.psi32, v32 * nbnd) &&
-         al((void**)&w.hpsi32, v32 * nbnd) && al((void**)&w.t32, v32 * nbnd) &&
+    ok = al((void**)&w.ysub32, sizeof(float2) * (size_t)mmax * w.kmax) && al((void**)&w.rst32, v32 * w.kmax) &&
+         al((void**)&w.sel, sizeof(int) * w.kmax) &&
+         al((void**)&w.phi32, v32 * mmax) && al((void**)&w.hphi32, v32 * mmax) && al((void**)&w.psi32, v32 * nbnd) &&
+         al((void**)&w.hpsi32, v32 * nbnd) && al((void**)&w.t32, v32 * nbnd) && al((void**)&w.lock32, v32 * nbnd) &&
          al((void**)&w.small32, sizeof(float2) * (size_t)mmax * nbnd) &&
          al((void**)&w.ovl32, sizeof(float2) * (size_t)nbnd * nbnd) &&
-         al((void**)&w.hcol32, sizeof(float2) * (size_t)mmax * nbnd) && al((void**)&w.hdiag32, sizeof(float) * npw) && al((void**)&w.in64, v * nbnd) &&
+         al((void**)&w.hcol32, sizeof(float2) * (size_t)mmax * w.kmax) && al((void**)&w.hdiag32, sizeof(float) * npw) && al((void**)&w.in64, v * nbnd) &&
          al((void**)&w.out64, v * nbnd);
   if (!ok) {
     free_work(w);
@@ -453,8 +471,12 @@ int davidson_run(Context& c, int ik, int nbnd, double tol, int maxiter, double2*
   std::vector<int> uidx(N);
   int it = 0;
   bool converged = false;
+  // Ritz vectors a restart keeps: the N wanted ones, or with thick restart up to half the basis
+  const int keep = c.thick_restart ? std::max(N, std::min(w.kmax, mmax / 2)) : N;
   for (;;) {
-    rc = lowest_eigh(c, *h, w.hsub, mmax, m, N);
+    // a restart is certain once m + N > mmax unless bands converge: solve for the kept vectors now
+    const int nev = m + N > mmax ? std::min(m, keep) : N;
+    rc = lowest_eigh(c, *h, w.hsub, mmax, m, nev);
     if (rc) return rc;
     // Ritz vectors psi = phi C[:, 0:N], hpsi = hphi C[:, 0:N]
     BCK(cublasZgemm(h->blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, N, m, &kOne, Z(w.phi), npw, Z(w.evec), m, &kZero,
@@ -484,10 +506,19 @@ int davidson_run(Context& c, int ik, int nbnd, double tol, int maxiter, double2*
     if (it >= maxiter) break;
     ++it;
     if (m + nc > mmax) {
-      // restart from the Ritz vectors
-      DCK(cudaMemcpyAsync(w.phi, w.psi, vb * N, cudaMemcpyDeviceToDevice, c.stream), "restart copy");
-      DCK(cudaMemcpyAsync(w.hphi, w.hpsi, vb * N, cudaMemcpyDeviceToDevice, c.stream), "restart copy");
-      m = N;
+      // restart from the lowest nev Ritz vectors: phi <- phi C[:, 0:nev], hphi <- hphi C[:, 0:nev]
+      if (nev == N) {
+        DCK(cudaMemcpyAsync(w.phi, w.psi, vb * N, cudaMemcpyDeviceToDevice, c.stream), "restart copy");
+        DCK(cudaMemcpyAsync(w.hphi, w.hpsi, vb * N, cudaMemcpyDeviceToDevice, c.stream), "restart copy");
+      } else {
+        for (double2* src : {w.phi, w.hphi}) {
+          BCK(cublasZgemm(h->blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, nev, m, &kOne, Z(src), npw, Z(w.evec), m, &kZero,
+                          Z(w.rst), npw),
+              "zgemm restart");
+          DCK(cudaMemcpyAsync(src, w.rst, vb * nev, cudaMemcpyDeviceToDevice, c.stream), "restart copy");
+        }
+      }
+      m = nev;
       BCK(cublasZgemm(h->blas, CUBLAS_OP_C, CUBLAS_OP_N, m, m, npw, &kOne, Z(w.phi), npw, Z(w.hphi), npw, &kZero,
                       Z(w.hsub), mmax),
           "zgemm H_sub restart");
@@ -746,6 +777,27 @@ __global__ void k_gather_rows(int npw, const int* __restrict__ perm, const doubl
   for (int g = threadIdx.x; g < npw; g += blockDim.x) o[g] = s[g];
 }
 
+// dst[b] = src[sel[b]] and, if given, dst2[b] = src2[sel[b]]; one CTA per row, rows of npw.
+__global__ void k_gather_rows32(int npw, const int* __restrict__ sel, const float2* __restrict__ src,
+                                float2* __restrict__ dst, const float2* __restrict__ src2, float2* __restrict__ dst2) {
+  const int b = blockIdx.x;
+  const size_t from = (size_t)sel[b] * npw, to = (size_t)b * npw;
+  for (int g = threadIdx.x; g < npw; g += blockDim.x) dst[to + g] = src[from + g];
+  if (src2)
+    for (int g = threadIdx.x; g < npw; g += blockDim.x) dst2[to + g] = src2[from + g];
+}
+
+// y[:, j] = float(v[:, sel[j]]) for the rows 0..rows-1 (column-major, ld rows for both).
+__global__ void k_select_columns32(int rows, int ncol, const int* __restrict__ sel, const double2* __restrict__ v,
+                                   float2* __restrict__ y) {
+  const size_t n = (size_t)rows * ncol;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t % rows), j = (int)(t / rows);
+    const double2 a = v[(size_t)sel[j] * rows + i];
+    y[t] = make_float2((float)a.x, (float)a.y);
+  }
+}
+
 const cuComplex cOne = {1.f, 0.f};
 const cuComplex cZero = {0.f, 0.f};
 const cuComplex cMinusOne = {-1.f, 0.f};
@@ -753,6 +805,8 @@ inline cuComplex* Cf(float2* p) { return reinterpret_cast<cuComplex*>(p); }
 
 // complex64 GEMM of the mixed subspace: plain CGEMM, or the Gauss three-product form (CGEMM3M)
 // when HPSI_OPT_FP32_GEMM is 2
+static int grid_of(size_t n) { return (int)std::min<size_t>(4096, (n + 255) / 256); }
+
 cublasStatus_t cgemm32(const Context& c, cublasHandle_t h, cublasOperation_t ta, cublasOperation_t tb, int m, int n,
                        int k, const cuComplex* alpha, const cuComplex* A, int lda, const cuComplex* B, int ldb,
                        const cuComplex* beta, cuComplex* C, int ldc) {
@@ -760,9 +814,68 @@ cublasStatus_t cgemm32(const Context& c, cublasHandle_t h, cublasOperation_t ta,
   return cublasCgemm(h, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
 }
 
+// out[i] = sum over the nch chunks of part[c * stride + i], added in float64.
+__global__ void k_sum_chunks(size_t n, int nch, size_t stride, const float2* __restrict__ part,
+                             float2* __restrict__ out) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    double x = 0.0, y = 0.0;
+    for (int ch = 0; ch < nch; ++ch) {
+      const float2 v = part[ch * stride + i];
+      x += v.x;
+      y += v.y;
+    }
+    out[i] = make_float2((float)x, (float)y);
+  }
+}
+
+// out[:, 0:nb] = A[:, 0:k] Y[0:k, 0:nb] for the tall A (ld npw).  A float32 GEMM accumulates its
+// rounding error along k; with HPSI_OPT_RITZ_SPLIT the k range is cut into ceil(k / 128) (at most 8)
+// equal chunks, each a float32 GEMM, and the chunk products are added in float64, so the error grows
+// with the chunk length instead of k.  out must not overlap A or Y.
+static int tall_gemm32(Context& c, DavHandles& h, int npw, int nb, int k, const float2* A, const float2* Y, int ldy,
+                       float2* out) {
+  DavWork& w = h.wk;
+  const int nch = c.ritz_split ? std::min(8, (k + 127) / 128) : 1;
+  if (nch <= 1) {
+    BCK(cgemm32(c, h.blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, nb, k, &cOne, reinterpret_cast<const cuComplex*>(A), npw,
+                reinterpret_cast<const cuComplex*>(Y), ldy, &cZero, Cf(out), npw),
+        "cgemm tall");
+    return HPSI_OK;
+  }
+  const int kc = (k + nch - 1) / nch, nfull = k / kc, rem = k - nfull * kc;
+  const int nparts = nfull + (rem > 0);
+  const size_t stride = (size_t)npw * nb, need = stride * nparts;
+  if (need > w.part_cap) {
+    cudaFree(w.part32);
+    w.part32 = nullptr;
+    w.part_cap = 0;
+    if (cudaMalloc((void**)&w.part32, sizeof(float2) * need) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, HPSI_ENOMEM, "davidson_solve: chunk-product allocation failed");
+    }
+    w.part_cap = need;
+  }
+  const cuComplex* a = reinterpret_cast<const cuComplex*>(A);
+  const cuComplex* y = reinterpret_cast<const cuComplex*>(Y);
+  if (c.fp32_gemm == 2)
+    BCK(cublasCgemm3mStridedBatched(h.blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, nb, kc, &cOne, a, npw, (long long)kc * npw, y,
+                                    ldy, kc, &cZero, Cf(w.part32), npw, (long long)stride, nfull),
+        "cgemm chunks");
+  else
+    BCK(cublasCgemmStridedBatched(h.blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, nb, kc, &cOne, a, npw, (long long)kc * npw, y,
+                                  ldy, kc, &cZero, Cf(w.part32), npw, (long long)stride, nfull),
+        "cgemm chunks");
+  if (rem > 0)
+    BCK(cgemm32(c, h.blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, nb, rem, &cOne, a + (size_t)nfull * kc * npw, npw,
+                y + (size_t)nfull * kc, ldy, &cZero, Cf(w.part32 + (size_t)nfull * stride), npw),
+        "cgemm chunk tail");
+  HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_sum_chunks<<<grid_of(stride), 256, 0, c.stream>>>(stride, nparts, stride,
+                                                                                       w.part32, out)));
+  return HPSI_OK;
+}
+
 }  // namespace
 
-static int grid_of(size_t n) { return (int)std::min<size_t>(4096, (n + 255) / 256); }
 
 // H applied to nb float32 vectors x32 -> float32 hx32, through the float64 staging buffers.
 static int apply32(Context& c, DavWork& w, int ik, const float2* x32, float2* hx32, int nb) {
@@ -910,34 +1023,53 @@ static int davidson_run_mixed(Context& c, DavHandles& h, int ik, int nbnd, doubl
   rc = hsub_columns32(c, h, m, 0, m);
   if (rc) return rc;
   std::vector<double> rn(N), ev(N);
-  std::vector<int> uidx(N);
+  std::vector<int> uidx(N), lsel, asel;
   int it = 0;
   bool converged = false;
+  // Hard locking: the first kL bands are frozen in lock32; the reduced basis phi32[0:m] spans only
+  // the active part of the search space (orthogonal to lock32) and the Rayleigh-Ritz step asks it
+  // for the NA = N - kL lowest pairs.  Without locking kL stays 0 and this is the plain block form.
+  int kL = 0;
+  // Ritz vectors a restart keeps: the active ones, or with thick restart up to half the basis limit.
+  // A thick-restarted vector is a float32 rotation of the basis whose stored H|phi> is the same
+  // rotation of the stored products; the two drift apart by rounding amplified by the largest
+  // eigenvalue of H, so a solve whose largest residual stops falling (kStall iterations without a
+  // 10% drop) goes on with plain restarts.
+  bool thick = c.thick_restart != 0;
+  int stall = 0;
+  double best = INFINITY;
+  auto basis_limit = [&](int locked) { return locked > 0 ? std::min(mmax, c.lock_basis * (N - locked)) : mmax; };
+  auto restart_size = [&](int locked, int m_avail) {
+    const int na = N - locked;
+    return thick ? std::min(m_avail, std::min(w.kmax, std::max(na, basis_limit(locked) / 2))) : na;
+  };
   for (;;) {
-    rc = lowest_eigh(c, h, w.hsub, mmax, m, N);
+    const int NA = N - kL;
+    const int mlim = basis_limit(kL);
+    // a restart is certain once m + NA > mlim unless bands converge; solve for its kept vectors now
+    int nev = NA;
+    if (m + NA > mlim) nev = std::max(NA, restart_size(kL, m));
+    rc = lowest_eigh(c, h, w.hsub, mmax, m, nev);
     if (rc) return rc;
     HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
-                (k_mat_64_to_32<<<(m * N + 255) / 256, 256, 0, c.stream>>>(m, N, w.evec, m, w.small32, m)));
+                (k_mat_64_to_32<<<(m * NA + 255) / 256, 256, 0, c.stream>>>(m, NA, w.evec, m, w.small32, m)));
     if (tc) {
-      rc = w.sg.a_b(c, h.blas, npw, N, m, w.phi_split, w.phi32, npw, w.small32, m, 1.f, 0.f, w.psi32, npw);
-      if (!rc) rc = w.sg.a_b(c, h.blas, npw, N, m, w.hphi_split, w.hphi32, npw, w.small32, m, 1.f, 0.f, w.hpsi32, npw);
+      rc = w.sg.a_b(c, h.blas, npw, NA, m, w.phi_split, w.phi32, npw, w.small32, m, 1.f, 0.f, w.psi32, npw);
+      if (!rc) rc = w.sg.a_b(c, h.blas, npw, NA, m, w.hphi_split, w.hphi32, npw, w.small32, m, 1.f, 0.f, w.hpsi32, npw);
       if (rc) return rc;
     } else {
-      BCK(cgemm32(c, h.blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, N, m, &cOne, Cf(w.phi32), npw, Cf(w.small32), m, &cZero,
-                  Cf(w.psi32), npw),
-          "cgemm Ritz vectors");
-      BCK(cgemm32(c, h.blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, N, m, &cOne, Cf(w.hphi32), npw, Cf(w.small32), m, &cZero,
-                  Cf(w.hpsi32), npw),
-          "cgemm H Ritz vectors");
+      rc = tall_gemm32(c, h, npw, NA, m, w.phi32, w.small32, m, w.psi32);
+      if (!rc) rc = tall_gemm32(c, h, npw, NA, m, w.hphi32, w.small32, m, w.hpsi32);
+      if (rc) return rc;
     }
-    DCK(cudaMemcpyAsync(w.eps, w.w, sizeof(double) * N, cudaMemcpyDeviceToDevice, c.stream), "eps copy");
-    HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_residual32<<<N, 1024, 0, c.stream>>>(npw, w.psi32, w.hpsi32, w.eps, w.t32, w.rnorm)));
-    DCK(cudaMemcpyAsync(rn.data(), w.rnorm, sizeof(double) * N, cudaMemcpyDeviceToHost, c.stream), "norm copy");
+    DCK(cudaMemcpyAsync(w.eps, w.w, sizeof(double) * NA, cudaMemcpyDeviceToDevice, c.stream), "eps copy");
+    HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_residual32<<<NA, 1024, 0, c.stream>>>(npw, w.psi32, w.hpsi32, w.eps, w.t32, w.rnorm)));
+    DCK(cudaMemcpyAsync(rn.data(), w.rnorm, sizeof(double) * NA, cudaMemcpyDeviceToHost, c.stream), "norm copy");
     DCK(cudaStreamSynchronize(c.stream), "davidson iteration");
     rc = check_device_error(c);
     if (rc) return rc;
     int nc = 0;
-    for (int i = 0; i < N; ++i)
+    for (int i = 0; i < NA; ++i)
       if (!(rn[i] <= tol)) uidx[nc++] = i;
     if (nc == 0) {
       converged = true;
@@ -945,22 +1077,104 @@ static int davidson_run_mixed(Context& c, DavHandles& h, int ik, int nbnd, doubl
     }
     if (it >= maxiter) break;
     ++it;
-    if (m + nc > mmax) {
-      DCK(cudaMemcpyAsync(w.phi32, w.psi32, vb * N, cudaMemcpyDeviceToDevice, c.stream), "restart copy");
-      DCK(cudaMemcpyAsync(w.hphi32, w.hpsi32, vb * N, cudaMemcpyDeviceToDevice, c.stream), "restart copy");
+    if (thick) {
+      double rmax = 0.0;
+      for (int i = 0; i < NA; ++i) rmax = std::max(rmax, rn[i]);
+      if (rmax < 0.9 * best) {
+        best = rmax;
+        stall = 0;
+      } else if (++stall >= kStall) {
+        thick = false;
+      }
+    }
+    // Lock: converged Ritz vectors move to lock32.  t32, eps and rnorm keep this iteration's
+    // numbering, which uidx indexes.
+    lsel.clear();
+    if (c.locking) {
+      if (c.locking == 1) {
+        while ((int)lsel.size() < NA && rn[lsel.size()] <= tol) lsel.push_back((int)lsel.size());
+      } else {
+        for (int i = 0; i < NA; ++i)
+          if (rn[i] <= tol) lsel.push_back(i);
+      }
+      if ((int)lsel.size() < std::max(1, (int)std::ceil(c.lock_batch * NA))) lsel.clear();
+    }
+    const int nl = (int)lsel.size();
+    if (nl > 0 || m + nc > mlim) {
+      if (nl > 0) {
+        DCK(cudaMemcpyAsync(w.idx2, lsel.data(), sizeof(int) * nl, cudaMemcpyHostToDevice, c.stream), "lock index copy");
+        HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_gather_rows32<<<nl, 256, 0, c.stream>>>(
+                                            npw, w.idx2, w.psi32, w.lock32 + (size_t)kL * npw, nullptr, nullptr)));
+      }
+      // restart from the lowest Ritz vectors that are not locked
+      const int kL2 = kL + nl, na = N - kL2;
+      const int keep = restart_size(kL2, m - nl);
+      asel.clear();
+      for (int i = 0, j = 0; i < m && (int)asel.size() < keep; ++i) {
+        if (j < nl && lsel[j] == i) {
+          ++j;
+          continue;
+        }
+        asel.push_back(i);
+      }
+      if (asel.back() < NA) {
+        // every kept vector is an active Ritz vector already formed in psi32 / hpsi32
+        if (nl == 0) {
+          DCK(cudaMemcpyAsync(w.phi32, w.psi32, vb * keep, cudaMemcpyDeviceToDevice, c.stream), "restart copy");
+          DCK(cudaMemcpyAsync(w.hphi32, w.hpsi32, vb * keep, cudaMemcpyDeviceToDevice, c.stream), "restart copy");
+        } else {
+          DCK(cudaMemcpyAsync(w.sel, asel.data(), sizeof(int) * keep, cudaMemcpyHostToDevice, c.stream), "restart index copy");
+          HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_gather_rows32<<<keep, 256, 0, c.stream>>>(npw, w.sel, w.psi32, w.phi32,
+                                                                                       w.hpsi32, w.hphi32)));
+        }
+      } else {
+        // thick restart: the kept Ritz vectors are phi32 and hphi32 times the selected reduced eigenvectors
+        if (asel.back() >= nev) {
+          rc = lowest_eigh(c, h, w.hsub, mmax, m, asel.back() + 1);
+          if (rc) return rc;
+        }
+        DCK(cudaMemcpyAsync(w.sel, asel.data(), sizeof(int) * keep, cudaMemcpyHostToDevice, c.stream), "restart index copy");
+        HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_select_columns32<<<grid_of((size_t)m * keep), 256, 0, c.stream>>>(
+                                            m, keep, w.sel, w.evec, w.ysub32)));
+        for (int pass = 0; pass < 2; ++pass) {
+          float2* src = pass == 0 ? w.phi32 : w.hphi32;
+          if (tc) {
+            rc = w.sg.a_b(c, h.blas, npw, keep, m, pass == 0 ? w.phi_split : w.hphi_split, src, npw, w.ysub32, m, 1.f,
+                          0.f, w.rst32, npw);
+            if (rc) return rc;
+          } else {
+            rc = tall_gemm32(c, h, npw, keep, m, src, w.ysub32, m, w.rst32);
+            if (rc) return rc;
+          }
+          DCK(cudaMemcpyAsync(src, w.rst32, vb * keep, cudaMemcpyDeviceToDevice, c.stream), "restart copy");
+        }
+      }
+      // psi32 keeps the active Ritz vectors in the new numbering for an exit before the next step
+      if (nl > 0) DCK(cudaMemcpyAsync(w.psi32, w.phi32, vb * na, cudaMemcpyDeviceToDevice, c.stream), "active copy");
+      kL = kL2;
       w.phi_split.invalidate();
       w.hphi_split.invalidate();
-      m = N;
+      m = keep;
       rc = hsub_columns32(c, h, m, 0, m);
       if (rc) return rc;
     }
     DCK(cudaMemcpyAsync(w.idx, uidx.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, c.stream), "index copy");
     float2* tnew = w.phi32 + (size_t)m * npw;
-    const int eshift = c.opt_shift == 1 ? N - 1 : -1;
+    const int eshift = c.opt_shift == 1 ? NA - 1 : -1;
     HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_precondition32<<<nc, 1024, 0, c.stream>>>(npw, w.idx, w.t32, w.hdiag32, w.eps,
                                                                                 c.opt_tau, eshift, tnew)));
     for (int round = 0; round < 2; ++round) {
       for (int pass = 0; pass < 2; ++pass) {
+        if (kL > 0) {
+          // the locked vectors are orthogonal to the basis: projecting them out first is the
+          // same as projecting out [lock32, phi32] in one block
+          BCK(cgemm32(c, h.blas, CUBLAS_OP_C, CUBLAS_OP_N, kL, nc, npw, &cOne, Cf(w.lock32), npw, Cf(tnew), npw,
+                      &cZero, Cf(w.small32), kL),
+              "cgemm lock projection");
+          BCK(cgemm32(c, h.blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, nc, kL, &cMinusOne, Cf(w.lock32), npw, Cf(w.small32),
+                      kL, &cOne, Cf(tnew), npw),
+              "cgemm lock projection update");
+        }
         if (tc) {
           rc = w.sg.ah_b(c, h.blas, m, nc, npw, w.phi_split, w.phi32, npw, tnew, npw, 1.f, 0.f, w.small32, nullptr, m);
           if (!rc) rc = w.sg.a_b(c, h.blas, npw, nc, m, w.phi_split, w.phi32, npw, w.small32, m, -1.f, 1.f, tnew, npw);
@@ -1001,8 +1215,11 @@ static int davidson_run_mixed(Context& c, DavHandles& h, int ik, int nbnd, doubl
   }
   // float64 Rayleigh quotients of the Ritz vectors with a fresh H|psi>, by default with the
   // float64 operator: the eigenvalue error is then second order in the eigenvector error
-  const size_t n = (size_t)N * npw;
-  HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_cvt_32_64<<<grid_of(n), 256, 0, c.stream>>>(n, w.psi32, w.in64)));
+  const size_t n = (size_t)N * npw, nl = (size_t)kL * npw;
+  if (kL > 0)
+    HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_cvt_32_64<<<grid_of(nl), 256, 0, c.stream>>>(nl, w.lock32, w.in64)));
+  HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
+              (k_cvt_32_64<<<grid_of(n - nl), 256, 0, c.stream>>>(n - nl, w.psi32, w.in64 + nl)));
   if (c.final_fp64) c.prec_override = HPSI_FP64;
   rc = apply_device(c, ik, w.in64, w.out64, N);
   c.prec_override = -1;

@@ -133,6 +133,11 @@ struct Context {
   int autotune = 1;                    // time the fast-path plans on the first apply of a problem
   int eigensolver = 1;                 // reduced eigenproblems: 1 = the library's kernels, 0 = cuSOLVER
   int fp32_gemm = 0;                   // mixed Davidson subspace GEMMs: 1 = bf16x9-emulated float32
+  int locking = 0;                     // mixed Davidson: 0 none, 1 lowest converged run, 2 every converged band
+  double lock_batch = 0.0;             // lock only once this fraction of the active bands is lockable
+  int lock_basis = 4;                  // after a lock the active basis grows to lock_basis * active bands
+  int thick_restart = 1;               // mixed Davidson: restarts keep up to half the basis limit of Ritz vectors
+  int ritz_split = 0;                  // mixed Davidson: Ritz / restart GEMMs in K chunks added in float64
   void* eigh = nullptr;                // eigensolver handles and work buffers (eigh.cu)
   cudaStream_t cap_stream = nullptr;   // internal stream for graph capture
   GraphCache graph;

@@ -175,3 +175,56 @@ def test_davidson_cusolver_option_matches(lib):
     e0, _, _, _ = B.davidson_solve(ctx, 0, x0.clone(), 1e-8, 200)
     assert B.hpsi_kernel_stats(ctx, -3)[0] == 0
     assert np.max(np.abs(e1 - e0)) < 1e-10
+
+
+def test_davidson_mixed_c3_320_bands(lib):
+    """The 320-band run of the mixed form on the 1500-PW cell: the reduced basis (up to 1280 vectors)
+    nearly fills the plane-wave space and the float32 residuals sit near their rounding floor."""
+    import torch
+    from paper_0906_2569_gb300 import binding as B
+    p = workloads.config3(320)
+    ctx, m, vr, beta, d = _setup(p, precision=B.HPSI_MIXED)
+    x = torch.from_numpy(workloads.psi0(p.lattice, p.kpts[0], m, p.nbnd, p.psi_seed)).cuda()
+    eig, it, res, rc = B.davidson_solve(ctx, 0, x, 1e-5, 400)
+    assert np.max(np.abs(eig - np.asarray(_golden("c3")[:320]))) < 1e-6
+
+
+@pytest.mark.parametrize("cfg,locking", [("c2", 1), ("c2", 2), ("c3", 2), ("c3_16", 2)])
+def test_davidson_mixed_locking(lib, cfg, locking):
+    """Hard locking (lowest converged run, or every converged band) reaches the same eigenvalues;
+    the returned block is orthonormal to float32 accuracy and sorted."""
+    import torch
+    from paper_0906_2569_gb300 import binding as B
+    p = workloads.config2() if cfg == "c2" else workloads.config3(16 if cfg == "c3_16" else 160)
+    ctx, m, vr, beta, d = _setup(p, precision=B.HPSI_MIXED)
+    B.hpsi_set_option(ctx, B.HPSI_OPT_LOCKING, locking)
+    B.hpsi_set_option(ctx, B.HPSI_OPT_LOCK_BATCH, 0.25)
+    x = torch.from_numpy(workloads.psi0(p.lattice, p.kpts[0], m, p.nbnd, p.psi_seed)).cuda()
+    eig, it, res, rc = B.davidson_solve(ctx, 0, x, 1e-5, 300)
+    ref = np.asarray(_golden("c2" if cfg == "c2" else "c3")[:p.nbnd])
+    assert np.max(np.abs(eig - ref)) < 1e-6
+    assert np.all(np.diff(eig) >= 0)
+    v = x.cpu().numpy()
+    assert np.max(np.abs(np.conj(v) @ v.T - np.eye(p.nbnd))) < 1e-4
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_davidson_plain_restart_option(lib, precision):
+    """HPSI_OPT_THICK_RESTART = 0 (restart from the wanted Ritz vectors only) and the default thick
+    restart reach the same eigenvalues; the Ritz-product chunking option changes nothing either."""
+    import torch
+    from paper_0906_2569_gb300 import binding as B
+    p = workloads.config1() if precision == 0 else workloads.config3(160)
+    tol, etol = (1e-8, 1e-10) if precision == 0 else (1e-5, 1e-6)
+    ctx, m, vr, beta, d = _setup(p, precision=precision)
+    ref = np.asarray(_golden("c1" if precision == 0 else "c3")[:p.nbnd])
+    x0 = torch.from_numpy(workloads.psi0(p.lattice, p.kpts[0], m, p.nbnd, p.psi_seed)).cuda()
+    its = {}
+    for thick, split in ((1, 0), (0, 0), (1, 1)):
+        B.hpsi_set_option(ctx, B.HPSI_OPT_THICK_RESTART, thick)
+        B.hpsi_set_option(ctx, B.HPSI_OPT_RITZ_SPLIT, split)
+        x = x0.clone()
+        eig, it, res, rc = B.davidson_solve(ctx, 0, x, tol, 300)
+        assert np.max(np.abs(eig - ref)) < etol
+        its[(thick, split)] = it
+    assert its[(1, 0)] <= its[(0, 0)]

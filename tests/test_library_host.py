@@ -65,3 +65,16 @@ def test_gsphere_errors(B):
         B.hpsi_gsphere(np.zeros((3, 3)), 1.0, np.zeros(3))
     with pytest.raises(B.HpsiError):
         B.hpsi_gsphere(np.eye(3) * 10, 1e9, np.zeros(3))
+
+
+def test_binding_constants_match_header(B):
+    """Every HPSI_* enumerator the binding names has the value include/hpsi.h gives it."""
+    src = open(os.path.join(ROOT, "include", "hpsi.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    declared = {n: int(v) for n, v in re.findall(r"\b(HPSI_[A-Z0-9_]+)\s*=\s*(-?\d+)", src)}
+    named = [n for n in dir(B) if n.startswith("HPSI_OPT_") or n.startswith("HPSI_E")
+             or n in ("HPSI_OK", "HPSI_FP64", "HPSI_MIXED")]
+    assert len([n for n in named if n.startswith("HPSI_OPT_")]) >= 16
+    for n in named:
+        assert n in declared, f"{n} is not declared in hpsi.h"
+        assert getattr(B, n) == declared[n], n
