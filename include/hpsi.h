@@ -69,7 +69,8 @@ enum hpsi_option {
                                  quotients with one float64 application of H to the Ritz vectors;
                                  0 with the mixed H */
   HPSI_OPT_BASIS = 8,         /* davidson_solve: the reduced basis grows to this many times N
-                                 vectors (2: the basic 2N form, 3 or 4 (default)) before a restart */
+                                 vectors (2: the basic 2N form, 3 or 4) before a restart; 0
+                                 (default): 3 in a mixed context, 4 in a float64 one */
   HPSI_OPT_AUTOTUNE = 9,      /* 1 (default): the first hpsi_apply of a problem with >= 4 bands at a
                                  precision times every shared-memory plan of the register-codelet
                                  kernels and three band-block sizes on its own bands and keeps the

@@ -741,7 +741,7 @@ extern "C" int davidson_solve(hpsi_ctx* ctx, int ik, int nbnd, double tol, int m
   Context& c = ctx->c;
   if (ik < 0 || ik >= (int)c.probs.size()) return fail(c, HPSI_EINVAL, "davidson_solve: problem index out of range");
   const Problem& p = c.probs[ik];
-  if (nbnd < 1 || c.basis_factor * nbnd > p.npw)
+  if (nbnd < 1 || basis_of(c) * nbnd > p.npw)
     return fail(c, HPSI_EINVAL, "davidson_solve: need 1 <= nbnd and (basis factor) * nbnd <= npw");
   if (!(tol > 0.0) || maxiter < 1 || !psi_inout || !eig_out)
     return fail(c, HPSI_EINVAL, "davidson_solve: bad tol, maxiter or null pointer");
@@ -835,7 +835,8 @@ extern "C" int hpsi_set_option(hpsi_ctx* ctx, int option, double value) {
     return HPSI_OK;
   }
   if (option == HPSI_OPT_BASIS) {
-    if (value != 2.0 && value != 3.0 && value != 4.0) return fail(c, HPSI_EINVAL, "HPSI_OPT_BASIS must be 2, 3 or 4");
+    if (value != 0.0 && value != 2.0 && value != 3.0 && value != 4.0)
+      return fail(c, HPSI_EINVAL, "HPSI_OPT_BASIS must be 0, 2, 3 or 4");
     c.basis_factor = (int)value;
     return HPSI_OK;
   }

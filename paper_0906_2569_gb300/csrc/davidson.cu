@@ -277,7 +277,7 @@ void davidson_release(Context& c) {
 
 static int alloc_work(Context& c, DavHandles& h, int npw, int nbnd, bool mixed) {
   DavWork& w = h.wk;
-  const int mmax = c.basis_factor * nbnd;
+  const int mmax = basis_of(c) * nbnd;
   if (w.npw == npw && w.nbnd == nbnd && w.mixed == mixed && w.mmax == mmax) return HPSI_OK;
   free_work(w);
   w.npw = npw;

@@ -129,7 +129,8 @@ struct Context {
   int tc_kmax = 0;                     // mixed calbec: max 64-wide K-steps per split (0: automatic)
   int prec_override = -1;              // >= 0: apply H at this precision instead of `precision`
   int final_fp64 = 1;                  // mixed davidson_solve: final Rayleigh quotients with the float64 H
-  int basis_factor = 4;                // Davidson: the reduced basis grows to basis_factor * N vectors
+  int basis_factor = 0;                // Davidson: the reduced basis grows to basis_factor * N vectors
+                                       // (0: 3 for a mixed context, 4 for float64)
   int autotune = 1;                    // time the fast-path plans on the first apply of a problem
   int eigensolver = 1;                 // reduced eigenproblems: 1 = the library's kernels, 0 = cuSOLVER
   int fp32_gemm = 0;                   // mixed Davidson subspace GEMMs: 1 = bf16x9-emulated float32
@@ -176,6 +177,9 @@ void make_fft_plan(int n, FftPlan& plan, std::vector<double2>& table);
 int build_geometry(Problem& p, std::string& err);
 
 // ---- launchers (local_kernels.cu, nonlocal_fp64.cu) ----
+// The Davidson basis factor in effect: HPSI_OPT_BASIS, or by precision when it is left at 0.
+inline int basis_of(const Context& c) { return c.basis_factor ? c.basis_factor : (c.precision == HPSI_MIXED ? 3 : 4); }
+
 size_t local_smem_bytes(const Problem& p, int precision, int which);
 int local_apply(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd);
 int nonlocal_apply_fp64(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd);
