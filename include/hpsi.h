@@ -105,10 +105,13 @@ enum hpsi_option {
                                  vectors up to half the basis limit (at least the active ones).  A
                                  mixed solve whose largest residual has not fallen by 10% in 8
                                  iterations continues with plain restarts */
-  HPSI_OPT_RITZ_SPLIT = 16    /* mixed davidson_solve: 1: the Ritz-vector and restart products
+  HPSI_OPT_RITZ_SPLIT = 16,   /* mixed davidson_solve: 1: the Ritz-vector and restart products
                                  (inner dimension = basis size) run as float32 GEMMs over at most 8
                                  chunks of the inner dimension whose results are added in float64;
-                                 0: one float32 GEMM */
+                                 0 (default): one float32 GEMM */
+  HPSI_OPT_REORTH_TEST = 17   /* davidson_solve: 1: the unit corrections are projected out of the
+                                 basis once, and a second time only if a column kept less than half
+                                 its squared norm; 0 (default): always twice */
 };
 
 /* Kernel classes reported by hpsi_kernel_stats. */

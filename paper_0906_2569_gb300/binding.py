@@ -21,7 +21,7 @@ HPSI_OPT_PRECOND_TAU, HPSI_OPT_PRECOND_SHIFT, HPSI_OPT_KERNEL_TIMING, HPSI_OPT_N
 HPSI_OPT_LOCAL_PATH, HPSI_OPT_TC_KSPLIT, HPSI_OPT_FINAL_FP64, HPSI_OPT_BASIS, HPSI_OPT_AUTOTUNE = 5, 6, 7, 8, 9
 HPSI_OPT_EIGENSOLVER, HPSI_OPT_FP32_GEMM = 10, 11
 HPSI_OPT_LOCKING, HPSI_OPT_LOCK_BATCH, HPSI_OPT_LOCK_BASIS, HPSI_OPT_THICK_RESTART = 12, 13, 14, 15
-HPSI_OPT_RITZ_SPLIT = 16
+HPSI_OPT_RITZ_SPLIT, HPSI_OPT_REORTH_TEST = 16, 17
 KERNELS = ("inv_zy", "xvx_y", "fwd_z", "calbec", "dscale", "addvus", "split", "davidson", "eigh", "tridiag")
 STATUS_NAMES = {0: "HPSI_OK", -1: "HPSI_EINVAL", -2: "HPSI_ENOMEM", -3: "HPSI_ECUDA", -4: "HPSI_ENOTCONV",
                 -5: "HPSI_ESINGULAR", -6: "HPSI_ETIMEOUT", -7: "HPSI_ENODEV"}

@@ -819,6 +819,11 @@ extern "C" int hpsi_set_option(hpsi_ctx* ctx, int option, double value) {
     c.thick_restart = (int)value;
     return HPSI_OK;
   }
+  if (option == HPSI_OPT_REORTH_TEST) {
+    if (value != 0.0 && value != 1.0) return fail(c, HPSI_EINVAL, "HPSI_OPT_REORTH_TEST must be 0 or 1");
+    c.reorth_test = (int)value;
+    return HPSI_OK;
+  }
   if (option == HPSI_OPT_RITZ_SPLIT) {
     if (value != 0.0 && value != 1.0) return fail(c, HPSI_EINVAL, "HPSI_OPT_RITZ_SPLIT must be 0 or 1");
     c.ritz_split = (int)value;

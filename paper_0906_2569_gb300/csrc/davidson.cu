@@ -43,6 +43,8 @@ namespace {
 
 constexpr double kDropAbs = 1e-8;     // overlap eigenvalues of unit corrections below this are dropped
 constexpr double kCollapse = 1e-6;    // squared norm left after projection that marks a collapse
+constexpr double kReorth = 0.5;       // squared norm a unit correction keeps after one projection pass
+                                      // below which a second pass runs (Daniel-Gragg-Kaufman-Stewart)
 constexpr int kStall = 8;             // mixed thick restart: iterations without progress before plain restarts
 
 struct DavWork {
@@ -529,22 +531,43 @@ int davidson_run(Context& c, int ik, int nbnd, double tol, int maxiter, double2*
     const int eshift = c.opt_shift == 1 ? N - 1 : -1;
     HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_precondition<<<nc, 256, 0, c.stream>>>(npw, w.idx, w.t, p.d_hdiag, w.eps, c.opt_tau, eshift, tnew)));
     DCK(cudaGetLastError(), "precondition kernel");
-    for (int round = 0; round < 2; ++round) {
-      // two passes of block Gram-Schmidt against phi[0:m]
-      for (int pass = 0; pass < 2; ++pass) {
-        BCK(cublasZgemm(h->blas, CUBLAS_OP_C, CUBLAS_OP_N, m, nc, npw, &kOne, Z(w.phi), npw, Z(tnew), npw, &kZero,
-                        Z(w.small), m),
-            "zgemm projection");
-        BCK(cublasZgemm(h->blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, nc, m, &kMinusOne, Z(w.phi), npw, Z(w.small), m,
-                        &kOne, Z(tnew), npw),
-            "zgemm projection update");
-      }
-      if (round == 1) break;
-      // corrections that lie in the basis are replaced by their raw residuals
+    // block Gram-Schmidt against phi[0:m]; a second pass only where the first cancelled (kReorth)
+    auto project = [&]() -> int {
+      BCK(cublasZgemm(h->blas, CUBLAS_OP_C, CUBLAS_OP_N, m, nc, npw, &kOne, Z(w.phi), npw, Z(tnew), npw, &kZero,
+                      Z(w.small), m),
+          "zgemm projection");
+      BCK(cublasZgemm(h->blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, nc, m, &kMinusOne, Z(w.phi), npw, Z(w.small), m, &kOne,
+                      Z(tnew), npw),
+          "zgemm projection update");
+      return HPSI_OK;
+    };
+    std::vector<double> cn(nc);
+    auto norms = [&]() -> int {
       HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_norm2<<<nc, 256, 0, c.stream>>>(npw, tnew, w.cn2)));
-      std::vector<double> cn(nc);
       DCK(cudaMemcpyAsync(cn.data(), w.cn2, sizeof(double) * nc, cudaMemcpyDeviceToHost, c.stream), "norm copy");
       DCK(cudaStreamSynchronize(c.stream), "correction norms");
+      return HPSI_OK;
+    };
+    for (int round = 0; round < 2; ++round) {
+      rc = project();
+      if (rc) return rc;
+      bool second = round == 1 || !c.reorth_test;
+      if (!second) {
+        rc = norms();
+        if (rc) return rc;
+        for (int j = 0; j < nc; ++j)
+          if (!(cn[j] >= kReorth)) second = true;
+      }
+      if (second) {
+        rc = project();
+        if (rc) return rc;
+      }
+      if (round == 1) break;
+      if (second) {
+        rc = norms();
+        if (rc) return rc;
+      }
+      // corrections that lie in the basis are replaced by their raw residuals
       std::vector<int> col;
       for (int j = 0; j < nc; ++j)
         if (!(cn[j] >= kCollapse)) col.push_back(j);
@@ -1163,36 +1186,59 @@ static int davidson_run_mixed(Context& c, DavHandles& h, int ik, int nbnd, doubl
     const int eshift = c.opt_shift == 1 ? NA - 1 : -1;
     HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_precondition32<<<nc, 1024, 0, c.stream>>>(npw, w.idx, w.t32, w.hdiag32, w.eps,
                                                                                 c.opt_tau, eshift, tnew)));
-    for (int round = 0; round < 2; ++round) {
-      for (int pass = 0; pass < 2; ++pass) {
-        if (kL > 0) {
-          // the locked vectors are orthogonal to the basis: projecting them out first is the
-          // same as projecting out [lock32, phi32] in one block
-          BCK(cgemm32(c, h.blas, CUBLAS_OP_C, CUBLAS_OP_N, kL, nc, npw, &cOne, Cf(w.lock32), npw, Cf(tnew), npw,
-                      &cZero, Cf(w.small32), kL),
-              "cgemm lock projection");
-          BCK(cgemm32(c, h.blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, nc, kL, &cMinusOne, Cf(w.lock32), npw, Cf(w.small32),
-                      kL, &cOne, Cf(tnew), npw),
-              "cgemm lock projection update");
-        }
-        if (tc) {
-          rc = w.sg.ah_b(c, h.blas, m, nc, npw, w.phi_split, w.phi32, npw, tnew, npw, 1.f, 0.f, w.small32, nullptr, m);
-          if (!rc) rc = w.sg.a_b(c, h.blas, npw, nc, m, w.phi_split, w.phi32, npw, w.small32, m, -1.f, 1.f, tnew, npw);
-          if (rc) return rc;
-        } else {
-          BCK(cgemm32(c, h.blas, CUBLAS_OP_C, CUBLAS_OP_N, m, nc, npw, &cOne, Cf(w.phi32), npw, Cf(tnew), npw, &cZero,
-                      Cf(w.small32), m),
-              "cgemm projection");
-          BCK(cgemm32(c, h.blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, nc, m, &cMinusOne, Cf(w.phi32), npw, Cf(w.small32), m,
-                      &cOne, Cf(tnew), npw),
-              "cgemm projection update");
-        }
+    // Block Gram-Schmidt against [lock32, phi32] (the locked vectors are orthogonal to the basis, so
+    // projecting them out first is the same as projecting out the union in one block).
+    auto project = [&]() -> int {
+      if (kL > 0) {
+        BCK(cgemm32(c, h.blas, CUBLAS_OP_C, CUBLAS_OP_N, kL, nc, npw, &cOne, Cf(w.lock32), npw, Cf(tnew), npw, &cZero,
+                    Cf(w.small32), kL),
+            "cgemm lock projection");
+        BCK(cgemm32(c, h.blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, nc, kL, &cMinusOne, Cf(w.lock32), npw, Cf(w.small32), kL,
+                    &cOne, Cf(tnew), npw),
+            "cgemm lock projection update");
       }
-      if (round == 1) break;
+      if (tc) {
+        int r = w.sg.ah_b(c, h.blas, m, nc, npw, w.phi_split, w.phi32, npw, tnew, npw, 1.f, 0.f, w.small32, nullptr, m);
+        if (!r) r = w.sg.a_b(c, h.blas, npw, nc, m, w.phi_split, w.phi32, npw, w.small32, m, -1.f, 1.f, tnew, npw);
+        return r;
+      }
+      BCK(cgemm32(c, h.blas, CUBLAS_OP_C, CUBLAS_OP_N, m, nc, npw, &cOne, Cf(w.phi32), npw, Cf(tnew), npw, &cZero,
+                  Cf(w.small32), m),
+          "cgemm projection");
+      BCK(cgemm32(c, h.blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, nc, m, &cMinusOne, Cf(w.phi32), npw, Cf(w.small32), m,
+                  &cOne, Cf(tnew), npw),
+          "cgemm projection update");
+      return HPSI_OK;
+    };
+    std::vector<double> cn(nc);
+    auto norms = [&]() -> int {
       HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_norm2_32<<<nc, 1024, 0, c.stream>>>(npw, tnew, w.cn2)));
-      std::vector<double> cn(nc);
       DCK(cudaMemcpyAsync(cn.data(), w.cn2, sizeof(double) * nc, cudaMemcpyDeviceToHost, c.stream), "norm copy");
       DCK(cudaStreamSynchronize(c.stream), "correction norms");
+      return HPSI_OK;
+    };
+    for (int round = 0; round < 2; ++round) {
+      rc = project();
+      if (rc) return rc;
+      // The corrections enter with unit norm.  One pass leaves them orthogonal to the basis up to
+      // rounding relative to their norm before it; a second pass only helps a column that the first
+      // cancelled (kept less than half its squared norm), so it runs only then.
+      bool second = round == 1 || !c.reorth_test;
+      if (!second) {
+        rc = norms();
+        if (rc) return rc;
+        for (int j = 0; j < nc; ++j)
+          if (!(cn[j] >= kReorth)) second = true;
+      }
+      if (second) {
+        rc = project();
+        if (rc) return rc;
+      }
+      if (round == 1) break;
+      if (second) {
+        rc = norms();
+        if (rc) return rc;
+      }
       std::vector<int> col;
       for (int j = 0; j < nc; ++j)
         if (!(cn[j] >= kCollapse)) col.push_back(j);

@@ -726,15 +726,19 @@ __global__ void k_eh_widen(int n, int nwant, const double* __restrict__ Z, doubl
 }
 
 // The upper-triangular factor of a compact-WY block, H_{k nb} ... H_{k nb + nb - 1} = I - V T V^H,
-// has the inverse S = T^-1 = diag(1 / tau_i) + (strictly upper part of G = V^H V).  Y = T W is then
-// a back substitution with S: y_q = tau_q (w_q - sum_{r > q} S_qr y_r), which needs no division and
-// gives y_q = 0 for an identity reflector (tau_q = 0).  One warp per column of W (in place), lane l
-// holds rows l, l + 32, ...; rows are finalised from the last one, each subtracting its
-// contribution from the rows above.  G is the block's Gram matrix (column-major kWY x kWY; only its strictly
-// upper part is read), tau the block's kWY reflector factors.
-__global__ void __launch_bounds__(128) k_eh_trsv(int ncol, const double2* __restrict__ G, const double2* __restrict__ tau,
-                                                 double2* __restrict__ W) {
+// has the inverse S = T^-1 = diag(1 / tau_i) + (strictly upper part of G = V^H V), so
+// T = (I + diag(tau) striu(G))^-1 diag(tau): a back substitution y_q = tau_q (w_q - sum_{r > q} S_qr y_r)
+// applied to the columns w = e_c of the identity.  It needs no division and gives a zero row and
+// column for an identity reflector (tau_q = 0).  Grid (kWY / 4, blocks): one warp per column of one
+// block's T; lane l holds rows l, l + 32, ...; rows are finalised from the last one, each
+// subtracting its contribution from the rows above.  G holds the blocks' Gram matrices and T receives
+// the factors (both column-major kWY x kWY per block; only the strictly upper part of G is read).
+__global__ void __launch_bounds__(128) k_eh_tfactor(const double2* __restrict__ Gall, const double2* __restrict__ tauall,
+                                                    double2* __restrict__ Tall) {
   extern __shared__ double2 gs[];   // strictly upper part of G, column q at q (q - 1) / 2
+  const size_t blk = (size_t)blockIdx.y * kWY * kWY;
+  const double2* G = Gall + blk;
+  const double2* tau = tauall + (size_t)blockIdx.y * kWY;
 #pragma unroll 4
   for (int idx = threadIdx.x; idx < kWY * (kWY - 1) / 2; idx += blockDim.x) {
     int q = (int)(0.5f * (1.0f + sqrtf(1.0f + 8.0f * (float)idx)));   // column: q (q - 1) / 2 <= idx
@@ -744,11 +748,10 @@ __global__ void __launch_bounds__(128) k_eh_trsv(int ncol, const double2* __rest
   }
   __syncthreads();
   const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (col >= ncol) return;
-  double2* w = W + (size_t)col * kWY;
+  if (col >= kWY) return;
   double2 acc[kWYRows];   // right-hand side rows lane + 32 s, reduced as rows finalise
 #pragma unroll
-  for (int sl = 0; sl < kWYRows; ++sl) acc[sl] = w[lane + 32 * sl];
+  for (int sl = 0; sl < kWYRows; ++sl) acc[sl] = make_double2(lane + 32 * sl == col ? 1.0 : 0.0, 0.0);
   for (int q = kWY - 1; q >= 0; --q) {
     // the owner finalises y_q = tau_q acc_q, then every row r < q subtracts S_rq y_q
     const int own = q & 31, oslot = q >> 5;
@@ -771,15 +774,16 @@ __global__ void __launch_bounds__(128) k_eh_trsv(int ncol, const double2* __rest
       if (32 * sl < q) {   // warp-uniform: some row of this slot lies above q
         const int r = lane + 32 * sl;
         if (r < q) {
-          const double2 s = gq[r];
-          acc[sl].x -= s.x * yq.x - s.y * yq.y;
-          acc[sl].y -= s.x * yq.y + s.y * yq.x;
+          const double2 g = gq[r];
+          acc[sl].x -= g.x * yq.x - g.y * yq.y;
+          acc[sl].y -= g.x * yq.y + g.y * yq.x;
         }
       }
     }
   }
+  double2* t = Tall + blk + (size_t)col * kWY;
 #pragma unroll
-  for (int sl = 0; sl < kWYRows; ++sl) w[lane + 32 * sl] = acc[sl];
+  for (int sl = 0; sl < kWYRows; ++sl) t[lane + 32 * sl] = acc[sl];
 }
 
 constexpr size_t kTrsvSmem = sizeof(double2) * (size_t)kWY * (kWY - 1) / 2;
@@ -791,7 +795,7 @@ struct EighState {
   double *d = nullptr, *e = nullptr, *e2 = nullptr, *sacc = nullptr, *lam = nullptr, *Z = nullptr, *Z2 = nullptr;
   double* gram = nullptr;
   double2 *tau = nullptr, *vref = nullptr, *ybuf = nullptr, *rnext = nullptr, *rowcoef = nullptr, *vscale = nullptr;
-  double2 *wgram = nullptr, *w1 = nullptr;   // compact-WY blocks
+  double2 *wgram = nullptr, *tfac = nullptr, *w1 = nullptr, *w2 = nullptr;   // compact-WY blocks
   unsigned int* bar = nullptr;
   int* info = nullptr;    // [0] orthogonality check of the eigenvectors, [1] inverse-iteration status
   // cuSOLVER zheevdx path
@@ -803,7 +807,7 @@ struct EighState {
 
 void free_state(EighState& s) {
   void* ptrs[] = {s.d,    s.e,     s.e2,    s.sacc,    s.lam,   s.Z,  s.gram, s.tau,
-                  s.vref, s.ybuf,  s.rnext, s.rowcoef, s.wgram, s.w1, s.bar,  s.info, s.vscale, s.Z2};
+                  s.vref, s.ybuf,  s.rnext, s.rowcoef, s.wgram, s.w1, s.bar,  s.info, s.vscale, s.Z2, s.tfac, s.w2};
   for (void* q : ptrs) cudaFree(q);
   const EighState keep = s;
   s = EighState{};
@@ -851,7 +855,9 @@ int grow(Context& c, EighState& s, int n, int nwant) {
   al((void**)&s.tau, sizeof(double2) * (N + kWY));
   al((void**)&s.vref, sizeof(double2) * (size_t)(N + kWY) * N);
   al((void**)&s.wgram, sizeof(double2) * (size_t)K * kWY * kWY);
+  al((void**)&s.tfac, sizeof(double2) * (size_t)K * kWY * kWY);
   al((void**)&s.w1, sizeof(double2) * (size_t)kWY * W);
+  al((void**)&s.w2, sizeof(double2) * (size_t)kWY * W);
   al((void**)&s.ybuf, sizeof(double2) * 2 * N);
   al((void**)&s.rnext, sizeof(double2) * 2 * N);
   al((void**)&s.bar, sizeof(unsigned int) * 64);
@@ -1035,17 +1041,18 @@ int eigh_lowest(Context& c, const double2* a, int lda, int n, int nwant, double*
                                   (long long)kWY * n, Zc(s->vref + 1), n, (long long)kWY * n, &zzero, Zc(s->wgram),
                                   kWY, (long long)kWY * kWY, K) != CUBLAS_STATUS_SUCCESS)
       return fail(c, HPSI_ECUDA, "eigh_lowest: reflector Gram matrices failed");
-    err = cudaFuncSetAttribute(k_eh_trsv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrsvSmem);
+    err = cudaFuncSetAttribute(k_eh_tfactor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrsvSmem);
     if (err != cudaSuccess) return cuda_fail(c, err, "eigh_lowest: smem attribute");
+    HPSI_LAUNCH(c, HPSI_K_EIGH,
+                (k_eh_tfactor<<<dim3(kWY / 4, K), 128, kTrsvSmem, c.stream>>>(s->wgram, s->tau, s->tfac)));
     for (int k = K - 1; k >= 0; --k) {
       const int r0 = k * kWY + 1, m = n - r0;
       double2* V = s->vref + (size_t)k * kWY * n + r0;
       if (cublasZgemm(s->blas, CUBLAS_OP_C, CUBLAS_OP_N, kWY, nwant, m, &zone, Zc(V), n, Zc(v_out + r0), n, &zzero,
                       Zc(s->w1), kWY) != CUBLAS_STATUS_SUCCESS ||
-          (k_eh_trsv<<<(nwant + 3) / 4, 128, kTrsvSmem, c.stream>>>(nwant, s->wgram + (size_t)k * kWY * kWY,
-                                                             s->tau + (size_t)k * kWY, s->w1),
-           cudaGetLastError() != cudaSuccess) ||
-          cublasZgemm(s->blas, CUBLAS_OP_N, CUBLAS_OP_N, m, nwant, kWY, &zmone, Zc(V), n, Zc(s->w1), kWY, &zone,
+          cublasZgemm(s->blas, CUBLAS_OP_N, CUBLAS_OP_N, kWY, nwant, kWY, &zone, Zc(s->tfac + (size_t)k * kWY * kWY),
+                      kWY, Zc(s->w1), kWY, &zzero, Zc(s->w2), kWY) != CUBLAS_STATUS_SUCCESS ||
+          cublasZgemm(s->blas, CUBLAS_OP_N, CUBLAS_OP_N, m, nwant, kWY, &zmone, Zc(V), n, Zc(s->w2), kWY, &zone,
                       Zc(v_out + r0), n) != CUBLAS_STATUS_SUCCESS)
         return fail(c, HPSI_ECUDA, "eigh_lowest: back-transformation GEMM failed");
     }

@@ -138,6 +138,7 @@ struct Context {
   double lock_batch = 0.0;             // lock only once this fraction of the active bands is lockable
   int lock_basis = 4;                  // after a lock the active basis grows to lock_basis * active bands
   int thick_restart = 1;               // mixed Davidson: restarts keep up to half the basis limit of Ritz vectors
+  int reorth_test = 0;                 // Davidson: second Gram-Schmidt pass only where the first cancelled
   int ritz_split = 0;                  // mixed Davidson: Ritz / restart GEMMs in K chunks added in float64
   void* eigh = nullptr;                // eigensolver handles and work buffers (eigh.cu)
   cudaStream_t cap_stream = nullptr;   // internal stream for graph capture
