@@ -45,7 +45,7 @@ FP64_ALU_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12    # 2 DFMA / clk / SM (measured)
 #   tridiag: k_eh_tridiag, one n = 640 launch, 3.372 MB read + 0.030 MB write, per matrix element
 #            (ncu_eigh_n640.md)
 NCU_TRAFFIC = {
-    ("tridiag", -1): (("eigh.cu",), "92283e7e012b", (3372032 + 30464) / 640 ** 2),
+    ("tridiag", -1): (("eigh_tridiag.cuh",), "7b3ca0b96a01", (3367936 + 31488) / 640 ** 2),
     ("xvx_y", 1): (("local_fast.cu", "fft_codelets.cuh"), "92564643ab55", (51.725568e6 + 4.813056e6) / 48),
     ("calbec", 0): (("nonlocal_fp64.cu",), "f2c91a1c9ad9", (267.307264e6 + 7.139584e6) / 160),
 }
