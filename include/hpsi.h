@@ -88,7 +88,11 @@ enum hpsi_option {
                                  three-product complex form (CGEMM3M); 3: the library's split:
                                  three bf16 terms per operand, six products accumulated in float32
                                  by bf16 tensor-core GEMMs, on the interleaved storage read as real
-                                 matrices (the basis splits are cached across the iteration) */
+                                 matrices (the basis splits are cached across the iteration); 4: the
+                                 inner products (projections onto the basis, H_sub columns, overlaps)
+                                 on the library's tcgen05 kernel, three bf16 terms per float32
+                                 operand (exact), six products, float32 accumulation per K-split and
+                                 float64 sums over splits; the outer products stay CGEMM */
   HPSI_OPT_LOCKING = 12,      /* mixed davidson_solve: hard locking of converged Ritz pairs.  0: none
                                  (converged bands get no correction but stay in the Rayleigh-Ritz
                                  problem); 1: the lowest run of converged bands is frozen, taken out

@@ -793,8 +793,8 @@ extern "C" int hpsi_set_option(hpsi_ctx* ctx, int option, double value) {
     return HPSI_OK;
   }
   if (option == HPSI_OPT_FP32_GEMM) {
-    if (value != 0.0 && value != 1.0 && value != 2.0 && value != 3.0)
-      return fail(c, HPSI_EINVAL, "HPSI_OPT_FP32_GEMM must be 0, 1, 2 or 3");
+    if (value != 0.0 && value != 1.0 && value != 2.0 && value != 3.0 && value != 4.0)
+      return fail(c, HPSI_EINVAL, "HPSI_OPT_FP32_GEMM must be 0, 1, 2, 3 or 4");
     c.fp32_gemm = (int)value;
     return HPSI_OK;
   }

@@ -88,6 +88,7 @@ struct DavWork {
   float* hdiag32 = nullptr;   // [npw] float copy of <k+G|H|k+G>
   SplitBasis phi_split, hphi_split;   // bf16 splits of the basis for the tensor-core products
   SubspaceGemm sg;
+  TcInner tci;                // tcgen05 inner products (HPSI_OPT_FP32_GEMM = 4); caches phi32's split
   double2* in64 = nullptr;    // [nbnd][npw]
   double2* out64 = nullptr;   // [nbnd][npw]
 };
@@ -262,6 +263,7 @@ static void free_work(DavWork& w) {
   w.phi_split.release();
   w.hphi_split.release();
   w.sg.release();
+  w.tci.release();
   cudaFree(w.in64);
   cudaFree(w.out64);
   w = DavWork();
@@ -914,13 +916,22 @@ static int apply32(Context& c, DavWork& w, int ik, const float2* x32, float2* hx
 // the block is well conditioned, Cholesky QR twice when it is moderately conditioned (absolute
 // threshold only), else canonically through the float64 eigen-decomposition of the overlap, where
 // directions with overlap eigenvalue <= thr (relative to the largest if relative) drop.
+// w.ovl32 = x^H x for the block x[0:n] (ld npw).
+static int overlap32(Context& c, DavHandles& h, const float2* x, int n) {
+  DavWork& w = h.wk;
+  if (c.fp32_gemm == 4) return tc_inner32(c, w.tci, false, 0, x, n, x, n, w.npw, nullptr, w.ovl32, n);
+  BCK(cgemm32(c, h.blas, CUBLAS_OP_C, CUBLAS_OP_N, n, n, w.npw, &cOne, reinterpret_cast<const cuComplex*>(x), w.npw,
+              reinterpret_cast<const cuComplex*>(x), w.npw, &cZero, Cf(w.ovl32), n),
+      "cgemm overlap");
+  return HPSI_OK;
+}
+
 static int canonical_orth32(Context& c, DavHandles& h, const float2* x, int n, float2* out, int* nkeep, double thr,
                             bool relative) {
   DavWork& w = h.wk;
   const int npw = w.npw;
-  BCK(cgemm32(c, h.blas, CUBLAS_OP_C, CUBLAS_OP_N, n, n, npw, &cOne, reinterpret_cast<const cuComplex*>(x), npw,
-                  reinterpret_cast<const cuComplex*>(x), npw, &cZero, Cf(w.ovl32), n),
-      "cgemm overlap");
+  int rc0 = overlap32(c, h, x, n);
+  if (rc0) return rc0;
   HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
               (k_mat_32_to_64<<<(n * n + 255) / 256, 256, 0, c.stream>>>(n, n, w.ovl32, n, w.ovl, n)));
   // Cholesky QR (float64 factor of the overlap) when the block is well conditioned enough for a
@@ -953,9 +964,8 @@ static int canonical_orth32(Context& c, DavHandles& h, const float2* x, int n, f
       BCK(cublasCtrsm(h.blas, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT, npw, n,
                       &cOne, Cf(w.ovl32), n, Cf(out), npw),
           "ctrsm");
-      BCK(cgemm32(c, h.blas, CUBLAS_OP_C, CUBLAS_OP_N, n, n, npw, &cOne, Cf(out), npw, Cf(out), npw, &cZero,
-                  Cf(w.ovl32), n),
-          "cgemm overlap");
+      rc = overlap32(c, h, out, n);
+      if (rc) return rc;
       HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
                   (k_mat_32_to_64<<<(n * n + 255) / 256, 256, 0, c.stream>>>(n, n, w.ovl32, n, w.ovl, n)));
       bool second_ok = false;
@@ -972,9 +982,8 @@ static int canonical_orth32(Context& c, DavHandles& h, const float2* x, int n, f
       }
     }
     // otherwise the overlap of x again, for its eigen-decomposition
-    BCK(cgemm32(c, h.blas, CUBLAS_OP_C, CUBLAS_OP_N, n, n, npw, &cOne, reinterpret_cast<const cuComplex*>(x), npw,
-                reinterpret_cast<const cuComplex*>(x), npw, &cZero, Cf(w.ovl32), n),
-        "cgemm overlap");
+    rc = overlap32(c, h, x, n);
+    if (rc) return rc;
   }
   HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
               (k_mat_32_to_64<<<(n * n + 255) / 256, 256, 0, c.stream>>>(n, n, w.ovl32, n, w.ovl, n)));
@@ -1004,6 +1013,9 @@ static int hsub_columns32(Context& c, DavHandles& h, int rows, int col0, int nco
   if (c.fp32_gemm == 3)
     return w.sg.ah_b(c, h.blas, rows, ncol, npw, w.phi_split, w.phi32, npw, w.hphi32 + (size_t)col0 * npw, npw, 1.f,
                      0.f, nullptr, w.hsub + (size_t)col0 * mmax, mmax);
+  if (c.fp32_gemm == 4)
+    return tc_inner32(c, w.tci, true, mmax, w.phi32, rows, w.hphi32 + (size_t)col0 * npw, ncol, npw,
+                      w.hsub + (size_t)col0 * mmax, nullptr, mmax);
   BCK(cgemm32(c, h.blas, CUBLAS_OP_C, CUBLAS_OP_N, rows, ncol, npw, &cOne, Cf(w.phi32), npw,
                   Cf(w.hphi32 + (size_t)col0 * npw), npw, &cZero, Cf(w.hcol32), mmax),
       "cgemm H_sub columns");
@@ -1032,6 +1044,7 @@ static int davidson_run_mixed(Context& c, DavHandles& h, int ik, int nbnd, doubl
   } math_reset{h.blas};
   w.phi_split.invalidate();
   w.hphi_split.invalidate();
+  w.tci.invalidate();
   const bool tc = c.fp32_gemm == 3;
   // phi32[0:N] <- orthonormalised initial guess
   HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
@@ -1177,6 +1190,7 @@ static int davidson_run_mixed(Context& c, DavHandles& h, int ik, int nbnd, doubl
       kL = kL2;
       w.phi_split.invalidate();
       w.hphi_split.invalidate();
+      w.tci.invalidate();
       m = keep;
       rc = hsub_columns32(c, h, m, 0, m);
       if (rc) return rc;
@@ -1202,9 +1216,14 @@ static int davidson_run_mixed(Context& c, DavHandles& h, int ik, int nbnd, doubl
         if (!r) r = w.sg.a_b(c, h.blas, npw, nc, m, w.phi_split, w.phi32, npw, w.small32, m, -1.f, 1.f, tnew, npw);
         return r;
       }
-      BCK(cgemm32(c, h.blas, CUBLAS_OP_C, CUBLAS_OP_N, m, nc, npw, &cOne, Cf(w.phi32), npw, Cf(tnew), npw, &cZero,
-                  Cf(w.small32), m),
-          "cgemm projection");
+      if (c.fp32_gemm == 4) {
+        const int r = tc_inner32(c, w.tci, true, mmax, w.phi32, m, tnew, nc, npw, nullptr, w.small32, m);
+        if (r) return r;
+      } else {
+        BCK(cgemm32(c, h.blas, CUBLAS_OP_C, CUBLAS_OP_N, m, nc, npw, &cOne, Cf(w.phi32), npw, Cf(tnew), npw, &cZero,
+                    Cf(w.small32), m),
+            "cgemm projection");
+      }
       BCK(cgemm32(c, h.blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, nc, m, &cMinusOne, Cf(w.phi32), npw, Cf(w.small32), m,
                   &cOne, Cf(tnew), npw),
           "cgemm projection update");

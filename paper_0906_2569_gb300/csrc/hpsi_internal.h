@@ -178,6 +178,24 @@ void make_fft_plan(int n, FftPlan& plan, std::vector<double2>& table);
 int build_geometry(Problem& p, std::string& err);
 
 // ---- launchers (local_kernels.cu, nonlocal_fp64.cu) ----
+// Complex64 inner products C = A^H B on the tcgen05 tensor cores (nonlocal_tc.cu): three bf16 terms
+// per float32 operand (exact), six products accumulated in float32 per K-split, splits summed in
+// float64.  A rows [0, M) and B rows [0, nb) are complex64 vectors of npw elements (ld npw).  With
+// cache_a the bf16 split of A's rows is kept across calls (for a basis that only grows; call
+// invalidate() when its rows change; rows_cap sizes the cache).  The result goes to out64 (or, when
+// out64 is null, out32), column-major with leading dimension ldo: element (i, b) at i + b ldo.
+struct TcInner {
+  void* terms = nullptr;      // cached bf16 split of A: 3 planes of caprows x kpad
+  const void* base = nullptr;
+  int caprows = 0, kpad = 0, valid = 0;
+  void* ws = nullptr;         // per-call splits and float partials
+  size_t wsbytes = 0;
+  void invalidate() { valid = 0; }
+  void release();
+};
+int tc_inner32(Context& c, TcInner& t, bool cache_a, int rows_cap, const float2* A, int M, const float2* B, int nb,
+               int npw, double2* out64, float2* out32, int ldo);
+
 // The Davidson basis factor in effect: HPSI_OPT_BASIS, or by precision when it is left at 0.
 inline int basis_of(const Context& c) { return c.basis_factor ? c.basis_factor : (c.precision == HPSI_MIXED ? 3 : 4); }
 

@@ -38,6 +38,7 @@ constexpr int TBN = 128;             // rows of B per tile (accumulator columns)
 constexpr int TBK = 64;              // bf16 per 128-byte swizzled row
 constexpr int kTileBytes = TBM * TBK * 2;   // 16 KB, A and B tiles alike
 constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
+constexpr int kInnerKsteps = 8;      // subspace inner products: K steps per float32 accumulation
 
 template <int NT> struct TcCfg {
   static constexpr int stages = NT == 2 ? 3 : 2;
@@ -370,6 +371,78 @@ __global__ void k_dscale_tc(int nproj, int nb, int nsplit, int ka, const float* 
   split_store<NT>(wi, wa, plane, (size_t)b * ka + 2 * p + 1);
 }
 
+// Rows r0 .. r1-1 of a complex64 block [rows][npw] as (re, im) bf16 pairs, K padded with zeros to
+// kc, into NT term planes of plane elements each (A of the subspace inner products).  One thread per
+// complex element or padding pair.
+template <int NT>
+__global__ void k_split_rows32(int r0, int r1, int npw, int kc, size_t plane, const float2* __restrict__ src,
+                               __nv_bfloat16* __restrict__ out) {
+  const int half = kc / 2;
+  const size_t n = (size_t)(r1 - r0) * half;
+  __nv_bfloat162* o2 = reinterpret_cast<__nv_bfloat162*>(out);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int row = r0 + (int)(i / half), g = (int)(i % half);
+    float2 v = make_float2(0.f, 0.f);
+    if (g < npw) v = src[(size_t)row * npw + g];
+    float x = v.x, y = v.y;
+    const size_t at = ((size_t)row * kc) / 2 + g;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const __nv_bfloat16 hx = __float2bfloat16_rn(x), hy = __float2bfloat16_rn(y);
+      o2[t * (plane / 2) + at] = __halves2bfloat162(hx, hy);
+      x -= __bfloat162float(hx);   // exact: the remainder of a float32 after a bf16 rounding
+      y -= __bfloat162float(hy);
+    }
+  }
+}
+
+// B of the subspace inner products from a complex64 block [nb][npw]: rows b: (re, im); rows nb + b:
+// (im, -re), K padded to kc (the calbec form, so that C[i][b] = Re<a_i|x_b>, C[i][nb+b] = Im).
+template <int NT>
+__global__ void k_split_inner_b(int nb, int npw, int kc, const float2* __restrict__ src,
+                                __nv_bfloat16* __restrict__ out) {
+  const size_t plane = (size_t)2 * nb * kc;
+  const int half = kc / 2;
+  const size_t n = (size_t)nb * half;
+  __nv_bfloat162* o2 = reinterpret_cast<__nv_bfloat162*>(out);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(i / half), g = (int)(i % half);
+    float2 v = make_float2(0.f, 0.f);
+    if (g < npw) v = src[(size_t)b * npw + g];
+    float r0 = v.x, r1 = v.y, s0 = v.y, s1 = -v.x;
+    const size_t i0 = ((size_t)b * kc) / 2 + g, i1 = ((size_t)(nb + b) * kc) / 2 + g;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const __nv_bfloat16 h0 = __float2bfloat16_rn(r0), h1 = __float2bfloat16_rn(r1);
+      const __nv_bfloat16 k0 = __float2bfloat16_rn(s0), k1 = __float2bfloat16_rn(s1);
+      o2[t * (plane / 2) + i0] = __halves2bfloat162(h0, h1);
+      o2[t * (plane / 2) + i1] = __halves2bfloat162(k0, k1);
+      r0 -= __bfloat162float(h0);
+      r1 -= __bfloat162float(h1);
+      s0 -= __bfloat162float(k0);
+      s1 -= __bfloat162float(k1);
+    }
+  }
+}
+
+// out[i + b ldo] = (sum_s part[s][i][b], sum_s part[s][i][nb + b]), summed in float64; part is
+// [nsplit][M][2 nb].  Threads run over b fastest (coalesced partial reads).
+__global__ void k_inner_reduce(int M, int nb, int nsplit, const float* __restrict__ part, double2* __restrict__ out64,
+                               float2* __restrict__ out32, int ldo) {
+  const size_t n = (size_t)M * nb, N = (size_t)2 * nb;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(t % nb), i = (int)(t / nb);
+    double re = 0.0, im = 0.0;
+    for (int s = 0; s < nsplit; ++s) {
+      const float* ps = part + ((size_t)s * M + i) * N;
+      re += (double)ps[b];
+      im += (double)ps[nb + b];
+    }
+    if (out64) out64[(size_t)b * ldo + i] = make_double2(re, im);
+    else out32[(size_t)b * ldo + i] = make_float2((float)re, (float)im);
+  }
+}
+
 // ---- host side ------------------------------------------------------------------------------
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -403,11 +476,12 @@ int make_map(Context& c, CUtensorMap* m, const void* base, int rows, int kpad) {
 
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
+// pa_stride / pb_stride: elements between the bf16 term planes of A / B (0: rows x kpad, packed)
 template <int NT>
 int launch_gemm(Context& c, const void* A, int M, const void* B, int N, int kpad, int nsplit, int ksplit, int mode,
-                float* part, double2* out, int ldo, int kernel_class) {
+                float* part, double2* out, int ldo, int kernel_class, size_t pa_stride = 0, size_t pb_stride = 0) {
   CUtensorMap ma[3], mb[3];
-  const size_t pa = (size_t)M * kpad, pb = (size_t)N * kpad;
+  const size_t pa = pa_stride ? pa_stride : (size_t)M * kpad, pb = pb_stride ? pb_stride : (size_t)N * kpad;
   for (int t = 0; t < 3; ++t) {
     const int tt = t < NT ? t : NT - 1;
     int rc = make_map(c, &ma[t], static_cast<const __nv_bfloat16*>(A) + tt * pa, M, kpad);
@@ -516,6 +590,88 @@ int mixed_prepare_beta(Context& c, Problem& p) {
 int nonlocal_apply_mixed(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd) {
   if (p.nproj == 0 || nbnd == 0) return HPSI_OK;
   return c.nl_terms == 3 ? apply_t<3>(c, p, psi, hpsi, nbnd) : apply_t<2>(c, p, psi, hpsi, nbnd);
+}
+
+void TcInner::release() {
+  cudaFree(terms);
+  cudaFree(ws);
+  *this = TcInner();
+}
+
+int tc_inner32(Context& c, TcInner& t, bool cache_a, int rows_cap, const float2* A, int M, const float2* B, int nb,
+               int npw, double2* out64, float2* out32, int ldo) {
+  constexpr int NT = 3;
+  if (M <= 0 || nb <= 0) return HPSI_OK;
+  int rc = get_encoder(c);
+  if (rc) return rc;
+  const int kc = round_up(2 * npw, TBK), nks = kc / TBK;
+  const int tiles = ((2 * nb + TBN - 1) / TBN) * ((M + TBM - 1) / TBM);
+  // float32 accumulation over at most kInnerKsteps 64-wide K steps, float64 across the splits
+  int nsplit = std::max(1, std::min(nks, (2 * c.sm_count + tiles - 1) / tiles));
+  int ksplit = std::min((nks + nsplit - 1) / nsplit, c.tc_kmax > 0 ? c.tc_kmax : kInnerKsteps);
+  nsplit = (nks + ksplit - 1) / ksplit;
+  // workspace: [A split, when not cached][B split][partials], each 256-byte aligned
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t abytes = cache_a ? 0 : al(sizeof(__nv_bfloat16) * NT * (size_t)M * kc);
+  const size_t bbytes = al(sizeof(__nv_bfloat16) * NT * (size_t)2 * nb * kc);
+  const size_t pbytes = al(sizeof(float) * (size_t)nsplit * M * 2 * nb);
+  if (abytes + bbytes + pbytes > t.wsbytes) {
+    cudaFree(t.ws);
+    t.ws = nullptr;
+    t.wsbytes = 0;
+    if (cudaMalloc(&t.ws, abytes + bbytes + pbytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, HPSI_ENOMEM, "tensor-core inner-product workspace allocation failed");
+    }
+    t.wsbytes = abytes + bbytes + pbytes;
+  }
+  unsigned char* w0 = static_cast<unsigned char*>(t.ws);
+  __nv_bfloat16* bsplit = reinterpret_cast<__nv_bfloat16*>(w0 + abytes);
+  float* part = reinterpret_cast<float*>(w0 + abytes + bbytes);
+  const __nv_bfloat16* asplit;
+  size_t pa;
+  if (cache_a) {
+    // the cached rows stay valid while A, npw and the capacity are unchanged (invalidate() otherwise)
+    const int cap = std::max(M, rows_cap);
+    if (t.base != A || t.kpad != kc || cap > t.caprows) {
+      if (cap > t.caprows) {
+        cudaFree(t.terms);
+        t.terms = nullptr;
+        t.caprows = 0;
+        if (cudaMalloc(&t.terms, sizeof(__nv_bfloat16) * NT * (size_t)cap * kc) != cudaSuccess) {
+          cudaGetLastError();
+          return fail(c, HPSI_ENOMEM, "tensor-core basis split allocation failed");
+        }
+        t.caprows = cap;
+      }
+      t.base = A;
+      t.kpad = kc;
+      t.valid = 0;
+    }
+    pa = (size_t)t.caprows * kc;
+    if (M > t.valid) {
+      HPSI_LAUNCH(c, HPSI_K_SPLIT,
+                  (k_split_rows32<NT><<<4 * c.sm_count, 256, 0, c.stream>>>(
+                      t.valid, M, npw, kc, pa, A, static_cast<__nv_bfloat16*>(t.terms))));
+      t.valid = M;
+    }
+    asplit = static_cast<const __nv_bfloat16*>(t.terms);
+  } else {
+    pa = (size_t)M * kc;
+    __nv_bfloat16* as = reinterpret_cast<__nv_bfloat16*>(w0);
+    HPSI_LAUNCH(c, HPSI_K_SPLIT, (k_split_rows32<NT><<<4 * c.sm_count, 256, 0, c.stream>>>(0, M, npw, kc, pa, A, as)));
+    asplit = as;
+  }
+  HPSI_LAUNCH(c, HPSI_K_SPLIT, (k_split_inner_b<NT><<<4 * c.sm_count, 256, 0, c.stream>>>(nb, npw, kc, B, bsplit)));
+  rc = launch_gemm<NT>(c, asplit, M, bsplit, 2 * nb, kc, nsplit, ksplit, 0, part, nullptr, 0, HPSI_K_DAVIDSON, pa);
+  if (rc) return rc;
+  const size_t n = (size_t)M * nb;
+  HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
+              (k_inner_reduce<<<(int)std::min<size_t>(4 * c.sm_count, (n + 255) / 256), 256, 0, c.stream>>>(
+                  M, nb, nsplit, part, out64, out32, ldo)));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "tensor-core inner products launch");
+  return HPSI_OK;
 }
 
 }  // namespace hpsi

@@ -146,8 +146,8 @@ def test_davidson_kpoints_c4a(lib):
 
 @pytest.mark.parametrize("gemm", [3, 2])
 def test_davidson_mixed_c2_subspace_gemm_options(lib, gemm):
-    """The mixed solve with the split-bf16 tensor-core subspace products (3) and with CGEMM3M (2)
-    reaches the same eigenvalues, and its reduced problems all go through the library's eigensolver."""
+    """The mixed solve with the split-bf16 cuBLAS subspace products (3) and with CGEMM3M (2) reaches
+    the same eigenvalues, and its reduced problems all go through the library's eigensolver."""
     import torch
     from paper_0906_2569_gb300 import binding as B
     p = workloads.config2()
@@ -228,3 +228,21 @@ def test_davidson_plain_restart_option(lib, precision):
         assert np.max(np.abs(eig - ref)) < etol
         its[(thick, split)] = it
     assert its[(1, 0)] <= its[(0, 0)]
+
+
+def test_davidson_mixed_tc_inner_products(lib):
+    """HPSI_OPT_FP32_GEMM = 4: the projections onto the basis, the H_sub columns and the overlaps run
+    on the library's tcgen05 kernel (split bf16, float64 sums over K-splits).  Same eigenvalues on the
+    160-band run of the small cell, orthonormal block, and the bf16 split kernels did run."""
+    import torch
+    from paper_0906_2569_gb300 import binding as B
+    p = workloads.config3(160)
+    ctx, m, vr, beta, d = _setup(p, precision=B.HPSI_MIXED)
+    B.hpsi_set_option(ctx, B.HPSI_OPT_FP32_GEMM, 4)
+    B.hpsi_kernel_stats(ctx, -1, reset=True)
+    x = torch.from_numpy(workloads.psi0(p.lattice, p.kpts[0], m, p.nbnd, p.psi_seed)).cuda()
+    eig, it, res, rc = B.davidson_solve(ctx, 0, x, 1e-5, 300)
+    assert np.max(np.abs(eig - np.asarray(_golden("c3")[:160]))) < 1e-6
+    v = x.cpu().numpy()
+    assert np.max(np.abs(np.conj(v) @ v.T - np.eye(160))) < 1e-4
+    assert B.hpsi_kernel_stats(ctx, B.KERNELS.index("split"))[0] > 3 * it
