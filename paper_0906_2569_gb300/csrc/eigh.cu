@@ -15,10 +15,11 @@
 //      loss of orthogonality, itself of the order of rounding / gap, so residuals stay at rounding
 //      level.
 //   4. Back-transformation x_i = Q z_i = H_0 (H_1 (... (H_{n-2} z_i))), in blocks of 64 reflectors
-//      written in compact WY form H_a ... H_b = I - V T V^H and applied with two ZGEMMs and a
-//      back substitution with T^-1 = diag(1 / tau) + strictly-upper(V^H V).
+//      written in compact WY form H_a ... H_b = I - V T V^H.  T^-1 = diag(1 / tau) +
+//      strictly-upper(V^H V); one launch forms every block's T from it, and each block is then three
+//      ZGEMMs (V^H X, T (V^H X), X - V (T V^H X)).
 //
-// Step 1 is one cooperative launch over G CTAs.  Row r of A lives in the shared memory of CTA
+// Step 1 (eigh_tridiag.cuh) is one cooperative launch over G CTAs.  Row r of A lives in the shared memory of CTA
 // r mod G for the whole reduction.  For column j every CTA rebuilds the same reflector from row j
 // (A is Hermitian, so the column below the diagonal is the conjugate of the row's tail; the owner
 // of row j published that row, updated, at the end of column j-1), updates its own rows with the
