@@ -16,6 +16,9 @@ What it computes is the plain definition of each step, in float64 / complex128:
 * ``davidson``  -- the per-step quantities of the block Davidson method of App. A.2.1:
                    residuals g_i = (H - eps_i S) psi_i with S = I, the diagonal correction
                    D g_i, and the Rayleigh-Ritz solve of the reduced problem.
+* ``cg``        -- the band-by-band preconditioned conjugate-gradient eigensolver of App. A.2.2
+                   (constrained minimisation per band, kinetic-only P^2, Polak-Ribiere
+                   directions, exact line minimum on the unit circle).
 * ``eigen``     -- reference eigenvalues: dense LAPACK ``eigh`` of H_GG' (small cells) and
                    scipy LOBPCG on the FFT H|psi> (large cells).
 
@@ -26,4 +29,4 @@ of a rank-one projector), brute-force O(N^2) sums with Cartesian G.r, invariants
 The absolute eigenvalues of the synthetic cells have no printed value in the paper: they
 are pinned only through those properties and the agreement of two independent routes.
 """
-from . import gsphere, hamiltonian, davidson, eigen  # noqa: F401
+from . import gsphere, hamiltonian, davidson, eigen, cg  # noqa: F401

@@ -203,3 +203,88 @@ def eigs_dense_of(lattice, atoms, ecut, fft, k, nbnd):
     beta = workloads.beta(lattice, atoms, k, miller)
     h = oracle.hamiltonian.dense_h(lattice, k, miller, fft, vr, beta, workloads.dmat(len(atoms)))
     return oracle.eigen.lowest_dense(h, nbnd)
+
+
+def cg_problem(seed=21, k=(0.07, -0.13, 0.05), ecut=3.0):
+    """A small fcc cell at a general k (complex H): its dense H, |k+G|^2/2 from Cartesian G and a
+    seeded start block [12][npw]."""
+    lat = 0.5 * 10.2 * np.array([[0.0, 1.0, 1.0], [1.0, 0.0, 1.0], [1.0, 1.0, 0.0]])
+    k = np.asarray(k, dtype=np.float64)
+    miller = oracle.gsphere.gsphere(lat, ecut, k)
+    fft = tuple(int(4 * v + 1) for v in np.max(np.abs(np.asarray(miller)), axis=0))   # no wrap of G - G'
+    p = workloads.small_cell(ecut=ecut, nat=2, fft=fft, seed=seed, k=k, lattice=lat)
+    vr = workloads.vloc_r(lat, p.atoms, fft)
+    beta = workloads.beta(lat, p.atoms, k, miller)
+    h = oracle.hamiltonian.dense_h(lat, k, miller, fft, vr, beta, workloads.dmat(len(p.atoms)))
+    kin = np.array([0.5 * float(np.sum((k + g_cart(lat, m)) ** 2)) for m in miller])
+    x0 = workloads.random_block(len(miller), 12, seed + 1)
+    return h, kin, x0
+
+
+def pin_cg_dense(nb=12, tol=1e-9) -> float:
+    """CG eigenvalues, in the order found, against LAPACK's eigvalsh of the dense H; the returned
+    block must be orthonormal and every residual within tol."""
+    h, kin, x0 = cg_problem()
+    eig, psi, res, steps = oracle.cg.cg_solve(lambda v: h @ v, x0[:nb], kin, tol, 500)
+    ref = np.linalg.eigvalsh(h)[:nb]
+    orth = float(np.max(np.abs(np.conj(psi) @ psi.T - np.eye(nb))))
+    rn = float(np.max(np.linalg.norm(psi @ h.T - eig[:, None] * psi, axis=1)))
+    return max(float(np.max(np.abs(eig - ref))), orth, max(0.0, rn - 10 * tol))
+
+
+def pin_cg_free(nb=10) -> float:
+    """V = 0, no projectors: H = diag(|k+G|^2/2), so the CG eigenvalues are the sorted kinetic
+    energies (closed form, from Cartesian G)."""
+    lat = 0.5 * 10.2 * np.array([[0.0, 1.0, 1.0], [1.0, 0.0, 1.0], [1.0, 1.0, 0.0]])
+    k = np.array([0.05, -0.11, 0.2])
+    miller = oracle.gsphere.gsphere(lat, 3.0, k)
+    kin = np.array([0.5 * float(np.sum((k + g_cart(lat, m)) ** 2)) for m in miller])
+    x0 = workloads.random_block(len(miller), nb, 9)
+    eig, psi, res, steps = oracle.cg.cg_solve(lambda v: kin * v, x0, kin, 1e-10, 500)
+    return float(np.max(np.abs(eig - np.sort(kin)[:nb])))
+
+
+def pin_cg_angle(n=200, seed=5) -> float:
+    """The line minimum on the unit circle is the smaller eigenvalue of [[eps, a/2], [a/2, b]]
+    (LAPACK on 2 x 2 matrices)."""
+    rng = np.random.default_rng(seed)
+    worst = 0.0
+    for _ in range(n):
+        eps, a, b = rng.standard_normal(3) * np.array([3.0, 2.0, 3.0])
+        t = oracle.cg.line_angle(eps, a, b)
+        e = eps * np.cos(t) ** 2 + b * np.sin(t) ** 2 + a * np.sin(t) * np.cos(t)
+        worst = max(worst, abs(e - np.linalg.eigvalsh(np.array([[eps, a / 2], [a / 2, b]]))[0]))
+    return worst
+
+
+def pin_cg_gradient(seed=8) -> float:
+    """The multiplier makes the preconditioned gradient orthogonal to the current vector
+    (<psi|P g> = 0, the constraint the paper imposes), for random psi and H psi."""
+    rng = np.random.default_rng(seed)
+    npw = 300
+    psi = rng.standard_normal(npw) + 1j * rng.standard_normal(npw)
+    psi /= np.linalg.norm(psi)
+    hpsi = rng.standard_normal(npw) + 1j * rng.standard_normal(npw)
+    p2 = 1.0 / np.maximum(rng.random(npw) * 20.0, 1.0)
+    lam, pg = oracle.cg.gradient(psi, hpsi, p2)
+    return float(abs(np.real(np.vdot(psi, pg))) / np.linalg.norm(pg))
+
+
+def pin_cg_precond_ratio(nb=6) -> float:
+    """The kinetic-only P^2 is an effective preconditioner where the kinetic term dominates (the
+    paper's argument): on a diagonal H = |k+G|^2/2 + V_G with V_G in [-2, 0] Ha at E_cut = 10 Ha
+    the CG steps with P^2 are a fraction of those with P^2 = 1.  Returns that fraction."""
+    lat = 10.0 * np.eye(3)
+    k = np.array([0.05, -0.11, 0.2])
+    miller = oracle.gsphere.gsphere(lat, 10.0, k)
+    kin = np.array([0.5 * float(np.sum((k + g_cart(lat, m)) ** 2)) for m in miller])
+    h = kin - 2.0 * np.random.default_rng(3).random(len(kin))
+    x0 = workloads.random_block(len(miller), nb, 9)
+    _, _, _, with_p = oracle.cg.cg_solve(lambda v: h * v, x0, kin, 1e-8, 4000)
+    saved = oracle.cg.precond_p2
+    try:
+        oracle.cg.precond_p2 = lambda t, t_min=1.0: np.ones_like(np.asarray(t, dtype=np.float64))
+        _, _, _, without = oracle.cg.cg_solve(lambda v: h * v, x0, kin, 1e-8, 4000)
+    finally:
+        oracle.cg.precond_p2 = saved
+    return float(np.sum(with_p)) / float(np.sum(without))

@@ -103,3 +103,44 @@ def test_planted_gsphere_k_shift_is_caught(monkeypatch):
     count = sum(1 for m1 in range(-8, 9) for m2 in range(-8, 9) for m3 in range(-8, 9)
                 if 0.5 * float(np.sum((k + _pins.g_cart(lat, (m1, m2, m3))) ** 2)) <= 4.0)
     assert not (ok and count == len(got))
+
+
+import oracle.cg as CG
+
+
+def _orth_none(v, lower):
+    return v
+
+
+def _angle_maximum(eps, a, b):
+    t = CG.__dict__["_orig_angle"](eps, a, b)
+    return t + 0.5 * np.pi
+
+
+def _gradient_rayleigh(psi, hpsi, p2):
+    lam = float(np.real(np.vdot(psi, hpsi)))
+    return lam, p2 * (hpsi - lam * psi)
+
+
+def _p2_inverted(kinetic, t_min=1.0):
+    return np.maximum(np.asarray(kinetic, dtype=np.float64), t_min)
+
+
+@pytest.mark.parametrize("attr,bad,pin,bad_if", [
+    ("_orth", _orth_none, "dense", lambda e: e > 1e-3),
+    ("line_angle", _angle_maximum, "angle", lambda e: e > 1e-3),
+    ("gradient", _gradient_rayleigh, "gradient", lambda e: e > 1e-6),
+    ("precond_p2", _p2_inverted, "precond", lambda e: e > 0.6),
+])
+def test_planted_cg_mistake_is_caught(monkeypatch, attr, bad, pin, bad_if):
+    monkeypatch.setattr(CG, "_orig_angle", CG.line_angle, raising=False)
+    monkeypatch.setattr(CG, attr, bad)
+    if pin == "dense":
+        err = _pins.pin_cg_dense()
+    elif pin == "angle":
+        err = _pins.pin_cg_angle()
+    elif pin == "gradient":
+        err = _pins.pin_cg_gradient()
+    else:
+        err = _pins.pin_cg_precond_ratio()
+    assert bad_if(err), f"pin {pin} missed a planted mistake in {attr}: err={err}"
