@@ -113,9 +113,11 @@ enum hpsi_option {
                                  (inner dimension = basis size) run as float32 GEMMs over at most 8
                                  chunks of the inner dimension whose results are added in float64;
                                  0 (default): one float32 GEMM */
-  HPSI_OPT_REORTH_TEST = 17   /* davidson_solve: 1: the unit corrections are projected out of the
+  HPSI_OPT_REORTH_TEST = 17,  /* davidson_solve: 1: the unit corrections are projected out of the
                                  basis once, and a second time only if a column kept less than half
                                  its squared norm; 0 (default): always twice */
+  HPSI_OPT_CG_TMIN = 18       /* cg_solve: the preconditioner is P^2 = 1 / max(|k+G|^2 / 2, value),
+                                 value > 0 in Ha (default 1) */
 };
 
 /* Kernel classes reported by hpsi_kernel_stats. */
@@ -246,7 +248,8 @@ HPSI_API int hpsi_apply_batch(hpsi_ctx* ctx, int nitem, const int* prob, const i
 /*
  * davidson_solve -- lowest nbnd eigenpairs of H for problem ik by block Davidson with the
  * diagonal preconditioner (App. A.2.1).
- *   nbnd         in   number of bands N (1 <= N, and N * basis factor <= npw; factor 4 by default)
+ *   nbnd         in   number of bands N (1 <= N, and N * basis factor <= npw; factor 3 in a mixed
+ *                     context, 4 in a float64 one, HPSI_OPT_BASIS)
  *   tol          in   convergence when max_i ||H psi_i - eps_i psi_i||_2 <= tol
  *   maxiter      in   iteration limit (>= 1)
  *   psi_inout    in/out complex128 [N][npw(ik)], device or host: initial guess in (need not be
@@ -258,7 +261,8 @@ HPSI_API int hpsi_apply_batch(hpsi_ctx* ctx, int nitem, const int* prob, const i
  * norms; corrections D g_i with <k+G|D|k+G> = 1/(<k+G|H|k+G> - eps_i) (denominator kept at
  * |.| >= 0.1 Ha); orthogonalise them against the reduced basis and add them; H_jk, S_jk of the
  * reduced basis; solve (H - eps S) c = 0 in float64; psi_i <- sum_j c_j phi_j; when the basis
- * would exceed 4N vectors (HPSI_OPT_BASIS) restart from the N Ritz vectors }.  At HPSI_MIXED the
+ * would exceed its limit restart from the lowest Ritz vectors (up to half the limit,
+ * HPSI_OPT_THICK_RESTART; hard locking with HPSI_OPT_LOCKING) }.  At HPSI_MIXED the
  * basis is complex64 and the returned eigenvalues are float64 Rayleigh quotients (see
  * HPSI_OPT_FINAL_FP64); the returned residual norms are those of the returned vectors.
  * Synchronous: returns when done.
@@ -266,6 +270,26 @@ HPSI_API int hpsi_apply_batch(hpsi_ctx* ctx, int nitem, const int* prob, const i
  */
 HPSI_API int davidson_solve(hpsi_ctx* ctx, int ik, int nbnd, double tol, int maxiter, void* psi_inout,
                    double* eig_out, int* iters_out, double* resnorm_out);
+
+/*
+ * cg_solve -- lowest nbnd eigenpairs of H for problem ik by the band-by-band preconditioned
+ * conjugate-gradient minimisation of App. A.2.2.
+ *   nbnd, psi_inout, eig_out, resnorm_out  as in davidson_solve, except that eig_out and the rows
+ *                     of psi_inout come in the order the bands were found (ascending when every
+ *                     band reached its minimum)
+ *   tol          in   a band stops when ||H psi - eps psi||_2 <= tol
+ *   maxiter      in   step limit per band (>= 1)
+ *   iters_out    out  nullable; CG steps over all bands (one application of H to one band each)
+ * Band i starts from row i of psi_inout, orthogonalised to the bands j < i and normalised; each
+ * step takes lambda = <psi|P^2 H|psi> / <psi|P^2|psi>, the gradient P^2 (H - lambda) psi
+ * orthogonalised to the bands j < i, a Polak-Ribiere direction orthogonalised to psi, and the
+ * exact minimum of <psi|H|psi> on psi cos t + n sin t.  P^2 = 1 / max(|k+G|^2/2, t_min) is the
+ * kinetic-only preconditioner (t_min: HPSI_OPT_CG_TMIN, 1 Ha).  Float64 vectors; H is applied at
+ * the context's precision.  Synchronous.  HPSI_ENOTCONV if a band reaches maxiter (outputs then
+ * hold the last iterate).
+ */
+HPSI_API int cg_solve(hpsi_ctx* ctx, int ik, int nbnd, double tol, int maxiter, void* psi_inout,
+                      double* eig_out, int* iters_out, double* resnorm_out);
 
 /*
  * hpsi_eigh_lowest -- the lowest nwant eigenpairs of a dense Hermitian matrix: the reduced

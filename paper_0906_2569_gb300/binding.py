@@ -21,13 +21,13 @@ HPSI_OPT_PRECOND_TAU, HPSI_OPT_PRECOND_SHIFT, HPSI_OPT_KERNEL_TIMING, HPSI_OPT_N
 HPSI_OPT_LOCAL_PATH, HPSI_OPT_TC_KSPLIT, HPSI_OPT_FINAL_FP64, HPSI_OPT_BASIS, HPSI_OPT_AUTOTUNE = 5, 6, 7, 8, 9
 HPSI_OPT_EIGENSOLVER, HPSI_OPT_FP32_GEMM = 10, 11
 HPSI_OPT_LOCKING, HPSI_OPT_LOCK_BATCH, HPSI_OPT_LOCK_BASIS, HPSI_OPT_THICK_RESTART = 12, 13, 14, 15
-HPSI_OPT_RITZ_SPLIT, HPSI_OPT_REORTH_TEST = 16, 17
+HPSI_OPT_RITZ_SPLIT, HPSI_OPT_REORTH_TEST, HPSI_OPT_CG_TMIN = 16, 17, 18
 KERNELS = ("inv_zy", "xvx_y", "fwd_z", "calbec", "dscale", "addvus", "split", "davidson", "eigh", "tridiag")
 STATUS_NAMES = {0: "HPSI_OK", -1: "HPSI_EINVAL", -2: "HPSI_ENOMEM", -3: "HPSI_ECUDA", -4: "HPSI_ENOTCONV",
                 -5: "HPSI_ESINGULAR", -6: "HPSI_ETIMEOUT", -7: "HPSI_ENODEV"}
 
 EXPORTS = ("hpsi_gsphere", "hpsi_setup", "hpsi_setup_cells", "hpsi_nprob", "hpsi_npw", "hpsi_nproj", "hpsi_apply",
-           "hpsi_apply_batch", "hpsi_apply_noalloc", "davidson_solve", "hpsi_eigh_lowest", "hpsi_set_option", "hpsi_kernel_stats", "hpsi_sync", "hpsi_selftest_timeout", "hpsi_last_error",
+           "hpsi_apply_batch", "hpsi_apply_noalloc", "davidson_solve", "cg_solve", "hpsi_eigh_lowest", "hpsi_set_option", "hpsi_kernel_stats", "hpsi_sync", "hpsi_selftest_timeout", "hpsi_last_error",
            "hpsi_destroy")
 
 _lib = None
@@ -60,6 +60,7 @@ def _declare(lib):
     lib.hpsi_apply_batch.argtypes = [V, I, P(I), P(I), P(V), P(V)]
     lib.hpsi_apply_batch.restype = I
     lib.davidson_solve.argtypes = [V, I, I, D, I, V, P(D), P(I), P(D)]
+    lib.cg_solve.argtypes = [V, I, I, D, I, V, P(D), P(I), P(D)]
     lib.davidson_solve.restype = I
     lib.hpsi_eigh_lowest.argtypes = [V, I, V, I, I, V, V]
     lib.hpsi_eigh_lowest.restype = I
@@ -277,4 +278,17 @@ def davidson_solve(ctx: Context, ik: int, psi_inout, tol: float, maxiter: int, r
                                 _dp(eig), ctypes.byref(it), _dp(res))
     if rc != HPSI_ENOTCONV or raise_on_notconv:
         _check(ctx.lib, ctx.handle, rc, "davidson_solve")
+    return eig, it.value, res, rc
+
+
+def cg_solve(ctx: Context, ik: int, psi_inout, tol: float, maxiter: int, raise_on_notconv: bool = True):
+    """cg_solve(): returns (eigenvalues in the order found, total CG steps, residual norms, status)."""
+    nbnd = int(psi_inout.shape[0])
+    eig = np.zeros(nbnd)
+    res = np.zeros(nbnd)
+    it = ctypes.c_int(0)
+    rc = ctx.lib.cg_solve(ctx.handle, int(ik), nbnd, float(tol), int(maxiter), ctypes.c_void_p(_ptr(psi_inout)),
+                          _dp(eig), ctypes.byref(it), _dp(res))
+    if rc != HPSI_ENOTCONV or raise_on_notconv:
+        _check(ctx.lib, ctx.handle, rc, "cg_solve")
     return eig, it.value, res, rc

@@ -351,6 +351,7 @@ static void free_context(Context& c) {
   if (c.cap_stream) cudaStreamDestroy(c.cap_stream);
   davidson_release(c);
   eigh_release(c);
+  cg_release(c);
 }
 
 int nonlocal_apply(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd) {
@@ -763,6 +764,32 @@ extern "C" int davidson_solve(hpsi_ctx* ctx, int ik, int nbnd, double tol, int m
   return rc;
 }
 
+extern "C" int cg_solve(hpsi_ctx* ctx, int ik, int nbnd, double tol, int maxiter, void* psi_inout, double* eig_out,
+                        int* iters_out, double* resnorm_out) {
+  if (!ctx) return HPSI_EINVAL;
+  Context& c = ctx->c;
+  if (ik < 0 || ik >= (int)c.probs.size()) return fail(c, HPSI_EINVAL, "cg_solve: problem index out of range");
+  const Problem& p = c.probs[ik];
+  if (nbnd < 1 || nbnd > p.npw) return fail(c, HPSI_EINVAL, "cg_solve: need 1 <= nbnd <= npw");
+  if (!(tol > 0.0) || maxiter < 1 || !psi_inout || !eig_out)
+    return fail(c, HPSI_EINVAL, "cg_solve: bad tol, maxiter or null pointer");
+  const int kind = pointer_kind(psi_inout);
+  if (kind < 0) return fail(c, HPSI_EINVAL, "cg_solve: unrecognised psi pointer");
+  const size_t bytes = sizeof(double2) * (size_t)nbnd * p.npw;
+  if (kind == 1) return cg_run(c, ik, nbnd, tol, maxiter, static_cast<double2*>(psi_inout), eig_out, iters_out, resnorm_out);
+  int rc = ensure_buffer(c, &c.ws.stage_in, &c.ws.stage_in_bytes, bytes);
+  if (rc) return rc;
+  cudaError_t e = cudaMemcpyAsync(c.ws.stage_in, psi_inout, bytes, cudaMemcpyHostToDevice, c.stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cg_solve host->device copy");
+  rc = cg_run(c, ik, nbnd, tol, maxiter, static_cast<double2*>(c.ws.stage_in), eig_out, iters_out, resnorm_out);
+  if (rc != HPSI_OK && rc != HPSI_ENOTCONV) return rc;
+  e = cudaMemcpyAsync(psi_inout, c.ws.stage_in, bytes, cudaMemcpyDeviceToHost, c.stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cg_solve device->host copy");
+  e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cg_solve");
+  return rc;
+}
+
 extern "C" int hpsi_set_option(hpsi_ctx* ctx, int option, double value) {
   if (!ctx) return HPSI_EINVAL;
   Context& c = ctx->c;
@@ -817,6 +844,11 @@ extern "C" int hpsi_set_option(hpsi_ctx* ctx, int option, double value) {
   if (option == HPSI_OPT_THICK_RESTART) {
     if (value != 0.0 && value != 1.0) return fail(c, HPSI_EINVAL, "HPSI_OPT_THICK_RESTART must be 0 or 1");
     c.thick_restart = (int)value;
+    return HPSI_OK;
+  }
+  if (option == HPSI_OPT_CG_TMIN) {
+    if (!(value > 0.0) || !std::isfinite(value)) return fail(c, HPSI_EINVAL, "HPSI_OPT_CG_TMIN must be > 0");
+    c.cg_tmin = value;
     return HPSI_OK;
   }
   if (option == HPSI_OPT_REORTH_TEST) {

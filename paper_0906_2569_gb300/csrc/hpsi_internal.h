@@ -141,6 +141,8 @@ struct Context {
   int reorth_test = 0;                 // Davidson: second Gram-Schmidt pass only where the first cancelled
   int ritz_split = 0;                  // mixed Davidson: Ritz / restart GEMMs in K chunks added in float64
   void* eigh = nullptr;                // eigensolver handles and work buffers (eigh.cu)
+  void* cg = nullptr;                  // conjugate-gradient solver handles and work buffers (cg.cu)
+  double cg_tmin = 1.0;                // CG preconditioner: P^2 = 1 / max(|k+G|^2/2, cg_tmin)
   cudaStream_t cap_stream = nullptr;   // internal stream for graph capture
   GraphCache graph;
   // launch accounting (always) and per-launch event timing (HPSI_OPT_KERNEL_TIMING)
@@ -231,6 +233,10 @@ int check_device_error(Context& c);   // synchronizes; HPSI_ETIMEOUT if a bounde
 int davidson_run(Context& c, int ik, int nbnd, double tol, int maxiter, double2* psi, double* eig,
                  int* iters, double* resnorm);
 void davidson_release(Context& c);
+// Band-by-band preconditioned CG eigensolver of App. A.2.2 (cg.cu); psi on the device.
+int cg_run(Context& c, int ik, int nbnd, double tol, int maxiter, double2* psi, double* eig, int* iters,
+           double* resnorm);
+void cg_release(Context& c);
 
 // ---- complex64 subspace products on the bf16 tensor cores (subspace_gemm.cu) ----
 // Three-term bf16 split of a complex64 matrix's columns, kept valid up to `valid` columns.
