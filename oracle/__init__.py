@@ -19,6 +19,9 @@ What it computes is the plain definition of each step, in float64 / complex128:
 * ``cg``        -- the band-by-band preconditioned conjugate-gradient eigensolver of App. A.2.2
                    (constrained minimisation per band, kinetic-only P^2, Polak-Ribiere
                    directions, exact line minimum on the unit circle).
+* ``scf``       -- the self-consistency loop of App. A.1 around H|psi>: density, Hartree and LDA
+                   potentials, the scf norm, the mixing of past densities, and the standard and
+                   Harris-Weinert-Foulkes energies.
 * ``eigen``     -- reference eigenvalues: dense LAPACK ``eigh`` of H_GG' (small cells) and
                    scipy LOBPCG on the FFT H|psi> (large cells).
 
@@ -29,4 +32,4 @@ of a rank-one projector), brute-force O(N^2) sums with Cartesian G.r, invariants
 The absolute eigenvalues of the synthetic cells have no printed value in the paper: they
 are pinned only through those properties and the agreement of two independent routes.
 """
-from . import gsphere, hamiltonian, davidson, eigen, cg  # noqa: F401
+from . import gsphere, hamiltonian, davidson, eigen, cg, scf  # noqa: F401

@@ -288,3 +288,129 @@ def pin_cg_precond_ratio(nb=6) -> float:
     finally:
         oracle.cg.precond_p2 = saved
     return float(np.sum(with_p)) / float(np.sum(without))
+
+
+# ---- self-consistency (App. A.1): Hartree, LDA, density, mixing ------------------------------
+
+MADELUNG_SC = 2.837297479480620   # point charge in a neutralising background, simple cubic lattice
+
+
+def pin_hartree_gaussian(L=14.0, sigma=0.6, n=48) -> float:
+    """Periodic Gaussian charge in a neutralising background: by Ewald's decomposition
+    E_H = q^2 / (2 sqrt(pi) sigma) - alpha q^2 / (2 L) + 2 pi q^2 sigma^2 / L^3 (alpha: the simple-cubic
+    Madelung constant), up to erfc(L / 2 sigma) terms."""
+    lat = L * np.eye(3)
+    f = np.arange(n) / n
+    r = np.stack(np.meshgrid(f, f, f, indexing="ij"), -1) * L
+    d = r - np.array([0.31, 0.47, 0.52]) * L
+    d -= L * np.round(d / L)
+    rho = np.exp(-np.sum(d * d, -1) / (2 * sigma ** 2)) / (2 * math.pi * sigma ** 2) ** 1.5
+    rho -= rho.mean()
+    _, eh = oracle.scf.hartree(rho, lat)
+    expect = 1.0 / (2 * math.sqrt(math.pi) * sigma) - MADELUNG_SC / (2 * L) + 2 * math.pi * sigma ** 2 / L ** 3
+    return abs(eh - expect)
+
+
+def pin_hartree_bruteforce(fft=(4, 5, 6), seed=2) -> float:
+    """V_H(r_j) = sum_{G != 0} 4 pi rho(G) e^{iG.r_j} / G^2 by explicit loops over the box with Cartesian
+    G (solve a_i . G = 2 pi m_i) and r_j = sum (j_i / n_i) a_i, on an oblique cell."""
+    lat = np.array([[5.0, 0.3, 0.0], [0.4, 5.5, 0.2], [0.1, -0.3, 6.0]])
+    rng = np.random.default_rng(seed)
+    rho = rng.standard_normal(fft)
+    rho -= rho.mean()
+    vh, _ = oracle.scf.hartree(rho, lat)
+    n1, n2, n3 = fft
+    pts = [(j1, j2, j3) for j1 in range(n1) for j2 in range(n2) for j3 in range(n3)]
+    rj = {p: (p[0] / n1) * lat[0] + (p[1] / n2) * lat[1] + (p[2] / n3) * lat[2] for p in pts}
+    freqs = [[m if m <= n // 2 else m - n for m in range(n)] for n in fft]
+    worst = 0.0
+    vg = {}
+    for m1 in freqs[0]:
+        for m2 in freqs[1]:
+            for m3 in freqs[2]:
+                if (m1, m2, m3) == (0, 0, 0):
+                    continue
+                g = g_cart(lat, (m1, m2, m3))
+                rg = sum(rho[p] * np.exp(-1j * float(g @ rj[p])) for p in pts) / len(pts)
+                vg[(m1, m2, m3)] = (g, 4 * math.pi * rg / float(g @ g))
+    for p in pts:
+        v = sum(val * np.exp(1j * float(g @ rj[p])) for g, val in vg.values())
+        worst = max(worst, abs(v.real - vh[p]))
+    return worst
+
+
+def pin_lda_derivative() -> float:
+    """V_xc = d(rho eps_xc)/d rho: central differences at densities on both sides of r_s = 1."""
+    rs = np.array([0.05, 0.3, 0.8, 0.999, 1.001, 1.5, 4.0, 12.0])
+    rho = 3.0 / (4.0 * math.pi * rs ** 3)
+    _, v = oracle.scf.lda_xc(rho)
+    h = 1e-6 * rho
+    ep, _ = oracle.scf.lda_xc(rho + h)
+    em, _ = oracle.scf.lda_xc(rho - h)
+    fd = ((rho + h) * ep - (rho - h) * em) / (2 * h)
+    return float(np.max(np.abs(fd - v) / np.abs(v)))
+
+
+def pin_lda_limits() -> float:
+    """High density: eps_xc r_s -> -(3/4)(9/(4 pi^2))^(1/3) (Slater exchange of the electron gas);
+    the correlation fit is continuous at r_s = 1 to within its published 1e-4 Ha."""
+    cx = 0.75 * (9.0 / (4.0 * math.pi ** 2)) ** (1.0 / 3.0)
+    rs = 1e-7
+    e, _ = oracle.scf.lda_xc(np.array([3.0 / (4.0 * math.pi * rs ** 3)]))
+    hi = abs(e[0] * rs + cx) / cx
+    a = 3.0 / (4.0 * math.pi * np.array([1.0 - 1e-9, 1.0 + 1e-9]) ** 3)
+    e2, _ = oracle.scf.lda_xc(a)
+    return max(hi / 1e-5, abs(e2[0] - e2[1]) / 1e-4)   # <= 1 when both hold
+
+
+def pin_density_charge(seed=4) -> float:
+    """A single plane wave gives the uniform density f / Omega; a random orthonormal block keeps
+    its charge (sum of occupations)."""
+    lat = 0.5 * 10.2 * np.array([[0.0, 1.0, 1.0], [1.0, 0.0, 1.0], [1.0, 1.0, 0.0]])
+    k = np.array([0.1, -0.05, 0.2])
+    miller = oracle.gsphere.gsphere(lat, 2.0, k)
+    fft = tuple(int(4 * v + 1) for v in np.max(np.abs(np.asarray(miller)), axis=0))
+    omega = abs(float(np.linalg.det(lat)))
+    pw = np.zeros((1, len(miller)), dtype=np.complex128)
+    pw[0, 3] = 1.0
+    rho = oracle.scf.density(pw, np.array([2.0]), miller, fft, lat)
+    e1 = float(np.max(np.abs(rho - 2.0 / omega))) * omega
+    q, _ = np.linalg.qr(workloads.random_block(len(miller), 5, seed).T)
+    occ = np.array([2.0, 2.0, 1.0, 0.5, 0.25])
+    rho = oracle.scf.density(q.T, occ, miller, fft, lat)
+    e2 = abs(oracle.scf.charge(rho, lat) - float(np.sum(occ)))
+    return max(e1, e2)
+
+
+def pin_mixer_linear(seed=6) -> float:
+    """The mixing on a linear contraction x_out = M x_in + b of zero-mean fields reaches the fixed
+    point (I - M)^-1 b (solved directly)."""
+    rng = np.random.default_rng(seed)
+    lat = 6.0 * np.eye(3)
+    fft = (3, 3, 3)
+    n = 27
+    q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    M = q @ np.diag(rng.uniform(-0.9, 0.95, n)) @ q.T
+    c = np.eye(n) - np.ones((n, n)) / n          # keep fields zero-mean
+    M = c @ M @ c
+    b = c @ rng.standard_normal(n)
+    xstar = np.linalg.lstsq(np.eye(n) - M, b, rcond=None)[0]
+    xstar = c @ xstar
+    mixer = oracle.scf.AndersonMixer(lat, nmix=8, beta=0.5)
+    x = np.zeros(fft)
+    for _ in range(80):
+        xo = (M @ x.ravel() + b).reshape(fft)
+        x = mixer.step(x, xo)
+    return float(np.max(np.abs(x.ravel() - xstar)))
+
+
+def scf_small(seed=21, k=(0.07, -0.13, 0.05), ecut=2.5):
+    """The small fcc cell of the CG pins, two atoms, four electrons (two bands)."""
+    lat = 0.5 * 10.2 * np.array([[0.0, 1.0, 1.0], [1.0, 0.0, 1.0], [1.0, 1.0, 0.0]])
+    k = np.asarray(k, dtype=np.float64)
+    miller = oracle.gsphere.gsphere(lat, ecut, k)
+    fft = tuple(int(4 * v + 1) for v in np.max(np.abs(np.asarray(miller)), axis=0))
+    p = workloads.small_cell(ecut=ecut, nat=2, fft=fft, seed=seed, k=k, lattice=lat)
+    vr = workloads.vloc_r(lat, p.atoms, fft)
+    beta = workloads.beta(lat, p.atoms, k, miller)
+    return lat, k, miller, fft, vr, beta, workloads.dmat(len(p.atoms))

@@ -144,3 +144,59 @@ def test_planted_cg_mistake_is_caught(monkeypatch, attr, bad, pin, bad_if):
     else:
         err = _pins.pin_cg_precond_ratio()
     assert bad_if(err), f"pin {pin} missed a planted mistake in {attr}: err={err}"
+
+
+import math
+
+import oracle.scf as SCF
+
+_hartree_ok = SCF.hartree
+_lda_ok = SCF.lda_xc
+_density_ok = SCF.density
+_step_ok = SCF.AndersonMixer.step
+
+
+def _hartree_no_4pi(rho, lattice):
+    vh, eh = _hartree_ok(rho, lattice)
+    return vh / (4 * math.pi), eh / (4 * math.pi)
+
+
+def _hartree_over_g(rho, lattice):      # 1/|G| instead of 1/G^2
+    import scipy.fft
+    rg = scipy.fft.fftn(rho) / rho.size
+    g2 = SCF.grid_g2(lattice, rho.shape)
+    inv = np.zeros_like(g2)
+    nz = g2 > 1e-12
+    inv[nz] = 4 * math.pi / np.sqrt(g2[nz])
+    return np.real(scipy.fft.ifftn(inv * rg) * rho.size), 0.5 * SCF.cell_volume(lattice) * float(np.sum(inv * np.abs(rg) ** 2))
+
+
+def _lda_vx_equals_ex(rho):
+    eps, v = _lda_ok(rho)
+    r = np.asarray(rho, dtype=np.float64)
+    ex = -0.75 * (3.0 * np.maximum(r, 0) / math.pi) ** (1.0 / 3.0)
+    return eps, v - ex / 3.0          # V_x = eps_x instead of 4/3 eps_x
+
+
+def _density_no_volume(psi, occ, miller, fft, lattice):
+    return _density_ok(psi, occ, miller, fft, lattice) * SCF.cell_volume(lattice)
+
+
+def _step_wrong_sign(self, xin, xout):
+    x = _step_ok(self, xin, xout)
+    return 2 * np.array(xin) - x + 0.0 * xout
+
+
+@pytest.mark.parametrize("target,attr,bad,pin,bad_if", [
+    (SCF, "hartree", _hartree_no_4pi, "gauss", lambda e: e > 1e-3),
+    (SCF, "hartree", _hartree_over_g, "brute", lambda e: e > 1e-3),
+    (SCF, "lda_xc", _lda_vx_equals_ex, "deriv", lambda e: e > 1e-3),
+    (SCF, "density", _density_no_volume, "charge", lambda e: e > 1e-3),
+    (SCF.AndersonMixer, "step", _step_wrong_sign, "mixer", lambda e: not (e < 1e-6)),
+])
+def test_planted_scf_mistake_is_caught(monkeypatch, target, attr, bad, pin, bad_if):
+    monkeypatch.setattr(target, attr, bad)
+    err = {"gauss": _pins.pin_hartree_gaussian, "brute": _pins.pin_hartree_bruteforce,
+           "deriv": _pins.pin_lda_derivative, "charge": _pins.pin_density_charge,
+           "mixer": _pins.pin_mixer_linear}[pin]()
+    assert bad_if(err), f"pin {pin} missed a planted mistake in {attr}: err={err}"
