@@ -498,6 +498,7 @@ def cg_throughput(B, torch):
     1503-PW cell (c1) in float64 to residual 1e-8, one untimed and one timed solve (CUDA events).
     Every step applies H to one band; the figure counts those band-applications over the solve.
     A failure here is reported in the JSON line instead of ending the run."""
+    import workloads
     try:
         p = workloads.config1()
         k = p.kpts[0]
