@@ -414,3 +414,63 @@ def scf_small(seed=21, k=(0.07, -0.13, 0.05), ecut=2.5):
     vr = workloads.vloc_r(lat, p.atoms, fft)
     beta = workloads.beta(lat, p.atoms, k, miller)
     return lat, k, miller, fft, vr, beta, workloads.dmat(len(p.atoms))
+
+
+# ---- Gamma-point real-wavefunction form -------------------------------------------------------
+
+def gamma_problem(ecut=2.5, seed=21):
+    """The small fcc cell at k = 0 with a no-wrap box and its dense H."""
+    lat = 0.5 * 10.2 * np.array([[0.0, 1.0, 1.0], [1.0, 0.0, 1.0], [1.0, 1.0, 0.0]])
+    k = np.zeros(3)
+    miller = oracle.gsphere.gsphere(lat, ecut, k)
+    fft = tuple(int(4 * v + 1) for v in np.max(np.abs(np.asarray(miller)), axis=0))
+    p = workloads.small_cell(ecut=ecut, nat=2, fft=fft, seed=seed, k=k, lattice=lat)
+    vr = workloads.vloc_r(lat, p.atoms, fft)
+    beta = workloads.beta(lat, p.atoms, k, miller)
+    h = oracle.hamiltonian.dense_h(lat, k, miller, fft, vr, beta, workloads.dmat(len(p.atoms)))
+    return lat, miller, fft, vr, h
+
+
+def real_fields(miller, fft, n=3, seed=7) -> np.ndarray:
+    """Sphere coefficients of n random real fields on the grid (truncated to the sphere, still real)."""
+    rng = np.random.default_rng(seed)
+    return oracle.hamiltonian.to_reciprocal(rng.standard_normal((n,) + tuple(fft)), miller, fft)
+
+
+def pin_gamma_storage() -> float:
+    """Half <-> full round trip of real functions; the half-storage product equals the full complex
+    product and, by Parseval, the grid sum (1/N_r) sum_j a(r_j) b(r_j) of the real fields."""
+    lat, miller, fft, vr, h = gamma_problem()
+    a = real_fields(miller, fft)
+    e1 = float(np.max(np.abs(oracle.gamma.to_full(oracle.gamma.to_half(a, miller), miller) - a)))
+    ah = oracle.gamma.to_half(a, miller)
+    e2 = abs(oracle.gamma.half_dot(ah[0], ah[1], miller) - float(np.real(np.vdot(a[0], a[1]))))
+    ar = oracle.hamiltonian.to_real_space(a, miller, fft)
+    e3 = float(np.max(np.abs(ar.imag)))
+    e4 = abs(oracle.gamma.half_dot(ah[0], ah[1], miller) - float(np.mean(ar[0].real * ar[1].real)))
+    return max(e1, e2, e3, e4)
+
+
+def pin_gamma_real_h() -> float:
+    """H in the real basis is real symmetric, and its LAPACK eigenvalues (real symmetric routine)
+    equal those of the complex H (Hermitian routine)."""
+    lat, miller, fft, vr, h = gamma_problem()
+    u = oracle.gamma.real_basis(miller)
+    e0 = float(np.max(np.abs(u.conj().T @ u - np.eye(len(miller)))))
+    cols = oracle.hamiltonian.to_real_space(u.T, miller, fft)
+    e1 = float(np.max(np.abs(cols.imag)))
+    hr = oracle.gamma.real_h(h, miller)
+    e2 = float(np.max(np.abs(hr.imag))) / float(np.max(np.abs(hr.real)))
+    e3 = float(np.max(np.abs(hr.real - hr.real.T)))
+    ev = np.linalg.eigvalsh(hr.real)
+    e4 = float(np.max(np.abs(ev - np.linalg.eigvalsh(h))))
+    return max(e0, e1, e2, e3, e4)
+
+
+def pin_gamma_pair_fft() -> float:
+    """Two real orbitals through one complex transform pair give the two local terms."""
+    lat, miller, fft, vr, h = gamma_problem()
+    a = real_fields(miller, fft, 2, seed=9)
+    va, vb = oracle.gamma.local_pair(vr, miller, fft, a[0], a[1])
+    ref = oracle.hamiltonian.local_term(vr, miller, fft, a)
+    return float(max(np.max(np.abs(va - ref[0])), np.max(np.abs(vb - ref[1]))))

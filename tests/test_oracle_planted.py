@@ -200,3 +200,37 @@ def test_planted_scf_mistake_is_caught(monkeypatch, target, attr, bad, pin, bad_
            "deriv": _pins.pin_lda_derivative, "charge": _pins.pin_density_charge,
            "mixer": _pins.pin_mixer_linear}[pin]()
     assert bad_if(err), f"pin {pin} missed a planted mistake in {attr}: err={err}"
+
+
+import oracle.gamma as GM
+
+_pair_ok = GM.local_pair
+_basis_ok = GM.real_basis
+
+
+def _partner_self(miller):
+    return np.arange(len(miller))
+
+
+def _pair_no_conj(vr, miller, fft, psi_a, psi_b):
+    par = GM.partner_index(miller)
+    phi = H.to_real_space(np.stack([psi_a + 1j * psi_b]), miller, fft)
+    c = H.to_reciprocal(phi * vr[None], miller, fft)[0]
+    return 0.5 * (c + c[par]), (c - c[par]) / 2j       # c(-G) without the conjugate
+
+
+def _basis_no_i(miller):
+    u = _basis_ok(miller)
+    return np.where(np.abs(u.imag) > 0, np.abs(u.imag) * np.sign(u.imag), u.real).astype(np.complex128)
+
+
+@pytest.mark.parametrize("attr,bad,pin", [
+    ("partner_index", _partner_self, "storage"),
+    ("local_pair", _pair_no_conj, "pair"),
+    ("real_basis", _basis_no_i, "realh"),
+])
+def test_planted_gamma_mistake_is_caught(monkeypatch, attr, bad, pin):
+    monkeypatch.setattr(GM, attr, bad)
+    err = {"storage": _pins.pin_gamma_storage, "pair": _pins.pin_gamma_pair_fft,
+           "realh": _pins.pin_gamma_real_h}[pin]()
+    assert err > 1e-3, f"pin {pin} missed a planted mistake in {attr}: err={err}"
