@@ -24,6 +24,8 @@ What it computes is the plain definition of each step, in float64 / complex128:
                    Harris-Weinert-Foulkes energies.
 * ``gamma``     -- the Gamma-point real-wavefunction form (Sec. 4): half-sphere storage, the real
                    basis in which H is real symmetric, two real bands per complex FFT.
+* ``fock``      -- Fock exchange at Gamma (App. A.5): codensity potentials by FFT, the
+                   Gygi-Baldereschi treatment of the G = 0 divergence, V_x psi and E_x.
 * ``eigen``     -- reference eigenvalues: dense LAPACK ``eigh`` of H_GG' (small cells) and
                    scipy LOBPCG on the FFT H|psi> (large cells).
 
@@ -34,4 +36,4 @@ of a rank-one projector), brute-force O(N^2) sums with Cartesian G.r, invariants
 The absolute eigenvalues of the synthetic cells have no printed value in the paper: they
 are pinned only through those properties and the agreement of two independent routes.
 """
-from . import gsphere, hamiltonian, davidson, eigen, cg, scf, gamma  # noqa: F401
+from . import gsphere, hamiltonian, davidson, eigen, cg, scf, gamma, fock  # noqa: F401

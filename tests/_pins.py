@@ -474,3 +474,44 @@ def pin_gamma_pair_fft() -> float:
     va, vb = oracle.gamma.local_pair(vr, miller, fft, a[0], a[1])
     ref = oracle.hamiltonian.local_term(vr, miller, fft, a)
     return float(max(np.max(np.abs(va - ref[0])), np.max(np.abs(vb - ref[1]))))
+
+
+# ---- Fock exchange at Gamma (App. A.5) ---------------------------------------------------------
+
+def pin_fock_gaussian(L=10.0, s=1.0, alpha=0.8, ecut=25.0) -> float:
+    """One normalised Gaussian orbital (width s) in a cubic cell: its density is a Gaussian of width
+    sigma = s / sqrt2, and by the Ewald decomposition of the Hartree pin the Gygi-Baldereschi Gamma
+    estimate of its self-exchange is E_x = -(1 / (sqrt(pi) sigma) + 4 pi (sigma^2 - alpha) / L^3): the
+    Madelung 1/L terms cancel."""
+    lat = L * np.eye(3)
+    k = np.zeros(3)
+    miller = oracle.gsphere.gsphere(lat, ecut, k)
+    fft = tuple(int(4 * v + 1) for v in np.max(np.abs(np.asarray(miller)), axis=0))
+    n = fft[0]
+    f = np.arange(n) / n
+    r = np.stack(np.meshgrid(f, f, f, indexing="ij"), -1) * L
+    d = r - np.array([0.37, 0.52, 0.44]) * L
+    d -= L * np.round(d / L)
+    phi = (math.pi * s * s) ** -0.75 * np.exp(-np.sum(d * d, -1) / (2 * s * s))
+    psi = oracle.hamiltonian.to_reciprocal((L ** 1.5 * phi)[None].astype(np.complex128), miller, fft)
+    psi /= np.linalg.norm(psi)
+    ex = oracle.fock.exchange_energy(psi, miller, fft, lat, alpha)
+    sigma = s / math.sqrt(2.0)
+    expect = -(1.0 / (math.sqrt(math.pi) * sigma) + 4 * math.pi * (sigma ** 2 - alpha) / L ** 3)
+    return abs(ex - expect)
+
+
+def pin_fock_hermitian_invariant(seed=12) -> float:
+    """<a|V_x b> = <V_x a|b>* for complex orbitals, and E_x depends only on the occupied subspace
+    (a unitary rotation of the occupied orbitals leaves it unchanged)."""
+    lat, miller, fft, vr, h = gamma_problem(ecut=2.0)
+    rng = np.random.default_rng(seed)
+    occ, _ = np.linalg.qr(rng.standard_normal((len(miller), 3)) + 1j * rng.standard_normal((len(miller), 3)))
+    occ = occ.T
+    ab = workloads.random_block(len(miller), 2, seed + 1)
+    vx = oracle.fock.apply_vx(ab, occ, miller, fft, lat)
+    e1 = abs(np.vdot(ab[0], vx[1]) - np.conj(np.vdot(ab[1], vx[0])))
+    u, _ = np.linalg.qr(rng.standard_normal((3, 3)) + 1j * rng.standard_normal((3, 3)))
+    e_a = oracle.fock.exchange_energy(occ, miller, fft, lat)
+    e_b = oracle.fock.exchange_energy(u.T @ occ, miller, fft, lat)
+    return max(float(e1), abs(e_a - e_b))

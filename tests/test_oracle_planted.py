@@ -234,3 +234,32 @@ def test_planted_gamma_mistake_is_caught(monkeypatch, attr, bad, pin):
     err = {"storage": _pins.pin_gamma_storage, "pair": _pins.pin_gamma_pair_fft,
            "realh": _pins.pin_gamma_real_h}[pin]()
     assert err > 1e-3, f"pin {pin} missed a planted mistake in {attr}: err={err}"
+
+
+import oracle.fock as FK
+
+
+def _xdiv_zero(lattice, fft, alpha=1.0):
+    return 0.0
+
+
+def _vx_codensity_swapped(psi, occupied, miller, fft, lattice, alpha=1.0):
+    omega = SCF.cell_volume(lattice)
+    xdiv = FK.exx_div(lattice, fft, alpha)
+    pr = H.to_real_space(np.asarray(psi, dtype=np.complex128), miller, fft)
+    orr = H.to_real_space(np.asarray(occupied, dtype=np.complex128), miller, fft)
+    out = np.zeros_like(pr)
+    for b in range(pr.shape[0]):
+        for j in range(orr.shape[0]):
+            out[b] -= orr[j] * FK.coulomb(orr[j] * np.conj(pr[b]) / omega, lattice, xdiv)
+    return H.to_reciprocal(out, miller, fft)
+
+
+@pytest.mark.parametrize("attr,bad,pin", [
+    ("exx_div", _xdiv_zero, "gauss"),
+    ("apply_vx", _vx_codensity_swapped, "herm"),
+])
+def test_planted_fock_mistake_is_caught(monkeypatch, attr, bad, pin):
+    monkeypatch.setattr(FK, attr, bad)
+    err = {"gauss": _pins.pin_fock_gaussian, "herm": _pins.pin_fock_hermitian_invariant}[pin]()
+    assert err > 1e-3, f"pin {pin} missed a planted mistake in {attr}: err={err}"
