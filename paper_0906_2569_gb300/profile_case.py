@@ -9,6 +9,11 @@ captures only them.
 With ``--eigh N`` it instead solves the reduced Hermitian eigenproblem of order N (lowest
 ``--nwant`` pairs) on a seeded random matrix of the scale of a Davidson reduced H, the same way:
 two warm-up solves, then ``--reps`` bracketed ones.
+
+With ``--cg B`` it runs the band-by-band CG eigensolver on the first B bands of the cell named by
+``--config`` in float64 (residual 1e-8, at most ``--cg-maxiter`` steps per band): one warm-up solve,
+then one bracketed solve.  Every CG step's launches (three single-CTA kernels, the Gram-Schmidt
+ZGEMVs and one single-band H|psi>) fall inside the bracket.
 """
 from __future__ import annotations
 
@@ -28,12 +33,17 @@ def main():
     ap.add_argument("--nbnd", type=int, default=0)
     ap.add_argument("--eigh", type=int, default=0)
     ap.add_argument("--nwant", type=int, default=160)
+    ap.add_argument("--cg", type=int, default=0)
+    ap.add_argument("--cg-maxiter", type=int, default=3000)
     args = ap.parse_args()
     import torch
     import workloads
     from paper_0906_2569_gb300 import binding as B
     if args.eigh:
         eigh_case(args, torch, workloads, B)
+        return
+    if args.cg:
+        cg_case(args, torch, workloads, B)
         return
     p = workloads.CONFIGS[args.config]()
     nb = args.nbnd or p.nbnd
@@ -75,6 +85,24 @@ def eigh_case(args, torch, workloads, B):
     torch.cuda.synchronize()
     torch.cuda.profiler.stop()
     print("ok eigh", n, nw, float(w.sum()))
+
+
+def cg_case(args, torch, workloads, B):
+    p = workloads.CONFIGS[args.config]()
+    k = p.kpts[0]
+    m = B.hpsi_gsphere(p.lattice, p.ecut, k)
+    ctx = B.hpsi_setup(p.lattice, p.ecut, [k], p.fft, workloads.vloc_r(p.lattice, p.atoms, p.fft),
+                       [workloads.beta(p.lattice, p.atoms, k, m)], workloads.dmat(len(p.atoms)), B.HPSI_FP64,
+                       torch.cuda.current_stream().cuda_stream)
+    x0 = torch.from_numpy(workloads.psi0(p.lattice, k, m, args.cg, p.psi_seed)).cuda()
+    B.cg_solve(ctx, 0, x0.clone(), 1e-8, args.cg_maxiter)
+    torch.cuda.synchronize()
+    x = x0.clone()
+    torch.cuda.profiler.start()
+    eig, steps, res, rc = B.cg_solve(ctx, 0, x, 1e-8, args.cg_maxiter)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    print("ok cg", args.config, args.cg, steps, float(eig.sum()))
 
 
 if __name__ == "__main__":
