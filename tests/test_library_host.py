@@ -78,3 +78,17 @@ def test_binding_constants_match_header(B):
     for n in named:
         assert n in declared, f"{n} is not declared in hpsi.h"
         assert getattr(B, n) == declared[n], n
+
+
+def test_every_declared_option_is_handled():
+    """Each hpsi_option enumerator in hpsi.h has a branch in hpsi_set_option (static check of
+    csrc/api.cu), so no declared option falls through to the 'unknown option' error."""
+    src = open(os.path.join(ROOT, "include", "hpsi.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    body = src[src.index("enum hpsi_option"):]
+    body = body[:body.index("};")]
+    opts = re.findall(r"\b(HPSI_OPT_[A-Z0-9_]+)\s*=", body)
+    api = open(os.path.join(ROOT, "paper_0906_2569_gb300", "csrc", "api.cu")).read()
+    assert len(opts) >= 18
+    for o in opts:
+        assert f"option == {o}" in api, f"{o} has no branch in hpsi_set_option"
