@@ -26,17 +26,22 @@ constexpr int kMaxDevices = 64;
 void* g_scratch_addr[kMaxDevices] = {nullptr};
 std::mutex g_scratch_mu;
 
-// Device address of the array on the current device, looked up once per device.  The host-side
-// name g_noalloc_scratch is only a stand-in: kernels must be given this address instead.
+// Device address of the array on the context's device, looked up once per device with that
+// device current (the caller's current device is restored).  The host-side name g_noalloc_scratch
+// is only a stand-in: kernels must be given this address instead.
 int scratch_address(hpsi::Context& c, void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return hpsi::cuda_fail(c, e, "hpsi_apply_noalloc: cudaGetDevice");
+  const int dev = c.device;
   if (dev < 0 || dev >= kMaxDevices) return hpsi::fail(c, HPSI_ENODEV, "hpsi_apply_noalloc: device index too large");
   std::lock_guard<std::mutex> lock(g_scratch_mu);
   if (!g_scratch_addr[dev]) {
+    int prev = 0;
+    cudaError_t e = cudaGetDevice(&prev);
+    if (e != cudaSuccess) return hpsi::cuda_fail(c, e, "hpsi_apply_noalloc: cudaGetDevice");
+    if (prev != dev && (e = cudaSetDevice(dev)) != cudaSuccess)
+      return hpsi::cuda_fail(c, e, "hpsi_apply_noalloc: cudaSetDevice");
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (prev != dev) cudaSetDevice(prev);
     if (e != cudaSuccess || !p) return hpsi::cuda_fail(c, e, "hpsi_apply_noalloc: cudaGetSymbolAddress");
     g_scratch_addr[dev] = p;
   }
@@ -74,17 +79,22 @@ extern "C" int hpsi_apply_noalloc(hpsi_ctx* ctx, int ik, const void* psi_in, voi
   void* base = nullptr;
   int rc = scratch_address(c, &base);
   if (rc) return rc;
-  // largest band chunk whose X, Y and nonlocal partials fit the array
+  // Largest band chunk whose X and Y and the nonlocal partials fit the array.  X and Y of a chunk
+  // scale with its bands, so a shorter last chunk fits in the same places; its nonlocal K-split
+  // is planned against the room left after the full chunk's X and Y, and one split of the partials
+  // grows with the bands too, so whatever fits the full chunk fits the last one.
+  const size_t cs = hpsi::cur_prec(c) == HPSI_FP64 ? sizeof(double2) : sizeof(float2);
+  auto xbytes = [&](int nb) { return align256(cs * (size_t)nb * p.n[2] * p.npl * p.n[1]); };
+  auto ybytes = [&](int nb) { return align256(cs * (size_t)nb * p.n[2] * p.nst); };
   const size_t per_band = hpsi::local_scratch_per_band(p, hpsi::cur_prec(c));
   int chunk = 0;
   for (int nb = std::min(nbnd, 4096); nb >= 1; nb = nb > 64 ? nb - 32 : nb - 1) {
+    const size_t xy = xbytes(nb) + ybytes(nb);
+    if (xy > kNoAllocBytes) continue;
     int ns = 0, kc = 0;
     size_t nl = 0;
     hpsi::nonlocal_fp64_plan(c, p, nb, &ns, &kc, &nl);
-    const size_t cs = hpsi::cur_prec(c) == HPSI_FP64 ? sizeof(double2) : sizeof(float2);
-    const size_t xb = align256(cs * (size_t)nb * p.n[2] * p.npl * p.n[1]);
-    const size_t yb = align256(cs * (size_t)nb * p.n[2] * p.nst);
-    if (xb + yb + align256(p.nproj ? nl : 0) <= kNoAllocBytes) {
+    if (p.nproj == 0 || xy + align256(nl) <= kNoAllocBytes) {
       chunk = nb;
       break;
     }
@@ -93,20 +103,22 @@ extern "C" int hpsi_apply_noalloc(hpsi_ctx* ctx, int ik, const void* psi_in, voi
     return hpsi::fail(c, HPSI_EINVAL,
                       "hpsi_apply_noalloc: one band needs " + std::to_string(per_band) +
                           " bytes of intermediates, more than the fixed 64 MiB array; use hpsi_apply");
-  const size_t cs = hpsi::cur_prec(c) == HPSI_FP64 ? sizeof(double2) : sizeof(float2);
   unsigned char* s = static_cast<unsigned char*>(base);
   void* X = s;
-  void* Y = s + align256(cs * (size_t)chunk * p.n[2] * p.npl * p.n[1]);
-  void* NL = static_cast<unsigned char*>(Y) + align256(cs * (size_t)chunk * p.n[2] * p.nst);
+  void* Y = s + xbytes(chunk);
+  void* NL = static_cast<unsigned char*>(Y) + ybytes(chunk);
+  const size_t nl_room = kNoAllocBytes - xbytes(chunk) - ybytes(chunk);
   const double2* psi = static_cast<const double2*>(psi_in);
   double2* hpsi = static_cast<double2*>(hpsi_out);
-  c.band_apps += nbnd;
   for (int b = 0; b < nbnd; b += chunk) {
     const int nb = std::min(chunk, nbnd - b);
+    if (xbytes(nb) > xbytes(chunk) || ybytes(nb) > ybytes(chunk))
+      return hpsi::fail(c, HPSI_EINVAL, "hpsi_apply_noalloc: internal chunk sizing error");
     rc = hpsi::local_apply_into(c, p, psi + (size_t)b * p.npw, hpsi + (size_t)b * p.npw, nb, X, Y, nb);
     if (rc) return rc;
-    rc = hpsi::nonlocal_fp64_into(c, p, psi + (size_t)b * p.npw, hpsi + (size_t)b * p.npw, nb, NL);
+    rc = hpsi::nonlocal_fp64_into(c, p, psi + (size_t)b * p.npw, hpsi + (size_t)b * p.npw, nb, NL, nl_room);
     if (rc) return rc;
+    c.band_apps += nb;
   }
   return HPSI_OK;
 }

@@ -171,24 +171,35 @@ int nonlocal_apply_fp64(Context& c, const Problem& p, const double2* psi, double
   return HPSI_OK;
 }
 
-// Split of calbec's K = npw range for nbnd bands, and the partial / w bytes it needs.
-void nonlocal_fp64_plan(const Context& c, const Problem& p, int nbnd, int* nsplit, int* kchunk, size_t* bytes) {
+// Split of calbec's K = npw range for nbnd bands, and the partial / w bytes it needs.  With
+// max_bytes > 0 the split count is lowered until the partials and w fit in max_bytes; *bytes is
+// then still larger than max_bytes only if one split does not fit either (nsplit = 1).
+void nonlocal_fp64_plan(const Context& c, const Problem& p, int nbnd, int* nsplit, int* kchunk, size_t* bytes,
+                        size_t max_bytes) {
   const int tilesp = (p.nproj + CB_TP - 1) / CB_TP, tilesb = (nbnd + CB_TB - 1) / CB_TB;
   int ns = std::max(1, (3 * c.sm_count) / std::max(1, tilesp * tilesb));
+  const size_t unit = sizeof(double2) * (size_t)nbnd * p.nproj;   // one split's partials, or w
+  if (max_bytes > 0 && unit > 0) {
+    const size_t cap = max_bytes / unit;                           // splits + 1 that fit
+    ns = std::min<size_t>(ns, cap > 1 ? cap - 1 : 1);
+  }
   int kc = (p.npw + ns - 1) / ns;
   kc = std::max(CB_TK * 4, ((kc + CB_TK - 1) / CB_TK) * CB_TK);
-  ns = (p.npw + kc - 1) / kc;
+  ns = (p.npw + kc - 1) / kc;   // never above the ns that kc was derived from
   *nsplit = ns;
   *kchunk = kc;
-  *bytes = sizeof(double2) * ((size_t)ns * nbnd * p.nproj + (size_t)nbnd * p.nproj);
+  *bytes = unit * ((size_t)ns + 1);
 }
 
-// The same three launches with caller-provided partial and w buffers (sized by nonlocal_fp64_plan).
-int nonlocal_fp64_into(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd, void* scratch) {
+// The same three launches with caller-provided partial and w buffers of `capacity` bytes; the
+// K-split is planned to fit them (HPSI_EINVAL, before any launch, if even one split does not).
+int nonlocal_fp64_into(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd, void* scratch,
+                       size_t capacity) {
   if (p.nproj == 0 || nbnd == 0) return HPSI_OK;
   int nsplit = 0, kchunk = 0;
   size_t bytes = 0;
-  nonlocal_fp64_plan(c, p, nbnd, &nsplit, &kchunk, &bytes);
+  nonlocal_fp64_plan(c, p, nbnd, &nsplit, &kchunk, &bytes, capacity);
+  if (bytes > capacity) return fail(c, HPSI_EINVAL, "nonlocal float64 kernels: partial sums do not fit the scratch");
   const int tilesp = (p.nproj + CB_TP - 1) / CB_TP, tilesb = (nbnd + CB_TB - 1) / CB_TB;
   double2* part = reinterpret_cast<double2*>(scratch);
   double2* w = part + (size_t)nsplit * nbnd * p.nproj;
