@@ -1072,6 +1072,7 @@ static int davidson_run_mixed(Context& c, DavHandles& h, int ik, int nbnd, doubl
   // eigenvalue of H, so a solve whose largest residual stops falling (kStall iterations without a
   // 10% drop) goes on with plain restarts.
   bool thick = c.thick_restart != 0;
+  bool refresh = false;
   int stall = 0;
   double best = INFINITY;
   auto basis_limit = [&](int locked) { return locked > 0 ? std::min(mmax, c.lock_basis * (N - locked)) : mmax; };
@@ -1113,14 +1114,19 @@ static int davidson_run_mixed(Context& c, DavHandles& h, int ik, int nbnd, doubl
     }
     if (it >= maxiter) break;
     ++it;
-    if (thick) {
+    {
+      // kStall iterations without a 10% drop of the largest residual: first switch thick restarts
+      // off; if it stalls again, restart with H applied afresh to the kept vectors, which replaces
+      // stored products that have drifted from H times the stored (rotated) vectors
       double rmax = 0.0;
       for (int i = 0; i < NA; ++i) rmax = std::max(rmax, rn[i]);
       if (rmax < 0.9 * best) {
         best = rmax;
         stall = 0;
       } else if (++stall >= kStall) {
-        thick = false;
+        stall = 0;
+        if (thick) thick = false;
+        else refresh = true;
       }
     }
     // Lock: converged Ritz vectors move to lock32.  t32, eps and rnorm keep this iteration's
@@ -1136,7 +1142,7 @@ static int davidson_run_mixed(Context& c, DavHandles& h, int ik, int nbnd, doubl
       if ((int)lsel.size() < std::max(1, (int)std::ceil(c.lock_batch * NA))) lsel.clear();
     }
     const int nl = (int)lsel.size();
-    if (nl > 0 || m + nc > mlim) {
+    if (nl > 0 || m + nc > mlim || refresh) {
       if (nl > 0) {
         DCK(cudaMemcpyAsync(w.idx2, lsel.data(), sizeof(int) * nl, cudaMemcpyHostToDevice, c.stream), "lock index copy");
         HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_gather_rows32<<<nl, 256, 0, c.stream>>>(
@@ -1184,6 +1190,13 @@ static int davidson_run_mixed(Context& c, DavHandles& h, int ik, int nbnd, doubl
           }
           DCK(cudaMemcpyAsync(src, w.rst32, vb * keep, cudaMemcpyDeviceToDevice, c.stream), "restart copy");
         }
+      }
+      if (refresh) {
+        for (int b = 0; b < keep; b += N) {
+          rc = apply32(c, w, ik, w.phi32 + (size_t)b * npw, w.hphi32 + (size_t)b * npw, std::min(N, keep - b));
+          if (rc) return rc;
+        }
+        refresh = false;
       }
       // psi32 keeps the active Ritz vectors in the new numbering for an exit before the next step
       if (nl > 0) DCK(cudaMemcpyAsync(w.psi32, w.phi32, vb * na, cudaMemcpyDeviceToDevice, c.stream), "active copy");
