@@ -64,7 +64,8 @@ enum hpsi_option {
                                  1: always the generic radix-2/3/4/5 kernels */
   HPSI_OPT_TC_KSPLIT = 6,     /* mixed path: at most this many 64-wide K steps accumulate in one
                                  tensor-memory accumulator of <beta|psi> before the partial sums
-                                 are added in float64 (0: chosen for occupancy) */
+                                 are added in float64 (0, default: at most 16, fewer where the
+                                 output tiles alone would not fill the GPU) */
   HPSI_OPT_FINAL_FP64 = 7,    /* mixed davidson_solve: 1 (default) takes the final Rayleigh
                                  quotients with one float64 application of H to the Ritz vectors;
                                  0 with the mixed H */
@@ -108,7 +109,8 @@ enum hpsi_option {
                                  Ritz vectors; 1 (default): it keeps the lowest non-locked Ritz
                                  vectors up to half the basis limit (at least the active ones).  A
                                  mixed solve whose largest residual has not fallen by 10% in 8
-                                 iterations continues with plain restarts */
+                                 iterations continues with plain restarts, and if it stalls again
+                                 restarts with H applied afresh to the kept vectors */
   HPSI_OPT_RITZ_SPLIT = 16,   /* mixed davidson_solve: 1: the Ritz-vector and restart products
                                  (inner dimension = basis size) run as float32 GEMMs over at most 8
                                  chunks of the inner dimension whose results are added in float64;
@@ -116,8 +118,13 @@ enum hpsi_option {
   HPSI_OPT_REORTH_TEST = 17,  /* davidson_solve: 1: the unit corrections are projected out of the
                                  basis once, and a second time only if a column kept less than half
                                  its squared norm; 0 (default): always twice */
-  HPSI_OPT_CG_TMIN = 18       /* cg_solve: the preconditioner is P^2 = 1 / max(|k+G|^2 / 2, value),
+  HPSI_OPT_CG_TMIN = 18,      /* cg_solve: the preconditioner is P^2 = 1 / max(|k+G|^2 / 2, value),
                                  value > 0 in Ha (default 1) */
+  HPSI_OPT_SCF_NMIX = 19,     /* hpsi_scf: past (input density, residual) pairs the mixing combines
+                                 (1..16, default 8) */
+  HPSI_OPT_SCF_BETA = 20,     /* hpsi_scf: step along the optimal residual (0 < value <= 1, default 0.5) */
+  HPSI_OPT_SCF_DAVIDSON_TOL = 21  /* hpsi_scf: residual tolerance of the Davidson solve of each
+                                 iteration (default 1e-9) */
 };
 
 /* Kernel classes reported by hpsi_kernel_stats. */
@@ -133,7 +140,15 @@ enum hpsi_kernel {
   HPSI_K_EIGH = 8,     /* reduced eigenproblem: multisection, inverse iteration,
                           back-transformation helpers */
   HPSI_K_TRIDIAG = 9,  /* reduced eigenproblem: the Householder reduction to tridiagonal form */
-  HPSI_K_COUNT = 10
+  HPSI_K_GAMMA = 10,   /* Gamma-point form: packing two real bands into one complex band, unpacking */
+  HPSI_K_SCF = 11,     /* self-consistency loop: density, full-box transforms, Hartree, LDA, mixing,
+                          potential update */
+  HPSI_K_FOCK = 12,    /* exchange operator: sphere <-> box maps, codensities, full-box transforms,
+                          Coulomb kernel, sums over occupied bands */
+  HPSI_K_COUNT = 13,
+  HPSI_K_AT_FP64 = 16  /* added to a class in hpsi_kernel_stats: only the launches made while H was
+                          applied in float64 (all of them in a float64 context; in a mixed context
+                          the final float64 application of davidson_solve) */
 };
 
 enum hpsi_precision {
@@ -232,6 +247,44 @@ HPSI_API int hpsi_apply(hpsi_ctx* ctx, int ik, const void* psi_in, void* hpsi_ou
 HPSI_API int hpsi_apply_noalloc(hpsi_ctx* ctx, int ik, const void* psi_in, void* hpsi_out, int nbnd);
 
 /*
+ * hpsi_apply_gamma -- H psi for real orbitals at k = 0, half the components stored (paper Sec. 4,
+ * the Gamma-point trick of PWscf).
+ *   psi_in, hpsi_out  complex128 [nbnd][nh], nh = (npw(ik) + 1) / 2: the coefficients c(G) of the
+ *                     half sphere S+, which is the last nh entries of the sphere's order: G = 0
+ *                     first (its coefficient must be real; an imaginary part is ignored), then
+ *                     every G whose first nonzero Miller index is positive.  c(-G) = conj(c(G))
+ *                     is implied.  Device (asynchronous) or host (synchronous) memory, as in
+ *                     hpsi_apply; must not overlap.
+ * Two bands share one complex transform pair and one pass of the nonlocal contractions: with
+ * f = psi_a + i psi_b, F = H f, (H psi_a)(G) = (F(G) + conj F(-G)) / 2 and
+ * (H psi_b)(G) = (F(G) - conj F(-G)) / (2i).  Valid when H maps real functions to real ones; the
+ * library checks at setup that problem ik is at k = 0, that its sphere is symmetric, and that each
+ * projector has beta_p(-G) = u_p conj(beta_p(G)) with |u_p| = 1 and conj(u_p) u_q conj(D_pq) = D_pq
+ * (true for real-Y_lm projectors with any per-projector phase and real diagonal D); otherwise
+ * HPSI_EINVAL with the reason in hpsi_last_error.  Counts nbnd band-applications.
+ */
+HPSI_API int hpsi_apply_gamma(hpsi_ctx* ctx, int ik, const void* psi_in, void* hpsi_out, int nbnd);
+
+/*
+ * davidson_solve_gamma -- davidson_solve for real orbitals at k = 0 (paper Sec. 4 with the block
+ * Davidson of App. A.2.1).
+ *   psi_inout    in/out complex128 [nbnd][nh] half-sphere coefficients (as hpsi_apply_gamma),
+ *                     device or host; initial guess in, orthonormal real eigenvectors out
+ *   other arguments as in davidson_solve (nbnd times the basis factor must not exceed npw)
+ * The real orbital with half coefficients c is the real vector x = (c(0), 0) at G = 0 and
+ * sqrt2 (Re c(G), Im c(G)) elsewhere; inner products are x_a . x_b and H is real symmetric, so the
+ * subspace products are real GEMMs (float64 in a float64 context, float32 in a mixed one) and the
+ * reduced problems real symmetric (float64, the library's real eigensolver as in
+ * hpsi_eigh_lowest_sym, cuSOLVER dsyevdx behind it).  Residual norms and Cholesky
+ * factors are float64; the preconditioner uses <G|H|G> for both coordinates of each G.  In a mixed
+ * context the returned eigenvalues are float64 Rayleigh quotients after one float64 application of
+ * H (HPSI_OPT_FINAL_FP64).  HPSI_OPT_BASIS, _THICK_RESTART, _PRECOND_TAU and _PRECOND_SHIFT apply;
+ * locking and the subspace-GEMM options do not.  Synchronous; HPSI_ENOTCONV if maxiter is reached.
+ */
+HPSI_API int davidson_solve_gamma(hpsi_ctx* ctx, int ik, int nbnd, double tol, int maxiter, void* psi_inout,
+                                  double* eig_out, int* iters_out, double* resnorm_out);
+
+/*
  * hpsi_apply_batch -- H psi for several problems (k-points or cells) in one launch sequence:
  * for i < nitem: hpsi_out[i] = H(prob[i]) psi_in[i] with nbnd[i] bands.  Device pointers only.
  * Items whose cubic box has register-codelet kernels share one launch of each local-potential
@@ -292,6 +345,59 @@ HPSI_API int cg_solve(hpsi_ctx* ctx, int ik, int nbnd, double tol, int maxiter, 
                       double* eig_out, int* iters_out, double* resnorm_out);
 
 /*
+ * hpsi_scf -- the self-consistency loop of App. A.1 around davidson_solve, for problem ik of a
+ * float64 context (its local potential as given at setup is V_ext).
+ *   nocc         in   occupied bands (two electrons each), >= 1
+ *   nbnd         in   bands solved each iteration, nocc <= nbnd (extra bands help the eigensolver)
+ *   tol          in   stop when the scf norm ||rho_out - rho_in||^2 < tol (Ha), with
+ *                     ||a||^2 = 4 pi Omega sum_{G != 0} |a(G)|^2 / G^2 (twice the Hartree energy of a)
+ *   maxiter      in   iteration limit
+ *   psi_inout    in/out complex128 [nbnd][npw(ik)], device or host: starting orbitals, then the
+ *                     orbitals of the last iteration
+ *   rho_inout    in/out host float64 [n1][n2][n3]: the starting density rho_in (electrons per bohr^3
+ *                     on the grid), then the converged input density
+ *   eig_out      out  host float64 [nbnd]: eigenvalues of the last iteration's H
+ *   energies_out out  host float64 [2]: E = sum_i f_i eps_i - int rho_out V_Hxc[rho_in] + E_Hxc[rho_out]
+ *                     and the Harris-Weinert-Foulkes E' with rho_in in place of rho_out (no ion-ion
+ *                     term); they agree at self-consistency
+ *   iters_out    out  nullable: iterations taken
+ *   norm2_out    out  nullable host float64 [maxiter]: ||rho_out - rho_in||^2 of each iteration
+ * Each iteration: V = V_ext + V_H[rho_in] + V_xc[rho_in] (V_H(G) = 4 pi rho(G) / G^2, V_H(0) = 0;
+ * LDA: Slater exchange and the Perdew-Zunger parametrisation of the Ceperley-Alder correlation) is
+ * written into the context; davidson_solve (tolerance HPSI_OPT_SCF_DAVIDSON_TOL) from the previous
+ * orbitals; rho_out = sum_{i < nocc} 2 |psi_i(r)|^2 / Omega; the next rho_in is the combination of
+ * the last HPSI_OPT_SCF_NMIX inputs whose combined residual has the smallest scf norm, plus
+ * HPSI_OPT_SCF_BETA times that residual (the Anderson form).  On return the context's potential is
+ * V[rho_in] of the last iteration, so hpsi_apply applies the self-consistent H.  The density is that
+ * of problem ik alone.  Synchronous.  HPSI_ENOTCONV if maxiter is reached (outputs hold the last
+ * iterate).
+ */
+HPSI_API int hpsi_scf(hpsi_ctx* ctx, int ik, int nocc, int nbnd, double tol, int maxiter, void* psi_inout,
+                      double* rho_inout, double* eig_out, double* energies_out, int* iters_out, double* norm2_out);
+
+/*
+ * hpsi_fock_apply -- the Fock exchange operator at the Gamma point (paper App. A.5) applied to a
+ * block of bands, for closed shells: with phi = psi / Omega^(1/2),
+ *     (V_x psi_b)(r) = - sum_j psi_j(r) v_bj(r),  v_bj = Coulomb potential of conj(psi_j) psi_b / Omega,
+ *     v(G) = 4 pi n(G) / G^2 (G != 0),  v(0) = 4 pi n(0) x_div,
+ *     x_div = Omega / (2 pi)^3 * 2 pi^(3/2) / alpha^(1/2) - sum_{G != 0 in the FFT box} e^{-alpha G^2} / G^2
+ * (the Gygi-Baldereschi treatment of the q -> 0 divergence with the auxiliary function
+ * e^{-alpha G^2} / G^2 for the single q point; the 0/0 term the paper estimates from a coarser q grid
+ * is left out).  Codensities are formed on the full FFT box.
+ *   ik           in   a problem at k = 0 (else HPSI_EINVAL)
+ *   nocc, occ    in   device complex128 [nocc][npw]: the occupied orbitals (two electrons each)
+ *   psi_in       in   device complex128 [nbnd][npw]
+ *   vx_out       out  device complex128 [nbnd][npw]: (V_x psi)(G) on the sphere; must not overlap
+ *                     occ or psi_in
+ *   alpha        in   exponent of the auxiliary function (bohr^2), > 0 (1 is the usual choice)
+ *   ex_out       out  nullable host double: Re sum_b <psi_b|V_x psi_b>; with psi_in = occ this is the
+ *                     exchange energy E_x = - sum_ij (ij|ji) of the occupied set (synchronizes)
+ * Asynchronous on the context's stream when ex_out is NULL.  Float64 throughout.
+ */
+HPSI_API int hpsi_fock_apply(hpsi_ctx* ctx, int ik, int nocc, const void* occ, const void* psi_in, void* vx_out,
+                             int nbnd, double alpha, double* ex_out);
+
+/*
  * hpsi_eigh_lowest -- the lowest nwant eigenpairs of a dense Hermitian matrix: the reduced
  * problem sum_k (H_jk - eps S_jk) c_k = 0 that the Rayleigh-Ritz step of block Davidson solves
  * over its orthonormal reduced basis (App. A.2.1; S_jk is then the identity).  davidson_solve
@@ -316,6 +422,22 @@ HPSI_API int cg_solve(hpsi_ctx* ctx, int ik, int nbnd, double tol, int maxiter, 
 HPSI_API int hpsi_eigh_lowest(hpsi_ctx* ctx, int n, const void* a, int lda, int nwant, void* w_out, void* v_out);
 
 /*
+ * hpsi_eigh_lowest_sym -- hpsi_eigh_lowest for a real symmetric matrix: the reduced problem of the
+ * Rayleigh-Ritz step when the reduced basis is real (davidson_solve_gamma, paper Sec. 4 with
+ * App. A.2.1).
+ *   a            in   device float64, column-major, leading dimension lda >= n; upper triangle read
+ *   w_out        out  device double[nwant], ascending
+ *   v_out        out  device float64 [nwant][n] (column-major n x nwant, leading dim n): orthonormal
+ *                     eigenvectors, each up to a sign (and a rotation within a degenerate eigenvalue)
+ * Float64.  Real Householder reduction to tridiagonal form (one cooperative launch, a quarter of the
+ * float64 work of the complex one), Sturm multisection, inverse iteration, real compact-WY
+ * back-transformation.  n up to 1824 on 152 SMs (the rows must fit their shared memory), otherwise
+ * HPSI_EINVAL; also HPSI_EINVAL if inverse iteration loses a vector (davidson_solve_gamma then uses
+ * cuSOLVER dsyevdx).  Synchronizes the context's stream.
+ */
+HPSI_API int hpsi_eigh_lowest_sym(hpsi_ctx* ctx, int n, const void* a, int lda, int nwant, void* w_out, void* v_out);
+
+/*
  * hpsi_set_option -- tune the Davidson solver of a context (App. A.2.1, the diagonal form of D).
  *   HPSI_OPT_PRECOND_TAU    value > 0 (Ha): denominators <k+G|H|k+G> - eps of D are kept at
  *                           |.| >= value (default 0.1).
@@ -329,7 +451,8 @@ HPSI_API int hpsi_set_option(hpsi_ctx* ctx, int option, double value);
 /*
  * hpsi_kernel_stats -- launches of the library's own kernels on ctx since the last reset, and
  * (with HPSI_OPT_KERNEL_TIMING on) their summed device time in ms from the bracketing events.
- *   kernel       in   an hpsi_kernel value, -1 for all classes together (total_ms then 0),
+ *   kernel       in   an hpsi_kernel value (plus HPSI_K_AT_FP64 for its float64-precision launches
+ *                     only), -1 for all classes together (total_ms then 0),
  *                     -2 for the number of H|psi> band-applications performed (in launches), or
  *                     -3 for the reduced eigenproblems solved by the library's own eigensolver
  *                     (in launches) and how many of them it handed to cuSOLVER (in total_ms), or

@@ -22,12 +22,14 @@ HPSI_OPT_LOCAL_PATH, HPSI_OPT_TC_KSPLIT, HPSI_OPT_FINAL_FP64, HPSI_OPT_BASIS, HP
 HPSI_OPT_EIGENSOLVER, HPSI_OPT_FP32_GEMM = 10, 11
 HPSI_OPT_LOCKING, HPSI_OPT_LOCK_BATCH, HPSI_OPT_LOCK_BASIS, HPSI_OPT_THICK_RESTART = 12, 13, 14, 15
 HPSI_OPT_RITZ_SPLIT, HPSI_OPT_REORTH_TEST, HPSI_OPT_CG_TMIN = 16, 17, 18
-KERNELS = ("inv_zy", "xvx_y", "fwd_z", "calbec", "dscale", "addvus", "split", "davidson", "eigh", "tridiag")
+HPSI_OPT_SCF_NMIX, HPSI_OPT_SCF_BETA, HPSI_OPT_SCF_DAVIDSON_TOL = 19, 20, 21
+KERNELS = ("inv_zy", "xvx_y", "fwd_z", "calbec", "dscale", "addvus", "split", "davidson", "eigh", "tridiag", "gamma", "scf", "fock")
+HPSI_K_AT_FP64 = 16   # added to a class: only its launches made while H was applied in float64
 STATUS_NAMES = {0: "HPSI_OK", -1: "HPSI_EINVAL", -2: "HPSI_ENOMEM", -3: "HPSI_ECUDA", -4: "HPSI_ENOTCONV",
                 -5: "HPSI_ESINGULAR", -6: "HPSI_ETIMEOUT", -7: "HPSI_ENODEV"}
 
 EXPORTS = ("hpsi_gsphere", "hpsi_setup", "hpsi_setup_cells", "hpsi_nprob", "hpsi_npw", "hpsi_nproj", "hpsi_apply",
-           "hpsi_apply_batch", "hpsi_apply_noalloc", "davidson_solve", "cg_solve", "hpsi_eigh_lowest", "hpsi_set_option", "hpsi_kernel_stats", "hpsi_sync", "hpsi_selftest_timeout", "hpsi_last_error",
+           "hpsi_apply_batch", "hpsi_apply_noalloc", "hpsi_apply_gamma", "davidson_solve", "davidson_solve_gamma", "hpsi_scf", "hpsi_fock_apply", "hpsi_eigh_lowest_sym", "cg_solve", "hpsi_eigh_lowest", "hpsi_set_option", "hpsi_kernel_stats", "hpsi_sync", "hpsi_selftest_timeout", "hpsi_last_error",
            "hpsi_destroy")
 
 _lib = None
@@ -59,11 +61,21 @@ def _declare(lib):
     lib.hpsi_apply_noalloc.restype = I
     lib.hpsi_apply_batch.argtypes = [V, I, P(I), P(I), P(V), P(V)]
     lib.hpsi_apply_batch.restype = I
+    lib.hpsi_apply_gamma.argtypes = [V, I, V, V, I]
+    lib.hpsi_apply_gamma.restype = I
     lib.davidson_solve.argtypes = [V, I, I, D, I, V, P(D), P(I), P(D)]
+    lib.davidson_solve_gamma.argtypes = [V, I, I, D, I, V, P(D), P(I), P(D)]
+    lib.davidson_solve_gamma.restype = I
+    lib.hpsi_scf.argtypes = [V, I, I, I, D, I, V, P(D), P(D), P(D), P(I), P(D)]
+    lib.hpsi_scf.restype = I
+    lib.hpsi_fock_apply.argtypes = [V, I, I, V, V, V, I, D, P(D)]
+    lib.hpsi_fock_apply.restype = I
     lib.cg_solve.argtypes = [V, I, I, D, I, V, P(D), P(I), P(D)]
     lib.davidson_solve.restype = I
     lib.hpsi_eigh_lowest.argtypes = [V, I, V, I, I, V, V]
     lib.hpsi_eigh_lowest.restype = I
+    lib.hpsi_eigh_lowest_sym.argtypes = [V, I, V, I, I, V, V]
+    lib.hpsi_eigh_lowest_sym.restype = I
     lib.hpsi_set_option.argtypes = [V, I, D]
     lib.hpsi_set_option.restype = I
     lib.hpsi_kernel_stats.argtypes = [V, I, P(ctypes.c_longlong), P(D), I]
@@ -105,9 +117,14 @@ def _check(lib, ctx, rc: int, what: str):
 
 
 def _ptr(x) -> int:
-    """Address of a torch tensor (device or host) or a numpy array."""
+    """Address of a torch tensor (device or host) or a numpy array; the library reads and writes
+    dense row-major blocks, so anything else is refused."""
     if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("libhpsi needs C-contiguous tensors")
         return x.data_ptr()
+    if not x.flags["C_CONTIGUOUS"]:
+        raise ValueError("libhpsi needs C-contiguous arrays")
     return x.ctypes.data
 
 
@@ -223,6 +240,14 @@ def hpsi_apply_noalloc(ctx: Context, ik: int, psi_in, hpsi_out, nbnd: int | None
     _check(ctx.lib, ctx.handle, rc, "hpsi_apply_noalloc")
 
 
+def hpsi_apply_gamma(ctx: Context, ik: int, psi_in, hpsi_out, nbnd: int | None = None) -> None:
+    """hpsi_apply_gamma(): half-sphere complex128 [nbnd][(npw+1)//2], device or host, as hpsi_apply."""
+    nb = int(psi_in.shape[0]) if nbnd is None else int(nbnd)
+    rc = ctx.lib.hpsi_apply_gamma(ctx.handle, int(ik), ctypes.c_void_p(_ptr(psi_in)), ctypes.c_void_p(_ptr(hpsi_out)),
+                                  nb)
+    _check(ctx.lib, ctx.handle, rc, "hpsi_apply_gamma")
+
+
 def hpsi_apply_batch(ctx: Context, probs, psi_list, hpsi_list) -> None:
     """hpsi_apply_batch(): lists of problem indices and device tensors [nbnd_i][npw_i]."""
     n = len(probs)
@@ -242,6 +267,13 @@ def hpsi_eigh_lowest(ctx: Context, a_colmajor, n: int, lda: int, nwant: int, w_o
     rc = ctx.lib.hpsi_eigh_lowest(ctx.handle, int(n), ctypes.c_void_p(_ptr(a_colmajor)), int(lda), int(nwant),
                                   ctypes.c_void_p(_ptr(w_out)), ctypes.c_void_p(_ptr(v_out)))
     _check(ctx.lib, ctx.handle, rc, "hpsi_eigh_lowest")
+
+
+def hpsi_eigh_lowest_sym(ctx: Context, a_colmajor, n: int, lda: int, nwant: int, w_out, v_out) -> None:
+    """hpsi_eigh_lowest_sym(): device float64 tensors, layouts as hpsi_eigh_lowest."""
+    rc = ctx.lib.hpsi_eigh_lowest_sym(ctx.handle, int(n), ctypes.c_void_p(_ptr(a_colmajor)), int(lda), int(nwant),
+                                      ctypes.c_void_p(_ptr(w_out)), ctypes.c_void_p(_ptr(v_out)))
+    _check(ctx.lib, ctx.handle, rc, "hpsi_eigh_lowest_sym")
 
 
 def hpsi_set_option(ctx: Context, option: int, value: float) -> None:
@@ -279,6 +311,47 @@ def davidson_solve(ctx: Context, ik: int, psi_inout, tol: float, maxiter: int, r
     if rc != HPSI_ENOTCONV or raise_on_notconv:
         _check(ctx.lib, ctx.handle, rc, "davidson_solve")
     return eig, it.value, res, rc
+
+
+def davidson_solve_gamma(ctx: Context, ik: int, psi_inout, tol: float, maxiter: int, raise_on_notconv: bool = True):
+    """davidson_solve_gamma(): half-sphere coefficients in and out; returns (eigenvalues, iterations,
+    residual norms, status)."""
+    nbnd = int(psi_inout.shape[0])
+    eig = np.zeros(nbnd)
+    res = np.zeros(nbnd)
+    it = ctypes.c_int(0)
+    rc = ctx.lib.davidson_solve_gamma(ctx.handle, int(ik), nbnd, float(tol), int(maxiter),
+                                      ctypes.c_void_p(_ptr(psi_inout)), _dp(eig), ctypes.byref(it), _dp(res))
+    if rc != HPSI_ENOTCONV or raise_on_notconv:
+        _check(ctx.lib, ctx.handle, rc, "davidson_solve_gamma")
+    return eig, it.value, res, rc
+
+
+def hpsi_scf(ctx: Context, ik: int, nocc: int, psi_inout, rho, tol: float, maxiter: int,
+             raise_on_notconv: bool = True):
+    """hpsi_scf(): rho (float64 [n1][n2][n3], C order) is overwritten by the converged input density;
+    returns (eigenvalues, (E, E_HWF), iterations, scf-norm history, status)."""
+    nbnd = int(psi_inout.shape[0])
+    assert rho.dtype == np.float64 and rho.flags.c_contiguous
+    eig = np.zeros(nbnd)
+    en = np.zeros(2)
+    hist = np.zeros(int(maxiter))
+    it = ctypes.c_int(0)
+    rc = ctx.lib.hpsi_scf(ctx.handle, int(ik), int(nocc), nbnd, float(tol), int(maxiter),
+                          ctypes.c_void_p(_ptr(psi_inout)), _dp(rho), _dp(eig), _dp(en), ctypes.byref(it), _dp(hist))
+    if rc != HPSI_ENOTCONV or raise_on_notconv:
+        _check(ctx.lib, ctx.handle, rc, "hpsi_scf")
+    return eig, (float(en[0]), float(en[1])), it.value, hist[:it.value], rc
+
+
+def hpsi_fock_apply(ctx: Context, ik: int, occ, psi_in, vx_out, alpha: float = 1.0, energy: bool = False):
+    """hpsi_fock_apply(): device tensors; returns E_x = Re sum_b <psi_b|V_x psi_b> when energy is set."""
+    ex = ctypes.c_double(0.0)
+    rc = ctx.lib.hpsi_fock_apply(ctx.handle, int(ik), int(occ.shape[0]), ctypes.c_void_p(_ptr(occ)),
+                                 ctypes.c_void_p(_ptr(psi_in)), ctypes.c_void_p(_ptr(vx_out)), int(psi_in.shape[0]),
+                                 float(alpha), ctypes.byref(ex) if energy else None)
+    _check(ctx.lib, ctx.handle, rc, "hpsi_fock_apply")
+    return ex.value if energy else None
 
 
 def cg_solve(ctx: Context, ik: int, psi_inout, tol: float, maxiter: int, raise_on_notconv: bool = True):

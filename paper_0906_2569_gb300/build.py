@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhpsi.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
-SOURCES = ["api.cu", "local_kernels.cu", "local_fast.cu", "nonlocal_fp64.cu", "nonlocal_tc.cu", "davidson.cu", "cg.cu", "eigh.cu", "subspace_gemm.cu", "noalloc.cu", "plan.cpp"]
+SOURCES = ["api.cu", "local_kernels.cu", "local_fast.cu", "nonlocal_fp64.cu", "nonlocal_tc.cu", "davidson.cu", "cg.cu", "eigh.cu", "subspace_gemm.cu", "noalloc.cu", "gamma.cu", "scf.cu", "fock.cu", "plan.cpp"]
 
 
 def nvcc() -> str:

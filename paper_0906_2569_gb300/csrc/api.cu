@@ -37,10 +37,12 @@ static cudaEvent_t pooled_event(Context& c) {
 
 int launch_begin(Context& c, int kernel) {
   c.launches[kernel]++;
+  const bool at64 = cur_prec(c) == HPSI_FP64;
+  if (at64) c.launches64[kernel]++;
   if (!c.timing) return -1;
   cudaEvent_t a = pooled_event(c), b = pooled_event(c);
   cudaEventRecord(a, c.stream);
-  c.trec.push_back({kernel, {a, b}});
+  c.trec.push_back({kernel + (at64 ? HPSI_K_AT_FP64 : 0), {a, b}});
   return (int)c.trec.size() - 1;
 }
 
@@ -54,7 +56,11 @@ static int collect_timing(Context& c) {
   if (e != cudaSuccess) return cuda_fail(c, e, "kernel timing");
   for (auto& r : c.trec) {
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, r.second.first, r.second.second) == cudaSuccess) c.tacc[r.first] += ms;
+    if (cudaEventElapsedTime(&ms, r.second.first, r.second.second) == cudaSuccess) {
+      const int k = r.first % HPSI_K_AT_FP64;
+      c.tacc[k] += ms;
+      if (r.first >= HPSI_K_AT_FP64) c.tacc64[k] += ms;
+    }
     c.evpool.push_back(r.second.first);
     c.evpool.push_back(r.second.second);
   }
@@ -213,6 +219,100 @@ static int plan_for(Context& c, int n, FftPlan* out) {
   return HPSI_OK;
 }
 
+// Whether the Gamma-point real form (Sec. 4) applies to a problem: k = 0, entry npw-1-i of the
+// sphere's order is -G of entry i, and H maps real functions to real ones.  V is real, so that
+// comes down to the projectors: beta_p(-G) = u_p conj(beta_p(G)) for every G with one |u_p| = 1
+// per projector, and conj(u_p) u_q conj(D_pq) = D_pq for the nonzeros of D (then the nonlocal
+// kernel K(G, G') satisfies conj(K(-G, -G')) = K(G, G')).  Checked to 1e-12 relative.
+static bool gamma_applies(const Problem& p, const double* beta, const double* dmat, std::string* why) {
+  if (p.k[0] != 0.0 || p.k[1] != 0.0 || p.k[2] != 0.0) {
+    *why = "the problem is not at k = 0";
+    return false;
+  }
+  const int n = p.npw;
+  for (int i = 0; i < n; ++i)
+    for (int a = 0; a < 3; ++a)
+      if (p.miller[(size_t)(n - 1 - i) * 3 + a] != -p.miller[(size_t)i * 3 + a]) {
+        *why = "the sphere is not symmetric under G -> -G";
+        return false;
+      }
+  const int P = p.nproj;
+  if (P == 0) return true;
+  const double2* B = reinterpret_cast<const double2*>(beta);
+  const double2* D = reinterpret_cast<const double2*>(dmat);
+  std::vector<double2> u(P);
+  for (int q = 0; q < P; ++q) {
+    const double2* b = B + (size_t)q * n;
+    int imax = 0;
+    double amax = 0.0;
+    for (int i = 0; i < n; ++i) {
+      const double a = std::hypot(b[i].x, b[i].y);
+      if (a > amax) {
+        amax = a;
+        imax = i;
+      }
+    }
+    if (amax == 0.0) {
+      u[q] = make_double2(1.0, 0.0);
+      continue;
+    }
+    // u = beta(-G) / conj(beta(G)) at the largest component
+    const double2 bp = b[imax], bm = b[n - 1 - imax];
+    const double den = bp.x * bp.x + bp.y * bp.y;
+    u[q] = make_double2((bm.x * bp.x - bm.y * bp.y) / den, (bm.x * bp.y + bm.y * bp.x) / den);
+    const double tol = 1e-12 * amax;
+    for (int i = 0; i < n; ++i) {
+      const double2 x = b[i], y = b[n - 1 - i];
+      const double rx = u[q].x * x.x + u[q].y * x.y, ry = u[q].y * x.x - u[q].x * x.y;   // u conj(x)
+      if (std::fabs(y.x - rx) > tol || std::fabs(y.y - ry) > tol) {
+        *why = "projector " + std::to_string(q) + " has no beta(-G) = u conj(beta(G)) symmetry";
+        return false;
+      }
+    }
+  }
+  double dmax = 0.0;
+  for (size_t i = 0; i < (size_t)P * P; ++i) dmax = std::max(dmax, std::hypot(D[i].x, D[i].y));
+  for (int a = 0; a < P; ++a)
+    for (int b = 0; b < P; ++b) {
+      const double2 d = D[(size_t)a * P + b];
+      if (d.x == 0.0 && d.y == 0.0) continue;
+      // conj(u_a) u_b conj(d)
+      const double2 w = make_double2(u[a].x * u[b].x + u[a].y * u[b].y, u[a].x * u[b].y - u[a].y * u[b].x);
+      const double rx = w.x * d.x + w.y * d.y, ry = w.y * d.x - w.x * d.y;
+      if (std::fabs(rx - d.x) > 1e-12 * dmax || std::fabs(ry - d.y) > 1e-12 * dmax) {
+        *why = "D couples projectors whose phases make the nonlocal term complex";
+        return false;
+      }
+    }
+  return true;
+}
+
+__global__ void k_v_to_f32(size_t n, const double* __restrict__ v, float* __restrict__ v32) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    v32[i] = (float)v[i];
+}
+
+// Replace the local potential of problem ik (and of every problem sharing its V) by v64, a device
+// float64 array [n3][n2][n1] with mean vmean; the diagonal <k+G|H|k+G> follows.
+int set_potential(Context& c, int ik, const double* v64, double vmean) {
+  Problem& p0 = c.probs[ik];
+  const size_t nr = (size_t)p0.n[0] * p0.n[1] * p0.n[2];
+  double* d64 = static_cast<double*>(c.vbufs[p0.vslot]);
+  float* d32 = static_cast<float*>(c.vbufs[p0.vslot + 1]);
+  cudaError_t e = cudaMemcpyAsync(d64, v64, sizeof(double) * nr, cudaMemcpyDeviceToDevice, c.stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "potential update");
+  HPSI_LAUNCH(c, HPSI_K_SCF, (k_v_to_f32<<<(int)std::min<size_t>(4096, (nr + 255) / 256), 256, 0, c.stream>>>(nr, d64, d32)));
+  for (Problem& p : c.probs) {
+    if (p.vslot != p0.vslot) continue;
+    HPSI_LAUNCH(c, HPSI_K_SCF,
+                (k_hdiag<<<(p.npw + 255) / 256, 256, 0, c.stream>>>(p.npw, vmean, p.d_kin, p.d_beta, p.nproj,
+                                                                    p.d_rowptr, p.d_col, p.d_dval, p.d_hdiag)));
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "potential update kernels");
+  return HPSI_OK;
+}
+
 // Everything of one problem after its sphere is known: geometry, plans, device copies, D, hdiag.
 static int finish_problem(Context& c, Problem& p, const double* vr, int vslot_shared, double vmean,
                           const double* beta, const double* dmat) {
@@ -246,7 +346,13 @@ static int finish_problem(Context& c, Problem& p, const double* vr, int vslot_sh
   }
   if ((rc = upload(c, &p.d_planes, p.planes.data(), p.planes.size()))) return rc;
   if ((rc = upload(c, &p.d_kin, p.kin.data(), p.kin.size()))) return rc;
-  (void)vr;
+  // the external (local pseudo)potential as given, in the device layout [n3][n2][n1], for the
+  // self-consistency loop, which adds V_Hxc to it
+  p.vext.resize((size_t)p.n[0] * p.n[1] * p.n[2]);
+  for (int j1 = 0; j1 < p.n[0]; ++j1)
+    for (int j2 = 0; j2 < p.n[1]; ++j2)
+      for (int j3 = 0; j3 < p.n[2]; ++j3)
+        p.vext[((size_t)j3 * p.n[1] + j2) * p.n[0] + j1] = vr[((size_t)j1 * p.n[1] + j2) * p.n[2] + j3];
   p.vslot = vslot_shared;
   p.d_v64 = reinterpret_cast<const double*>(c.vbufs[vslot_shared]);
   p.d_v32 = reinterpret_cast<const float*>(c.vbufs[vslot_shared + 1]);
@@ -284,6 +390,7 @@ static int finish_problem(Context& c, Problem& p, const double* vr, int vslot_sh
   } else {
     if ((rc = upload(c, &p.d_rowptr, rowptr.data(), rowptr.size()))) return rc;
   }
+  p.gamma_ok = gamma_applies(p, beta, dmat, &p.gamma_why);
   cudaError_t e = cudaMalloc((void**)&p.d_hdiag, sizeof(double) * std::max(1, p.npw));
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -347,11 +454,16 @@ static void free_context(Context& c) {
   cudaFree(c.ws.stage_out);
   cudaFree(c.ws.mixed);
   cudaFree(c.ws.batch);
+  cudaFree(c.ws.gin);
+  cudaFree(c.ws.gout);
   if (c.graph.exec) cudaGraphExecDestroy(c.graph.exec);
   if (c.cap_stream) cudaStreamDestroy(c.cap_stream);
   davidson_release(c);
   eigh_release(c);
   cg_release(c);
+  gamma_release(c);
+  scf_release(c);
+  fock_release(c);
 }
 
 int nonlocal_apply(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd) {
@@ -427,7 +539,7 @@ int batch_apply(Context& c, int nitem, const int* prob, const int* nbnd, const d
 }
 
 // 1 = device (or managed), 0 = host, -1 = error
-static int pointer_kind(const void* ptr) {
+int pointer_kind(const void* ptr) {
   cudaPointerAttributes at;
   cudaError_t e = cudaPointerGetAttributes(&at, ptr);
   if (e != cudaSuccess) {
@@ -687,7 +799,10 @@ extern "C" int hpsi_apply_batch(hpsi_ctx* ctx, int nitem, const int* prob, const
   if (g.exec && g.key == key && g.epoch == c.ws.epoch) {
     cudaError_t e = cudaGraphLaunch(g.exec, c.stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "hpsi_apply_batch graph launch");
-    for (int k = 0; k < HPSI_K_COUNT; ++k) c.launches[k] += g.launches[k];
+    for (int k = 0; k < HPSI_K_COUNT; ++k) {
+      c.launches[k] += g.launches[k];
+      if (cur_prec(c) == HPSI_FP64) c.launches64[k] += g.launches[k];
+    }
     c.band_apps += g.band_apps;
     return HPSI_OK;
   }
@@ -705,8 +820,11 @@ extern "C" int hpsi_apply_batch(hpsi_ctx* ctx, int nitem, const int* prob, const
     cudaGetLastError();
     return HPSI_OK;   // no capture stream: this call ran eagerly, later calls will too
   }
-  long long after[HPSI_K_COUNT];
-  for (int k = 0; k < HPSI_K_COUNT; ++k) after[k] = c.launches[k];
+  long long after[HPSI_K_COUNT], after64[HPSI_K_COUNT];
+  for (int k = 0; k < HPSI_K_COUNT; ++k) {
+    after[k] = c.launches[k];
+    after64[k] = c.launches64[k];
+  }
   const long long bapps1 = c.band_apps;
   const long long epoch = c.ws.epoch;
   cudaStream_t orig = c.stream;
@@ -719,7 +837,10 @@ extern "C" int hpsi_apply_batch(hpsi_ctx* ctx, int nitem, const int* prob, const
   cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(c.cap_stream, &graph) : e;
   c.stream = orig;
   c.timing = timing;
-  for (int k = 0; k < HPSI_K_COUNT; ++k) c.launches[k] = after[k];
+  for (int k = 0; k < HPSI_K_COUNT; ++k) {
+    c.launches[k] = after[k];
+    c.launches64[k] = after64[k];
+  }
   c.band_apps = bapps1;
   if (rc2 == HPSI_OK && e2 == cudaSuccess && graph && c.ws.epoch == epoch) {
     cudaGraphExec_t exec = nullptr;
@@ -851,6 +972,22 @@ extern "C" int hpsi_set_option(hpsi_ctx* ctx, int option, double value) {
     c.cg_tmin = value;
     return HPSI_OK;
   }
+  if (option == HPSI_OPT_SCF_NMIX) {
+    if (!(value >= 1.0 && value <= 16.0) || value != std::floor(value))
+      return fail(c, HPSI_EINVAL, "HPSI_OPT_SCF_NMIX must be an integer in [1, 16]");
+    c.scf_nmix = (int)value;
+    return HPSI_OK;
+  }
+  if (option == HPSI_OPT_SCF_BETA) {
+    if (!(value > 0.0 && value <= 1.0)) return fail(c, HPSI_EINVAL, "HPSI_OPT_SCF_BETA must be in (0, 1]");
+    c.scf_beta = value;
+    return HPSI_OK;
+  }
+  if (option == HPSI_OPT_SCF_DAVIDSON_TOL) {
+    if (!(value > 0.0) || !std::isfinite(value)) return fail(c, HPSI_EINVAL, "HPSI_OPT_SCF_DAVIDSON_TOL must be > 0");
+    c.scf_dav_tol = value;
+    return HPSI_OK;
+  }
   if (option == HPSI_OPT_REORTH_TEST) {
     if (value != 0.0 && value != 1.0) return fail(c, HPSI_EINVAL, "HPSI_OPT_REORTH_TEST must be 0 or 1");
     c.reorth_test = (int)value;
@@ -903,7 +1040,10 @@ extern "C" int hpsi_set_option(hpsi_ctx* ctx, int option, double value) {
 extern "C" int hpsi_kernel_stats(hpsi_ctx* ctx, int kernel, long long* launches, double* total_ms, int reset) {
   if (!ctx) return HPSI_EINVAL;
   Context& c = ctx->c;
-  if (kernel < -4 || kernel >= HPSI_K_COUNT) return fail(c, HPSI_EINVAL, "hpsi_kernel_stats: bad kernel class");
+  const bool only64 = kernel >= HPSI_K_AT_FP64;
+  if (only64) kernel -= HPSI_K_AT_FP64;
+  if (kernel < -4 || kernel >= HPSI_K_COUNT || (only64 && kernel < 0))
+    return fail(c, HPSI_EINVAL, "hpsi_kernel_stats: bad kernel class");
   if (kernel == -4) {
     if (launches) *launches = c.tri_calls;
     if (total_ms) *total_ms = c.tri_flops;
@@ -931,16 +1071,16 @@ extern "C" int hpsi_kernel_stats(hpsi_ctx* ctx, int kernel, long long* launches,
   double ms = 0.0;
   for (int k = 0; k < HPSI_K_COUNT; ++k)
     if (kernel == -1 || kernel == k) {
-      n += c.launches[k];
-      if (kernel != -1) ms += c.tacc[k];
+      n += only64 ? c.launches64[k] : c.launches[k];
+      if (kernel != -1) ms += only64 ? c.tacc64[k] : c.tacc[k];
     }
   if (launches) *launches = n;
   if (total_ms) *total_ms = ms;
   if (reset)
     for (int k = 0; k < HPSI_K_COUNT; ++k)
       if (kernel == -1 || kernel == k) {
-        c.launches[k] = 0;
-        c.tacc[k] = 0.0;
+        c.launches[k] = c.launches64[k] = 0;
+        c.tacc[k] = c.tacc64[k] = 0.0;
       }
   return HPSI_OK;
 }

@@ -37,6 +37,7 @@
 
 #include "hpsi_internal.h"
 #include "eigh_tridiag.cuh"
+#include "eigh_tridiag_real.cuh"
 
 namespace hpsi {
 
@@ -377,6 +378,61 @@ __global__ void __launch_bounds__(128) k_eh_tfactor(const double2* __restrict__ 
 
 constexpr size_t kTrsvSmem = sizeof(double2) * (size_t)kWY * (kWY - 1) / 2;
 
+// Real forms of the two back-transformation helpers (the reduction of a real symmetric matrix):
+// v_j[c] = u_j[c] scale_j for c > j + 1 and v_j[j + 1] = 1.
+__global__ void k_eh_vscale_r(int n, const double* __restrict__ vscale, double* __restrict__ vref) {
+  const int j = blockIdx.y;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n - 1 || c <= j || c >= n) return;
+  double* v = vref + (size_t)j * n + c;
+  *v = c == j + 1 ? 1.0 : *v * vscale[j];
+}
+
+// T of a real compact-WY block from G = V^T V and tau, as k_eh_tfactor does for complex blocks.
+__global__ void __launch_bounds__(128) k_eh_tfactor_r(const double* __restrict__ Gall, const double* __restrict__ tauall,
+                                                      double* __restrict__ Tall) {
+  extern __shared__ double gsr[];   // strictly upper part of G, column q at q (q - 1) / 2
+  const size_t blk = (size_t)blockIdx.y * kWY * kWY;
+  const double* G = Gall + blk;
+  const double* tau = tauall + (size_t)blockIdx.y * kWY;
+  for (int idx = threadIdx.x; idx < kWY * (kWY - 1) / 2; idx += blockDim.x) {
+    int q = (int)(0.5f * (1.0f + sqrtf(1.0f + 8.0f * (float)idx)));
+    while (q * (q - 1) / 2 > idx) --q;
+    while ((q + 1) * q / 2 <= idx) ++q;
+    gsr[idx] = G[(idx - q * (q - 1) / 2) + (size_t)q * kWY];
+  }
+  __syncthreads();
+  const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (col >= kWY) return;
+  double acc[kWYRows];
+#pragma unroll
+  for (int sl = 0; sl < kWYRows; ++sl) acc[sl] = lane + 32 * sl == col ? 1.0 : 0.0;
+  for (int q = kWY - 1; q >= 0; --q) {
+    const int own = q & 31, oslot = q >> 5;
+    double yq = 0.0;
+    if (lane == own) {
+#pragma unroll
+      for (int sl = 0; sl < kWYRows; ++sl)
+        if (sl == oslot) {
+          yq = tau[q] * acc[sl];
+          acc[sl] = yq;
+        }
+    }
+    yq = __shfl_sync(0xffffffffu, yq, own);
+    const double* gq = gsr + q * (q - 1) / 2;
+#pragma unroll
+    for (int sl = 0; sl < kWYRows; ++sl) {
+      if (32 * sl < q) {
+        const int r = lane + 32 * sl;
+        if (r < q) acc[sl] = fma(-gq[r], yq, acc[sl]);
+      }
+    }
+  }
+  double* t = Tall + blk + (size_t)col * kWY;
+#pragma unroll
+  for (int sl = 0; sl < kWYRows; ++sl) t[lane + 32 * sl] = acc[sl];
+}
+
 struct EighState {
   cublasHandle_t blas = nullptr;
   cusolverDnHandle_t solver = nullptr;
@@ -531,6 +587,11 @@ size_t tri_smem(int n, int G) {
   return sizeof(double2) * ((size_t)(3 + R) * n + 8 * (size_t)R);
 }
 
+size_t tri_smem_r(int n, int G) {
+  const int R = (n + G - 1) / G;
+  return sizeof(double) * ((size_t)(3 + R) * n + 8 * (size_t)R);
+}
+
 }  // namespace
 
 bool eigh_supported(const Context& c, int n) {
@@ -661,6 +722,127 @@ int eigh_lowest(Context& c, const double2* a, int lda, int n, int nwant, double*
   return HPSI_OK;
 }
 
+bool eigh_supported_real(const Context& c, int n) {
+  if (n < 1 || n > kMaxNR) return false;
+  return tri_smem_r(n, tri_ctas(c, n)) <= c.smem_optin;
+}
+
+// The same four steps for a real symmetric matrix (float64, column-major, upper triangle read):
+// real Householder reduction, multisection and inverse iteration on T, real compact-WY
+// back-transformation by DGEMMs.  Eigenvectors go to v_out [nwant][n] (column-major, ld n).
+int eigh_lowest_real(Context& c, const double* a, int lda, int n, int nwant, double* w_out, double* v_out,
+                     bool* fallback) {
+  *fallback = false;
+  if (n < 1 || nwant < 1 || nwant > n || lda < n) return fail(c, HPSI_EINVAL, "eigh_lowest_real: bad sizes");
+  if (!eigh_supported_real(c, n)) {
+    *fallback = true;
+    return HPSI_OK;
+  }
+  EighState* s = nullptr;
+  int rc = ensure_state(c, &s);
+  if (rc) return rc;
+  rc = grow(c, *s, n, nwant);
+  if (rc) return rc;
+  cudaError_t err;
+  // the complex work buffers are reused as real ones (each holds at least twice the doubles needed)
+  double* tau = reinterpret_cast<double*>(s->tau);
+  double* vref = reinterpret_cast<double*>(s->vref);
+  double* vscale = reinterpret_cast<double*>(s->vscale);
+  double* wgram = reinterpret_cast<double*>(s->wgram);
+  double* tfac = reinterpret_cast<double*>(s->tfac);
+  double* w1 = reinterpret_cast<double*>(s->w1);
+  double* w2 = reinterpret_cast<double*>(s->w2);
+
+  // 1. tridiagonal reduction (cooperative)
+  const int G = tri_ctas(c, n);
+  const size_t smem = tri_smem_r(n, G);
+  err = cudaFuncSetAttribute(k_eh_tridiag_r, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return cuda_fail(c, err, "eigh_lowest_real: smem attribute");
+  err = cudaMemsetAsync(s->bar, 0, sizeof(unsigned int) * 64, c.stream);
+  if (err == cudaSuccess) err = cudaMemsetAsync(vref, 0, sizeof(double) * (size_t)(n + kWY) * n, c.stream);
+  if (err == cudaSuccess) err = cudaMemsetAsync(tau, 0, sizeof(double) * (n + kWY), c.stream);
+  if (err == cudaSuccess) err = cudaMemsetAsync(s->sacc, 0, sizeof(double) * 4, c.stream);
+  if (err == cudaSuccess) err = cudaMemsetAsync(s->info, 0, sizeof(int) * 2, c.stream);
+  if (err != cudaSuccess) return cuda_fail(c, err, "eigh_lowest_real: workspace reset");
+  TriArgsR ta{n,     lda,
+              G,     a,
+              s->d,  s->e,
+              s->e2, tau,
+              vref,  reinterpret_cast<double*>(s->ybuf),
+              reinterpret_cast<double*>(s->rnext), reinterpret_cast<double*>(s->rowcoef),
+              vscale, s->sacc,
+              s->bar, c.d_err};
+  void* args[] = {&ta};
+  HPSI_LAUNCH(c, HPSI_K_TRIDIAG,
+              (err = cudaLaunchCooperativeKernel((const void*)k_eh_tridiag_r, dim3(G), dim3(kTriThreads), args, smem,
+                                                 c.stream)));
+  ++c.tri_calls;
+  c.tri_flops += 4.0 / 3.0 * (double)n * (double)n * (double)n;
+  if (err == cudaErrorCooperativeLaunchTooLarge) {
+    cudaGetLastError();
+    *fallback = true;
+    return HPSI_OK;
+  }
+  if (err != cudaSuccess) return cuda_fail(c, err, "eigh_lowest_real: tridiagonal reduction launch");
+  // 2. eigenvalues, 3. eigenvectors of T (the same kernels as the complex solver)
+  HPSI_LAUNCH(c, HPSI_K_EIGH,
+              (k_eh_bisect<<<nwant, 32 * kBisWarps, 0, c.stream>>>(n, s->d, s->e, s->e2, nwant, s->lam)));
+  const size_t ismem = sizeof(double) * 7 * (size_t)n + (size_t)n + 16;
+  if (ismem > 48 * 1024) {
+    err = cudaFuncSetAttribute(k_eh_invit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ismem);
+    if (err != cudaSuccess) return cuda_fail(c, err, "eigh_lowest_real: smem attribute");
+  }
+  HPSI_LAUNCH(c, HPSI_K_EIGH,
+              (k_eh_invit<<<nwant, 32, ismem, c.stream>>>(n, s->d, s->e, nwant, s->lam, s->Z, s->info + 1)));
+  const double one = 1.0, zero = 0.0, mone = -1.0, mhalf = -0.5, three_half = 1.5;
+  if (cublasDgemm(s->blas, CUBLAS_OP_T, CUBLAS_OP_N, nwant, nwant, n, &one, s->Z, n, s->Z, n, &zero, s->gram, nwant) !=
+      CUBLAS_STATUS_SUCCESS)
+    return fail(c, HPSI_ECUDA, "eigh_lowest_real: Gram matrix of the eigenvectors failed");
+  HPSI_LAUNCH(c, HPSI_K_EIGH,
+              (k_eh_orthcheck<<<(nwant * nwant + 255) / 256, 256, 0, c.stream>>>(nwant, s->gram, 1e-4, s->info)));
+  // Newton-Schulz step straight into the output: v_out = Z (3 I - Z^T Z) / 2
+  if (cudaMemcpyAsync(v_out, s->Z, sizeof(double) * (size_t)n * nwant, cudaMemcpyDeviceToDevice, c.stream) !=
+          cudaSuccess ||
+      cublasDgemm(s->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, nwant, nwant, &mhalf, s->Z, n, s->gram, nwant, &three_half,
+                  v_out, n) != CUBLAS_STATUS_SUCCESS)
+    return fail(c, HPSI_ECUDA, "eigh_lowest_real: Newton-Schulz step failed");
+  // 4. back-transformation, one compact-WY block of kWY reflectors at a time from the last
+  if (n > 1) {
+    HPSI_LAUNCH(c, HPSI_K_EIGH, (k_eh_vscale_r<<<dim3((n + 255) / 256, n - 1), 256, 0, c.stream>>>(n, vscale, vref)));
+    const int K = (n - 1 + kWY - 1) / kWY;
+    if (cublasDgemmStridedBatched(s->blas, CUBLAS_OP_T, CUBLAS_OP_N, kWY, kWY, n - 1, &one, vref + 1, n,
+                                  (long long)kWY * n, vref + 1, n, (long long)kWY * n, &zero, wgram, kWY,
+                                  (long long)kWY * kWY, K) != CUBLAS_STATUS_SUCCESS)
+      return fail(c, HPSI_ECUDA, "eigh_lowest_real: reflector Gram matrices failed");
+    const size_t tsm = sizeof(double) * (size_t)kWY * (kWY - 1) / 2;
+    HPSI_LAUNCH(c, HPSI_K_EIGH, (k_eh_tfactor_r<<<dim3(kWY / 4, K), 128, tsm, c.stream>>>(wgram, tau, tfac)));
+    for (int k = K - 1; k >= 0; --k) {
+      const int r0 = k * kWY + 1, m = n - r0;
+      double* V = vref + (size_t)k * kWY * n + r0;
+      if (cublasDgemm(s->blas, CUBLAS_OP_T, CUBLAS_OP_N, kWY, nwant, m, &one, V, n, v_out + r0, n, &zero, w1, kWY) !=
+              CUBLAS_STATUS_SUCCESS ||
+          cublasDgemm(s->blas, CUBLAS_OP_N, CUBLAS_OP_N, kWY, nwant, kWY, &one, tfac + (size_t)k * kWY * kWY, kWY, w1,
+                      kWY, &zero, w2, kWY) != CUBLAS_STATUS_SUCCESS ||
+          cublasDgemm(s->blas, CUBLAS_OP_N, CUBLAS_OP_N, m, nwant, kWY, &mone, V, n, w2, kWY, &one, v_out + r0, n) !=
+              CUBLAS_STATUS_SUCCESS)
+        return fail(c, HPSI_ECUDA, "eigh_lowest_real: back-transformation GEMM failed");
+    }
+  }
+  err = cudaMemcpyAsync(w_out, s->lam, sizeof(double) * nwant, cudaMemcpyDeviceToDevice, c.stream);
+  if (err != cudaSuccess) return cuda_fail(c, err, "eigh_lowest_real: eigenvalue copy");
+  int info[2] = {0, 0};
+  err = cudaMemcpyAsync(info, s->info, sizeof(int) * 2, cudaMemcpyDeviceToHost, c.stream);
+  if (err != cudaSuccess) return cuda_fail(c, err, "eigh_lowest_real: status copy");
+  rc = check_device_error(c);
+  if (rc) return rc;
+  ++c.eig_calls;
+  if (info[0] != 0 || info[1] != 0) {
+    *fallback = true;
+    ++c.eig_fallbacks;
+  }
+  return HPSI_OK;
+}
+
 int eigh_reduced(Context& c, const double2* a, int lda, int n, int nwant, double* w_out, double2* v_out) {
   if (c.eigensolver == 1) {
     bool fallback = false;
@@ -682,4 +864,19 @@ extern "C" int hpsi_eigh_lowest(hpsi_ctx* ctx, int n, const void* a, int lda, in
   if (n < 1 || nwant < 1 || nwant > n || lda < n) return hpsi::fail(c, HPSI_EINVAL, "hpsi_eigh_lowest: bad sizes");
   return hpsi::eigh_reduced(c, static_cast<const double2*>(a), lda, n, nwant, static_cast<double*>(w_out),
                             static_cast<double2*>(v_out));
+}
+
+extern "C" int hpsi_eigh_lowest_sym(hpsi_ctx* ctx, int n, const void* a, int lda, int nwant, void* w_out,
+                                    void* v_out) {
+  if (!ctx) return HPSI_EINVAL;
+  hpsi::Context& c = ctx->c;
+  if (!a || !w_out || !v_out) return hpsi::fail(c, HPSI_EINVAL, "hpsi_eigh_lowest_sym: null pointer");
+  if (n < 1 || nwant < 1 || nwant > n || lda < n) return hpsi::fail(c, HPSI_EINVAL, "hpsi_eigh_lowest_sym: bad sizes");
+  if (c.eigensolver == 1) {
+    bool fallback = false;
+    const int rc = hpsi::eigh_lowest_real(c, static_cast<const double*>(a), lda, n, nwant, static_cast<double*>(w_out),
+                                          static_cast<double*>(v_out), &fallback);
+    if (rc || !fallback) return rc;
+  }
+  return hpsi::fail(c, HPSI_EINVAL, "hpsi_eigh_lowest_sym: n too large for the library's real eigensolver");
 }

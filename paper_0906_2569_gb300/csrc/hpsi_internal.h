@@ -77,6 +77,9 @@ struct Problem {
   int* d_xmap = nullptr;           // [n1]: plane of ix or -1
   const double2* d_ftw64 = nullptr;   // e^{-2 pi i j / n}, j < n (owned by the twiddle table)
   const float2* d_ftw32 = nullptr;
+  std::vector<double> vext;        // the potential given at setup, host, layout [n3][n2][n1]
+  bool gamma_ok = false;           // the Gamma-point real form applies (gamma.cu)
+  std::string gamma_why;           // why not, when it does not
 };
 
 struct TwiddleTable {
@@ -97,6 +100,8 @@ struct Workspace {
   void* stage_out = nullptr; size_t stage_out_bytes = 0;
   void* mixed = nullptr; size_t mixedbytes = 0;  // bf16 operand planes of the mixed path
   void* batch = nullptr; size_t batchbytes = 0;  // stick rows of a batched apply
+  void* gin = nullptr; size_t ginbytes = 0;      // Gamma form: packed pairs of real bands, and H of them
+  void* gout = nullptr; size_t goutbytes = 0;
   long long epoch = 0;                           // bumped whenever a buffer is reallocated
 };
 
@@ -142,6 +147,12 @@ struct Context {
   int ritz_split = 0;                  // mixed Davidson: Ritz / restart GEMMs in K chunks added in float64
   void* eigh = nullptr;                // eigensolver handles and work buffers (eigh.cu)
   void* cg = nullptr;                  // conjugate-gradient solver handles and work buffers (cg.cu)
+  void* gam = nullptr;                 // Gamma-point Davidson handles and work buffers (gamma.cu)
+  void* scf = nullptr;                 // self-consistency loop buffers (scf.cu)
+  void* fock = nullptr;                // exchange-operator buffers (fock.cu)
+  int scf_nmix = 8;                    // SCF: past (input, residual) pairs the mixing combines
+  double scf_beta = 0.5;               // SCF: step along the optimal residual
+  double scf_dav_tol = 1e-9;           // SCF: residual tolerance of each Davidson solve
   double cg_tmin = 1.0;                // CG preconditioner: P^2 = 1 / max(|k+G|^2/2, cg_tmin)
   cudaStream_t cap_stream = nullptr;   // internal stream for graph capture
   GraphCache graph;
@@ -156,6 +167,8 @@ struct Context {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> trec;   // (kernel, start, end)
   std::vector<cudaEvent_t> evpool;
   double tacc[HPSI_K_COUNT] = {0.0};
+  long long launches64[HPSI_K_COUNT] = {0};   // the part of launches made while H was applied in float64
+  double tacc64[HPSI_K_COUNT] = {0.0};
 };
 
 // Precision at which H is applied right now.
@@ -215,12 +228,18 @@ int local_fast_apply(Context& c, const Problem& p, const double2* psi, double2* 
 int local_fast_apply_multi(Context& c, int nitem, const int* prob, const int* nbnd, const double2* const* psi,
                            double2* const* hpsi, void* const* zt, void* const* yb);
 int nonlocal_apply(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd);
+// rho[j3][j2][j1] += sum_b wb[b] |psi_b(r_j)|^2 (float64 bands, wb on the device; local_kernels.cu)
+int local_density(Context& c, const Problem& p, const double2* psi, int nbnd, const double* wb, double* rho);
+// Replace V of problem ik (and of the problems sharing it) by a device float64 [n3][n2][n1] array
+int set_potential(Context& c, int ik, const double* v64, double vmean);
 int batch_apply(Context& c, int nitem, const int* prob, const int* nbnd, const double2* const* psi,
                 double2* const* hpsi);
 int local_apply_into(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd, void* X, void* Y,
                      int nbb);
-void nonlocal_fp64_plan(const Context& c, const Problem& p, int nbnd, int* nsplit, int* kchunk, size_t* bytes);
-int nonlocal_fp64_into(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd, void* scratch);
+void nonlocal_fp64_plan(const Context& c, const Problem& p, int nbnd, int* nsplit, int* kchunk, size_t* bytes,
+                        size_t max_bytes = 0);
+int nonlocal_fp64_into(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd, void* scratch,
+                       size_t capacity);
 
 // ---- context helpers (api.cpp) ----
 int ensure_buffer(Context& c, void** ptr, size_t* have, size_t need);
@@ -228,6 +247,7 @@ int fail(Context& c, int code, const std::string& msg);
 int cuda_fail(Context& c, cudaError_t e, const char* what);
 int apply_device(Context& c, int ik, const double2* psi, double2* hpsi, int nbnd);
 int check_device_error(Context& c);   // synchronizes; HPSI_ETIMEOUT if a bounded wait expired
+int pointer_kind(const void* ptr);    // 1 device (or managed), 0 host, -1 unknown
 
 // ---- Davidson (davidson.cu) ----
 int davidson_run(Context& c, int ik, int nbnd, double tol, int maxiter, double2* psi, double* eig,
@@ -237,6 +257,15 @@ void davidson_release(Context& c);
 int cg_run(Context& c, int ik, int nbnd, double tol, int maxiter, double2* psi, double* eig, int* iters,
            double* resnorm);
 void cg_release(Context& c);
+// Gamma-point real form (gamma.cu): H on half-sphere bands (scaled: real-basis coordinates), block
+// Davidson on real orbitals, and the check that a problem allows the form.
+int gamma_apply(Context& c, int ik, const double2* x, double2* y, int nb, bool scaled);
+int gamma_check(Context& c, int ik, const char* who);
+int gamma_davidson_run(Context& c, int ik, int nbnd, double tol, int maxiter, double2* psio, double* eig_out,
+                       int* iters_out, double* resnorm_out);
+void gamma_release(Context& c);
+void scf_release(Context& c);
+void fock_release(Context& c);
 
 // ---- complex64 subspace products on the bf16 tensor cores (subspace_gemm.cu) ----
 // Three-term bf16 split of a complex64 matrix's columns, kept valid up to `valid` columns.
@@ -273,6 +302,11 @@ int eigh_lowest(Context& c, const double2* a, int lda, int n, int nwant, double*
 // The solver chosen by HPSI_OPT_EIGENSOLVER, with cuSOLVER zheevdx behind the library kernels.
 int eigh_reduced(Context& c, const double2* a, int lda, int n, int nwant, double* w_out, double2* v_out);
 void eigh_release(Context& c);
+// Real symmetric form (the reduced problems of the Gamma-point Davidson): the library's kernels for
+// n up to 1824 on 152 SMs; *fallback as above.  Vectors to v_out [nwant][n] (column-major, ld n).
+bool eigh_supported_real(const Context& c, int n);
+int eigh_lowest_real(Context& c, const double* a, int lda, int n, int nwant, double* w_out, double* v_out,
+                     bool* fallback);
 
 }  // namespace hpsi
 
