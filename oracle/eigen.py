@@ -22,16 +22,24 @@ def lowest_dense(h: np.ndarray, nbnd: int) -> np.ndarray:
 
 
 def lowest_lobpcg(lattice, k, miller, fft, vr, beta, dmat, nbnd: int, x0: np.ndarray,
-                  tol: float = 1e-9, maxiter: int = 400, nguard: int = 8, verbose: bool = False):
+                  tol: float = 1e-9, maxiter: int = 400, nguard: int = 8, verbose: bool = False,
+                  chunk: int = 0):
     """Lowest nbnd eigenvalues by LOBPCG on the FFT H|psi>, with a guard block of extra vectors.
 
+    ``chunk`` > 0 applies H to at most that many vectors at a time (the bands are independent, so
+    this only bounds the memory of the full-box transforms).
     Returns (eigenvalues, residual norms of the returned vectors).
     """
     npw = len(miller)
     hdiag = hamiltonian.h_diagonal(lattice, k, miller, vr, beta, dmat)
 
     def matmat(x):
-        return hamiltonian.hpsi(lattice, k, miller, fft, vr, beta, dmat, np.asarray(x).T).T
+        x = np.asarray(x)
+        step = chunk if chunk > 0 else max(1, x.shape[1])
+        out = np.empty(x.shape, dtype=np.complex128)
+        for j in range(0, x.shape[1], step):
+            out[:, j:j + step] = hamiltonian.hpsi(lattice, k, miller, fft, vr, beta, dmat, x[:, j:j + step].T).T
+        return out
 
     op = sla.LinearOperator((npw, npw), matmat=matmat, matvec=lambda v: matmat(v[:, None])[:, 0],
                             dtype=np.complex128)

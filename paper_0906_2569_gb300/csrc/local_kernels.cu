@@ -158,6 +158,70 @@ __global__ void __launch_bounds__(256) k_fwd_z(LocalArgs a) {
   }
 }
 
+// Density of the orbitals on the grid (App. A.1, rho = sum_i f_i |psi_i(r)|^2): one CTA per j3 takes
+// every band of the block in turn, inverse x-transforms its m1-plane entries (X, from k_inv_zy) and
+// adds wb[b] |psi_b(r)|^2 into rho[j3][j2][j1].  Element (j3, j2, j1) is only ever touched by CTA
+// j3, warp j2 mod 8, lane j1 mod 32, so the bands are summed in order without atomics.
+__global__ void __launch_bounds__(256) k_x_density(LocalArgs a, const double* __restrict__ wb,
+                                                   double* __restrict__ rho) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* P = reinterpret_cast<double2*>(smem_raw);       // [npl][n2]
+  double2* L = P + (size_t)a.npl * a.n2;                   // [8][n1]
+  int* ix = reinterpret_cast<int*>(L + kWarpsPerCta * a.n1);   // [npl]
+  const int j3 = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n1 = a.n1, n2 = a.n2, npl = a.npl;
+  for (int q = threadIdx.x; q < npl; q += blockDim.x) ix[q] = a.planes[q].ix;
+  double2* Lw = L + warp * n1;
+  for (int b = 0; b < a.nb; ++b) {
+    __syncthreads();
+    const double2* X = reinterpret_cast<const double2*>(a.X) + ((size_t)b * a.n3 + j3) * npl * n2;
+    for (int i = threadIdx.x; i < npl * n2; i += blockDim.x) P[i] = X[i];
+    __syncthreads();
+    const double w = wb[b];
+    for (int j2 = warp; j2 < n2; j2 += kWarpsPerCta) {
+      for (int i = lane; i < n1; i += 32) Lw[i] = czero<double2>();
+      __syncwarp();
+      for (int q = lane; q < npl; q += 32) Lw[ix[q]] = P[q * n2 + j2];
+      __syncwarp();
+      warp_fft<+1>(Lw, a.p1, lane);
+      double* row = rho + ((size_t)j3 * n2 + j2) * n1;
+      for (int i = lane; i < n1; i += 32) row[i] += w * (Lw[i].x * Lw[i].x + Lw[i].y * Lw[i].y);
+      __syncwarp();
+    }
+  }
+}
+
+// rho[j3][j2][j1] += sum_b wb[b] |psi_b(r_j)|^2 for nbnd float64 bands (wb on the device).
+int local_density(Context& c, const Problem& p, const double2* psi, int nbnd, const double* wb, double* rho) {
+  if (nbnd == 0) return HPSI_OK;
+  const int nbb = std::max(1, std::min(p.nbb[HPSI_FP64], nbnd));
+  const size_t xneed = sizeof(double2) * (size_t)nbb * p.n[2] * p.npl * p.n[1];
+  int rc = ensure_buffer(c, &c.ws.X, &c.ws.xbytes, xneed);
+  if (rc) return rc;
+  const size_t s0 = local_smem_bytes(p, HPSI_FP64, 0), s1 = local_smem_bytes(p, HPSI_FP64, 1);
+  const int mx = (int)c.smem_optin;
+  cudaFuncSetAttribute(k_inv_zy<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_x_density, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  LocalArgs a;
+  a.n1 = p.n[0]; a.n2 = p.n[1]; a.n3 = p.n[2];
+  a.npw = p.npw; a.npl = p.npl; a.nst = p.nst; a.ns_max = p.ns_max;
+  a.sticks = p.d_sticks; a.planes = p.d_planes; a.kin = p.d_kin;
+  a.X = c.ws.X; a.Y = nullptr; a.V = nullptr; a.hpsi = nullptr;
+  a.p1 = p.plan[0]; a.p2 = p.plan[1]; a.p3 = p.plan[2];
+  a.inv_nr = 1.0 / ((double)p.n[0] * p.n[1] * p.n[2]);
+  for (int b0 = 0; b0 < nbnd; b0 += nbb) {
+    const int nb = std::min(nbb, nbnd - b0);
+    a.nb = nb;
+    a.psi = psi + (size_t)b0 * p.npw;
+    HPSI_LAUNCH(c, HPSI_K_SCF, (k_inv_zy<double><<<dim3(p.npl, nb), 256, s0, c.stream>>>(a)));
+    HPSI_LAUNCH(c, HPSI_K_SCF, (k_x_density<<<p.n[2], 256, s1, c.stream>>>(a, wb + b0, rho)));
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "density kernels launch");
+  return HPSI_OK;
+}
+
 // Shared memory of each kernel (bytes) for a problem at a precision; which = 0, 1, 2.
 size_t local_smem_bytes(const Problem& p, int precision, int which) {
   const size_t cs = precision == HPSI_FP64 ? sizeof(double2) : sizeof(float2);

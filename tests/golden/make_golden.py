@@ -5,7 +5,7 @@ here is the oracle's: the lowest eigenvalues of H (App. A.2, Eq. (diag) with S =
 LAPACK (oracle.eigen.lowest_dense on the element-by-element H_GG') where the matrix fits, else by
 LOBPCG on the FFT form of H|psi> (oracle.eigen.lowest_lobpcg).  Usage:
 
-    python tests/golden/make_golden.py [c1 c3 c4a c2 c4b]
+    python tests/golden/make_golden.py [c1 c3 c4a c2 c4b c5 scf_c1]
 """
 from __future__ import annotations
 
@@ -38,21 +38,27 @@ def dense(p, k, nbnd):
     return oracle.eigen.lowest_dense(h, nbnd).tolist(), {"method": "dense LAPACK eigvalsh", "npw": len(m)}
 
 
-def lobpcg(p, k, nbnd, tol=1e-9):
+def lobpcg(p, k, nbnd, tol=1e-9, chunk=0, verbose=False):
     m, vr, beta, d = inputs(p, k)
     x0 = workloads.psi0(p.lattice, k, m, nbnd + 16, p.psi_seed + 7)
     w, res = oracle.eigen.lowest_lobpcg(p.lattice, k, m, p.fft, vr, beta, d, nbnd, x0, tol=tol, maxiter=600,
-                                        nguard=16)
+                                        nguard=16, chunk=chunk, verbose=verbose)
     return w.tolist(), {"method": "LOBPCG on the FFT H|psi>", "npw": len(m), "max_residual": float(np.max(res))}
 
 
+OUT_SCF = os.path.join(os.path.dirname(os.path.abspath(__file__)), "scf.json")
+
+
 def main(names):
-    data = {}
-    if os.path.exists(OUT):
-        data = json.load(open(OUT))
-    data["_about"] = ("Lowest eigenvalues (Ha) of the seeded synthetic cells of workloads/, from the CPU oracle "
-                      "only (App. A.2 Eq. (diag), S = I); written by tests/golden/make_golden.py.")
     for name in names:
+        out = OUT_SCF if name.startswith("scf") else OUT
+        data = json.load(open(out)) if os.path.exists(out) else {}
+        if out == OUT:
+            data["_about"] = ("Lowest eigenvalues (Ha) of the seeded synthetic cells of workloads/, from the CPU "
+                              "oracle only (App. A.2 Eq. (diag), S = I); written by tests/golden/make_golden.py.")
+        else:
+            data["_about"] = ("Self-consistent solutions (App. A.1) of seeded synthetic cells of workloads/, from the "
+                              "CPU oracle only (oracle.scf.scf); written by tests/golden/make_golden.py.")
         t0 = time.time()
         if name == "c1":
             p = workloads.config1()
@@ -76,11 +82,37 @@ def main(names):
         elif name == "c2":
             p = workloads.config2()
             ev, info = lobpcg(p, p.kpts[0], p.nbnd)
+        elif name == "scf_c1":
+            # the self-consistency loop of App. A.1 on the c1 cell: V_ext = the synthetic local
+            # potential, two electrons per atom (nocc = 2), uniform starting density, dense H
+            p = workloads.config1()
+            k = p.kpts[0]
+            m, vr, beta, d = inputs(p, k)
+            omega = oracle.scf.cell_volume(p.lattice)
+            rho0 = np.full(p.fft, 4.0 / omega)
+            out = oracle.scf.scf(p.lattice, k, m, p.fft, vr, beta, d, 2, rho0, tol=1e-16, maxiter=100)
+            rng = np.random.default_rng(5000)
+            idx = rng.choice(out["rho"].size, 64, replace=False)
+            ev = out["eig"].tolist()
+            info = {"method": "oracle.scf.scf, dense H, Anderson mixing (8, 0.5), tol 1e-16", "npw": len(m),
+                    "nocc": 2, "e": out["e"], "e_hwf": out["e_hwf"], "iters": out["iters"],
+                    "charge": oracle.scf.charge(out["rho"], p.lattice),
+                    "rho_sample_index": idx.tolist(), "rho_sample": out["rho"].reshape(-1)[idx].tolist(),
+                    "rho_max": float(np.max(out["rho"])), "rho_sum2": float(np.sum(out["rho"] ** 2))}
+        elif name.startswith("c5"):
+            # the large cell: the lowest C5_NBND (default 64) of its 512 bands, H applied 16 bands
+            # at a time to bound the memory of the 144^3 transforms
+            nb = int(os.environ.get("C5_NBND", "64"))
+            p = workloads.config5()
+            ev, info = lobpcg(p, p.kpts[0], nb, chunk=16, verbose=True)
+            name = "c5"
         else:
             raise SystemExit(f"unknown config {name}")
         info["seconds"] = round(time.time() - t0, 1)
+        # re-read before writing: another run of this script may have added entries meanwhile
+        data = json.load(open(out)) if os.path.exists(out) else data
         data[name] = {"eigenvalues": ev, **info}
-        json.dump(data, open(OUT, "w"), indent=1)
+        json.dump(data, open(out, "w"), indent=1)
         print(name, info, flush=True)
 
 
