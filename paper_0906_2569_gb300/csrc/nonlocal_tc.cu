@@ -39,6 +39,12 @@ constexpr int TBK = 64;              // bf16 per 128-byte swizzled row
 constexpr int kTileBytes = TBM * TBK * 2;   // 16 KB, A and B tiles alike
 constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
 constexpr int kInnerKsteps = 8;      // subspace inner products: K steps per float32 accumulation
+constexpr int kCalbecKsteps = 16;    // calbec: at most this many K steps per float32 accumulation by default;
+                                     // the error of a float32 accumulation grows with its length, and
+                                     // the partial sums of the splits are added in float64
+constexpr int kAddKsteps = 8;        // add_vuspsi: at most this many K steps (of K = 2P) per float32
+                                     // accumulation; more splits are added in float64 (the measured
+                                     // error of one long accumulation grows in proportion to P)
 
 template <int NT> struct TcCfg {
   static constexpr int stages = NT == 2 ? 3 : 2;
@@ -266,6 +272,24 @@ __global__ void __launch_bounds__(128, 1)
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TBN));
+}
+
+// hpsi[b][g] += sum_s (part[s][b][2g], part[s][b][2g+1]), summed in float64
+__global__ void k_add_partials(int nb, int npw, int nsplit, const float* __restrict__ part, double2* __restrict__ hpsi) {
+  const size_t n = (size_t)nb * npw, plane = 2 * n;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float2* p = reinterpret_cast<const float2*>(part) + i;
+    double sx = 0.0, sy = 0.0;
+    for (int s = 0; s < nsplit; ++s) {
+      const float2 v = p[(size_t)s * (plane / 2)];
+      sx += (double)v.x;
+      sy += (double)v.y;
+    }
+    double2 o = hpsi[i];
+    o.x += sx;
+    o.y += sy;
+    hpsi[i] = o;
+  }
 }
 
 // ---- operand preparation ----------------------------------------------------------------------
@@ -541,12 +565,17 @@ int apply_t(Context& c, const Problem& p, const double2* psi, double2* hpsi, int
   const int tiles = ((2 * nbnd + TBN - 1) / TBN) * ((P + TBM - 1) / TBM);
   int nsplit = std::max(1, std::min(nks, (2 * c.sm_count + tiles - 1) / tiles));
   int ksplit = (nks + nsplit - 1) / nsplit;
-  if (c.tc_kmax > 0) ksplit = std::min(ksplit, c.tc_kmax);
+  ksplit = std::min(ksplit, c.tc_kmax > 0 ? c.tc_kmax : kCalbecKsteps);
   nsplit = (nks + ksplit - 1) / ksplit;
   const size_t psib = sizeof(__nv_bfloat16) * (size_t)NT * 2 * nbnd * kc;
   const size_t partb = sizeof(float) * (size_t)nsplit * P * 2 * nbnd;
   const size_t wab = sizeof(__nv_bfloat16) * (size_t)NT * nbnd * ka;
-  const size_t need = psib + partb + wab + 3 * 256;
+  // add_vuspsi in K-splits of at most kAddKsteps steps when 2P is longer than that
+  const int naks = ka / TBK;
+  const int aksplit = (naks + (naks + kAddKsteps - 1) / kAddKsteps - 1) / ((naks + kAddKsteps - 1) / kAddKsteps);
+  const int ansplit = (naks + aksplit - 1) / aksplit;   // every split has at least one K step
+  const size_t addb = ansplit > 1 ? sizeof(float) * (size_t)ansplit * nbnd * 2 * npw : 0;
+  const size_t need = psib + partb + wab + addb + 4 * 256;
   int rc = ensure_buffer(c, &c.ws.mixed, &c.ws.mixedbytes, need);
   if (rc) return rc;
   unsigned char* w0 = static_cast<unsigned char*>(c.ws.mixed);
@@ -564,8 +593,17 @@ int apply_t(Context& c, const Problem& p, const double2* psi, double2* hpsi, int
   HPSI_LAUNCH(c, HPSI_K_DSCALE,
               (k_dscale_tc<NT><<<(n + 255) / 256, 256, 0, c.stream>>>(P, nbnd, nsplit, ka, part, p.d_rowptr, p.d_col,
                                                                       p.d_dval, wa)));
-  rc = launch_gemm<NT>(c, wa, nbnd, badd, 2 * npw, ka, 1, ka / TBK, 1, nullptr, hpsi, npw, HPSI_K_ADDVUS);
-  if (rc) return rc;
+  if (ansplit > 1) {
+    float* apart = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(wa) + ((wab + 255) & ~size_t(255)));
+    rc = launch_gemm<NT>(c, wa, nbnd, badd, 2 * npw, ka, ansplit, aksplit, 0, apart, nullptr, 0, HPSI_K_ADDVUS);
+    if (rc) return rc;
+    const size_t nel = (size_t)nbnd * npw;
+    HPSI_LAUNCH(c, HPSI_K_ADDVUS, (k_add_partials<<<(int)std::min<size_t>(8 * c.sm_count, (nel + 255) / 256), 256, 0,
+                                                    c.stream>>>(nbnd, npw, ansplit, apart, hpsi)));
+  } else {
+    rc = launch_gemm<NT>(c, wa, nbnd, badd, 2 * npw, ka, 1, naks, 1, nullptr, hpsi, npw, HPSI_K_ADDVUS);
+    if (rc) return rc;
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(c, e, "tensor-core nonlocal kernels launch");
   return HPSI_OK;
