@@ -832,8 +832,16 @@ int gamma_davidson_run(Context& c, int ik, int nbnd, double tol, int maxiter, do
   GBK(cublasSetStream(h->blas, c.stream), "cublasSetStream");
   GBK(cusolverDnSetStream(h->solver, c.stream), "cusolverDnSetStream");
   if (c.precision == HPSI_MIXED) {
+    // HPSI_OPT_FP32_GEMM = 1: the float32 subspace GEMMs emulated by cuBLAS with bf16 tensor-core
+    // products (float32-accurate); the other values of the option do not apply to real GEMMs
+    GBK(cublasSetMathMode(h->blas, c.fp32_gemm == 1 ? CUBLAS_FP32_EMULATED_BF16X9_MATH : CUBLAS_DEFAULT_MATH),
+        "cublasSetMathMode");
+    if (c.fp32_gemm == 1) GBK(cublasSetEmulationStrategy(h->blas, CUBLAS_EMULATION_STRATEGY_EAGER),
+                              "cublasSetEmulationStrategy");
     GammaDavidson<float> d(c, *h, ik);
-    return d.run(nbnd, tol, maxiter, psio, eig_out, iters_out, resnorm_out);
+    const int rc = d.run(nbnd, tol, maxiter, psio, eig_out, iters_out, resnorm_out);
+    cublasSetMathMode(h->blas, CUBLAS_DEFAULT_MATH);
+    return rc;
   }
   GammaDavidson<double> d(c, *h, ik);
   return d.run(nbnd, tol, maxiter, psio, eig_out, iters_out, resnorm_out);
