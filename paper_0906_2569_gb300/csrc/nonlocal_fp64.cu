@@ -16,6 +16,20 @@ namespace hpsi {
 
 namespace {
 
+// acc += conj(x) y and acc += x y, four float64 FMAs each
+__device__ __forceinline__ void cmac_conj(double2& acc, double2 x, double2 y) {
+  acc.x = fma(x.x, y.x, acc.x);
+  acc.x = fma(x.y, y.y, acc.x);
+  acc.y = fma(x.x, y.y, acc.y);
+  acc.y = fma(-x.y, y.x, acc.y);
+}
+__device__ __forceinline__ void cmac(double2& acc, double2 x, double2 y) {
+  acc.x = fma(x.x, y.x, acc.x);
+  acc.x = fma(-x.y, y.y, acc.x);
+  acc.y = fma(x.x, y.y, acc.y);
+  acc.y = fma(x.y, y.x, acc.y);
+}
+
 constexpr int CB_TP = 32;   // projectors per CTA
 constexpr int CB_TB = 32;   // bands per CTA
 constexpr int CB_TK = 32;   // G per shared-memory tile
@@ -46,11 +60,12 @@ __global__ void __launch_bounds__(256) k_calbec64(int npw, int nproj, int nb, in
     for (int kk = 0; kk < CB_TK; ++kk) {
       const double2 x0 = sb[tx][kk], x1 = sb[tx + 16][kk];
       const double2 y0 = sp[ty][kk], y1 = sp[ty + 16][kk];
-      // conj(x) * y
-      acc[0][0].x += x0.x * y0.x + x0.y * y0.y; acc[0][0].y += x0.x * y0.y - x0.y * y0.x;
-      acc[0][1].x += x0.x * y1.x + x0.y * y1.y; acc[0][1].y += x0.x * y1.y - x0.y * y1.x;
-      acc[1][0].x += x1.x * y0.x + x1.y * y0.y; acc[1][0].y += x1.x * y0.y - x1.y * y0.x;
-      acc[1][1].x += x1.x * y1.x + x1.y * y1.y; acc[1][1].y += x1.x * y1.y - x1.y * y1.x;
+      // acc += conj(x) * y as four fused multiply-adds per complex product (written out so that
+      // no separate multiply or add reaches the float64 pipe)
+      cmac_conj(acc[0][0], x0, y0);
+      cmac_conj(acc[0][1], x0, y1);
+      cmac_conj(acc[1][0], x1, y0);
+      cmac_conj(acc[1][1], x1, y1);
     }
     __syncthreads();
   }
@@ -117,11 +132,7 @@ __global__ void __launch_bounds__(256) k_addvus64(int npw, int nproj, int nb, co
     for (int kk = 0; kk < AV_TP; ++kk) {
       const double2 x = sb[kk][tx];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const double2 y = sw[ty + 4 * j][kk];
-        acc[j].x += y.x * x.x - y.y * x.y;
-        acc[j].y += y.x * x.y + y.y * x.x;
-      }
+      for (int j = 0; j < 8; ++j) cmac(acc[j], sw[ty + 4 * j][kk], x);
     }
     __syncthreads();
   }

@@ -409,7 +409,7 @@ int Scf::run(int nocc, int nbnd, double tol, int maxiter, double2* psi, double* 
   HPSI_LAUNCH(c, HPSI_K_SCF, (k_norm_weight<<<grid_for(nr_), 256, 0, c.stream>>>(p_.n[0], p_.n[1], p_.n[2], rc_, omega_,
                                                                                  w.wgt)));
   std::vector<double> eig(nbnd), res(nbnd);
-  int nhist = 0;   // entries in the mixing history (oldest first)
+  int nhist = 0, head = 0;   // entries in the mixing history (oldest first) and the oldest's slot
   const size_t rb = sizeof(double) * nr_;
   for (int it = 0; it < maxiter; ++it) {
     // V[rho_in] into the context, then the lowest bands of H[V]
@@ -449,18 +449,16 @@ int Scf::run(int nocc, int nbnd, double tol, int maxiter, double2* psi, double* 
       for (int i = 0; i < nbnd; ++i) eig_out[i] = eig[i];
       return HPSI_OK;
     }
-    // mixing: append (rho_in, r = rho_out - rho_in, r(G)), keep the last nmix
+    // mixing: append (rho_in, r = rho_out - rho_in, r(G)) to the history, a ring of nmix slots
+    // (entry e, counted from the oldest kept, lives in slot (head + e) mod nmix)
     if (nhist == nmix) {
-      // drop the oldest entry: shift the history down by one slot
-      SCK(cudaMemcpyAsync(w.xin, w.xin + nr_, rb * (nmix - 1), cudaMemcpyDeviceToDevice, c.stream), "history shift");
-      SCK(cudaMemcpyAsync(w.res, w.res + nr_, rb * (nmix - 1), cudaMemcpyDeviceToDevice, c.stream), "history shift");
-      SCK(cudaMemcpyAsync(w.rhat, w.rhat + nr_, 2 * rb * (nmix - 1), cudaMemcpyDeviceToDevice, c.stream),
-          "history shift");
+      head = (head + 1) % nmix;   // the oldest entry's slot is reused
       --nhist;
     }
-    double* xn = w.xin + nhist * nr_;
-    double* rn = w.res + nhist * nr_;
-    double2* hn = w.rhat + nhist * nr_;
+    auto slot = [&](int e) { return (size_t)((head + e) % nmix) * nr_; };
+    double* xn = w.xin + slot(nhist);
+    double* rn = w.res + slot(nhist);
+    double2* hn = w.rhat + slot(nhist);
     SCK(cudaMemcpyAsync(xn, w.rho_in, rb, cudaMemcpyDeviceToDevice, c.stream), "history");
     HPSI_LAUNCH(c, HPSI_K_SCF, (k_sub<<<grid_for(nr_), 256, 0, c.stream>>>(nr_, w.rho_out, w.rho_in, rn)));
     SCK(cudaMemcpyAsync(hn, w.box, 2 * rb, cudaMemcpyDeviceToDevice, c.stream), "history");
@@ -477,7 +475,7 @@ int Scf::run(int nocc, int nbnd, double tol, int maxiter, double2* psi, double* 
       for (int i = 0; i <= k; ++i)
         for (int j = i; j <= k; ++j) {
           double v = 0.0;
-          rc = wdot(w.rhat + (size_t)(base + i) * nr_, w.rhat + (size_t)(base + j) * nr_, &v);
+          rc = wdot(w.rhat + slot(base + i), w.rhat + slot(base + j), &v);
           if (rc) return rc;
           H[(size_t)i * (k + 1) + j] = H[(size_t)j * (k + 1) + i] = v;
         }
@@ -494,10 +492,10 @@ int Scf::run(int nocc, int nbnd, double tol, int maxiter, double2* psi, double* 
     SCK(cudaMemcpyAsync(w.tmp, rn, rb, cudaMemcpyDeviceToDevice, c.stream), "mix");
     const int base = nhist - 1 - k;
     for (int j = 0; j < (int)g.size(); ++j) {
-      const double* x0 = w.xin + (size_t)(base + j) * nr_;
-      const double* x1 = x0 + nr_;
-      const double* r0 = w.res + (size_t)(base + j) * nr_;
-      const double* r1 = r0 + nr_;
+      const double* x0 = w.xin + slot(base + j);
+      const double* x1 = w.xin + slot(base + j + 1);
+      const double* r0 = w.res + slot(base + j);
+      const double* r1 = w.res + slot(base + j + 1);
       HPSI_LAUNCH(c, HPSI_K_SCF, (k_axpby<<<grid_for(nr_), 256, 0, c.stream>>>(nr_, -g[j], x1, 1.0, w.rho_in)));
       HPSI_LAUNCH(c, HPSI_K_SCF, (k_axpby<<<grid_for(nr_), 256, 0, c.stream>>>(nr_, g[j], x0, 1.0, w.rho_in)));
       HPSI_LAUNCH(c, HPSI_K_SCF, (k_axpby<<<grid_for(nr_), 256, 0, c.stream>>>(nr_, -g[j], r1, 1.0, w.tmp)));

@@ -10,6 +10,14 @@ With ``--eigh N`` it instead solves the reduced Hermitian eigenproblem of order 
 ``--nwant`` pairs) on a seeded random matrix of the scale of a Davidson reduced H, the same way:
 two warm-up solves, then ``--reps`` bracketed ones.
 
+With ``--solve`` it runs the block-Davidson solve of the whole band block of the cell named by
+``--config`` at the chosen precision (``--form gamma``: davidson_solve_gamma on the half-sphere
+block, the default for a Gamma-only cell; ``--form complex``: davidson_solve), tolerance ``--tol``
+(default 5e-5 mixed, 1e-8 float64): one warm-up solve, then one bracketed solve -- every launch of
+a solve, the library's and cuBLAS's, falls inside the bracket.
+
+With ``--eigh-real N`` the eigenproblem of order N is real symmetric (hpsi_eigh_lowest_sym).
+
 With ``--cg B`` it runs the band-by-band CG eigensolver on the first B bands of the cell named by
 ``--config`` in float64 (residual 1e-8, at most ``--cg-maxiter`` steps per band): one warm-up solve,
 then one bracketed solve.  Every CG step's launches (three single-CTA kernels, the Gram-Schmidt
@@ -35,12 +43,19 @@ def main():
     ap.add_argument("--nwant", type=int, default=160)
     ap.add_argument("--cg", type=int, default=0)
     ap.add_argument("--cg-maxiter", type=int, default=3000)
+    ap.add_argument("--solve", action="store_true")
+    ap.add_argument("--form", default="auto", choices=["auto", "gamma", "complex"])
+    ap.add_argument("--tol", type=float, default=0.0)
+    ap.add_argument("--eigh-real", type=int, default=0)
     args = ap.parse_args()
     import torch
     import workloads
     from paper_0906_2569_gb300 import binding as B
-    if args.eigh:
+    if args.eigh or args.eigh_real:
         eigh_case(args, torch, workloads, B)
+        return
+    if args.solve:
+        solve_case(args, torch, workloads, B)
         return
     if args.cg:
         cg_case(args, torch, workloads, B)
@@ -72,19 +87,56 @@ def eigh_case(args, torch, workloads, B):
     p = workloads.config1()
     ctx = B.hpsi_setup(p.lattice, p.ecut, [p.kpts[0]], p.fft, np.zeros(p.fft), None, None, B.HPSI_FP64,
                        torch.cuda.current_stream().cuda_stream)
-    n, nw = args.eigh, min(args.nwant, args.eigh)
-    a = torch.from_numpy(np.ascontiguousarray(workloads.hermitian_matrix(n, n, scale=20.0).T)).cuda()
+    real = args.eigh_real > 0
+    n = args.eigh_real if real else args.eigh
+    nw = min(args.nwant, n)
+    if real:
+        rng = np.random.default_rng(n)
+        q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+        a = torch.from_numpy(np.ascontiguousarray(((q * rng.uniform(-20.0, 20.0, n)[None, :]) @ q.T).T)).cuda()
+        v = torch.empty((nw, n), dtype=torch.float64, device="cuda")
+        solve = B.hpsi_eigh_lowest_sym
+    else:
+        a = torch.from_numpy(np.ascontiguousarray(workloads.hermitian_matrix(n, n, scale=20.0).T)).cuda()
+        v = torch.empty((nw, n), dtype=torch.complex128, device="cuda")
+        solve = B.hpsi_eigh_lowest
     w = torch.empty(nw, dtype=torch.float64, device="cuda")
-    v = torch.empty((nw, n), dtype=torch.complex128, device="cuda")
     for _ in range(2):
-        B.hpsi_eigh_lowest(ctx, a, n, n, nw, w, v)
+        solve(ctx, a, n, n, nw, w, v)
     torch.cuda.synchronize()
     torch.cuda.profiler.start()
     for _ in range(args.reps):
-        B.hpsi_eigh_lowest(ctx, a, n, n, nw, w, v)
+        solve(ctx, a, n, n, nw, w, v)
     torch.cuda.synchronize()
     torch.cuda.profiler.stop()
-    print("ok eigh", n, nw, float(w.sum()))
+    print("ok eigh", "real" if real else "complex", n, nw, float(w.sum()))
+
+
+def solve_case(args, torch, workloads, B):
+    import numpy as np
+    import oracle
+    p = workloads.CONFIGS[args.config]()
+    k = p.kpts[0]
+    m = B.hpsi_gsphere(p.lattice, p.ecut, k)
+    prec = B.HPSI_MIXED if args.precision == "mixed" else B.HPSI_FP64
+    gamma = args.form == "gamma" or (args.form == "auto" and not np.any(k))
+    tol = args.tol or (5e-5 if prec == B.HPSI_MIXED else 1e-8)
+    ctx = B.hpsi_setup(p.lattice, p.ecut, [k], p.fft, workloads.vloc_r(p.lattice, p.atoms, p.fft),
+                       [workloads.beta(p.lattice, p.atoms, k, m)], workloads.dmat(len(p.atoms)), prec,
+                       torch.cuda.current_stream().cuda_stream)
+    x0 = workloads.psi0(p.lattice, k, m, p.nbnd, p.psi_seed)
+    if gamma:
+        x0 = np.ascontiguousarray(oracle.gamma.to_half(x0, m))
+    x0 = torch.from_numpy(x0).cuda()
+    solve = B.davidson_solve_gamma if gamma else B.davidson_solve
+    solve(ctx, 0, x0.clone(), tol, 400, raise_on_notconv=False)
+    torch.cuda.synchronize()
+    x = x0.clone()
+    torch.cuda.profiler.start()
+    eig, it, res, rc = solve(ctx, 0, x, tol, 400, raise_on_notconv=False)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    print("ok solve", args.config, args.precision, "gamma" if gamma else "complex", it, rc, float(eig.sum()))
 
 
 def cg_case(args, torch, workloads, B):
