@@ -90,15 +90,15 @@ def main(names):
             m, vr, beta, d = inputs(p, k)
             omega = oracle.scf.cell_volume(p.lattice)
             rho0 = np.full(p.fft, 4.0 / omega)
-            out = oracle.scf.scf(p.lattice, k, m, p.fft, vr, beta, d, 2, rho0, tol=1e-16, maxiter=100)
+            sol = oracle.scf.scf(p.lattice, k, m, p.fft, vr, beta, d, 2, rho0, tol=1e-16, maxiter=100)
             rng = np.random.default_rng(5000)
-            idx = rng.choice(out["rho"].size, 64, replace=False)
-            ev = out["eig"].tolist()
+            idx = rng.choice(sol["rho"].size, 64, replace=False)
+            ev = sol["eig"].tolist()
             info = {"method": "oracle.scf.scf, dense H, Anderson mixing (8, 0.5), tol 1e-16", "npw": len(m),
-                    "nocc": 2, "e": out["e"], "e_hwf": out["e_hwf"], "iters": out["iters"],
-                    "charge": oracle.scf.charge(out["rho"], p.lattice),
-                    "rho_sample_index": idx.tolist(), "rho_sample": out["rho"].reshape(-1)[idx].tolist(),
-                    "rho_max": float(np.max(out["rho"])), "rho_sum2": float(np.sum(out["rho"] ** 2))}
+                    "nocc": 2, "e": sol["e"], "e_hwf": sol["e_hwf"], "iters": sol["iters"],
+                    "charge": oracle.scf.charge(sol["rho"], p.lattice),
+                    "rho_sample_index": idx.tolist(), "rho_sample": sol["rho"].reshape(-1)[idx].tolist(),
+                    "rho_max": float(np.max(sol["rho"])), "rho_sum2": float(np.sum(sol["rho"] ** 2))}
         elif name.startswith("c5"):
             # the large cell: the lowest C5_NBND (default 64) of its 512 bands, H applied 16 bands
             # at a time to bound the memory of the 144^3 transforms
