@@ -48,12 +48,14 @@ FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # 152 SMs x 128 FP32 lanes x F
 # with the hash of its source files at capture time; a mismatch reports null.  Units: a band of
 # the kernel's launch for the H|psi> classes, a matrix element for the reduction.
 #   xvx_y mixed: k_plane<float,9,10>, 48-band launch, 51.73 MB read + 4.81 MB write
-#   calbec fp64: k_calbec64, 160-band launch, 267.31 MB read + 7.14 MB write
+#   calbec fp64: k_calbec64, 160-band launch, 270.83 MB read + 7.20 MB write
 #   tridiag: k_eh_tridiag, one n = 640 launch, 3.372 MB read + 0.030 MB write
+#   tridiag_real: k_eh_tridiag_r, one n = 1536 launch, 9.580 MB read + 2.8 KB write
 NCU_TRAFFIC = {
     ("tridiag", -1): (("eigh_tridiag.cuh",), "7b3ca0b96a01", (3367936 + 31488) / 640 ** 2),
+    ("tridiag_real", -1): (("eigh_tridiag_real.cuh",), "9dff8d240ee0", (9579520 + 2816) / 1536 ** 2),
     ("xvx_y", 1): (("local_fast.cu", "fft_codelets.cuh"), "92564643ab55", (51.725568e6 + 4.813056e6) / 48),
-    ("calbec", 0): (("nonlocal_fp64.cu",), "f2c91a1c9ad9", (267.307264e6 + 7.139584e6) / 160),
+    ("calbec", 0): (("nonlocal_fp64.cu",), "dc474a4712d7", (270.831104e6 + 7.199488e6) / 160),
 }
 
 
