@@ -75,14 +75,17 @@ enum hpsi_option {
   HPSI_OPT_AUTOTUNE = 9,      /* 1 (default): the first hpsi_apply of a problem with >= 4 bands at a
                                  precision times every shared-memory plan of the register-codelet
                                  kernels and three band-block sizes on its own bands and keeps the
-                                 fastest (that call synchronizes; results do not depend on the
-                                 choice); 0: fixed defaults */
+                                 fastest (results do not depend on the choice); at HPSI_MIXED it
+                                 also times caps of 4, 8 and 16 K-steps per float32 accumulation of
+                                 the tensor-core calbec (unless HPSI_OPT_TC_KSPLIT is set; results
+                                 differ at float32 rounding level).  That call synchronizes.
+                                 0: fixed defaults */
   HPSI_OPT_EIGENSOLVER = 10,  /* reduced eigenproblems of davidson_solve and hpsi_eigh_lowest:
                                  1 (default): the library's own kernels (Householder reduction,
                                  Sturm multisection, inverse iteration, back-transformation) for
                                  n <= 1024, cuSOLVER zheevdx above that or if inverse iteration
                                  loses a vector; 0: cuSOLVER zheevdx always */
-  HPSI_OPT_FP32_GEMM = 11,    /* mixed davidson_solve: complex64 subspace GEMMs (projections, reduced
+  HPSI_OPT_FP32_GEMM = 11,    /* mixed davidson_solve (complex form): complex64 subspace GEMMs (projections, reduced
                                  matrices, Ritz vectors) 0 (default): float32 on the CUDA cores;
                                  1: float32 emulated by cuBLAS with bf16 tensor-core products
                                  (three bf16 terms per operand, nine products); 2: the Gauss
@@ -123,8 +126,11 @@ enum hpsi_option {
   HPSI_OPT_SCF_NMIX = 19,     /* hpsi_scf: past (input density, residual) pairs the mixing combines
                                  (1..16, default 8) */
   HPSI_OPT_SCF_BETA = 20,     /* hpsi_scf: step along the optimal residual (0 < value <= 1, default 0.5) */
-  HPSI_OPT_SCF_DAVIDSON_TOL = 21  /* hpsi_scf: residual tolerance of the Davidson solve of each
+  HPSI_OPT_SCF_DAVIDSON_TOL = 21, /* hpsi_scf: residual tolerance of the Davidson solve of each
                                  iteration (default 1e-9) */
+  HPSI_OPT_GAMMA_GEMM = 22    /* mixed davidson_solve_gamma: 1 (default): the float32 subspace GEMMs
+                                 run as cuBLAS's float32 emulation with bf16 tensor-core products
+                                 (float32-accurate); 0: float32 on the CUDA cores */
 };
 
 /* Kernel classes reported by hpsi_kernel_stats. */
@@ -273,13 +279,14 @@ HPSI_API int hpsi_apply_gamma(hpsi_ctx* ctx, int ik, const void* psi_in, void* h
  *   other arguments as in davidson_solve (nbnd times the basis factor must not exceed npw)
  * The real orbital with half coefficients c is the real vector x = (c(0), 0) at G = 0 and
  * sqrt2 (Re c(G), Im c(G)) elsewhere; inner products are x_a . x_b and H is real symmetric, so the
- * subspace products are real GEMMs (float64 in a float64 context, float32 in a mixed one) and the
+ * subspace products are real GEMMs (float64 in a float64 context; float32 in a mixed one, by default
+ * emulated on the bf16 tensor cores, HPSI_OPT_GAMMA_GEMM) and the
  * reduced problems real symmetric (float64, the library's real eigensolver as in
  * hpsi_eigh_lowest_sym, cuSOLVER dsyevdx behind it).  Residual norms and Cholesky
  * factors are float64; the preconditioner uses <G|H|G> for both coordinates of each G.  In a mixed
  * context the returned eigenvalues are float64 Rayleigh quotients after one float64 application of
- * H (HPSI_OPT_FINAL_FP64).  HPSI_OPT_BASIS, _THICK_RESTART, _PRECOND_TAU and _PRECOND_SHIFT apply;
- * locking and the subspace-GEMM options do not.  Synchronous; HPSI_ENOTCONV if maxiter is reached.
+ * H (HPSI_OPT_FINAL_FP64).  HPSI_OPT_BASIS, _THICK_RESTART, _PRECOND_TAU, _PRECOND_SHIFT and
+ * _GAMMA_GEMM apply; locking and HPSI_OPT_FP32_GEMM do not.  Synchronous; HPSI_ENOTCONV if maxiter is reached.
  */
 HPSI_API int davidson_solve_gamma(hpsi_ctx* ctx, int ik, int nbnd, double tol, int maxiter, void* psi_inout,
                                   double* eig_out, int* iters_out, double* resnorm_out);

@@ -529,10 +529,18 @@ int batch_apply(Context& c, int nitem, const int* prob, const int* nbnd, const d
     int rc = local_apply(c, c.probs[prob[i]], psi[i], hpsi[i], nbnd[i]);
     if (rc) return rc;
   }
+  // the nonlocal term: in float64 all items share one launch per kernel class; the tensor-core
+  // form runs per item
+  if (cur_prec(c) == HPSI_FP64) {
+    int rc = nonlocal_batch_fp64(c, nitem, prob, nbnd, psi, hpsi);
+    if (rc) return rc;
+  }
   for (int i = 0; i < nitem; ++i) {
     if (nbnd[i] == 0) continue;
-    int rc = nonlocal_apply(c, c.probs[prob[i]], psi[i], hpsi[i], nbnd[i]);
-    if (rc) return rc;
+    if (cur_prec(c) != HPSI_FP64) {
+      int rc = nonlocal_apply(c, c.probs[prob[i]], psi[i], hpsi[i], nbnd[i]);
+      if (rc) return rc;
+    }
     c.band_apps += nbnd[i];
   }
   return HPSI_OK;
@@ -981,6 +989,11 @@ extern "C" int hpsi_set_option(hpsi_ctx* ctx, int option, double value) {
   if (option == HPSI_OPT_SCF_BETA) {
     if (!(value > 0.0 && value <= 1.0)) return fail(c, HPSI_EINVAL, "HPSI_OPT_SCF_BETA must be in (0, 1]");
     c.scf_beta = value;
+    return HPSI_OK;
+  }
+  if (option == HPSI_OPT_GAMMA_GEMM) {
+    if (value != 0.0 && value != 1.0) return fail(c, HPSI_EINVAL, "HPSI_OPT_GAMMA_GEMM must be 0 or 1");
+    c.gamma_gemm = (int)value;
     return HPSI_OK;
   }
   if (option == HPSI_OPT_SCF_DAVIDSON_TOL) {

@@ -112,7 +112,8 @@ __device__ int sturm_count(int n, const double* __restrict__ d, const double* __
 // One CTA of kBisWarps warps per wanted eigenvalue i: (32 kBisWarps + 1)-way multisection of an
 // interval with count(lo) <= i < count(hi), one Sturm count per thread and round, so the float64
 // recurrences run on every sub-partition of the SM at once.
-constexpr int kBisWarps = 2;
+constexpr int kBisWarps = 1;   // 32 points per round: float64 Sturm counts are the bottleneck on this GPU, and
+                                // 32 points take ~40% fewer of them than 64 for the same bracket width
 __global__ void __launch_bounds__(32 * kBisWarps) k_eh_bisect(int n, const double* __restrict__ d,
                                                               const double* __restrict__ e,
                                                               const double* __restrict__ e2, int nwant,

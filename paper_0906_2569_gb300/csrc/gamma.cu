@@ -226,7 +226,10 @@ __global__ void __launch_bounds__(512) k_g_residual(int n, const T* __restrict__
   if (threadIdx.x == 0) rnorm[b] = sqrt(s);
 }
 
-// t_j = r_{idx[j]} / clamp(hd - eps_{idx[j]}), normalised; one CTA per correction.
+// t_j = r_{idx[j]} / clamp(hd - eps_{idx[j]}), normalised; one CTA per correction.  A preconditioner
+// needs no exact quotient, and a float64 division is a long instruction sequence on this GPU: the
+// float32 basis takes the quotient and its partial norms in float32, the float64 basis a float32
+// reciprocal refined by one float64 Newton step (relative error ~1e-14).
 template <typename T>
 __global__ void __launch_bounds__(512) k_g_precondition(int n, const int* __restrict__ idx, const T* __restrict__ r,
                                                         const T* __restrict__ hd, const double* __restrict__ eps,
@@ -237,16 +240,32 @@ __global__ void __launch_bounds__(512) k_g_precondition(int n, const int* __rest
   const T* rb = r + (size_t)i * n;
   T* tb = t + (size_t)j * n;
   double s = 0.0;
-  for (int g = threadIdx.x; g < n; g += blockDim.x) {
-    double d = (double)hd[g] - e;
-    if (fabs(d) < tau) d = d >= 0.0 ? tau : -tau;
-    const T q = (T)((double)rb[g] / d);
-    tb[g] = q;
-    s += (double)q * (double)q;
+  if (sizeof(T) == 4) {
+    const float ef = (float)e, tf = (float)tau;
+    float sf = 0.f;
+    for (int g = threadIdx.x; g < n; g += blockDim.x) {
+      float d = (float)hd[g] - ef;
+      if (fabsf(d) < tf) d = d >= 0.f ? tf : -tf;
+      const float q = (float)rb[g] * __frcp_rn(d);
+      tb[g] = (T)q;
+      sf = fmaf(q, q, sf);
+    }
+    s = sf;
+  } else {
+    for (int g = threadIdx.x; g < n; g += blockDim.x) {
+      double d = (double)hd[g] - e;
+      if (fabs(d) < tau) d = d >= 0.0 ? tau : -tau;
+      double inv = (double)__frcp_rn((float)d);
+      inv = fma(inv, fma(-d, inv, 1.0), inv);
+      const T q = (T)((double)rb[g] * inv);
+      tb[g] = q;
+      s = fma((double)q, (double)q, s);
+    }
   }
   s = block_sum<T>(s, red);
   const double inv = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
-  for (int g = threadIdx.x; g < n; g += blockDim.x) tb[g] = (T)((double)tb[g] * inv);
+  const T invT = (T)inv;
+  for (int g = threadIdx.x; g < n; g += blockDim.x) tb[g] = tb[g] * invT;
 }
 
 template <typename T>
@@ -832,12 +851,11 @@ int gamma_davidson_run(Context& c, int ik, int nbnd, double tol, int maxiter, do
   GBK(cublasSetStream(h->blas, c.stream), "cublasSetStream");
   GBK(cusolverDnSetStream(h->solver, c.stream), "cusolverDnSetStream");
   if (c.precision == HPSI_MIXED) {
-    // HPSI_OPT_FP32_GEMM = 1: the float32 subspace GEMMs emulated by cuBLAS with bf16 tensor-core
-    // products (float32-accurate); the other values of the option do not apply to real GEMMs
-    GBK(cublasSetMathMode(h->blas, c.fp32_gemm == 1 ? CUBLAS_FP32_EMULATED_BF16X9_MATH : CUBLAS_DEFAULT_MATH),
-        "cublasSetMathMode");
-    if (c.fp32_gemm == 1) GBK(cublasSetEmulationStrategy(h->blas, CUBLAS_EMULATION_STRATEGY_EAGER),
-                              "cublasSetEmulationStrategy");
+    // HPSI_OPT_GAMMA_GEMM = 1 (default): the float32 subspace GEMMs emulated by cuBLAS with bf16
+    // tensor-core products (float32-accurate); 0: float32 on the CUDA cores
+    const bool emu = c.gamma_gemm == 1;
+    GBK(cublasSetMathMode(h->blas, emu ? CUBLAS_FP32_EMULATED_BF16X9_MATH : CUBLAS_DEFAULT_MATH), "cublasSetMathMode");
+    if (emu) GBK(cublasSetEmulationStrategy(h->blas, CUBLAS_EMULATION_STRATEGY_EAGER), "cublasSetEmulationStrategy");
     GammaDavidson<float> d(c, *h, ik);
     const int rc = d.run(nbnd, tol, maxiter, psio, eig_out, iters_out, resnorm_out);
     cublasSetMathMode(h->blas, CUBLAS_DEFAULT_MATH);

@@ -73,6 +73,8 @@ struct Problem {
   mutable int fflags[2] = {0, 0};  // fast path: bit 2 enabled, bit 0 stage V, bit 1 stage the stick row
   mutable int nbbf[2] = {1, 1};    // band block of the fast local kernels
   mutable bool tuned[2] = {false, false};   // autotuner has chosen fflags / nbbf
+  mutable int nl_kmax = 0;         // mixed calbec: K-steps per float32 accumulation the autotuner chose
+                                   // (0: not tuned yet)
   int* d_ymap = nullptr;           // [npl][n2]: stick of (plane, j2) or -1
   int* d_xmap = nullptr;           // [n1]: plane of ix or -1
   const double2* d_ftw64 = nullptr;   // e^{-2 pi i j / n}, j < n (owned by the twiddle table)
@@ -153,6 +155,7 @@ struct Context {
   int scf_nmix = 8;                    // SCF: past (input, residual) pairs the mixing combines
   double scf_beta = 0.5;               // SCF: step along the optimal residual
   double scf_dav_tol = 1e-9;           // SCF: residual tolerance of each Davidson solve
+  int gamma_gemm = 1;                  // mixed Gamma Davidson: 1 bf16x9-emulated float32 GEMMs, 0 plain float32
   double cg_tmin = 1.0;                // CG preconditioner: P^2 = 1 / max(|k+G|^2/2, cg_tmin)
   cudaStream_t cap_stream = nullptr;   // internal stream for graph capture
   GraphCache graph;
@@ -240,6 +243,9 @@ void nonlocal_fp64_plan(const Context& c, const Problem& p, int nbnd, int* nspli
                         size_t max_bytes = 0);
 int nonlocal_fp64_into(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd, void* scratch,
                        size_t capacity);
+// The float64 nonlocal term of several problems' band blocks, one launch per kernel class
+int nonlocal_batch_fp64(Context& c, int nitem, const int* prob, const int* nbnd, const double2* const* psi,
+                        double2* const* hpsi);
 
 // ---- context helpers (api.cpp) ----
 int ensure_buffer(Context& c, void** ptr, size_t* have, size_t need);

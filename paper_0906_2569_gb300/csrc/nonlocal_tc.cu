@@ -554,7 +554,52 @@ int prepare_t(Context& c, Problem& p) {
 }
 
 template <int NT>
-int apply_t(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd) {
+int apply_t(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd, int kmax);
+
+// Autotuner of the mixed calbec's K-split: on the first application of a problem with >= 4 bands
+// (not under stream capture), time the caps of 4, 8 and 16 K-steps per float32 accumulation on
+// this call's own bands (one warm-up and one timed run each) and keep the fastest.  Every
+// candidate is at or below the default cap, so none is less accurate than the default.
+template <int NT>
+int tune_ksplit(Context& c, const Problem& p, const double2* psi, int nbnd) {
+  // add_vuspsi adds into its output, so the timed runs write a scratch block, not the caller's
+  cudaEvent_t e0, e1;
+  double2* scratch = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
+      cudaMalloc((void**)&scratch, sizeof(double2) * (size_t)nbnd * p.npw) != cudaSuccess) {
+    cudaGetLastError();
+    p.nl_kmax = kCalbecKsteps;
+    return HPSI_OK;
+  }
+  double2* hpsi = scratch;
+  const bool timing = c.timing;
+  c.timing = false;
+  float best = 1e30f;
+  int pick = kCalbecKsteps, rc = HPSI_OK;
+  for (int km : {kCalbecKsteps, 8, 4}) {
+    float ms = 0.f;
+    for (int rep = 0; rep < 2 && !rc; ++rep) {
+      cudaEventRecord(e0, c.stream);
+      rc = apply_t<NT>(c, p, psi, hpsi, nbnd, km);
+      cudaEventRecord(e1, c.stream);
+    }
+    if (rc) break;
+    if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best) {
+      best = ms;
+      pick = km;
+    }
+  }
+  c.timing = timing;
+  cudaStreamSynchronize(c.stream);
+  cudaFree(scratch);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  p.nl_kmax = pick;
+  return rc;
+}
+
+template <int NT>
+int apply_t(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd, int kmax) {
   const int P = p.nproj, npw = p.npw;
   const int kc = round_up(2 * npw, TBK), ka = round_up(2 * P, TBK);
   const size_t cal = (size_t)NT * P * kc;
@@ -565,7 +610,7 @@ int apply_t(Context& c, const Problem& p, const double2* psi, double2* hpsi, int
   const int tiles = ((2 * nbnd + TBN - 1) / TBN) * ((P + TBM - 1) / TBM);
   int nsplit = std::max(1, std::min(nks, (2 * c.sm_count + tiles - 1) / tiles));
   int ksplit = (nks + nsplit - 1) / nsplit;
-  ksplit = std::min(ksplit, c.tc_kmax > 0 ? c.tc_kmax : kCalbecKsteps);
+  ksplit = std::min(ksplit, kmax);
   nsplit = (nks + ksplit - 1) / ksplit;
   const size_t psib = sizeof(__nv_bfloat16) * (size_t)NT * 2 * nbnd * kc;
   const size_t partb = sizeof(float) * (size_t)nsplit * P * 2 * nbnd;
@@ -627,7 +672,16 @@ int mixed_prepare_beta(Context& c, Problem& p) {
 
 int nonlocal_apply_mixed(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd) {
   if (p.nproj == 0 || nbnd == 0) return HPSI_OK;
-  return c.nl_terms == 3 ? apply_t<3>(c, p, psi, hpsi, nbnd) : apply_t<2>(c, p, psi, hpsi, nbnd);
+  if (c.tc_kmax <= 0 && p.nl_kmax == 0) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(c.stream, &cap);
+    if (c.autotune && nbnd >= 4 && cap == cudaStreamCaptureStatusNone) {
+      const int rc = c.nl_terms == 3 ? tune_ksplit<3>(c, p, psi, nbnd) : tune_ksplit<2>(c, p, psi, nbnd);
+      if (rc) return rc;
+    }
+  }
+  const int kmax = c.tc_kmax > 0 ? c.tc_kmax : (p.nl_kmax > 0 ? p.nl_kmax : kCalbecKsteps);
+  return c.nl_terms == 3 ? apply_t<3>(c, p, psi, hpsi, nbnd, kmax) : apply_t<2>(c, p, psi, hpsi, nbnd, kmax);
 }
 
 void TcInner::release() {
