@@ -6,8 +6,10 @@
 // asynchronous stream pipeline.  This entry point computes the same H|psi> as hpsi_apply, but
 // every intermediate (the plane and stick buffers of the FFTs, the partial sums of <beta|psi>
 // and D<beta|psi>) lives in one fixed array compiled into the library.  Bands are processed in
-// chunks that fit the array.  The nonlocal term runs on the float64 kernels at either
-// precision (they need no buffers beyond the array).
+// chunks that fit the array.  The local term runs on the register-codelet kernels where the box
+// has them (with the plan chosen at setup or by an earlier hpsi_apply), else on the generic ones;
+// the nonlocal term runs on the float64 kernels at either precision (they need no buffers beyond
+// the array).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -83,10 +85,16 @@ extern "C" int hpsi_apply_noalloc(hpsi_ctx* ctx, int ik, const void* psi_in, voi
   // scale with its bands, so a shorter last chunk fits in the same places; its nonlocal K-split
   // is planned against the room left after the full chunk's X and Y, and one split of the partials
   // grows with the bands too, so whatever fits the full chunk fits the last one.
-  const size_t cs = hpsi::cur_prec(c) == HPSI_FP64 ? sizeof(double2) : sizeof(float2);
-  auto xbytes = [&](int nb) { return align256(cs * (size_t)nb * p.n[2] * p.npl * p.n[1]); };
+  // The register-codelet kernels (cubic boxes with a two-factor edge) need two stick-row buffers per
+  // band; the generic kernels an m1-plane buffer and a stick-row buffer.
+  const int prec = hpsi::cur_prec(c);
+  const bool fast = (p.fflags[prec] & 4) && !c.force_generic;
+  const size_t cs = prec == HPSI_FP64 ? sizeof(double2) : sizeof(float2);
+  auto xbytes = [&](int nb) {
+    return align256(cs * (size_t)nb * p.n[2] * (fast ? (size_t)p.nst : (size_t)p.npl * p.n[1]));
+  };
   auto ybytes = [&](int nb) { return align256(cs * (size_t)nb * p.n[2] * p.nst); };
-  const size_t per_band = hpsi::local_scratch_per_band(p, hpsi::cur_prec(c));
+  const size_t per_band = xbytes(1) + ybytes(1);
   int chunk = 0;
   for (int nb = std::min(nbnd, 4096); nb >= 1; nb = nb > 64 ? nb - 32 : nb - 1) {
     const size_t xy = xbytes(nb) + ybytes(nb);
@@ -114,7 +122,8 @@ extern "C" int hpsi_apply_noalloc(hpsi_ctx* ctx, int ik, const void* psi_in, voi
     const int nb = std::min(chunk, nbnd - b);
     if (xbytes(nb) > xbytes(chunk) || ybytes(nb) > ybytes(chunk))
       return hpsi::fail(c, HPSI_EINVAL, "hpsi_apply_noalloc: internal chunk sizing error");
-    rc = hpsi::local_apply_into(c, p, psi + (size_t)b * p.npw, hpsi + (size_t)b * p.npw, nb, X, Y, nb);
+    rc = fast ? hpsi::local_fast_apply(c, p, psi + (size_t)b * p.npw, hpsi + (size_t)b * p.npw, nb, X, Y, nb)
+              : hpsi::local_apply_into(c, p, psi + (size_t)b * p.npw, hpsi + (size_t)b * p.npw, nb, X, Y, nb);
     if (rc) return rc;
     rc = hpsi::nonlocal_fp64_into(c, p, psi + (size_t)b * p.npw, hpsi + (size_t)b * p.npw, nb, NL, nl_room);
     if (rc) return rc;

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "hpsi_internal.h"
 
@@ -35,12 +36,12 @@ constexpr int CB_TB = 32;   // bands per CTA
 constexpr int CB_TK = 32;   // G per shared-memory tile
 
 // part[split][b][p] = sum_{G in split} conj(beta[p][G]) psi[b][G]
-__global__ void __launch_bounds__(256) k_calbec64(int npw, int nproj, int nb, int kchunk,
-                                                  const double2* __restrict__ beta,
-                                                  const double2* __restrict__ psi, double2* __restrict__ part) {
+__device__ __forceinline__ void calbec_tile(int npw, int nproj, int nb, int kchunk, const double2* __restrict__ beta,
+                                            const double2* __restrict__ psi, double2* __restrict__ part, int tp,
+                                            int tb, int split) {
   __shared__ double2 sb[CB_TP][CB_TK + 1];
   __shared__ double2 sp[CB_TB][CB_TK + 1];
-  const int p0 = blockIdx.x * CB_TP, b0 = blockIdx.y * CB_TB, split = blockIdx.z;
+  const int p0 = tp * CB_TP, b0 = tb * CB_TB;
   const int gbeg = split * kchunk, gend = min(npw, gbeg + kchunk);
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // tx -> p, ty -> b
   double2 acc[2][2];
@@ -79,11 +80,16 @@ __global__ void __launch_bounds__(256) k_calbec64(int npw, int nproj, int nb, in
     }
 }
 
+__global__ void __launch_bounds__(256) k_calbec64(int npw, int nproj, int nb, int kchunk,
+                                                  const double2* __restrict__ beta,
+                                                  const double2* __restrict__ psi, double2* __restrict__ part) {
+  calbec_tile(npw, nproj, nb, kchunk, beta, psi, part, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
 // w[b][p] = sum_{q in row p of D} D_pq sum_s part[s][b][q]
-__global__ void k_dscale64(int nproj, int nb, int nsplit, const double2* __restrict__ part,
-                           const int* __restrict__ rowptr, const int* __restrict__ col,
-                           const double2* __restrict__ val, double2* __restrict__ w) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void dscale_one(int i, int nproj, int nb, int nsplit, const double2* __restrict__ part,
+                                           const int* __restrict__ rowptr, const int* __restrict__ col,
+                                           const double2* __restrict__ val, double2* __restrict__ w) {
   if (i >= nproj * nb) return;
   const int b = i / nproj, p = i % nproj;
   double2 acc = make_double2(0.0, 0.0);
@@ -102,16 +108,23 @@ __global__ void k_dscale64(int nproj, int nb, int nsplit, const double2* __restr
   w[i] = acc;
 }
 
+__global__ void k_dscale64(int nproj, int nb, int nsplit, const double2* __restrict__ part,
+                           const int* __restrict__ rowptr, const int* __restrict__ col,
+                           const double2* __restrict__ val, double2* __restrict__ w) {
+  dscale_one(blockIdx.x * blockDim.x + threadIdx.x, nproj, nb, nsplit, part, rowptr, col, val, w);
+}
+
 constexpr int AV_TG = 64;   // G per CTA
 constexpr int AV_TB = 32;   // bands per CTA
 constexpr int AV_TP = 16;   // projectors per shared-memory tile
 
 // hpsi[b][G] += sum_p w[b][p] beta[p][G]
-__global__ void __launch_bounds__(256) k_addvus64(int npw, int nproj, int nb, const double2* __restrict__ w,
-                                                  const double2* __restrict__ beta, double2* __restrict__ hpsi) {
+__device__ __forceinline__ void addvus_tile(int npw, int nproj, int nb, const double2* __restrict__ w,
+                                            const double2* __restrict__ beta, double2* __restrict__ hpsi, int tg,
+                                            int tb) {
   __shared__ double2 sb[AV_TP][AV_TG];
   __shared__ double2 sw[AV_TB][AV_TP + 1];
-  const int g0 = blockIdx.x * AV_TG, b0 = blockIdx.y * AV_TB;
+  const int g0 = tg * AV_TG, b0 = tb * AV_TB;
   const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;   // tx -> G, ty -> bands ty + 4 j
   double2 acc[8];
 #pragma unroll
@@ -150,6 +163,64 @@ __global__ void __launch_bounds__(256) k_addvus64(int npw, int nproj, int nb, co
       }
     }
   }
+}
+
+__global__ void __launch_bounds__(256) k_addvus64(int npw, int nproj, int nb, const double2* __restrict__ w,
+                                                  const double2* __restrict__ beta, double2* __restrict__ hpsi) {
+  addvus_tile(npw, nproj, nb, w, beta, hpsi, blockIdx.x, blockIdx.y);
+}
+
+// ---- many problems in one launch per kernel (hpsi_apply_batch) ----
+// Each launch takes every item's geometry by value; CTA i finds its item from the running tile
+// counts (at most kNlBatch items, a short scan) and then does exactly what the one-item kernel does.
+constexpr int kNlBatch = 32;
+
+struct NlItem {
+  int npw, nproj, nb, kchunk, nsplit, tilesp, tilesb, gtiles;
+  const double2* beta;
+  const double2* psi;
+  double2* hpsi;
+  double2* part;
+  double2* w;
+  const int* rowptr;
+  const int* col;
+  const double2* dval;
+};
+
+struct NlBatch {
+  int nitems;
+  int off_cal[kNlBatch + 1];   // first calbec tile of each item (tilesp x tilesb x nsplit each)
+  int off_ds[kNlBatch + 1];    // first D-scale block (256 outputs each)
+  int off_add[kNlBatch + 1];   // first add_vuspsi tile (gtiles x tilesb)
+  NlItem item[kNlBatch];
+};
+
+__device__ __forceinline__ int find_item(const int* off, int nitems, int blk) {
+  int i = 0;
+  while (i + 1 < nitems && off[i + 1] <= blk) ++i;
+  return i;
+}
+
+__global__ void __launch_bounds__(256) k_calbec64_batch(const __grid_constant__ NlBatch bt) {
+  const int i = find_item(bt.off_cal, bt.nitems, blockIdx.x);
+  const NlItem& a = bt.item[i];
+  const int l = blockIdx.x - bt.off_cal[i];
+  const int tp = l % a.tilesp, r = l / a.tilesp;
+  calbec_tile(a.npw, a.nproj, a.nb, a.kchunk, a.beta, a.psi, a.part, tp, r % a.tilesb, r / a.tilesb);
+}
+
+__global__ void __launch_bounds__(256) k_dscale64_batch(const __grid_constant__ NlBatch bt) {
+  const int i = find_item(bt.off_ds, bt.nitems, blockIdx.x);
+  const NlItem& a = bt.item[i];
+  dscale_one((blockIdx.x - bt.off_ds[i]) * blockDim.x + threadIdx.x, a.nproj, a.nb, a.nsplit, a.part, a.rowptr,
+             a.col, a.dval, a.w);
+}
+
+__global__ void __launch_bounds__(256) k_addvus64_batch(const __grid_constant__ NlBatch bt) {
+  const int i = find_item(bt.off_add, bt.nitems, blockIdx.x);
+  const NlItem& a = bt.item[i];
+  const int l = blockIdx.x - bt.off_add[i];
+  addvus_tile(a.npw, a.nproj, a.nb, a.w, a.beta, a.hpsi, l % a.gtiles, l / a.gtiles);
 }
 
 }  // namespace
@@ -226,6 +297,66 @@ int nonlocal_fp64_into(Context& c, const Problem& p, const double2* psi, double2
                   p.npw, p.nproj, nbnd, w, p.d_beta, hpsi)));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(c, e, "nonlocal float64 kernels launch");
+  return HPSI_OK;
+}
+
+// The float64 nonlocal term of several items in one launch per kernel class (groups of kNlBatch).
+int nonlocal_batch_fp64(Context& c, int nitem, const int* prob, const int* nbnd, const double2* const* psi,
+                        double2* const* hpsi) {
+  std::vector<int> items;
+  for (int i = 0; i < nitem; ++i)
+    if (nbnd[i] > 0 && c.probs[prob[i]].nproj > 0) items.push_back(i);
+  // partial sums and w of every item side by side in one workspace
+  std::vector<size_t> off(items.size());
+  std::vector<int> ns(items.size()), kc(items.size());
+  size_t total = 0;
+  for (size_t j = 0; j < items.size(); ++j) {
+    const Problem& p = c.probs[prob[items[j]]];
+    size_t bytes = 0;
+    nonlocal_fp64_plan(c, p, nbnd[items[j]], &ns[j], &kc[j], &bytes);
+    off[j] = total;
+    total += (bytes + 255) & ~size_t(255);
+  }
+  if (items.empty()) return HPSI_OK;
+  int rc = ensure_buffer(c, &c.ws.part, &c.ws.partbytes, total);
+  if (rc) return rc;
+  unsigned char* base = static_cast<unsigned char*>(c.ws.part);
+  static NlBatch bt;   // host staging of the parameter block (calls are not thread-safe by contract)
+  for (size_t g0 = 0; g0 < items.size(); g0 += kNlBatch) {
+    const int n = (int)std::min<size_t>(kNlBatch, items.size() - g0);
+    bt.nitems = n;
+    bt.off_cal[0] = bt.off_ds[0] = bt.off_add[0] = 0;
+    for (int t = 0; t < n; ++t) {
+      const size_t j = g0 + t;
+      const int i = items[j];
+      const Problem& p = c.probs[prob[i]];
+      NlItem& a = bt.item[t];
+      a.npw = p.npw;
+      a.nproj = p.nproj;
+      a.nb = nbnd[i];
+      a.kchunk = kc[j];
+      a.nsplit = ns[j];
+      a.tilesp = (p.nproj + CB_TP - 1) / CB_TP;
+      a.tilesb = (a.nb + CB_TB - 1) / CB_TB;
+      a.gtiles = (p.npw + AV_TG - 1) / AV_TG;
+      a.beta = p.d_beta;
+      a.psi = psi[i];
+      a.hpsi = hpsi[i];
+      a.part = reinterpret_cast<double2*>(base + off[j]);
+      a.w = a.part + (size_t)a.nsplit * a.nb * a.nproj;
+      a.rowptr = p.d_rowptr;
+      a.col = p.d_col;
+      a.dval = p.d_dval;
+      bt.off_cal[t + 1] = bt.off_cal[t] + a.tilesp * a.tilesb * a.nsplit;
+      bt.off_ds[t + 1] = bt.off_ds[t] + (a.nproj * a.nb + 255) / 256;
+      bt.off_add[t + 1] = bt.off_add[t] + a.gtiles * ((a.nb + AV_TB - 1) / AV_TB);
+    }
+    HPSI_LAUNCH(c, HPSI_K_CALBEC, (k_calbec64_batch<<<bt.off_cal[n], 256, 0, c.stream>>>(bt)));
+    HPSI_LAUNCH(c, HPSI_K_DSCALE, (k_dscale64_batch<<<bt.off_ds[n], 256, 0, c.stream>>>(bt)));
+    HPSI_LAUNCH(c, HPSI_K_ADDVUS, (k_addvus64_batch<<<bt.off_add[n], 256, 0, c.stream>>>(bt)));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "batched float64 nonlocal kernels launch");
+  }
   return HPSI_OK;
 }
 

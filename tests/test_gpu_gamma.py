@@ -177,3 +177,38 @@ def test_gamma_rejected_where_it_does_not_apply(lib):
         B.hpsi_apply_gamma(ctx, 0, x, np.zeros_like(x))
     assert e.value.status == B.HPSI_EINVAL and "projector" in str(e.value)
     ctx.close()
+
+
+def test_gamma_many_cells(lib):
+    """The Gamma form on a context of independent cells (boxes 25^3..50^3): H on half storage for
+    three cells against the oracle, and the Davidson eigenvalues of one cell against the golden
+    dense-LAPACK values (float64)."""
+    import json
+    import torch
+    from paper_0906_2569_gb300 import binding as B
+    cells = workloads.config4b()
+    ms = [B.hpsi_gsphere(c.lattice, c.ecut, c.kpts[0]) for c in cells]
+    vrs = [workloads.vloc_r(c.lattice, c.atoms, c.fft) for c in cells]
+    betas = [workloads.beta(c.lattice, c.atoms, c.kpts[0], m) for c, m in zip(cells, ms)]
+    ds = [workloads.dmat(len(c.atoms)) for c in cells]
+    ctx = B.hpsi_setup_cells([c.lattice for c in cells], [c.ecut for c in cells], [c.fft for c in cells], vrs,
+                             betas, ds, B.HPSI_FP64, torch.cuda.current_stream().cuda_stream)
+    for i in (0, 17, 31):
+        c = cells[i]
+        half = _half_block(ms[i], 5, 60 + i)
+        x = torch.from_numpy(half).cuda()
+        y = torch.full_like(x, float("nan"))
+        B.hpsi_apply_gamma(ctx, i, x, y)
+        B.hpsi_sync(ctx)
+        full = oracle.gamma.to_full(half, ms[i])
+        ref = oracle.gamma.to_half(oracle.hamiltonian.hpsi(c.lattice, c.kpts[0], ms[i], c.fft, vrs[i], betas[i], ds[i],
+                                                           full), ms[i])
+        assert _maxrel(y.cpu().numpy(), ref) < 1e-12
+    i = 5
+    c = cells[i]
+    x = torch.from_numpy(np.ascontiguousarray(
+        oracle.gamma.to_half(workloads.psi0(c.lattice, c.kpts[0], ms[i], c.nbnd, c.psi_seed), ms[i]))).cuda()
+    eig, it, res, rc = B.davidson_solve_gamma(ctx, i, x, 1e-8, 300)
+    gold = np.asarray(json.load(open(os.path.join(HERE, "golden", "eigenvalues.json")))["c4b"]["eigenvalues"][i])
+    assert np.max(np.abs(eig - gold[:c.nbnd])) < 1e-10
+    ctx.close()
