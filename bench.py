@@ -624,11 +624,14 @@ def stick_counts(miller, fft):
     return len(sticks), len(planes)
 
 
-def kernel_work(name, p, npw, nst, npl, precision, nproj):
-    """Algorithmic (bytes, flops) of one complex band through a kernel class of the fast path.
+def kernel_work(name, p, npw, nst, npl, precision, nproj, real=False):
+    """Algorithmic (bytes, flops) of one complex band through a kernel class of the fast path, or,
+    with real (the Gamma form's nonlocal classes), of one real band in real-basis coordinates.
 
     Line FFTs count 5 n log2 n flops; bytes are the HBM data the method itself must move per band
-    (psi in, H|psi> out, the stick rows between the z and the plane kernels)."""
+    (psi in, H|psi> out, the stick rows between the z and the plane kernels).  The nonlocal GEMMs
+    count 8 P npw flops per complex band, 2 P (npw + 1) per real band (x 6 bf16 products at mixed
+    precision)."""
     n1, n2, n3 = p.fft
     cs = 16 if precision == 0 else 8
     fft = lambda n: 5.0 * n * math.log2(n)
@@ -640,6 +643,8 @@ def kernel_work(name, p, npw, nst, npl, precision, nproj):
     if name == "fwd_z":
         return rows + 2 * 16 * npw + 8 * npw, nst * fft(n3)
     if name in ("calbec", "addvus"):
+        if real:
+            return 8 * (npw + 1), 2.0 * nproj * (npw + 1) * (6 if precision == 1 else 1)
         return 16 * npw, 8.0 * nproj * npw * (6 if precision == 1 else 1)
     return None, None
 
@@ -686,12 +691,16 @@ def roofline(res, p, npw, nst, npl, precision, units_per_band=1):
         return tridiag_roofline(res, cand[name], real=units_per_band == 2)
     base = name.split("@")[0]
     prec = 0 if name.endswith("@fp64") else precision
-    # complex bands through the class in that solve: the final float64 application of a mixed solve
-    # handles the nbnd Ritz vectors, the rest of the band-applications ran at the working precision
-    total = res["timed_band_apps"] / units_per_band
-    final = p.nbnd / units_per_band if precision == 1 else 0
+    # bands through the class in that solve: the final float64 application of a mixed solve handles
+    # the nbnd Ritz vectors, the rest of the band-applications ran at the working precision.  The
+    # Gamma form (units_per_band 2) packs two real bands per complex band for the local classes and
+    # runs the nonlocal classes on the real bands themselves.
+    real_nl = units_per_band == 2 and base in ("calbec", "addvus")
+    upb = 1 if real_nl else units_per_band
+    total = res["timed_band_apps"] / upb
+    final = p.nbnd / upb if precision == 1 else 0
     bands = final if name.endswith("@fp64") else total - final
-    byt, flop = kernel_work(base, p, npw, nst, npl, prec, p.nproj)
+    byt, flop = kernel_work(base, p, npw, nst, npl, prec, p.nproj, real=real_nl)
     secs = cand[name]["ms"] / 1e3
     avg_ms = cand[name]["ms"] / cand[name]["launches"]
     traffic = None

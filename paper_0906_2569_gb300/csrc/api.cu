@@ -224,7 +224,7 @@ static int plan_for(Context& c, int n, FftPlan* out) {
 // comes down to the projectors: beta_p(-G) = u_p conj(beta_p(G)) for every G with one |u_p| = 1
 // per projector, and conj(u_p) u_q conj(D_pq) = D_pq for the nonzeros of D (then the nonlocal
 // kernel K(G, G') satisfies conj(K(-G, -G')) = K(G, G')).  Checked to 1e-12 relative.
-static bool gamma_applies(const Problem& p, const double* beta, const double* dmat, std::string* why) {
+static bool gamma_applies(Problem& p, const double* beta, const double* dmat, std::string* why) {
   if (p.k[0] != 0.0 || p.k[1] != 0.0 || p.k[2] != 0.0) {
     *why = "the problem is not at k = 0";
     return false;
@@ -284,6 +284,7 @@ static bool gamma_applies(const Problem& p, const double* beta, const double* dm
         return false;
       }
     }
+  p.gamma_u = u;
   return true;
 }
 
@@ -430,6 +431,9 @@ static void free_problem(Problem& p) {
   cudaFree(p.d_col);
   cudaFree(p.d_dval);
   cudaFree(p.d_beta_bf);
+  cudaFree(p.d_betar);
+  cudaFree(p.d_dvalr);
+  cudaFree(p.d_betar_bf);
 }
 
 static void free_context(Context& c) {
@@ -456,6 +460,7 @@ static void free_context(Context& c) {
   cudaFree(c.ws.batch);
   cudaFree(c.ws.gin);
   cudaFree(c.ws.gout);
+  cudaFree(c.ws.gnl);
   if (c.graph.exec) cudaGraphExecDestroy(c.graph.exec);
   if (c.cap_stream) cudaStreamDestroy(c.cap_stream);
   davidson_release(c);

@@ -79,10 +79,15 @@ __global__ void k_gamma_pack(int npw, int nb, const S* __restrict__ x, int scale
   }
 }
 
-// Unpack F = H f into the two bands' half-sphere results (see the file header).
+// Unpack F = H f into the two bands' half-sphere results (see the file header), adding the
+// nonlocal term given in real-basis coordinates: nl64 [nb][nr], or the float partial sums
+// nl32 [ns32][nb][nr] (added in float64); neither: the local part alone.
 template <typename S>
-__global__ void k_gamma_unpack(int npw, int nb, const double2* __restrict__ F, int scaled, S* __restrict__ y) {
+__global__ void k_gamma_unpack(int npw, int nb, const double2* __restrict__ F, int scaled,
+                               const double* __restrict__ nl64, const float* __restrict__ nl32, int ns32,
+                               S* __restrict__ y) {
   const int nh = (npw + 1) / 2, i0 = nh - 1;
+  const size_t nr = 2 * (size_t)nh;
   const int q = blockIdx.y;
   const int a = 2 * q, b = 2 * q + 1;
   const double2* Fq = F + (size_t)q * npw;
@@ -95,24 +100,142 @@ __global__ void k_gamma_unpack(int npw, int nb, const double2* __restrict__ F, i
       ya.x *= kSqrt2; ya.y *= kSqrt2;
       yb.x *= kSqrt2; yb.y *= kSqrt2;
     }
+    if (nl64 || nl32) {
+      // the nonlocal term is in real-basis coordinates: 1/sqrt2 for coefficients at G != 0
+      const double sn = (!scaled && h > 0) ? kInvSqrt2 : 1.0;
+      double na0 = 0.0, na1 = 0.0, nb0 = 0.0, nb1 = 0.0;
+      const size_t ia = (size_t)a * nr + 2 * h, ib = (size_t)b * nr + 2 * h;
+      if (nl64) {
+        na0 = nl64[ia];
+        na1 = nl64[ia + 1];
+        if (b < nb) {
+          nb0 = nl64[ib];
+          nb1 = nl64[ib + 1];
+        }
+      } else {
+        const size_t plane = (size_t)nb * nr;
+        for (int sp = 0; sp < ns32; ++sp) {
+          const float2 va = *reinterpret_cast<const float2*>(nl32 + sp * plane + ia);
+          na0 += (double)va.x;
+          na1 += (double)va.y;
+          if (b < nb) {
+            const float2 vb = *reinterpret_cast<const float2*>(nl32 + sp * plane + ib);
+            nb0 += (double)vb.x;
+            nb1 += (double)vb.y;
+          }
+        }
+      }
+      ya.x = fma(sn, na0, ya.x);
+      ya.y = fma(sn, na1, ya.y);
+      yb.x = fma(sn, nb0, yb.x);
+      yb.y = fma(sn, nb1, yb.y);
+    }
     st2(y + (size_t)a * nh + h, ya);
     if (b < nb) st2(y + (size_t)b * nh + h, yb);
   }
 }
 
+// The projectors rephased by w_q = conj(sqrt(u_q)), so that beta'(-G) = conj(beta'(G)), in
+// real-basis coordinates [P][2 nh].
+__global__ void k_gamma_betar(int npw, const double2* __restrict__ beta, const double2* __restrict__ wph,
+                              double* __restrict__ betar) {
+  const int nh = (npw + 1) / 2, i0 = nh - 1;
+  const int q = blockIdx.y;
+  const double2 w = wph[q];
+  const double2* bq = beta + (size_t)q * npw;
+  double* out = betar + (size_t)q * 2 * nh;
+  for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < nh; h += gridDim.x * blockDim.x) {
+    const double2 b = bq[i0 + h];
+    double re = w.x * b.x - w.y * b.y, im = w.x * b.y + w.y * b.x;
+    if (h == 0) {
+      im = 0.0;   // beta'(0) is real
+    } else {
+      re *= kSqrt2;
+      im *= kSqrt2;
+    }
+    out[2 * h] = re;
+    out[2 * h + 1] = im;
+  }
+}
+
+// D'_pq = conj(w_p) D_pq w_q on D's CSR pattern (real when the Gamma form applies)
+__global__ void k_gamma_dreal(int nproj, const int* __restrict__ rowptr, const int* __restrict__ col,
+                              const double2* __restrict__ dval, const double2* __restrict__ wph,
+                              double* __restrict__ dvalr) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nproj) return;
+  const double2 wp = wph[p];
+  for (int e = rowptr[p]; e < rowptr[p + 1]; ++e) {
+    const double2 d = dval[e], wq = wph[col[e]];
+    const double ax = wp.x * d.x + wp.y * d.y, ay = wp.x * d.y - wp.y * d.x;   // conj(w_p) D_pq
+    dvalr[e] = ax * wq.x - ay * wq.y;
+  }
+}
+
 int grid_x(size_t n) { return (int)std::min<size_t>(1024, (n + 255) / 256); }
+
+// Build the rephased projectors and D' of problem p on first use (and their bf16 terms for a mixed
+// context).
+int gamma_nl_prepare(Context& c, Problem& p) {
+  const int P = p.nproj;
+  if (P == 0) return HPSI_OK;
+  if (!p.d_betar) {
+    if ((int)p.gamma_u.size() != P) return fail(c, HPSI_EINVAL, "Gamma-form projector phases are missing");
+    std::vector<double2> w(P);
+    for (int q = 0; q < P; ++q) {
+      const double th = std::atan2(p.gamma_u[q].y, p.gamma_u[q].x);
+      w[q] = make_double2(std::cos(0.5 * th), -std::sin(0.5 * th));
+    }
+    const int nr = 2 * ((p.npw + 1) / 2);
+    double2* dw = nullptr;
+    if (cudaMalloc((void**)&p.d_betar, sizeof(double) * (size_t)P * nr) != cudaSuccess ||
+        cudaMalloc((void**)&p.d_dvalr, sizeof(double) * (size_t)std::max(1, p.nnz)) != cudaSuccess ||
+        cudaMalloc((void**)&dw, sizeof(double2) * P) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(p.d_betar);
+      cudaFree(p.d_dvalr);
+      p.d_betar = nullptr;
+      p.d_dvalr = nullptr;
+      return fail(c, HPSI_ENOMEM, "device allocation of the Gamma-form projectors failed");
+    }
+    cudaError_t e = cudaMemcpyAsync(dw, w.data(), sizeof(double2) * P, cudaMemcpyHostToDevice, c.stream);
+    if (e == cudaSuccess) {
+      HPSI_LAUNCH(c, HPSI_K_GAMMA, (k_gamma_betar<<<dim3(grid_x((p.npw + 1) / 2), P), 256, 0, c.stream>>>(
+                                       p.npw, p.d_beta, dw, p.d_betar)));
+      if (p.nnz)
+        HPSI_LAUNCH(c, HPSI_K_GAMMA, (k_gamma_dreal<<<(P + 127) / 128, 128, 0, c.stream>>>(
+                                         P, p.d_rowptr, p.d_col, p.d_dval, dw, p.d_dvalr)));
+      e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+    }
+    cudaFree(dw);
+    if (e != cudaSuccess) {
+      cudaFree(p.d_betar);
+      cudaFree(p.d_dvalr);
+      p.d_betar = nullptr;
+      p.d_dvalr = nullptr;
+      return cuda_fail(c, e, "Gamma-form projector setup");
+    }
+  }
+  if (c.precision == HPSI_MIXED) return gamma_prepare_tc(c, p);
+  return HPSI_OK;
+}
 
 }  // namespace
 
 // y = H x for nb real orbitals in half-sphere storage (S = double2 or float2 elements, nh per
-// band); scaled: real-basis coordinates in and out.  Counts nb band-applications.
+// band); scaled: real-basis coordinates in and out.  The local term runs on packed pairs of bands
+// through the complex transforms; the nonlocal term runs on the real coordinates (half the work of
+// the packed complex form) and is added while unpacking.  Counts nb band-applications.
 template <typename S>
 static int gamma_apply_t(Context& c, int ik, const S* x, S* y, int nb, bool scaled) {
-  const Problem& p = c.probs[ik];
+  Problem& p = c.probs[ik];
   if (nb == 0) return HPSI_OK;
+  int rc = gamma_nl_prepare(c, p);
+  if (rc) return rc;
   const int npairs = (nb + 1) / 2;
   const size_t bytes = sizeof(double2) * (size_t)npairs * p.npw;
-  int rc = ensure_buffer(c, &c.ws.gin, &c.ws.ginbytes, bytes);
+  rc = ensure_buffer(c, &c.ws.gin, &c.ws.ginbytes, bytes);
   if (rc) return rc;
   rc = ensure_buffer(c, &c.ws.gout, &c.ws.goutbytes, bytes);
   if (rc) return rc;
@@ -120,12 +243,28 @@ static int gamma_apply_t(Context& c, int ik, const S* x, S* y, int nb, bool scal
   double2* F = static_cast<double2*>(c.ws.gout);
   HPSI_LAUNCH(c, HPSI_K_GAMMA, (k_gamma_pack<S><<<dim3(grid_x(p.npw), npairs), 256, 0, c.stream>>>(
                                    p.npw, nb, x, scaled ? 1 : 0, f)));
-  const long long b0 = c.band_apps;
-  rc = apply_device(c, ik, f, F, npairs);
+  rc = local_apply(c, p, f, F, npairs);
   if (rc) return rc;
-  c.band_apps = b0 + nb;
+  const double* nl64 = nullptr;
+  const float* nl32 = nullptr;
+  int ns32 = 0;
+  if (p.nproj > 0) {
+    constexpr bool x32 = sizeof(S) == sizeof(float2);
+    if (cur_prec(c) == HPSI_FP64) {
+      const int nr = 2 * ((p.npw + 1) / 2);
+      rc = ensure_buffer(c, &c.ws.gnl, &c.ws.gnlbytes, sizeof(double) * (size_t)nb * nr);
+      if (rc) return rc;
+      double* out = static_cast<double*>(c.ws.gnl);
+      rc = gamma_nonlocal_fp64(c, p, x, x32, nb, scaled, out);
+      nl64 = out;
+    } else {
+      rc = gamma_nonlocal_mixed(c, p, x, x32, nb, scaled, &nl32, &ns32);
+    }
+    if (rc) return rc;
+  }
+  c.band_apps += nb;
   HPSI_LAUNCH(c, HPSI_K_GAMMA, (k_gamma_unpack<S><<<dim3(grid_x((p.npw + 1) / 2), npairs), 256, 0, c.stream>>>(
-                                   p.npw, nb, F, scaled ? 1 : 0, y)));
+                                   p.npw, nb, F, scaled ? 1 : 0, nl64, nl32, ns32, y)));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(c, e, "gamma pack / unpack kernels");
   return HPSI_OK;
@@ -529,13 +668,15 @@ int GammaDavidson<T>::alloc(int N) {
 // Lowest nwant eigenpairs of the symmetric leading n x n block of a (ld lda), float64: values in
 // w.wv, vectors in the first nwant columns of w.evec (ld n).  The library's real eigensolver
 // (HPSI_OPT_EIGENSOLVER = 1), cuSOLVER dsyevdx where it does not apply or hands the problem back.
+// A float32 basis takes the vectors to float32 accuracy (they rotate float32 vectors), the values
+// always to float64.
 template <typename T>
 int GammaDavidson<T>::eig_lowest(const double* a, int lda, int n, int nwant) {
   Context& c = c_;
   GamWork& w = w_;
   if (c.eigensolver == 1) {
     bool fallback = false;
-    const int rc = eigh_lowest_real(c, a, lda, n, nwant, w.wv, w.evec, &fallback);
+    const int rc = eigh_lowest_real(c, a, lda, n, nwant, w.wv, w.evec, &fallback, sizeof(T) == sizeof(float));
     if (rc || !fallback) return rc;
   }
   HPSI_LAUNCH(c, HPSI_K_DAVIDSON,

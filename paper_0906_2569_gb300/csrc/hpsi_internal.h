@@ -82,6 +82,13 @@ struct Problem {
   std::vector<double> vext;        // the potential given at setup, host, layout [n3][n2][n1]
   bool gamma_ok = false;           // the Gamma-point real form applies (gamma.cu)
   std::string gamma_why;           // why not, when it does not
+  std::vector<double2> gamma_u;    // per projector: beta(-G) = u conj(beta(G)) (when gamma_ok)
+  // Gamma form, built on first use: the projectors rephased by conj(sqrt(u)) in real-basis
+  // coordinates [P][2 nh], D in that basis (real, on D's CSR pattern), and (mixed contexts) their
+  // bf16 terms: calbec's A [NT][P][round64(2 nh)], then add_vuspsi's B [NT][2 nh][round64(P)]
+  double* d_betar = nullptr;
+  double* d_dvalr = nullptr;
+  uint16_t* d_betar_bf = nullptr;
 };
 
 struct TwiddleTable {
@@ -104,6 +111,7 @@ struct Workspace {
   void* batch = nullptr; size_t batchbytes = 0;  // stick rows of a batched apply
   void* gin = nullptr; size_t ginbytes = 0;      // Gamma form: packed pairs of real bands, and H of them
   void* gout = nullptr; size_t goutbytes = 0;
+  void* gnl = nullptr; size_t gnlbytes = 0;      // Gamma form: the float64 nonlocal term in real coordinates
   long long epoch = 0;                           // bumped whenever a buffer is reallocated
 };
 
@@ -270,6 +278,14 @@ int gamma_check(Context& c, int ik, const char* who);
 int gamma_davidson_run(Context& c, int ik, int nbnd, double tol, int maxiter, double2* psio, double* eig_out,
                        int* iters_out, double* resnorm_out);
 void gamma_release(Context& c);
+// Nonlocal term of the Gamma form in real-basis coordinates (x: nb bands of nr = 2 nh reals, float
+// or double; scaled = false: half-sphere coefficients, converted on load).  The float64 form writes
+// out[b][r] = sum_p betar[p][r] (D' <betar|x>)[b][p]; the mixed form leaves float partial sums
+// [*nsplit][nb][nr] (to be added in float64) in the mixed workspace and points *part at them.
+int gamma_nonlocal_fp64(Context& c, const Problem& p, const void* x, bool x32, int nb, bool scaled, double* out);
+int gamma_prepare_tc(Context& c, Problem& p);
+int gamma_nonlocal_mixed(Context& c, const Problem& p, const void* x, bool x32, int nb, bool scaled,
+                         const float** part, int* nsplit);
 void scf_release(Context& c);
 void fock_release(Context& c);
 
@@ -312,7 +328,7 @@ void eigh_release(Context& c);
 // n up to 1824 on 152 SMs; *fallback as above.  Vectors to v_out [nwant][n] (column-major, ld n).
 bool eigh_supported_real(const Context& c, int n);
 int eigh_lowest_real(Context& c, const double* a, int lda, int n, int nwant, double* w_out, double* v_out,
-                     bool* fallback);
+                     bool* fallback, bool vec32 = false);
 
 }  // namespace hpsi
 

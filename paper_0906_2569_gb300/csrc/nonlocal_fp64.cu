@@ -223,7 +223,158 @@ __global__ void __launch_bounds__(256) k_addvus64_batch(const __grid_constant__ 
   addvus_tile(a.npw, a.nproj, a.nb, a.w, a.beta, a.hpsi, l % a.gtiles, l / a.gtiles);
 }
 
+// ---- Gamma-point real form (Sec. 4) ----
+// Real orbitals in real-basis coordinates x (nr = 2 nh reals: (c(0), 0) at G = 0, sqrt2 (Re c, Im c)
+// elsewhere) and projectors rephased so that beta'(-G) = conj(beta'(G)), in the same coordinates
+// (betar): <beta'_p|psi> = betar_p . x, D' is real, and V_NL psi has the coordinates
+// sum_p betar_p (D' becp)_p.  Three real GEMMs, half the float64 work of the packed complex form.
+
+constexpr double kSqrt2r = 1.4142135623730950488;
+constexpr int RB_TP = 32;   // projectors per CTA
+constexpr int RB_TB = 32;   // bands per CTA
+constexpr int RB_TK = 64;   // coordinates per shared-memory tile
+
+// part[split][b][p] = sum_{r in split} betar[p][r] x[b][r]; scaled = 0: x holds coefficients and
+// r >= 2 is multiplied by sqrt2 on load
+template <typename R>
+__global__ void __launch_bounds__(256) k_calbec64r(int nr, int nproj, int nb, int kchunk, int scaled,
+                                                   const double* __restrict__ betar, const R* __restrict__ x,
+                                                   double* __restrict__ part) {
+  __shared__ double sb[RB_TP][RB_TK + 1];
+  __shared__ double sx[RB_TB][RB_TK + 1];
+  const int p0 = blockIdx.x * RB_TP, b0 = blockIdx.y * RB_TB, split = blockIdx.z;
+  const int rbeg = split * kchunk, rend = min(nr, rbeg + kchunk);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // tx -> p, ty -> b
+  double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  for (int r0 = rbeg; r0 < rend; r0 += RB_TK) {
+    for (int i = threadIdx.x; i < RB_TP * RB_TK; i += 256) {
+      const int row = i / RB_TK, cc = i % RB_TK, r = r0 + cc;
+      const bool in = r < rend;
+      sb[row][cc] = (p0 + row < nproj && in) ? betar[(size_t)(p0 + row) * nr + r] : 0.0;
+      double v = (b0 + row < nb && in) ? (double)x[(size_t)(b0 + row) * nr + r] : 0.0;
+      if (!scaled && r >= 2) v *= kSqrt2r;
+      sx[row][cc] = v;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < RB_TK; ++kk) {
+      const double a0 = sb[tx][kk], a1 = sb[tx + 16][kk];
+      const double y0 = sx[ty][kk], y1 = sx[ty + 16][kk];
+      acc[0][0] = fma(a0, y0, acc[0][0]);
+      acc[0][1] = fma(a0, y1, acc[0][1]);
+      acc[1][0] = fma(a1, y0, acc[1][0]);
+      acc[1][1] = fma(a1, y1, acc[1][1]);
+    }
+    __syncthreads();
+  }
+  double* out = part + (size_t)split * nb * nproj;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int pp = p0 + tx + 16 * i, b = b0 + ty + 16 * j;
+      if (pp < nproj && b < nb) out[(size_t)b * nproj + pp] = acc[i][j];
+    }
+}
+
+// w[b][p] = sum_{q in row p of D} D'_pq sum_s part[s][b][q]
+__global__ void k_dscale64r(int nproj, int nb, int nsplit, const double* __restrict__ part,
+                            const int* __restrict__ rowptr, const int* __restrict__ col,
+                            const double* __restrict__ val, double* __restrict__ w) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nproj * nb) return;
+  const int b = i / nproj, p = i % nproj;
+  double acc = 0.0;
+  for (int e = rowptr[p]; e < rowptr[p + 1]; ++e) {
+    const int q = col[e];
+    double s = 0.0;
+    for (int sp = 0; sp < nsplit; ++sp) s += part[((size_t)sp * nb + b) * nproj + q];
+    acc = fma(val[e], s, acc);
+  }
+  w[i] = acc;
+}
+
+constexpr int RA_TR = 64;   // coordinates per CTA
+constexpr int RA_TB = 32;   // bands per CTA
+constexpr int RA_TP = 32;   // projectors per shared-memory tile
+
+// out[b][r] = sum_p w[b][p] betar[p][r]
+__global__ void __launch_bounds__(256) k_addvus64r(int nr, int nproj, int nb, const double* __restrict__ w,
+                                                   const double* __restrict__ betar, double* __restrict__ out) {
+  __shared__ double sb[RA_TP][RA_TR];
+  __shared__ double sw[RA_TB][RA_TP + 1];
+  const int r0 = blockIdx.x * RA_TR, b0 = blockIdx.y * RA_TB;
+  const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;   // tx -> r, ty -> bands ty + 4 j
+  double acc[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) acc[j] = 0.0;
+  for (int q0 = 0; q0 < nproj; q0 += RA_TP) {
+    for (int i = threadIdx.x; i < RA_TP * RA_TR; i += 256) {
+      const int row = i / RA_TR, cc = i % RA_TR;
+      const int q = q0 + row, r = r0 + cc;
+      sb[row][cc] = (q < nproj && r < nr) ? betar[(size_t)q * nr + r] : 0.0;
+    }
+    for (int i = threadIdx.x; i < RA_TB * RA_TP; i += 256) {
+      const int row = i / RA_TP, cc = i % RA_TP;
+      const int b = b0 + row, q = q0 + cc;
+      sw[row][cc] = (b < nb && q < nproj) ? w[(size_t)b * nproj + q] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < RA_TP; ++kk) {
+      const double xv = sb[kk][tx];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[j] = fma(sw[ty + 4 * j][kk], xv, acc[j]);
+    }
+    __syncthreads();
+  }
+  const int r = r0 + tx;
+  if (r < nr) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int b = b0 + ty + 4 * j;
+      if (b < nb) out[(size_t)b * nr + r] = acc[j];
+    }
+  }
+}
+
 }  // namespace
+
+int gamma_nonlocal_fp64(Context& c, const Problem& p, const void* x, bool x32, int nb, bool scaled, double* out) {
+  if (p.nproj == 0 || nb == 0) return HPSI_OK;
+  if (!p.d_betar) return fail(c, HPSI_EINVAL, "Gamma-form projectors are not prepared");
+  const int nr = 2 * ((p.npw + 1) / 2);
+  const int tilesp = (p.nproj + RB_TP - 1) / RB_TP, tilesb = (nb + RB_TB - 1) / RB_TB;
+  int nsplit = std::max(1, (3 * c.sm_count) / std::max(1, tilesp * tilesb));
+  int kchunk = (nr + nsplit - 1) / nsplit;
+  kchunk = std::max(RB_TK * 2, ((kchunk + RB_TK - 1) / RB_TK) * RB_TK);
+  nsplit = (nr + kchunk - 1) / kchunk;
+  int rc = ensure_buffer(c, &c.ws.part, &c.ws.partbytes, sizeof(double) * (size_t)nsplit * nb * p.nproj);
+  if (rc) return rc;
+  rc = ensure_buffer(c, &c.ws.w, &c.ws.wbytes, sizeof(double) * (size_t)nb * p.nproj);
+  if (rc) return rc;
+  double* part = static_cast<double*>(c.ws.part);
+  double* w = static_cast<double*>(c.ws.w);
+  const dim3 gc(tilesp, tilesb, nsplit);
+  if (x32)
+    HPSI_LAUNCH(c, HPSI_K_CALBEC, (k_calbec64r<float><<<gc, 256, 0, c.stream>>>(
+                                      nr, p.nproj, nb, kchunk, scaled ? 1 : 0, p.d_betar,
+                                      static_cast<const float*>(x), part)));
+  else
+    HPSI_LAUNCH(c, HPSI_K_CALBEC, (k_calbec64r<double><<<gc, 256, 0, c.stream>>>(
+                                      nr, p.nproj, nb, kchunk, scaled ? 1 : 0, p.d_betar,
+                                      static_cast<const double*>(x), part)));
+  const int n = p.nproj * nb;
+  HPSI_LAUNCH(c, HPSI_K_DSCALE,
+              (k_dscale64r<<<(n + 255) / 256, 256, 0, c.stream>>>(p.nproj, nb, nsplit, part, p.d_rowptr, p.d_col,
+                                                                  p.d_dvalr, w)));
+  HPSI_LAUNCH(c, HPSI_K_ADDVUS,
+              (k_addvus64r<<<dim3((nr + RA_TR - 1) / RA_TR, (nb + RA_TB - 1) / RA_TB), 256, 0, c.stream>>>(
+                  nr, p.nproj, nb, w, p.d_betar, out)));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "Gamma-form float64 nonlocal kernels launch");
+  return HPSI_OK;
+}
 
 int nonlocal_apply_fp64(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd) {
   if (p.nproj == 0 || nbnd == 0) return HPSI_OK;

@@ -467,6 +467,71 @@ __global__ void k_inner_reduce(int M, int nb, int nsplit, const float* __restric
   }
 }
 
+// ---- Gamma-point real form: operands ------------------------------------------------------------
+
+// B of add_vuspsi in the real form: row r (real-basis coordinate), column k = projector (K padded
+// to ka): betar[k][r].  Setup only.
+template <int NT>
+__global__ void k_split_betar_add(int nproj, int nr, int ka, const double* __restrict__ betar,
+                                  __nv_bfloat16* __restrict__ out) {
+  const size_t plane = (size_t)nr * ka;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < plane; i += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(i / ka), k = (int)(i % ka);
+    split_store<NT>(k < nproj ? betar[(size_t)k * nr + r] : 0.0, out, plane, i);
+  }
+}
+
+// B of calbec in the real form: row b = x_b (nr real coordinates, K padded to kc with zeros);
+// scaled = 0: x holds coefficients and r >= 2 is multiplied by sqrt2.  One thread per pair of
+// coordinates.
+template <int NT, typename R>
+__global__ void k_split_xr(int nb, int nr, int kc, int scaled, const R* __restrict__ x,
+                           __nv_bfloat16* __restrict__ out) {
+  const size_t plane = (size_t)nb * kc;
+  const int half = kc / 2;
+  const size_t n = (size_t)nb * half;
+  __nv_bfloat162* o2 = reinterpret_cast<__nv_bfloat162*>(out);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(i / half), h = (int)(i - (size_t)b * half);
+    double r0 = 0.0, r1 = 0.0;
+    if (2 * h < nr) {
+      r0 = (double)x[(size_t)b * nr + 2 * h];
+      r1 = (double)x[(size_t)b * nr + 2 * h + 1];
+      if (!scaled && h > 0) {
+        r0 *= 1.4142135623730950488;
+        r1 *= 1.4142135623730950488;
+      }
+    }
+    const size_t at = (size_t)b * half + h;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const __nv_bfloat16 h0 = __float2bfloat16_rn((float)r0), h1 = __float2bfloat16_rn((float)r1);
+      o2[t * (plane / 2) + at] = __halves2bfloat162(h0, h1);
+      r0 -= (double)__bfloat162float(h0);
+      r1 -= (double)__bfloat162float(h1);
+    }
+  }
+}
+
+// w[b][p] = sum_q D'_pq becp[q][b] with becp from the float partials [split][P][nb] (summed in
+// float64), written as the bf16 terms of A of the real add_vuspsi (row b, K = projector, pad ka).
+template <int NT>
+__global__ void k_dscale_tc_r(int nproj, int nb, int nsplit, int ka, const float* __restrict__ part,
+                              const int* __restrict__ rowptr, const int* __restrict__ col,
+                              const double* __restrict__ val, __nv_bfloat16* __restrict__ wa) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nproj * nb) return;
+  const int b = i / nproj, p = i % nproj;
+  double acc = 0.0;
+  for (int e = rowptr[p]; e < rowptr[p + 1]; ++e) {
+    const int q = col[e];
+    double sq = 0.0;
+    for (int s = 0; s < nsplit; ++s) sq += (double)part[((size_t)s * nproj + q) * nb + b];
+    acc = fma(val[e], sq, acc);
+  }
+  split_store<NT>(acc, wa, (size_t)nb * ka, (size_t)b * ka + p);
+}
+
 // ---- host side ------------------------------------------------------------------------------
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -654,7 +719,96 @@ int apply_t(Context& c, const Problem& p, const double2* psi, double2* hpsi, int
   return HPSI_OK;
 }
 
+template <int NT>
+int gamma_prepare_t(Context& c, Problem& p) {
+  const int P = p.nproj, nh = (p.npw + 1) / 2, nr = 2 * nh;
+  const int kc = round_up(nr, TBK), ka = round_up(P, TBK);
+  const size_t cal = (size_t)NT * P * kc, add = (size_t)NT * nr * ka;
+  cudaError_t e = cudaMalloc((void**)&p.d_betar_bf, sizeof(__nv_bfloat16) * (cal + add));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    p.d_betar_bf = nullptr;
+    return fail(c, HPSI_ENOMEM, "device allocation of the Gamma-form bf16 projector terms failed");
+  }
+  __nv_bfloat16* base = reinterpret_cast<__nv_bfloat16*>(p.d_betar_bf);
+  // calbec's A: the rows of betar read as interleaved pairs (nh pairs of a 2 nh row)
+  HPSI_LAUNCH(c, HPSI_K_SPLIT, (k_split_beta_cal<NT><<<4 * c.sm_count, 256, 0, c.stream>>>(
+                                   P, nh, kc, reinterpret_cast<const double2*>(p.d_betar), base)));
+  HPSI_LAUNCH(c, HPSI_K_SPLIT,
+              (k_split_betar_add<NT><<<4 * c.sm_count, 256, 0, c.stream>>>(P, nr, ka, p.d_betar, base + cal)));
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "Gamma-form bf16 projector split");
+  return HPSI_OK;
+}
+
+template <int NT, typename R>
+int gamma_apply_tc(Context& c, const Problem& p, const R* x, int nb, bool scaled, int kmax, const float** out,
+                   int* nout) {
+  const int P = p.nproj, nr = 2 * ((p.npw + 1) / 2);
+  const int kc = round_up(nr, TBK), ka = round_up(P, TBK);
+  const __nv_bfloat16* bcal = reinterpret_cast<const __nv_bfloat16*>(p.d_betar_bf);
+  const __nv_bfloat16* badd = bcal + (size_t)NT * P * kc;
+  const int nks = kc / TBK;
+  const int tiles = ((nb + TBN - 1) / TBN) * ((P + TBM - 1) / TBM);
+  int nsplit = std::max(1, std::min(nks, (2 * c.sm_count + tiles - 1) / tiles));
+  int ksplit = std::min((nks + nsplit - 1) / nsplit, kmax);
+  nsplit = (nks + ksplit - 1) / ksplit;
+  const int naks = ka / TBK;
+  const int aksplit = (naks + (naks + kAddKsteps - 1) / kAddKsteps - 1) / ((naks + kAddKsteps - 1) / kAddKsteps);
+  const int ansplit = (naks + aksplit - 1) / aksplit;
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t xb = al(sizeof(__nv_bfloat16) * (size_t)NT * nb * kc);
+  const size_t pb = al(sizeof(float) * (size_t)nsplit * P * nb);
+  const size_t wb = al(sizeof(__nv_bfloat16) * (size_t)NT * nb * ka);
+  const size_t ab = al(sizeof(float) * (size_t)ansplit * nb * nr);
+  int rc = ensure_buffer(c, &c.ws.mixed, &c.ws.mixedbytes, xb + pb + wb + ab);
+  if (rc) return rc;
+  unsigned char* w0 = static_cast<unsigned char*>(c.ws.mixed);
+  __nv_bfloat16* xs = reinterpret_cast<__nv_bfloat16*>(w0);
+  float* part = reinterpret_cast<float*>(w0 + xb);
+  __nv_bfloat16* wa = reinterpret_cast<__nv_bfloat16*>(w0 + xb + pb);
+  float* apart = reinterpret_cast<float*>(w0 + xb + pb + wb);
+  cudaError_t e0 = cudaMemsetAsync(wa, 0, wb, c.stream);   // the K padding of w
+  if (e0 != cudaSuccess) return cuda_fail(c, e0, "workspace clear");
+  HPSI_LAUNCH(c, HPSI_K_SPLIT,
+              (k_split_xr<NT, R><<<8 * c.sm_count, 256, 0, c.stream>>>(nb, nr, kc, scaled ? 1 : 0, x, xs)));
+  rc = launch_gemm<NT>(c, bcal, P, xs, nb, kc, nsplit, ksplit, 0, part, nullptr, 0, HPSI_K_CALBEC);
+  if (rc) return rc;
+  const int n = P * nb;
+  HPSI_LAUNCH(c, HPSI_K_DSCALE,
+              (k_dscale_tc_r<NT><<<(n + 255) / 256, 256, 0, c.stream>>>(P, nb, nsplit, ka, part, p.d_rowptr, p.d_col,
+                                                                        p.d_dvalr, wa)));
+  rc = launch_gemm<NT>(c, wa, nb, badd, nr, ka, ansplit, aksplit, 0, apart, nullptr, 0, HPSI_K_ADDVUS);
+  if (rc) return rc;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "Gamma-form tensor-core nonlocal kernels launch");
+  *out = apart;
+  *nout = ansplit;
+  return HPSI_OK;
+}
+
 }  // namespace
+
+int gamma_prepare_tc(Context& c, Problem& p) {
+  if (p.nproj == 0 || p.d_betar_bf) return HPSI_OK;
+  int rc = get_encoder(c);
+  if (rc) return rc;
+  return c.nl_terms == 3 ? gamma_prepare_t<3>(c, p) : gamma_prepare_t<2>(c, p);
+}
+
+int gamma_nonlocal_mixed(Context& c, const Problem& p, const void* x, bool x32, int nb, bool scaled,
+                         const float** part, int* nsplit) {
+  *part = nullptr;
+  *nsplit = 0;
+  if (p.nproj == 0 || nb == 0) return HPSI_OK;
+  if (!p.d_betar_bf) return fail(c, HPSI_EINVAL, "Gamma-form bf16 projector terms are not prepared");
+  const int kmax = c.tc_kmax > 0 ? c.tc_kmax : (p.nl_kmax > 0 ? p.nl_kmax : kCalbecKsteps);
+  if (c.nl_terms == 3)
+    return x32 ? gamma_apply_tc<3, float>(c, p, static_cast<const float*>(x), nb, scaled, kmax, part, nsplit)
+               : gamma_apply_tc<3, double>(c, p, static_cast<const double*>(x), nb, scaled, kmax, part, nsplit);
+  return x32 ? gamma_apply_tc<2, float>(c, p, static_cast<const float*>(x), nb, scaled, kmax, part, nsplit)
+             : gamma_apply_tc<2, double>(c, p, static_cast<const double*>(x), nb, scaled, kmax, part, nsplit);
+}
 
 // Launch the bounded-wait self-test (about 2e6 cycles, ~1 ms).
 int wait_selftest(Context& c) {

@@ -108,6 +108,70 @@ def test_gamma_apply_mixed_terms(lib):
     ctx.close()
 
 
+def _coupled_d(nat, seed, scale=0.3):
+    """A dense Hermitian D that couples every projector pair and still allows the real form: real
+    symmetric between projectors of the same parity under G -> -G (s with s, p with p), imaginary
+    antisymmetric between s and p (whose beta(-G) = -conj(beta(G)))."""
+    rng = np.random.default_rng(seed)
+    P = 4 * nat
+    odd = np.array([k % 4 != 0 for k in range(P)])
+    a = rng.standard_normal((P, P))
+    b = rng.standard_normal((P, P))
+    cross = odd[:, None] != odd[None, :]
+    return scale * np.where(cross, 1j * (b - b.T) / 2, (a + a.T) / 2 + 0j)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_gamma_apply_coupled_d(lib, precision):
+    """Projectors with beta(-G) = -conj(beta(G)) (p-type) coupled to s-type ones through a dense D:
+    the real form rephases them, and D in the rephased basis has real off-diagonal entries.  H on
+    half storage against the oracle (float64: 1e-12; mixed: (H - T) psi element by element, 1e-5)."""
+    import torch
+    from paper_0906_2569_gb300 import binding as B
+    p = workloads.config1()
+    k = p.kpts[0]
+    m = B.hpsi_gsphere(p.lattice, p.ecut, k)
+    vr = workloads.vloc_r(p.lattice, p.atoms, p.fft)
+    beta = workloads.beta(p.lattice, p.atoms, k, m)
+    d = _coupled_d(len(p.atoms), 5)
+    ctx = B.hpsi_setup(p.lattice, p.ecut, [k], p.fft, vr, [beta], d, precision, torch.cuda.current_stream().cuda_stream)
+    half = _half_block(m, 7, 77)
+    got = _apply(ctx, half)
+    ref = _oracle_gamma(p, m, vr, beta, d, half)
+    if precision == 0:
+        err = _maxrel(got, ref)
+        assert err < 1e-12
+    else:
+        t = oracle.gamma.to_half(oracle.gsphere.kinetic(p.lattice, k, m)[None, :], m) * half
+        err = _maxrel(got - t, ref - t)
+        assert err < 1e-5
+    print(f"Gamma coupled D, precision {precision}: max-element error {err:.2e}")
+    assert np.all(got[:, 0].imag == 0.0)
+    ctx.close()
+
+
+def test_gamma_davidson_coupled_d(lib):
+    """Float64 Davidson on real orbitals with the coupled D reaches the eigenvalues of the complex
+    form's Davidson on the same problem (1e-10 Ha)."""
+    import torch
+    from paper_0906_2569_gb300 import binding as B
+    p = workloads.config1()
+    k = p.kpts[0]
+    m = B.hpsi_gsphere(p.lattice, p.ecut, k)
+    vr = workloads.vloc_r(p.lattice, p.atoms, p.fft)
+    beta = workloads.beta(p.lattice, p.atoms, k, m)
+    d = _coupled_d(len(p.atoms), 9)
+    ctx = B.hpsi_setup(p.lattice, p.ecut, [k], p.fft, vr, [beta], d, B.HPSI_FP64,
+                       torch.cuda.current_stream().cuda_stream)
+    psi = workloads.psi0(p.lattice, k, m, p.nbnd, p.psi_seed)
+    xg = torch.from_numpy(np.ascontiguousarray(oracle.gamma.to_half(psi, m))).cuda()
+    eg, _, _, _ = B.davidson_solve_gamma(ctx, 0, xg, 1e-9, 300)
+    xc = torch.from_numpy(np.ascontiguousarray(psi)).cuda()
+    ec, _, _, _ = B.davidson_solve(ctx, 0, xc, 1e-9, 300)
+    assert np.max(np.abs(eg - ec)) < 1e-10
+    ctx.close()
+
+
 @pytest.mark.parametrize("cfg,precision,tol,bound", [("c1", 0, 1e-8, 1e-10), ("c2", 0, 1e-8, 1e-10),
                                                      ("c2", 1, 1e-5, 1e-6)])
 def test_gamma_davidson(lib, cfg, precision, tol, bound):
