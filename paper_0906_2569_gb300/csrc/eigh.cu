@@ -302,12 +302,22 @@ __global__ void k_eh_vscale(int n, const double2* __restrict__ vscale, double2* 
 }
 
 // status[0] = 1 when some |G_ij - delta_ij| exceeds tol (G = Z^T Z, nwant x nwant)
-__global__ void k_eh_orthcheck(int nw, const double* __restrict__ G, double tol, int* __restrict__ status) {
+template <typename T>
+__global__ void k_eh_orthcheck(int nw, const T* __restrict__ G, double tol, int* __restrict__ status) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nw * nw) return;
-  const double g = G[i] - ((i % nw) == (i / nw) ? 1.0 : 0.0);
+  const double g = (double)G[i] - ((i % nw) == (i / nw) ? 1.0 : 0.0);
   if (!(fabs(g) <= tol)) atomicExch(status, 1);
 }
+
+// out = in, element type converted (grid-stride)
+template <typename A, typename B>
+__global__ void k_eh_cvt(size_t n, const A* __restrict__ in, B* __restrict__ out) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (B)in[i];
+}
+
+inline int cvt_grid(size_t n) { return (int)std::min<size_t>(4096, (n + 255) / 256); }
 
 // x = z (real eigenvectors of T into the complex output, column-major, leading dim n)
 __global__ void k_eh_widen(int n, int nwant, const double* __restrict__ Z, double2* __restrict__ X) {
@@ -672,7 +682,7 @@ int eigh_lowest(Context& c, const double2* a, int lda, int n, int nwant, double*
       CUBLAS_STATUS_SUCCESS)
     return fail(c, HPSI_ECUDA, "eigh_lowest: Gram matrix of the eigenvectors failed");
   HPSI_LAUNCH(c, HPSI_K_EIGH,
-              (k_eh_orthcheck<<<(nwant * nwant + 255) / 256, 256, 0, c.stream>>>(nwant, s->gram, 1e-4, s->info)));
+              (k_eh_orthcheck<double><<<(nwant * nwant + 255) / 256, 256, 0, c.stream>>>(nwant, s->gram, 1e-4, s->info)));
   if (cudaMemcpyAsync(s->Z2, s->Z, sizeof(double) * (size_t)n * nwant, cudaMemcpyDeviceToDevice, c.stream) !=
           cudaSuccess ||
       cublasDgemm(s->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, nwant, nwant, &mhalf, s->Z, n, s->gram, nwant, &three_half,
@@ -731,8 +741,12 @@ bool eigh_supported_real(const Context& c, int n) {
 // The same four steps for a real symmetric matrix (float64, column-major, upper triangle read):
 // real Householder reduction, multisection and inverse iteration on T, real compact-WY
 // back-transformation by DGEMMs.  Eigenvectors go to v_out [nwant][n] (column-major, ld n).
+// vec32: the eigenvectors are wanted to float32 accuracy only (a float32 basis is rotated by them),
+// so their Gram matrix, the Newton-Schulz step and the back-transformation run as float32 GEMMs on
+// float32 copies (FP32 throughput is ~64x FP64 on GB300); the reduction, the eigenvalues and the
+// inverse iteration stay float64.
 int eigh_lowest_real(Context& c, const double* a, int lda, int n, int nwant, double* w_out, double* v_out,
-                     bool* fallback) {
+                     bool* fallback, bool vec32) {
   *fallback = false;
   if (n < 1 || nwant < 1 || nwant > n || lda < n) return fail(c, HPSI_EINVAL, "eigh_lowest_real: bad sizes");
   if (!eigh_supported_real(c, n)) {
@@ -796,17 +810,38 @@ int eigh_lowest_real(Context& c, const double* a, int lda, int n, int nwant, dou
   HPSI_LAUNCH(c, HPSI_K_EIGH,
               (k_eh_invit<<<nwant, 32, ismem, c.stream>>>(n, s->d, s->e, nwant, s->lam, s->Z, s->info + 1)));
   const double one = 1.0, zero = 0.0, mone = -1.0, mhalf = -0.5, three_half = 1.5;
-  if (cublasDgemm(s->blas, CUBLAS_OP_T, CUBLAS_OP_N, nwant, nwant, n, &one, s->Z, n, s->Z, n, &zero, s->gram, nwant) !=
-      CUBLAS_STATUS_SUCCESS)
-    return fail(c, HPSI_ECUDA, "eigh_lowest_real: Gram matrix of the eigenvectors failed");
-  HPSI_LAUNCH(c, HPSI_K_EIGH,
-              (k_eh_orthcheck<<<(nwant * nwant + 255) / 256, 256, 0, c.stream>>>(nwant, s->gram, 1e-4, s->info)));
-  // Newton-Schulz step straight into the output: v_out = Z (3 I - Z^T Z) / 2
-  if (cudaMemcpyAsync(v_out, s->Z, sizeof(double) * (size_t)n * nwant, cudaMemcpyDeviceToDevice, c.stream) !=
-          cudaSuccess ||
-      cublasDgemm(s->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, nwant, nwant, &mhalf, s->Z, n, s->gram, nwant, &three_half,
-                  v_out, n) != CUBLAS_STATUS_SUCCESS)
-    return fail(c, HPSI_ECUDA, "eigh_lowest_real: Newton-Schulz step failed");
+  const size_t nz = (size_t)n * nwant;
+  // float32 copies (vec32) live in the unused halves of the buffers sized for the complex solver:
+  // Z and the Newton-Schulz output in Z2, the Gram matrix in gram, the reflectors and T factors
+  // behind their float64 forms, the compact-WY products in w1 and w2
+  float* zf = reinterpret_cast<float*>(s->Z2);
+  float* vf = zf + nz;
+  float* gf = reinterpret_cast<float*>(s->gram);
+  if (vec32) {
+    const float f1 = 1.f, f0 = 0.f, fmhalf = -0.5f, f3half = 1.5f;
+    HPSI_LAUNCH(c, HPSI_K_EIGH, (k_eh_cvt<double, float><<<cvt_grid(nz), 256, 0, c.stream>>>(nz, s->Z, zf)));
+    if (cublasSgemm(s->blas, CUBLAS_OP_T, CUBLAS_OP_N, nwant, nwant, n, &f1, zf, n, zf, n, &f0, gf, nwant) !=
+        CUBLAS_STATUS_SUCCESS)
+      return fail(c, HPSI_ECUDA, "eigh_lowest_real: Gram matrix of the eigenvectors failed");
+    HPSI_LAUNCH(c, HPSI_K_EIGH,
+                (k_eh_orthcheck<float><<<(nwant * nwant + 255) / 256, 256, 0, c.stream>>>(nwant, gf, 1e-4, s->info)));
+    if (cudaMemcpyAsync(vf, zf, sizeof(float) * nz, cudaMemcpyDeviceToDevice, c.stream) != cudaSuccess ||
+        cublasSgemm(s->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, nwant, nwant, &fmhalf, zf, n, gf, nwant, &f3half, vf, n) !=
+            CUBLAS_STATUS_SUCCESS)
+      return fail(c, HPSI_ECUDA, "eigh_lowest_real: Newton-Schulz step failed");
+  } else {
+    if (cublasDgemm(s->blas, CUBLAS_OP_T, CUBLAS_OP_N, nwant, nwant, n, &one, s->Z, n, s->Z, n, &zero, s->gram,
+                    nwant) != CUBLAS_STATUS_SUCCESS)
+      return fail(c, HPSI_ECUDA, "eigh_lowest_real: Gram matrix of the eigenvectors failed");
+    HPSI_LAUNCH(c, HPSI_K_EIGH,
+                (k_eh_orthcheck<double><<<(nwant * nwant + 255) / 256, 256, 0, c.stream>>>(nwant, s->gram, 1e-4,
+                                                                                          s->info)));
+    // Newton-Schulz step straight into the output: v_out = Z (3 I - Z^T Z) / 2
+    if (cudaMemcpyAsync(v_out, s->Z, sizeof(double) * nz, cudaMemcpyDeviceToDevice, c.stream) != cudaSuccess ||
+        cublasDgemm(s->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, nwant, nwant, &mhalf, s->Z, n, s->gram, nwant, &three_half,
+                    v_out, n) != CUBLAS_STATUS_SUCCESS)
+      return fail(c, HPSI_ECUDA, "eigh_lowest_real: Newton-Schulz step failed");
+  }
   // 4. back-transformation, one compact-WY block of kWY reflectors at a time from the last
   if (n > 1) {
     HPSI_LAUNCH(c, HPSI_K_EIGH, (k_eh_vscale_r<<<dim3((n + 255) / 256, n - 1), 256, 0, c.stream>>>(n, vscale, vref)));
@@ -817,7 +852,28 @@ int eigh_lowest_real(Context& c, const double* a, int lda, int n, int nwant, dou
       return fail(c, HPSI_ECUDA, "eigh_lowest_real: reflector Gram matrices failed");
     const size_t tsm = sizeof(double) * (size_t)kWY * (kWY - 1) / 2;
     HPSI_LAUNCH(c, HPSI_K_EIGH, (k_eh_tfactor_r<<<dim3(kWY / 4, K), 128, tsm, c.stream>>>(wgram, tau, tfac)));
-    for (int k = K - 1; k >= 0; --k) {
+    if (vec32) {
+      const size_t nv = (size_t)K * kWY * n, nt = (size_t)K * kWY * kWY;
+      float* vr32 = reinterpret_cast<float*>(vref + (size_t)(n + kWY) * n);
+      float* tf32 = reinterpret_cast<float*>(tfac + nt);
+      float* w1f = reinterpret_cast<float*>(w1);
+      float* w2f = reinterpret_cast<float*>(w2);
+      HPSI_LAUNCH(c, HPSI_K_EIGH, (k_eh_cvt<double, float><<<cvt_grid(nv), 256, 0, c.stream>>>(nv, vref, vr32)));
+      HPSI_LAUNCH(c, HPSI_K_EIGH, (k_eh_cvt<double, float><<<cvt_grid(nt), 256, 0, c.stream>>>(nt, tfac, tf32)));
+      const float f1 = 1.f, f0 = 0.f, fm1 = -1.f;
+      for (int k = K - 1; k >= 0; --k) {
+        const int r0 = k * kWY + 1, m = n - r0;
+        const float* V = vr32 + (size_t)k * kWY * n + r0;
+        if (cublasSgemm(s->blas, CUBLAS_OP_T, CUBLAS_OP_N, kWY, nwant, m, &f1, V, n, vf + r0, n, &f0, w1f, kWY) !=
+                CUBLAS_STATUS_SUCCESS ||
+            cublasSgemm(s->blas, CUBLAS_OP_N, CUBLAS_OP_N, kWY, nwant, kWY, &f1, tf32 + (size_t)k * kWY * kWY, kWY,
+                        w1f, kWY, &f0, w2f, kWY) != CUBLAS_STATUS_SUCCESS ||
+            cublasSgemm(s->blas, CUBLAS_OP_N, CUBLAS_OP_N, m, nwant, kWY, &fm1, V, n, w2f, kWY, &f1, vf + r0, n) !=
+                CUBLAS_STATUS_SUCCESS)
+          return fail(c, HPSI_ECUDA, "eigh_lowest_real: back-transformation GEMM failed");
+      }
+    }
+    for (int k = vec32 ? -1 : K - 1; k >= 0; --k) {
       const int r0 = k * kWY + 1, m = n - r0;
       double* V = vref + (size_t)k * kWY * n + r0;
       if (cublasDgemm(s->blas, CUBLAS_OP_T, CUBLAS_OP_N, kWY, nwant, m, &one, V, n, v_out + r0, n, &zero, w1, kWY) !=
@@ -829,6 +885,7 @@ int eigh_lowest_real(Context& c, const double* a, int lda, int n, int nwant, dou
         return fail(c, HPSI_ECUDA, "eigh_lowest_real: back-transformation GEMM failed");
     }
   }
+  if (vec32) HPSI_LAUNCH(c, HPSI_K_EIGH, (k_eh_cvt<float, double><<<cvt_grid(nz), 256, 0, c.stream>>>(nz, vf, v_out)));
   err = cudaMemcpyAsync(w_out, s->lam, sizeof(double) * nwant, cudaMemcpyDeviceToDevice, c.stream);
   if (err != cudaSuccess) return cuda_fail(c, err, "eigh_lowest_real: eigenvalue copy");
   int info[2] = {0, 0};
