@@ -66,8 +66,9 @@ enum hpsi_option {
                                  tensor-memory accumulator of <beta|psi> before the partial sums
                                  are added in float64 (0, default: at most 16, fewer where the
                                  output tiles alone would not fill the GPU) */
-  HPSI_OPT_FINAL_FP64 = 7,    /* mixed davidson_solve: 1 (default) takes the final Rayleigh
+  HPSI_OPT_FINAL_FP64 = 7,    /* mixed davidson_solve(_gamma): 1 (default) takes the final Rayleigh
                                  quotients with one float64 application of H to the Ritz vectors;
+                                 2 with the float64 nonlocal term and the float32 local term;
                                  0 with the mixed H */
   HPSI_OPT_BASIS = 8,         /* davidson_solve: the reduced basis grows to this many times N
                                  vectors (2: the basic 2N form, 3 or 4) before a restart; 0
@@ -128,9 +129,17 @@ enum hpsi_option {
   HPSI_OPT_SCF_BETA = 20,     /* hpsi_scf: step along the optimal residual (0 < value <= 1, default 0.5) */
   HPSI_OPT_SCF_DAVIDSON_TOL = 21, /* hpsi_scf: residual tolerance of the Davidson solve of each
                                  iteration (default 1e-9) */
-  HPSI_OPT_GAMMA_GEMM = 22    /* mixed davidson_solve_gamma: 1 (default): the float32 subspace GEMMs
+  HPSI_OPT_GAMMA_GEMM = 22,   /* mixed davidson_solve_gamma: 1 (default): the float32 subspace GEMMs
                                  run as cuBLAS's float32 emulation with bf16 tensor-core products
                                  (float32-accurate); 0: float32 on the CUDA cores */
+  HPSI_OPT_EIGH_DF = 23       /* real symmetric reduced problems.  1 (default): in the mixed
+                                 davidson_solve_gamma the Householder reduction works in double-float
+                                 arithmetic (pairs of float32, ~1e-13 relative, on the float32 pipes)
+                                 and the eigenvectors' Gram, Newton-Schulz and back-transformation
+                                 GEMMs in float32, since they rotate a float32 basis; float64 elsewhere.
+                                 0: float64 throughout.  2: the double-float reduction also in
+                                 hpsi_eigh_lowest_sym and the float64 davidson_solve_gamma (float64
+                                 eigenvector GEMMs) */
 };
 
 /* Kernel classes reported by hpsi_kernel_stats. */

@@ -37,7 +37,8 @@ static cudaEvent_t pooled_event(Context& c) {
 
 int launch_begin(Context& c, int kernel) {
   c.launches[kernel]++;
-  const bool at64 = cur_prec(c) == HPSI_FP64;
+  const bool nl = kernel == HPSI_K_CALBEC || kernel == HPSI_K_DSCALE || kernel == HPSI_K_ADDVUS;
+  const bool at64 = (nl ? nl_prec(c) : cur_prec(c)) == HPSI_FP64;
   if (at64) c.launches64[kernel]++;
   if (!c.timing) return -1;
   cudaEvent_t a = pooled_event(c), b = pooled_event(c);
@@ -472,7 +473,7 @@ static void free_context(Context& c) {
 }
 
 int nonlocal_apply(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd) {
-  if (cur_prec(c) == HPSI_FP64) return nonlocal_apply_fp64(c, p, psi, hpsi, nbnd);
+  if (nl_prec(c) == HPSI_FP64) return nonlocal_apply_fp64(c, p, psi, hpsi, nbnd);
   return nonlocal_apply_mixed(c, p, psi, hpsi, nbnd);
 }
 
@@ -536,13 +537,13 @@ int batch_apply(Context& c, int nitem, const int* prob, const int* nbnd, const d
   }
   // the nonlocal term: in float64 all items share one launch per kernel class; the tensor-core
   // form runs per item
-  if (cur_prec(c) == HPSI_FP64) {
+  if (nl_prec(c) == HPSI_FP64) {
     int rc = nonlocal_batch_fp64(c, nitem, prob, nbnd, psi, hpsi);
     if (rc) return rc;
   }
   for (int i = 0; i < nitem; ++i) {
     if (nbnd[i] == 0) continue;
-    if (cur_prec(c) != HPSI_FP64) {
+    if (nl_prec(c) != HPSI_FP64) {
       int rc = nonlocal_apply(c, c.probs[prob[i]], psi[i], hpsi[i], nbnd[i]);
       if (rc) return rc;
     }
@@ -1001,6 +1002,11 @@ extern "C" int hpsi_set_option(hpsi_ctx* ctx, int option, double value) {
     c.gamma_gemm = (int)value;
     return HPSI_OK;
   }
+  if (option == HPSI_OPT_EIGH_DF) {
+    if (value != 0.0 && value != 1.0 && value != 2.0) return fail(c, HPSI_EINVAL, "HPSI_OPT_EIGH_DF must be 0, 1 or 2");
+    c.eigh_df = (int)value;
+    return HPSI_OK;
+  }
   if (option == HPSI_OPT_SCF_DAVIDSON_TOL) {
     if (!(value > 0.0) || !std::isfinite(value)) return fail(c, HPSI_EINVAL, "HPSI_OPT_SCF_DAVIDSON_TOL must be > 0");
     c.scf_dav_tol = value;
@@ -1033,7 +1039,7 @@ extern "C" int hpsi_set_option(hpsi_ctx* ctx, int option, double value) {
     return HPSI_OK;
   }
   if (option == HPSI_OPT_FINAL_FP64) {
-    if (value != 0.0 && value != 1.0) return fail(c, HPSI_EINVAL, "HPSI_OPT_FINAL_FP64 must be 0 or 1");
+    if (value != 0.0 && value != 1.0 && value != 2.0) return fail(c, HPSI_EINVAL, "HPSI_OPT_FINAL_FP64 must be 0, 1 or 2");
     c.final_fp64 = (int)value;
     return HPSI_OK;
   }

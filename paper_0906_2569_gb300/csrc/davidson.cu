@@ -1298,9 +1298,9 @@ static int davidson_run_mixed(Context& c, DavHandles& h, int ik, int nbnd, doubl
     HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_cvt_32_64<<<grid_of(nl), 256, 0, c.stream>>>(nl, w.lock32, w.in64)));
   HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
               (k_cvt_32_64<<<grid_of(n - nl), 256, 0, c.stream>>>(n - nl, w.psi32, w.in64 + nl)));
-  if (c.final_fp64) c.prec_override = HPSI_FP64;
+  final_precision_begin(c);
   rc = apply_device(c, ik, w.in64, w.out64, N);
-  c.prec_override = -1;
+  final_precision_end(c);
   if (rc) return rc;
   HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_rayleigh<<<N, 1024, 0, c.stream>>>(npw, w.in64, w.out64, w.eps, w.rnorm)));
   DCK(cudaMemcpyAsync(ev.data(), w.eps, sizeof(double) * N, cudaMemcpyDeviceToHost, c.stream), "eig copy");

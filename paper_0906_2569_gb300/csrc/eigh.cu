@@ -38,6 +38,7 @@
 #include "hpsi_internal.h"
 #include "eigh_tridiag.cuh"
 #include "eigh_tridiag_real.cuh"
+#include "eigh_tridiag_df.cuh"
 
 namespace hpsi {
 
@@ -399,6 +400,16 @@ __global__ void k_eh_vscale_r(int n, const double* __restrict__ vscale, double* 
   *v = c == j + 1 ? 1.0 : *v * vscale[j];
 }
 
+// After a double-float reduction: tau_j = 2 / (v_j^T v_j) from the diagonal of the blocks' Gram
+// matrices (the reduction's tau agrees to ~1e-14), so that every reflector I - tau v v^T is
+// orthogonal to float64 rounding; a zero tau (no reflection) stays zero.
+__global__ void k_eh_tau_fix(int nref, const double* __restrict__ Gall, double* __restrict__ tau) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nref || tau[j] == 0.0) return;
+  const int k = j / kWY, jj = j % kWY;
+  tau[j] = 2.0 / Gall[(size_t)k * kWY * kWY + (size_t)jj * kWY + jj];
+}
+
 // T of a real compact-WY block from G = V^T V and tau, as k_eh_tfactor does for complex blocks.
 __global__ void __launch_bounds__(128) k_eh_tfactor_r(const double* __restrict__ Gall, const double* __restrict__ tauall,
                                                       double* __restrict__ Tall) {
@@ -743,10 +754,11 @@ bool eigh_supported_real(const Context& c, int n) {
 // back-transformation by DGEMMs.  Eigenvectors go to v_out [nwant][n] (column-major, ld n).
 // vec32: the eigenvectors are wanted to float32 accuracy only (a float32 basis is rotated by them),
 // so their Gram matrix, the Newton-Schulz step and the back-transformation run as float32 GEMMs on
-// float32 copies (FP32 throughput is ~64x FP64 on GB300); the reduction, the eigenvalues and the
-// inverse iteration stay float64.
+// float32 copies (FP32 throughput is ~64x FP64 on GB300); the eigenvalues and the inverse iteration
+// stay float64.  df: the reduction's row work in double-float arithmetic (k_eh_tridiag_df, ~1e-13
+// relative) instead of float64.
 int eigh_lowest_real(Context& c, const double* a, int lda, int n, int nwant, double* w_out, double* v_out,
-                     bool* fallback, bool vec32) {
+                     bool* fallback, bool vec32, bool df) {
   *fallback = false;
   if (n < 1 || nwant < 1 || nwant > n || lda < n) return fail(c, HPSI_EINVAL, "eigh_lowest_real: bad sizes");
   if (!eigh_supported_real(c, n)) {
@@ -771,7 +783,8 @@ int eigh_lowest_real(Context& c, const double* a, int lda, int n, int nwant, dou
   // 1. tridiagonal reduction (cooperative)
   const int G = tri_ctas(c, n);
   const size_t smem = tri_smem_r(n, G);
-  err = cudaFuncSetAttribute(k_eh_tridiag_r, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const void* tri_kernel = df ? (const void*)k_eh_tridiag_df : (const void*)k_eh_tridiag_r;
+  err = cudaFuncSetAttribute(tri_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return cuda_fail(c, err, "eigh_lowest_real: smem attribute");
   err = cudaMemsetAsync(s->bar, 0, sizeof(unsigned int) * 64, c.stream);
   if (err == cudaSuccess) err = cudaMemsetAsync(vref, 0, sizeof(double) * (size_t)(n + kWY) * n, c.stream);
@@ -789,8 +802,7 @@ int eigh_lowest_real(Context& c, const double* a, int lda, int n, int nwant, dou
               s->bar, c.d_err};
   void* args[] = {&ta};
   HPSI_LAUNCH(c, HPSI_K_TRIDIAG,
-              (err = cudaLaunchCooperativeKernel((const void*)k_eh_tridiag_r, dim3(G), dim3(kTriThreads), args, smem,
-                                                 c.stream)));
+              (err = cudaLaunchCooperativeKernel(tri_kernel, dim3(G), dim3(kTriThreads), args, smem, c.stream)));
   ++c.tri_calls;
   c.tri_flops += 4.0 / 3.0 * (double)n * (double)n * (double)n;
   if (err == cudaErrorCooperativeLaunchTooLarge) {
@@ -844,13 +856,19 @@ int eigh_lowest_real(Context& c, const double* a, int lda, int n, int nwant, dou
   }
   // 4. back-transformation, one compact-WY block of kWY reflectors at a time from the last
   if (n > 1) {
-    HPSI_LAUNCH(c, HPSI_K_EIGH, (k_eh_vscale_r<<<dim3((n + 255) / 256, n - 1), 256, 0, c.stream>>>(n, vscale, vref)));
+    if (df)
+      HPSI_LAUNCH(c, HPSI_K_EIGH,
+                  (k_eh_vscale_df<<<dim3((n + 255) / 256, n - 1), 256, 0, c.stream>>>(n, vscale, vref)));
+    else
+      HPSI_LAUNCH(c, HPSI_K_EIGH,
+                  (k_eh_vscale_r<<<dim3((n + 255) / 256, n - 1), 256, 0, c.stream>>>(n, vscale, vref)));
     const int K = (n - 1 + kWY - 1) / kWY;
     if (cublasDgemmStridedBatched(s->blas, CUBLAS_OP_T, CUBLAS_OP_N, kWY, kWY, n - 1, &one, vref + 1, n,
                                   (long long)kWY * n, vref + 1, n, (long long)kWY * n, &zero, wgram, kWY,
                                   (long long)kWY * kWY, K) != CUBLAS_STATUS_SUCCESS)
       return fail(c, HPSI_ECUDA, "eigh_lowest_real: reflector Gram matrices failed");
     const size_t tsm = sizeof(double) * (size_t)kWY * (kWY - 1) / 2;
+    if (df) HPSI_LAUNCH(c, HPSI_K_EIGH, (k_eh_tau_fix<<<(n - 1 + 255) / 256, 256, 0, c.stream>>>(n - 1, wgram, tau)));
     HPSI_LAUNCH(c, HPSI_K_EIGH, (k_eh_tfactor_r<<<dim3(kWY / 4, K), 128, tsm, c.stream>>>(wgram, tau, tfac)));
     if (vec32) {
       const size_t nv = (size_t)K * kWY * n, nt = (size_t)K * kWY * kWY;
@@ -933,7 +951,7 @@ extern "C" int hpsi_eigh_lowest_sym(hpsi_ctx* ctx, int n, const void* a, int lda
   if (c.eigensolver == 1) {
     bool fallback = false;
     const int rc = hpsi::eigh_lowest_real(c, static_cast<const double*>(a), lda, n, nwant, static_cast<double*>(w_out),
-                                          static_cast<double*>(v_out), &fallback);
+                                          static_cast<double*>(v_out), &fallback, false, c.eigh_df == 2);
     if (rc || !fallback) return rc;
   }
   return hpsi::fail(c, HPSI_EINVAL, "hpsi_eigh_lowest_sym: n too large for the library's real eigensolver");

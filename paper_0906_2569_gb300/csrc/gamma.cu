@@ -41,10 +41,6 @@ template <> struct V2<double> { using type = double2; };
 template <> struct V2<float> { using type = float2; };
 
 __device__ __forceinline__ double2 ld2(const double2* p) { return *p; }
-__device__ __forceinline__ double2 ld2(const float2* p) {
-  const float2 v = *p;
-  return make_double2(v.x, v.y);
-}
 __device__ __forceinline__ void st2(double2* p, double2 v) { *p = v; }
 __device__ __forceinline__ void st2(float2* p, double2 v) { *p = make_float2((float)v.x, (float)v.y); }
 
@@ -61,21 +57,40 @@ __global__ void k_gamma_pack(int npw, int nb, const S* __restrict__ x, int scale
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npw; i += gridDim.x * blockDim.x) {
     const bool neg = i < i0;
     const int h = neg ? i0 - i : i - i0;
-    double2 ca = ld2(xa + h);
-    double2 cb = b < nb ? ld2(xb + h) : make_double2(0.0, 0.0);
-    if (scaled && h > 0) {
-      ca.x *= kInvSqrt2; ca.y *= kInvSqrt2;
-      cb.x *= kInvSqrt2; cb.y *= kInvSqrt2;
+    if constexpr (sizeof(S) == sizeof(float2)) {
+      // float32 arithmetic (the float64 unit only widens the result)
+      float2 ca = xa[h];
+      float2 cb = b < nb ? xb[h] : make_float2(0.f, 0.f);
+      if (scaled && h > 0) {
+        ca.x *= (float)kInvSqrt2; ca.y *= (float)kInvSqrt2;
+        cb.x *= (float)kInvSqrt2; cb.y *= (float)kInvSqrt2;
+      }
+      if (h == 0) {
+        ca.y = 0.f;
+        cb.y = 0.f;
+      }
+      if (neg) {
+        ca.y = -ca.y;
+        cb.y = -cb.y;
+      }
+      fq[i] = make_double2((double)(ca.x - cb.y), (double)(ca.y + cb.x));
+    } else {
+      double2 ca = ld2(xa + h);
+      double2 cb = b < nb ? ld2(xb + h) : make_double2(0.0, 0.0);
+      if (scaled && h > 0) {
+        ca.x *= kInvSqrt2; ca.y *= kInvSqrt2;
+        cb.x *= kInvSqrt2; cb.y *= kInvSqrt2;
+      }
+      if (h == 0) {   // a real orbital has a real G = 0 component
+        ca.y = 0.0;
+        cb.y = 0.0;
+      }
+      if (neg) {
+        ca.y = -ca.y;
+        cb.y = -cb.y;
+      }
+      fq[i] = make_double2(ca.x - cb.y, ca.y + cb.x);
     }
-    if (h == 0) {   // a real orbital has a real G = 0 component
-      ca.y = 0.0;
-      cb.y = 0.0;
-    }
-    if (neg) {
-      ca.y = -ca.y;
-      cb.y = -cb.y;
-    }
-    fq[i] = make_double2(ca.x - cb.y, ca.y + cb.x);
   }
 }
 
@@ -92,6 +107,49 @@ __global__ void k_gamma_unpack(int npw, int nb, const double2* __restrict__ F, i
   const int a = 2 * q, b = 2 * q + 1;
   const double2* Fq = F + (size_t)q * npw;
   for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < nh; h += gridDim.x * blockDim.x) {
+    if constexpr (sizeof(S) == sizeof(float2)) {
+      // float32 result: float32 arithmetic, the float64 unit only narrows F and nl64
+      const double2 fpd = Fq[i0 + h], fmd = Fq[i0 - h];
+      const float2 fp = make_float2((float)fpd.x, (float)fpd.y), fm = make_float2((float)fmd.x, (float)fmd.y);
+      float2 ya = make_float2(0.5f * (fp.x + fm.x), 0.5f * (fp.y - fm.y));
+      float2 yb = make_float2(0.5f * (fp.y + fm.y), -0.5f * (fp.x - fm.x));
+      if (scaled && h > 0) {
+        ya.x *= (float)kSqrt2; ya.y *= (float)kSqrt2;
+        yb.x *= (float)kSqrt2; yb.y *= (float)kSqrt2;
+      }
+      if (nl64 || nl32) {
+        const float sn = (!scaled && h > 0) ? (float)kInvSqrt2 : 1.f;
+        float na0 = 0.f, na1 = 0.f, nb0 = 0.f, nb1 = 0.f;
+        const size_t ia = (size_t)a * nr + 2 * h, ib = (size_t)b * nr + 2 * h;
+        if (nl64) {
+          na0 = (float)nl64[ia];
+          na1 = (float)nl64[ia + 1];
+          if (b < nb) {
+            nb0 = (float)nl64[ib];
+            nb1 = (float)nl64[ib + 1];
+          }
+        } else {
+          const size_t plane = (size_t)nb * nr;
+          for (int sp = 0; sp < ns32; ++sp) {
+            const float2 va = *reinterpret_cast<const float2*>(nl32 + sp * plane + ia);
+            na0 += va.x;
+            na1 += va.y;
+            if (b < nb) {
+              const float2 vb = *reinterpret_cast<const float2*>(nl32 + sp * plane + ib);
+              nb0 += vb.x;
+              nb1 += vb.y;
+            }
+          }
+        }
+        ya.x = fmaf(sn, na0, ya.x);
+        ya.y = fmaf(sn, na1, ya.y);
+        yb.x = fmaf(sn, nb0, yb.x);
+        yb.y = fmaf(sn, nb1, yb.y);
+      }
+      y[(size_t)a * nh + h] = ya;
+      if (b < nb) y[(size_t)b * nh + h] = yb;
+      continue;
+    }
     const double2 fp = Fq[i0 + h], fm = Fq[i0 - h];
     // conj(F(-G)) = (fm.x, -fm.y)
     double2 ya = make_double2(0.5 * (fp.x + fm.x), 0.5 * (fp.y - fm.y));
@@ -231,6 +289,15 @@ template <typename S>
 static int gamma_apply_t(Context& c, int ik, const S* x, S* y, int nb, bool scaled) {
   Problem& p = c.probs[ik];
   if (nb == 0) return HPSI_OK;
+  constexpr int kMaxBlock = 65534;   // bands (and pairs) index gridDim.y
+  if (nb > kMaxBlock) {
+    const size_t nh = (size_t)(p.npw + 1) / 2;
+    for (int b0 = 0; b0 < nb; b0 += kMaxBlock) {
+      const int rc = gamma_apply_t<S>(c, ik, x + b0 * nh, y + b0 * nh, std::min(kMaxBlock, nb - b0), scaled);
+      if (rc) return rc;
+    }
+    return HPSI_OK;
+  }
   int rc = gamma_nl_prepare(c, p);
   if (rc) return rc;
   const int npairs = (nb + 1) / 2;
@@ -250,7 +317,7 @@ static int gamma_apply_t(Context& c, int ik, const S* x, S* y, int nb, bool scal
   int ns32 = 0;
   if (p.nproj > 0) {
     constexpr bool x32 = sizeof(S) == sizeof(float2);
-    if (cur_prec(c) == HPSI_FP64) {
+    if (nl_prec(c) == HPSI_FP64) {
       const int nr = 2 * ((p.npw + 1) / 2);
       rc = ensure_buffer(c, &c.ws.gnl, &c.ws.gnlbytes, sizeof(double) * (size_t)nb * nr);
       if (rc) return rc;
@@ -344,7 +411,26 @@ __global__ void k_g_hdiag(int nh, const double* __restrict__ hdiag, T* __restric
   }
 }
 
-// r_i = hx_i - eps_i x_i (arithmetic in float64, stored in T), ||r_i||_2 in float64; one CTA per band.
+// Sum of squares of float32 values to float64 accuracy without a float64 instruction per element:
+// each square split exactly by an FMA (q^2 = p + e) and accumulated in a (hi, lo) pair of floats
+// through TwoSum; the _rn intrinsics keep the compiler from contracting or reassociating it.
+struct SqAcc {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float q) {
+    const float p = __fmul_rn(q, q);
+    const float e = __fmaf_rn(q, q, -p);
+    const float s = __fadd_rn(hi, p);
+    const float bb = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(err, e));
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// r_i = hx_i - eps_i x_i, stored in T, and ||r_i||_2 to float64 accuracy; one CTA per band.  A float32
+// basis forms r in float32 with eps as a (hi, lo) pair of floats (two FMAs: r to within an ulp of
+// itself), a float64 basis in float64.
 template <typename T>
 __global__ void __launch_bounds__(512) k_g_residual(int n, const T* __restrict__ x, const T* __restrict__ hx,
                                                     const double* __restrict__ eps, T* __restrict__ r,
@@ -356,10 +442,22 @@ __global__ void __launch_bounds__(512) k_g_residual(int n, const T* __restrict__
   const T* hb = hx + (size_t)b * n;
   T* rb = r + (size_t)b * n;
   double s = 0.0;
-  for (int g = threadIdx.x; g < n; g += blockDim.x) {
-    const T q = (T)((double)hb[g] - e * (double)xb[g]);
-    rb[g] = q;
-    s += (double)q * (double)q;
+  if constexpr (sizeof(T) == 4) {
+    const float eh = (float)e, el = (float)(e - (double)eh);
+    SqAcc acc;
+    for (int g = threadIdx.x; g < n; g += blockDim.x) {
+      const float xv = xb[g];
+      const float q = __fmaf_rn(-el, xv, __fmaf_rn(-eh, xv, hb[g]));
+      rb[g] = q;
+      acc.add(q);
+    }
+    s = acc.value();
+  } else {
+    for (int g = threadIdx.x; g < n; g += blockDim.x) {
+      const T q = (T)((double)hb[g] - e * (double)xb[g]);
+      rb[g] = q;
+      s += (double)q * (double)q;
+    }
   }
   s = block_sum<T>(s, red);
   if (threadIdx.x == 0) rnorm[b] = sqrt(s);
@@ -412,7 +510,13 @@ __global__ void __launch_bounds__(512) k_g_norm2(int n, const T* __restrict__ t,
   __shared__ double red[33];
   const T* tb = t + (size_t)blockIdx.x * n;
   double s = 0.0;
-  for (int g = threadIdx.x; g < n; g += blockDim.x) s += (double)tb[g] * (double)tb[g];
+  if constexpr (sizeof(T) == 4) {
+    SqAcc acc;
+    for (int g = threadIdx.x; g < n; g += blockDim.x) acc.add(tb[g]);
+    s = acc.value();
+  } else {
+    for (int g = threadIdx.x; g < n; g += blockDim.x) s += (double)tb[g] * (double)tb[g];
+  }
   s = block_sum<T>(s, red);
   if (threadIdx.x == 0) out[blockIdx.x] = s;
 }
@@ -668,15 +772,17 @@ int GammaDavidson<T>::alloc(int N) {
 // Lowest nwant eigenpairs of the symmetric leading n x n block of a (ld lda), float64: values in
 // w.wv, vectors in the first nwant columns of w.evec (ld n).  The library's real eigensolver
 // (HPSI_OPT_EIGENSOLVER = 1), cuSOLVER dsyevdx where it does not apply or hands the problem back.
-// A float32 basis takes the vectors to float32 accuracy (they rotate float32 vectors), the values
-// always to float64.
+// A float32 basis (HPSI_OPT_EIGH_DF >= 1) takes the vectors to float32 accuracy (they rotate
+// float32 vectors) and the reduction in double-float arithmetic, the values to ~1e-13 relative.
 template <typename T>
 int GammaDavidson<T>::eig_lowest(const double* a, int lda, int n, int nwant) {
   Context& c = c_;
   GamWork& w = w_;
   if (c.eigensolver == 1) {
     bool fallback = false;
-    const int rc = eigh_lowest_real(c, a, lda, n, nwant, w.wv, w.evec, &fallback, sizeof(T) == sizeof(float));
+    const bool mixed = sizeof(T) == sizeof(float);
+    const int rc = eigh_lowest_real(c, a, lda, n, nwant, w.wv, w.evec, &fallback, mixed && c.eigh_df >= 1,
+                                    c.eigh_df == 2 || (mixed && c.eigh_df == 1));
     if (rc || !fallback) return rc;
   }
   HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
@@ -953,10 +1059,10 @@ int GammaDavidson<T>::run(int N, double tol, int maxiter, double2* psio, double*
     const size_t n = (size_t)N * n2;
     HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
                 (k_g_copy<T, double><<<grid_of(n), 256, 0, c.stream>>>((int)n2, N, psi(), n2, w.x64, n2)));
-    if (c.final_fp64) c.prec_override = HPSI_FP64;
+    final_precision_begin(c);
     rc = gamma_apply_t<double2>(c, ik_, reinterpret_cast<const double2*>(w.x64), reinterpret_cast<double2*>(w.hx64),
                                 N, true);
-    c.prec_override = -1;
+    final_precision_end(c);
     if (rc) return rc;
     HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_g_rayleigh<<<N, 512, 0, c.stream>>>(n2, w.x64, w.hx64, w.eps, w.rnorm)));
     GCK(cudaMemcpyAsync(ev.data(), w.eps, sizeof(double) * N, cudaMemcpyDeviceToHost, c.stream), "eig copy");

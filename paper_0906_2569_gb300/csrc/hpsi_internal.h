@@ -143,7 +143,9 @@ struct Context {
   int force_generic = 0;               // 1: local part on the generic FFT kernels
   int tc_kmax = 0;                     // mixed calbec: max 64-wide K-steps per split (0: automatic)
   int prec_override = -1;              // >= 0: apply H at this precision instead of `precision`
+  int nl_prec_override = -1;           // >= 0: the nonlocal term alone at this precision
   int final_fp64 = 1;                  // mixed davidson_solve: final Rayleigh quotients with the float64 H
+                                       // (2: float64 nonlocal term, local term at the working precision)
   int basis_factor = 0;                // Davidson: the reduced basis grows to basis_factor * N vectors
                                        // (0: 3 for a mixed context, 4 for float64)
   int autotune = 1;                    // time the fast-path plans on the first apply of a problem
@@ -164,6 +166,9 @@ struct Context {
   double scf_beta = 0.5;               // SCF: step along the optimal residual
   double scf_dav_tol = 1e-9;           // SCF: residual tolerance of each Davidson solve
   int gamma_gemm = 1;                  // mixed Gamma Davidson: 1 bf16x9-emulated float32 GEMMs, 0 plain float32
+  int eigh_df = 1;                     // real reduced problems: 0 float64; 1 double-float reduction and float32
+                                       // eigenvector GEMMs in the mixed Gamma Davidson; 2 also the double-float
+                                       // reduction in hpsi_eigh_lowest_sym and the float64 Gamma Davidson
   double cg_tmin = 1.0;                // CG preconditioner: P^2 = 1 / max(|k+G|^2/2, cg_tmin)
   cudaStream_t cap_stream = nullptr;   // internal stream for graph capture
   GraphCache graph;
@@ -184,6 +189,18 @@ struct Context {
 
 // Precision at which H is applied right now.
 inline int cur_prec(const Context& c) { return c.prec_override >= 0 ? c.prec_override : c.precision; }
+// Precision of the nonlocal term right now.
+inline int nl_prec(const Context& c) { return c.nl_prec_override >= 0 ? c.nl_prec_override : cur_prec(c); }
+// Bracket the final Rayleigh quotients of a mixed solve: HPSI_OPT_FINAL_FP64 1 applies H in float64,
+// 2 only its nonlocal term.
+inline void final_precision_begin(Context& c) {
+  if (c.final_fp64 == 1) c.prec_override = HPSI_FP64;
+  else if (c.final_fp64 == 2) c.nl_prec_override = HPSI_FP64;
+}
+inline void final_precision_end(Context& c) {
+  c.prec_override = -1;
+  c.nl_prec_override = -1;
+}
 
 // Bracket one launch: call before (returns a record slot or -1) and after the launch.
 int launch_begin(Context& c, int kernel);
@@ -328,7 +345,7 @@ void eigh_release(Context& c);
 // n up to 1824 on 152 SMs; *fallback as above.  Vectors to v_out [nwant][n] (column-major, ld n).
 bool eigh_supported_real(const Context& c, int n);
 int eigh_lowest_real(Context& c, const double* a, int lda, int n, int nwant, double* w_out, double* v_out,
-                     bool* fallback, bool vec32 = false);
+                     bool* fallback, bool vec32 = false, bool df = false);
 
 }  // namespace hpsi
 

@@ -483,32 +483,51 @@ __global__ void k_split_betar_add(int nproj, int nr, int ka, const double* __res
 
 // B of calbec in the real form: row b = x_b (nr real coordinates, K padded to kc with zeros);
 // scaled = 0: x holds coefficients and r >= 2 is multiplied by sqrt2.  One thread per pair of
-// coordinates.
+// coordinates, band b = blockIdx.y.
 template <int NT, typename R>
 __global__ void k_split_xr(int nb, int nr, int kc, int scaled, const R* __restrict__ x,
                            __nv_bfloat16* __restrict__ out) {
   const size_t plane = (size_t)nb * kc;
-  const int half = kc / 2;
-  const size_t n = (size_t)nb * half;
+  const int half = kc / 2, b = blockIdx.y;
   __nv_bfloat162* o2 = reinterpret_cast<__nv_bfloat162*>(out);
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const int b = (int)(i / half), h = (int)(i - (size_t)b * half);
-    double r0 = 0.0, r1 = 0.0;
-    if (2 * h < nr) {
-      r0 = (double)x[(size_t)b * nr + 2 * h];
-      r1 = (double)x[(size_t)b * nr + 2 * h + 1];
-      if (!scaled && h > 0) {
-        r0 *= 1.4142135623730950488;
-        r1 *= 1.4142135623730950488;
-      }
-    }
+  for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < half; h += gridDim.x * blockDim.x) {
     const size_t at = (size_t)b * half + h;
+    if constexpr (sizeof(R) == 4) {
+      // float32 input: the three bf16 terms of a float are exact, and float32 arithmetic finds them
+      float r0 = 0.f, r1 = 0.f;
+      if (2 * h < nr) {
+        const float2 v = *reinterpret_cast<const float2*>(x + (size_t)b * nr + 2 * h);
+        r0 = v.x;
+        r1 = v.y;
+        if (!scaled && h > 0) {
+          r0 *= 1.41421356f;
+          r1 *= 1.41421356f;
+        }
+      }
 #pragma unroll
-    for (int t = 0; t < NT; ++t) {
-      const __nv_bfloat16 h0 = __float2bfloat16_rn((float)r0), h1 = __float2bfloat16_rn((float)r1);
-      o2[t * (plane / 2) + at] = __halves2bfloat162(h0, h1);
-      r0 -= (double)__bfloat162float(h0);
-      r1 -= (double)__bfloat162float(h1);
+      for (int t = 0; t < NT; ++t) {
+        const __nv_bfloat16 h0 = __float2bfloat16_rn(r0), h1 = __float2bfloat16_rn(r1);
+        o2[t * (plane / 2) + at] = __halves2bfloat162(h0, h1);
+        r0 -= __bfloat162float(h0);
+        r1 -= __bfloat162float(h1);
+      }
+    } else {
+      double r0 = 0.0, r1 = 0.0;
+      if (2 * h < nr) {
+        r0 = (double)x[(size_t)b * nr + 2 * h];
+        r1 = (double)x[(size_t)b * nr + 2 * h + 1];
+        if (!scaled && h > 0) {
+          r0 *= 1.4142135623730950488;
+          r1 *= 1.4142135623730950488;
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        const __nv_bfloat16 h0 = __float2bfloat16_rn((float)r0), h1 = __float2bfloat16_rn((float)r1);
+        o2[t * (plane / 2) + at] = __halves2bfloat162(h0, h1);
+        r0 -= (double)__bfloat162float(h0);
+        r1 -= (double)__bfloat162float(h1);
+      }
     }
   }
 }
@@ -771,7 +790,8 @@ int gamma_apply_tc(Context& c, const Problem& p, const R* x, int nb, bool scaled
   cudaError_t e0 = cudaMemsetAsync(wa, 0, wb, c.stream);   // the K padding of w
   if (e0 != cudaSuccess) return cuda_fail(c, e0, "workspace clear");
   HPSI_LAUNCH(c, HPSI_K_SPLIT,
-              (k_split_xr<NT, R><<<8 * c.sm_count, 256, 0, c.stream>>>(nb, nr, kc, scaled ? 1 : 0, x, xs)));
+              (k_split_xr<NT, R><<<dim3(std::min(1024, (kc / 2 + 255) / 256), nb), 256, 0, c.stream>>>(
+                  nb, nr, kc, scaled ? 1 : 0, x, xs)));
   rc = launch_gemm<NT>(c, bcal, P, xs, nb, kc, nsplit, ksplit, 0, part, nullptr, 0, HPSI_K_CALBEC);
   if (rc) return rc;
   const int n = P * nb;

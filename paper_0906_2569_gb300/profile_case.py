@@ -16,7 +16,8 @@ block, the default for a Gamma-only cell; ``--form complex``: davidson_solve), t
 (default 5e-5 mixed, 1e-8 float64): one warm-up solve, then one bracketed solve -- every launch of
 a solve, the library's and cuBLAS's, falls inside the bracket.
 
-With ``--eigh-real N`` the eigenproblem of order N is real symmetric (hpsi_eigh_lowest_sym).
+With ``--eigh-real N`` the eigenproblem of order N is real symmetric (hpsi_eigh_lowest_sym);
+``--df`` runs its reduction in double-float arithmetic (HPSI_OPT_EIGH_DF = 2).
 
 With ``--cg B`` it runs the band-by-band CG eigensolver on the first B bands of the cell named by
 ``--config`` in float64 (residual 1e-8, at most ``--cg-maxiter`` steps per band): one warm-up solve,
@@ -47,6 +48,7 @@ def main():
     ap.add_argument("--form", default="auto", choices=["auto", "gamma", "complex"])
     ap.add_argument("--tol", type=float, default=0.0)
     ap.add_argument("--eigh-real", type=int, default=0)
+    ap.add_argument("--df", action="store_true")
     args = ap.parse_args()
     import torch
     import workloads
@@ -88,6 +90,8 @@ def eigh_case(args, torch, workloads, B):
     ctx = B.hpsi_setup(p.lattice, p.ecut, [p.kpts[0]], p.fft, np.zeros(p.fft), None, None, B.HPSI_FP64,
                        torch.cuda.current_stream().cuda_stream)
     real = args.eigh_real > 0
+    if args.df:
+        B.hpsi_set_option(ctx, B.HPSI_OPT_EIGH_DF, 2)
     n = args.eigh_real if real else args.eigh
     nw = min(args.nwant, n)
     if real:

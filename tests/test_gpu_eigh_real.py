@@ -115,3 +115,35 @@ def test_too_large_is_refused(ctx):
     with pytest.raises(B.HpsiError) as e:
         B.hpsi_eigh_lowest_sym(ctx, a, n, n, 1, w, w)
     assert e.value.status == B.HPSI_EINVAL
+
+
+@pytest.fixture(scope="module")
+def ctx_df(lib):
+    """A context whose real reduction runs in double-float arithmetic (HPSI_OPT_EIGH_DF = 2)."""
+    import torch
+    from paper_0906_2569_gb300 import binding as B
+    p = workloads.config1()
+    c = B.hpsi_setup(p.lattice, p.ecut, [p.kpts[0]], p.fft, np.zeros(p.fft), None, None, B.HPSI_FP64,
+                     torch.cuda.current_stream().cuda_stream)
+    B.hpsi_set_option(c, B.HPSI_OPT_EIGH_DF, 2)
+    return c
+
+
+@pytest.mark.parametrize("n,nwant", [(1, 1), (2, 1), (3, 3), (31, 8), (333, 160), (1024, 256), (1536, 512),
+                                     (1824, 64)])
+def test_double_float_reduction(ctx_df, n, nwant):
+    """The Householder reduction on pairs of float32 (~48-bit significands): eigenvalues and
+    residuals within 5e-12 of the spectral radius, eigenvectors orthonormal to 1e-12."""
+    a = _sym(n, 100 + n, scale=20.0)
+    w, x = _solve(ctx_df, a, nwant)
+    ref = oracle.eigen.lowest_dense(a, nwant)
+    print(f"n {n}: double-float reduction, max eigenvalue error {np.max(np.abs(w - ref)) / 20.0:.2e} of the radius")
+    _check(a, w, x, tol_eig=5e-12, tol_res=5e-11)
+
+
+def test_double_float_reduction_clusters(ctx_df):
+    spec = np.concatenate([np.repeat([-3.0, 0.5], [6, 24]), 1.0 + 1e-9 * np.arange(10),
+                           1.0 + 1e-6 * np.arange(1, 11), np.linspace(2, 40, 150)])
+    a = _sym(len(spec), 9, spectrum=spec)
+    w, x = _solve(ctx_df, a, 60)
+    _check(a, w, x, tol_eig=5e-12, tol_res=5e-11)
