@@ -427,7 +427,9 @@ def run_gpu(args):
         "value": value, "unit": "band-applications/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": mix_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": ("mixed: f32 FFT + xV, bf16 3-term split (6-product) tensor-core nonlocal with f32 accumulation, "
-                  "f32 subspace GEMMs; f64 residual norms, reduced eigenproblems, Cholesky and final Rayleigh quotients"),
+                  "f32 subspace GEMMs; f64-accurate residual norms, reduced eigenproblems (double-float Householder "
+                  "reduction, f64 Sturm counts), Cholesky factors, and f64 projections <beta|psi>, D for the final "
+                  "Rayleigh quotients"),
         "data": "synthetic",
         "config": {"workload": desc, "npw": npw, "form": form,
                    "fp64": {"value": v64, "ms_per_step": f64_ms / args.fp64_steps, "steps": args.fp64_steps,
@@ -438,8 +440,8 @@ def run_gpu(args):
                    "band_apps_per_step": mixed["band_apps"] // max(1, args.steps),
                    "step": (f"one {'davidson_solve_gamma' if gamma else 'davidson_solve'} of the {p.nbnd}-band block "
                             f"to max residual {tol_mixed:g} from the seeded start (every H|psi>, residual, "
-                            "preconditioner and Rayleigh-Ritz of the solve; final Rayleigh quotients with one float64 "
-                            "H application)"),
+                            "preconditioner and Rayleigh-Ritz of the solve; final Rayleigh quotients after one more "
+                            "application of H with float64 projections and D)"),
                    "iterations": mixed["iters"], "max_residual": mixed["max_residual"],
                    "max_eig_error_ha_vs_oracle": mixed["max_eig_error_ha"],
                    "eigenvalues_checked": mixed["n_eig_checked"],

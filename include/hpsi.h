@@ -66,10 +66,13 @@ enum hpsi_option {
                                  tensor-memory accumulator of <beta|psi> before the partial sums
                                  are added in float64 (0, default: at most 16, fewer where the
                                  output tiles alone would not fill the GPU) */
-  HPSI_OPT_FINAL_FP64 = 7,    /* mixed davidson_solve(_gamma): 1 (default) takes the final Rayleigh
-                                 quotients with one float64 application of H to the Ritz vectors;
-                                 2 with the float64 nonlocal term and the float32 local term;
-                                 0 with the mixed H */
+  HPSI_OPT_FINAL_FP64 = 7,    /* mixed davidson_solve(_gamma): the final Rayleigh quotients after one
+                                 more application of H to the Ritz vectors.  2 (default): with float64
+                                 projections <beta|psi> and D, the local term at the working precision
+                                 and add_vuspsi on the tensor cores with one K-step per float32
+                                 partial (the projections' error enters the quotients at first
+                                 order; ~5e-8 Ha on the 144^3 cell); 1: with the float64 H (~3e-9 Ha);
+                                 0: with the mixed H (~2e-6 Ha) */
   HPSI_OPT_BASIS = 8,         /* davidson_solve: the reduced basis grows to this many times N
                                  vectors (2: the basic 2N form, 3 or 4) before a restart; 0
                                  (default): 3 in a mixed context, 4 in a float64 one */

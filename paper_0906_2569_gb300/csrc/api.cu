@@ -37,8 +37,13 @@ static cudaEvent_t pooled_event(Context& c) {
 
 int launch_begin(Context& c, int kernel) {
   c.launches[kernel]++;
-  const bool nl = kernel == HPSI_K_CALBEC || kernel == HPSI_K_DSCALE || kernel == HPSI_K_ADDVUS;
-  const bool at64 = (nl ? nl_prec(c) : cur_prec(c)) == HPSI_FP64;
+  // the class's precision: the nonlocal kernels follow the nonlocal term's (with kNlProj64 the
+  // projections are float64 and add_vuspsi is not)
+  const int np = nl_prec(c);
+  bool at64;
+  if (kernel == HPSI_K_CALBEC || kernel == HPSI_K_DSCALE) at64 = np == HPSI_FP64 || np == kNlProj64;
+  else if (kernel == HPSI_K_ADDVUS) at64 = np == HPSI_FP64;
+  else at64 = cur_prec(c) == HPSI_FP64;
   if (at64) c.launches64[kernel]++;
   if (!c.timing) return -1;
   cudaEvent_t a = pooled_event(c), b = pooled_event(c);
@@ -473,7 +478,16 @@ static void free_context(Context& c) {
 }
 
 int nonlocal_apply(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd) {
-  if (nl_prec(c) == HPSI_FP64) return nonlocal_apply_fp64(c, p, psi, hpsi, nbnd);
+  const int np = nl_prec(c);
+  if (np == HPSI_FP64 || (np == kNlProj64 && c.precision != HPSI_MIXED))
+    return nonlocal_apply_fp64(c, p, psi, hpsi, nbnd);
+  if (np == kNlProj64) {
+    if (p.nproj == 0 || nbnd == 0) return HPSI_OK;
+    double2* w = nullptr;
+    const int rc = nonlocal_w_fp64(c, p, psi, nbnd, &w);
+    if (rc) return rc;
+    return nonlocal_add_tc(c, p, w, hpsi, nbnd);
+  }
   return nonlocal_apply_mixed(c, p, psi, hpsi, nbnd);
 }
 

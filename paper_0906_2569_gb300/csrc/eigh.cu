@@ -286,6 +286,7 @@ __global__ void __launch_bounds__(32) k_eh_invit(int n, const double* __restrict
 }
 
 constexpr int kWY = 64;   // reflectors per compact-WY block of the back-transformation
+constexpr int kMaxCtas = 1024;   // CTAs of a reduction at most (one per SM)
 constexpr int kWYRows = kWY / 32;   // rows of a block per lane in the back substitution
 
 // v_j[c] = conj(u_j[c]) scale_j for c > j + 1 and v_j[j + 1] = 1, in place (rows j < n - 1).
@@ -460,6 +461,7 @@ struct EighState {
   cusolverDnHandle_t solver = nullptr;
   int ncap = 0, wcap = 0;
   double *d = nullptr, *e = nullptr, *e2 = nullptr, *sacc = nullptr, *lam = nullptr, *Z = nullptr, *Z2 = nullptr;
+  double* spart = nullptr;   // [2][kMaxCtas] the double-float reduction's per-CTA parts of s
   double* gram = nullptr;
   double2 *tau = nullptr, *vref = nullptr, *ybuf = nullptr, *rnext = nullptr, *rowcoef = nullptr, *vscale = nullptr;
   double2 *wgram = nullptr, *tfac = nullptr, *w1 = nullptr, *w2 = nullptr;   // compact-WY blocks
@@ -474,7 +476,8 @@ struct EighState {
 
 void free_state(EighState& s) {
   void* ptrs[] = {s.d,    s.e,     s.e2,    s.sacc,    s.lam,   s.Z,  s.gram, s.tau,
-                  s.vref, s.ybuf,  s.rnext, s.rowcoef, s.wgram, s.w1, s.bar,  s.info, s.vscale, s.Z2, s.tfac, s.w2};
+                  s.vref, s.ybuf,  s.rnext, s.rowcoef, s.wgram, s.w1, s.bar,  s.info, s.vscale, s.Z2, s.tfac, s.w2,
+                  s.spart};
   for (void* q : ptrs) cudaFree(q);
   const EighState keep = s;
   s = EighState{};
@@ -513,6 +516,7 @@ int grow(Context& c, EighState& s, int n, int nwant) {
   al((void**)&s.e2, sizeof(double) * N);
   al((void**)&s.sacc, sizeof(double) * 4);
   al((void**)&s.rowcoef, sizeof(double2) * 8);
+  al((void**)&s.spart, sizeof(double) * 2 * kMaxCtas);
   al((void**)&s.vscale, sizeof(double2) * N);
   al((void**)&s.lam, sizeof(double) * W);
   al((void**)&s.Z, sizeof(double) * (size_t)N * W);
@@ -600,7 +604,7 @@ int eigh_zheevdx(Context& c, EighState& s, const double2* a, int lda, int n, int
 }
 
 int tri_ctas(const Context& c, int n) {
-  int G = std::min(c.sm_count, std::max(8, (n + 3) / 4));
+  int G = std::min(std::min(c.sm_count, kMaxCtas), std::max(8, (n + 3) / 4));
   return std::max(1, std::min(G, n));
 }
 
@@ -799,7 +803,7 @@ int eigh_lowest_real(Context& c, const double* a, int lda, int n, int nwant, dou
               vref,  reinterpret_cast<double*>(s->ybuf),
               reinterpret_cast<double*>(s->rnext), reinterpret_cast<double*>(s->rowcoef),
               vscale, s->sacc,
-              s->bar, c.d_err};
+              s->bar, c.d_err, s->spart};
   void* args[] = {&ta};
   HPSI_LAUNCH(c, HPSI_K_TRIDIAG,
               (err = cudaLaunchCooperativeKernel(tri_kernel, dim3(G), dim3(kTriThreads), args, smem, c.stream)));

@@ -1,18 +1,20 @@
-// Householder reduction of a real symmetric matrix to tridiagonal form with the row work in
-// double-float arithmetic: every element of the trailing block is a pair of floats (hi, lo) whose
-// sum carries ~48 significant bits, and the per-column rank-2 update and dot product run on the
-// float32 pipes through error-free transformations (Knuth's TwoSum, Dekker's FastTwoSum and the
-// FMA split of a product).  On GB300 an SM issues float32 at 128 lanes per cycle against ~1.7 for
-// float64, so ~40 float32 operations per element still beat the 3 float64 FMAs of the float64
-// kernel several times over.  The scalars of each column (the reflector's beta, tau and scale, the
-// rows' coefficients, s and the diagonal) stay float64.
+// Householder reduction of a real symmetric matrix to tridiagonal form in double-float arithmetic:
+// every element of the trailing block, and every per-column scalar, is a pair of floats (hi, lo)
+// whose sum carries ~48 significant bits, computed on the float32 pipes through error-free
+// transformations (Knuth's TwoSum, Dekker's FastTwoSum, the FMA split of a product) and Newton steps
+// from float32 seeds for 1/sqrt and 1/x.  On GB300 an SM issues float32 at 128 lanes per cycle and
+// float64 at ~1.7, and a float64 instruction holds its scheduler's unit for ~64 cycles; the float64
+// reduction (k_eh_tridiag_r) spends most of each column on serial float64 chains.  Here no float64
+// instruction is left on a column's critical path: the float64 outputs (d, e, tau, the reflector
+// scales) are written after the CTA has arrived at the grid barrier.
 //
-// Same algorithm and data flow as k_eh_tridiag_r (eigh_tridiag_real.cuh): one pass over the own
-// rows per column that applies column j-1's rank-2 update and forms column j's matrix-vector
-// product, one grid barrier per column.  The published row, y and the reflector rows (vref) are
-// double-float pairs; k_eh_vscale_df turns the reflector rows into float64 afterwards.  Relative
-// accuracy ~1e-13 of the matrix norm: for reduced problems whose eigenvectors rotate a float32
-// basis.  Included once, by eigh.cu, after eigh_tridiag_real.cuh.
+// Algorithm and data flow as k_eh_tridiag_r (eigh_tridiag_real.cuh): one pass over the own rows per
+// column applies column j-1's rank-2 update and forms column j's matrix-vector product; one grid
+// barrier per column publishes y, the CTAs' parts of s = v^T y (one pair per CTA, summed by every
+// CTA after the barrier instead of float64 atomics) and the next row with its coefficients.  The
+// reflector rows (vref) are stored as pairs; k_eh_vscale_df widens and scales them.  Relative
+// accuracy ~1e-14 of the matrix norm (tests/test_gpu_eigh_real.py).  Included once, by eigh.cu,
+// after eigh_tridiag_real.cuh.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -49,6 +51,12 @@ __device__ __forceinline__ float2 df_add(float2 a, float2 b) {
   const float2 s = df_two_sum(a.x, b.x);
   return df_fast_sum(s.x, __fadd_rn(s.y, __fadd_rn(a.y, b.y)));
 }
+__device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+  float p, e;
+  df_prod(a, b, p, e);
+  return df_fast_sum(p, e);
+}
 // acc + a u
 __device__ __forceinline__ float2 df_mac(float2 acc, float2 a, float2 u) {
   float p, e;
@@ -66,14 +74,29 @@ __device__ __forceinline__ float2 df_rank2(float2 a, float2 P, float2 u, float2 
   const float lo = __fadd_rn(__fsub_rn(__fsub_rn(a.y, e1), e2), __fadd_rn(s1.y, s2.y));
   return df_fast_sum(s2.x, lo);
 }
+// 1 / sqrt(s) for s > 0: float32 seed, two Newton steps y += y (1 - s y^2) / 2 in pairs
+__device__ __forceinline__ float2 df_rsqrt(float2 s) {
+  float2 y = make_float2(rsqrtf(s.x), 0.f);
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const float2 r = df_add(make_float2(1.f, 0.f), df_neg(df_mul(s, df_mul(y, y))));
+    y = df_mac(y, df_mul(make_float2(0.5f, 0.f), y), r);
+  }
+  return y;
+}
+// 1 / d for d != 0: float32 seed, two Newton steps r += r (1 - d r) in pairs
+__device__ __forceinline__ float2 df_rcp(float2 d) {
+  float2 r = make_float2(__frcp_rn(d.x), 0.f);
+#pragma unroll
+  for (int it = 0; it < 2; ++it) r = df_mac(r, r, df_add(make_float2(1.f, 0.f), df_neg(df_mul(d, r))));
+  return r;
+}
+__device__ __forceinline__ float2 df_shfl_xor(float2 v, int o) {
+  return make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+}
 __device__ __forceinline__ float2 df_warp_sum(float2 v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    float2 w;
-    w.x = __shfl_xor_sync(0xffffffffu, v.x, o);
-    w.y = __shfl_xor_sync(0xffffffffu, v.y, o);
-    v = df_add(v, w);
-  }
+  for (int o = 16; o > 0; o >>= 1) v = df_add(v, df_shfl_xor(v, o));
   return v;
 }
 
@@ -81,6 +104,8 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_eh_tridiag_df(TriArgsR p) {
   extern __shared__ double smd[];
   constexpr int NW = kTriThreads / 32;
   constexpr int kChainWarp = NW - 1;
+  constexpr int kSumWarp = 2;      // sums the CTAs' parts of s after the barrier
+  constexpr int kOutWarp = 3;      // writes the float64 outputs while the CTA waits at the barrier
   const int n = p.n, G = p.G, g = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int R = g < n ? (n - 1 - g) / G + 1 : 0;
   const int Rmax = (n + G - 1) / G;
@@ -97,15 +122,17 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_eh_tridiag_df(TriArgsR p) {
   float2* rnext = reinterpret_cast<float2*>(p.rnext);
   float2* ybuf = reinterpret_cast<float2*>(p.ybuf);
   float2* vref = reinterpret_cast<float2*>(p.vref);
+  float2* rc2 = reinterpret_cast<float2*>(p.rowcoef);   // [2][4] A, B, Q, E of the published row
+  float2* sp2 = reinterpret_cast<float2*>(p.spart);     // [2][G] each CTA's part of s
   __shared__ float2 red[NW];
-  __shared__ double alpha_sh, tau_sh, scale_sh, beta_sh, hh_sh, ej_sh;
-  __shared__ float2 pj_sh, qj_sh, hhd_sh;
+  __shared__ float2 alpha_sh, dj_sh, tau_sh, scale_sh, beta_sh, ts_sh, hh_sh, pj_sh, qj_sh, ej_sh;
+  const float2 zero2 = make_float2(0.f, 0.f), one2 = make_float2(1.f, 0.f);
 
   for (int lr = 0; lr < R; ++lr) {
     const int r = g + lr * G;
     for (int c = tid; c < n; c += kTriThreads) rows[(size_t)lr * n + c] = df_of(sym_at(p.a, p.lda, r, c));
   }
-  double tauPrev2 = 0.0;   // tau_{j-1}^2
+  float2 tau2 = zero2;     // tau_{j-1}^2
   int first = 0;           // the own rows r > j are lr = first .. R-1
   int jmodG = 0;           // j mod G: this CTA owns row j when jmodG == g
   for (int j = 0; j < n; ++j, jmodG = jmodG + 1 == G ? 0 : jmodG + 1) {
@@ -113,7 +140,8 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_eh_tridiag_df(TriArgsR p) {
     const int Ra = R - first;
     float2* uC = (j & 1) ? ubuf1 : ubuf0;   // this column's reflector, unscaled
     float2* uP = (j & 1) ? ubuf0 : ubuf1;   // previous column's
-    // (A) row j and y of column j-1 into shared memory; s, hh and row j's coefficients (one lane)
+    // (A) row j and y of column j-1 into shared memory; one warp sums s_{j-1} and forms hh and row
+    //     j's coefficients
     {
       float2 ra[kLoadKR], ya[kLoadKR];
 #pragma unroll
@@ -123,11 +151,29 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_eh_tridiag_df(TriArgsR p) {
           if (j == 0) {
             ra[k] = df_of(sym_at(p.a, p.lda, 0, c));
           } else {
-            const float2* rs = rnext + ((j - 1) & 1) * n + c;
-            const float2* ys = ybuf + ((j - 1) & 1) * n + c;
-            ra[k] = __ldcg(rs);
-            ya[k] = __ldcg(ys);
+            ra[k] = __ldcg(rnext + ((j - 1) & 1) * n + c);
+            ya[k] = __ldcg(ybuf + ((j - 1) & 1) * n + c);
           }
+        }
+      }
+      if (wid == kSumWarp) {
+        float2 hh = zero2, P = zero2, Q = zero2, E = zero2;
+        if (j > 0) {
+          const float2* sp = sp2 + ((j - 1) & 1) * G;
+          float2 s = zero2;
+          for (int q = lane; q < G; q += 32) s = df_add(s, __ldcg(sp + q));
+          s = df_warp_sum(s);
+          const float2* rc = rc2 + ((j - 1) & 1) * 4;
+          hh = df_mul(make_float2(0.5f, 0.f), df_mul(tau2, s));
+          P = df_rank2(__ldcg(rc), hh, __ldcg(rc + 1), zero2, zero2);   // A - hh B
+          Q = __ldcg(rc + 2);
+          E = __ldcg(rc + 3);
+        }
+        if (lane == 0) {
+          hh_sh = hh;
+          pj_sh = P;
+          qj_sh = Q;
+          ej_sh = E;
         }
       }
 #pragma unroll
@@ -138,89 +184,80 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_eh_tridiag_df(TriArgsR p) {
           if (j > 0) yP[c] = ya[k];
         }
       }
-      if (tid == 0) {
-        double hh = 0.0, Pj = 0.0, Qj = 0.0, Ej = 0.0;
-        if (j > 0) {
-          const double* rc = p.rowcoef + ((j - 1) & 1) * 4;
-          const double sv = __ldcg(&p.sacc[(j - 1) & 3]);
-          hh = 0.5 * tauPrev2 * sv;
-          Pj = fma(-hh, __ldcg(&rc[1]), __ldcg(&rc[0]));
-          Qj = __ldcg(&rc[2]);
-          Ej = __ldcg(&rc[3]);
-        }
-        hh_sh = hh;
-        ej_sh = Ej;
-        pj_sh = df_of(Pj);
-        qj_sh = df_of(Qj);
-        hhd_sh = df_of(hh);
-      }
     }
-    if (g == 0 && tid == 0) p.sacc[(j + 2) & 3] = 0.0;   // slot of column j-2, read at the start of j-1
     __syncthreads();
-    const double hh = hh_sh;
-    // (B) column j-1's update of row j, its diagonal, the reflector's vector uC[c] (c > j) and sigma
-    float2 sig = make_float2(0.f, 0.f);
-    double dj = 0.0;
+    // (B) column j-1's update of row j, its diagonal (thread 0: c = j), the reflector's vector uC[c]
+    //     (c > j; thread 1 holds alpha at c = j+1) and sigma, two columns per step
     {
       const float2 Pj = pj_sh, Qj = qj_sh;
-      for (int c = j + tid; c < n; c += kTriThreads) {
+      float2 sg0 = zero2, sg1 = zero2;
+      for (int c = j + tid; c < n; c += 2 * kTriThreads) {
+        const int c2 = c + kTriThreads;
         float2 a = uC[c];
+        float2 b = c2 < n ? uC[c2] : zero2;
+        if (j > 0) {
+          a = df_rank2(a, Pj, uP[c], Qj, yP[c]);
+          if (c2 < n) b = df_rank2(b, Pj, uP[c2], Qj, yP[c2]);
+        }
         if (c == j) {
-          dj = df_val(a) - (ej_sh - 2.0 * hh);
+          // the diagonal took its update in the published row but for E - 2 hh
+          dj_sh = df_add(uC[c], df_neg(df_add(ej_sh, df_mul(make_float2(-2.f, 0.f), hh_sh))));
         } else {
-          if (j > 0) a = df_rank2(a, Pj, uP[c], Qj, yP[c]);
           uC[c] = a;
-          if (c == j + 1) alpha_sh = df_val(a);
-          else sig = df_mac(sig, a, a);
+          if (c == j + 1) alpha_sh = a;
+          else sg0 = df_mac(sg0, a, a);
+        }
+        if (c2 < n) {
+          uC[c2] = b;
+          sg1 = df_mac(sg1, b, b);
         }
       }
+      sg0 = df_warp_sum(df_add(sg0, sg1));
+      if (lane == 0) red[wid] = sg0;
     }
     if (j == n - 1) {
-      if (g == 0 && tid == 0) p.d[j] = dj;
+      __syncthreads();
+      if (g == 0 && tid == 0) p.d[j] = df_val(dj_sh);
       break;
     }
-    sig = df_warp_sum(sig);
-    if (lane == 0) red[wid] = sig;
     __syncthreads();
-    // (C) the chain warp: beta, tau, scale of column j;  all warps: own rows r > j, in parts
+    // (C) the chain warp: beta, tau, scale of column j in pairs;  all warps: own rows r > j
     if (wid == kChainWarp) {
-      float2 sg = lane < NW ? red[lane] : make_float2(0.f, 0.f);
+      float2 sg = lane < NW ? red[lane] : zero2;
 #pragma unroll
-      for (int o = 4; o > 0; o >>= 1) {
-        float2 w;
-        w.x = __shfl_xor_sync(0xffffffffu, sg.x, o);
-        w.y = __shfl_xor_sync(0xffffffffu, sg.y, o);
-        sg = df_add(sg, w);
-      }
+      for (int o = 4; o > 0; o >>= 1) sg = df_add(sg, df_shfl_xor(sg, o));
       if (lane == 0) {
-        const double ar = alpha_sh, sgd = df_val(sg);
-        double beta, tau, scale;
-        if ((__double_as_longlong(sgd) << 1) == 0) {
+        const float2 ar = alpha_sh;
+        float2 beta, tau, scale;
+        if (sg.x == 0.f) {
           beta = ar;
-          tau = 0.0;
-          scale = 0.0;
+          tau = zero2;
+          scale = zero2;
         } else {
-          const double S = fma(ar, ar, sgd);
-          const double y = rsqrt_nr(S);
-          const bool neg = __double_as_longlong(ar) < 0;     // beta = -sign(ar) |x|
-          beta = neg ? S * y : -(S * y);
-          const double ib = neg ? y : -y;                    // 1 / beta
-          tau = fma(-ar, ib, 1.0);
-          scale = recip_nr(ar - beta);                       // 1 / (alpha - beta)
+          const float2 S = df_mac(sg, ar, ar);
+          const float2 y = df_rsqrt(S);
+          const bool neg = __float_as_int(ar.x) < 0;            // beta = -sign(ar) |x|
+          const float2 sy = df_mul(S, y);
+          beta = neg ? sy : df_neg(sy);
+          const float2 ib = neg ? y : df_neg(y);                 // 1 / beta
+          tau = df_mac(one2, df_neg(ar), ib);                    // 1 - alpha / beta
+          scale = df_rcp(df_add(ar, df_neg(beta)));              // 1 / (alpha - beta)
         }
         tau_sh = tau;
         scale_sh = scale;
         beta_sh = beta;
+        ts_sh = df_mul(tau, scale);
       }
     }
     if (Ra > 0) {
       // whole rows round-robin over the four schedulers, leftover rows cut into quarters (as in the
-      // float64 kernel); slot k of a row's partial sums is its quarter k
+      // float64 kernel); slot k of a row's partial sums is its quarter k.  Four columns per lane
+      // and step, with four independent sums, so that the pairs' dependent chains overlap.
       const int m = n - 1 - j;
       const int rem = Ra & 3, full = Ra - rem;
       const int sched = wid & 3, half = wid >> 2;
       const int quarter = split_chunk(m, 4);
-      const float2 hhd = hhd_sh, zero2 = make_float2(0.f, 0.f);
+      const float2 hhd = hh_sh;
       int ord = 0;
       for (int it = sched; it < full + 4 * rem; it += 4, ++ord) {
         if ((ord & 1) != half) continue;
@@ -241,29 +278,36 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_eh_tridiag_df(TriArgsR p) {
         float2* row = rows + (size_t)lr * n;
         const float2 P = df_rank2(cA[lr], hhd, cB[lr], zero2, zero2);   // A_r - hh B_r
         const float2 Q = cQ[lr];
-        float2 ax = zero2, bx = zero2, a1 = zero2;
-        for (int c = c0 + lane; c < c1; c += 64) {
-          const int c2 = c + 32;
-          const bool two = c2 < c1;
-          float2 a = row[c];
-          float2 b = two ? row[c2] : zero2;
+        float2 acc[4] = {zero2, zero2, zero2, zero2};
+        float2 a1 = zero2;
+        for (int c = c0 + lane; c < c1; c += 128) {
+          float2 a[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int cq = c + 32 * q;
+            a[q] = cq < c1 ? row[cq] : zero2;
+          }
           if (j > 0) {
-            a = df_rank2(a, P, uP[c], Q, yP[c]);
-            row[c] = a;
-            if (two) {
-              b = df_rank2(b, P, uP[c2], Q, yP[c2]);
-              row[c2] = b;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int cq = c + 32 * q;
+              if (cq < c1) {
+                a[q] = df_rank2(a[q], P, uP[cq], Q, yP[cq]);
+                row[cq] = a[q];
+              }
             }
           }
-          if (c == j + 1) a1 = a;
-          else ax = df_mac(ax, a, uC[c]);
-          if (two) bx = df_mac(bx, b, uC[c2]);
-          if (r == j + 1) {
-            rnext[(j & 1) * n + c] = a;
-            if (two) rnext[(j & 1) * n + c2] = b;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int cq = c + 32 * q;
+            if (cq < c1) {
+              if (cq == j + 1) a1 = a[q];
+              else acc[q] = df_mac(acc[q], a[q], uC[cq]);
+              if (r == j + 1) rnext[(j & 1) * n + cq] = a[q];
+            }
           }
         }
-        ax = df_warp_sum(df_add(ax, bx));
+        const float2 ax = df_warp_sum(df_add(df_add(acc[0], acc[1]), df_add(acc[2], acc[3])));
         if (lane == 0) {
           pacc[i * 4 + k] = ax;
           if (k == 0) pa1[i] = a1;
@@ -271,72 +315,59 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_eh_tridiag_df(TriArgsR p) {
       }
     }
     __syncthreads();
-    // (D) warp 0: y_j[r] = a1 + scale * sum for the own rows and their part of s_j = v_j^T y_j;
-    //     warp 1: the own rows' A, B, Q for column j+1 (E for row j+1, published with it);
-    //     the owner of row j stores u_j; CTA 0 the outputs of column j
-    const double tauC = tau_sh, scC = scale_sh;
+    // (D) warp 0: y_j[r] = a1 + scale * sum for the own rows and the CTA's part of s_j = v_j^T y_j;
+    //     warp 1: row j+1's coefficients (and E = 2 tau y), published with it;
+    //     the owner of row j stores u_j
+    const float2 tauC = tau_sh, scC = scale_sh, tsC = ts_sh;
     auto row_y = [&](int i) {
       float2 acc = pacc[i * 4];
       if (i >= Ra - (Ra & 3)) acc = df_add(df_add(acc, pacc[i * 4 + 1]), df_add(pacc[i * 4 + 2], pacc[i * 4 + 3]));
-      return fma(scC, df_val(acc), df_val(pa1[i]));
-    };
-    auto coefs = [&](int r, double y, double* A, double* B, double* Q) {
-      const double v = r == j + 1 ? 1.0 : df_val(uC[r]) * scC;
-      *A = tauC * scC * y;
-      *B = 2.0 * scC * v;
-      *Q = tauC * v;
+      return df_mac(pa1[i], scC, acc);
     };
     if (wid == 0) {
-      // y and s in double-float (float64 only for the scale and the final sum)
-      const float2 scD = df_of(scC), one2 = make_float2(1.f, 0.f);
-      float2 spd = make_float2(0.f, 0.f);
+      float2 spd = zero2;
       for (int i = lane; i < Ra; i += 32) {
         const int r = g + (first + i) * G;
-        float2 acc = pacc[i * 4];
-        if (i >= Ra - (Ra & 3)) acc = df_add(df_add(acc, pacc[i * 4 + 1]), df_add(pacc[i * 4 + 2], pacc[i * 4 + 3]));
-        const float2 y = df_mac(pa1[i], scD, acc);
+        const float2 y = row_y(i);
         ybuf[(j & 1) * n + r] = y;
-        float2 v = one2;
-        if (r != j + 1) v = df_mac(make_float2(0.f, 0.f), uC[r], scD);
+        const float2 v = r == j + 1 ? one2 : df_mul(uC[r], scC);
         spd = df_mac(spd, v, y);
       }
-      const double sp = df_val(df_warp_sum(spd));
-      if (lane == 0) {
-        atomicAdd(&p.sacc[j & 3], sp);
-        if (g == 0) {
-          p.d[j] = dj;
-          p.e[j] = beta_sh;
-          p.e2[j] = beta_sh * beta_sh;
-          p.tau[j] = tauC;
-          p.vscale[j] = scC;
-        }
-      }
+      spd = df_warp_sum(spd);
+      if (lane == 0) sp2[(j & 1) * G + g] = spd;
     } else if (wid == 1 && Ra > 0 && g + first * G == j + 1 && lane == 0) {
-      // this CTA owns row j+1: publish its coefficients (and E = 2 tau y) before arriving
-      const double y = row_y(0);
-      double A, B, Q;
-      coefs(j + 1, y, &A, &B, &Q);
-      double* rc = p.rowcoef + (j & 1) * 4;
-      rc[0] = A;
-      rc[1] = B;
-      rc[2] = Q;
-      rc[3] = 2.0 * tauC * y;
+      // this CTA owns row j+1 (v = 1): A = tau scale y, B = 2 scale, Q = tau, E = 2 tau y
+      const float2 y = row_y(0);
+      float2* rc = rc2 + (j & 1) * 4;
+      rc[0] = df_mul(tsC, y);
+      rc[1] = df_mul(make_float2(2.f, 0.f), scC);
+      rc[2] = tauC;
+      rc[3] = df_mul(make_float2(2.f, 0.f), df_mul(tauC, y));
     }
     if (jmodG == g) {   // the owner of row j stores u_j (pairs; k_eh_vscale_df scales them)
       for (int c = j + 2 + tid; c < n; c += kTriThreads) vref[(size_t)j * n + c] = uC[c];
     }
     grid_arrive(p.bar);
+    // while the other CTAs arrive: the own rows' coefficients for column j+1, tau_j^2, and (CTA 0)
+    // the float64 outputs of column j
     if (wid == 1) {
       for (int i = lane; i < Ra; i += 32) {
         const int lr = first + i, r = g + lr * G;
-        double A, B, Q;
-        coefs(r, row_y(i), &A, &B, &Q);
-        cA[lr] = df_of(A);
-        cB[lr] = df_of(B);
-        cQ[lr] = df_of(Q);
+        const float2 y = row_y(i);
+        const float2 v = r == j + 1 ? one2 : df_mul(uC[r], scC);
+        cA[lr] = df_mul(tsC, y);
+        cB[lr] = df_mul(make_float2(2.f, 0.f), df_mul(scC, v));
+        cQ[lr] = df_mul(tauC, v);
       }
+    } else if (wid == kOutWarp && g == 0 && lane == 0) {
+      const double be = df_val(beta_sh);
+      p.d[j] = df_val(dj_sh);
+      p.e[j] = be;
+      p.e2[j] = be * be;
+      p.tau[j] = df_val(tauC);
+      p.vscale[j] = df_val(scC);
     }
-    tauPrev2 = tauC * tauC;
+    tau2 = df_mul(tauC, tauC);
     if (!grid_wait(p.bar, (unsigned)(G * (j + 1)), p.err)) return;
   }
 }

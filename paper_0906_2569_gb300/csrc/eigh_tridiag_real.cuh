@@ -44,6 +44,7 @@ struct TriArgsR {
   double* sacc;         // [4] s of the last columns (slot j & 3), accumulated by atomics
   unsigned int* bar;    // barrier arrival counter (zero at launch)
   int* err;             // device error word
+  double* spart;        // [2][G] each CTA's part of s (the double-float kernel's pairs)
 };
 
 __global__ void __launch_bounds__(kTriThreads, 1) k_eh_tridiag_r(TriArgsR p) {

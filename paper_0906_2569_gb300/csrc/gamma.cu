@@ -317,7 +317,13 @@ static int gamma_apply_t(Context& c, int ik, const S* x, S* y, int nb, bool scal
   int ns32 = 0;
   if (p.nproj > 0) {
     constexpr bool x32 = sizeof(S) == sizeof(float2);
-    if (nl_prec(c) == HPSI_FP64) {
+    const int np = nl_prec(c);
+    if (np == kNlProj64 && c.precision == HPSI_MIXED) {
+      // projections in float64, add_vuspsi on the tensor cores
+      double* w = nullptr;
+      rc = gamma_w_fp64(c, p, x, x32, nb, scaled, &w);
+      if (!rc) rc = gamma_add_tc(c, p, w, nb, &nl32, &ns32);
+    } else if (np == HPSI_FP64 || np == kNlProj64) {
       const int nr = 2 * ((p.npw + 1) / 2);
       rc = ensure_buffer(c, &c.ws.gnl, &c.ws.gnlbytes, sizeof(double) * (size_t)nb * nr);
       if (rc) return rc;

@@ -144,8 +144,8 @@ struct Context {
   int tc_kmax = 0;                     // mixed calbec: max 64-wide K-steps per split (0: automatic)
   int prec_override = -1;              // >= 0: apply H at this precision instead of `precision`
   int nl_prec_override = -1;           // >= 0: the nonlocal term alone at this precision
-  int final_fp64 = 1;                  // mixed davidson_solve: final Rayleigh quotients with the float64 H
-                                       // (2: float64 nonlocal term, local term at the working precision)
+  int final_fp64 = 2;                  // mixed davidson_solve: final Rayleigh quotients with float64
+                                       // projections and D (2), the float64 H (1), the mixed H (0)
   int basis_factor = 0;                // Davidson: the reduced basis grows to basis_factor * N vectors
                                        // (0: 3 for a mixed context, 4 for float64)
   int autotune = 1;                    // time the fast-path plans on the first apply of a problem
@@ -189,13 +189,15 @@ struct Context {
 
 // Precision at which H is applied right now.
 inline int cur_prec(const Context& c) { return c.prec_override >= 0 ? c.prec_override : c.precision; }
-// Precision of the nonlocal term right now.
+// Precision of the nonlocal term right now: HPSI_FP64, HPSI_MIXED, or kNlProj64 (the projections
+// <beta|psi> and D in float64, add_vuspsi on the tensor cores; mixed contexts only).
+constexpr int kNlProj64 = 2;
 inline int nl_prec(const Context& c) { return c.nl_prec_override >= 0 ? c.nl_prec_override : cur_prec(c); }
-// Bracket the final Rayleigh quotients of a mixed solve: HPSI_OPT_FINAL_FP64 1 applies H in float64,
-// 2 only its nonlocal term.
+// Bracket the final Rayleigh quotients of a mixed solve: HPSI_OPT_FINAL_FP64 1 applies H in float64;
+// 2 the projections in float64 and the rest at the working precision.
 inline void final_precision_begin(Context& c) {
   if (c.final_fp64 == 1) c.prec_override = HPSI_FP64;
-  else if (c.final_fp64 == 2) c.nl_prec_override = HPSI_FP64;
+  else if (c.final_fp64 == 2) c.nl_prec_override = kNlProj64;
 }
 inline void final_precision_end(Context& c) {
   c.prec_override = -1;
@@ -301,6 +303,12 @@ void gamma_release(Context& c);
 // [*nsplit][nb][nr] (to be added in float64) in the mixed workspace and points *part at them.
 int gamma_nonlocal_fp64(Context& c, const Problem& p, const void* x, bool x32, int nb, bool scaled, double* out);
 int gamma_prepare_tc(Context& c, Problem& p);
+// The projection half in float64 (w = D' <betar|x>, real form; w = D <beta|psi>, complex form),
+// left in the workspace, and add_vuspsi from such a w on the tensor cores (mixed contexts).
+int gamma_w_fp64(Context& c, const Problem& p, const void* x, bool x32, int nb, bool scaled, double** w);
+int nonlocal_w_fp64(Context& c, const Problem& p, const double2* psi, int nbnd, double2** w);
+int gamma_add_tc(Context& c, const Problem& p, const double* w, int nb, const float** part, int* nsplit);
+int nonlocal_add_tc(Context& c, const Problem& p, const double2* w, double2* hpsi, int nbnd);
 int gamma_nonlocal_mixed(Context& c, const Problem& p, const void* x, bool x32, int nb, bool scaled,
                          const float** part, int* nsplit);
 void scf_release(Context& c);

@@ -340,8 +340,8 @@ __global__ void __launch_bounds__(256) k_addvus64r(int nr, int nproj, int nb, co
 
 }  // namespace
 
-int gamma_nonlocal_fp64(Context& c, const Problem& p, const void* x, bool x32, int nb, bool scaled, double* out) {
-  if (p.nproj == 0 || nb == 0) return HPSI_OK;
+// w = D' <betar|x> of the real form in float64 (calbec and D-scale); *w points into the workspace.
+int gamma_w_fp64(Context& c, const Problem& p, const void* x, bool x32, int nb, bool scaled, double** wout) {
   if (!p.d_betar) return fail(c, HPSI_EINVAL, "Gamma-form projectors are not prepared");
   const int nr = 2 * ((p.npw + 1) / 2);
   const int tilesp = (p.nproj + RB_TP - 1) / RB_TP, tilesb = (nb + RB_TB - 1) / RB_TB;
@@ -368,6 +368,18 @@ int gamma_nonlocal_fp64(Context& c, const Problem& p, const void* x, bool x32, i
   HPSI_LAUNCH(c, HPSI_K_DSCALE,
               (k_dscale64r<<<(n + 255) / 256, 256, 0, c.stream>>>(p.nproj, nb, nsplit, part, p.d_rowptr, p.d_col,
                                                                   p.d_dvalr, w)));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "Gamma-form float64 projection kernels launch");
+  *wout = w;
+  return HPSI_OK;
+}
+
+int gamma_nonlocal_fp64(Context& c, const Problem& p, const void* x, bool x32, int nb, bool scaled, double* out) {
+  if (p.nproj == 0 || nb == 0) return HPSI_OK;
+  const int nr = 2 * ((p.npw + 1) / 2);
+  double* w = nullptr;
+  int rc = gamma_w_fp64(c, p, x, x32, nb, scaled, &w);
+  if (rc) return rc;
   HPSI_LAUNCH(c, HPSI_K_ADDVUS,
               (k_addvus64r<<<dim3((nr + RA_TR - 1) / RA_TR, (nb + RA_TB - 1) / RA_TB), 256, 0, c.stream>>>(
                   nr, p.nproj, nb, w, p.d_betar, out)));
@@ -376,13 +388,12 @@ int gamma_nonlocal_fp64(Context& c, const Problem& p, const void* x, bool x32, i
   return HPSI_OK;
 }
 
-int nonlocal_apply_fp64(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd) {
-  if (p.nproj == 0 || nbnd == 0) return HPSI_OK;
+// w = D <beta|psi> of the complex form in float64 (calbec and D-scale); *w points into the workspace.
+int nonlocal_w_fp64(Context& c, const Problem& p, const double2* psi, int nbnd, double2** wout) {
   const int tilesp = (p.nproj + CB_TP - 1) / CB_TP, tilesb = (nbnd + CB_TB - 1) / CB_TB;
-  int nsplit = std::max(1, (3 * c.sm_count) / std::max(1, tilesp * tilesb));
-  int kchunk = (p.npw + nsplit - 1) / nsplit;
-  kchunk = std::max(CB_TK * 4, ((kchunk + CB_TK - 1) / CB_TK) * CB_TK);
-  nsplit = (p.npw + kchunk - 1) / kchunk;
+  int nsplit = 0, kchunk = 0;
+  size_t bytes = 0;
+  nonlocal_fp64_plan(c, p, nbnd, &nsplit, &kchunk, &bytes);
   int rc = ensure_buffer(c, &c.ws.part, &c.ws.partbytes, sizeof(double2) * (size_t)nsplit * nbnd * p.nproj);
   if (rc) return rc;
   rc = ensure_buffer(c, &c.ws.w, &c.ws.wbytes, sizeof(double2) * (size_t)nbnd * p.nproj);
@@ -396,6 +407,17 @@ int nonlocal_apply_fp64(Context& c, const Problem& p, const double2* psi, double
   HPSI_LAUNCH(c, HPSI_K_DSCALE,
               (k_dscale64<<<(n + 255) / 256, 256, 0, c.stream>>>(p.nproj, nbnd, nsplit, part, p.d_rowptr, p.d_col,
                                                                  p.d_dval, w)));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "float64 projection kernels launch");
+  *wout = w;
+  return HPSI_OK;
+}
+
+int nonlocal_apply_fp64(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd) {
+  if (p.nproj == 0 || nbnd == 0) return HPSI_OK;
+  double2* w = nullptr;
+  int rc = nonlocal_w_fp64(c, p, psi, nbnd, &w);
+  if (rc) return rc;
   HPSI_LAUNCH(c, HPSI_K_ADDVUS,
               (k_addvus64<<<dim3((p.npw + AV_TG - 1) / AV_TG, (nbnd + AV_TB - 1) / AV_TB), 256, 0, c.stream>>>(
                   p.npw, p.nproj, nbnd, w, p.d_beta, hpsi)));

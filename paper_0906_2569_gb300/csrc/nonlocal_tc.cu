@@ -209,19 +209,22 @@ __global__ void __launch_bounds__(128, 1)
       if (!mbar_wait(smem_u32(&full_bar[s]), round & 1, &abort_flag)) break;
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       const unsigned char* st = smem + s * Cfg::stage_bytes;
+      // smallest products first: the float32 accumulation rounds (with a bias, measured) relative to
+      // the running sum, so the 2^-16 and 2^-8 terms go in while it is still small and only the last
+      // four MMAs of a K-step, the leading products, round at full magnitude
 #pragma unroll
-      for (int kk = 0; kk < TBK / 16; ++kk) {
+      for (int lvl = NT - 1; lvl >= 0; --lvl)
 #pragma unroll
-        for (int ia = 0; ia < NT; ++ia)
+        for (int ia = 0; ia <= lvl; ++ia) {
+          const int ib = lvl - ia;
 #pragma unroll
-          for (int ib = 0; ib < NT; ++ib) {
-            if (ia + ib >= NT) continue;
+          for (int kk = 0; kk < TBK / 16; ++kk) {
             const uint64_t da = sw128_desc(smem_u32(st + ia * kTileBytes) + kk * 32);
             const uint64_t db = sw128_desc(smem_u32(st + (NT + ib) * kTileBytes) + kk * 32);
             mma_bf16(tmem, da, db, acc);
             acc = 1;
           }
-      }
+        }
       mma_commit(smem_u32(&empty_bar[s]));
     }
     mma_commit(smem_u32(&acc_bar));
@@ -551,6 +554,18 @@ __global__ void k_dscale_tc_r(int nproj, int nb, int nsplit, int ka, const float
   split_store<NT>(acc, wa, (size_t)nb * ka, (size_t)b * ka + p);
 }
 
+// A of add_vuspsi from float64 rows: out[row][k] = src[row][k] for k < kin, 0 up to kpad (w as
+// interleaved (re, im) pairs, kin = 2P, or real, kin = P).
+template <int NT>
+__global__ void k_split_rows64(int rows, int kin, int kpad, const double* __restrict__ src,
+                               __nv_bfloat16* __restrict__ out) {
+  const size_t plane = (size_t)rows * kpad;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < plane; i += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(i / kpad), k = (int)(i % kpad);
+    split_store<NT>(k < kin ? src[(size_t)r * kin + k] : 0.0, out, plane, i);
+  }
+}
+
 // ---- host side ------------------------------------------------------------------------------
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -807,7 +822,75 @@ int gamma_apply_tc(Context& c, const Problem& p, const R* x, int nb, bool scaled
   return HPSI_OK;
 }
 
+// add_vuspsi on the tensor cores from a float64 w: the complex form (w [nb][P] complex, into hpsi)
+// or the real form (w [nb][P] real, float partials [*nout][nb][nr] left in the workspace).  Each
+// float32 partial sums one 64-wide K-step: the tensor cores' float32 accumulation is biased (its
+// error does not average out in <psi|V_NL psi>, measured 1.3e-6 Ha on the 36785-PW cell at eight
+// K-steps per partial), so the quotients this serves get the shortest accumulations, added in
+// float64.
+template <int NT>
+int add_from_w64(Context& c, const Problem& p, const double* w, bool real, int nb, double2* hpsi, const float** out,
+                 int* nout) {
+  const int P = p.nproj;
+  const int kin = real ? P : 2 * P, ka = round_up(kin, TBK);
+  const int N = real ? 2 * ((p.npw + 1) / 2) : 2 * p.npw;   // output columns
+  const __nv_bfloat16* badd;
+  if (real) {
+    const int kc = round_up(N, TBK);
+    badd = reinterpret_cast<const __nv_bfloat16*>(p.d_betar_bf) + (size_t)NT * P * kc;
+  } else {
+    badd = reinterpret_cast<const __nv_bfloat16*>(p.d_beta_bf) + (size_t)NT * P * round_up(2 * p.npw, TBK);
+  }
+  const int naks = ka / TBK;
+  const int aksplit = 1, ansplit = naks;
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t wb = al(sizeof(__nv_bfloat16) * (size_t)NT * nb * ka);
+  const bool partials = real || ansplit > 1;
+  const size_t ab = partials ? al(sizeof(float) * (size_t)ansplit * nb * N) : 0;
+  int rc = ensure_buffer(c, &c.ws.mixed, &c.ws.mixedbytes, wb + ab);
+  if (rc) return rc;
+  unsigned char* w0 = static_cast<unsigned char*>(c.ws.mixed);
+  __nv_bfloat16* wa = reinterpret_cast<__nv_bfloat16*>(w0);
+  float* apart = reinterpret_cast<float*>(w0 + wb);
+  HPSI_LAUNCH(c, HPSI_K_SPLIT, (k_split_rows64<NT><<<4 * c.sm_count, 256, 0, c.stream>>>(nb, kin, ka, w, wa)));
+  if (partials) {
+    rc = launch_gemm<NT>(c, wa, nb, badd, N, ka, ansplit, aksplit, 0, apart, nullptr, 0, HPSI_K_ADDVUS);
+    if (rc) return rc;
+    if (real) {
+      *out = apart;
+      *nout = ansplit;
+    } else {
+      const size_t nel = (size_t)nb * p.npw;
+      HPSI_LAUNCH(c, HPSI_K_ADDVUS, (k_add_partials<<<(int)std::min<size_t>(8 * c.sm_count, (nel + 255) / 256), 256,
+                                                      0, c.stream>>>(nb, p.npw, ansplit, apart, hpsi)));
+    }
+  } else {
+    rc = launch_gemm<NT>(c, wa, nb, badd, N, ka, 1, naks, 1, nullptr, hpsi, p.npw, HPSI_K_ADDVUS);
+    if (rc) return rc;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "tensor-core add_vuspsi launch");
+  return HPSI_OK;
+}
+
 }  // namespace
+
+int nonlocal_add_tc(Context& c, const Problem& p, const double2* w, double2* hpsi, int nbnd) {
+  if (p.nproj == 0 || nbnd == 0) return HPSI_OK;
+  if (!p.d_beta_bf) return fail(c, HPSI_EINVAL, "bf16 projector terms are not prepared");
+  const double* wd = reinterpret_cast<const double*>(w);
+  return c.nl_terms == 3 ? add_from_w64<3>(c, p, wd, false, nbnd, hpsi, nullptr, nullptr)
+                         : add_from_w64<2>(c, p, wd, false, nbnd, hpsi, nullptr, nullptr);
+}
+
+int gamma_add_tc(Context& c, const Problem& p, const double* w, int nb, const float** part, int* nsplit) {
+  *part = nullptr;
+  *nsplit = 0;
+  if (p.nproj == 0 || nb == 0) return HPSI_OK;
+  if (!p.d_betar_bf) return fail(c, HPSI_EINVAL, "Gamma-form bf16 projector terms are not prepared");
+  return c.nl_terms == 3 ? add_from_w64<3>(c, p, w, true, nb, nullptr, part, nsplit)
+                         : add_from_w64<2>(c, p, w, true, nb, nullptr, part, nsplit);
+}
 
 int gamma_prepare_tc(Context& c, Problem& p) {
   if (p.nproj == 0 || p.d_betar_bf) return HPSI_OK;

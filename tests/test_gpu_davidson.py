@@ -246,3 +246,20 @@ def test_davidson_mixed_tc_inner_products(lib):
     v = x.cpu().numpy()
     assert np.max(np.abs(np.conj(v) @ v.T - np.eye(160))) < 1e-4
     assert B.hpsi_kernel_stats(ctx, B.KERNELS.index("split"))[0] > 3 * it
+
+
+@pytest.mark.parametrize("final", [0, 1, 2])
+def test_davidson_mixed_c2_final_quotients(lib, final):
+    """The final Rayleigh quotients of the mixed solve: 1 with the float64 H, 2 with float64
+    projections <beta|psi> and D only (the rest at the working precision), 0 with the mixed H.
+    Modes 1 and 2 stay within 1e-6 Ha of the oracle; every mode within 1e-5 Ha."""
+    import torch
+    from paper_0906_2569_gb300 import binding as B
+    p = workloads.config2()
+    ctx, m, vr, beta, d = _setup(p, precision=B.HPSI_MIXED)
+    B.hpsi_set_option(ctx, B.HPSI_OPT_FINAL_FP64, final)
+    x = torch.from_numpy(workloads.psi0(p.lattice, p.kpts[0], m, p.nbnd, p.psi_seed)).cuda()
+    eig, it, res, rc = B.davidson_solve(ctx, 0, x, 1e-5, 300)
+    err = float(np.max(np.abs(eig - np.asarray(_golden("c2")))))
+    print(f"c2 mixed, final quotients mode {final}: {it} iterations, max eigenvalue error {err:.2e} Ha")
+    assert err < (1e-5 if final == 0 else 1e-6)

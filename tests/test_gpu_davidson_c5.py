@@ -41,11 +41,11 @@ def c5():
         eig, it, res, rc = B.davidson_solve_gamma(ctx, 0, x, tol, 300)
         out[prec] = (eig, it, res)
         if prec == B.HPSI_MIXED:
-            # the final quotients with only the nonlocal term in float64
-            B.hpsi_set_option(ctx, B.HPSI_OPT_FINAL_FP64, 2)
+            # the final quotients with the whole H in float64 (the default takes only the projections)
+            B.hpsi_set_option(ctx, B.HPSI_OPT_FINAL_FP64, 1)
             x = torch.from_numpy(x0).cuda()
             eig, it, res, rc = B.davidson_solve_gamma(ctx, 0, x, tol, 300)
-            out["final_nl64"] = (eig, it, res)
+            out["final_h64"] = (eig, it, res)
         ctx.close()
         del x
         torch.cuda.empty_cache()
@@ -72,15 +72,15 @@ def test_c5_mixed_matches_oracle_and_fp64(c5):
     assert err < 1e-6 and err64 < 1e-6
 
 
-def test_c5_mixed_final_nonlocal_fp64(c5):
-    """HPSI_OPT_FINAL_FP64 = 2 (float32 local term, float64 nonlocal term in the final quotients):
-    within 1e-6 Ha of the oracle and of the float64 solve."""
+def test_c5_mixed_final_float64_h(c5):
+    """HPSI_OPT_FINAL_FP64 = 1 (the final quotients with the float64 H): within 1e-6 Ha of the oracle
+    and of the float64 solve."""
     from paper_0906_2569_gb300 import binding as B
-    eig, it, res = c5["final_nl64"]
+    eig, it, res = c5["final_h64"]
     g = c5["gold"]
     err = float(np.max(np.abs(eig[:len(g)] - g)))
     e64 = c5[B.HPSI_FP64][0]
     d64 = float(np.max(np.abs(eig - e64)))
-    print(f"c5 mixed, float64 nonlocal only at the end: {it} iterations, max error vs oracle {err:.2e} Ha, "
+    print(f"c5 mixed, float64 H at the end: {it} iterations, max error vs oracle {err:.2e} Ha, "
           f"vs float64 over all {len(eig)} bands {d64:.2e} Ha")
     assert err < 1e-6 and d64 < 1e-6

@@ -278,18 +278,19 @@ def test_gamma_many_cells(lib):
     ctx.close()
 
 
-def test_gamma_davidson_final_nonlocal_fp64(lib):
-    """HPSI_OPT_FINAL_FP64 = 2: the final Rayleigh quotients of the mixed solve with the float64
-    nonlocal term and the float32 local term; eigenvalues within 1e-6 Ha of the golden values."""
+@pytest.mark.parametrize("final", [1, 2])
+def test_gamma_davidson_final_quotients(lib, final):
+    """HPSI_OPT_FINAL_FP64 = 1 (float64 H) and 2 (float64 projections and D, the rest at the working
+    precision; the default): eigenvalues of the mixed solve within 1e-6 Ha of the golden values."""
     import torch
     from paper_0906_2569_gb300 import binding as B
     p = workloads.config2()
     ctx, m, vr, beta, d = _setup(p, B.HPSI_MIXED)
-    B.hpsi_set_option(ctx, B.HPSI_OPT_FINAL_FP64, 2)
+    B.hpsi_set_option(ctx, B.HPSI_OPT_FINAL_FP64, final)
     x = torch.from_numpy(np.ascontiguousarray(
         oracle.gamma.to_half(workloads.psi0(p.lattice, p.kpts[0], m, p.nbnd, p.psi_seed), m))).cuda()
     eig, it, res, rc = B.davidson_solve_gamma(ctx, 0, x, 1e-5, 300)
     err = float(np.max(np.abs(eig - np.asarray(_golden("c2")[:p.nbnd]))))
-    print(f"c2 mixed, float64 nonlocal only in the final quotients: {it} iterations, max eigenvalue error {err:.2e}")
+    print(f"c2 Gamma mixed, final quotients mode {final}: {it} iterations, max eigenvalue error {err:.2e}")
     assert err < 1e-6
     ctx.close()
