@@ -1037,10 +1037,18 @@ static int davidson_run_mixed(Context& c, DavHandles& h, int ik, int nbnd, doubl
   // subspace GEMMs: float32 on the CUDA cores, or float32 emulated with bf16 tensor-core products
   BCK(cublasSetMathMode(h.blas, c.fp32_gemm == 1 ? CUBLAS_FP32_EMULATED_BF16X9_MATH : CUBLAS_DEFAULT_MATH),
       "cublasSetMathMode");
-  if (c.fp32_gemm == 1) BCK(cublasSetEmulationStrategy(h.blas, CUBLAS_EMULATION_STRATEGY_EAGER), "cublasSetEmulationStrategy");
+  if (c.fp32_gemm == 1) {
+    BCK(cublasSetEmulationStrategy(h.blas, CUBLAS_EMULATION_STRATEGY_EAGER), "cublasSetEmulationStrategy");
+    // finite operands (a NaN would surface in the float64 residual norms): no special-value passes
+    BCK(cublasSetEmulationSpecialValuesSupport(h.blas, CUDA_EMULATION_SPECIAL_VALUES_SUPPORT_NONE),
+        "cublasSetEmulationSpecialValuesSupport");
+  }
   struct MathReset {
     cublasHandle_t b;
-    ~MathReset() { cublasSetMathMode(b, CUBLAS_DEFAULT_MATH); }
+    ~MathReset() {
+      cublasSetMathMode(b, CUBLAS_DEFAULT_MATH);
+      cublasSetEmulationSpecialValuesSupport(b, CUDA_EMULATION_SPECIAL_VALUES_SUPPORT_DEFAULT);
+    }
   } math_reset{h.blas};
   w.phi_split.invalidate();
   w.hphi_split.invalidate();

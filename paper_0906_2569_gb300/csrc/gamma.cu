@@ -1108,10 +1108,17 @@ int gamma_davidson_run(Context& c, int ik, int nbnd, double tol, int maxiter, do
     // tensor-core products (float32-accurate); 0: float32 on the CUDA cores
     const bool emu = c.gamma_gemm == 1;
     GBK(cublasSetMathMode(h->blas, emu ? CUBLAS_FP32_EMULATED_BF16X9_MATH : CUBLAS_DEFAULT_MATH), "cublasSetMathMode");
-    if (emu) GBK(cublasSetEmulationStrategy(h->blas, CUBLAS_EMULATION_STRATEGY_EAGER), "cublasSetEmulationStrategy");
+    if (emu) {
+      GBK(cublasSetEmulationStrategy(h->blas, CUBLAS_EMULATION_STRATEGY_EAGER), "cublasSetEmulationStrategy");
+      // the basis and its products are finite (a NaN would surface in the float64 residual norms),
+      // so the emulation needs no infinity / NaN patching passes over its operands
+      GBK(cublasSetEmulationSpecialValuesSupport(h->blas, CUDA_EMULATION_SPECIAL_VALUES_SUPPORT_NONE),
+          "cublasSetEmulationSpecialValuesSupport");
+    }
     GammaDavidson<float> d(c, *h, ik);
     const int rc = d.run(nbnd, tol, maxiter, psio, eig_out, iters_out, resnorm_out);
     cublasSetMathMode(h->blas, CUBLAS_DEFAULT_MATH);
+    cublasSetEmulationSpecialValuesSupport(h->blas, CUDA_EMULATION_SPECIAL_VALUES_SUPPORT_DEFAULT);
     return rc;
   }
   GammaDavidson<double> d(c, *h, ik);
