@@ -440,6 +440,7 @@ static void free_problem(Problem& p) {
   cudaFree(p.d_betar);
   cudaFree(p.d_dvalr);
   cudaFree(p.d_betar_bf);
+  cudaFree(p.d_betar_df);
 }
 
 static void free_context(Context& c) {
@@ -467,6 +468,7 @@ static void free_context(Context& c) {
   cudaFree(c.ws.gin);
   cudaFree(c.ws.gout);
   cudaFree(c.ws.gnl);
+  cudaFree(c.ws.gdf);
   if (c.graph.exec) cudaGraphExecDestroy(c.graph.exec);
   if (c.cap_stream) cudaStreamDestroy(c.cap_stream);
   davidson_release(c);

@@ -193,9 +193,107 @@ __device__ bool orth_normalize(int n, double* z, const double* __restrict__ Z, i
 
 // One warp (one CTA) per cluster of the wanted eigenvalues; lane 0 factors T - lam I and runs the
 // solves, the warp orthogonalises and normalises.  Vectors go to Z (column i, leading dim n).
+// Inverse iteration for the eigenvalues without a neighbour within the cluster tolerance, one per
+// lane: a float64 warp instruction costs the same with one active lane as with 32, so 32 of the
+// serial tridiagonal recurrences share each instruction.  Per lane: T - lambda I = P L U with partial
+// pivoting (the pivot choice as selects, the row interchanges as one ballot mask per step), then
+// kInvIters solves from a hashed start, normalised after each.  The factors and z live in a global
+// scratch laid out [k][lane] per warp (5 n 32 doubles and n masks), so every step's accesses are
+// coalesced.  Members of clusters are left to k_eh_invit.
+__global__ void __launch_bounds__(32) k_eh_invit_lanes(int n, const double* __restrict__ d,
+                                                       const double* __restrict__ e, int nwant,
+                                                       const double* __restrict__ lam, double* __restrict__ Z,
+                                                       double* __restrict__ scratch, int* __restrict__ status) {
+  const int lane = threadIdx.x, i = blockIdx.x * 32 + lane;
+  double glo, ghi, emax2;
+  gershgorin(n, d, e, &glo, &ghi, &emax2);
+  double tnorm = fmax(fabs(glo), fabs(ghi));
+  if (!(tnorm > 0.0)) tnorm = 1.0;
+  const double ctol = 1e-10 * tnorm, tiny = DBL_EPSILON * tnorm;
+  bool mine = i < nwant;
+  if (mine && i > 0 && lam[i] - lam[i - 1] <= ctol) mine = false;
+  if (mine && i + 1 < nwant && lam[i + 1] - lam[i] <= ctol) mine = false;
+  if (__ballot_sync(0xffffffffu, mine) == 0u) return;
+  const double li = mine ? lam[i] : lam[0];
+  double* base = scratch + (size_t)blockIdx.x * ((size_t)5 * 32 * n + (n + 1) / 2);
+  double* SL = base + lane;
+  double* SU1 = SL + (size_t)32 * n;
+  double* SU2 = SU1 + (size_t)32 * n;
+  double* SU3 = SU2 + (size_t)32 * n;
+  double* Zs = SU3 + (size_t)32 * n;
+  unsigned* PIV = reinterpret_cast<unsigned*>(base + (size_t)5 * 32 * n);
+  constexpr long long kMag = 0x7fffffffffffffffLL;
+  auto guard = [&](double u) {
+    return (__double_as_longlong(u) & kMag) < (__double_as_longlong(tiny) & kMag) ? (u < 0.0 ? -tiny : tiny) : u;
+  };
+  double al = d[0] - li, be = n > 1 ? e[0] : 0.0;
+  for (int k = 0; k < n - 1; ++k) {
+    const double sub = e[k], dn = d[k + 1] - li, cn = k + 1 < n - 1 ? e[k + 1] : 0.0;
+    const bool np = (__double_as_longlong(al) & kMag) >= (__double_as_longlong(sub) & kMag);
+    const double ui = recip_nr(np ? guard(al) : sub);
+    const double l = (np ? sub : al) * ui;
+    SL[(size_t)k * 32] = l;
+    SU1[(size_t)k * 32] = ui;
+    SU2[(size_t)k * 32] = np ? be : dn;
+    SU3[(size_t)k * 32] = np ? 0.0 : cn;
+    const unsigned pv = __ballot_sync(0xffffffffu, !np);
+    if (lane == 0) PIV[k] = pv;
+    const double nal = fma(-l, np ? be : dn, np ? dn : be);
+    be = np ? cn : -l * cn;
+    al = nal;
+  }
+  SU1[(size_t)(n - 1) * 32] = recip_nr(guard(al));
+  double nn = 0.0;
+  for (int k = 0; k < n; ++k) {
+    const double v = hash_unit((unsigned)i, (unsigned)k);
+    Zs[(size_t)k * 32] = v;
+    nn = fma(v, v, nn);
+  }
+  bool ok = true;
+  double sc = 1.0 / sqrt(nn);
+  __syncwarp();
+  for (int it = 0; it < kInvIters; ++it) {
+    // forward: row interchanges and L
+    double zk = Zs[0] * sc;
+    for (int k = 0; k < n - 1; ++k) {
+      const double z1 = Zs[(size_t)(k + 1) * 32] * sc;
+      const bool sw = (PIV[k] >> lane) & 1u;
+      const double a = sw ? z1 : zk, b = sw ? zk : z1;
+      Zs[(size_t)k * 32] = a;
+      zk = fma(-SL[(size_t)k * 32], a, b);
+    }
+    // backward: U (three diagonals), with the squared norm of the result
+    double z2 = zk * SU1[(size_t)(n - 1) * 32];
+    Zs[(size_t)(n - 1) * 32] = z2;
+    nn = z2 * z2;
+    double z1 = 0.0;
+    if (n >= 2) {
+      z1 = (Zs[(size_t)(n - 2) * 32] - SU2[(size_t)(n - 2) * 32] * z2) * SU1[(size_t)(n - 2) * 32];
+      Zs[(size_t)(n - 2) * 32] = z1;
+      nn = fma(z1, z1, nn);
+    }
+    for (int k = n - 3; k >= 0; --k) {
+      const double zz = (Zs[(size_t)k * 32] - SU2[(size_t)k * 32] * z1 - SU3[(size_t)k * 32] * z2) * SU1[(size_t)k * 32];
+      Zs[(size_t)k * 32] = zz;
+      nn = fma(zz, zz, nn);
+      z2 = z1;
+      z1 = zz;
+    }
+    if (!(nn > 0.0) || !isfinite(nn)) ok = false;
+    sc = ok ? 1.0 / sqrt(nn) : 1.0;
+  }
+  if (!mine) return;
+  if (!ok) {
+    atomicExch(status, 1);
+    return;
+  }
+  double* zi = Z + (size_t)i * n;
+  for (int k = 0; k < n; ++k) zi[k] = Zs[(size_t)k * 32] * sc;
+}
+
 __global__ void __launch_bounds__(32) k_eh_invit(int n, const double* __restrict__ d, const double* __restrict__ e,
                                                  int nwant, const double* __restrict__ lam, double* __restrict__ Z,
-                                                 int* __restrict__ status) {
+                                                 int* __restrict__ status, int skip_single) {
   extern __shared__ double sh[];
   double* sd = sh;
   double* se = sd + n;
@@ -213,6 +311,7 @@ __global__ void __launch_bounds__(32) k_eh_invit(int n, const double* __restrict
   if (!(tnorm > 0.0)) tnorm = 1.0;
   const double ctol = 1e-10 * tnorm;
   if (i0 > 0 && lam[i0] - lam[i0 - 1] <= ctol) return;   // not the first of its cluster
+  if (skip_single && (i0 + 1 >= nwant || lam[i0 + 1] - lam[i0] > ctol)) return;   // k_eh_invit_lanes has it
   for (int k = lane; k < n; k += 32) {
     sd[k] = d[k];
     se[k] = k < n - 1 ? e[k] : 0.0;
@@ -462,6 +561,8 @@ struct EighState {
   int ncap = 0, wcap = 0;
   double *d = nullptr, *e = nullptr, *e2 = nullptr, *sacc = nullptr, *lam = nullptr, *Z = nullptr, *Z2 = nullptr;
   double* spart = nullptr;   // [2][kMaxCtas] the double-float reduction's per-CTA parts of s
+  double* invs = nullptr;    // k_eh_invit_lanes scratch
+  size_t invcap = 0;
   double* gram = nullptr;
   double2 *tau = nullptr, *vref = nullptr, *ybuf = nullptr, *rnext = nullptr, *rowcoef = nullptr, *vscale = nullptr;
   double2 *wgram = nullptr, *tfac = nullptr, *w1 = nullptr, *w2 = nullptr;   // compact-WY blocks
@@ -479,6 +580,7 @@ void free_state(EighState& s) {
                   s.vref, s.ybuf,  s.rnext, s.rowcoef, s.wgram, s.w1, s.bar,  s.info, s.vscale, s.Z2, s.tfac, s.w2,
                   s.spart};
   for (void* q : ptrs) cudaFree(q);
+  cudaFree(s.invs);
   const EighState keep = s;
   s = EighState{};
   s.blas = keep.blas;
@@ -539,6 +641,34 @@ int grow(Context& c, EighState& s, int n, int nwant) {
   }
   s.ncap = N;
   s.wcap = W;
+  return HPSI_OK;
+}
+
+// Eigenvectors of T for the lowest nwant eigenvalues in s.lam: one lane per isolated eigenvalue
+// (k_eh_invit_lanes), one warp per cluster of close ones (k_eh_invit).  Vectors to s.Z.
+int invit_all(Context& c, EighState& s, int n, int nwant) {
+  const int nblk = (nwant + 31) / 32;
+  const size_t per = (size_t)5 * 32 * n + (n + 1) / 2;
+  const size_t need = sizeof(double) * per * nblk;
+  if (need > s.invcap) {
+    cudaFree(s.invs);
+    s.invs = nullptr;
+    s.invcap = 0;
+    if (cudaMalloc((void**)&s.invs, need) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, HPSI_ENOMEM, "inverse-iteration scratch allocation failed");
+    }
+    s.invcap = need;
+  }
+  HPSI_LAUNCH(c, HPSI_K_EIGH, (k_eh_invit_lanes<<<nblk, 32, 0, c.stream>>>(n, s.d, s.e, nwant, s.lam, s.Z, s.invs,
+                                                                          s.info + 1)));
+  const size_t ismem = sizeof(double) * 7 * (size_t)n + (size_t)n + 16;
+  if (ismem > 48 * 1024) {
+    const cudaError_t err = cudaFuncSetAttribute(k_eh_invit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ismem);
+    if (err != cudaSuccess) return cuda_fail(c, err, "inverse iteration: smem attribute");
+  }
+  HPSI_LAUNCH(c, HPSI_K_EIGH,
+              (k_eh_invit<<<nwant, 32, ismem, c.stream>>>(n, s.d, s.e, nwant, s.lam, s.Z, s.info + 1, 1)));
   return HPSI_OK;
 }
 
@@ -681,13 +811,8 @@ int eigh_lowest(Context& c, const double2* a, int lda, int n, int nwant, double*
   HPSI_LAUNCH(c, HPSI_K_EIGH,
               (k_eh_bisect<<<nwant, 32 * kBisWarps, 0, c.stream>>>(n, s->d, s->e, s->e2, nwant, s->lam)));
   // 3. eigenvectors of T
-  const size_t ismem = sizeof(double) * 7 * (size_t)n + (size_t)n + 16;
-  if (ismem > 48 * 1024) {
-    err = cudaFuncSetAttribute(k_eh_invit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ismem);
-    if (err != cudaSuccess) return cuda_fail(c, err, "eigh_lowest: smem attribute");
-  }
-  HPSI_LAUNCH(c, HPSI_K_EIGH,
-              (k_eh_invit<<<nwant, 32, ismem, c.stream>>>(n, s->d, s->e, nwant, s->lam, s->Z, s->info + 1)));
+  rc = invit_all(c, *s, n, nwant);
+  if (rc) return rc;
   //    orthonormalisation of Z by one Newton-Schulz step of the polar decomposition,
   //    Z <- Z (3 I - Z^T Z) / 2: inverse iteration leaves |Z^T Z - I| at rounding / gap (below
   //    1e-6 for gaps above the cluster tolerance), which one step squares; a larger departure
@@ -818,13 +943,8 @@ int eigh_lowest_real(Context& c, const double* a, int lda, int n, int nwant, dou
   // 2. eigenvalues, 3. eigenvectors of T (the same kernels as the complex solver)
   HPSI_LAUNCH(c, HPSI_K_EIGH,
               (k_eh_bisect<<<nwant, 32 * kBisWarps, 0, c.stream>>>(n, s->d, s->e, s->e2, nwant, s->lam)));
-  const size_t ismem = sizeof(double) * 7 * (size_t)n + (size_t)n + 16;
-  if (ismem > 48 * 1024) {
-    err = cudaFuncSetAttribute(k_eh_invit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ismem);
-    if (err != cudaSuccess) return cuda_fail(c, err, "eigh_lowest_real: smem attribute");
-  }
-  HPSI_LAUNCH(c, HPSI_K_EIGH,
-              (k_eh_invit<<<nwant, 32, ismem, c.stream>>>(n, s->d, s->e, nwant, s->lam, s->Z, s->info + 1)));
+  rc = invit_all(c, *s, n, nwant);
+  if (rc) return rc;
   const double one = 1.0, zero = 0.0, mone = -1.0, mhalf = -0.5, three_half = 1.5;
   const size_t nz = (size_t)n * nwant;
   // float32 copies (vec32) live in the unused halves of the buffers sized for the complex solver:
@@ -833,6 +953,23 @@ int eigh_lowest_real(Context& c, const double* a, int lda, int n, int nwant, dou
   float* zf = reinterpret_cast<float*>(s->Z2);
   float* vf = zf + nz;
   float* gf = reinterpret_cast<float*>(s->gram);
+  // vec32: the float32 GEMMs below run as cuBLAS's float32 emulation on the bf16 tensor cores
+  // (float32-accurate; finite operands, so without special-value passes), reset on every exit
+  struct Emu {
+    cublasHandle_t b = nullptr;
+    void on(cublasHandle_t h) {
+      b = h;
+      cublasSetMathMode(h, CUBLAS_FP32_EMULATED_BF16X9_MATH);
+      cublasSetEmulationStrategy(h, CUBLAS_EMULATION_STRATEGY_EAGER);
+      cublasSetEmulationSpecialValuesSupport(h, CUDA_EMULATION_SPECIAL_VALUES_SUPPORT_NONE);
+    }
+    ~Emu() {
+      if (!b) return;
+      cublasSetMathMode(b, CUBLAS_DEFAULT_MATH);
+      cublasSetEmulationSpecialValuesSupport(b, CUDA_EMULATION_SPECIAL_VALUES_SUPPORT_DEFAULT);
+    }
+  } emu;
+  if (vec32) emu.on(s->blas);
   if (vec32) {
     const float f1 = 1.f, f0 = 0.f, fmhalf = -0.5f, f3half = 1.5f;
     HPSI_LAUNCH(c, HPSI_K_EIGH, (k_eh_cvt<double, float><<<cvt_grid(nz), 256, 0, c.stream>>>(nz, s->Z, zf)));

@@ -251,8 +251,8 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_eh_tridiag_df(TriArgsR p) {
     }
     if (Ra > 0) {
       // whole rows round-robin over the four schedulers, leftover rows cut into quarters (as in the
-      // float64 kernel); slot k of a row's partial sums is its quarter k.  Four columns per lane
-      // and step, with four independent sums, so that the pairs' dependent chains overlap.
+      // float64 kernel); slot k of a row's partial sums is its quarter k.  Two columns per lane and
+      // step (measured faster than four).
       const int m = n - 1 - j;
       const int rem = Ra & 3, full = Ra - rem;
       const int sched = wid & 3, half = wid >> 2;
@@ -278,36 +278,29 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_eh_tridiag_df(TriArgsR p) {
         float2* row = rows + (size_t)lr * n;
         const float2 P = df_rank2(cA[lr], hhd, cB[lr], zero2, zero2);   // A_r - hh B_r
         const float2 Q = cQ[lr];
-        float2 acc[4] = {zero2, zero2, zero2, zero2};
-        float2 a1 = zero2;
-        for (int c = c0 + lane; c < c1; c += 128) {
-          float2 a[4];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int cq = c + 32 * q;
-            a[q] = cq < c1 ? row[cq] : zero2;
-          }
+        float2 ax = zero2, bx = zero2, a1 = zero2;
+        for (int c = c0 + lane; c < c1; c += 64) {
+          const int c2 = c + 32;
+          const bool two = c2 < c1;
+          float2 a = row[c];
+          float2 b = two ? row[c2] : zero2;
           if (j > 0) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const int cq = c + 32 * q;
-              if (cq < c1) {
-                a[q] = df_rank2(a[q], P, uP[cq], Q, yP[cq]);
-                row[cq] = a[q];
-              }
+            a = df_rank2(a, P, uP[c], Q, yP[c]);
+            row[c] = a;
+            if (two) {
+              b = df_rank2(b, P, uP[c2], Q, yP[c2]);
+              row[c2] = b;
             }
           }
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int cq = c + 32 * q;
-            if (cq < c1) {
-              if (cq == j + 1) a1 = a[q];
-              else acc[q] = df_mac(acc[q], a[q], uC[cq]);
-              if (r == j + 1) rnext[(j & 1) * n + cq] = a[q];
-            }
+          if (c == j + 1) a1 = a;
+          else ax = df_mac(ax, a, uC[c]);
+          if (two) bx = df_mac(bx, b, uC[c2]);
+          if (r == j + 1) {
+            rnext[(j & 1) * n + c] = a;
+            if (two) rnext[(j & 1) * n + c2] = b;
           }
         }
-        const float2 ax = df_warp_sum(df_add(df_add(acc[0], acc[1]), df_add(acc[2], acc[3])));
+        ax = df_warp_sum(df_add(ax, bx));
         if (lane == 0) {
           pacc[i * 4 + k] = ax;
           if (k == 0) pa1[i] = a1;

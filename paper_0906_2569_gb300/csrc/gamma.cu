@@ -275,7 +275,11 @@ int gamma_nl_prepare(Context& c, Problem& p) {
       return cuda_fail(c, e, "Gamma-form projector setup");
     }
   }
-  if (c.precision == HPSI_MIXED) return gamma_prepare_tc(c, p);
+  if (c.precision == HPSI_MIXED) {
+    const int rc = gamma_prepare_tc(c, p);
+    if (rc) return rc;
+    return gamma_prepare_df(c, p);
+  }
   return HPSI_OK;
 }
 
@@ -319,9 +323,10 @@ static int gamma_apply_t(Context& c, int ik, const S* x, S* y, int nb, bool scal
     constexpr bool x32 = sizeof(S) == sizeof(float2);
     const int np = nl_prec(c);
     if (np == kNlProj64 && c.precision == HPSI_MIXED) {
-      // projections in float64, add_vuspsi on the tensor cores
+      // projections to float64 accuracy (a double-float GEMM on the float32 pipes), add_vuspsi on
+      // the tensor cores
       double* w = nullptr;
-      rc = gamma_w_fp64(c, p, x, x32, nb, scaled, &w);
+      rc = gamma_w_df(c, p, x, x32, nb, scaled, &w);
       if (!rc) rc = gamma_add_tc(c, p, w, nb, &nl32, &ns32);
     } else if (np == HPSI_FP64 || np == kNlProj64) {
       const int nr = 2 * ((p.npw + 1) / 2);
@@ -397,6 +402,13 @@ __global__ void k_g_from_half(int nh, const double2* __restrict__ c, T* __restri
     }
   }
 }
+// a = I (n x n, float64)
+__global__ void k_g_eye(int n, double* __restrict__ a) {
+  const size_t nn = (size_t)n * n;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nn; i += (size_t)gridDim.x * blockDim.x)
+    a[i] = (i % n) == (i / n) ? 1.0 : 0.0;
+}
+
 template <typename T>
 __global__ void k_g_to_half(int nh, const T* __restrict__ x, double2* __restrict__ c) {
   const int b = blockIdx.y;
@@ -649,6 +661,7 @@ struct GamWork {
   int lwork = 0;
   double* x64 = nullptr;   // [N][n2] float64 Ritz vectors (mixed exit)
   double* hx64 = nullptr;  // [N][n2]
+  double* rinv = nullptr;  // [nt][nt] product of inverse Cholesky factors (float32 basis)
 };
 
 struct GamHandles {
@@ -659,7 +672,7 @@ struct GamHandles {
 
 static void free_gwork(GamWork& w) {
   for (void* p : {w.phi, w.hphi, w.psi, w.hpsi, w.r, w.t, w.small, w.hcol, w.hd}) cudaFree(p);
-  for (double* p : {w.hsub, w.evec, w.wv, w.ovl, w.eps, w.rnorm, w.cn2, w.work, w.x64, w.hx64}) cudaFree(p);
+  for (double* p : {w.hsub, w.evec, w.wv, w.ovl, w.eps, w.rnorm, w.cn2, w.work, w.x64, w.hx64, w.rinv}) cudaFree(p);
   cudaFree(w.idx);
   cudaFree(w.idx2);
   cudaFree(w.info);
@@ -752,7 +765,9 @@ int GammaDavidson<T>::alloc(int N) {
             al((void**)&w.rnorm, sizeof(double) * N) && al((void**)&w.cn2, sizeof(double) * nt) &&
             al((void**)&w.idx, sizeof(int) * N) && al((void**)&w.idx2, sizeof(int) * nt) &&
             al((void**)&w.info, sizeof(int));
-  if (ok && prec == HPSI_MIXED) ok = al((void**)&w.x64, 8 * n2 * N) && al((void**)&w.hx64, 8 * n2 * N);
+  if (ok && prec == HPSI_MIXED)
+    ok = al((void**)&w.x64, 8 * n2 * N) && al((void**)&w.hx64, 8 * n2 * N) &&
+         al((void**)&w.rinv, sizeof(double) * nt * nt);
   if (!ok) {
     free_gwork(w);
     return fail(c, HPSI_ENOMEM, "davidson_solve_gamma: device allocation of the reduced basis failed");
@@ -847,10 +862,26 @@ int GammaDavidson<T>::orth(const T* x, int n, T* out, int* nkeep, double thr, bo
   Context& c = c_;
   GamWork& w = w_;
   const bool f64 = sizeof(T) == 8;
+  // A float64 basis: y <- y R^{-1} by TRSM with the factor in w.ovl.  A float32 basis: the product
+  // M of the inverse factors is kept in float64 (w.rinv, M <- M R^{-1} by a small TRSM) and out = x M
+  // is one float32 GEMM (emulated on the bf16 tensor cores by default), far cheaper than a float32
+  // TRSM over the whole block; every pass still factors the Gram matrix of the vectors it produced.
   auto solve_with_factor = [&](T* y) -> int {
     HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
                 (k_g_copy<double, T><<<grid_of((size_t)n * n), 256, 0, c.stream>>>(n, n, w.ovl, n, hcol(), n)));
     GBK(trsm_ru(h_.blas, n2_, n, hcol(), n, y, n2_), "trsm");
+    return HPSI_OK;
+  };
+  auto apply_inverse = [&](bool first) -> int {   // float32 basis: out = x M, M <- M R^{-1}
+    if (first) HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_g_eye<<<grid_of((size_t)n * n), 256, 0, c.stream>>>(n, w.rinv)));
+    const double one = 1.0;
+    GBK(cublasDtrsm(h_.blas, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT, n, n, &one,
+                    w.ovl, n, w.rinv, n),
+        "trsm inverse factor");
+    HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
+                (k_g_copy<double, T><<<grid_of((size_t)n * n), 256, 0, c.stream>>>(n, n, w.rinv, n, hcol(), n)));
+    GBK(gemm(h_.blas, CUBLAS_OP_N, CUBLAS_OP_N, n2_, n, n, 1.0, x, n2_, hcol(), n, 0.0, out, n2_),
+        "gemm orthonormalise");
     return HPSI_OK;
   };
   int rc = overlap(x, n);
@@ -859,9 +890,13 @@ int GammaDavidson<T>::orth(const T* x, int n, T* out, int* nkeep, double thr, bo
   rc = chol(n, relative ? (f64 ? 1e-10 : 1e-6) : (f64 ? 1e-6 : 1e-2), relative, &ok);
   if (rc) return rc;
   if (ok) {
-    GCK(cudaMemcpyAsync(out, x, sizeof(T) * (size_t)n * n2_, cudaMemcpyDeviceToDevice, c.stream), "copy");
     *nkeep = n;
-    return solve_with_factor(out);
+    if constexpr (sizeof(T) == 8) {
+      GCK(cudaMemcpyAsync(out, x, sizeof(T) * (size_t)n * n2_, cudaMemcpyDeviceToDevice, c.stream), "copy");
+      return solve_with_factor(out);
+    } else {
+      return apply_inverse(true);
+    }
   }
   if (!relative) {
     rc = overlap(x, n);
@@ -869,8 +904,12 @@ int GammaDavidson<T>::orth(const T* x, int n, T* out, int* nkeep, double thr, bo
     rc = chol(n, 1e-6, false, &ok);
     if (rc) return rc;
     if (ok) {
-      GCK(cudaMemcpyAsync(out, x, sizeof(T) * (size_t)n * n2_, cudaMemcpyDeviceToDevice, c.stream), "copy");
-      rc = solve_with_factor(out);
+      if (f64) {
+        GCK(cudaMemcpyAsync(out, x, sizeof(T) * (size_t)n * n2_, cudaMemcpyDeviceToDevice, c.stream), "copy");
+        rc = solve_with_factor(out);
+      } else {
+        rc = apply_inverse(true);
+      }
       if (rc) return rc;
       rc = overlap(out, n);
       if (rc) return rc;
@@ -878,7 +917,7 @@ int GammaDavidson<T>::orth(const T* x, int n, T* out, int* nkeep, double thr, bo
       if (rc) return rc;
       if (ok) {
         *nkeep = n;
-        return solve_with_factor(out);
+        return f64 ? solve_with_factor(out) : apply_inverse(false);
       }
     }
   }

@@ -89,6 +89,7 @@ struct Problem {
   double* d_betar = nullptr;
   double* d_dvalr = nullptr;
   uint16_t* d_betar_bf = nullptr;
+  float2* d_betar_df = nullptr;    // (mixed contexts) betar as double-float pairs
 };
 
 struct TwiddleTable {
@@ -112,6 +113,7 @@ struct Workspace {
   void* gin = nullptr; size_t ginbytes = 0;      // Gamma form: packed pairs of real bands, and H of them
   void* gout = nullptr; size_t goutbytes = 0;
   void* gnl = nullptr; size_t gnlbytes = 0;      // Gamma form: the float64 nonlocal term in real coordinates
+  void* gdf = nullptr; size_t gdfbytes = 0;      // Gamma form: bands as double-float pairs
   long long epoch = 0;                           // bumped whenever a buffer is reallocated
 };
 
@@ -306,6 +308,9 @@ int gamma_prepare_tc(Context& c, Problem& p);
 // The projection half in float64 (w = D' <betar|x>, real form; w = D <beta|psi>, complex form),
 // left in the workspace, and add_vuspsi from such a w on the tensor cores (mixed contexts).
 int gamma_w_fp64(Context& c, const Problem& p, const void* x, bool x32, int nb, bool scaled, double** w);
+// The same w with calbec as a double-float GEMM on the float32 pipes (needs d_betar_df)
+int gamma_w_df(Context& c, const Problem& p, const void* x, bool x32, int nb, bool scaled, double** w);
+int gamma_prepare_df(Context& c, Problem& p);
 int nonlocal_w_fp64(Context& c, const Problem& p, const double2* psi, int nbnd, double2** w);
 int gamma_add_tc(Context& c, const Problem& p, const double* w, int nb, const float** part, int* nsplit);
 int nonlocal_add_tc(Context& c, const Problem& p, const double2* w, double2* hpsi, int nbnd);

@@ -338,7 +338,130 @@ __global__ void __launch_bounds__(256) k_addvus64r(int nr, int nproj, int nb, co
   }
 }
 
+// ---- double-float calbec (the projections of the mixed solve's final quotients) ----
+// Pairs of floats (hi + lo, ~48 bits) multiplied and accumulated with error-free transformations
+// on the float32 pipes (Knuth's TwoSum, Dekker's FastTwoSum, the FMA split of a product); the _rn
+// intrinsics keep the compiler from contracting or reassociating them.
+__device__ __forceinline__ float2 dfr_fast(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ float2 dfr_mac(float2 acc, float2 a, float2 u) {
+  const float p = __fmul_rn(a.x, u.x);
+  float e = __fmaf_rn(a.x, u.x, -p);
+  e = __fmaf_rn(a.x, u.y, e);
+  e = __fmaf_rn(a.y, u.x, e);
+  const float s = __fadd_rn(acc.x, p);
+  const float bb = __fsub_rn(s, acc.x);
+  const float err = __fadd_rn(__fsub_rn(acc.x, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  return dfr_fast(s, __fadd_rn(err, __fadd_rn(acc.y, e)));
+}
+__device__ __forceinline__ float2 dfr_of(double x) {
+  const float h = __double2float_rn(x);
+  return make_float2(h, __double2float_rn(x - (double)h));
+}
+
+// out[i] = pairs of in[i] (x sqrt2 for coordinates r >= 2 of each nr-long row when !scaled)
+template <typename R>
+__global__ void k_to_df(size_t n, int nr, int scaled, const R* __restrict__ in, float2* __restrict__ out) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    double v = (double)in[i];
+    if (!scaled && (int)(i % nr) >= 2) v *= kSqrt2r;
+    out[i] = dfr_of(v);
+  }
+}
+
+// part[split][b][p] = sum_{r in split} betar[p][r] x[b][r] in pairs, written as float64
+__global__ void __launch_bounds__(256) k_calbec_df(int nr, int nproj, int nb, int kchunk,
+                                                   const float2* __restrict__ betar, const float2* __restrict__ x,
+                                                   double* __restrict__ part) {
+  __shared__ float2 sb[RB_TP][RB_TK + 1];
+  __shared__ float2 sx[RB_TB][RB_TK + 1];
+  const int p0 = blockIdx.x * RB_TP, b0 = blockIdx.y * RB_TB, split = blockIdx.z;
+  const int rbeg = split * kchunk, rend = min(nr, rbeg + kchunk);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // tx -> p, ty -> b
+  const float2 z = make_float2(0.f, 0.f);
+  float2 c00 = z, c01 = z, c10 = z, c11 = z;
+  for (int r0 = rbeg; r0 < rend; r0 += RB_TK) {
+    for (int i = threadIdx.x; i < RB_TP * RB_TK; i += 256) {
+      const int row = i / RB_TK, cc = i % RB_TK, r = r0 + cc;
+      const bool in = r < rend;
+      sb[row][cc] = (p0 + row < nproj && in) ? betar[(size_t)(p0 + row) * nr + r] : z;
+      sx[row][cc] = (b0 + row < nb && in) ? x[(size_t)(b0 + row) * nr + r] : z;
+    }
+    __syncthreads();
+#pragma unroll 2
+    for (int kk = 0; kk < RB_TK; ++kk) {
+      const float2 a0 = sb[tx][kk], a1 = sb[tx + 16][kk];
+      const float2 y0 = sx[ty][kk], y1 = sx[ty + 16][kk];
+      c00 = dfr_mac(c00, a0, y0);
+      c01 = dfr_mac(c01, a0, y1);
+      c10 = dfr_mac(c10, a1, y0);
+      c11 = dfr_mac(c11, a1, y1);
+    }
+    __syncthreads();
+  }
+  double* out = part + (size_t)split * nb * nproj;
+  const int pa = p0 + tx, pb = pa + 16, ba = b0 + ty, bb = ba + 16;
+  if (pa < nproj && ba < nb) out[(size_t)ba * nproj + pa] = (double)c00.x + (double)c00.y;
+  if (pa < nproj && bb < nb) out[(size_t)bb * nproj + pa] = (double)c01.x + (double)c01.y;
+  if (pb < nproj && ba < nb) out[(size_t)ba * nproj + pb] = (double)c10.x + (double)c10.y;
+  if (pb < nproj && bb < nb) out[(size_t)bb * nproj + pb] = (double)c11.x + (double)c11.y;
+}
+
 }  // namespace
+
+int gamma_prepare_df(Context& c, Problem& p) {
+  if (p.nproj == 0 || p.d_betar_df) return HPSI_OK;
+  const int nr = 2 * ((p.npw + 1) / 2);
+  const size_t n = (size_t)p.nproj * nr;
+  if (cudaMalloc((void**)&p.d_betar_df, sizeof(float2) * n) != cudaSuccess) {
+    cudaGetLastError();
+    p.d_betar_df = nullptr;
+    return fail(c, HPSI_ENOMEM, "device allocation of the Gamma-form double-float projectors failed");
+  }
+  HPSI_LAUNCH(c, HPSI_K_GAMMA, (k_to_df<double><<<4 * c.sm_count, 256, 0, c.stream>>>(n, nr, 1, p.d_betar,
+                                                                                      p.d_betar_df)));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "Gamma-form double-float projector setup");
+  return HPSI_OK;
+}
+
+int gamma_w_df(Context& c, const Problem& p, const void* x, bool x32, int nb, bool scaled, double** wout) {
+  if (!p.d_betar_df) return fail(c, HPSI_EINVAL, "Gamma-form double-float projectors are not prepared");
+  const int nr = 2 * ((p.npw + 1) / 2);
+  const size_t nx = (size_t)nb * nr;
+  int rc = ensure_buffer(c, &c.ws.gdf, &c.ws.gdfbytes, sizeof(float2) * nx);
+  if (rc) return rc;
+  float2* xdf = static_cast<float2*>(c.ws.gdf);
+  if (x32)
+    HPSI_LAUNCH(c, HPSI_K_CALBEC, (k_to_df<float><<<4 * c.sm_count, 256, 0, c.stream>>>(
+                                      nx, nr, scaled ? 1 : 0, static_cast<const float*>(x), xdf)));
+  else
+    HPSI_LAUNCH(c, HPSI_K_CALBEC, (k_to_df<double><<<4 * c.sm_count, 256, 0, c.stream>>>(
+                                      nx, nr, scaled ? 1 : 0, static_cast<const double*>(x), xdf)));
+  const int tilesp = (p.nproj + RB_TP - 1) / RB_TP, tilesb = (nb + RB_TB - 1) / RB_TB;
+  int nsplit = std::max(1, (3 * c.sm_count) / std::max(1, tilesp * tilesb));
+  int kchunk = (nr + nsplit - 1) / nsplit;
+  kchunk = std::max(RB_TK * 2, ((kchunk + RB_TK - 1) / RB_TK) * RB_TK);
+  nsplit = (nr + kchunk - 1) / kchunk;
+  rc = ensure_buffer(c, &c.ws.part, &c.ws.partbytes, sizeof(double) * (size_t)nsplit * nb * p.nproj);
+  if (rc) return rc;
+  rc = ensure_buffer(c, &c.ws.w, &c.ws.wbytes, sizeof(double) * (size_t)nb * p.nproj);
+  if (rc) return rc;
+  double* part = static_cast<double*>(c.ws.part);
+  double* w = static_cast<double*>(c.ws.w);
+  HPSI_LAUNCH(c, HPSI_K_CALBEC, (k_calbec_df<<<dim3(tilesp, tilesb, nsplit), 256, 0, c.stream>>>(
+                                    nr, p.nproj, nb, kchunk, p.d_betar_df, xdf, part)));
+  const int n = p.nproj * nb;
+  HPSI_LAUNCH(c, HPSI_K_DSCALE,
+              (k_dscale64r<<<(n + 255) / 256, 256, 0, c.stream>>>(p.nproj, nb, nsplit, part, p.d_rowptr, p.d_col,
+                                                                  p.d_dvalr, w)));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "Gamma-form double-float projection kernels launch");
+  *wout = w;
+  return HPSI_OK;
+}
 
 // w = D' <betar|x> of the real form in float64 (calbec and D-scale); *w points into the workspace.
 int gamma_w_fp64(Context& c, const Problem& p, const void* x, bool x32, int nb, bool scaled, double** wout) {
