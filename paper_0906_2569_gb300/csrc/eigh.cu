@@ -44,7 +44,6 @@ namespace hpsi {
 
 namespace {
 
-constexpr int kInvIters = 2;                         // inverse-iteration solves per eigenvector
 
 
 // Gershgorin interval [lo, hi] of T, |T| bound and largest e^2, reduced over a warp.
@@ -197,13 +196,14 @@ __device__ bool orth_normalize(int n, double* z, const double* __restrict__ Z, i
 // lane: a float64 warp instruction costs the same with one active lane as with 32, so 32 of the
 // serial tridiagonal recurrences share each instruction.  Per lane: T - lambda I = P L U with partial
 // pivoting (the pivot choice as selects, the row interchanges as one ballot mask per step), then
-// kInvIters solves from a hashed start, normalised after each.  The factors and z live in a global
+// `iters` solves from a hashed start, normalised after each.  The factors and z live in a global
 // scratch laid out [k][lane] per warp (5 n 32 doubles and n masks), so every step's accesses are
 // coalesced.  Members of clusters are left to k_eh_invit.
 __global__ void __launch_bounds__(32) k_eh_invit_lanes(int n, const double* __restrict__ d,
                                                        const double* __restrict__ e, int nwant,
                                                        const double* __restrict__ lam, double* __restrict__ Z,
-                                                       double* __restrict__ scratch, int* __restrict__ status) {
+                                                       double* __restrict__ scratch, int* __restrict__ status,
+                                                       int iters) {
   const int lane = threadIdx.x, i = blockIdx.x * 32 + lane;
   double glo, ghi, emax2;
   gershgorin(n, d, e, &glo, &ghi, &emax2);
@@ -226,9 +226,12 @@ __global__ void __launch_bounds__(32) k_eh_invit_lanes(int n, const double* __re
   auto guard = [&](double u) {
     return (__double_as_longlong(u) & kMag) < (__double_as_longlong(tiny) & kMag) ? (u < 0.0 ? -tiny : tiny) : u;
   };
+  // every loop takes its independent loads kB steps at a time ahead of the dependent recurrence,
+  // so that the L2 latency of the scratch is paid once per block, not once per step
+  constexpr int kB = 8;
   double al = d[0] - li, be = n > 1 ? e[0] : 0.0;
-  for (int k = 0; k < n - 1; ++k) {
-    const double sub = e[k], dn = d[k + 1] - li, cn = k + 1 < n - 1 ? e[k + 1] : 0.0;
+  auto lu_step = [&](int k, double sub, double dk1, double cn) {
+    const double dn = dk1 - li;
     const bool np = (__double_as_longlong(al) & kMag) >= (__double_as_longlong(sub) & kMag);
     const double ui = recip_nr(np ? guard(al) : sub);
     const double l = (np ? sub : al) * ui;
@@ -241,27 +244,54 @@ __global__ void __launch_bounds__(32) k_eh_invit_lanes(int n, const double* __re
     const double nal = fma(-l, np ? be : dn, np ? dn : be);
     be = np ? cn : -l * cn;
     al = nal;
+  };
+  int k = 0;
+  for (; k + kB <= n - 1; k += kB) {
+    double ev[kB], dv[kB], cv[kB];
+#pragma unroll
+    for (int u = 0; u < kB; ++u) {
+      ev[u] = e[k + u];
+      dv[u] = d[k + u + 1];
+      cv[u] = k + u + 1 < n - 1 ? e[k + u + 1] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kB; ++u) lu_step(k + u, ev[u], dv[u], cv[u]);
   }
+  for (; k < n - 1; ++k) lu_step(k, e[k], d[k + 1], k + 1 < n - 1 ? e[k + 1] : 0.0);
   SU1[(size_t)(n - 1) * 32] = recip_nr(guard(al));
   double nn = 0.0;
-  for (int k = 0; k < n; ++k) {
-    const double v = hash_unit((unsigned)i, (unsigned)k);
-    Zs[(size_t)k * 32] = v;
+  for (int q = 0; q < n; ++q) {
+    const double v = hash_unit((unsigned)i, (unsigned)q);
+    Zs[(size_t)q * 32] = v;
     nn = fma(v, v, nn);
   }
   bool ok = true;
   double sc = 1.0 / sqrt(nn);
   __syncwarp();
-  for (int it = 0; it < kInvIters; ++it) {
+  for (int it = 0; it < iters; ++it) {
     // forward: row interchanges and L
     double zk = Zs[0] * sc;
-    for (int k = 0; k < n - 1; ++k) {
-      const double z1 = Zs[(size_t)(k + 1) * 32] * sc;
-      const bool sw = (PIV[k] >> lane) & 1u;
+    auto fwd_step = [&](int q, double z1r, double lq, unsigned pq) {
+      const double z1 = z1r * sc;
+      const bool sw = (pq >> lane) & 1u;
       const double a = sw ? z1 : zk, b = sw ? zk : z1;
-      Zs[(size_t)k * 32] = a;
-      zk = fma(-SL[(size_t)k * 32], a, b);
+      Zs[(size_t)q * 32] = a;
+      zk = fma(-lq, a, b);
+    };
+    int q = 0;
+    for (; q + kB <= n - 1; q += kB) {
+      double zv[kB], lv[kB];
+      unsigned pv[kB];
+#pragma unroll
+      for (int u = 0; u < kB; ++u) {
+        zv[u] = Zs[(size_t)(q + u + 1) * 32];
+        lv[u] = SL[(size_t)(q + u) * 32];
+        pv[u] = PIV[q + u];
+      }
+#pragma unroll
+      for (int u = 0; u < kB; ++u) fwd_step(q + u, zv[u], lv[u], pv[u]);
     }
+    for (; q < n - 1; ++q) fwd_step(q, Zs[(size_t)(q + 1) * 32], SL[(size_t)q * 32], PIV[q]);
     // backward: U (three diagonals), with the squared norm of the result
     double z2 = zk * SU1[(size_t)(n - 1) * 32];
     Zs[(size_t)(n - 1) * 32] = z2;
@@ -272,12 +302,30 @@ __global__ void __launch_bounds__(32) k_eh_invit_lanes(int n, const double* __re
       Zs[(size_t)(n - 2) * 32] = z1;
       nn = fma(z1, z1, nn);
     }
-    for (int k = n - 3; k >= 0; --k) {
-      const double zz = (Zs[(size_t)k * 32] - SU2[(size_t)k * 32] * z1 - SU3[(size_t)k * 32] * z2) * SU1[(size_t)k * 32];
-      Zs[(size_t)k * 32] = zz;
+    auto bwd_step = [&](int q, double zq, double u1, double u2, double u3) {
+      const double zz = (zq - u2 * z1 - u3 * z2) * u1;
+      Zs[(size_t)q * 32] = zz;
       nn = fma(zz, zz, nn);
       z2 = z1;
       z1 = zz;
+    };
+    q = n - 3;
+    for (; q - kB + 1 >= 0; q -= kB) {
+      double zv[kB], a1[kB], a2[kB], a3[kB];
+#pragma unroll
+      for (int u = 0; u < kB; ++u) {
+        const size_t o = (size_t)(q - u) * 32;
+        zv[u] = Zs[o];
+        a1[u] = SU1[o];
+        a2[u] = SU2[o];
+        a3[u] = SU3[o];
+      }
+#pragma unroll
+      for (int u = 0; u < kB; ++u) bwd_step(q - u, zv[u], a1[u], a2[u], a3[u]);
+    }
+    for (; q >= 0; --q) {
+      const size_t o = (size_t)q * 32;
+      bwd_step(q, Zs[o], SU1[o], SU2[o], SU3[o]);
     }
     if (!(nn > 0.0) || !isfinite(nn)) ok = false;
     sc = ok ? 1.0 / sqrt(nn) : 1.0;
@@ -293,7 +341,7 @@ __global__ void __launch_bounds__(32) k_eh_invit_lanes(int n, const double* __re
 
 __global__ void __launch_bounds__(32) k_eh_invit(int n, const double* __restrict__ d, const double* __restrict__ e,
                                                  int nwant, const double* __restrict__ lam, double* __restrict__ Z,
-                                                 int* __restrict__ status, int skip_single) {
+                                                 int* __restrict__ status, int skip_single, int iters) {
   extern __shared__ double sh[];
   double* sd = sh;
   double* se = sd + n;
@@ -357,7 +405,7 @@ __global__ void __launch_bounds__(32) k_eh_invit(int n, const double* __restrict
     for (int k = lane; k < n; k += 32) z[k] = hash_unit((unsigned)i, (unsigned)k);
     __syncwarp();
     bool ok = orth_normalize(n, z, Z, i0, i);
-    for (int it = 0; it < kInvIters && ok; ++it) {
+    for (int it = 0; it < iters && ok; ++it) {
       if (lane == 0) {
         for (int k = 0; k < n - 1; ++k) {
           if (spv[k]) {
@@ -645,8 +693,11 @@ int grow(Context& c, EighState& s, int n, int nwant) {
 }
 
 // Eigenvectors of T for the lowest nwant eigenvalues in s.lam: one lane per isolated eigenvalue
-// (k_eh_invit_lanes), one warp per cluster of close ones (k_eh_invit).  Vectors to s.Z.
-int invit_all(Context& c, EighState& s, int n, int nwant) {
+// (k_eh_invit_lanes), one warp per cluster of close ones (k_eh_invit).  Vectors to s.Z.  iters
+// solves from a random start: a neighbour at a gap g just above the cluster tolerance keeps a share
+// (4 eps |T| / g)^iters, ~1e-5 after two solves, which one Newton-Schulz step only squares; three
+// solves for float64 eigenvectors, two for float32 ones.
+int invit_all(Context& c, EighState& s, int n, int nwant, int iters) {
   const int nblk = (nwant + 31) / 32;
   const size_t per = (size_t)5 * 32 * n + (n + 1) / 2;
   const size_t need = sizeof(double) * per * nblk;
@@ -661,14 +712,14 @@ int invit_all(Context& c, EighState& s, int n, int nwant) {
     s.invcap = need;
   }
   HPSI_LAUNCH(c, HPSI_K_EIGH, (k_eh_invit_lanes<<<nblk, 32, 0, c.stream>>>(n, s.d, s.e, nwant, s.lam, s.Z, s.invs,
-                                                                          s.info + 1)));
+                                                                          s.info + 1, iters)));
   const size_t ismem = sizeof(double) * 7 * (size_t)n + (size_t)n + 16;
   if (ismem > 48 * 1024) {
     const cudaError_t err = cudaFuncSetAttribute(k_eh_invit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ismem);
     if (err != cudaSuccess) return cuda_fail(c, err, "inverse iteration: smem attribute");
   }
   HPSI_LAUNCH(c, HPSI_K_EIGH,
-              (k_eh_invit<<<nwant, 32, ismem, c.stream>>>(n, s.d, s.e, nwant, s.lam, s.Z, s.info + 1, 1)));
+              (k_eh_invit<<<nwant, 32, ismem, c.stream>>>(n, s.d, s.e, nwant, s.lam, s.Z, s.info + 1, 1, iters)));
   return HPSI_OK;
 }
 
@@ -811,7 +862,7 @@ int eigh_lowest(Context& c, const double2* a, int lda, int n, int nwant, double*
   HPSI_LAUNCH(c, HPSI_K_EIGH,
               (k_eh_bisect<<<nwant, 32 * kBisWarps, 0, c.stream>>>(n, s->d, s->e, s->e2, nwant, s->lam)));
   // 3. eigenvectors of T
-  rc = invit_all(c, *s, n, nwant);
+  rc = invit_all(c, *s, n, nwant, 3);
   if (rc) return rc;
   //    orthonormalisation of Z by one Newton-Schulz step of the polar decomposition,
   //    Z <- Z (3 I - Z^T Z) / 2: inverse iteration leaves |Z^T Z - I| at rounding / gap (below
@@ -931,7 +982,8 @@ int eigh_lowest_real(Context& c, const double* a, int lda, int n, int nwant, dou
               s->bar, c.d_err, s->spart};
   void* args[] = {&ta};
   HPSI_LAUNCH(c, HPSI_K_TRIDIAG,
-              (err = cudaLaunchCooperativeKernel(tri_kernel, dim3(G), dim3(kTriThreads), args, smem, c.stream)));
+              (err = cudaLaunchCooperativeKernel(tri_kernel, dim3(G), dim3(df ? kDfThreads : kTriThreads), args, smem,
+                                                 c.stream)));
   ++c.tri_calls;
   c.tri_flops += 4.0 / 3.0 * (double)n * (double)n * (double)n;
   if (err == cudaErrorCooperativeLaunchTooLarge) {
@@ -943,7 +995,7 @@ int eigh_lowest_real(Context& c, const double* a, int lda, int n, int nwant, dou
   // 2. eigenvalues, 3. eigenvectors of T (the same kernels as the complex solver)
   HPSI_LAUNCH(c, HPSI_K_EIGH,
               (k_eh_bisect<<<nwant, 32 * kBisWarps, 0, c.stream>>>(n, s->d, s->e, s->e2, nwant, s->lam)));
-  rc = invit_all(c, *s, n, nwant);
+  rc = invit_all(c, *s, n, nwant, vec32 ? 2 : 3);
   if (rc) return rc;
   const double one = 1.0, zero = 0.0, mone = -1.0, mhalf = -0.5, three_half = 1.5;
   const size_t nz = (size_t)n * nwant;

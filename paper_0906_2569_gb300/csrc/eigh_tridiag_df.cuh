@@ -100,9 +100,13 @@ __device__ __forceinline__ float2 df_warp_sum(float2 v) {
   return v;
 }
 
-__global__ void __launch_bounds__(kTriThreads, 1) k_eh_tridiag_df(TriArgsR p) {
+constexpr int kDfThreads = 512;                       // four warps per scheduler: the pairs' dependent
+                                                      // chains need the extra warps to keep issuing
+constexpr int kLoadKD = (kMaxNR + kDfThreads - 1) / kDfThreads;
+
+__global__ void __launch_bounds__(kDfThreads, 1) k_eh_tridiag_df(TriArgsR p) {
   extern __shared__ double smd[];
-  constexpr int NW = kTriThreads / 32;
+  constexpr int NW = kDfThreads / 32;
   constexpr int kChainWarp = NW - 1;
   constexpr int kSumWarp = 2;      // sums the CTAs' parts of s after the barrier
   constexpr int kOutWarp = 3;      // writes the float64 outputs while the CTA waits at the barrier
@@ -130,7 +134,7 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_eh_tridiag_df(TriArgsR p) {
 
   for (int lr = 0; lr < R; ++lr) {
     const int r = g + lr * G;
-    for (int c = tid; c < n; c += kTriThreads) rows[(size_t)lr * n + c] = df_of(sym_at(p.a, p.lda, r, c));
+    for (int c = tid; c < n; c += kDfThreads) rows[(size_t)lr * n + c] = df_of(sym_at(p.a, p.lda, r, c));
   }
   float2 tau2 = zero2;     // tau_{j-1}^2
   int first = 0;           // the own rows r > j are lr = first .. R-1
@@ -143,10 +147,10 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_eh_tridiag_df(TriArgsR p) {
     // (A) row j and y of column j-1 into shared memory; one warp sums s_{j-1} and forms hh and row
     //     j's coefficients
     {
-      float2 ra[kLoadKR], ya[kLoadKR];
+      float2 ra[kLoadKD], ya[kLoadKD];
 #pragma unroll
-      for (int k = 0; k < kLoadKR; ++k) {
-        const int c = j + tid + k * kTriThreads;
+      for (int k = 0; k < kLoadKD; ++k) {
+        const int c = j + tid + k * kDfThreads;
         if (c < n) {
           if (j == 0) {
             ra[k] = df_of(sym_at(p.a, p.lda, 0, c));
@@ -177,8 +181,8 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_eh_tridiag_df(TriArgsR p) {
         }
       }
 #pragma unroll
-      for (int k = 0; k < kLoadKR; ++k) {
-        const int c = j + tid + k * kTriThreads;
+      for (int k = 0; k < kLoadKD; ++k) {
+        const int c = j + tid + k * kDfThreads;
         if (c < n) {
           uC[c] = ra[k];
           if (j > 0) yP[c] = ya[k];
@@ -191,8 +195,8 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_eh_tridiag_df(TriArgsR p) {
     {
       const float2 Pj = pj_sh, Qj = qj_sh;
       float2 sg0 = zero2, sg1 = zero2;
-      for (int c = j + tid; c < n; c += 2 * kTriThreads) {
-        const int c2 = c + kTriThreads;
+      for (int c = j + tid; c < n; c += 2 * kDfThreads) {
+        const int c2 = c + kDfThreads;
         float2 a = uC[c];
         float2 b = c2 < n ? uC[c2] : zero2;
         if (j > 0) {
@@ -225,7 +229,7 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_eh_tridiag_df(TriArgsR p) {
     if (wid == kChainWarp) {
       float2 sg = lane < NW ? red[lane] : zero2;
 #pragma unroll
-      for (int o = 4; o > 0; o >>= 1) sg = df_add(sg, df_shfl_xor(sg, o));
+      for (int o = NW / 2; o > 0; o >>= 1) sg = df_add(sg, df_shfl_xor(sg, o));
       if (lane == 0) {
         const float2 ar = alpha_sh;
         float2 beta, tau, scale;
@@ -250,29 +254,14 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_eh_tridiag_df(TriArgsR p) {
       }
     }
     if (Ra > 0) {
-      // whole rows round-robin over the four schedulers, leftover rows cut into quarters (as in the
-      // float64 kernel); slot k of a row's partial sums is its quarter k.  Two columns per lane and
-      // step (measured faster than four).
+      // every own row cut into quarters, the quarters round-robin over all warps; slot k of a row's
+      // partial sums is its quarter k.  Two columns per lane and step (measured faster than four).
       const int m = n - 1 - j;
-      const int rem = Ra & 3, full = Ra - rem;
-      const int sched = wid & 3, half = wid >> 2;
       const int quarter = split_chunk(m, 4);
       const float2 hhd = hh_sh;
-      int ord = 0;
-      for (int it = sched; it < full + 4 * rem; it += 4, ++ord) {
-        if ((ord & 1) != half) continue;
-        int i, k, c0, c1;
-        if (it < full) {
-          i = it;
-          k = 0;
-          c0 = j + 1;
-          c1 = n;
-        } else {
-          i = full + (it - full) / 4;
-          k = sched;
-          c0 = j + 1 + k * quarter;
-          c1 = min(n, c0 + quarter);
-        }
+      for (int it = wid; it < 4 * Ra; it += NW) {
+        const int i = it >> 2, k = it & 3;
+        const int c0 = j + 1 + k * quarter, c1 = min(n, c0 + quarter);
         const int lr = first + i;
         const int r = g + lr * G;
         float2* row = rows + (size_t)lr * n;
@@ -313,8 +302,7 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_eh_tridiag_df(TriArgsR p) {
     //     the owner of row j stores u_j
     const float2 tauC = tau_sh, scC = scale_sh, tsC = ts_sh;
     auto row_y = [&](int i) {
-      float2 acc = pacc[i * 4];
-      if (i >= Ra - (Ra & 3)) acc = df_add(df_add(acc, pacc[i * 4 + 1]), df_add(pacc[i * 4 + 2], pacc[i * 4 + 3]));
+      const float2 acc = df_add(df_add(pacc[i * 4], pacc[i * 4 + 1]), df_add(pacc[i * 4 + 2], pacc[i * 4 + 3]));
       return df_mac(pa1[i], scC, acc);
     };
     if (wid == 0) {
@@ -338,7 +326,7 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_eh_tridiag_df(TriArgsR p) {
       rc[3] = df_mul(make_float2(2.f, 0.f), df_mul(tauC, y));
     }
     if (jmodG == g) {   // the owner of row j stores u_j (pairs; k_eh_vscale_df scales them)
-      for (int c = j + 2 + tid; c < n; c += kTriThreads) vref[(size_t)j * n + c] = uC[c];
+      for (int c = j + 2 + tid; c < n; c += kDfThreads) vref[(size_t)j * n + c] = uC[c];
     }
     grid_arrive(p.bar);
     // while the other CTAs arrive: the own rows' coefficients for column j+1, tau_j^2, and (CTA 0)

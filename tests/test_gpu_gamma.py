@@ -192,6 +192,7 @@ def test_gamma_davidson(lib, cfg, precision, tol, bound):
     w = np.full(xh.shape[1], 2.0)
     w[0] = 1.0
     s = np.real((xh.conj() * w[None, :]) @ xh.T)
+    print(f"  orthonormality of the returned orbitals: {np.max(np.abs(s - np.eye(p.nbnd))):.2e}")
     assert np.max(np.abs(s - np.eye(p.nbnd))) < (1e-10 if precision == 0 else 1e-4)
     # and they are eigenvectors: residuals of the oracle's H on a few of them
     sel = [0, p.nbnd - 1]
