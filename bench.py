@@ -54,6 +54,7 @@ FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # 152 SMs x 128 FP32 lanes x F
 NCU_TRAFFIC = {
     ("tridiag", -1): (("eigh_tridiag.cuh",), "7b3ca0b96a01", (3367936 + 31488) / 640 ** 2),
     ("tridiag_real", -1): (("eigh_tridiag_real.cuh",), "9dff8d240ee0", (9579520 + 2816) / 1536 ** 2),
+    ("tridiag_df", -1): (("eigh_tridiag_df.cuh",), "d822de855785", (9583104 + 8704) / 1536 ** 2),
     ("xvx_y", 1): (("local_fast.cu", "fft_codelets.cuh"), "92564643ab55", (51.725568e6 + 4.813056e6) / 48),
     ("calbec", 0): (("nonlocal_fp64.cu",), "dc474a4712d7", (270.831104e6 + 7.199488e6) / 160),
 }
@@ -651,8 +652,10 @@ def kernel_work(name, p, npw, nst, npl, precision, nproj, real=False):
     return None, None
 
 
-def tridiag_roofline(res, kst, real=False):
-    """Roofline of the Householder reduction of the reduced eigenproblems: float64 ALU bound.
+def tridiag_roofline(res, kst, real=False, df=False):
+    """Roofline of the Householder reduction of the reduced eigenproblems, against the float64 ALU
+    roof (the precision it delivers; df: the double-float kernel of the mixed Gamma solve, which does
+    that work on the float32 pipes).
 
     Algorithmic work per launch: 16 n^3 / 3 real flops for a complex Hermitian matrix, 4 n^3 / 3 for
     a real symmetric one (the Gamma-point form), summed by the library over the timed launches; the
@@ -662,7 +665,7 @@ def tridiag_roofline(res, kst, real=False):
     nlaunch = kst["launches"]
     n_eff = (res["tridiag_flops"] / nlaunch / ((4.0 if real else 16.0) / 3.0)) ** (1.0 / 3.0)
     traffic = None
-    key = ("tridiag_real" if real else "tridiag", -1)
+    key = ("tridiag_df" if df else ("tridiag_real" if real else "tridiag"), -1)
     if key in NCU_TRAFFIC and NCU_TRAFFIC[key][1] == source_hash(NCU_TRAFFIC[key][0]):
         traffic = NCU_TRAFFIC[key][2] * n_eff ** 2      # bytes per matrix element, x n^2
     return {"kernel": "tridiag", "avg_launch_ms": kst["ms"] / nlaunch, "launches": nlaunch,
@@ -690,7 +693,7 @@ def roofline(res, p, npw, nst, npl, precision, units_per_band=1):
         return None
     name = max(cand, key=lambda k: cand[k]["ms"])
     if name == "tridiag" and res.get("tridiag_flops"):
-        return tridiag_roofline(res, cand[name], real=units_per_band == 2)
+        return tridiag_roofline(res, cand[name], real=units_per_band == 2, df=units_per_band == 2 and precision == 1)
     base = name.split("@")[0]
     prec = 0 if name.endswith("@fp64") else precision
     # bands through the class in that solve: the final float64 application of a mixed solve handles
