@@ -643,9 +643,26 @@ struct CompSum {
   __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
 
-// R_i = HPsi_i - eps_i Psi_i (float32 data) and ||R_i||_2 (float64 total of compensated float32
-// partial sums); one CTA per band.  eps = e_hi + e_lo in two floats keeps hpsi - eps psi at
-// float32 accuracy of the (small) result.
+// Sum of squares of float32 values to float64 accuracy without a float64 instruction per element:
+// each square split exactly by an FMA (q^2 = p + e) and accumulated in a (hi, lo) pair of floats
+// through TwoSum; the _rn intrinsics keep the compiler from contracting or reassociating it.
+struct SqSum {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float q) {
+    const float p = __fmul_rn(q, q);
+    const float e = __fmaf_rn(q, q, -p);
+    const float s = __fadd_rn(hi, p);
+    const float bb = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(err, e));
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// R_i = HPsi_i - eps_i Psi_i (float32 data) and ||R_i||_2 to float64 accuracy (SqSum partial sums,
+// float64 across threads); one CTA per band.  eps = e_hi + e_lo in two floats keeps hpsi - eps psi
+// at float32 accuracy of the (small) result.
 __global__ void __launch_bounds__(1024) k_residual32(int npw, const float2* __restrict__ psi,
                                                     const float2* __restrict__ hpsi, const double* __restrict__ eps,
                                                     float2* __restrict__ r, double* __restrict__ rnorm) {
@@ -656,13 +673,14 @@ __global__ void __launch_bounds__(1024) k_residual32(int npw, const float2* __re
   const float2* x = psi + (size_t)b * npw;
   const float2* hx = hpsi + (size_t)b * npw;
   float2* rb = r + (size_t)b * npw;
-  CompSum cs;
+  SqSum cs;
   for (int g = threadIdx.x; g < npw; g += blockDim.x) {
     const float2 xv = x[g], hv = hx[g];
     const float qx = fmaf(-elo, xv.x, fmaf(-ehi, xv.x, hv.x));
     const float qy = fmaf(-elo, xv.y, fmaf(-ehi, xv.y, hv.y));
     rb[g] = make_float2(qx, qy);
-    cs.add(fmaf(qx, qx, qy * qy));
+    cs.add(qx);
+    cs.add(qy);
   }
   const double s = block_sum256(cs.value(), red);
   if (threadIdx.x == 0) rnorm[b] = sqrt(s);
@@ -699,10 +717,11 @@ __global__ void __launch_bounds__(1024) k_precondition32(int npw, const int* __r
 __global__ void __launch_bounds__(1024) k_norm2_32(int npw, const float2* __restrict__ t, double* __restrict__ out) {
   __shared__ double red[33];
   const float2* tb = t + (size_t)blockIdx.x * npw;
-  CompSum cs;
+  SqSum cs;
   for (int g = threadIdx.x; g < npw; g += blockDim.x) {
     const float2 v = tb[g];
-    cs.add(fmaf(v.x, v.x, v.y * v.y));
+    cs.add(v.x);
+    cs.add(v.y);
   }
   const double s = block_sum256(cs.value(), red);
   if (threadIdx.x == 0) out[blockIdx.x] = s;
