@@ -135,7 +135,7 @@ enum hpsi_option {
   HPSI_OPT_GAMMA_GEMM = 22,   /* mixed davidson_solve_gamma: 1 (default): the float32 subspace GEMMs
                                  run as cuBLAS's float32 emulation with bf16 tensor-core products
                                  (float32-accurate); 0: float32 on the CUDA cores */
-  HPSI_OPT_EIGH_DF = 23       /* real symmetric reduced problems.  1 (default): in the mixed
+  HPSI_OPT_EIGH_DF = 23,      /* real symmetric reduced problems.  1 (default): in the mixed
                                  davidson_solve_gamma the Householder reduction works in double-float
                                  arithmetic (pairs of float32, ~1e-13 relative, on the float32 pipes)
                                  and the eigenvectors' Gram, Newton-Schulz and back-transformation
@@ -143,6 +143,11 @@ enum hpsi_option {
                                  0: float64 throughout.  2: the double-float reduction also in
                                  hpsi_eigh_lowest_sym and the float64 davidson_solve_gamma (float64
                                  eigenvector GEMMs) */
+  HPSI_OPT_PERSISTENT = 24    /* hpsi_apply_batch: 1: one persistent cooperative launch per box edge
+                                 (<= 32 items each) when every item has the register-codelet
+                                 kernels; 0 (default): one launch per kernel class and box edge.
+                                 The results are identical; the separate launches, replayed from a
+                                 CUDA graph, are faster since each kernel runs at its own occupancy */
 };
 
 /* Kernel classes reported by hpsi_kernel_stats. */
@@ -163,7 +168,9 @@ enum hpsi_kernel {
                           potential update */
   HPSI_K_FOCK = 12,    /* exchange operator: sphere <-> box maps, codensities, full-box transforms,
                           Coulomb kernel, sums over occupied bands */
-  HPSI_K_COUNT = 13,
+  HPSI_K_BATCH = 13,   /* hpsi_apply_batch: the persistent launch over every item (local term and,
+                          in float64, the nonlocal term) */
+  HPSI_K_COUNT = 14,
   HPSI_K_AT_FP64 = 16  /* added to a class in hpsi_kernel_stats: only the launches made while H was
                           applied in float64 (all of them in a float64 context; in a mixed context
                           the final float64 application of davidson_solve) */
@@ -307,7 +314,14 @@ HPSI_API int davidson_solve_gamma(hpsi_ctx* ctx, int ik, int nbnd, double tol, i
  * hpsi_apply_batch -- H psi for several problems (k-points or cells) in one launch sequence:
  * for i < nitem: hpsi_out[i] = H(prob[i]) psi_in[i] with nbnd[i] bands.  Device pointers only.
  * Items whose cubic box has register-codelet kernels share one launch of each local-potential
- * kernel per box edge (blockIdx.z runs over the items); the nonlocal term follows per item.
+ * kernel per box edge (blockIdx.z runs over the items), and the nonlocal term follows (float64: one
+ * launch per kernel class over all items; HPSI_MIXED: the tensor-core form per item).  With
+ * HPSI_OPT_PERSISTENT = 1, and every item on those kernels, each box edge (<= 32 items) is instead
+ * one persistent cooperative launch whose CTAs take tiles from per-phase work lists: the
+ * z-scatter/inverse transforms, the plane transforms with x V, the forward transforms and gather,
+ * and in a float64 context the nonlocal calbec, D and add_vuspsi of its items, with a bounded grid
+ * barrier between the phases (an expired wait sets the error word that hpsi_sync reports as
+ * HPSI_ETIMEOUT).  Both forms give the same results bit for bit.
  * The first call with a given argument list runs eagerly and captures the same sequence in a CUDA
  * graph; later calls with identical arguments (same problems, band counts and pointers) replay
  * the graph with one launch.  Items are independent; outputs must not overlap inputs or each other.

@@ -24,7 +24,9 @@ HPSI_OPT_LOCKING, HPSI_OPT_LOCK_BATCH, HPSI_OPT_LOCK_BASIS, HPSI_OPT_THICK_RESTA
 HPSI_OPT_RITZ_SPLIT, HPSI_OPT_REORTH_TEST, HPSI_OPT_CG_TMIN = 16, 17, 18
 HPSI_OPT_SCF_NMIX, HPSI_OPT_SCF_BETA, HPSI_OPT_SCF_DAVIDSON_TOL, HPSI_OPT_GAMMA_GEMM = 19, 20, 21, 22
 HPSI_OPT_EIGH_DF = 23
-KERNELS = ("inv_zy", "xvx_y", "fwd_z", "calbec", "dscale", "addvus", "split", "davidson", "eigh", "tridiag", "gamma", "scf", "fock")
+HPSI_OPT_PERSISTENT = 24
+KERNELS = ("inv_zy", "xvx_y", "fwd_z", "calbec", "dscale", "addvus", "split", "davidson", "eigh", "tridiag", "gamma", "scf", "fock",
+           "batch")
 HPSI_K_AT_FP64 = 16   # added to a class: only its launches made while H was applied in float64
 STATUS_NAMES = {0: "HPSI_OK", -1: "HPSI_EINVAL", -2: "HPSI_ENOMEM", -3: "HPSI_ECUDA", -4: "HPSI_ENOTCONV",
                 -5: "HPSI_ESINGULAR", -6: "HPSI_ETIMEOUT", -7: "HPSI_ENODEV"}

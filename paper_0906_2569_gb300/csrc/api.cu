@@ -501,9 +501,11 @@ int apply_device(Context& c, int ik, const double2* psi, double2* hpsi, int nbnd
   return nonlocal_apply(c, p, psi, hpsi, nbnd);
 }
 
-// All items at once: problems whose box has the fast kernels share one launch per kernel and box
-// edge (their stick rows live side by side in one workspace); the others take the generic path;
-// the nonlocal term follows per item.
+// All items at once.  Problems whose box has the fast kernels share, per box edge, one persistent
+// cooperative launch (the three FFT phases and, when the nonlocal term is float64, its three phases
+// too), or, with HPSI_OPT_PERSISTENT off or when another item takes the generic path, one launch per
+// kernel and box edge; their stick rows live side by side in one workspace.  The tensor-core
+// nonlocal term follows per item.
 int batch_apply(Context& c, int nitem, const int* prob, const int* nbnd, const double2* const* psi,
                 double2* const* hpsi) {
   std::vector<int> fast, slow;
@@ -513,11 +515,8 @@ int batch_apply(Context& c, int nitem, const int* prob, const int* nbnd, const d
     if ((p.fflags[cur_prec(c)] & 4) && !c.force_generic) fast.push_back(i);
     else slow.push_back(i);
   }
-  std::stable_sort(fast.begin(), fast.end(), [&](int x, int y) {
-    const Problem& a = c.probs[prob[x]];
-    const Problem& b = c.probs[prob[y]];
-    return a.n[0] != b.n[0] ? a.n[0] < b.n[0] : a.fflags[cur_prec(c)] < b.fflags[cur_prec(c)];
-  });
+  std::stable_sort(fast.begin(), fast.end(),
+                   [&](int x, int y) { return c.probs[prob[x]].n[0] < c.probs[prob[y]].n[0]; });
   const size_t cs = cur_prec(c) == HPSI_FP64 ? sizeof(double2) : sizeof(float2);
   std::vector<size_t> off(fast.size());
   size_t total = 0;
@@ -543,6 +542,41 @@ int batch_apply(Context& c, int nitem, const int* prob, const int* nbnd, const d
       fo[j] = hpsi[i];
       zt[j] = base + off[j];
       yb[j] = base + off[j] + ((cs * (size_t)nbnd[i] * p.n[2] * p.nst + 255) & ~size_t(255));
+    }
+    // one persistent launch per box edge (up to 32 items each), with the float64 nonlocal term of
+    // its items; a group whose launch does not fit takes the launch-per-kernel path
+    if (c.persistent && slow.empty()) {
+      const bool with_nl = nl_prec(c) == HPSI_FP64;
+      const int nf = (int)fast.size();
+      for (int g0 = 0; g0 < nf;) {
+        const Problem& q = c.probs[fp[g0]];
+        int g1 = g0 + 1;
+        while (g1 < nf && g1 - g0 < 32 && c.probs[fp[g1]].n[0] == q.n[0]) ++g1;
+        const int n = g1 - g0;
+        bool done = false;
+        rc = local_batch_persistent(c, n, fp.data() + g0, fn.data() + g0, fi.data() + g0, fo.data() + g0,
+                                    zt.data() + g0, yb.data() + g0, with_nl, &done);
+        if (rc) return rc;
+        if (!done) {
+          rc = local_fast_apply_multi(c, n, fp.data() + g0, fn.data() + g0, fi.data() + g0, fo.data() + g0,
+                                      zt.data() + g0, yb.data() + g0);
+          if (rc) return rc;
+          if (with_nl) {
+            rc = nonlocal_batch_fp64(c, n, fp.data() + g0, fn.data() + g0, fi.data() + g0, fo.data() + g0);
+            if (rc) return rc;
+          }
+        }
+        g0 = g1;
+      }
+      for (int i = 0; i < nitem; ++i) {
+        if (nbnd[i] == 0) continue;
+        if (!with_nl) {
+          rc = nonlocal_apply(c, c.probs[prob[i]], psi[i], hpsi[i], nbnd[i]);
+          if (rc) return rc;
+        }
+        c.band_apps += nbnd[i];
+      }
+      return HPSI_OK;
     }
     rc = local_fast_apply_multi(c, (int)fast.size(), fp.data(), fn.data(), fi.data(), fo.data(), zt.data(), yb.data());
     if (rc) return rc;
@@ -817,6 +851,7 @@ extern "C" int hpsi_apply_batch(hpsi_ctx* ctx, int nitem, const int* prob, const
   std::vector<unsigned long long> key;
   key.push_back((unsigned long long)nitem);
   key.push_back((unsigned long long)(c.precision * 16 + c.nl_terms * 2 + c.force_generic));
+  key.push_back((unsigned long long)(nl_prec(c) * 2 + (c.persistent ? 1 : 0)));
   for (int i = 0; i < nitem; ++i) {
     key.push_back((unsigned long long)prob[i]);
     key.push_back((unsigned long long)nbnd[i]);
@@ -1016,6 +1051,11 @@ extern "C" int hpsi_set_option(hpsi_ctx* ctx, int option, double value) {
   if (option == HPSI_OPT_GAMMA_GEMM) {
     if (value != 0.0 && value != 1.0) return fail(c, HPSI_EINVAL, "HPSI_OPT_GAMMA_GEMM must be 0 or 1");
     c.gamma_gemm = (int)value;
+    return HPSI_OK;
+  }
+  if (option == HPSI_OPT_PERSISTENT) {
+    if (value != 0.0 && value != 1.0) return fail(c, HPSI_EINVAL, "HPSI_OPT_PERSISTENT must be 0 or 1");
+    c.persistent = (int)value;
     return HPSI_OK;
   }
   if (option == HPSI_OPT_EIGH_DF) {

@@ -114,6 +114,7 @@ struct Workspace {
   void* gout = nullptr; size_t goutbytes = 0;
   void* gnl = nullptr; size_t gnlbytes = 0;      // Gamma form: the float64 nonlocal term in real coordinates
   void* gdf = nullptr; size_t gdfbytes = 0;      // Gamma form: bands as double-float pairs
+  void* pbar = nullptr; size_t pbarbytes = 0;    // grid-barrier counter of the persistent batch kernel
   long long epoch = 0;                           // bumped whenever a buffer is reallocated
 };
 
@@ -151,6 +152,7 @@ struct Context {
   int basis_factor = 0;                // Davidson: the reduced basis grows to basis_factor * N vectors
                                        // (0: 3 for a mixed context, 4 for float64)
   int autotune = 1;                    // time the fast-path plans on the first apply of a problem
+  int persistent = 0;                  // hpsi_apply_batch: one persistent launch per box edge
   int eigensolver = 1;                 // reduced eigenproblems: 1 = the library's kernels, 0 = cuSOLVER
   int fp32_gemm = 0;                   // mixed Davidson subspace GEMMs: 1 = bf16x9-emulated float32
   int locking = 0;                     // mixed Davidson: 0 none, 1 lowest converged run, 2 every converged band
@@ -259,6 +261,10 @@ int local_fast_apply(Context& c, const Problem& p, const double2* psi, double2* 
                      int nbb);
 int local_fast_apply_multi(Context& c, int nitem, const int* prob, const int* nbnd, const double2* const* psi,
                            double2* const* hpsi, void* const* zt, void* const* yb);
+// The whole batch (and with_nl its float64 nonlocal term) in one persistent cooperative launch;
+// *done = false when it does not apply (the caller then launches per kernel class).
+int local_batch_persistent(Context& c, int nitem, const int* prob, const int* nbnd, const double2* const* psi,
+                           double2* const* hpsi, void* const* zt, void* const* yb, bool with_nl, bool* done);
 int nonlocal_apply(Context& c, const Problem& p, const double2* psi, double2* hpsi, int nbnd);
 // rho[j3][j2][j1] += sum_b wb[b] |psi_b(r_j)|^2 (float64 bands, wb on the device; local_kernels.cu)
 int local_density(Context& c, const Problem& p, const double2* psi, int nbnd, const double* wb, double* rho);

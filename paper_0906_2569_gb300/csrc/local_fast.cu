@@ -24,6 +24,7 @@ namespace {
 // One problem's share of a launch (a k-point or a cell with its band block).
 struct FastItem {
   int nb, npw, npl, nst, bpc;  // bpc: bands per k_plane CTA
+  int stage_v, stage_row;      // the item's plan: V plane and stick row staged in shared memory
   const StickDev* sticks;
   const int* ymap;     // [npl][N]: stick of (plane, j2) or -1
   const int* xmap;     // [N]: plane of ix or -1
@@ -39,7 +40,7 @@ constexpr int kMaxItems = 32;
 
 // Every launch takes its items by value (the parameter block is 32 KB on sm_70 and later).
 struct FastBatch {
-  int nitems, N, stage_v, stage_row;
+  int nitems, N;
   const double2* tw64; // e^{-2 pi i j / N}, j < N
   const float2* tw32;
   double inv_nr;
@@ -63,13 +64,15 @@ template <int R1, int R2> struct Geo {
   static constexpr int PS = N + 1;            // row stride of the plane array (one pad entry)
 };
 
+// Each kernel's work is a tile function of its block coordinates (bx, by, bz), so that the
+// persistent batched kernel below runs exactly the same code on the same tiles.
 template <typename T, int R1, int R2>
-__global__ void __launch_bounds__(256) k_zinv(const __grid_constant__ FastBatch bt) {
+__device__ __forceinline__ void zinv_tile(const FastBatch& bt, int bx, int by, int bz) {
   using V = typename Cx<T>::type;
   using Gm = Geo<R1, R2>;
   constexpr int N = Gm::N, G = Gm::G, SC = Gm::GROUPS;
-  const FastItem& a = bt.item[blockIdx.z];
-  if ((int)blockIdx.x * SC >= a.nst || (int)blockIdx.y >= a.nb) return;
+  const FastItem& a = bt.item[bz];
+  if (bx * SC >= a.nst || by >= a.nb) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* tw = reinterpret_cast<V*>(smem_raw);
   V* xbuf = tw + N;                       // [SC][XS]
@@ -77,7 +80,7 @@ __global__ void __launch_bounds__(256) k_zinv(const __grid_constant__ FastBatch 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int grp = warp * Gm::LPW + lane / G, t = lane % G;
   const bool in_grp = lane < Gm::LPW * G;
-  const int s0 = blockIdx.x * SC, b = blockIdx.y;
+  const int s0 = bx * SC, b = by;
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twt<V>(bt)[i];
   __syncthreads();
   const int s = s0 + grp;
@@ -108,43 +111,48 @@ __global__ void __launch_bounds__(256) k_zinv(const __grid_constant__ FastBatch 
 }
 
 template <typename T, int R1, int R2>
-__global__ void __launch_bounds__(256) k_plane(const __grid_constant__ FastBatch bt) {
+__global__ void __launch_bounds__(256) k_zinv(const __grid_constant__ FastBatch bt) {
+  zinv_tile<T, R1, R2>(bt, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+template <typename T, int R1, int R2>
+__device__ __forceinline__ void plane_tile(const FastBatch& bt, int bx, int by, int bz) {
   using V = typename Cx<T>::type;
   using Gm = Geo<R1, R2>;
   constexpr int N = Gm::N, G = Gm::G, NG = Gm::GROUPS;
-  const FastItem& a = bt.item[blockIdx.z];
-  if ((int)blockIdx.y * a.bpc >= a.nb) return;
+  const FastItem& a = bt.item[bz];
+  if (by * a.bpc >= a.nb) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* tw = reinterpret_cast<V*>(smem_raw);
   constexpr int PS = Gm::PS;
   V* xbuf = tw + N;                              // [NG][XS]
   V* P = xbuf + NG * Gm::XS;                     // [npl][PS]
   V* row = P + (size_t)a.npl * PS;               // [nst] if stage_row
-  T* vpl = reinterpret_cast<T*>(row + (bt.stage_row ? a.nst : 0));   // [N][N] if stage_v
-  int* xm = reinterpret_cast<int*>(vpl + (bt.stage_v ? N * N : 0));  // [N]
+  T* vpl = reinterpret_cast<T*>(row + (a.stage_row ? a.nst : 0));   // [N][N] if stage_v
+  int* xm = reinterpret_cast<int*>(vpl + (a.stage_v ? N * N : 0));  // [N]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int grp = warp * Gm::LPW + lane / G, t = lane % G;
   const bool in_grp = lane < Gm::LPW * G;
   V* xb = xbuf + (in_grp ? grp : 0) * Gm::XS;
-  const int j3 = blockIdx.x;
+  const int j3 = bx;
   const T* Vg = reinterpret_cast<const T*>(a.V) + (size_t)j3 * N * N;
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     tw[i] = twt<V>(bt)[i];
     xm[i] = a.xmap[i];
   }
-  if (bt.stage_v)
+  if (a.stage_v)
     for (int i = threadIdx.x; i < N * N; i += blockDim.x) vpl[i] = Vg[i];
-  const T* Vp = bt.stage_v ? vpl : Vg;
+  const T* Vp = a.stage_v ? vpl : Vg;
   for (int bi = 0; bi < a.bpc; ++bi) {
-    const int b = blockIdx.y * a.bpc + bi;
+    const int b = by * a.bpc + bi;
     if (b >= a.nb) break;
     const V* zin = reinterpret_cast<const V*>(a.Zt) + ((size_t)b * N + j3) * a.nst;
     V* yout = reinterpret_cast<V*>(a.Yb) + ((size_t)b * N + j3) * a.nst;
     __syncthreads();
-    if (bt.stage_row)
+    if (a.stage_row)
       for (int i = threadIdx.x; i < a.nst; i += blockDim.x) row[i] = zin[i];
     __syncthreads();
-    const V* src = bt.stage_row ? row : zin;
+    const V* src = a.stage_row ? row : zin;
     V reg[G];
     // inverse y per m1-plane: inputs at the plane's sticks
     for (int p0 = 0; p0 < a.npl; p0 += NG) {
@@ -193,7 +201,7 @@ __global__ void __launch_bounds__(256) k_plane(const __grid_constant__ FastBatch
     }
     __syncthreads();
     // forward y per m1-plane, keep the sticks
-    V* dst = bt.stage_row ? row : yout;
+    V* dst = a.stage_row ? row : yout;
     for (int p0 = 0; p0 < a.npl; p0 += NG) {
       const int p = p0 + grp;
       const bool act = in_grp && p < a.npl;
@@ -211,7 +219,7 @@ __global__ void __launch_bounds__(256) k_plane(const __grid_constant__ FastBatch
         }
       }
     }
-    if (bt.stage_row) {
+    if (a.stage_row) {
       __syncthreads();
       for (int i = threadIdx.x; i < a.nst; i += blockDim.x) yout[i] = row[i];
     }
@@ -219,12 +227,17 @@ __global__ void __launch_bounds__(256) k_plane(const __grid_constant__ FastBatch
 }
 
 template <typename T, int R1, int R2>
-__global__ void __launch_bounds__(256) k_zfwd(const __grid_constant__ FastBatch bt) {
+__global__ void __launch_bounds__(256) k_plane(const __grid_constant__ FastBatch bt) {
+  plane_tile<T, R1, R2>(bt, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+template <typename T, int R1, int R2>
+__device__ __forceinline__ void zfwd_tile(const FastBatch& bt, int bx, int by, int bz) {
   using V = typename Cx<T>::type;
   using Gm = Geo<R1, R2>;
   constexpr int N = Gm::N, G = Gm::G, SC = Gm::GROUPS;
-  const FastItem& a = bt.item[blockIdx.z];
-  if ((int)blockIdx.x * SC >= a.nst || (int)blockIdx.y >= a.nb) return;
+  const FastItem& a = bt.item[bz];
+  if (bx * SC >= a.nst || by >= a.nb) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* tw = reinterpret_cast<V*>(smem_raw);
   V* xbuf = tw + N;                       // [SC][XS]
@@ -232,7 +245,7 @@ __global__ void __launch_bounds__(256) k_zfwd(const __grid_constant__ FastBatch 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int grp = warp * Gm::LPW + lane / G, t = lane % G;
   const bool in_grp = lane < Gm::LPW * G;
-  const int s0 = blockIdx.x * SC, b = blockIdx.y;
+  const int s0 = bx * SC, b = by;
   const int ns = min(SC, a.nst - s0);
   const V* Y = reinterpret_cast<const V*>(a.Yb) + (size_t)b * N * a.nst;
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twt<V>(bt)[i];
@@ -269,6 +282,119 @@ __global__ void __launch_bounds__(256) k_zfwd(const __grid_constant__ FastBatch 
 }
 
 template <typename T, int R1, int R2>
+__global__ void __launch_bounds__(256) k_zfwd(const __grid_constant__ FastBatch bt) {
+  zfwd_tile<T, R1, R2>(bt, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+#include "nonlocal_tiles.cuh"
+
+// ---- persistent batched H|psi> (hpsi_apply_batch): one cooperative launch over every item ----
+// The grid works through the tile list of each phase in turn (the same tile functions as the
+// separate kernels: zinv, plane, zfwd, and in float64 the nonlocal calbec, D-scale and add_vuspsi of
+// all items), with a grid barrier between phases.  A phase's list holds each item's own tiles only
+// (items with fewer bands have fewer), and CTAs take tiles from it one at a time through an atomic
+// counter, so that uneven items balance as they do under the hardware block scheduler.  Every wait
+// is bounded: on expiry the CTA raises the context's error word and leaves.
+struct PersistCtl {
+  int nitems;
+  int off_z[kMaxItems + 1];   // first zinv / zfwd tile of each item (zch_i x nb_i tiles)
+  int off_p[kMaxItems + 1];   // first plane tile of each item (N x ceil(nb_i / bpc) tiles)
+  unsigned* bar;              // [0]: arrival counter; [1 + phase]: tile counters; zero at launch
+  int* err;
+};
+
+constexpr long long kPersistWait = 2000000000LL;   // clock cycles (about 1 s) per barrier wait
+
+__device__ bool persist_sync(unsigned* bar, unsigned target, int* err) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
+    int good = 1;
+    const long long t0 = clock64();
+    for (unsigned spins = 0;; ++spins) {
+      unsigned v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+      if ((int)(v - target) >= 0) break;
+      if ((spins & 255u) == 255u && (*(volatile int*)err != 0 || clock64() - t0 > kPersistWait)) {
+        atomicCAS(err, 0, 3);
+        good = 0;
+        break;
+      }
+    }
+    ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// The CTA's next tile of a phase (all threads get the same index).
+__device__ __forceinline__ int persist_next(unsigned* ctr) {
+  __shared__ int tile;
+  __syncthreads();   // the previous tile is done with shared memory and with `tile`
+  if (threadIdx.x == 0) tile = (int)atomicAdd(ctr, 1u);
+  __syncthreads();
+  return tile;
+}
+
+template <typename T, int R1, int R2, bool NL>
+__global__ void __launch_bounds__(256) k_hpsi_batch(const __grid_constant__ FastBatch bt,
+                                                    const __grid_constant__ NlBatch nl,
+                                                    const __grid_constant__ PersistCtl pc) {
+  using Gm = Geo<R1, R2>;
+  constexpr int N = Gm::N;
+  const unsigned G = gridDim.x;
+  const int nz = pc.off_z[pc.nitems], np = pc.off_p[pc.nitems];
+  for (int t = persist_next(pc.bar + 1); t < nz; t = persist_next(pc.bar + 1)) {
+    const int i = find_item(pc.off_z, pc.nitems, t);
+    const int l = t - pc.off_z[i], zch = (bt.item[i].nst + Gm::GROUPS - 1) / Gm::GROUPS;
+    zinv_tile<T, R1, R2>(bt, l % zch, l / zch, i);
+  }
+  if (!persist_sync(pc.bar, G, pc.err)) return;
+  for (int t = persist_next(pc.bar + 2); t < np; t = persist_next(pc.bar + 2)) {
+    const int i = find_item(pc.off_p, pc.nitems, t);
+    const int l = t - pc.off_p[i];
+    plane_tile<T, R1, R2>(bt, l % N, l / N, i);
+  }
+  if (!persist_sync(pc.bar, 2 * G, pc.err)) return;
+  for (int t = persist_next(pc.bar + 3); t < nz; t = persist_next(pc.bar + 3)) {
+    const int i = find_item(pc.off_z, pc.nitems, t);
+    const int l = t - pc.off_z[i], zch = (bt.item[i].nst + Gm::GROUPS - 1) / Gm::GROUPS;
+    zfwd_tile<T, R1, R2>(bt, l % zch, l / zch, i);
+  }
+  if constexpr (NL) {
+    // the nonlocal term of every item, added to the local result; its tiles reuse the dynamic
+    // shared memory of the FFT phases
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double2* sm = reinterpret_cast<double2*>(smem_raw);
+    if (!persist_sync(pc.bar, 3 * G, pc.err)) return;
+    const int nc = nl.off_cal[nl.nitems];
+    for (int t = persist_next(pc.bar + 4); t < nc; t = persist_next(pc.bar + 4)) {
+      const int i = find_item(nl.off_cal, nl.nitems, t);
+      const NlItem& a = nl.item[i];
+      const int l = t - nl.off_cal[i], r = l / a.tilesp;
+      calbec_tile(a.npw, a.nproj, a.nb, a.kchunk, a.beta, a.psi, a.part, l % a.tilesp, r % a.tilesb, r / a.tilesb,
+                  sm);
+    }
+    if (!persist_sync(pc.bar, 4 * G, pc.err)) return;
+    for (int t = blockIdx.x; t < nl.off_ds[nl.nitems]; t += G) {
+      const int i = find_item(nl.off_ds, nl.nitems, t);
+      const NlItem& a = nl.item[i];
+      dscale_one((t - nl.off_ds[i]) * blockDim.x + threadIdx.x, a.nproj, a.nb, a.nsplit, a.part, a.rowptr, a.col,
+                 a.dval, a.w);
+    }
+    if (!persist_sync(pc.bar, 5 * G, pc.err)) return;
+    const int na = nl.off_add[nl.nitems];
+    for (int t = persist_next(pc.bar + 5); t < na; t = persist_next(pc.bar + 5)) {
+      const int i = find_item(nl.off_add, nl.nitems, t);
+      const NlItem& a = nl.item[i];
+      const int l = t - nl.off_add[i];
+      addvus_tile(a.npw, a.nproj, a.nb, a.w, a.beta, a.hpsi, l % a.gtiles, l / a.gtiles, sm);
+    }
+  }
+}
+
+template <typename T, int R1, int R2>
 struct FastKernels {
   using V = typename Cx<T>::type;
   using Gm = Geo<R1, R2>;
@@ -277,7 +403,79 @@ struct FastKernels {
     return sizeof(V) * (size_t)(Gm::N + Gm::GROUPS * Gm::XS + (size_t)p.npl * Gm::PS + (sr ? p.nst : 0)) +
            (sv ? sizeof(T) * (size_t)Gm::N * Gm::N : 0) + sizeof(int) * Gm::N;
   }
-  // One launch of each kernel over every item of the batch (all share the edge N and the flags).
+  // Tile grid of the three kernels over the batch; sets each item's bands per k_plane CTA.
+  static void geometry(const Context& c, FastBatch& bt, size_t max_plane_smem, int* zch, int* nbmax, int* pyb) {
+    int total_rows = 0;
+    for (int i = 0; i < bt.nitems; ++i) {
+      const FastItem& it = bt.item[i];
+      *zch = std::max(*zch, (it.nst + Gm::GROUPS - 1) / Gm::GROUPS);
+      *nbmax = std::max(*nbmax, it.nb);
+      total_rows += it.nb;
+    }
+    // bands per k_plane CTA: amortise the staged V plane while keeping >= 2 waves over the batch
+    const int occ = max_plane_smem <= c.smem_optin / 2 ? 2 : 1;
+    int bpc = std::max(1, (Gm::N * total_rows) / (2 * c.sm_count * occ));
+    bpc = std::min(bpc, 8);
+    for (int i = 0; i < bt.nitems; ++i) {
+      bt.item[i].bpc = bpc;
+      *pyb = std::max(*pyb, (bt.item[i].nb + bpc - 1) / bpc);
+    }
+  }
+  // The whole batch in one cooperative launch of k_hpsi_batch (with the float64 nonlocal term when
+  // nl is given); *done = false, and nothing launched, when the kernel does not fit.
+  static int run_persistent(Context& c, FastBatch& bt, size_t max_plane_smem, const NlBatch* nl, unsigned* bar,
+                            bool* done) {
+    *done = false;
+    const void* kern = nl ? (const void*)k_hpsi_batch<T, R1, R2, true> : (const void*)k_hpsi_batch<T, R1, R2, false>;
+    size_t dyn = std::max(smem_z(), max_plane_smem);
+    if (nl) dyn = std::max(dyn, sizeof(double2) * (size_t)std::max(CB_SMEM, AV_SMEM));
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess || fa.sharedSizeBytes + dyn > c.smem_optin) {
+      cudaGetLastError();
+      return HPSI_OK;
+    }
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess) {
+      cudaGetLastError();
+      return HPSI_OK;
+    }
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, dyn) != cudaSuccess || occ < 1) {
+      cudaGetLastError();
+      return HPSI_OK;
+    }
+    static PersistCtl pc;
+    int zch = 1, nbmax = 1, pyb = 1;
+    geometry(c, bt, max_plane_smem, &zch, &nbmax, &pyb);   // sets each item's bands per plane tile
+    pc.nitems = bt.nitems;
+    pc.off_z[0] = pc.off_p[0] = 0;
+    for (int i = 0; i < bt.nitems; ++i) {
+      const FastItem& it = bt.item[i];
+      pc.off_z[i + 1] = pc.off_z[i] + ((it.nst + Gm::GROUPS - 1) / Gm::GROUPS) * it.nb;
+      pc.off_p[i + 1] = pc.off_p[i] + Gm::N * ((it.nb + it.bpc - 1) / it.bpc);
+    }
+    pc.bar = bar;
+    pc.err = c.d_err;
+    static NlBatch empty;   // nitems = 0 (zero-initialised); the float32 form takes no nonlocal phases
+    const NlBatch& nb = nl ? *nl : empty;
+    cudaError_t e = cudaMemsetAsync(bar, 0, 8 * sizeof(unsigned), c.stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "persistent batch barrier reset");
+    void* args[] = {(void*)&bt, (void*)&nb, (void*)&pc};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(occ * c.sm_count);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = dyn;
+    cfg.stream = c.stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    HPSI_LAUNCH(c, HPSI_K_BATCH, (e = cudaLaunchKernelExC(&cfg, kern, args)));
+    if (e != cudaSuccess) return cuda_fail(c, e, "persistent batched H|psi> launch");
+    *done = true;
+    return HPSI_OK;
+  }
+  // One launch of each kernel over every item of the batch (all share the edge N).
   static int run(Context& c, FastBatch& bt, size_t max_plane_smem) {
     static bool attr = false;
     if (!attr) {
@@ -288,21 +486,8 @@ struct FastKernels {
       attr = true;
     }
     const size_t sz = smem_z();
-    int zch = 1, nbmax = 1, pyb = 1, total_rows = 0;
-    for (int i = 0; i < bt.nitems; ++i) {
-      FastItem& it = bt.item[i];
-      zch = std::max(zch, (it.nst + Gm::GROUPS - 1) / Gm::GROUPS);
-      nbmax = std::max(nbmax, it.nb);
-      total_rows += it.nb;
-    }
-    // bands per k_plane CTA: amortise the staged V plane while keeping >= 2 waves over the batch
-    const int occ = max_plane_smem <= c.smem_optin / 2 ? 2 : 1;
-    int bpc = std::max(1, (Gm::N * total_rows) / (2 * c.sm_count * occ));
-    bpc = std::min(bpc, 8);
-    for (int i = 0; i < bt.nitems; ++i) {
-      bt.item[i].bpc = bpc;
-      pyb = std::max(pyb, (bt.item[i].nb + bpc - 1) / bpc);
-    }
+    int zch = 1, nbmax = 1, pyb = 1;
+    geometry(c, bt, max_plane_smem, &zch, &nbmax, &pyb);
     HPSI_LAUNCH(c, HPSI_K_INV_ZY, (k_zinv<T, R1, R2><<<dim3(zch, nbmax, bt.nitems), 256, sz, c.stream>>>(bt)));
     HPSI_LAUNCH(c, HPSI_K_XVX_Y,
                 (k_plane<T, R1, R2><<<dim3(Gm::N, pyb, bt.nitems), 256, max_plane_smem, c.stream>>>(bt)));
@@ -370,6 +555,9 @@ static FastItem make_item(Context& c, const Problem& p, const double2* psi, doub
   it.npl = p.npl;
   it.nst = p.nst;
   it.bpc = 1;
+  const int fl = p.fflags[cur_prec(c)];
+  it.stage_v = fl & 1;
+  it.stage_row = (fl >> 1) & 1;
   it.sticks = p.d_sticks;
   it.ymap = p.d_ymap;
   it.xmap = p.d_xmap;
@@ -398,11 +586,9 @@ static int run_batch(Context& c, FastBatch& bt, size_t smem) {
   return rc;
 }
 
-static void batch_header(FastBatch& bt, const Problem& p, int flags) {
+static void batch_header(FastBatch& bt, const Problem& p) {
   bt.nitems = 0;
   bt.N = p.n[0];
-  bt.stage_v = flags & 1;
-  bt.stage_row = (flags >> 1) & 1;
   bt.tw64 = p.d_ftw64;
   bt.tw32 = p.d_ftw32;
   bt.inv_nr = 1.0 / ((double)p.n[0] * p.n[1] * p.n[2]);
@@ -427,7 +613,7 @@ int local_fast_apply(Context& c, const Problem& p, const double2* psi, double2* 
                      int nbb) {
   static FastBatch bt;   // host staging of the parameter block (calls are not thread-safe by contract)
   const int fl = p.fflags[cur_prec(c)];
-  batch_header(bt, p, fl);
+  batch_header(bt, p);
   const size_t smem = plane_smem(c, p, fl);
   for (int b0 = 0; b0 < nbnd; b0 += nbb) {
     const int nb = std::min(nbb, nbnd - b0);
@@ -439,8 +625,8 @@ int local_fast_apply(Context& c, const Problem& p, const double2* psi, double2* 
   return HPSI_OK;
 }
 
-// Several problems with the same cubic edge and flags in one launch per kernel; scratch[i] holds
-// item i's Zt and Y (each n3 * nst * nbnd complex values).
+// Several problems with the same cubic edge in one launch per kernel, each item with its own plan;
+// scratch[i] holds item i's Zt and Y (each n3 * nst * nbnd complex values).
 int local_fast_apply_multi(Context& c, int nitem, const int* prob, const int* nbnd, const double2* const* psi,
                            double2* const* hpsi, void* const* zt, void* const* yb) {
   static FastBatch bt;
@@ -448,12 +634,12 @@ int local_fast_apply_multi(Context& c, int nitem, const int* prob, const int* nb
   while (done < nitem) {
     const Problem& p0 = c.probs[prob[done]];
     const int pr = cur_prec(c);
-    batch_header(bt, p0, p0.fflags[pr]);
+    batch_header(bt, p0);
     size_t smem = 0;
     int n = 0;
     while (done + n < nitem && n < kMaxItems) {
       const Problem& p = c.probs[prob[done + n]];
-      if (p.n[0] != p0.n[0] || p.fflags[pr] != p0.fflags[pr]) break;
+      if (p.n[0] != p0.n[0]) break;
       bt.item[n] = make_item(c, p, psi[done + n], hpsi[done + n], nbnd[done + n], zt[done + n], yb[done + n]);
       smem = std::max(smem, plane_smem(c, p, p.fflags[pr]));
       ++n;
@@ -464,6 +650,85 @@ int local_fast_apply_multi(Context& c, int nitem, const int* prob, const int* nb
     done += n;
   }
   return HPSI_OK;
+}
+
+// The whole hpsi_apply_batch in one persistent launch: every item on the fast path with one box
+// edge, at most kMaxItems of them (and kNlBatch with a nonlocal term in float64).  with_nl:
+// the float64 nonlocal term of the items joins the launch.  *done = false: nothing was launched
+// and the caller takes the launch-per-kernel path.
+int local_batch_persistent(Context& c, int nitem, const int* prob, const int* nbnd, const double2* const* psi,
+                           double2* const* hpsi, void* const* zt, void* const* yb, bool with_nl, bool* done) {
+  *done = false;
+  if (nitem < 1 || nitem > kMaxItems || nitem > kNlBatch || c.force_generic) return HPSI_OK;
+  const int pr = cur_prec(c);
+  const Problem& p0 = c.probs[prob[0]];
+  for (int i = 0; i < nitem; ++i) {
+    const Problem& p = c.probs[prob[i]];
+    if (!(p.fflags[pr] & 4) || p.n[0] != p0.n[0] || nbnd[i] < 1) return HPSI_OK;
+  }
+  static FastBatch bt;
+  static NlBatch nl;
+  batch_header(bt, p0);
+  size_t smem = 0;
+  for (int i = 0; i < nitem; ++i) {
+    const Problem& p = c.probs[prob[i]];
+    bt.item[i] = make_item(c, p, psi[i], hpsi[i], nbnd[i], zt[i], yb[i]);
+    smem = std::max(smem, plane_smem(c, p, p.fflags[pr]));
+  }
+  bt.nitems = nitem;
+  const NlBatch* nlp = nullptr;
+  if (with_nl) {
+    // partial sums and w of every item side by side in the workspace (as the launch-per-kernel form)
+    std::vector<size_t> off(nitem);
+    std::vector<int> ns(nitem), kc(nitem);
+    size_t total = 0;
+    for (int i = 0; i < nitem; ++i) {
+      size_t bytes = 0;
+      nonlocal_fp64_plan(c, c.probs[prob[i]], nbnd[i], &ns[i], &kc[i], &bytes);
+      off[i] = total;
+      total += (bytes + 255) & ~size_t(255);
+    }
+    int rc = ensure_buffer(c, &c.ws.part, &c.ws.partbytes, std::max<size_t>(total, 256));
+    if (rc) return rc;
+    unsigned char* base = static_cast<unsigned char*>(c.ws.part);
+    int n = 0;
+    nl.off_cal[0] = nl.off_ds[0] = nl.off_add[0] = 0;
+    for (int i = 0; i < nitem; ++i) {
+      const Problem& p = c.probs[prob[i]];
+      if (p.nproj == 0) continue;
+      NlItem& a = nl.item[n];
+      a.npw = p.npw;
+      a.nproj = p.nproj;
+      a.nb = nbnd[i];
+      a.kchunk = kc[i];
+      a.nsplit = ns[i];
+      a.tilesp = (p.nproj + CB_TP - 1) / CB_TP;
+      a.tilesb = (a.nb + CB_TB - 1) / CB_TB;
+      a.gtiles = (p.npw + AV_TG - 1) / AV_TG;
+      a.beta = p.d_beta;
+      a.psi = psi[i];
+      a.hpsi = hpsi[i];
+      a.part = reinterpret_cast<double2*>(base + off[i]);
+      a.w = a.part + (size_t)a.nsplit * a.nb * a.nproj;
+      a.rowptr = p.d_rowptr;
+      a.col = p.d_col;
+      a.dval = p.d_dval;
+      nl.off_cal[n + 1] = nl.off_cal[n] + a.tilesp * a.tilesb * a.nsplit;
+      nl.off_ds[n + 1] = nl.off_ds[n] + (a.nproj * a.nb + 255) / 256;
+      nl.off_add[n + 1] = nl.off_add[n] + a.gtiles * ((a.nb + AV_TB - 1) / AV_TB);
+      ++n;
+    }
+    nl.nitems = n;
+    if (n > 0) nlp = &nl;
+  }
+  int rc = ensure_buffer(c, &c.ws.pbar, &c.ws.pbarbytes, 256);
+  if (rc) return rc;
+  unsigned* bar = static_cast<unsigned*>(c.ws.pbar);
+  rc = HPSI_EINVAL;
+  auto go = [&](auto k) { rc = decltype(k)::run_persistent(c, bt, smem, nlp, bar, done); };
+  if (pr == HPSI_FP64) dispatch_size<double>(bt.N, go);
+  else dispatch_size<float>(bt.N, go);
+  return rc;
 }
 
 }  // namespace hpsi
