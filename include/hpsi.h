@@ -143,11 +143,15 @@ enum hpsi_option {
                                  0: float64 throughout.  2: the double-float reduction also in
                                  hpsi_eigh_lowest_sym and the float64 davidson_solve_gamma (float64
                                  eigenvector GEMMs) */
-  HPSI_OPT_PERSISTENT = 24    /* hpsi_apply_batch: 1: one persistent cooperative launch per box edge
+  HPSI_OPT_PERSISTENT = 24,   /* hpsi_apply_batch: 1: one persistent cooperative launch per box edge
                                  (<= 32 items each) when every item has the register-codelet
                                  kernels; 0 (default): one launch per kernel class and box edge.
                                  The results are identical; the separate launches, replayed from a
                                  CUDA graph, are faster since each kernel runs at its own occupancy */
+  HPSI_OPT_BATCH_NL = 25      /* hpsi_apply_batch in a mixed context: the nonlocal term.  0 (default):
+                                 in float64 on the CUDA cores, one launch per kernel class over all
+                                 items, when every item has at most 64 projectors, else 1.  1: the
+                                 tensor-core form per item.  2: always the float64 batched form */
 };
 
 /* Kernel classes reported by hpsi_kernel_stats. */

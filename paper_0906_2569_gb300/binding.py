@@ -25,6 +25,7 @@ HPSI_OPT_RITZ_SPLIT, HPSI_OPT_REORTH_TEST, HPSI_OPT_CG_TMIN = 16, 17, 18
 HPSI_OPT_SCF_NMIX, HPSI_OPT_SCF_BETA, HPSI_OPT_SCF_DAVIDSON_TOL, HPSI_OPT_GAMMA_GEMM = 19, 20, 21, 22
 HPSI_OPT_EIGH_DF = 23
 HPSI_OPT_PERSISTENT = 24
+HPSI_OPT_BATCH_NL = 25
 KERNELS = ("inv_zy", "xvx_y", "fwd_z", "calbec", "dscale", "addvus", "split", "davidson", "eigh", "tridiag", "gamma", "scf", "fock",
            "batch")
 HPSI_K_AT_FP64 = 16   # added to a class: only its launches made while H was applied in float64

@@ -506,8 +506,8 @@ int apply_device(Context& c, int ik, const double2* psi, double2* hpsi, int nbnd
 // too), or, with HPSI_OPT_PERSISTENT off or when another item takes the generic path, one launch per
 // kernel and box edge; their stick rows live side by side in one workspace.  The tensor-core
 // nonlocal term follows per item.
-int batch_apply(Context& c, int nitem, const int* prob, const int* nbnd, const double2* const* psi,
-                double2* const* hpsi) {
+static int batch_apply_items(Context& c, int nitem, const int* prob, const int* nbnd, const double2* const* psi,
+                             double2* const* hpsi) {
   std::vector<int> fast, slow;
   for (int i = 0; i < nitem; ++i) {
     if (nbnd[i] == 0) continue;
@@ -612,6 +612,27 @@ int pointer_kind(const void* ptr) {
   }
   if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return 1;
   return 0;
+}
+
+// In a mixed context, whether the batch's nonlocal term runs in float64 on the CUDA cores, one launch
+// per kernel class over all items (HPSI_OPT_BATCH_NL): the tensor-core form works on tiles of 128
+// projector rows, and with a few projectors per item its per-item launches are mostly empty tiles.
+static bool batch_nl64(const Context& c, int nitem, const int* prob, const int* nbnd) {
+  if (c.precision != HPSI_MIXED || nl_prec(c) != HPSI_MIXED || c.batch_nl == 1) return false;
+  if (c.batch_nl == 2) return true;
+  for (int i = 0; i < nitem; ++i)
+    if (nbnd[i] > 0 && c.probs[prob[i]].nproj > kBatchNl64MaxProj) return false;
+  return true;
+}
+
+int batch_apply(Context& c, int nitem, const int* prob, const int* nbnd, const double2* const* psi,
+                double2* const* hpsi) {
+  if (!batch_nl64(c, nitem, prob, nbnd)) return batch_apply_items(c, nitem, prob, nbnd, psi, hpsi);
+  const int saved = c.nl_prec_override;
+  c.nl_prec_override = HPSI_FP64;
+  const int rc = batch_apply_items(c, nitem, prob, nbnd, psi, hpsi);
+  c.nl_prec_override = saved;
+  return rc;
 }
 
 }  // namespace hpsi
@@ -851,7 +872,7 @@ extern "C" int hpsi_apply_batch(hpsi_ctx* ctx, int nitem, const int* prob, const
   std::vector<unsigned long long> key;
   key.push_back((unsigned long long)nitem);
   key.push_back((unsigned long long)(c.precision * 16 + c.nl_terms * 2 + c.force_generic));
-  key.push_back((unsigned long long)(nl_prec(c) * 2 + (c.persistent ? 1 : 0)));
+  key.push_back((unsigned long long)(nl_prec(c) * 2 + (c.persistent ? 1 : 0) + 16 * c.batch_nl));
   for (int i = 0; i < nitem; ++i) {
     key.push_back((unsigned long long)prob[i]);
     key.push_back((unsigned long long)nbnd[i]);
@@ -1051,6 +1072,11 @@ extern "C" int hpsi_set_option(hpsi_ctx* ctx, int option, double value) {
   if (option == HPSI_OPT_GAMMA_GEMM) {
     if (value != 0.0 && value != 1.0) return fail(c, HPSI_EINVAL, "HPSI_OPT_GAMMA_GEMM must be 0 or 1");
     c.gamma_gemm = (int)value;
+    return HPSI_OK;
+  }
+  if (option == HPSI_OPT_BATCH_NL) {
+    if (value != 0.0 && value != 1.0 && value != 2.0) return fail(c, HPSI_EINVAL, "HPSI_OPT_BATCH_NL must be 0, 1 or 2");
+    c.batch_nl = (int)value;
     return HPSI_OK;
   }
   if (option == HPSI_OPT_PERSISTENT) {

@@ -153,6 +153,7 @@ struct Context {
                                        // (0: 3 for a mixed context, 4 for float64)
   int autotune = 1;                    // time the fast-path plans on the first apply of a problem
   int persistent = 0;                  // hpsi_apply_batch: one persistent launch per box edge
+  int batch_nl = 0;                    // hpsi_apply_batch, mixed: 0 auto, 1 tensor-core, 2 float64 batched
   int eigensolver = 1;                 // reduced eigenproblems: 1 = the library's kernels, 0 = cuSOLVER
   int fp32_gemm = 0;                   // mixed Davidson subspace GEMMs: 1 = bf16x9-emulated float32
   int locking = 0;                     // mixed Davidson: 0 none, 1 lowest converged run, 2 every converged band
@@ -196,6 +197,9 @@ inline int cur_prec(const Context& c) { return c.prec_override >= 0 ? c.prec_ove
 // Precision of the nonlocal term right now: HPSI_FP64, HPSI_MIXED, or kNlProj64 (the projections
 // <beta|psi> and D in float64, add_vuspsi on the tensor cores; mixed contexts only).
 constexpr int kNlProj64 = 2;
+// hpsi_apply_batch in a mixed context: items with at most this many projectors take the float64
+// CUDA-core nonlocal term over the whole batch (HPSI_OPT_BATCH_NL = 0)
+constexpr int kBatchNl64MaxProj = 64;
 inline int nl_prec(const Context& c) { return c.nl_prec_override >= 0 ? c.nl_prec_override : cur_prec(c); }
 // Bracket the final Rayleigh quotients of a mixed solve: HPSI_OPT_FINAL_FP64 1 applies H in float64;
 // 2 the projections in float64 and the rest at the working precision.

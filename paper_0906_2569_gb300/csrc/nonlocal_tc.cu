@@ -370,10 +370,23 @@ __global__ void k_split_psi(int nb, int npw, int kc, const double2* __restrict__
   }
 }
 
-// w[b][p] = sum_q D_pq becp[b][q], becp from the float partials (summed in float64); written as
-// the bf16 terms of A of add_vuspsi, row b = (re, im) pairs of w_b.
-template <int NT>
-__global__ void k_dscale_tc(int nproj, int nb, int nsplit, int ka, const float* __restrict__ part,
+// out[i] = sum over the K-splits s of part[s][i] (float64, splits in order), i < n: the partials
+// of calbec summed once, so that the D-scale reads each <beta_q|psi_b> once per use instead of
+// re-adding its nsplit partials for every nonzero D_pq
+__global__ void k_sum_partials(size_t n, int nsplit, const float* __restrict__ part, double* __restrict__ out) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+#pragma unroll 8
+    for (int k = 0; k < nsplit; ++k) s += (double)part[(size_t)k * n + i];
+    out[i] = s;
+  }
+}
+
+// w[b][p] = sum_q D_pq becp[b][q], becp from the partials [split][P][2 nb] (float, summed in
+// float64, or already summed: S = double, nsplit = 1); written as the bf16 terms of A of
+// add_vuspsi, row b = (re, im) pairs of w_b.
+template <int NT, typename S>
+__global__ void k_dscale_tc(int nproj, int nb, int nsplit, int ka, const S* __restrict__ part,
                             const int* __restrict__ rowptr, const int* __restrict__ col,
                             const double2* __restrict__ val, __nv_bfloat16* __restrict__ wa) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -385,7 +398,7 @@ __global__ void k_dscale_tc(int nproj, int nb, int nsplit, int ka, const float* 
     const int q = col[e];
     double sr = 0.0, si = 0.0;
     for (int s = 0; s < nsplit; ++s) {
-      const float* ps = part + ((size_t)s * nproj + q) * N;
+      const S* ps = part + ((size_t)s * nproj + q) * N;
       sr += (double)ps[b];
       si += (double)ps[nb + b];
     }
@@ -535,10 +548,11 @@ __global__ void k_split_xr(int nb, int nr, int kc, int scaled, const R* __restri
   }
 }
 
-// w[b][p] = sum_q D'_pq becp[q][b] with becp from the float partials [split][P][nb] (summed in
-// float64), written as the bf16 terms of A of the real add_vuspsi (row b, K = projector, pad ka).
-template <int NT>
-__global__ void k_dscale_tc_r(int nproj, int nb, int nsplit, int ka, const float* __restrict__ part,
+// w[b][p] = sum_q D'_pq becp[q][b] with becp from the partials [split][P][nb] (float, summed in
+// float64, or already summed: S = double, nsplit = 1), written as the bf16 terms of A of the real
+// add_vuspsi (row b, K = projector, pad ka).
+template <int NT, typename S>
+__global__ void k_dscale_tc_r(int nproj, int nb, int nsplit, int ka, const S* __restrict__ part,
                               const int* __restrict__ rowptr, const int* __restrict__ col,
                               const double* __restrict__ val, __nv_bfloat16* __restrict__ wa) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -719,7 +733,8 @@ int apply_t(Context& c, const Problem& p, const double2* psi, double2* hpsi, int
   const int aksplit = (naks + (naks + kAddKsteps - 1) / kAddKsteps - 1) / ((naks + kAddKsteps - 1) / kAddKsteps);
   const int ansplit = (naks + aksplit - 1) / aksplit;   // every split has at least one K step
   const size_t addb = ansplit > 1 ? sizeof(float) * (size_t)ansplit * nbnd * 2 * npw : 0;
-  const size_t need = psib + partb + wab + addb + 4 * 256;
+  const size_t becb = nsplit > 1 ? sizeof(double) * (size_t)P * 2 * nbnd : 0;
+  const size_t need = psib + partb + wab + addb + becb + 5 * 256;
   int rc = ensure_buffer(c, &c.ws.mixed, &c.ws.mixedbytes, need);
   if (rc) return rc;
   unsigned char* w0 = static_cast<unsigned char*>(c.ws.mixed);
@@ -730,15 +745,26 @@ int apply_t(Context& c, const Problem& p, const double2* psi, double2* hpsi, int
   // the K padding of w (columns 2P .. ka) is not written by the D-scale kernel
   cudaError_t e0 = cudaMemsetAsync(wa, 0, wab, c.stream);
   if (e0 != cudaSuccess) return cuda_fail(c, e0, "workspace clear");
-  HPSI_LAUNCH(c, HPSI_K_SPLIT, (k_split_psi<NT><<<8 * c.sm_count, 256, 0, c.stream>>>(nbnd, npw, kc, psi, psi_bf)));
+  const int split_grid = (int)std::min<size_t>(8 * c.sm_count, ((size_t)nbnd * (kc / 2) + 255) / 256);
+  HPSI_LAUNCH(c, HPSI_K_SPLIT, (k_split_psi<NT><<<split_grid, 256, 0, c.stream>>>(nbnd, npw, kc, psi, psi_bf)));
   rc = launch_gemm<NT>(c, bcal, P, psi_bf, 2 * nbnd, kc, nsplit, ksplit, 0, part, nullptr, 0, HPSI_K_CALBEC);
   if (rc) return rc;
   const int n = P * nbnd;
-  HPSI_LAUNCH(c, HPSI_K_DSCALE,
-              (k_dscale_tc<NT><<<(n + 255) / 256, 256, 0, c.stream>>>(P, nbnd, nsplit, ka, part, p.d_rowptr, p.d_col,
-                                                                      p.d_dval, wa)));
+  float* apart = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(wa) + ((wab + 255) & ~size_t(255)));
+  if (nsplit > 1) {
+    double* becp = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(apart) + ((addb + 255) & ~size_t(255)));
+    const size_t nel = (size_t)P * 2 * nbnd;
+    HPSI_LAUNCH(c, HPSI_K_DSCALE, (k_sum_partials<<<(int)std::min<size_t>(8 * c.sm_count, (nel + 255) / 256), 256, 0,
+                                                    c.stream>>>(nel, nsplit, part, becp)));
+    HPSI_LAUNCH(c, HPSI_K_DSCALE,
+                (k_dscale_tc<NT, double><<<(n + 255) / 256, 256, 0, c.stream>>>(P, nbnd, 1, ka, becp, p.d_rowptr,
+                                                                                p.d_col, p.d_dval, wa)));
+  } else {
+    HPSI_LAUNCH(c, HPSI_K_DSCALE,
+                (k_dscale_tc<NT, float><<<(n + 255) / 256, 256, 0, c.stream>>>(P, nbnd, 1, ka, part, p.d_rowptr,
+                                                                               p.d_col, p.d_dval, wa)));
+  }
   if (ansplit > 1) {
-    float* apart = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(wa) + ((wab + 255) & ~size_t(255)));
     rc = launch_gemm<NT>(c, wa, nbnd, badd, 2 * npw, ka, ansplit, aksplit, 0, apart, nullptr, 0, HPSI_K_ADDVUS);
     if (rc) return rc;
     const size_t nel = (size_t)nbnd * npw;
@@ -795,7 +821,8 @@ int gamma_apply_tc(Context& c, const Problem& p, const R* x, int nb, bool scaled
   const size_t pb = al(sizeof(float) * (size_t)nsplit * P * nb);
   const size_t wb = al(sizeof(__nv_bfloat16) * (size_t)NT * nb * ka);
   const size_t ab = al(sizeof(float) * (size_t)ansplit * nb * nr);
-  int rc = ensure_buffer(c, &c.ws.mixed, &c.ws.mixedbytes, xb + pb + wb + ab);
+  const size_t bb = nsplit > 1 ? al(sizeof(double) * (size_t)P * nb) : 0;
+  int rc = ensure_buffer(c, &c.ws.mixed, &c.ws.mixedbytes, xb + pb + wb + ab + bb);
   if (rc) return rc;
   unsigned char* w0 = static_cast<unsigned char*>(c.ws.mixed);
   __nv_bfloat16* xs = reinterpret_cast<__nv_bfloat16*>(w0);
@@ -810,9 +837,19 @@ int gamma_apply_tc(Context& c, const Problem& p, const R* x, int nb, bool scaled
   rc = launch_gemm<NT>(c, bcal, P, xs, nb, kc, nsplit, ksplit, 0, part, nullptr, 0, HPSI_K_CALBEC);
   if (rc) return rc;
   const int n = P * nb;
-  HPSI_LAUNCH(c, HPSI_K_DSCALE,
-              (k_dscale_tc_r<NT><<<(n + 255) / 256, 256, 0, c.stream>>>(P, nb, nsplit, ka, part, p.d_rowptr, p.d_col,
-                                                                        p.d_dvalr, wa)));
+  if (nsplit > 1) {
+    double* becp = reinterpret_cast<double*>(w0 + xb + pb + wb + ab);
+    const size_t nel = (size_t)P * nb;
+    HPSI_LAUNCH(c, HPSI_K_DSCALE, (k_sum_partials<<<(int)std::min<size_t>(8 * c.sm_count, (nel + 255) / 256), 256, 0,
+                                                    c.stream>>>(nel, nsplit, part, becp)));
+    HPSI_LAUNCH(c, HPSI_K_DSCALE,
+                (k_dscale_tc_r<NT, double><<<(n + 255) / 256, 256, 0, c.stream>>>(P, nb, 1, ka, becp, p.d_rowptr,
+                                                                                  p.d_col, p.d_dvalr, wa)));
+  } else {
+    HPSI_LAUNCH(c, HPSI_K_DSCALE,
+                (k_dscale_tc_r<NT, float><<<(n + 255) / 256, 256, 0, c.stream>>>(P, nb, 1, ka, part, p.d_rowptr,
+                                                                                 p.d_col, p.d_dvalr, wa)));
+  }
   rc = launch_gemm<NT>(c, wa, nb, badd, nr, ka, ansplit, aksplit, 0, apart, nullptr, 0, HPSI_K_ADDVUS);
   if (rc) return rc;
   cudaError_t e = cudaGetLastError();

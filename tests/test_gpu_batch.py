@@ -44,16 +44,22 @@ def test_batch_kpoints(lib, precision):
     xs = [torch.from_numpy(workloads.psi0(p.lattice, k, m, p.nbnd, p.psi_seed + i)).cuda()
           for i, (k, m) in enumerate(zip(p.kpts, ms))]
     each = _run_each(ctx, xs)
+    B.hpsi_set_option(ctx, B.HPSI_OPT_BATCH_NL, 1)   # mixed: the per-item tensor-core nonlocal form
     first = _run_batch(ctx, xs)      # eager + capture
     second = _run_batch(ctx, xs)     # graph replay
     for i in range(len(xs)):
         assert np.array_equal(first[i], each[i]) and np.array_equal(second[i], each[i])
+    B.hpsi_set_option(ctx, B.HPSI_OPT_BATCH_NL, 0)
+    B.hpsi_kernel_stats(ctx, -1, reset=True)
+    third = _run_batch(ctx, xs)      # mixed: the float64 nonlocal term over the batch (8 projectors each)
+    assert B.hpsi_kernel_stats(ctx, B.KERNELS.index("calbec") + B.HPSI_K_AT_FP64)[0] == 1
     tol = 1e-12 if precision == 0 else 1e-5
     for i in (0, 7, 15):
         ref = oracle.hamiltonian.hpsi(p.lattice, p.kpts[i], ms[i], p.fft, vr, betas[i], d, xs[i].cpu().numpy())
-        assert np.linalg.norm(first[i] - ref) / np.linalg.norm(ref) < tol
+        for y in (first, third):
+            assert np.linalg.norm(y[i] - ref) / np.linalg.norm(ref) < tol
     n, _ = B.hpsi_kernel_stats(ctx, -2)
-    assert n == 3 * 16 * p.nbnd
+    assert n == 4 * 16 * p.nbnd   # the per-item pass and three batches
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -73,14 +79,18 @@ def test_batch_cells(lib, precision):
     xs = [torch.from_numpy(workloads.psi0(c.lattice, c.kpts[0], m, c.nbnd, c.psi_seed)).cuda()
           for c, m in zip(cells, ms)]
     each = _run_each(ctx, xs)
+    B.hpsi_set_option(ctx, B.HPSI_OPT_BATCH_NL, 1)   # mixed: the per-item tensor-core nonlocal form
     first = _run_batch(ctx, xs)
     second = _run_batch(ctx, xs)
     for i in range(32):
         assert np.array_equal(first[i], each[i]) and np.array_equal(second[i], each[i])
+    B.hpsi_set_option(ctx, B.HPSI_OPT_BATCH_NL, 0)
+    third = _run_batch(ctx, xs)      # mixed: the float64 nonlocal term over the batch
     for i in (0, 5, 17, 31):
         c = cells[i]
         ref = oracle.hamiltonian.hpsi(c.lattice, c.kpts[0], ms[i], c.fft, vrs[i], betas[i], ds[i], xs[i].cpu().numpy())
-        assert np.linalg.norm(first[i] - ref) / np.linalg.norm(ref) < (1e-12 if precision == 0 else 1e-5)
+        for y in (first, third):
+            assert np.linalg.norm(y[i] - ref) / np.linalg.norm(ref) < (1e-12 if precision == 0 else 1e-5)
 
 
 def test_batch_graph_invalidated_by_new_arguments(lib):
@@ -125,8 +135,7 @@ def test_batch_persistent_launch(lib, precision):
     per = _run_batch(ctx, xs)
     k = {name: B.hpsi_kernel_stats(ctx, i)[0] for i, name in enumerate(B.KERNELS)}
     assert k["batch"] == 1 and k["inv_zy"] == 0 and k["xvx_y"] == 0 and k["fwd_z"] == 0
-    if precision == 0:
-        assert k["calbec"] == 0 and k["addvus"] == 0
+    assert k["calbec"] == 0 and k["addvus"] == 0   # mixed too: 8 projectors, the float64 batched form
     B.hpsi_set_option(ctx, B.HPSI_OPT_PERSISTENT, 0)
     B.hpsi_kernel_stats(ctx, -1, reset=True)
     sep = _run_batch(ctx, xs)

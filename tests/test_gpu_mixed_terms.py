@@ -72,10 +72,12 @@ def test_mixed_terms(lib, cfg, nbnd, sel):
     assert e_loc < TOL_TERM and e_nl < TOL_TERM
 
 
-def test_mixed_batch_cells(lib):
-    """The 32 independent cells at mixed precision through hpsi_apply_batch: every item equals its own
-    hpsi_apply, and on four cells (H - T) psi matches the oracle's local + nonlocal terms element by
-    element."""
+@pytest.mark.parametrize("batch_nl", [1, 0])
+def test_mixed_batch_cells(lib, batch_nl):
+    """The 32 independent cells at mixed precision through hpsi_apply_batch, with the per-item
+    tensor-core nonlocal term (HPSI_OPT_BATCH_NL = 1: every item equals its own hpsi_apply) and with
+    the default float64 nonlocal term over the batch (these cells have 4-16 projectors); on four
+    cells (H - T) psi matches the oracle's local + nonlocal terms element by element."""
     import torch
     from paper_0906_2569_gb300 import binding as B
     cells = workloads.config4b()
@@ -88,13 +90,18 @@ def test_mixed_batch_cells(lib):
     xs = [torch.from_numpy(workloads.psi0(c.lattice, c.kpts[0], m, c.nbnd, c.psi_seed)).cuda()
           for c, m in zip(cells, ms)]
     ys = [torch.full_like(x, float("nan")) for x in xs]
+    B.hpsi_set_option(ctx, B.HPSI_OPT_BATCH_NL, batch_nl)
+    B.hpsi_kernel_stats(ctx, -1, reset=True)
     B.hpsi_apply_batch(ctx, list(range(32)), xs, ys)
     B.hpsi_sync(ctx)
+    nl64 = B.hpsi_kernel_stats(ctx, B.KERNELS.index("calbec") + B.HPSI_K_AT_FP64)[0]
+    assert nl64 == (1 if batch_nl == 0 else 0)
     for i, x in enumerate(xs):
         y = torch.full_like(x, float("nan"))
         B.hpsi_apply(ctx, i, x, y)
         B.hpsi_sync(ctx)
-        assert torch.equal(y, ys[i])
+        if batch_nl == 1:
+            assert torch.equal(y, ys[i])
     for i in (0, 5, 17, 31):
         c = cells[i]
         psi = xs[i].cpu().numpy()
