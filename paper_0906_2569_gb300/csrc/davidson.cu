@@ -437,177 +437,6 @@ static int canonical_orth(Context& c, DavHandles& h, const double2* x, int n, do
   return HPSI_OK;
 }
 
-static int davidson_run_mixed(Context& c, DavHandles& h, int ik, int nbnd, double tol, int maxiter, double2* psio,
-                              double* eig_out, int* iters_out, double* resnorm_out);
-
-int davidson_run(Context& c, int ik, int nbnd, double tol, int maxiter, double2* psio, double* eig_out, int* iters_out,
-                 double* resnorm_out) {
-  const Problem& p = c.probs[ik];
-  DavHandles* h = reinterpret_cast<DavHandles*>(c.blas);
-  if (!h) {
-    h = new DavHandles();
-    c.blas = h;
-    BCK(cublasCreate(&h->blas), "cublasCreate");
-    BCK(cusolverDnCreate(&h->solver), "cusolverDnCreate");
-  }
-  BCK(cublasSetStream(h->blas, c.stream), "cublasSetStream");
-  BCK(cusolverDnSetStream(h->solver, c.stream), "cusolverDnSetStream");
-  if (c.precision == HPSI_MIXED) return davidson_run_mixed(c, *h, ik, nbnd, tol, maxiter, psio, eig_out, iters_out,
-                                                          resnorm_out);
-  int rc = alloc_work(c, *h, p.npw, nbnd, false);
-  if (rc) return rc;
-  DavWork& w = h->wk;
-  const int npw = p.npw, N = nbnd, mmax = w.mmax;
-  const size_t vb = sizeof(double2) * (size_t)npw;
-
-  // phi[0:N] <- orthonormalised initial guess
-  int nk = 0;
-  rc = canonical_orth(c, *h, psio, N, w.phi, &nk, 1e-12, true);
-  if (rc) return rc;
-  if (nk < N) return fail(c, HPSI_EINVAL, "davidson_solve: initial guess is linearly dependent");
-  rc = apply_device(c, ik, w.phi, w.hphi, N);
-  if (rc) return rc;
-  int m = N;
-  BCK(cublasZgemm(h->blas, CUBLAS_OP_C, CUBLAS_OP_N, m, m, npw, &kOne, Z(w.phi), npw, Z(w.hphi), npw, &kZero,
-                  Z(w.hsub), mmax),
-      "zgemm H_sub");
-  std::vector<double> rn(N), ev(N);
-  std::vector<int> uidx(N);
-  int it = 0;
-  bool converged = false;
-  // Ritz vectors a restart keeps: the N wanted ones, or with thick restart up to half the basis
-  const int keep = c.thick_restart ? std::max(N, std::min(w.kmax, mmax / 2)) : N;
-  for (;;) {
-    // a restart is certain once m + N > mmax unless bands converge: solve for the kept vectors now
-    const int nev = m + N > mmax ? std::min(m, keep) : N;
-    rc = lowest_eigh(c, *h, w.hsub, mmax, m, nev);
-    if (rc) return rc;
-    // Ritz vectors psi = phi C[:, 0:N], hpsi = hphi C[:, 0:N]
-    BCK(cublasZgemm(h->blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, N, m, &kOne, Z(w.phi), npw, Z(w.evec), m, &kZero,
-                    Z(w.psi), npw),
-        "zgemm Ritz vectors");
-    BCK(cublasZgemm(h->blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, N, m, &kOne, Z(w.hphi), npw, Z(w.evec), m, &kZero,
-                    Z(w.hpsi), npw),
-        "zgemm H Ritz vectors");
-    DCK(cudaMemcpyAsync(w.eps, w.w, sizeof(double) * N, cudaMemcpyDeviceToDevice, c.stream), "eps copy");
-    HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_residual<<<N, 256, 0, c.stream>>>(npw, w.psi, w.hpsi, w.eps, w.t, w.rnorm)));
-    DCK(cudaGetLastError(), "residual kernel");
-    DCK(cudaMemcpyAsync(rn.data(), w.rnorm, sizeof(double) * N, cudaMemcpyDeviceToHost, c.stream), "norm copy");
-    DCK(cudaMemcpyAsync(ev.data(), w.eps, sizeof(double) * N, cudaMemcpyDeviceToHost, c.stream), "eig copy");
-    DCK(cudaStreamSynchronize(c.stream), "davidson iteration");
-    rc = check_device_error(c);
-    if (rc) return rc;
-    int nc = 0;
-    double rmax = 0.0;
-    for (int i = 0; i < N; ++i) {
-      rmax = std::max(rmax, rn[i]);
-      if (!(rn[i] <= tol)) uidx[nc++] = i;
-    }
-    if (nc == 0) {
-      converged = true;
-      break;
-    }
-    if (it >= maxiter) break;
-    ++it;
-    if (m + nc > mmax) {
-      // restart from the lowest nev Ritz vectors: phi <- phi C[:, 0:nev], hphi <- hphi C[:, 0:nev]
-      if (nev == N) {
-        DCK(cudaMemcpyAsync(w.phi, w.psi, vb * N, cudaMemcpyDeviceToDevice, c.stream), "restart copy");
-        DCK(cudaMemcpyAsync(w.hphi, w.hpsi, vb * N, cudaMemcpyDeviceToDevice, c.stream), "restart copy");
-      } else {
-        for (double2* src : {w.phi, w.hphi}) {
-          BCK(cublasZgemm(h->blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, nev, m, &kOne, Z(src), npw, Z(w.evec), m, &kZero,
-                          Z(w.rst), npw),
-              "zgemm restart");
-          DCK(cudaMemcpyAsync(src, w.rst, vb * nev, cudaMemcpyDeviceToDevice, c.stream), "restart copy");
-        }
-      }
-      m = nev;
-      BCK(cublasZgemm(h->blas, CUBLAS_OP_C, CUBLAS_OP_N, m, m, npw, &kOne, Z(w.phi), npw, Z(w.hphi), npw, &kZero,
-                      Z(w.hsub), mmax),
-          "zgemm H_sub restart");
-    }
-    DCK(cudaMemcpyAsync(w.idx, uidx.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, c.stream), "index copy");
-    // corrections into phi[m : m+nc] (t holds the residuals)
-    double2* tnew = w.phi + (size_t)m * npw;
-    const int eshift = c.opt_shift == 1 ? N - 1 : -1;
-    HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_precondition<<<nc, 256, 0, c.stream>>>(npw, w.idx, w.t, p.d_hdiag, w.eps, c.opt_tau, eshift, tnew)));
-    DCK(cudaGetLastError(), "precondition kernel");
-    // block Gram-Schmidt against phi[0:m]; a second pass only where the first cancelled (kReorth)
-    auto project = [&]() -> int {
-      BCK(cublasZgemm(h->blas, CUBLAS_OP_C, CUBLAS_OP_N, m, nc, npw, &kOne, Z(w.phi), npw, Z(tnew), npw, &kZero,
-                      Z(w.small), m),
-          "zgemm projection");
-      BCK(cublasZgemm(h->blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, nc, m, &kMinusOne, Z(w.phi), npw, Z(w.small), m, &kOne,
-                      Z(tnew), npw),
-          "zgemm projection update");
-      return HPSI_OK;
-    };
-    std::vector<double> cn(nc);
-    auto norms = [&]() -> int {
-      HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_norm2<<<nc, 256, 0, c.stream>>>(npw, tnew, w.cn2)));
-      DCK(cudaMemcpyAsync(cn.data(), w.cn2, sizeof(double) * nc, cudaMemcpyDeviceToHost, c.stream), "norm copy");
-      DCK(cudaStreamSynchronize(c.stream), "correction norms");
-      return HPSI_OK;
-    };
-    for (int round = 0; round < 2; ++round) {
-      rc = project();
-      if (rc) return rc;
-      bool second = round == 1 || !c.reorth_test;
-      if (!second) {
-        rc = norms();
-        if (rc) return rc;
-        for (int j = 0; j < nc; ++j)
-          if (!(cn[j] >= kReorth)) second = true;
-      }
-      if (second) {
-        rc = project();
-        if (rc) return rc;
-      }
-      if (round == 1) break;
-      if (second) {
-        rc = norms();
-        if (rc) return rc;
-      }
-      // corrections that lie in the basis are replaced by their raw residuals
-      std::vector<int> col;
-      for (int j = 0; j < nc; ++j)
-        if (!(cn[j] >= kCollapse)) col.push_back(j);
-      if (col.empty()) break;
-      DCK(cudaMemcpyAsync(w.idx2, col.data(), sizeof(int) * col.size(), cudaMemcpyHostToDevice, c.stream),
-          "index copy");
-      HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_fallback<<<(int)col.size(), 256, 0, c.stream>>>(npw, w.idx2, w.idx, w.t, w.rnorm, tnew)));
-      DCK(cudaGetLastError(), "fallback kernel");
-    }
-    // orthonormalise the block itself (w.t is free now: residuals were consumed)
-    int nkeep = 0;
-    rc = canonical_orth(c, *h, tnew, nc, w.t, &nkeep, kDropAbs, false);
-    if (rc) return rc;
-    if (nkeep == 0) {
-      // nothing new can be added: the residuals lie in the basis up to rounding
-      converged = rmax <= tol;
-      break;
-    }
-    DCK(cudaMemcpyAsync(tnew, w.t, vb * nkeep, cudaMemcpyDeviceToDevice, c.stream), "basis copy");
-    rc = apply_device(c, ik, tnew, w.hphi + (size_t)m * npw, nkeep);
-    if (rc) return rc;
-    // new columns of H_sub: phi[0:m+nkeep]^H hphi[m:m+nkeep]  (upper triangle is what zheevd reads)
-    BCK(cublasZgemm(h->blas, CUBLAS_OP_C, CUBLAS_OP_N, m + nkeep, nkeep, npw, &kOne, Z(w.phi), npw,
-                    Z(w.hphi + (size_t)m * npw), npw, &kZero, Z(w.hsub + (size_t)m * mmax), mmax),
-        "zgemm H_sub columns");
-    m += nkeep;
-  }
-  DCK(cudaMemcpyAsync(psio, w.psi, vb * N, cudaMemcpyDeviceToDevice, c.stream), "eigenvector copy");
-  DCK(cudaStreamSynchronize(c.stream), "davidson end");
-  for (int i = 0; i < N; ++i) eig_out[i] = ev[i];
-  if (resnorm_out)
-    for (int i = 0; i < N; ++i) resnorm_out[i] = rn[i];
-  if (iters_out) *iters_out = it;
-  if (!converged) return fail(c, HPSI_ENOTCONV, "davidson_solve: not converged within maxiter");
-  return HPSI_OK;
-}
-
-
 // ---- mixed path: float32 basis, float64 small problems, norms and Rayleigh quotients ----------
 
 namespace {
@@ -1044,60 +873,346 @@ static int hsub_columns32(Context& c, DavHandles& h, int rows, int col0, int nco
   return HPSI_OK;
 }
 
-static int davidson_run_mixed(Context& c, DavHandles& h, int ik, int nbnd, double tol, int maxiter, double2* psio,
-                              double* eig_out, int* iters_out, double* resnorm_out) {
-  const Problem& p = c.probs[ik];
-  int rc = alloc_work(c, h, p.npw, nbnd, true);
-  if (rc) return rc;
-  DavWork& w = h.wk;
-  const int npw = p.npw, N = nbnd, mmax = w.mmax;
-  const size_t vb = sizeof(float2) * (size_t)npw;
-  HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_cvt_d2f<<<(npw + 255) / 256, 256, 0, c.stream>>>(npw, p.d_hdiag, w.hdiag32)));
-  // subspace GEMMs: float32 on the CUDA cores, or float32 emulated with bf16 tensor-core products
-  BCK(cublasSetMathMode(h.blas, c.fp32_gemm == 1 ? CUBLAS_FP32_EMULATED_BF16X9_MATH : CUBLAS_DEFAULT_MATH),
-      "cublasSetMathMode");
-  if (c.fp32_gemm == 1) {
-    BCK(cublasSetEmulationStrategy(h.blas, CUBLAS_EMULATION_STRATEGY_EAGER), "cublasSetEmulationStrategy");
-    // finite operands (a NaN would surface in the float64 residual norms): no special-value passes
-    BCK(cublasSetEmulationSpecialValuesSupport(h.blas, CUDA_EMULATION_SPECIAL_VALUES_SUPPORT_NONE),
-        "cublasSetEmulationSpecialValuesSupport");
+// ---- the Davidson iteration, one loop for both precisions ----------------------------------------
+// The loop below is written once; a precision policy supplies the basis arithmetic:
+//   Fp64Ops  - complex128 basis, cuBLAS ZGEMMs and the float64 kernels; the eigenvalues are the
+//              Ritz values of the last Rayleigh-Ritz step;
+//   MixedOps - complex64 basis (float32 or emulated-float32 GEMMs), float64 small problems and
+//              norms; hard locking, stall detection and a float64 Rayleigh quotient at exit.
+// Both keep the basis orthonormal, restart from the wanted (or, thick, up to half the basis limit
+// of the lowest) Ritz vectors and grow it by the orthonormalised preconditioned residuals of the
+// unconverged bands (App. A.2.1).
+
+struct Fp64Ops {
+  using V = double2;
+  static constexpr bool kMixed = false;
+  Context& c;
+  DavHandles& h;
+  DavWork& w;
+  const int ik, npw;
+  Fp64Ops(Context& c_, DavHandles& h_, int ik_) : c(c_), h(h_), w(h_.wk), ik(ik_), npw(h_.wk.npw) {}
+  V* phi() { return w.phi; }
+  V* hphi() { return w.hphi; }
+  V* psi() { return w.psi; }
+  V* t() { return w.t; }
+  void invalidate() {}
+  // phi[0:N] <- the orthonormalised start
+  int start(const double2* psio, int N, int* nk) { return canonical_orth(c, h, psio, N, w.phi, nk, 1e-12, true); }
+  int apply(const V* x, V* hx, int nb) { return apply_device(c, ik, x, hx, nb); }
+  // H_sub[0:rows, col0:col0+ncol] = phi[0:rows]^H hphi[col0:col0+ncol]
+  int hsub(int rows, int col0, int ncol) {
+    BCK(cublasZgemm(h.blas, CUBLAS_OP_C, CUBLAS_OP_N, rows, ncol, npw, &kOne, Z(w.phi), npw,
+                    Z(w.hphi + (size_t)col0 * npw), npw, &kZero, Z(w.hsub + (size_t)col0 * w.mmax), w.mmax),
+        "zgemm H_sub columns");
+    return HPSI_OK;
   }
-  struct MathReset {
-    cublasHandle_t b;
-    ~MathReset() {
-      cublasSetMathMode(b, CUBLAS_DEFAULT_MATH);
-      cublasSetEmulationSpecialValuesSupport(b, CUDA_EMULATION_SPECIAL_VALUES_SUPPORT_DEFAULT);
+  // out = src[0:m] times the leading n columns of the reduced eigenvectors (ld m)
+  int rotate(const V* src, int m, int n, V* out) {
+    BCK(cublasZgemm(h.blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, n, m, &kOne, Z(src), npw, Z(w.evec), m, &kZero, Z(out), npw),
+        "zgemm Ritz vectors");
+    return HPSI_OK;
+  }
+  // Ritz vectors psi = phi C[:, 0:NA], hpsi = hphi C[:, 0:NA]; residuals into t, norms into rnorm
+  int ritz_residuals(int m, int NA) {
+    int rc = rotate(w.phi, m, NA, w.psi);
+    if (!rc) rc = rotate(w.hphi, m, NA, w.hpsi);
+    if (rc) return rc;
+    DCK(cudaMemcpyAsync(w.eps, w.w, sizeof(double) * NA, cudaMemcpyDeviceToDevice, c.stream), "eps copy");
+    HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_residual<<<NA, 256, 0, c.stream>>>(npw, w.psi, w.hpsi, w.eps, w.t, w.rnorm)));
+    DCK(cudaGetLastError(), "residual kernel");
+    return HPSI_OK;
+  }
+  // restart: phi, hphi <- the first keep Ritz vectors (psi, hpsi)
+  int restart_copy(int keep) {
+    DCK(cudaMemcpyAsync(w.phi, w.psi, sizeof(V) * (size_t)keep * npw, cudaMemcpyDeviceToDevice, c.stream), "restart copy");
+    DCK(cudaMemcpyAsync(w.hphi, w.hpsi, sizeof(V) * (size_t)keep * npw, cudaMemcpyDeviceToDevice, c.stream),
+        "restart copy");
+    return HPSI_OK;
+  }
+  // thick restart: phi, hphi <- phi, hphi times the reduced eigenvectors sel (the lowest keep here:
+  // the float64 solve locks nothing)
+  int restart_rotate(int m, int keep, const std::vector<int>& sel) {
+    for (int j = 0; j < keep; ++j)
+      if (sel[j] != j) return fail(c, HPSI_EINVAL, "davidson_solve: internal restart selection error");
+    for (V* src : {w.phi, w.hphi}) {
+      int rc = rotate(src, m, keep, w.rst);
+      if (rc) return rc;
+      DCK(cudaMemcpyAsync(src, w.rst, sizeof(V) * (size_t)keep * npw, cudaMemcpyDeviceToDevice, c.stream),
+          "restart copy");
     }
-  } math_reset{h.blas};
-  w.phi_split.invalidate();
-  w.hphi_split.invalidate();
-  w.tci.invalidate();
-  const bool tc = c.fp32_gemm == 3;
-  // phi32[0:N] <- orthonormalised initial guess
-  HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
-              (k_cvt_64_32<<<grid_of((size_t)N * npw), 256, 0, c.stream>>>((size_t)N * npw, psio, w.t32)));
+    return HPSI_OK;
+  }
+  int precondition(int nc, int eshift, V* tnew) {
+    HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_precondition<<<nc, 256, 0, c.stream>>>(npw, w.idx, w.t, c.probs[ik].d_hdiag,
+                                                                              w.eps, c.opt_tau, eshift, tnew)));
+    DCK(cudaGetLastError(), "precondition kernel");
+    return HPSI_OK;
+  }
+  // tnew[0:nc] -= phi[0:m] (phi[0:m]^H tnew)
+  int project(int m, int /*locked*/, int nc, V* tnew) {
+    BCK(cublasZgemm(h.blas, CUBLAS_OP_C, CUBLAS_OP_N, m, nc, npw, &kOne, Z(w.phi), npw, Z(tnew), npw, &kZero,
+                    Z(w.small), m),
+        "zgemm projection");
+    BCK(cublasZgemm(h.blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, nc, m, &kMinusOne, Z(w.phi), npw, Z(w.small), m, &kOne,
+                    Z(tnew), npw),
+        "zgemm projection update");
+    return HPSI_OK;
+  }
+  int norm2(int nc, const V* tnew) {
+    HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_norm2<<<nc, 256, 0, c.stream>>>(npw, tnew, w.cn2)));
+    return HPSI_OK;
+  }
+  int fallback(int ncol, V* tnew) {
+    HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_fallback<<<ncol, 256, 0, c.stream>>>(npw, w.idx2, w.idx, w.t, w.rnorm, tnew)));
+    DCK(cudaGetLastError(), "fallback kernel");
+    return HPSI_OK;
+  }
+  int orth(const V* x, int n, int* nkeep) { return canonical_orth(c, h, x, n, w.t, nkeep, kDropAbs, false); }
+  // eigenvalues: the last Ritz values; eigenvectors: the last Ritz vectors
+  int finish(int N, int /*locked*/, double2* psio, std::vector<double>& ev, std::vector<double>& rn, double* eig_out,
+             double* resnorm_out) {
+    DCK(cudaMemcpyAsync(psio, w.psi, sizeof(V) * (size_t)N * npw, cudaMemcpyDeviceToDevice, c.stream),
+        "eigenvector copy");
+    DCK(cudaMemcpyAsync(ev.data(), w.eps, sizeof(double) * N, cudaMemcpyDeviceToHost, c.stream), "eig copy");
+    DCK(cudaStreamSynchronize(c.stream), "davidson end");
+    for (int i = 0; i < N; ++i) {
+      eig_out[i] = ev[i];
+      if (resnorm_out) resnorm_out[i] = rn[i];
+    }
+    return HPSI_OK;
+  }
+  // the locked-vector and refresh operations exist only in the mixed form
+  int lock(int, int, const int*) { return HPSI_OK; }
+  int restart_gather(int, const std::vector<int>&) { return fail(c, HPSI_EINVAL, "davidson_solve: no locking in float64"); }
+  int refresh(int, int) { return HPSI_OK; }
+  int keep_active(int) { return HPSI_OK; }
+};
+
+struct MixedOps {
+  using V = float2;
+  static constexpr bool kMixed = true;
+  Context& c;
+  DavHandles& h;
+  DavWork& w;
+  const int ik, npw;
+  const bool tc;   // subspace GEMMs through the bf16-split tensor-core products
+  MixedOps(Context& c_, DavHandles& h_, int ik_)
+      : c(c_), h(h_), w(h_.wk), ik(ik_), npw(h_.wk.npw), tc(c_.fp32_gemm == 3) {}
+  // subspace GEMMs: float32 on the CUDA cores, or float32 emulated with bf16 tensor-core products
+  // (cuBLAS math mode, restored by the destructor)
+  int setup() {
+    HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
+                (k_cvt_d2f<<<(npw + 255) / 256, 256, 0, c.stream>>>(npw, c.probs[ik].d_hdiag, w.hdiag32)));
+    BCK(cublasSetMathMode(h.blas, c.fp32_gemm == 1 ? CUBLAS_FP32_EMULATED_BF16X9_MATH : CUBLAS_DEFAULT_MATH),
+        "cublasSetMathMode");
+    if (c.fp32_gemm == 1) {
+      BCK(cublasSetEmulationStrategy(h.blas, CUBLAS_EMULATION_STRATEGY_EAGER), "cublasSetEmulationStrategy");
+      // finite operands (a NaN would surface in the float64 residual norms): no special-value passes
+      BCK(cublasSetEmulationSpecialValuesSupport(h.blas, CUDA_EMULATION_SPECIAL_VALUES_SUPPORT_NONE),
+          "cublasSetEmulationSpecialValuesSupport");
+    }
+    invalidate();
+    return HPSI_OK;
+  }
+  ~MixedOps() {
+    cublasSetMathMode(h.blas, CUBLAS_DEFAULT_MATH);
+    cublasSetEmulationSpecialValuesSupport(h.blas, CUDA_EMULATION_SPECIAL_VALUES_SUPPORT_DEFAULT);
+  }
+  V* phi() { return w.phi32; }
+  V* hphi() { return w.hphi32; }
+  V* psi() { return w.psi32; }
+  V* t() { return w.t32; }
+  // the cached bf16 splits of the basis are stale once its rows change
+  void invalidate() {
+    w.phi_split.invalidate();
+    w.hphi_split.invalidate();
+    w.tci.invalidate();
+  }
+  int start(const double2* psio, int N, int* nk) {
+    HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
+                (k_cvt_64_32<<<grid_of((size_t)N * npw), 256, 0, c.stream>>>((size_t)N * npw, psio, w.t32)));
+    return canonical_orth32(c, h, w.t32, N, w.phi32, nk, 1e-12, true);
+  }
+  int apply(const V* x, V* hx, int nb) { return apply32(c, w, ik, x, hx, nb); }
+  int hsub(int rows, int col0, int ncol) { return hsub_columns32(c, h, rows, col0, ncol); }
+  int ritz_residuals(int m, int NA) {
+    HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
+                (k_mat_64_to_32<<<(m * NA + 255) / 256, 256, 0, c.stream>>>(m, NA, w.evec, m, w.small32, m)));
+    int rc;
+    if (tc) {
+      rc = w.sg.a_b(c, h.blas, npw, NA, m, w.phi_split, w.phi32, npw, w.small32, m, 1.f, 0.f, w.psi32, npw);
+      if (!rc) rc = w.sg.a_b(c, h.blas, npw, NA, m, w.hphi_split, w.hphi32, npw, w.small32, m, 1.f, 0.f, w.hpsi32, npw);
+    } else {
+      rc = tall_gemm32(c, h, npw, NA, m, w.phi32, w.small32, m, w.psi32);
+      if (!rc) rc = tall_gemm32(c, h, npw, NA, m, w.hphi32, w.small32, m, w.hpsi32);
+    }
+    if (rc) return rc;
+    DCK(cudaMemcpyAsync(w.eps, w.w, sizeof(double) * NA, cudaMemcpyDeviceToDevice, c.stream), "eps copy");
+    HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
+                (k_residual32<<<NA, 1024, 0, c.stream>>>(npw, w.psi32, w.hpsi32, w.eps, w.t32, w.rnorm)));
+    return HPSI_OK;
+  }
+  // the nl converged Ritz vectors sel (device list in idx2) join lock32 after the locked ones
+  int lock(int locked, int nl, const int* sel) {
+    DCK(cudaMemcpyAsync(w.idx2, sel, sizeof(int) * nl, cudaMemcpyHostToDevice, c.stream), "lock index copy");
+    HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_gather_rows32<<<nl, 256, 0, c.stream>>>(
+                                        npw, w.idx2, w.psi32, w.lock32 + (size_t)locked * npw, nullptr, nullptr)));
+    return HPSI_OK;
+  }
+  int restart_copy(int keep) {
+    const size_t b = sizeof(V) * (size_t)keep * npw;
+    DCK(cudaMemcpyAsync(w.phi32, w.psi32, b, cudaMemcpyDeviceToDevice, c.stream), "restart copy");
+    DCK(cudaMemcpyAsync(w.hphi32, w.hpsi32, b, cudaMemcpyDeviceToDevice, c.stream), "restart copy");
+    return HPSI_OK;
+  }
+  // restart from Ritz vectors already formed in psi32 / hpsi32, selected by sel
+  int restart_gather(int keep, const std::vector<int>& sel) {
+    DCK(cudaMemcpyAsync(w.sel, sel.data(), sizeof(int) * keep, cudaMemcpyHostToDevice, c.stream), "restart index copy");
+    HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
+                (k_gather_rows32<<<keep, 256, 0, c.stream>>>(npw, w.sel, w.psi32, w.phi32, w.hpsi32, w.hphi32)));
+    return HPSI_OK;
+  }
+  // thick restart: phi32 and hphi32 times the selected reduced eigenvectors
+  int restart_rotate(int m, int keep, const std::vector<int>& sel) {
+    DCK(cudaMemcpyAsync(w.sel, sel.data(), sizeof(int) * keep, cudaMemcpyHostToDevice, c.stream), "restart index copy");
+    HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_select_columns32<<<grid_of((size_t)m * keep), 256, 0, c.stream>>>(
+                                        m, keep, w.sel, w.evec, w.ysub32)));
+    for (int pass = 0; pass < 2; ++pass) {
+      float2* src = pass == 0 ? w.phi32 : w.hphi32;
+      int rc;
+      if (tc)
+        rc = w.sg.a_b(c, h.blas, npw, keep, m, pass == 0 ? w.phi_split : w.hphi_split, src, npw, w.ysub32, m, 1.f,
+                      0.f, w.rst32, npw);
+      else
+        rc = tall_gemm32(c, h, npw, keep, m, src, w.ysub32, m, w.rst32);
+      if (rc) return rc;
+      DCK(cudaMemcpyAsync(src, w.rst32, sizeof(V) * (size_t)keep * npw, cudaMemcpyDeviceToDevice, c.stream),
+          "restart copy");
+    }
+    return HPSI_OK;
+  }
+  // H applied afresh to the keep restart vectors (replacing stored products that drifted)
+  int refresh(int keep, int N) {
+    for (int b = 0; b < keep; b += N) {
+      const int rc = apply32(c, w, ik, w.phi32 + (size_t)b * npw, w.hphi32 + (size_t)b * npw, std::min(N, keep - b));
+      if (rc) return rc;
+    }
+    return HPSI_OK;
+  }
+  // psi32 keeps the na active Ritz vectors in the new numbering for an exit before the next step
+  int keep_active(int na) {
+    DCK(cudaMemcpyAsync(w.psi32, w.phi32, sizeof(V) * (size_t)na * npw, cudaMemcpyDeviceToDevice, c.stream),
+        "active copy");
+    return HPSI_OK;
+  }
+  int precondition(int nc, int eshift, V* tnew) {
+    HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_precondition32<<<nc, 1024, 0, c.stream>>>(npw, w.idx, w.t32, w.hdiag32, w.eps,
+                                                                                c.opt_tau, eshift, tnew)));
+    return HPSI_OK;
+  }
+  // Block Gram-Schmidt against [lock32, phi32] (the locked vectors are orthogonal to the basis, so
+  // projecting them out first is the same as projecting out the union in one block).
+  int project(int m, int locked, int nc, V* tnew) {
+    if (locked > 0) {
+      BCK(cgemm32(c, h.blas, CUBLAS_OP_C, CUBLAS_OP_N, locked, nc, npw, &cOne, Cf(w.lock32), npw, Cf(tnew), npw,
+                  &cZero, Cf(w.small32), locked),
+          "cgemm lock projection");
+      BCK(cgemm32(c, h.blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, nc, locked, &cMinusOne, Cf(w.lock32), npw, Cf(w.small32),
+                  locked, &cOne, Cf(tnew), npw),
+          "cgemm lock projection update");
+    }
+    if (tc) {
+      int r = w.sg.ah_b(c, h.blas, m, nc, npw, w.phi_split, w.phi32, npw, tnew, npw, 1.f, 0.f, w.small32, nullptr, m);
+      if (!r) r = w.sg.a_b(c, h.blas, npw, nc, m, w.phi_split, w.phi32, npw, w.small32, m, -1.f, 1.f, tnew, npw);
+      return r;
+    }
+    if (c.fp32_gemm == 4) {
+      const int r = tc_inner32(c, w.tci, true, w.mmax, w.phi32, m, tnew, nc, npw, nullptr, w.small32, m);
+      if (r) return r;
+    } else {
+      BCK(cgemm32(c, h.blas, CUBLAS_OP_C, CUBLAS_OP_N, m, nc, npw, &cOne, Cf(w.phi32), npw, Cf(tnew), npw, &cZero,
+                  Cf(w.small32), m),
+          "cgemm projection");
+    }
+    BCK(cgemm32(c, h.blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, nc, m, &cMinusOne, Cf(w.phi32), npw, Cf(w.small32), m, &cOne,
+                Cf(tnew), npw),
+        "cgemm projection update");
+    return HPSI_OK;
+  }
+  int norm2(int nc, const V* tnew) {
+    HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_norm2_32<<<nc, 1024, 0, c.stream>>>(npw, tnew, w.cn2)));
+    return HPSI_OK;
+  }
+  int fallback(int ncol, V* tnew) {
+    HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
+                (k_fallback32<<<ncol, 1024, 0, c.stream>>>(npw, w.idx2, w.idx, w.t32, w.rnorm, tnew)));
+    return HPSI_OK;
+  }
+  int orth(const V* x, int n, int* nkeep) { return canonical_orth32(c, h, x, n, w.t32, nkeep, kDropAbs, false); }
+  // float64 Rayleigh quotients of the Ritz vectors (locked ones first) with a fresh H|psi>, by
+  // default with float64 projections and D: the eigenvalue error is then second order in the
+  // eigenvector error left by the mixed iterations.  Bands are returned in ascending order.
+  int finish(int N, int locked, double2* psio, std::vector<double>& ev, std::vector<double>& rn, double* eig_out,
+             double* resnorm_out) {
+    const size_t n = (size_t)N * npw, nl = (size_t)locked * npw;
+    if (locked > 0)
+      HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_cvt_32_64<<<grid_of(nl), 256, 0, c.stream>>>(nl, w.lock32, w.in64)));
+    HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
+                (k_cvt_32_64<<<grid_of(n - nl), 256, 0, c.stream>>>(n - nl, w.psi32, w.in64 + nl)));
+    final_precision_begin(c);
+    int rc = apply_device(c, ik, w.in64, w.out64, N);
+    final_precision_end(c);
+    if (rc) return rc;
+    HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_rayleigh<<<N, 1024, 0, c.stream>>>(npw, w.in64, w.out64, w.eps, w.rnorm)));
+    DCK(cudaMemcpyAsync(ev.data(), w.eps, sizeof(double) * N, cudaMemcpyDeviceToHost, c.stream), "eig copy");
+    DCK(cudaMemcpyAsync(rn.data(), w.rnorm, sizeof(double) * N, cudaMemcpyDeviceToHost, c.stream), "norm copy");
+    DCK(cudaStreamSynchronize(c.stream), "davidson end");
+    rc = check_device_error(c);
+    if (rc) return rc;
+    std::vector<int> perm(N);
+    for (int i = 0; i < N; ++i) perm[i] = i;
+    std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return ev[a] < ev[b]; });
+    DCK(cudaMemcpyAsync(w.idx, perm.data(), sizeof(int) * N, cudaMemcpyHostToDevice, c.stream), "perm copy");
+    HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_gather_rows<<<N, 256, 0, c.stream>>>(npw, w.idx, w.in64, psio)));
+    DCK(cudaStreamSynchronize(c.stream), "davidson end");
+    for (int i = 0; i < N; ++i) {
+      eig_out[i] = ev[perm[i]];
+      if (resnorm_out) resnorm_out[i] = rn[perm[i]];
+    }
+    return HPSI_OK;
+  }
+};
+
+template <class Ops>
+static int davidson_loop(Context& c, DavHandles& h, Ops& ops, int N, double tol, int maxiter, double2* psio,
+                         double* eig_out, int* iters_out, double* resnorm_out) {
+  using V = typename Ops::V;
+  DavWork& w = h.wk;
+  const int npw = w.npw, mmax = w.mmax;
+  const size_t vb = sizeof(V) * (size_t)npw;
+  // phi[0:N] <- orthonormalised initial guess, hphi = H phi, H_sub = phi^H hphi
   int nk = 0;
-  rc = canonical_orth32(c, h, w.t32, N, w.phi32, &nk, 1e-12, true);
+  int rc = ops.start(psio, N, &nk);
   if (rc) return rc;
   if (nk < N) return fail(c, HPSI_EINVAL, "davidson_solve: initial guess is linearly dependent");
-  rc = apply32(c, w, ik, w.phi32, w.hphi32, N);
+  rc = ops.apply(ops.phi(), ops.hphi(), N);
   if (rc) return rc;
   int m = N;
-  rc = hsub_columns32(c, h, m, 0, m);
+  rc = ops.hsub(m, 0, m);
   if (rc) return rc;
-  std::vector<double> rn(N), ev(N);
-  std::vector<int> uidx(N), lsel, asel;
+  std::vector<double> rn(N), ev(N), cn;
+  std::vector<int> uidx(N), lsel, asel, col;
   int it = 0;
   bool converged = false;
-  // Hard locking: the first kL bands are frozen in lock32; the reduced basis phi32[0:m] spans only
-  // the active part of the search space (orthogonal to lock32) and the Rayleigh-Ritz step asks it
-  // for the NA = N - kL lowest pairs.  Without locking kL stays 0 and this is the plain block form.
+  // Hard locking (mixed form only): the first kL bands are frozen in lock32; the reduced basis
+  // phi[0:m] spans only the active part of the search space (orthogonal to lock32) and the
+  // Rayleigh-Ritz step asks it for the NA = N - kL lowest pairs.  Without locking kL stays 0.
   int kL = 0;
   // Ritz vectors a restart keeps: the active ones, or with thick restart up to half the basis limit.
-  // A thick-restarted vector is a float32 rotation of the basis whose stored H|phi> is the same
-  // rotation of the stored products; the two drift apart by rounding amplified by the largest
-  // eigenvalue of H, so a solve whose largest residual stops falling (kStall iterations without a
-  // 10% drop) goes on with plain restarts.
+  // In the mixed form a thick-restarted vector is a float32 rotation of the basis whose stored
+  // H|phi> is the same rotation of the stored products; the two drift apart by rounding amplified
+  // by the largest eigenvalue of H, so a solve whose largest residual stops falling (kStall
+  // iterations without a 10% drop) goes on with plain restarts, then with H applied afresh.
   bool thick = c.thick_restart != 0;
   bool refresh = false;
   int stall = 0;
@@ -1115,38 +1230,26 @@ static int davidson_run_mixed(Context& c, DavHandles& h, int ik, int nbnd, doubl
     if (m + NA > mlim) nev = std::max(NA, restart_size(kL, m));
     rc = lowest_eigh(c, h, w.hsub, mmax, m, nev);
     if (rc) return rc;
-    HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
-                (k_mat_64_to_32<<<(m * NA + 255) / 256, 256, 0, c.stream>>>(m, NA, w.evec, m, w.small32, m)));
-    if (tc) {
-      rc = w.sg.a_b(c, h.blas, npw, NA, m, w.phi_split, w.phi32, npw, w.small32, m, 1.f, 0.f, w.psi32, npw);
-      if (!rc) rc = w.sg.a_b(c, h.blas, npw, NA, m, w.hphi_split, w.hphi32, npw, w.small32, m, 1.f, 0.f, w.hpsi32, npw);
-      if (rc) return rc;
-    } else {
-      rc = tall_gemm32(c, h, npw, NA, m, w.phi32, w.small32, m, w.psi32);
-      if (!rc) rc = tall_gemm32(c, h, npw, NA, m, w.hphi32, w.small32, m, w.hpsi32);
-      if (rc) return rc;
-    }
-    DCK(cudaMemcpyAsync(w.eps, w.w, sizeof(double) * NA, cudaMemcpyDeviceToDevice, c.stream), "eps copy");
-    HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_residual32<<<NA, 1024, 0, c.stream>>>(npw, w.psi32, w.hpsi32, w.eps, w.t32, w.rnorm)));
+    rc = ops.ritz_residuals(m, NA);
+    if (rc) return rc;
     DCK(cudaMemcpyAsync(rn.data(), w.rnorm, sizeof(double) * NA, cudaMemcpyDeviceToHost, c.stream), "norm copy");
     DCK(cudaStreamSynchronize(c.stream), "davidson iteration");
     rc = check_device_error(c);
     if (rc) return rc;
     int nc = 0;
-    for (int i = 0; i < NA; ++i)
+    double rmax = 0.0;
+    for (int i = 0; i < NA; ++i) {
+      rmax = std::max(rmax, rn[i]);
       if (!(rn[i] <= tol)) uidx[nc++] = i;
+    }
     if (nc == 0) {
       converged = true;
       break;
     }
     if (it >= maxiter) break;
     ++it;
-    {
-      // kStall iterations without a 10% drop of the largest residual: first switch thick restarts
-      // off; if it stalls again, restart with H applied afresh to the kept vectors, which replaces
-      // stored products that have drifted from H times the stored (rotated) vectors
-      double rmax = 0.0;
-      for (int i = 0; i < NA; ++i) rmax = std::max(rmax, rn[i]);
+    lsel.clear();
+    if constexpr (Ops::kMixed) {
       if (rmax < 0.9 * best) {
         best = rmax;
         stall = 0;
@@ -1155,25 +1258,23 @@ static int davidson_run_mixed(Context& c, DavHandles& h, int ik, int nbnd, doubl
         if (thick) thick = false;
         else refresh = true;
       }
-    }
-    // Lock: converged Ritz vectors move to lock32.  t32, eps and rnorm keep this iteration's
-    // numbering, which uidx indexes.
-    lsel.clear();
-    if (c.locking) {
-      if (c.locking == 1) {
-        while ((int)lsel.size() < NA && rn[lsel.size()] <= tol) lsel.push_back((int)lsel.size());
-      } else {
-        for (int i = 0; i < NA; ++i)
-          if (rn[i] <= tol) lsel.push_back(i);
+      // Lock: converged Ritz vectors move to lock32.  t, eps and rnorm keep this iteration's
+      // numbering, which uidx indexes.
+      if (c.locking) {
+        if (c.locking == 1) {
+          while ((int)lsel.size() < NA && rn[lsel.size()] <= tol) lsel.push_back((int)lsel.size());
+        } else {
+          for (int i = 0; i < NA; ++i)
+            if (rn[i] <= tol) lsel.push_back(i);
+        }
+        if ((int)lsel.size() < std::max(1, (int)std::ceil(c.lock_batch * NA))) lsel.clear();
       }
-      if ((int)lsel.size() < std::max(1, (int)std::ceil(c.lock_batch * NA))) lsel.clear();
     }
     const int nl = (int)lsel.size();
     if (nl > 0 || m + nc > mlim || refresh) {
       if (nl > 0) {
-        DCK(cudaMemcpyAsync(w.idx2, lsel.data(), sizeof(int) * nl, cudaMemcpyHostToDevice, c.stream), "lock index copy");
-        HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_gather_rows32<<<nl, 256, 0, c.stream>>>(
-                                            npw, w.idx2, w.psi32, w.lock32 + (size_t)kL * npw, nullptr, nullptr)));
+        rc = ops.lock(kL, nl, lsel.data());
+        if (rc) return rc;
       }
       // restart from the lowest Ritz vectors that are not locked
       const int kL2 = kL + nl, na = N - kL2;
@@ -1187,101 +1288,52 @@ static int davidson_run_mixed(Context& c, DavHandles& h, int ik, int nbnd, doubl
         asel.push_back(i);
       }
       if (asel.back() < NA) {
-        // every kept vector is an active Ritz vector already formed in psi32 / hpsi32
-        if (nl == 0) {
-          DCK(cudaMemcpyAsync(w.phi32, w.psi32, vb * keep, cudaMemcpyDeviceToDevice, c.stream), "restart copy");
-          DCK(cudaMemcpyAsync(w.hphi32, w.hpsi32, vb * keep, cudaMemcpyDeviceToDevice, c.stream), "restart copy");
-        } else {
-          DCK(cudaMemcpyAsync(w.sel, asel.data(), sizeof(int) * keep, cudaMemcpyHostToDevice, c.stream), "restart index copy");
-          HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_gather_rows32<<<keep, 256, 0, c.stream>>>(npw, w.sel, w.psi32, w.phi32,
-                                                                                       w.hpsi32, w.hphi32)));
-        }
+        // every kept vector is an active Ritz vector already formed in psi / hpsi
+        rc = nl == 0 ? ops.restart_copy(keep) : ops.restart_gather(keep, asel);
       } else {
-        // thick restart: the kept Ritz vectors are phi32 and hphi32 times the selected reduced eigenvectors
+        // thick restart: the kept Ritz vectors are phi and hphi times the selected reduced eigenvectors
         if (asel.back() >= nev) {
           rc = lowest_eigh(c, h, w.hsub, mmax, m, asel.back() + 1);
           if (rc) return rc;
         }
-        DCK(cudaMemcpyAsync(w.sel, asel.data(), sizeof(int) * keep, cudaMemcpyHostToDevice, c.stream), "restart index copy");
-        HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_select_columns32<<<grid_of((size_t)m * keep), 256, 0, c.stream>>>(
-                                            m, keep, w.sel, w.evec, w.ysub32)));
-        for (int pass = 0; pass < 2; ++pass) {
-          float2* src = pass == 0 ? w.phi32 : w.hphi32;
-          if (tc) {
-            rc = w.sg.a_b(c, h.blas, npw, keep, m, pass == 0 ? w.phi_split : w.hphi_split, src, npw, w.ysub32, m, 1.f,
-                          0.f, w.rst32, npw);
-            if (rc) return rc;
-          } else {
-            rc = tall_gemm32(c, h, npw, keep, m, src, w.ysub32, m, w.rst32);
-            if (rc) return rc;
-          }
-          DCK(cudaMemcpyAsync(src, w.rst32, vb * keep, cudaMemcpyDeviceToDevice, c.stream), "restart copy");
-        }
+        rc = ops.restart_rotate(m, keep, asel);
       }
+      if (rc) return rc;
       if (refresh) {
-        for (int b = 0; b < keep; b += N) {
-          rc = apply32(c, w, ik, w.phi32 + (size_t)b * npw, w.hphi32 + (size_t)b * npw, std::min(N, keep - b));
-          if (rc) return rc;
-        }
+        rc = ops.refresh(keep, N);
+        if (rc) return rc;
         refresh = false;
       }
-      // psi32 keeps the active Ritz vectors in the new numbering for an exit before the next step
-      if (nl > 0) DCK(cudaMemcpyAsync(w.psi32, w.phi32, vb * na, cudaMemcpyDeviceToDevice, c.stream), "active copy");
+      if (nl > 0) {
+        rc = ops.keep_active(na);
+        if (rc) return rc;
+      }
       kL = kL2;
-      w.phi_split.invalidate();
-      w.hphi_split.invalidate();
-      w.tci.invalidate();
+      ops.invalidate();
       m = keep;
-      rc = hsub_columns32(c, h, m, 0, m);
+      rc = ops.hsub(m, 0, m);
       if (rc) return rc;
     }
     DCK(cudaMemcpyAsync(w.idx, uidx.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, c.stream), "index copy");
-    float2* tnew = w.phi32 + (size_t)m * npw;
-    const int eshift = c.opt_shift == 1 ? NA - 1 : -1;
-    HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_precondition32<<<nc, 1024, 0, c.stream>>>(npw, w.idx, w.t32, w.hdiag32, w.eps,
-                                                                                c.opt_tau, eshift, tnew)));
-    // Block Gram-Schmidt against [lock32, phi32] (the locked vectors are orthogonal to the basis, so
-    // projecting them out first is the same as projecting out the union in one block).
-    auto project = [&]() -> int {
-      if (kL > 0) {
-        BCK(cgemm32(c, h.blas, CUBLAS_OP_C, CUBLAS_OP_N, kL, nc, npw, &cOne, Cf(w.lock32), npw, Cf(tnew), npw, &cZero,
-                    Cf(w.small32), kL),
-            "cgemm lock projection");
-        BCK(cgemm32(c, h.blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, nc, kL, &cMinusOne, Cf(w.lock32), npw, Cf(w.small32), kL,
-                    &cOne, Cf(tnew), npw),
-            "cgemm lock projection update");
-      }
-      if (tc) {
-        int r = w.sg.ah_b(c, h.blas, m, nc, npw, w.phi_split, w.phi32, npw, tnew, npw, 1.f, 0.f, w.small32, nullptr, m);
-        if (!r) r = w.sg.a_b(c, h.blas, npw, nc, m, w.phi_split, w.phi32, npw, w.small32, m, -1.f, 1.f, tnew, npw);
-        return r;
-      }
-      if (c.fp32_gemm == 4) {
-        const int r = tc_inner32(c, w.tci, true, mmax, w.phi32, m, tnew, nc, npw, nullptr, w.small32, m);
-        if (r) return r;
-      } else {
-        BCK(cgemm32(c, h.blas, CUBLAS_OP_C, CUBLAS_OP_N, m, nc, npw, &cOne, Cf(w.phi32), npw, Cf(tnew), npw, &cZero,
-                    Cf(w.small32), m),
-            "cgemm projection");
-      }
-      BCK(cgemm32(c, h.blas, CUBLAS_OP_N, CUBLAS_OP_N, npw, nc, m, &cMinusOne, Cf(w.phi32), npw, Cf(w.small32), m,
-                  &cOne, Cf(tnew), npw),
-          "cgemm projection update");
-      return HPSI_OK;
-    };
-    std::vector<double> cn(nc);
+    // corrections into phi[m : m+nc] (t holds the residuals)
+    V* tnew = ops.phi() + (size_t)m * npw;
+    rc = ops.precondition(nc, c.opt_shift == 1 ? NA - 1 : -1, tnew);
+    if (rc) return rc;
+    cn.resize(nc);
     auto norms = [&]() -> int {
-      HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_norm2_32<<<nc, 1024, 0, c.stream>>>(npw, tnew, w.cn2)));
+      int r = ops.norm2(nc, tnew);
+      if (r) return r;
       DCK(cudaMemcpyAsync(cn.data(), w.cn2, sizeof(double) * nc, cudaMemcpyDeviceToHost, c.stream), "norm copy");
       DCK(cudaStreamSynchronize(c.stream), "correction norms");
       return HPSI_OK;
     };
+    // Block Gram-Schmidt against the basis.  The corrections enter with unit norm.  One pass leaves
+    // them orthogonal to the basis up to rounding relative to their norm before it; a second pass
+    // only helps a column that the first cancelled (kept less than kReorth of its squared norm), so
+    // with HPSI_OPT_REORTH_TEST it runs only then.
     for (int round = 0; round < 2; ++round) {
-      rc = project();
+      rc = ops.project(m, kL, nc, tnew);
       if (rc) return rc;
-      // The corrections enter with unit norm.  One pass leaves them orthogonal to the basis up to
-      // rounding relative to their norm before it; a second pass only helps a column that the first
-      // cancelled (kept less than half its squared norm), so it runs only then.
       bool second = round == 1 || !c.reorth_test;
       if (!second) {
         rc = norms();
@@ -1290,7 +1342,7 @@ static int davidson_run_mixed(Context& c, DavHandles& h, int ik, int nbnd, doubl
           if (!(cn[j] >= kReorth)) second = true;
       }
       if (second) {
-        rc = project();
+        rc = ops.project(m, kL, nc, tnew);
         if (rc) return rc;
       }
       if (round == 1) break;
@@ -1298,56 +1350,59 @@ static int davidson_run_mixed(Context& c, DavHandles& h, int ik, int nbnd, doubl
         rc = norms();
         if (rc) return rc;
       }
-      std::vector<int> col;
+      // corrections that lie in the basis are replaced by their raw residuals
+      col.clear();
       for (int j = 0; j < nc; ++j)
         if (!(cn[j] >= kCollapse)) col.push_back(j);
       if (col.empty()) break;
       DCK(cudaMemcpyAsync(w.idx2, col.data(), sizeof(int) * col.size(), cudaMemcpyHostToDevice, c.stream),
           "index copy");
-      HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
-                  (k_fallback32<<<(int)col.size(), 1024, 0, c.stream>>>(npw, w.idx2, w.idx, w.t32, w.rnorm, tnew)));
+      rc = ops.fallback((int)col.size(), tnew);
+      if (rc) return rc;
     }
+    // orthonormalise the block itself (t is free now: the residuals were consumed)
     int nkeep = 0;
-    rc = canonical_orth32(c, h, tnew, nc, w.t32, &nkeep, kDropAbs, false);
+    rc = ops.orth(tnew, nc, &nkeep);
     if (rc) return rc;
-    if (nkeep == 0) break;
-    DCK(cudaMemcpyAsync(tnew, w.t32, vb * nkeep, cudaMemcpyDeviceToDevice, c.stream), "basis copy");
-    rc = apply32(c, w, ik, tnew, w.hphi32 + (size_t)m * npw, nkeep);
+    if (nkeep == 0) break;   // nothing new can be added: the residuals lie in the basis up to rounding
+    DCK(cudaMemcpyAsync(tnew, ops.t(), vb * nkeep, cudaMemcpyDeviceToDevice, c.stream), "basis copy");
+    rc = ops.apply(tnew, ops.hphi() + (size_t)m * npw, nkeep);
     if (rc) return rc;
-    rc = hsub_columns32(c, h, m + nkeep, m, nkeep);
+    // new columns of H_sub: phi[0:m+nkeep]^H hphi[m:m+nkeep] (the upper triangle is what is read)
+    rc = ops.hsub(m + nkeep, m, nkeep);
     if (rc) return rc;
     m += nkeep;
   }
-  // float64 Rayleigh quotients of the Ritz vectors with a fresh H|psi>, by default with the
-  // float64 operator: the eigenvalue error is then second order in the eigenvector error
-  const size_t n = (size_t)N * npw, nl = (size_t)kL * npw;
-  if (kL > 0)
-    HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_cvt_32_64<<<grid_of(nl), 256, 0, c.stream>>>(nl, w.lock32, w.in64)));
-  HPSI_LAUNCH(c, HPSI_K_DAVIDSON,
-              (k_cvt_32_64<<<grid_of(n - nl), 256, 0, c.stream>>>(n - nl, w.psi32, w.in64 + nl)));
-  final_precision_begin(c);
-  rc = apply_device(c, ik, w.in64, w.out64, N);
-  final_precision_end(c);
+  rc = ops.finish(N, kL, psio, ev, rn, eig_out, resnorm_out);
   if (rc) return rc;
-  HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_rayleigh<<<N, 1024, 0, c.stream>>>(npw, w.in64, w.out64, w.eps, w.rnorm)));
-  DCK(cudaMemcpyAsync(ev.data(), w.eps, sizeof(double) * N, cudaMemcpyDeviceToHost, c.stream), "eig copy");
-  DCK(cudaMemcpyAsync(rn.data(), w.rnorm, sizeof(double) * N, cudaMemcpyDeviceToHost, c.stream), "norm copy");
-  DCK(cudaStreamSynchronize(c.stream), "davidson end");
-  rc = check_device_error(c);
-  if (rc) return rc;
-  std::vector<int> perm(N);
-  for (int i = 0; i < N; ++i) perm[i] = i;
-  std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return ev[a] < ev[b]; });
-  DCK(cudaMemcpyAsync(w.idx, perm.data(), sizeof(int) * N, cudaMemcpyHostToDevice, c.stream), "perm copy");
-  HPSI_LAUNCH(c, HPSI_K_DAVIDSON, (k_gather_rows<<<N, 256, 0, c.stream>>>(npw, w.idx, w.in64, psio)));
-  DCK(cudaStreamSynchronize(c.stream), "davidson end");
-  for (int i = 0; i < N; ++i) {
-    eig_out[i] = ev[perm[i]];
-    if (resnorm_out) resnorm_out[i] = rn[perm[i]];
-  }
   if (iters_out) *iters_out = it;
   if (!converged) return fail(c, HPSI_ENOTCONV, "davidson_solve: not converged within maxiter");
   return HPSI_OK;
+}
+
+int davidson_run(Context& c, int ik, int nbnd, double tol, int maxiter, double2* psio, double* eig_out, int* iters_out,
+                 double* resnorm_out) {
+  const Problem& p = c.probs[ik];
+  DavHandles* h = reinterpret_cast<DavHandles*>(c.blas);
+  if (!h) {
+    h = new DavHandles();
+    c.blas = h;
+    BCK(cublasCreate(&h->blas), "cublasCreate");
+    BCK(cusolverDnCreate(&h->solver), "cusolverDnCreate");
+  }
+  BCK(cublasSetStream(h->blas, c.stream), "cublasSetStream");
+  BCK(cusolverDnSetStream(h->solver, c.stream), "cusolverDnSetStream");
+  const bool mixed = c.precision == HPSI_MIXED;
+  int rc = alloc_work(c, *h, p.npw, nbnd, mixed);
+  if (rc) return rc;
+  if (!mixed) {
+    Fp64Ops ops(c, *h, ik);
+    return davidson_loop(c, *h, ops, nbnd, tol, maxiter, psio, eig_out, iters_out, resnorm_out);
+  }
+  MixedOps ops(c, *h, ik);
+  rc = ops.setup();
+  if (rc) return rc;
+  return davidson_loop(c, *h, ops, nbnd, tol, maxiter, psio, eig_out, iters_out, resnorm_out);
 }
 
 }  // namespace hpsi
