@@ -318,8 +318,9 @@ HPSI_API int davidson_solve_gamma(hpsi_ctx* ctx, int ik, int nbnd, double tol, i
  * hpsi_apply_batch -- H psi for several problems (k-points or cells) in one launch sequence:
  * for i < nitem: hpsi_out[i] = H(prob[i]) psi_in[i] with nbnd[i] bands.  Device pointers only.
  * Items whose cubic box has register-codelet kernels share one launch of each local-potential
- * kernel per box edge (blockIdx.z runs over the items), and the nonlocal term follows (float64: one
- * launch per kernel class over all items; HPSI_MIXED: the tensor-core form per item).  With
+ * kernel per box edge (blockIdx.z runs over the items), and the nonlocal term follows: one launch
+ * per kernel class over all items in float64, which a mixed context also takes when every item has
+ * at most 64 projectors (HPSI_OPT_BATCH_NL), else the tensor-core form per item.  With
  * HPSI_OPT_PERSISTENT = 1, and every item on those kernels, each box edge (<= 32 items) is instead
  * one persistent cooperative launch whose CTAs take tiles from per-phase work lists: the
  * z-scatter/inverse transforms, the plane transforms with x V, the forward transforms and gather,
