@@ -702,6 +702,7 @@ int local_batch_persistent(Context& c, int nitem, const int* prob, const int* nb
       a.nb = nbnd[i];
       a.kchunk = kc[i];
       a.nsplit = ns[i];
+      a.tp = CB_TP;
       a.tilesp = (p.nproj + CB_TP - 1) / CB_TP;
       a.tilesb = (a.nb + CB_TB - 1) / CB_TB;
       a.gtiles = (p.npw + AV_TG - 1) / AV_TG;

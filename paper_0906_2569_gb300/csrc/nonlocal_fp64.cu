@@ -44,7 +44,12 @@ __global__ void __launch_bounds__(256) k_calbec64_batch(const __grid_constant__ 
   const int l = blockIdx.x - bt.off_cal[i];
   const int tp = l % a.tilesp, r = l / a.tilesp;
   __shared__ double2 sm[CB_SMEM];
-  calbec_tile(a.npw, a.nproj, a.nb, a.kchunk, a.beta, a.psi, a.part, tp, r % a.tilesb, r / a.tilesb, sm);
+  if (a.tp == 8)
+    calbec_tile_t<8>(a.npw, a.nproj, a.nb, a.kchunk, a.beta, a.psi, a.part, tp, r % a.tilesb, r / a.tilesb, sm);
+  else if (a.tp == 16)
+    calbec_tile_t<16>(a.npw, a.nproj, a.nb, a.kchunk, a.beta, a.psi, a.part, tp, r % a.tilesb, r / a.tilesb, sm);
+  else
+    calbec_tile_t<CB_TP>(a.npw, a.nproj, a.nb, a.kchunk, a.beta, a.psi, a.part, tp, r % a.tilesb, r / a.tilesb, sm);
 }
 
 __global__ void __launch_bounds__(256) k_dscale64_batch(const __grid_constant__ NlBatch bt) {
@@ -471,7 +476,8 @@ int nonlocal_batch_fp64(Context& c, int nitem, const int* prob, const int* nbnd,
       a.nb = nbnd[i];
       a.kchunk = kc[j];
       a.nsplit = ns[j];
-      a.tilesp = (p.nproj + CB_TP - 1) / CB_TP;
+      a.tp = calbec_tp(p.nproj);
+      a.tilesp = (p.nproj + a.tp - 1) / a.tp;
       a.tilesb = (a.nb + CB_TB - 1) / CB_TB;
       a.gtiles = (p.npw + AV_TG - 1) / AV_TG;
       a.beta = p.d_beta;

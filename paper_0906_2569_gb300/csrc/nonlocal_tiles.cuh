@@ -24,51 +24,74 @@ constexpr int CB_TK = 32;   // G per shared-memory tile
 
 constexpr int CB_SMEM = (CB_TP + CB_TB) * (CB_TK + 1);   // double2 entries of shared memory
 
-// part[split][b][p] = sum_{G in split} conj(beta[p][G]) psi[b][G]; sm: CB_SMEM entries of shared
-// memory
-__device__ __forceinline__ void calbec_tile(int npw, int nproj, int nb, int kchunk, const double2* __restrict__ beta,
-                                            const double2* __restrict__ psi, double2* __restrict__ part, int tp,
-                                            int tb, int split, double2* sm) {
-  auto sb = reinterpret_cast<double2 (*)[CB_TK + 1]>(sm);                       // [CB_TP][CB_TK + 1]
-  auto sp = reinterpret_cast<double2 (*)[CB_TK + 1]>(sm + CB_TP * (CB_TK + 1));  // [CB_TB][CB_TK + 1]
-  const int p0 = tp * CB_TP, b0 = tb * CB_TB;
+// part[split][b][p] = sum_{G in split} conj(beta[p][G]) psi[b][G] for the TP projectors of tile tp
+// and the CB_TB bands of tile tb; sm: CB_SMEM entries of shared memory.  TP = 32: 2 x 2 outputs per
+// thread; TP = 16 and 8 (items with few projectors): 1 x 2 and 1 x 1, so that fewer rows of the
+// tile are padding.  Each output is the same chain of FMAs over G in order whatever TP is.
+template <int TP>
+__device__ __forceinline__ void calbec_tile_t(int npw, int nproj, int nb, int kchunk, const double2* __restrict__ beta,
+                                              const double2* __restrict__ psi, double2* __restrict__ part, int tp,
+                                              int tb, int split, double2* sm) {
+  constexpr int TX = TP < 16 ? TP : 16;        // threads along the projectors
+  constexpr int TY = 256 / TX;                 // threads along the bands
+  constexpr int PI = TP / TX, BJ = CB_TB / TY; // outputs per thread
+  static_assert(TP <= CB_TP && PI >= 1 && BJ >= 1 && TX * TY == 256, "calbec tile shape");
+  auto sb = reinterpret_cast<double2 (*)[CB_TK + 1]>(sm);                    // [TP][CB_TK + 1]
+  auto sp = reinterpret_cast<double2 (*)[CB_TK + 1]>(sm + TP * (CB_TK + 1));  // [CB_TB][CB_TK + 1]
+  const int p0 = tp * TP, b0 = tb * CB_TB;
   const int gbeg = split * kchunk, gend = min(npw, gbeg + kchunk);
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // tx -> p, ty -> b
-  double2 acc[2][2];
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;   // tx -> p, ty -> b
+  double2 acc[PI][BJ];
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < PI; ++i)
 #pragma unroll
-    for (int j = 0; j < 2; ++j) acc[i][j] = make_double2(0.0, 0.0);
+    for (int j = 0; j < BJ; ++j) acc[i][j] = make_double2(0.0, 0.0);
   for (int g0 = gbeg; g0 < gend; g0 += CB_TK) {
-    for (int i = threadIdx.x; i < CB_TP * CB_TK; i += 256) {
+    for (int i = threadIdx.x; i < TP * CB_TK; i += 256) {
       const int r = i / CB_TK, cc = i % CB_TK;
       const int g = g0 + cc;
       sb[r][cc] = (p0 + r < nproj && g < gend) ? beta[(size_t)(p0 + r) * npw + g] : make_double2(0.0, 0.0);
+    }
+    for (int i = threadIdx.x; i < CB_TB * CB_TK; i += 256) {
+      const int r = i / CB_TK, cc = i % CB_TK;
+      const int g = g0 + cc;
       sp[r][cc] = (b0 + r < nb && g < gend) ? psi[(size_t)(b0 + r) * npw + g] : make_double2(0.0, 0.0);
     }
     __syncthreads();
 #pragma unroll 4
     for (int kk = 0; kk < CB_TK; ++kk) {
-      const double2 x0 = sb[tx][kk], x1 = sb[tx + 16][kk];
-      const double2 y0 = sp[ty][kk], y1 = sp[ty + 16][kk];
+      double2 x[PI], y[BJ];
+#pragma unroll
+      for (int i = 0; i < PI; ++i) x[i] = sb[tx + TX * i][kk];
+#pragma unroll
+      for (int j = 0; j < BJ; ++j) y[j] = sp[ty + TY * j][kk];
       // acc += conj(x) * y as four fused multiply-adds per complex product (written out so that
       // no separate multiply or add reaches the float64 pipe)
-      cmac_conj(acc[0][0], x0, y0);
-      cmac_conj(acc[0][1], x0, y1);
-      cmac_conj(acc[1][0], x1, y0);
-      cmac_conj(acc[1][1], x1, y1);
+#pragma unroll
+      for (int i = 0; i < PI; ++i)
+#pragma unroll
+        for (int j = 0; j < BJ; ++j) cmac_conj(acc[i][j], x[i], y[j]);
     }
     __syncthreads();
   }
   double2* out = part + (size_t)split * nb * nproj;
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < PI; ++i)
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int p = p0 + tx + 16 * i, b = b0 + ty + 16 * j;
+    for (int j = 0; j < BJ; ++j) {
+      const int p = p0 + tx + TX * i, b = b0 + ty + TY * j;
       if (p < nproj && b < nb) out[(size_t)b * nproj + p] = acc[i][j];
     }
 }
+
+__device__ __forceinline__ void calbec_tile(int npw, int nproj, int nb, int kchunk, const double2* __restrict__ beta,
+                                            const double2* __restrict__ psi, double2* __restrict__ part, int tp,
+                                            int tb, int split, double2* sm) {
+  calbec_tile_t<CB_TP>(npw, nproj, nb, kchunk, beta, psi, part, tp, tb, split, sm);
+}
+
+// projectors per calbec tile for an item with nproj projectors
+inline int calbec_tp(int nproj) { return nproj <= 8 ? 8 : (nproj <= 16 ? 16 : CB_TP); }
 
 
 // w[b][p] = sum_{q in row p of D} D_pq sum_s part[s][b][q]
@@ -155,6 +178,7 @@ constexpr int kNlBatch = 32;
 
 struct NlItem {
   int npw, nproj, nb, kchunk, nsplit, tilesp, tilesb, gtiles;
+  int tp;   // projectors per calbec tile (8, 16 or 32; 32 in the persistent launch)
   const double2* beta;
   const double2* psi;
   double2* hpsi;

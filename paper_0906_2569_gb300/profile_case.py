@@ -19,6 +19,11 @@ a solve, the library's and cuBLAS's, falls inside the bracket.
 With ``--eigh-real N`` the eigenproblem of order N is real symmetric (hpsi_eigh_lowest_sym);
 ``--df`` runs its reduction in double-float arithmetic (HPSI_OPT_EIGH_DF = 2).
 
+With ``--batch c4a`` (the 16 k-points of the fcc cell) or ``--batch c4b`` (the 32 cells) it runs
+hpsi_apply_batch on every item at the chosen precision: two warm-up batches (the first one eager,
+then the captured graph), then ``--reps`` bracketed graph replays.  ``--batch-nl`` sets
+HPSI_OPT_BATCH_NL and ``--persistent`` HPSI_OPT_PERSISTENT.
+
 With ``--cg B`` it runs the band-by-band CG eigensolver on the first B bands of the cell named by
 ``--config`` in float64 (residual 1e-8, at most ``--cg-maxiter`` steps per band): one warm-up solve,
 then one bracketed solve.  Every CG step's launches (three single-CTA kernels, the Gram-Schmidt
@@ -49,6 +54,9 @@ def main():
     ap.add_argument("--tol", type=float, default=0.0)
     ap.add_argument("--eigh-real", type=int, default=0)
     ap.add_argument("--df", action="store_true")
+    ap.add_argument("--batch", default="", choices=["", "c4a", "c4b"])
+    ap.add_argument("--batch-nl", type=int, default=0)
+    ap.add_argument("--persistent", type=int, default=0)
     args = ap.parse_args()
     import torch
     import workloads
@@ -61,6 +69,9 @@ def main():
         return
     if args.cg:
         cg_case(args, torch, workloads, B)
+        return
+    if args.batch:
+        batch_case(args, torch, workloads, B)
         return
     p = workloads.CONFIGS[args.config]()
     nb = args.nbnd or p.nbnd
@@ -159,6 +170,41 @@ def cg_case(args, torch, workloads, B):
     torch.cuda.synchronize()
     torch.cuda.profiler.stop()
     print("ok cg", args.config, args.cg, steps, float(eig.sum()))
+
+
+def batch_case(args, torch, workloads, B):
+    prec = B.HPSI_MIXED if args.precision == "mixed" else B.HPSI_FP64
+    stream = torch.cuda.current_stream().cuda_stream
+    if args.batch == "c4a":
+        p = workloads.config4a()
+        ms = [B.hpsi_gsphere(p.lattice, p.ecut, k) for k in p.kpts]
+        betas = [workloads.beta(p.lattice, p.atoms, k, m) for k, m in zip(p.kpts, ms)]
+        ctx = B.hpsi_setup(p.lattice, p.ecut, p.kpts, p.fft, workloads.vloc_r(p.lattice, p.atoms, p.fft), betas,
+                           workloads.dmat(len(p.atoms)), prec, stream)
+        xs = [torch.from_numpy(workloads.psi0(p.lattice, k, m, p.nbnd, p.psi_seed + i)).cuda()
+              for i, (k, m) in enumerate(zip(p.kpts, ms))]
+    else:
+        cells = workloads.config4b()
+        ms = [B.hpsi_gsphere(c.lattice, c.ecut, c.kpts[0]) for c in cells]
+        ctx = B.hpsi_setup_cells([c.lattice for c in cells], [c.ecut for c in cells], [c.fft for c in cells],
+                                 [workloads.vloc_r(c.lattice, c.atoms, c.fft) for c in cells],
+                                 [workloads.beta(c.lattice, c.atoms, c.kpts[0], m) for c, m in zip(cells, ms)],
+                                 [workloads.dmat(len(c.atoms)) for c in cells], prec, stream)
+        xs = [torch.from_numpy(workloads.psi0(c.lattice, c.kpts[0], m, c.nbnd, c.psi_seed)).cuda()
+              for c, m in zip(cells, ms)]
+    B.hpsi_set_option(ctx, B.HPSI_OPT_BATCH_NL, args.batch_nl)
+    B.hpsi_set_option(ctx, B.HPSI_OPT_PERSISTENT, args.persistent)
+    ys = [torch.empty_like(x) for x in xs]
+    items = list(range(len(xs)))
+    for _ in range(2):
+        B.hpsi_apply_batch(ctx, items, xs, ys)
+    B.hpsi_sync(ctx)
+    torch.cuda.profiler.start()
+    for _ in range(args.reps):
+        B.hpsi_apply_batch(ctx, items, xs, ys)
+    B.hpsi_sync(ctx)
+    torch.cuda.profiler.stop()
+    print("ok batch", args.batch, args.precision, len(xs), sum(int(x.shape[0]) for x in xs))
 
 
 if __name__ == "__main__":
