@@ -175,16 +175,19 @@ enum hpsi_kernel {
   HPSI_K_BATCH = 13,   /* hpsi_apply_batch: the persistent launch over every item (local term and,
                           in float64, the nonlocal term) */
   HPSI_K_COUNT = 14,
-  HPSI_K_AT_FP64 = 16  /* added to a class in hpsi_kernel_stats: only the launches made while H was
-                          applied in float64 (all of them in a float64 context; in a mixed context
-                          the final float64 application of davidson_solve) */
+  HPSI_K_AT_FP64 = 16  /* added to a class in hpsi_kernel_stats: only the launches made while H (or,
+                          for the nonlocal classes, its nonlocal term) was applied in float64: all
+                          of them in a float64 context; in a mixed context the final float64
+                          application of davidson_solve and the float64 nonlocal term of a batch
+                          (HPSI_OPT_BATCH_NL) */
 };
 
 enum hpsi_precision {
   HPSI_FP64 = 0,  /* every step in float64 / complex128 */
   HPSI_MIXED = 1  /* FFTs and x V(r) in float32, nonlocal contractions as split-bf16
                      tensor-core GEMMs with float32 accumulation (three bf16 terms per operand,
-                     six products, by default); kinetic term in float64.  davidson_solve keeps
+                     six products, by default; a batch of items with few projectors takes the
+                     float64 form, HPSI_OPT_BATCH_NL); kinetic term in float64.  davidson_solve keeps
                      its reduced basis in complex64 and does the small eigensolves, the residual
                      norms and the final Rayleigh quotients in float64 */
 };
